@@ -1,0 +1,383 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test names the passage it follows.  None of them re-types the oracle's
+own formula: they compare against closed forms (Slater-Condon), brute-force
+Fock-space linear algebra, library routines (expm, QR, eigh), published
+known-answer vectors, exact estimators and invariants.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+import scipy.stats
+
+import workloads
+from fock import Fock, eri_from_cholesky
+from oracle import afqmc, philox, scf
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def small_system(M=4, G=6, seed=77, scale=0.6, N=2, H0=0.3):
+    h1, L, _ = workloads.hamiltonian(M, G, seed)
+    L = L * scale
+    C, e, conv, _ = scf.rhf(h1, L, N, H0=H0)
+    assert conv
+    return h1, L, C, H0
+
+
+# ---------------------------------------------------------------- Philox ----
+def test_philox_known_answers():
+    """Philox4x32-10 reproduces the published known-answer vectors."""
+    rows = [ln.split() for ln in open(os.path.join(GOLDEN, "philox4x32_10_kat.txt"))
+            if ln.strip() and not ln.startswith("#")]
+    assert len(rows) == 3
+    for r in rows:
+        v = [int(x, 16) for x in r]
+        out = philox.philox4x32_10(*v[:6])
+        assert [int(o) for o in out] == v[6:]
+
+
+def test_gaussian_fields_moments():
+    """xi ~ N(0,1): moments J_n of Appendix A.2 (0 for odd n, (n-1)!! for even)
+    and a Kolmogorov-Smirnov test."""
+    xi = philox.gaussian_fields(12345, 7, np.arange(2000), 500).ravel()
+    n = xi.size
+    for k, jn in [(1, 0.0), (2, 1.0), (3, 0.0), (4, 3.0), (6, 15.0)]:
+        m = np.mean(xi ** k)
+        sd = math.sqrt(max(np.var(xi ** k), 1e-30) / n)
+        assert abs(m - jn) < 5 * sd, (k, m, jn, sd)
+    assert scipy.stats.kstest(xi, "norm").pvalue > 1e-3
+
+
+def test_fields_are_keyed_by_step_walker_gamma():
+    a = philox.gaussian_fields(1, 3, [0, 1, 2], 11)
+    b = philox.gaussian_fields(1, 3, [2], 11)
+    assert np.array_equal(a[2], b[0])
+    c = philox.gaussian_fields(1, 4, [2], 11)
+    assert not np.array_equal(b, c)
+    d = philox.gaussian_fields(2, 3, [2], 11)
+    assert not np.array_equal(b, d)
+    # an odd number of fields is the prefix of the next even count
+    e = philox.gaussian_fields(1, 3, [0, 1, 2], 12)
+    assert np.array_equal(a, e[:, :11])
+
+
+# ----------------------------------------------------- closed forms (P1-3) --
+def test_trial_energy_is_slater_condon():
+    """tau = 0: E_loc(Psi_T) equals the closed-shell Slater-Condon energy
+    2 sum_i h_ii + sum_ij [2 (ii|jj) - (ij|ji)] built from v_pqrs (Eq. bo_ham2,
+    v_pqrs = (pr|qs)); this fixes the 1/2 of Eq. localenergy3."""
+    w = workloads.config("c0")
+    h1, L, _ = w.hamiltonian()
+    C, e_scf, conv, _ = scf.rhf(h1, L, w.N)
+    st = afqmc.Setup(h1, L, C, H0=0.7)
+    v = eri_from_cholesky(L)
+    vmo = np.einsum("pqrs,pi,qj,rk,sl->ijkl", v, C, C, C, C)
+    hmo = C.T @ h1 @ C
+    n = w.N
+    e_sc = 0.7 + 2 * np.trace(hmo) + sum(
+        2 * vmo[i, j, i, j] - vmo[i, j, j, i] for i in range(n) for j in range(n))
+    assert abs(st.E_T - e_sc) < 1e-11 * abs(e_sc)
+    assert abs(st.E_T - (e_scf + 0.7)) < 1e-11 * abs(e_sc)
+
+
+def test_force_bias_vanishes_at_trial():
+    """With the mean-field background vbar = <v>_T (Sec. 2.4) the force bias of
+    Eq. fb is zero when the walker is the trial."""
+    w = workloads.config("c0")
+    h1, L, _ = w.hamiltonian()
+    C, _, _, _ = scf.rhf(h1, L, w.N)
+    st = afqmc.Setup(h1, L, C)
+    _, theta = afqmc.overlap(st, C[None].astype(complex))
+    t = afqmc.force_bias_trace(st, theta)[0]
+    assert np.max(np.abs(t - st.c)) < 1e-12 * np.max(np.abs(st.c))
+
+
+def test_cholesky_vectors_reconstruct_psd_eri():
+    """Eq. chol: V_(pr),(qs) = sum_g L_pr L_qs is symmetric positive
+    semi-definite and has the 8-fold symmetry of real orbitals."""
+    h1, L, _ = workloads.hamiltonian(5, 9, 3)
+    v = eri_from_cholesky(L)
+    V = v.transpose(0, 2, 1, 3).reshape(25, 25)  # rows (p,r), cols (q,s)
+    assert np.allclose(V, V.T)
+    assert np.min(np.linalg.eigvalsh(V)) > -1e-12
+    assert np.allclose(v, v.transpose(2, 1, 0, 3))  # p <-> r
+    assert np.allclose(v, v.transpose(1, 0, 3, 2))  # (pr) <-> (qs)
+
+
+# ----------------------------------------- brute-force Fock space (P4) -----
+@pytest.fixture(scope="module")
+def fock_case():
+    h1, L, C, H0 = small_system()
+    M, N = C.shape
+    F = Fock(M)
+    H = F.hamiltonian(h1, eri_from_cholesky(L), H0)
+    rng = np.random.default_rng(5)
+    phi = C + 0.3 * rng.standard_normal((M, N)) + 0.3j * rng.standard_normal((M, N))
+    return dict(h1=h1, L=L, C=C, H0=H0, F=F, H=H, phi=phi)
+
+
+def test_overlap_greens_function_and_energy_vs_fock(fock_case):
+    """Theorem 1.1 (overlap), Eq. precomputing2 (<v_g>_m = i t_g) and
+    Eq. localenergy2/3 against explicit Fock-space vectors."""
+    c = fock_case
+    F, H, phi = c["F"], c["H"], c["phi"]
+    st = afqmc.Setup(c["h1"], c["L"], c["C"], c["H0"], dt=0.01)
+    logdet, theta = afqmc.overlap(st, phi[None])
+    psiT, psi = F.determinant(c["C"]), F.determinant(phi)
+    ov = psiT.conj() @ psi
+    assert abs(np.exp(logdet[0]) - ov) < 1e-13 * abs(ov)
+    eloc = (psiT.conj() @ (H @ psi)) / ov
+    assert abs(afqmc.local_energy(st, theta)[0] - eloc) < 1e-12 * abs(eloc)
+    t = afqmc.force_bias_trace(st, theta)[0]
+    for g in range(c["L"].shape[0]):
+        vm = psiT.conj() @ (1j * F.one_body(c["L"][g]) @ psi) / ov
+        assert abs(vm - 1j * t[g]) < 1e-13
+
+
+def test_mean_field_rewrite_reproduces_hamiltonian(fock_case):
+    """Sec. 2.4: H = H0' + v0' - 1/2 sum_g (v_g - vbar_g)^2 as Fock operators,
+    with the oracle's v0' and H0' and vbar_g = <Psi_T|v_g|Psi_T>."""
+    c = fock_case
+    F = c["F"]
+    st = afqmc.Setup(c["h1"], c["L"], c["C"], c["H0"], dt=0.01)
+    psiT = F.determinant(c["C"])
+    I = np.eye(F.dim)
+    H = (st.H0p * I + F.one_body(st.v0p).toarray())
+    for g in range(c["L"].shape[0]):
+        vg = 1j * F.one_body(c["L"][g]).toarray()
+        vbar = psiT.conj() @ vg @ psiT
+        d = vg - vbar * I
+        H = H - 0.5 * d @ d
+    assert np.max(np.abs(H - c["H"].toarray())) < 1e-12
+
+
+def _fock_propagator(c, st, x, dt):
+    """B(x) of Eq. hs2 with the mean-field operators, split as Eq. primitive,
+    built from Fock-space exponentials (no Taylor series)."""
+    F = c["F"]
+    psiT = F.determinant(c["C"])
+    I = np.eye(F.dim)
+    v = eri_from_cholesky(c["L"])
+    v0 = F.one_body(c["h1"] - 0.5 * np.einsum("prrq->pq", v)).toarray()
+    A = np.zeros((F.dim, F.dim), complex)
+    vbars = []
+    for g in range(c["L"].shape[0]):
+        vg = 1j * F.one_body(c["L"][g]).toarray()
+        vbar = psiT.conj() @ vg @ psiT
+        vbars.append(vbar)
+        v0 = v0 - vbar * vg
+        A = A + math.sqrt(dt) * x[g] * (vg - vbar * I)
+    H0p = c["H0"] + 0.5 * np.sum(np.array(vbars) ** 2)
+    half = sla.expm(-0.5 * dt * v0)
+    return np.exp(-dt * (H0p - st.E_T)) * half @ sla.expm(A) @ half
+
+
+def test_one_step_ratio_and_thouless_vs_fock(fock_case):
+    """Eq. weight_update: the free-projection weight after one step is
+    <Psi_T|B(x)|Psi>/<Psi_T|Psi>, and the new orbitals span B(x)|Psi>
+    (Theorem 1.4)."""
+    c = fock_case
+    F, phi = c["F"], c["phi"]
+    dt = 0.01
+    p = afqmc.Params(dt=dt, taylor_order=40, qr_period=0, energy_period=0,
+                     mode="free", seed=9)
+    o = afqmc.Oracle(c["h1"], c["L"], c["C"], 1, p, H0=c["H0"], phi0=phi)
+    xi = philox.gaussian_fields(9, 0, [0], c["L"].shape[0])[0]
+    o.step()
+    psiT, psi = F.determinant(c["C"]), F.determinant(phi)
+    psi1 = _fock_propagator(c, o.setup, xi, dt) @ psi
+    ratio = (psiT.conj() @ psi1) / (psiT.conj() @ psi)
+    assert abs(o.weight[0] - ratio) < 1e-12
+    psi1o = F.determinant(o.phi[0])
+    k = np.argmax(np.abs(psi1o))
+    assert np.max(np.abs(psi1 - psi1[k] / psi1o[k] * psi1o)) < 1e-12 * np.max(np.abs(psi1))
+
+
+def test_hybrid_importance_function_vs_fock(fock_case):
+    """Eq. hybrid-wt with the optimal force bias of Eq. fb, evaluated by brute
+    force, equals the oracle's complex importance weight after one step."""
+    c = fock_case
+    F, phi = c["F"], c["phi"]
+    dt = 0.01
+    p = afqmc.Params(dt=dt, taylor_order=40, qr_period=0, energy_period=0,
+                     mode="complex_is", seed=9)
+    o = afqmc.Oracle(c["h1"], c["L"], c["C"], 1, p, H0=c["H0"], phi0=phi)
+    xi = philox.gaussian_fields(9, 0, [0], c["L"].shape[0])[0]
+    o.step()
+    psiT, psi = F.determinant(c["C"]), F.determinant(phi)
+    ov = psiT.conj() @ psi
+    xbar = []
+    for g in range(c["L"].shape[0]):
+        vg = 1j * F.one_body(c["L"][g]).toarray()
+        vbar = psiT.conj() @ vg @ psiT
+        vm = psiT.conj() @ vg @ psi / ov
+        xbar.append(-math.sqrt(dt) * (vm - vbar))
+    xbar = np.array(xbar)
+    I = (psiT.conj() @ (_fock_propagator(c, o.setup, xi - xbar, dt) @ psi)) / ov \
+        * np.exp(np.sum(xi * xbar) - 0.5 * np.sum(xbar * xbar))
+    assert abs(o.weight[0] - I) < 1e-12
+
+
+# ------------------------------------------------ library routines (P5-6) --
+def test_taylor_converges_to_expm():
+    """Sec. 3.4.2: the truncated Taylor series tends to exp(V) phi, and the
+    order-n error obeys |V|^(n+1) e^|V| / (n+1)!."""
+    rng = np.random.default_rng(1)
+    M, N = 10, 3
+    V = 0.1 * (rng.standard_normal((M, M)) + 1j * rng.standard_normal((M, M)))
+    V = V + V.T
+    phi = rng.standard_normal((1, M, N)) + 1j * rng.standard_normal((1, M, N))
+    exact = sla.expm(V) @ phi[0]
+    assert np.max(np.abs(afqmc.taylor(V[None], phi, 25)[0] - exact)) < 1e-13
+    nv = np.linalg.norm(V, 2)
+    for n in (2, 4, 6):
+        err = np.linalg.norm(afqmc.taylor(V[None], phi, n)[0] - exact, 2)
+        bound = nv ** (n + 1) * math.exp(nv) / math.factorial(n + 1) * np.linalg.norm(phi[0], 2)
+        assert err <= bound
+
+
+def test_mgs_matches_qr_and_leaves_estimators_invariant():
+    """Sec. 3.4.5 / Theorem 1.5: mGS gives the Q of a QR factorisation (up to
+    column phases); force bias and local energy are unchanged and the overlap
+    scales by det(R)^2 (Appendix A.1)."""
+    w = workloads.config("c0")
+    h1, L, _ = w.hamiltonian()
+    C, _, _, _ = scf.rhf(h1, L, w.N)
+    st = afqmc.Setup(h1, L, C)
+    rng = np.random.default_rng(3)
+    phi = (C + 0.5 * rng.standard_normal(C.shape) + 0.5j * rng.standard_normal(C.shape))[None] * 3.0
+    q = afqmc.mgs(phi)
+    Q, R = np.linalg.qr(phi[0])
+    ph = np.diag(R) / np.abs(np.diag(R))
+    assert np.max(np.abs(q[0] - Q * ph)) < 1e-13
+    ld0, th0 = afqmc.overlap(st, phi)
+    ld1, th1 = afqmc.overlap(st, q)
+    assert np.max(np.abs(afqmc.force_bias_trace(st, th0) - afqmc.force_bias_trace(st, th1))) < 1e-11
+    e0, e1 = afqmc.local_energy(st, th0), afqmc.local_energy(st, th1)
+    assert abs(e0[0] - e1[0]) < 1e-11 * abs(e0[0])
+    detR = np.prod(np.abs(np.diag(R)))
+    assert abs((ld0[0].real - ld1[0].real) - 2 * math.log(detR)) < 1e-12
+
+
+def test_propagator_half_step_is_matrix_exponential():
+    w = workloads.config("c0")
+    h1, L, _ = w.hamiltonian()
+    C, _, _, _ = scf.rhf(h1, L, w.N)
+    st = afqmc.Setup(h1, L, C, dt=0.01)
+    assert np.max(np.abs(st.Bhalf - sla.expm(-0.005 * st.v0p))) < 1e-13
+
+
+# ----------------------------------------------------------- limits (P7) --
+def test_one_body_limit_projects_to_lowest_orbitals():
+    """h2 = 0 (all L_g = 0): the walk is deterministic and the mixed energy
+    tends to 2 * (sum of the N lowest eigenvalues of h) (Sec. 2.2)."""
+    M, N = 6, 2
+    h1, L, _ = workloads.hamiltonian(M, 3, 11)
+    L = np.zeros_like(L)
+    rng = np.random.default_rng(0)
+    trial = np.linalg.qr(rng.standard_normal((M, N)))[0]
+    phi0 = np.linalg.qr(rng.standard_normal((M, N)))[0]
+    p = afqmc.Params(dt=0.05, qr_period=5, energy_period=0, seed=2)
+    o = afqmc.Oracle(h1, L, trial, 2, p, phi0=phi0).run(800)
+    exact = 2 * np.sum(np.linalg.eigvalsh(h1)[:N])
+    e = afqmc.local_energy(o.setup, o.theta)
+    assert np.max(np.abs(e - exact)) < 1e-9
+    assert np.allclose(o.weight, o.weight[0])
+
+
+# ---------------------------------------------------- exact estimators (P8) --
+@pytest.fixture(scope="module")
+def fci_case():
+    h1, L, C, _ = small_system(M=4, G=8, N=2, H0=0.0)
+    F = Fock(4)
+    H = F.hamiltonian(h1, eri_from_cholesky(L)).toarray()
+    sec = F.number_sector(2, 2)
+    Hs = H[np.ix_(sec, sec)]
+    psiT = F.determinant(C)[sec]
+    ev, U = np.linalg.eigh(Hs)
+
+    def e_beta(beta):
+        pb = (U * np.exp(-beta * (ev - ev[0]))) @ (U.conj().T @ psiT)
+        return ((psiT.conj() @ Hs @ pb) / (psiT.conj() @ pb)).real
+
+    return h1, L, C, e_beta, ev[0]
+
+
+@pytest.mark.parametrize("mode", ["free", "complex_is"])
+def test_exact_estimators_match_fci_imaginary_time(fci_case, mode):
+    """Free projection (Eq. freep) and force-biased importance sampling with
+    complex weights are exact up to the Trotter error: at beta = 1 the mixed
+    energy matches <Psi_T|H e^(-beta H)|Psi_T>/<Psi_T|e^(-beta H)|Psi_T> from
+    exact diagonalisation in the (2, 2) electron sector."""
+    h1, L, C, e_beta, _ = fci_case
+    W, dt = 4000, 0.01
+    p = afqmc.Params(dt=dt, seed=3, mode=mode, qr_period=5, energy_period=0,
+                     ecap_C=-1, fb_cap=-1, wmax=1e300)
+    o = afqmc.Oracle(h1, L, C, W, p).run(100)
+    e = afqmc.local_energy(o.setup, o.theta)
+    w = o.weight
+    est = (np.sum(w * e) / np.sum(w)).real
+    groups = np.array_split(np.arange(W), 20)
+    sub = [(np.sum(w[g] * e[g]) / np.sum(w[g])).real for g in groups]
+    err = np.std(sub) / math.sqrt(len(groups))
+    exact = e_beta(1.0)
+    assert abs(est - exact) < 4 * err + 2e-4, (est, exact, err)
+    # and the projection moved away from the trial energy by many error bars
+    assert abs(exact - afqmc.Setup(h1, L, C).E_T) > 10 * err
+
+
+def test_phaseless_close_to_exact_for_weak_phase(fci_case):
+    """The phaseless walk (Eq. weight_update_2) stays within a few mHa of the
+    exact projection for this weakly correlated case (Fig. 3 behaviour)."""
+    h1, L, C, e_beta, _ = fci_case
+    W, dt = 4000, 0.01
+    o = afqmc.Oracle(h1, L, C, W, afqmc.Params(dt=dt, seed=4, energy_period=0)).run(100)
+    e = afqmc.local_energy(o.setup, o.theta).real
+    est = np.sum(o.weight * e) / np.sum(o.weight)
+    assert abs(est - e_beta(1.0)) < 0.01
+
+
+# --------------------------------------------------------------- comb (P11) --
+def test_comb_conserves_weight_and_population():
+    rng = np.random.default_rng(2)
+    w = rng.exponential(size=64)
+    w[[3, 10, 11]] = 0.0
+    parent, wnew = afqmc.comb(w, 0.37)
+    assert parent.size == w.size
+    assert abs(wnew * w.size - np.sum(w)) < 1e-12 * np.sum(w)
+    assert np.all(np.diff(parent) >= 0)
+    assert not np.any(np.isin(parent, [3, 10, 11]))
+
+
+def test_comb_is_unbiased_over_u():
+    """E_u[copies of j] = N_w W_j / W_tot for u uniform on [0, 1)."""
+    rng = np.random.default_rng(7)
+    w = rng.exponential(size=20)
+    n = w.size
+    us = (np.arange(4000) + 0.5) / 4000
+    counts = np.zeros(n)
+    for u in us:
+        parent, _ = afqmc.comb(w, u)
+        counts += np.bincount(parent, minlength=n)
+    counts /= us.size
+    assert np.max(np.abs(counts - n * w / np.sum(w))) < 2e-3
+
+
+def test_population_control_keeps_total_weight_in_a_run():
+    w = workloads.config("c0")
+    h1, L, _ = w.hamiltonian()
+    C, _, _, _ = scf.rhf(h1, L, w.N)
+    o = afqmc.Oracle(h1, L, C, 16, afqmc.Params(seed=5, pc_period=0, energy_period=0))
+    o.run(10)
+    before = np.sum(o.weight)
+    e_before = afqmc.local_energy(o.setup, o.theta)
+    o.population_control(9)
+    assert abs(np.sum(o.weight) - before) < 1e-12 * before
+    assert np.allclose(o.weight, o.weight[0])
+    # every new walker is an exact copy of an old one
+    e_after = afqmc.local_energy(o.setup, o.theta)
+    assert all(np.min(np.abs(e_before - e)) == 0 for e in e_after)

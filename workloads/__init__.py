@@ -1,0 +1,141 @@
+"""Seeded synthetic inputs for phaseless AFQMC runs.
+
+This module only draws random numbers and describes workload shapes. It holds
+none of the AFQMC arithmetic: no SCF, no propagation, no energies. Both the
+CPU oracle (``oracle/``) and the GPU library's callers (``bench.py``, tests)
+take their Hamiltonians from here, so the two sides always see the same input.
+
+Hamiltonian recipe (the synthetic stand-in for the molecular integrals of the
+paper, Sec. 2 "The AFQMC method", Eqs. bo_ham2 / bo_ham_matel):
+
+* ``h1`` is real symmetric, ``M x M``: diagonal ``linspace(-2, 2, M)`` Ha,
+  strictly-upper entries drawn ``N(0, 0.05)`` (0.05 is the standard
+  deviation) in row-major order, then mirrored.
+* each Cholesky vector ``L[g]`` (``g = 0 .. nchol-1``) is real symmetric
+  ``M x M``: upper-triangle entries including the diagonal drawn
+  ``N(0, 0.5 * exp(-g / M))`` in row-major order, then mirrored.  The
+  two-electron tensor ``v_pqrs = sum_g L[g]_pr L[g]_qs`` (Sec. 2.3, Eq. chol)
+  is then positive semi-definite by construction.
+* draws come from numpy's PCG64 generator seeded ``1000 + config_index``;
+  ``h1`` is drawn first, then ``L[0]``, ``L[1]``, ...
+* the nuclear repulsion ``H0`` is 0.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+__all__ = [
+    "Workload",
+    "CONFIGS",
+    "config",
+    "hamiltonian",
+    "batched_systems",
+    "request_stream",
+]
+
+
+@dataclasses.dataclass(frozen=True)
+class Workload:
+    """Shape and run parameters of one synthetic phaseless-AFQMC run."""
+
+    name: str
+    M: int  # orbitals
+    N: int  # electrons per spin (N_up = N_dn, closed shell)
+    nchol: int  # Cholesky vectors N_gamma
+    nwalkers: int
+    dt: float = 0.005
+    nsteps: int = 200
+    qr_period: int = 5
+    pc_period: int = 0
+    energy_period: int = 1
+    taylor_order: int = 6
+    seed: int = 1  # Philox key for the auxiliary fields
+    ham_seed: int = 1000  # PCG64 seed of the Hamiltonian draw
+
+    def hamiltonian(self):
+        return hamiltonian(self.M, self.nchol, self.ham_seed)
+
+
+# The five workloads of the phaseless-AFQMC hot path.  Index i uses PCG64
+# seed 1000 + i for its Hamiltonian and Philox seed 1 + i for its fields.
+CONFIGS = {
+    # M=12 closed shell, 3+3 electrons, 48 Cholesky vectors, 32 walkers.
+    "c0": Workload("c0", M=12, N=3, nchol=48, nwalkers=32, nsteps=200,
+                   qr_period=5, energy_period=1, seed=1, ham_seed=1000),
+    # M=100, 10+10 electrons, 500 vectors, 1024 walkers, 1000 steps.
+    "c1": Workload("c1", M=100, N=10, nchol=500, nwalkers=1024, nsteps=1000,
+                   qr_period=5, energy_period=10, seed=2, ham_seed=1001),
+    # M=300, 25+25 electrons, 1800 vectors, 512 walkers, energy every 10 steps.
+    "c2": Workload("c2", M=300, N=25, nchol=1800, nwalkers=512, nsteps=100,
+                   qr_period=5, energy_period=10, seed=3, ham_seed=1002),
+}
+
+
+def config(name: str) -> Workload:
+    return CONFIGS[name]
+
+
+def _sym_from_upper(rng: np.random.Generator, M: int, scale: float,
+                    include_diag: bool) -> np.ndarray:
+    iu = np.triu_indices(M, 0 if include_diag else 1)
+    a = np.zeros((M, M))
+    a[iu] = rng.normal(0.0, scale, size=iu[0].size)
+    a = a + np.triu(a, 1).T
+    return a
+
+
+def hamiltonian(M: int, nchol: int, ham_seed: int, decay: float | None = None,
+                l_scale: float = 0.5):
+    """Return ``(h1, L, H0)``: ``h1`` (M, M), ``L`` (nchol, M, M), float64.
+
+    ``decay`` is the decay length of the Cholesky-vector amplitudes
+    (default ``M``); ``l_scale`` the amplitude of ``L[0]`` (default 0.5).
+    """
+    if decay is None:
+        decay = float(M)
+    rng = np.random.Generator(np.random.PCG64(ham_seed))
+    h1 = _sym_from_upper(rng, M, 0.05, include_diag=False)
+    h1[np.diag_indices(M)] = np.linspace(-2.0, 2.0, M)
+    L = np.empty((nchol, M, M))
+    for g in range(nchol):
+        L[g] = _sym_from_upper(rng, M, l_scale * math.exp(-g / decay), True)
+    return h1, L, 0.0
+
+
+def batched_systems(seed: int = 3000, count: int = 16):
+    """Uneven systems for one grouped launch: M in {40, 60, ..., 200},
+    N = M/8, nchol = 5M, walkers in {64, 128, ..., 1024}."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for i in range(count):
+        M = int(rng.choice(np.arange(40, 201, 20)))
+        W = int(rng.choice(np.arange(64, 1025, 64)))
+        out.append(Workload(f"sys{i}", M=M, N=M // 8, nchol=5 * M, nwalkers=W,
+                            nsteps=500, qr_period=5, energy_period=10,
+                            seed=100 + i, ham_seed=seed + 1 + i))
+    return out
+
+
+def request_stream(seed: int = 4000, count: int = 200, rate: float = 20.0,
+                   blocks: int = 20, steps_per_block: int = 50):
+    """Poisson stream of run requests: arrival times (s) and workloads.
+
+    M uniform in [20, 300], N uniform in [2, M/8], nchol = 5M, walkers
+    uniform in [128, 2048], ``blocks`` blocks of ``steps_per_block`` steps.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    t = 0.0
+    reqs = []
+    for i in range(count):
+        t += float(rng.exponential(1.0 / rate))
+        M = int(rng.integers(20, 301))
+        N = int(rng.integers(2, max(2, M // 8) + 1))
+        W = int(rng.integers(128, 2049))
+        reqs.append((t, Workload(f"req{i}", M=M, N=N, nchol=5 * M, nwalkers=W,
+                                 nsteps=blocks * steps_per_block, qr_period=5,
+                                 energy_period=steps_per_block,
+                                 seed=10_000 + i, ham_seed=seed + 1 + i)))
+    return reqs
