@@ -1,0 +1,354 @@
+"""Benchmark: walker-steps/s of phaseless AFQMC at M=300 on GB300.
+
+Workload (the M=300 configuration): synthetic closed-shell Hamiltonian with
+M=300 orbitals, N_up=N_dn=25, 1800 Cholesky vectors, 512 walkers, dt=0.005,
+modified Gram-Schmidt every 5 steps, local energy every 10 steps.  One step
+is one pass of the whole hot path over all walkers (force bias, fields, V,
+propagation, overlap/LU, weights, and the periodic QR and energy).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64]
+    python bench.py --impl reference      # the CPU oracle on the host cores
+
+Prints one JSON line.  Under torchrun (N > 1) every rank runs an independent
+replica (its own walker population and Philox seed) on its own GPU; time is
+the max over ranks and the value the walker-steps of all ranks per second
+(weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+PHASES = ["force_bias", "fields", "v_assembly", "bhalf", "taylor", "overlap", "weight", "qr",
+          "comb", "energy"]
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# FP64 DFMA throughput of GB300, measured on this machine with a dependent-chain
+# probe kernel (152 SMs, 256-thread blocks): 1.198 TFLOP/s.
+FP64_PEAK_TFLOPS = 1.198
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples taken during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def flops_per_walker_step(w: workloads.Workload, s=1):
+    """Algorithmic FLOPs per walker-step (packed symmetric V, real Lh, s spin
+    blocks run): force bias, V, Taylor, B_half, overlap/Theta, QR/q,
+    exchange/k_E."""
+    M, N, G, n = w.M, w.N, w.nchol, w.taylor_order
+    f_fb = 4 * s * G * N * M
+    f_v = 2 * G * M * (M + 1)
+    f_t = 8 * n * s * M * M * N
+    f_b = 8 * s * M * M * N
+    f_ov = 4 * s * N * N * M + 8 * s * M * N * N + (8 / 3) * s * N ** 3
+    f_qr = (8 * s * M * N * N + f_ov) / w.qr_period if w.qr_period else 0
+    f_e = (4 * s * G * N * N * M + 4 * s * N * M + f_fb) / w.energy_period if w.energy_period else 0
+    return dict(force_bias=f_fb, v_assembly=f_v, taylor=f_t, bhalf=f_b, overlap=f_ov, qr=f_qr,
+                energy=f_e, total=f_fb + f_v + f_t + f_b + f_ov + f_qr + f_e)
+
+
+def make_inputs(w: workloads.Workload, rank=0):
+    from paper_1711_02242_gb300.rhf import rhf_trial
+
+    h1, L, H0 = w.hamiltonian()
+    C, conv, grad = rhf_trial(h1, L, w.N, max_iter=25)
+    return h1, L, H0, C, conv, grad
+
+
+def run_gpu(args, w: workloads.Workload):
+    import torch
+
+    import paper_1711_02242_gb300 as pkg
+    from paper_1711_02242_gb300 import build as b
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    b.build()
+    prec = {"fp64": pkg.AFQMC_FP64, "tf32": pkg.AFQMC_MIXED_TF32, "bf16": pkg.AFQMC_MIXED_BF16}[
+        args.precision]
+    h1, L, H0, C, conv, grad = make_inputs(w)
+    p = pkg.default_params(w.M, w.N, w.nchol, w.nwalkers, dt=w.dt, seed=w.seed + 1000 * rank,
+                           qr_period=w.qr_period, energy_period=w.energy_period,
+                           taylor_order=w.taylor_order, precision=prec, H0=H0)
+    stream = torch.cuda.Stream(device=dev)
+    run = pkg.AfqmcRun(h1, L, C, p, device=dev, stream=stream)
+    K, Wm = args.steps, args.warmup
+    run.propagate(Wm)
+    stream.synchronize()
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+
+            dist.barrier()
+
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    lib = pkg.lib()
+    lib.afqmc_profile_start(run.s, K)
+    launches0 = pkg.afqmc_launch_count()
+    barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        run.propagate(K)
+        e1.record(stream)
+        stream.synchronize()
+    torch.cuda.synchronize(dev)
+    barrier()
+    launches = pkg.afqmc_launch_count() - launches0
+    ms_total = e0.elapsed_time(e1)
+    import ctypes
+
+    ph_ms = (ctypes.c_double * 10)()
+    ph_n = (ctypes.c_int64 * 10)()
+    ph_k = (ctypes.c_int64 * 10)()
+    pkg._check(lib.afqmc_profile_stop(run.s, ph_ms, ph_n, ph_k))
+    if ws > 1:
+        import torch.distributed as dist
+
+        t = torch.tensor([ms_total], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    info = run.info()
+    E, wsum = run.energy()
+    run.close()
+    del run
+    torch.cuda.empty_cache()
+
+    # end to end through the public API with host buffers: set-up (upload of
+    # h1, L and the trial from host memory), K steps, energy read back
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    run2 = pkg.AfqmcRun(h1, L, C, p, device=dev, stream=stream)
+    run2.propagate(K)
+    E2, _ = run2.energy()
+    t_e2e = time.perf_counter() - t0
+    run2.close()
+
+    phases = {PHASES[i]: {"ms": ph_ms[i], "count": int(ph_n[i]), "kernels": int(ph_k[i])}
+              for i in range(10)}
+    return dict(ms_total=ms_total, phases=phases, launches=launches, info=info, E=E, wsum=wsum,
+                clocks=clk.summary(), e2e_s=t_e2e, trial_converged=conv, trial_grad=grad,
+                h2d_bytes=h1.nbytes + L.nbytes + C.nbytes, world=ws, rank=rank)
+
+
+def cpu_sample(w: workloads.Workload, n_walkers=8, n_steps=2):
+    """Time the oracle as it stands on a bounded sample of the workload:
+    n_walkers walkers of the population for n_steps steps (set-up excluded,
+    as the GPU number excludes afqmc_init)."""
+    from oracle import afqmc
+
+    h1, L, H0, C, _, _ = make_inputs(w)
+    p = afqmc.Params(dt=w.dt, seed=w.seed, qr_period=w.qr_period, energy_period=w.energy_period,
+                     taylor_order=w.taylor_order)
+    orc = afqmc.Oracle(h1, L, C, w.nwalkers, p, H0=H0)
+    orc.weight[n_walkers:] = 0.0  # the oracle skips zero-weight walkers
+    t0 = time.perf_counter()
+    for _ in range(n_steps):
+        orc.step()
+    dt = time.perf_counter() - t0
+    cores = len(os.sched_getaffinity(0))
+    return dict(value=n_walkers * n_steps / dt, unit="walker-steps/s", cores=cores, kind="oracle",
+                sample=f"{n_walkers} of {w.nwalkers} walkers x {n_steps} steps of the M=300 "
+                       f"workload (set-up excluded), numpy float64, {cores} host threads",
+                seconds=dt)
+
+
+def run_reference(args, w):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    from oracle import afqmc
+
+    h1, L, H0, C, _, _ = make_inputs(w)
+    p = afqmc.Params(dt=w.dt, seed=w.seed, qr_period=w.qr_period, energy_period=w.energy_period,
+                     taylor_order=w.taylor_order)
+    orc = afqmc.Oracle(h1, L, C, w.nwalkers, p, H0=H0)
+    sample = args.ref_walkers
+    orc.weight[sample:] = 0.0
+    for _ in range(args.warmup):
+        orc.step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        orc.step()
+    dt = time.perf_counter() - t0
+    cores = len(os.sched_getaffinity(0))
+    val = sample * args.steps / dt
+    line = {
+        "impl": "reference", "metric": "walker-steps/s at M=300", "value": val,
+        "unit": "walker-steps/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "M=300 N=25 nchol=1800 512 walkers dt=0.005 (oracle sample)",
+                   "sampled_walkers": sample},
+        "cpu_baseline": {"value": val, "unit": "walker-steps/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{sample} walkers x {args.steps} steps per run"},
+        "e2e": {"value": val, "unit": "walker-steps/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "tf32", "bf16"])
+    ap.add_argument("--config", default="c2", choices=sorted(workloads.CONFIGS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-walkers", type=int, default=4)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    w = workloads.config(args.config)
+    if args.impl == "reference":
+        return run_reference(args, w)
+    r = run_gpu(args, w)
+    if r["rank"] != 0:
+        return 0
+    K = args.steps
+    N = r["world"]
+    ms_step = r["ms_total"] / K
+    value = N * w.nwalkers * K / (r["ms_total"] * 1e-3)
+    fl = flops_per_walker_step(w)
+    pk, pk_kind = peaks()
+    # dominant kernel: the V contraction (one launch per step)
+    v = r["phases"]["v_assembly"]
+    v_ms = v["ms"] / max(1, v["kernels"])
+    v_flops = fl["v_assembly"] * w.nwalkers
+    if args.precision == "fp64":
+        peak = FP64_PEAK_TFLOPS
+        roof = {"bound": "alu", "kernel": "k_gemm_nt_f64 (V = sum_g x_g L_g)",
+                "achieved": v_flops / (v_ms * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s",
+                "peak_source": "measured FP64 DFMA throughput (probe kernel)",
+                "traffic": None}
+    else:
+        peak = pk["bf16_tflops_sustained"] if args.precision == "bf16" else pk["bf16_tflops_sustained"] / 2
+        roof = {"bound": "tensor", "kernel": "V contraction", "achieved": v_flops / (v_ms * 1e-3) / 1e12,
+                "peak": peak, "unit": "TFLOP/s", "peak_source": pk_kind, "traffic": None}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["launch_ms"] = v_ms
+    line = {
+        "metric": "walker-steps/s at M=300", "value": value, "unit": "walker-steps/s",
+        "n_gpus": N, "steps": K, "warmup": args.warmup, "ms_per_step": ms_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp64": "f64", "tf32": "tf32/f32/f64", "bf16": "bf16/f32/f64"}[args.precision],
+        "data": "synthetic",
+        "config": {"workload": f"M={w.M} N_up=N_dn={w.N} nchol={w.nchol} walkers={w.nwalkers} "
+                               f"dt={w.dt} qr/{w.qr_period} energy/{w.energy_period} taylor {w.taylor_order}",
+                   "precision": args.precision, "l2": "inputs larger than L2 (packed L "
+                   f"{w.M * (w.M + 1) // 2 * w.nchol * 8 / 1e6:.0f} MB float64)",
+                   "trial": f"RHF (25 iterations, converged={r['trial_converged']}, "
+                            f"|FD-DF|={r['trial_grad']:.2e})"},
+        "roofline": roof,
+        "phases_ms_per_step": {k: round(v["ms"] / K, 4) for k, v in r["phases"].items()},
+        "gpu_launches": r["launches"],
+        "clocks": r["clocks"],
+        "e2e": {"value": N * w.nwalkers * K / r["e2e_s"], "unit": "walker-steps/s",
+                "h2d_bytes_per_step": r["h2d_bytes"] / K, "d2h_bytes_per_step": 16 / K,
+                "includes": "afqmc_init from host arrays (h1, L, trial upload and set-up), "
+                            f"{K} steps, energy read back"},
+        "energy": {"E": r["E"], "wsum": r["wsum"], "alive": int(r["info"].alive),
+                   "E_T": r["info"].E_T, "nonfinite": int(r["info"].nonfinite)},
+        "flops_per_walker_step": fl["total"],
+    }
+    if N == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_sample(w)
+    print(json.dumps(line))
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

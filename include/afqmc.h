@@ -1,0 +1,286 @@
+/*
+ * afqmc.h -- C ABI of the GB300 phaseless-AFQMC library (libafqmc.so).
+ *
+ * The library runs the per-walker imaginary-time step of phaseless
+ * auxiliary-field quantum Monte Carlo for a closed-shell molecule with a
+ * single-determinant (RHF) trial, after M. Motta and S. Zhang, "Ab initio
+ * computations of molecular systems by the auxiliary-field quantum Monte
+ * Carlo method" (2017):
+ *   force bias            Sec. 3.2, Eq. fb; Sec. 3.4.2, Eq. precomputing2
+ *   auxiliary fields      Sec. 2.2, Eqs. hs / hs2 (Gaussian p(x))
+ *   propagation           Eq. primitive (Trotter split), Sec. 3.4.2
+ *                         (A(x), truncated Taylor series), Theorem 1.4
+ *   mean-field background Sec. 2.4
+ *   weights               Eq. hybrid-wt, Eq. if_rle, Eq. weight_update_2
+ *   local energy          Eqs. localenergy, localenergy2, localenergy3
+ *   stabilisation         Sec. 3.4.5 (modified Gram-Schmidt), Theorem 1.5
+ *   population control    Sec. 3.4.4 (a fixed-size comb)
+ *   rare-event caps       Appendix B, Eq. cap
+ *
+ * Conventions shared by every entry point:
+ *   - Return value: AFQMC_OK (0) or a negative afqmc_status.  Nothing aborts,
+ *     traps or exits; afqmc_last_error() gives a message for the calling
+ *     thread's last failure.
+ *   - Host arrays are row-major float64 ("C order") unless stated.  They are
+ *     read (and copied) during the call; the caller keeps ownership.
+ *   - Device memory is owned by the caller: the library never allocates
+ *     device memory.  afqmc_workspace_size() says how many bytes one state
+ *     needs; the caller passes a buffer of at least that size (256-byte
+ *     aligned) to afqmc_init() and keeps it alive until afqmc_destroy().
+ *   - Every kernel of a state runs on the CUDA stream given to afqmc_init()
+ *     (a cudaStream_t passed as void*, NULL = legacy default stream).
+ *     Calls that return results to the host synchronise that stream.
+ *   - One host thread at a time per state.  Different states are
+ *     independent.
+ *   - Spin: the walkers are restricted closed shell (N_up = N_dn = N); the
+ *     up and down blocks of every walker are the same M x N matrix, because
+ *     the trial is RHF and the propagator B(x) is spin independent
+ *     (Sec. 2.3: v_g acts identically on both spins).
+ */
+#ifndef AFQMC_H
+#define AFQMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define AFQMC_API __attribute__((visibility("default")))
+#else
+#define AFQMC_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum afqmc_status {
+  AFQMC_OK = 0,
+  AFQMC_EINVAL = -1,      /* bad argument, shape or parameter              */
+  AFQMC_ENOSPC = -2,      /* workspace smaller than afqmc_workspace_size() */
+  AFQMC_ENONFINITE = -3,  /* non-finite value in a host input              */
+  AFQMC_ECUDA = -4,       /* a CUDA runtime call failed                    */
+  AFQMC_ETIMEOUT = -5,    /* a bounded device-side wait gave up            */
+  AFQMC_ESTATE = -6,      /* state not usable (destroyed, wrong phase)     */
+  AFQMC_EUNSUPPORTED = -7 /* mode not built into this library              */
+} afqmc_status;
+
+/* Arithmetic of the step. */
+enum {
+  AFQMC_FP64 = 0,       /* every step in float64 / complex128                   */
+  AFQMC_MIXED_TF32 = 1, /* contractions on tcgen05 tensor cores, TF32 inputs,   */
+                        /* FP32 accumulation; Theta, LU, overlap ratios,        */
+                        /* weights and Gram-Schmidt in FP64                     */
+  AFQMC_MIXED_BF16 = 2  /* as MIXED_TF32 with BF16 inputs to the contractions   */
+};
+
+/* Walker update rule. */
+enum {
+  AFQMC_PHASELESS = 0, /* Eq. weight_update_2: hybrid weight, cos projection */
+  AFQMC_FREE = 1       /* Eq. weight_update: free projection, complex weight */
+};
+
+typedef struct afqmc_params {
+  int32_t M;             /* orbitals (orthonormal basis)                       */
+  int32_t N;             /* electrons per spin, N_up = N_dn = N, 1 <= N <= M   */
+  int32_t nchol;         /* Cholesky vectors N_gamma                           */
+  int32_t nwalkers;      /* population size N_w                                */
+  double dt;             /* imaginary time step, > 0                           */
+  double e_shift;        /* energy shift E_0 in B(x); NaN -> trial energy E_T  */
+  double H0;             /* constant (nuclear repulsion) of Eq. bo_ham2        */
+  uint64_t seed;         /* Philox key of the auxiliary fields                 */
+  int32_t taylor_order;  /* order n of the truncated exp(V) series (>= 1)      */
+  int32_t qr_period;     /* steps between Gram-Schmidt passes (0 = never)      */
+  int32_t pc_period;     /* steps between comb population controls (0 = off)   */
+  int32_t energy_period; /* steps between energy measurements (0 = never)      */
+  int32_t precision;     /* AFQMC_FP64 / AFQMC_MIXED_TF32 / AFQMC_MIXED_BF16   */
+  int32_t mode;          /* AFQMC_PHASELESS / AFQMC_FREE                       */
+  double ecap_C;         /* local-energy cap constant C of Eq. cap; <= 0: off  */
+  double fb_cap;         /* force-bias magnitude cap v_max; <= 0: off          */
+  double wmax;           /* weight cap; NaN -> max(100, nwalkers / 10)         */
+  int32_t max_records;   /* capacity of the device energy log (>= 1)           */
+  int32_t reserved;      /* must be 0                                          */
+} afqmc_params;
+
+/* Fill *p with the defaults: dt 0.005, e_shift NaN, H0 0, seed 1,
+ * taylor_order 6, qr_period 5, pc_period 0, energy_period 1, FP64,
+ * phaseless, ecap_C 2, fb_cap 1, wmax NaN, max_records 4096.  The sizes
+ * (M, N, nchol, nwalkers) are set to 0 and must be filled in. */
+AFQMC_API void afqmc_default_params(afqmc_params* p);
+
+/* Bytes of device workspace one state needs for *p (sizes and precision). */
+AFQMC_API int afqmc_workspace_size(const afqmc_params* p, size_t* bytes);
+
+typedef struct afqmc_state afqmc_state; /* opaque */
+
+/*
+ * Create a state and run the once-per-run set-up on the device:
+ *   h1     [M][M]         one-body matrix h_pq (Eq. bo_ham_matel), symmetric
+ *   L      [nchol][M][M]  Cholesky vectors, v_pqrs = sum_g L[g]_pr L[g]_qs
+ *                         (Sec. 2.3, Eq. chol), each L[g] symmetric
+ *   trial  [M][N]         occupied orbitals V_T of the RHF trial, orthonormal
+ *                         columns (Sec. 3.4.1)
+ * all host, row-major float64.  The set-up computes, on the GPU,
+ * c_g = 2 Tr(L_g V_T V_T^T) (the mean-field background vbar_g = i c_g,
+ * Sec. 2.4), v0' = h - 1/2 sum_g L_g^2 + sum_g c_g L_g, H0' = H0 -
+ * 1/2 sum_g c_g^2, B_half = exp(-dt v0'/2), the half-rotated vectors
+ * V_T^T L_g and V_T^T h (Eq. precomputing2) and the trial energy E_T, and
+ * puts every walker at {V_T, W = 1, theta = 0} (algorithm outline, step 1).
+ * d_workspace: device buffer of ws_bytes >= afqmc_workspace_size(p).
+ * stream: cudaStream_t (as void*) on which every kernel of the state runs.
+ * Synchronises the stream.  On failure *out is NULL.
+ */
+AFQMC_API int afqmc_init(const afqmc_params* p, const double* h1, const double* L,
+               const double* trial, void* d_workspace, size_t ws_bytes,
+               void* stream, afqmc_state** out);
+
+/*
+ * Enqueue nsteps steps of the random walk (algorithm outline, steps 2-9):
+ * per step and walker with W != 0: force bias, fields, propagation
+ * B_half T_n(V) B_half, new overlap / Theta, weight update (phaseless or
+ * free); then every qr_period steps modified Gram-Schmidt, every pc_period
+ * steps the comb, every energy_period steps one energy record (local
+ * energies and the mixed estimator, Eq. localenergy).  Asynchronous: returns
+ * once the work is enqueued on the state's stream.
+ */
+AFQMC_API int afqmc_propagate(afqmc_state* s, int32_t nsteps);
+
+/*
+ * Mixed estimator of the energy at the current walkers, Eq. localenergy:
+ * *E = sum_w W_w Re E_loc,w / sum_w W_w (phaseless; E_loc capped by Eq. cap)
+ * or Re(sum W e^{i theta} E_loc / sum W e^{i theta}) (free projection),
+ * *wsum = sum_w W_w (real part).  Synchronises the stream.
+ */
+AFQMC_API int afqmc_energy(afqmc_state* s, double* E, double* wsum);
+
+/*
+ * Local energies of all walkers (Eqs. localenergy2/3), uncapped:
+ * eloc [nwalkers][2] host (re, im).  Synchronises the stream.
+ */
+AFQMC_API int afqmc_local_energies(afqmc_state* s, double* eloc);
+
+/*
+ * Copy walkers to the host: phi [nwalkers][M][N][2] (re, im, row-major
+ * orbital coefficients), weight [nwalkers][2] (real and imaginary part of
+ * the walker weight W e^{i theta}; theta = 0 for phaseless walks), logov
+ * [nwalkers][2] (log <Psi_T|Psi> = 2 log det(V_T^T phi) for both spins: real
+ * part and phase in (-pi, pi]).  Any pointer may be NULL.
+ * Synchronises the stream.
+ */
+AFQMC_API int afqmc_get_walkers(afqmc_state* s, double* phi, double* weight, double* logov);
+
+/*
+ * Replace the walkers from host arrays laid out as in afqmc_get_walkers
+ * (phi and weight required).  Overlaps and Theta are recomputed on the
+ * device.  Synchronises the stream.
+ */
+AFQMC_API int afqmc_set_walkers(afqmc_state* s, const double* phi, const double* weight);
+
+/*
+ * Energy log: up to max_records records (step, mixed estimate E, Re sum W,
+ * live walkers) written by afqmc_propagate every energy_period steps, oldest
+ * first, to rec [cap][4] host.  *n receives the number of records copied;
+ * the log keeps the newest max_records.  Synchronises the stream.
+ */
+AFQMC_API int afqmc_get_energy_log(afqmc_state* s, double* rec, int32_t cap, int32_t* n);
+
+typedef struct afqmc_info {
+  double E_T;            /* trial energy <Psi_T|H|Psi_T>                       */
+  double H0p;            /* H0' after the mean-field shift                     */
+  double e_shift;        /* shift used in B(x)                                 */
+  double wmax;           /* weight cap in use                                  */
+  int64_t step;          /* steps taken                                        */
+  int64_t nonfinite;     /* walkers zeroed for a non-finite weight             */
+  int64_t launches;      /* kernels this state has launched                    */
+  int32_t alive;         /* walkers with W != 0 (at the last sync)             */
+  int32_t status;        /* sticky device status (afqmc_status)                */
+} afqmc_info;
+
+/* State summary; synchronises the stream. */
+AFQMC_API int afqmc_get_info(afqmc_state* s, afqmc_info* info);
+
+/*
+ * Checkpoint: serialise walkers, weights, overlaps, the step counter and the
+ * energy log into host memory.  With buf == NULL, *bytes receives the size
+ * needed; otherwise *bytes must be at least that.  The fields are keyed by
+ * (seed, step, walker, gamma), so a state restored with afqmc_load() into a
+ * state created with the same inputs continues bit-identically.
+ */
+AFQMC_API int afqmc_save(afqmc_state* s, void* buf, size_t* bytes);
+AFQMC_API int afqmc_load(afqmc_state* s, const void* buf, size_t bytes);
+
+/* Release the host side of a state (the workspace stays the caller's). */
+AFQMC_API int afqmc_destroy(afqmc_state* s);
+
+/*
+ * Phases of a step, for afqmc_profile_stop():
+ *   FORCE_BIAS  t_g = 2 Tr(Lh_g Theta) contraction (Eq. precomputing2)
+ *   FIELDS      Philox fields, force bias and its cap, x = xi - xbar
+ *   V           sum_g x_g L_g contraction (A(x) of Sec. 3.4.2)
+ *   BHALF       the two exp(-dt v0'/2) products (Eq. primitive)
+ *   TAYLOR      the truncated exp(V) series
+ *   OVERLAP     S = V_T^T Phi, LU, log det, Theta (Theorem 1.1)
+ *   WEIGHT      overlap ratio, phaseless / free weight update
+ *   QR          modified Gram-Schmidt and the overlap after it
+ *   COMB        population control
+ *   ENERGY      local energies (exchange contraction) and the estimator
+ */
+enum {
+  AFQMC_PH_FORCE_BIAS = 0,
+  AFQMC_PH_FIELDS,
+  AFQMC_PH_V,
+  AFQMC_PH_BHALF,
+  AFQMC_PH_TAYLOR,
+  AFQMC_PH_OVERLAP,
+  AFQMC_PH_WEIGHT,
+  AFQMC_PH_QR,
+  AFQMC_PH_COMB,
+  AFQMC_PH_ENERGY,
+  AFQMC_NPHASE
+};
+
+/*
+ * Time the phases of the next steps with CUDA events recorded on the state's
+ * stream around each phase (no host synchronisation while recording).
+ * max_steps bounds how many steps are recorded; later steps run untimed.
+ */
+AFQMC_API int afqmc_profile_start(afqmc_state* s, int32_t max_steps);
+
+/*
+ * Stop recording, synchronise the stream and return per phase the summed
+ * device time in milliseconds (ms [AFQMC_NPHASE]) and how many times the
+ * phase ran (count [AFQMC_NPHASE]); kernels [AFQMC_NPHASE] (may be NULL)
+ * receives the kernels each phase launched.  Host arrays.
+ */
+AFQMC_API int afqmc_profile_stop(afqmc_state* s, double* ms, int64_t* count, int64_t* kernels);
+
+/*
+ * The counter-based generator behind the auxiliary fields: Philox4x32 with
+ * 10 rounds (J. K. Salmon et al., "Parallel random numbers: as easy as 1, 2,
+ * 3", SC'11), key = (key & 0xffffffff, key >> 32).
+ * d_ctr [n][4] and d_out [n][4] are DEVICE uint32 arrays owned by the caller;
+ * the call is asynchronous on `stream`.
+ */
+AFQMC_API int afqmc_philox4x32_10(uint64_t key, const uint32_t* d_ctr, int64_t n,
+                                  uint32_t* d_out, void* stream);
+
+/*
+ * The standard normal fields x ~ p(x) of Eq. hs2 that afqmc_propagate draws
+ * for walkers [w0, w0 + nw) at step `step`: d_out [nw][nchol] DEVICE float64.
+ * Field pair (2k, 2k+1) of walker w comes from Philox counter
+ * (k, w, step, 0) by the Box-Muller transform of u1 (words 0, 1) and u2
+ * (words 2, 3), u = fl(fl(a + 0.5) 2^-53), a = (hi >> 5) 2^26 + (lo >> 6).
+ * Asynchronous on `stream`.
+ */
+AFQMC_API int afqmc_gaussian_fields(uint64_t seed, int64_t step, int32_t w0, int32_t nw,
+                                    int32_t nchol, double* d_out, void* stream);
+
+/* Message for the calling thread's last failed call (never NULL). */
+AFQMC_API const char* afqmc_last_error(void);
+
+/* Number of kernels launched by this library in this process. */
+AFQMC_API int64_t afqmc_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AFQMC_H */

@@ -29,7 +29,7 @@ def fock(h1, L, C):
     coul = Lf @ P.reshape(M * M)  # Tr(L_g P) for symmetric L_g
     J = 2.0 * (coul @ Lf).reshape(M, M)
     LC = L @ C  # (nchol, M, N)
-    K = np.einsum("gpi,gqi->pq", LC, LC)  # sum_g L_g P L_g
+    K = np.tensordot(LC, LC, axes=([0, 2], [0, 2]))  # sum_g L_g P L_g
     del N
     return h1 + J - K, P, coul
 

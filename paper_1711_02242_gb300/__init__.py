@@ -1,0 +1,255 @@
+"""Python binding of libafqmc.so, the GB300 phaseless-AFQMC library.
+
+Argument marshalling only: every step of the walk runs in the library's CUDA
+kernels.  PyTorch provides the device workspace (a uint8 tensor) and the CUDA
+stream.  The functions keep the C names of ``include/afqmc.h``; ``AfqmcRun``
+wraps one state.
+
+There is no CPU fallback: if the library has not been built (``build()``),
+``lib()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libafqmc.so")
+
+AFQMC_OK = 0
+AFQMC_FP64, AFQMC_MIXED_TF32, AFQMC_MIXED_BF16 = 0, 1, 2
+AFQMC_PHASELESS, AFQMC_FREE = 0, 1
+STATUS = {0: "OK", -1: "EINVAL", -2: "ENOSPC", -3: "ENONFINITE", -4: "ECUDA",
+          -5: "ETIMEOUT", -6: "ESTATE", -7: "EUNSUPPORTED"}
+
+EXPORTED = ["afqmc_default_params", "afqmc_workspace_size", "afqmc_init", "afqmc_propagate",
+            "afqmc_energy", "afqmc_local_energies", "afqmc_get_walkers", "afqmc_set_walkers",
+            "afqmc_get_energy_log", "afqmc_get_info", "afqmc_save", "afqmc_load",
+            "afqmc_destroy", "afqmc_last_error", "afqmc_launch_count",
+            "afqmc_philox4x32_10", "afqmc_gaussian_fields"]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("M", ctypes.c_int32), ("N", ctypes.c_int32), ("nchol", ctypes.c_int32),
+                ("nwalkers", ctypes.c_int32), ("dt", ctypes.c_double),
+                ("e_shift", ctypes.c_double), ("H0", ctypes.c_double),
+                ("seed", ctypes.c_uint64), ("taylor_order", ctypes.c_int32),
+                ("qr_period", ctypes.c_int32), ("pc_period", ctypes.c_int32),
+                ("energy_period", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("mode", ctypes.c_int32), ("ecap_C", ctypes.c_double),
+                ("fb_cap", ctypes.c_double), ("wmax", ctypes.c_double),
+                ("max_records", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("E_T", ctypes.c_double), ("H0p", ctypes.c_double),
+                ("e_shift", ctypes.c_double), ("wmax", ctypes.c_double),
+                ("step", ctypes.c_int64), ("nonfinite", ctypes.c_int64),
+                ("launches", ctypes.c_int64), ("alive", ctypes.c_int32),
+                ("status", ctypes.c_int32)]
+
+
+class AfqmcError(RuntimeError):
+    pass
+
+
+_lib = None
+
+
+def lib():
+    """Load libafqmc.so (built by ``build()``); raise if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise AfqmcError(f"{LIB_PATH} is not built; run paper_1711_02242_gb300.build.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    P = ctypes.POINTER
+    dp = P(ctypes.c_double)
+    vp = ctypes.c_void_p
+    sig = {
+        "afqmc_default_params": (None, [P(Params)]),
+        "afqmc_workspace_size": (ctypes.c_int, [P(Params), P(ctypes.c_size_t)]),
+        "afqmc_init": (ctypes.c_int, [P(Params), dp, dp, dp, vp, ctypes.c_size_t, vp, P(vp)]),
+        "afqmc_propagate": (ctypes.c_int, [vp, ctypes.c_int32]),
+        "afqmc_energy": (ctypes.c_int, [vp, dp, dp]),
+        "afqmc_local_energies": (ctypes.c_int, [vp, dp]),
+        "afqmc_get_walkers": (ctypes.c_int, [vp, dp, dp, dp]),
+        "afqmc_set_walkers": (ctypes.c_int, [vp, dp, dp]),
+        "afqmc_get_energy_log": (ctypes.c_int, [vp, dp, ctypes.c_int32, P(ctypes.c_int32)]),
+        "afqmc_get_info": (ctypes.c_int, [vp, P(Info)]),
+        "afqmc_save": (ctypes.c_int, [vp, vp, P(ctypes.c_size_t)]),
+        "afqmc_load": (ctypes.c_int, [vp, vp, ctypes.c_size_t]),
+        "afqmc_destroy": (ctypes.c_int, [vp]),
+        "afqmc_last_error": (ctypes.c_char_p, []),
+        "afqmc_launch_count": (ctypes.c_int64, []),
+        "afqmc_philox4x32_10": (ctypes.c_int, [ctypes.c_uint64, vp, ctypes.c_int64, vp, vp]),
+        "afqmc_gaussian_fields": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_int64, ctypes.c_int32,
+                                                 ctypes.c_int32, ctypes.c_int32, vp, vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(rc):
+    if rc != AFQMC_OK:
+        msg = lib().afqmc_last_error().decode(errors="replace")
+        raise AfqmcError(f"{STATUS.get(rc, rc)}: {msg}")
+
+
+def _dptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def default_params(M=0, N=0, nchol=0, nwalkers=0, **kw) -> Params:
+    p = Params()
+    lib().afqmc_default_params(ctypes.byref(p))
+    p.M, p.N, p.nchol, p.nwalkers = M, N, nchol, nwalkers
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+def afqmc_workspace_size(p: Params) -> int:
+    n = ctypes.c_size_t(0)
+    _check(lib().afqmc_workspace_size(ctypes.byref(p), ctypes.byref(n)))
+    return n.value
+
+
+def afqmc_philox4x32_10(key: int, ctr):
+    """Philox4x32-10 words for a (n, 4) int32/uint32 CUDA tensor of counters."""
+    import torch
+
+    ctr = ctr.contiguous()
+    out = torch.empty_like(ctr)
+    st = torch.cuda.current_stream(ctr.device)
+    _check(lib().afqmc_philox4x32_10(key, ctypes.c_void_p(ctr.data_ptr()), ctr.shape[0],
+                                     ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(st.cuda_stream)))
+    return out
+
+
+def afqmc_gaussian_fields(seed: int, step: int, w0: int, nw: int, nchol: int, device="cuda:0"):
+    """The fields afqmc_propagate draws for walkers [w0, w0+nw) at one step."""
+    import torch
+
+    out = torch.empty((nw, nchol), dtype=torch.float64, device=device)
+    st = torch.cuda.current_stream(out.device)
+    _check(lib().afqmc_gaussian_fields(seed, step, w0, nw, nchol, ctypes.c_void_p(out.data_ptr()),
+                                       ctypes.c_void_p(st.cuda_stream)))
+    return out
+
+
+def afqmc_launch_count() -> int:
+    return int(lib().afqmc_launch_count())
+
+
+class AfqmcRun:
+    """One AFQMC state on a CUDA device: workspace, stream, walkers."""
+
+    def __init__(self, h1, L, trial, params: Params, device="cuda:0", stream=None,
+                 workspace=None):
+        import torch
+
+        self.p = params
+        self.device = torch.device(device)
+        nbytes = afqmc_workspace_size(params)
+        if workspace is None:
+            workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        self.ws = workspace
+        base = workspace.data_ptr()
+        off = (-base) % 256
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        h1 = np.ascontiguousarray(h1, np.float64)
+        L = np.ascontiguousarray(L, np.float64)
+        trial = np.ascontiguousarray(trial, np.float64)
+        if h1.shape != (params.M, params.M) or L.shape != (params.nchol, params.M, params.M) \
+                or trial.shape != (params.M, params.N):
+            raise AfqmcError("input shapes do not match the parameters")
+        st = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            rc = lib().afqmc_init(ctypes.byref(params), _dptr(h1), _dptr(L), _dptr(trial),
+                                  ctypes.c_void_p(base + off), ctypes.c_size_t(workspace.numel() - off),
+                                  ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(st))
+        _check(rc)
+        self.s = st
+
+    # -- the walk ---------------------------------------------------------------
+    def propagate(self, nsteps: int):
+        _check(lib().afqmc_propagate(self.s, int(nsteps)))
+
+    def energy(self):
+        E, w = ctypes.c_double(), ctypes.c_double()
+        _check(lib().afqmc_energy(self.s, ctypes.byref(E), ctypes.byref(w)))
+        return E.value, w.value
+
+    def local_energies(self):
+        out = np.empty((self.p.nwalkers, 2))
+        _check(lib().afqmc_local_energies(self.s, _dptr(out)))
+        return out[:, 0] + 1j * out[:, 1]
+
+    def get_walkers(self):
+        W, M, N = self.p.nwalkers, self.p.M, self.p.N
+        phi = np.empty((W, M, N, 2))
+        wt = np.empty((W, 2))
+        lo = np.empty((W, 2))
+        _check(lib().afqmc_get_walkers(self.s, _dptr(phi), _dptr(wt), _dptr(lo)))
+        return phi[..., 0] + 1j * phi[..., 1], wt[:, 0] + 1j * wt[:, 1], lo[:, 0] + 1j * lo[:, 1]
+
+    def set_walkers(self, phi, weight):
+        W, M, N = self.p.nwalkers, self.p.M, self.p.N
+        phi = np.asarray(phi, np.complex128).reshape(W, M, N)
+        ph = np.ascontiguousarray(np.stack([phi.real, phi.imag], -1))
+        w = np.asarray(weight, np.complex128).reshape(W)
+        wt = np.ascontiguousarray(np.stack([w.real, w.imag], -1))
+        _check(lib().afqmc_set_walkers(self.s, _dptr(ph), _dptr(wt)))
+
+    def energy_log(self):
+        cap = self.p.max_records
+        rec = np.empty((cap, 4))
+        n = ctypes.c_int32()
+        _check(lib().afqmc_get_energy_log(self.s, _dptr(rec), cap, ctypes.byref(n)))
+        return rec[: n.value].copy()
+
+    def info(self) -> Info:
+        i = Info()
+        _check(lib().afqmc_get_info(self.s, ctypes.byref(i)))
+        return i
+
+    def save(self) -> bytes:
+        n = ctypes.c_size_t(0)
+        _check(lib().afqmc_save(self.s, None, ctypes.byref(n)))
+        buf = ctypes.create_string_buffer(n.value)
+        _check(lib().afqmc_save(self.s, buf, ctypes.byref(n)))
+        return buf.raw[: n.value]
+
+    def load(self, blob: bytes):
+        buf = ctypes.create_string_buffer(blob, len(blob))
+        _check(lib().afqmc_load(self.s, buf, len(blob)))
+
+    def close(self):
+        if getattr(self, "s", None):
+            lib().afqmc_destroy(self.s)
+            self.s = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def wmax_default(nwalkers: int) -> float:
+    return max(100.0, nwalkers / 10.0)
+
+
+__all__ = ["AfqmcRun", "Params", "Info", "AfqmcError", "default_params", "lib",
+           "afqmc_workspace_size", "afqmc_launch_count", "EXPORTED", "math"]

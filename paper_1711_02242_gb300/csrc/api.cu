@@ -1,0 +1,873 @@
+// C ABI of the AFQMC library: workspace plan, set-up, step sequencing.
+#include <cstdarg>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "kernels.cuh"
+#include "state.cuh"
+
+namespace afq {
+
+static thread_local char g_err[512] = "no error";
+int64_t g_launches = 0;
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+// ----------------------------------------------------------- workspace plan --
+namespace {
+struct Bump {
+  char* base;
+  size_t off = 0;
+  template <typename T>
+  T* take(size_t count) {
+    off = (off + 255) & ~size_t(255);
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += count * sizeof(T);
+    return p;
+  }
+};
+}  // namespace
+
+size_t plan(const afqmc_params& p, Bufs* b, char* base) {
+  Bufs tmp;
+  if (!b) b = &tmp;
+  const size_t M = p.M, N = p.N, G = p.nchol, W = p.nwalkers;
+  const size_t P = M * (M + 1) / 2;
+  const size_t nchunk = (G + exchange_chunk(p.N, p.nchol) - 1) / exchange_chunk(p.N, p.nchol);
+  Bump a{base};
+  // constants
+  b->LpT = a.take<double>(P * G);
+  b->Lh = a.take<double>(G * N * M);
+  b->hh = a.take<double>(N * M);
+  b->c = a.take<double>(G);
+  b->Bh = a.take<double>(M * M);
+  b->VTt = a.take<double>(N * M);
+  b->h1 = a.take<double>(M * M);
+  // walkers
+  b->phiT = a.take<double>(W * 2 * N * M);
+  b->thetaT = a.take<double>(W * 2 * N * M);
+  b->ld = a.take<double>(2 * W);
+  b->ld_new = a.take<double>(2 * W);
+  b->wt = a.take<double>(2 * W);
+  b->S = a.take<double>(W * 2 * N * N);
+  b->Sinv = a.take<double>(W * 2 * N * N);
+  b->t = a.take<double>(W * 2 * G);
+  b->x = a.take<double>(W * 2 * G);
+  b->scal = a.take<double>(8 * W);
+  b->eloc = a.take<double>(2 * W);
+  b->part = a.take<double>(W * nchunk * 2);
+  b->cum = a.take<double>(W);
+  b->parent = a.take<int>(W);
+  b->wtot = a.take<double>(8);
+  b->last = a.take<double>(8);
+  b->records = a.take<double>(4 * (size_t)(p.max_records > 0 ? p.max_records : 1));
+  b->counters = a.take<unsigned long long>(8);
+  // scratch: the set-up and the step never run at the same time
+  const size_t scratch_at = (a.off + 255) & ~size_t(255);
+  Bump s1{base, scratch_at};
+  b->Y = s1.take<double>(W * 2 * P);
+  b->T0 = s1.take<double>(W * 2 * N * M);
+  b->T1 = s1.take<double>(W * 2 * N * M);
+  b->acc = s1.take<double>(W * 2 * N * M);
+  b->tmp_ld = s1.take<double>(2 * W);
+  Bump s2{base, scratch_at};
+  b->Lfull = s2.take<double>(G * M * M);
+  b->L2 = s2.take<double>(M * M);
+  b->cLp = s2.take<double>(P);
+  b->E0 = s2.take<double>(M * M);
+  b->E1 = s2.take<double>(M * M);
+  b->X = s2.take<double>(M * M);
+  b->red = s2.take<double>(8);
+  b->P = (int)P;
+  b->nchunk = (int)nchunk;
+  b->gc = exchange_chunk(p.N, p.nchol);
+  return ((s1.off > s2.off ? s1.off : s2.off) + 255) & ~size_t(255);
+}
+
+// --------------------------------------------------------------- validation --
+static int check_params(const afqmc_params* p) {
+  if (!p) {
+    set_error("params is NULL");
+    return AFQMC_EINVAL;
+  }
+  if (p->M < 1 || p->N < 1 || p->N > p->M || p->nchol < 1 || p->nwalkers < 1) {
+    set_error("bad sizes M=%d N=%d nchol=%d nwalkers=%d", p->M, p->N, p->nchol, p->nwalkers);
+    return AFQMC_EINVAL;
+  }
+  if (p->N > 64) {
+    set_error("N=%d: at most 64 electrons per spin are supported", p->N);
+    return AFQMC_EUNSUPPORTED;
+  }
+  if (!(p->dt > 0.0) || !std::isfinite(p->dt)) {
+    set_error("dt must be positive and finite");
+    return AFQMC_EINVAL;
+  }
+  if (p->taylor_order < 1 || p->qr_period < 0 || p->pc_period < 0 || p->energy_period < 0 ||
+      p->max_records < 1 || p->reserved != 0) {
+    set_error("bad taylor_order / periods / max_records / reserved");
+    return AFQMC_EINVAL;
+  }
+  if (p->mode != AFQMC_PHASELESS && p->mode != AFQMC_FREE) {
+    set_error("unknown mode %d", p->mode);
+    return AFQMC_EINVAL;
+  }
+  if (p->mode == AFQMC_FREE && p->pc_period) {
+    set_error("the comb needs real weights: pc_period must be 0 for free projection");
+    return AFQMC_EINVAL;
+  }
+  if (p->precision != AFQMC_FP64) {
+    set_error("precision %d is not available in this build", p->precision);
+    return AFQMC_EUNSUPPORTED;
+  }
+  const double P = 0.5 * p->M * (p->M + 1.0);
+  if ((double)p->nwalkers * 2 * p->N > 65535.0 * 64 || P * p->nchol > 4e10) {
+    set_error("problem too large for this build");
+    return AFQMC_EUNSUPPORTED;
+  }
+  if (!std::isfinite(p->H0) || !(std::isnan(p->e_shift) || std::isfinite(p->e_shift))) {
+    set_error("H0 / e_shift not finite");
+    return AFQMC_ENONFINITE;
+  }
+  return AFQMC_OK;
+}
+
+static int all_finite(const double* v, size_t n, const char* what) {
+  for (size_t i = 0; i < n; ++i)
+    if (!std::isfinite(v[i])) {
+      set_error("%s[%zu] is not finite", what, i);
+      return AFQMC_ENONFINITE;
+    }
+  return AFQMC_OK;
+}
+
+// ------------------------------------------------------------ step pieces ---
+int overlap_update(afqmc_state* s, bool into_ld) {
+  const afqmc_params& p = s->p;
+  const Bufs& b = s->b;
+  GemmF64 g;
+  g.m = 2 * p.N * p.nwalkers;
+  g.n = p.N;
+  g.k = p.M;
+  g.A = b.phiT;
+  g.lda = p.M;
+  g.B = b.VTt;
+  g.ldb = p.M;
+  g.C = b.S;
+  g.ldc = p.N;
+  AFQ_TRY(gemm_nt_f64(g, s->st));
+  LuArgs lu{p.nwalkers, p.N, b.S, b.Sinv, into_ld ? b.ld : b.ld_new, b.wt};
+  AFQ_TRY(launch_lu_inv(lu, s->st));
+  ThetaArgs th{p.nwalkers, p.M, p.N, b.Sinv, b.phiT, b.thetaT, b.wt};
+  AFQ_TRY(launch_theta(th, s->st));
+  return AFQMC_OK;
+}
+
+int force_bias_gemm(afqmc_state* s) {
+  const afqmc_params& p = s->p;
+  const Bufs& b = s->b;
+  GemmF64 g;
+  g.m = 2 * p.nwalkers;
+  g.n = p.nchol;
+  g.k = p.N * p.M;
+  g.alpha = 2.0;
+  g.A = b.thetaT;
+  g.lda = (long)p.N * p.M;
+  g.B = b.Lh;
+  g.ldb = (long)p.N * p.M;
+  g.C = b.t;
+  g.ldc = p.nchol;
+  AFQ_TRY(gemm_nt_f64(g, s->st));
+  s->t_fresh = true;
+  return AFQMC_OK;
+}
+
+int energy_eval(afqmc_state* s, bool append) {
+  const afqmc_params& p = s->p;
+  const Bufs& b = s->b;
+  if (!s->t_fresh) AFQ_TRY(force_bias_gemm(s));
+  ExchArgs ex{p.nwalkers, p.M, p.N, p.nchol, b.gc, b.nchunk, b.Lh, b.thetaT, b.part, b.wt};
+  AFQ_TRY(launch_exchange(ex, s->st));
+  ElocArgs el{p.nwalkers, p.M, p.N, p.nchol, b.nchunk, p.H0, b.hh, b.thetaT, b.t, b.part, b.eloc, b.wt};
+  AFQ_TRY(launch_eloc(el, s->st));
+  RecordArgs rc;
+  rc.W = p.nwalkers;
+  rc.mode = p.mode;
+  rc.max_records = p.max_records;
+  rc.lo = s->elo;
+  rc.hi = s->ehi;
+  rc.eloc = b.eloc;
+  rc.wt = b.wt;
+  rc.records = append ? b.records : nullptr;
+  rc.rec_count = b.counters + CTR_RECORDS;
+  rc.last = b.last;
+  rc.step = reinterpret_cast<const int64_t*>(b.counters + CTR_STEP);
+  AFQ_TRY(launch_record(rc, s->st));
+  return AFQMC_OK;
+}
+
+static int step_once(afqmc_state* s) {
+  const afqmc_params& p = s->p;
+  const Bufs& b = s->b;
+  const int W = p.nwalkers, N = p.N, M = p.M, G = p.nchol;
+  // force bias traces t = 2 Tr(Lh_g Theta) for every walker (Eq. precomputing2)
+  if (!s->t_fresh) {
+    prof_begin(s, AFQMC_PH_FORCE_BIAS);
+    AFQ_TRY(force_bias_gemm(s));
+    prof_end(s);
+  }
+  // fields and shifted fields
+  FieldArgs fa{W, G, p.mode, p.seed, s->sdt, p.fb_cap, b.t, b.c, b.wt, b.x, b.scal,
+               reinterpret_cast<const int64_t*>(b.counters + CTR_STEP)};
+  prof_begin(s, AFQMC_PH_FIELDS);
+  AFQ_TRY(launch_field(fa, s->st));
+  prof_end(s);
+  // Y = sum_g x_g L_g (packed), the dense contraction with K = N_gamma
+  prof_begin(s, AFQMC_PH_V);
+  {
+    GemmF64 g;
+    g.m = 2 * W;
+    g.n = b.P;
+    g.k = G;
+    g.A = b.x;
+    g.lda = G;
+    g.B = b.LpT;
+    g.ldb = G;
+    g.C = b.Y;
+    g.ldc = b.P;
+    AFQ_TRY(gemm_nt_f64(g, s->st));
+  }
+  prof_end(s);
+  // Phi <- B_half Phi  (Phi^T <- Phi^T B_half, B_half symmetric)
+  prof_begin(s, AFQMC_PH_BHALF);
+  GemmF64 bh;
+  bh.m = 2 * N * W;
+  bh.n = M;
+  bh.k = M;
+  bh.A = b.phiT;
+  bh.lda = M;
+  bh.B = b.Bh;
+  bh.ldb = M;
+  bh.C = b.T0;
+  bh.ldc = M;
+  AFQ_TRY(gemm_nt_f64(bh, s->st));
+  prof_end(s);
+  // truncated Taylor series of exp(V) (Sec. 3.4.2)
+  prof_begin(s, AFQMC_PH_TAYLOR);
+  double* tin = b.T0;
+  double* tout = b.T1;
+  for (int k = 1; k <= p.taylor_order; ++k) {
+    TaylorArgs ta{W, M, N, b.P, k, s->sdt / k, b.Y, tin, tout, b.acc, b.wt};
+    AFQ_TRY(launch_taylor_term(ta, s->st));
+    double* t_ = tin;
+    tin = tout;
+    tout = t_;
+  }
+  prof_end(s);
+  // Phi <- B_half acc, stored only for live walkers
+  prof_begin(s, AFQMC_PH_BHALF);
+  bh.A = b.acc;
+  bh.C = b.phiT;
+  bh.mask = b.wt;
+  bh.mask_rows = 2 * N;
+  AFQ_TRY(gemm_nt_f64(bh, s->st));
+  prof_end(s);
+  // new overlap, log det, Theta; then the weights (and step += 1)
+  prof_begin(s, AFQMC_PH_OVERLAP);
+  AFQ_TRY(overlap_update(s, false));
+  prof_end(s);
+  WeightArgs wa{W, p.mode, p.dt, s->sdt, s->H0p, s->e_shift, s->wmax, b.ld_new, b.ld, b.scal,
+                b.wt, b.counters + CTR_NONFINITE,
+                reinterpret_cast<int64_t*>(b.counters + CTR_STEP)};
+  prof_begin(s, AFQMC_PH_WEIGHT);
+  AFQ_TRY(launch_weight(wa, s->st));
+  prof_end(s);
+  s->t_fresh = false;
+  s->h_step += 1;
+  const int64_t n = s->h_step;
+  if (p.qr_period && n % p.qr_period == 0) {
+    prof_begin(s, AFQMC_PH_QR);
+    MgsArgs ma{W, M, N, b.phiT, b.wt};
+    AFQ_TRY(launch_mgs(ma, s->st));
+    AFQ_TRY(overlap_update(s, true));
+    prof_end(s);
+  }
+  if (p.pc_period && n % p.pc_period == 0) {
+    prof_begin(s, AFQMC_PH_COMB);
+    CombArgs ca{W, M, N, p.seed, reinterpret_cast<const int64_t*>(b.counters + CTR_STEP),
+                b.wt, b.cum, b.parent, b.phiT, b.thetaT, b.ld, b.T0, b.T1, b.tmp_ld, b.wtot};
+    AFQ_TRY(launch_comb(ca, s->st));
+    prof_end(s);
+  }
+  if (p.energy_period && n % p.energy_period == 0) {
+    prof_begin(s, AFQMC_PH_ENERGY);
+    AFQ_TRY(energy_eval(s, true));
+    prof_end(s);
+  }
+  return AFQMC_OK;
+}
+
+// B_half = exp(X), X = -dt v0'/2, by scaling and squaring of a degree-18
+// Taylor polynomial evaluated by Horner's rule (all float64 GEMMs).
+static int expm_device(afqmc_state* s) {
+  const afqmc_params& p = s->p;
+  const Bufs& b = s->b;
+  const int M = p.M;
+  AFQ_TRY(launch_norm1(b.X, b.red, M, s->st));
+  double nrm = 0.0;
+  AFQ_CUDA(cudaMemcpyAsync(&nrm, b.red, sizeof(double), cudaMemcpyDeviceToHost, s->st));
+  AFQ_CUDA(cudaStreamSynchronize(s->st));
+  if (!std::isfinite(nrm)) {
+    set_error("one-body operator is not finite");
+    return AFQMC_ENONFINITE;
+  }
+  int sq = 0;
+  while (nrm > 0.5 && sq < 60) {
+    nrm *= 0.5;
+    ++sq;
+  }
+  if (sq) AFQ_TRY(launch_scale(b.X, (long)M * M, std::ldexp(1.0, -sq), s->st));
+  double* E = b.E0;
+  double* F = b.E1;
+  AFQ_TRY(launch_fill_identity(E, M, 1.0, s->st));
+  for (int k = 18; k >= 1; --k) {
+    AFQ_TRY(launch_fill_identity(F, M, 1.0, s->st));
+    GemmF64 g;
+    g.m = g.n = g.k = M;
+    g.alpha = 1.0 / k;
+    g.beta = 1.0;
+    g.A = b.X;
+    g.lda = M;
+    g.B = E;
+    g.ldb = M;
+    g.C = F;
+    g.ldc = M;
+    AFQ_TRY(gemm_nt_f64(g, s->st));
+    double* t_ = E;
+    E = F;
+    F = t_;
+  }
+  for (int i = 0; i < sq; ++i) {
+    GemmF64 g;
+    g.m = g.n = g.k = M;
+    g.A = E;
+    g.lda = M;
+    g.B = E;
+    g.ldb = M;
+    g.C = F;
+    g.ldc = M;
+    AFQ_TRY(gemm_nt_f64(g, s->st));
+    double* t_ = E;
+    E = F;
+    F = t_;
+  }
+  AFQ_CUDA(cudaMemcpyAsync(b.Bh, E, sizeof(double) * M * M, cudaMemcpyDeviceToDevice, s->st));
+  return AFQMC_OK;
+}
+
+static int setup_device(afqmc_state* s, const double* h1, const double* L, const double* trial) {
+  const afqmc_params& p = s->p;
+  const Bufs& b = s->b;
+  const int M = p.M, N = p.N, G = p.nchol, W = p.nwalkers;
+  cudaStream_t st = s->st;
+  std::vector<double> vtt((size_t)N * M);
+  for (int i = 0; i < N; ++i)
+    for (int q = 0; q < M; ++q) vtt[(size_t)i * M + q] = trial[(size_t)q * N + i];
+  AFQ_CUDA(cudaMemcpyAsync(b.VTt, vtt.data(), sizeof(double) * N * M, cudaMemcpyHostToDevice, st));
+  AFQ_CUDA(cudaMemcpyAsync(b.h1, h1, sizeof(double) * M * M, cudaMemcpyHostToDevice, st));
+  AFQ_CUDA(cudaMemcpyAsync(b.Lfull, L, sizeof(double) * G * M * M, cudaMemcpyHostToDevice, st));
+  AFQ_CUDA(cudaMemsetAsync(b.counters, 0, 8 * sizeof(unsigned long long), st));
+  // packed, transposed Cholesky vectors for the V contraction
+  AFQ_TRY(launch_pack_transpose(b.Lfull, b.LpT, G, M, st));
+  // half-rotated vectors Lh_g = V_T^T L_g and hh = V_T^T h (Eq. precomputing2)
+  {
+    GemmF64 g;
+    g.m = N;
+    g.n = M;
+    g.k = M;
+    g.batch = G;
+    g.A = b.VTt;
+    g.lda = M;
+    g.B = b.Lfull;
+    g.ldb = M;
+    g.sBb = (long)M * M;
+    g.C = b.Lh;
+    g.ldc = M;
+    g.sCb = (long)N * M;
+    AFQ_TRY(gemm_nt_f64(g, st));
+    GemmF64 h;
+    h.m = N;
+    h.n = M;
+    h.k = M;
+    h.A = b.VTt;
+    h.lda = M;
+    h.B = b.h1;
+    h.ldb = M;
+    h.C = b.hh;
+    h.ldc = M;
+    AFQ_TRY(gemm_nt_f64(h, st));
+  }
+  // c_g = 2 Tr(L_g P) = 2 Tr(Lh_g V_T): vbar_g = i c_g (Sec. 2.4)
+  AFQ_TRY(launch_rowdot(b.Lh, b.VTt, b.c, G, N * M, 2.0, st));
+  // sum_g L_g L_g
+  {
+    GemmF64 g;
+    g.m = g.n = g.k = M;
+    g.kb = G;
+    g.A = b.Lfull;
+    g.lda = M;
+    g.sAk = (long)M * M;
+    g.B = b.Lfull;
+    g.ldb = M;
+    g.sBk = (long)M * M;
+    g.C = b.L2;
+    g.ldc = M;
+    AFQ_TRY(gemm_nt_f64(g, st));
+  }
+  // sum_g c_g L_g (packed)
+  {
+    GemmF64 g;
+    g.m = 1;
+    g.n = b.P;
+    g.k = G;
+    g.A = b.c;
+    g.lda = G;
+    g.B = b.LpT;
+    g.ldb = G;
+    g.C = b.cLp;
+    g.ldc = b.P;
+    AFQ_TRY(gemm_nt_f64(g, st));
+  }
+  AFQ_TRY(launch_v0p(b.h1, b.L2, b.cLp, b.X, M, -0.5 * p.dt, st));
+  AFQ_TRY(launch_sumsq(b.c, b.red + 1, G, st));
+  double sumc2 = 0.0;
+  AFQ_CUDA(cudaMemcpyAsync(&sumc2, b.red + 1, sizeof(double), cudaMemcpyDeviceToHost, st));
+  AFQ_TRY(expm_device(s));  // synchronises once
+  s->H0p = p.H0 - 0.5 * sumc2;
+  // walkers at the trial, their overlaps, and the trial energy
+  AFQ_TRY(launch_init_walkers(b.VTt, b.phiT, b.wt, W, N, M, st));
+  AFQ_TRY(overlap_update(s, true));
+  s->t_fresh = false;
+  s->elo = -INFINITY;
+  s->ehi = INFINITY;
+  AFQ_TRY(energy_eval(s, false));
+  double e0[2];
+  AFQ_CUDA(cudaMemcpyAsync(e0, b.eloc, sizeof(e0), cudaMemcpyDeviceToHost, st));
+  AFQ_CUDA(cudaStreamSynchronize(st));
+  s->E_T = e0[0];
+  s->e_shift = std::isnan(p.e_shift) ? s->E_T : p.e_shift;
+  s->wmax = std::isnan(p.wmax) ? std::fmax(100.0, W / 10.0) : p.wmax;
+  if (p.ecap_C > 0.0) {
+    const double half = std::sqrt(p.ecap_C / p.dt);
+    s->elo = s->E_T - half;
+    s->ehi = s->E_T + half;
+  }
+  if (!std::isfinite(s->E_T)) {
+    set_error("trial energy is not finite");
+    return AFQMC_ENONFINITE;
+  }
+  return AFQMC_OK;
+}
+
+}  // namespace afq
+
+static_assert(sizeof(afqmc_params) == 104, "afqmc_params layout");
+static_assert(sizeof(afqmc_info) == 64, "afqmc_info layout");
+
+using namespace afq;
+
+// ================================================================= C ABI ====
+extern "C" {
+
+void afqmc_default_params(afqmc_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->dt = 0.005;
+  p->e_shift = NAN;
+  p->H0 = 0.0;
+  p->seed = 1;
+  p->taylor_order = 6;
+  p->qr_period = 5;
+  p->pc_period = 0;
+  p->energy_period = 1;
+  p->precision = AFQMC_FP64;
+  p->mode = AFQMC_PHASELESS;
+  p->ecap_C = 2.0;
+  p->fb_cap = 1.0;
+  p->wmax = NAN;
+  p->max_records = 4096;
+}
+
+int afqmc_workspace_size(const afqmc_params* p, size_t* bytes) {
+  AFQ_TRY(check_params(p));
+  if (!bytes) {
+    set_error("bytes is NULL");
+    return AFQMC_EINVAL;
+  }
+  *bytes = plan(*p, nullptr, nullptr);
+  return AFQMC_OK;
+}
+
+int afqmc_init(const afqmc_params* p, const double* h1, const double* L, const double* trial,
+               void* d_workspace, size_t ws_bytes, void* stream, afqmc_state** out) {
+  if (!out) {
+    set_error("out is NULL");
+    return AFQMC_EINVAL;
+  }
+  *out = nullptr;
+  AFQ_TRY(check_params(p));
+  if (!h1 || !L || !trial || !d_workspace) {
+    set_error("h1, L, trial and d_workspace are required");
+    return AFQMC_EINVAL;
+  }
+  if (reinterpret_cast<uintptr_t>(d_workspace) % 256) {
+    set_error("workspace must be 256-byte aligned");
+    return AFQMC_EINVAL;
+  }
+  const size_t need = plan(*p, nullptr, nullptr);
+  if (ws_bytes < need) {
+    set_error("workspace %zu bytes < %zu needed", ws_bytes, need);
+    return AFQMC_ENOSPC;
+  }
+  const size_t M = p->M, N = p->N, G = p->nchol;
+  AFQ_TRY(all_finite(h1, M * M, "h1"));
+  AFQ_TRY(all_finite(trial, M * N, "trial"));
+  AFQ_TRY(all_finite(L, G * M * M, "L"));
+  afqmc_state* s = new (std::nothrow) afqmc_state();
+  if (!s) {
+    set_error("out of host memory");
+    return AFQMC_EINVAL;
+  }
+  s->p = *p;
+  s->st = static_cast<cudaStream_t>(stream);
+  s->ws = static_cast<char*>(d_workspace);
+  s->ws_bytes = ws_bytes;
+  plan(*p, &s->b, s->ws);
+  s->sdt = std::sqrt(p->dt);
+  int r = setup_device(s, h1, L, trial);
+  if (r != AFQMC_OK) {
+    delete s;
+    return r;
+  }
+  s->valid = true;
+  *out = s;
+  return AFQMC_OK;
+}
+
+#define AFQ_STATE(s)                       \
+  do {                                     \
+    if (!(s) || !(s)->valid) {             \
+      set_error("invalid state");          \
+      return AFQMC_ESTATE;                 \
+    }                                      \
+  } while (0)
+
+int afqmc_propagate(afqmc_state* s, int32_t nsteps) {
+  AFQ_STATE(s);
+  if (nsteps < 0) {
+    set_error("nsteps < 0");
+    return AFQMC_EINVAL;
+  }
+  for (int i = 0; i < nsteps; ++i) AFQ_TRY(step_once(s));
+  return AFQMC_OK;
+}
+
+int afqmc_energy(afqmc_state* s, double* E, double* wsum) {
+  AFQ_STATE(s);
+  AFQ_TRY(energy_eval(s, false));
+  double last[8];
+  AFQ_CUDA(cudaMemcpyAsync(last, s->b.last, sizeof(last), cudaMemcpyDeviceToHost, s->st));
+  AFQ_CUDA(cudaStreamSynchronize(s->st));
+  if (E) *E = last[4];
+  if (wsum) *wsum = last[1];
+  return AFQMC_OK;
+}
+
+int afqmc_local_energies(afqmc_state* s, double* eloc) {
+  AFQ_STATE(s);
+  if (!eloc) {
+    set_error("eloc is NULL");
+    return AFQMC_EINVAL;
+  }
+  AFQ_TRY(energy_eval(s, false));
+  AFQ_CUDA(cudaMemcpyAsync(eloc, s->b.eloc, sizeof(double) * 2 * s->p.nwalkers,
+                           cudaMemcpyDeviceToHost, s->st));
+  AFQ_CUDA(cudaStreamSynchronize(s->st));
+  return AFQMC_OK;
+}
+
+int afqmc_get_walkers(afqmc_state* s, double* phi, double* weight, double* logov) {
+  AFQ_STATE(s);
+  const afqmc_params& p = s->p;
+  const size_t W = p.nwalkers, N = p.N, M = p.M;
+  if (phi) {
+    std::vector<double> h(W * 2 * N * M);
+    AFQ_CUDA(cudaMemcpyAsync(h.data(), s->b.phiT, sizeof(double) * h.size(),
+                             cudaMemcpyDeviceToHost, s->st));
+    AFQ_CUDA(cudaStreamSynchronize(s->st));
+    for (size_t w = 0; w < W; ++w)
+      for (size_t c = 0; c < 2; ++c)
+        for (size_t i = 0; i < N; ++i)
+          for (size_t q = 0; q < M; ++q)
+            phi[((w * M + q) * N + i) * 2 + c] = h[((w * 2 + c) * N + i) * M + q];
+  }
+  if (weight)
+    AFQ_CUDA(cudaMemcpyAsync(weight, s->b.wt, sizeof(double) * 2 * W, cudaMemcpyDeviceToHost, s->st));
+  if (logov)
+    AFQ_CUDA(cudaMemcpyAsync(logov, s->b.ld, sizeof(double) * 2 * W, cudaMemcpyDeviceToHost, s->st));
+  AFQ_CUDA(cudaStreamSynchronize(s->st));
+  return AFQMC_OK;
+}
+
+int afqmc_set_walkers(afqmc_state* s, const double* phi, const double* weight) {
+  AFQ_STATE(s);
+  if (!phi || !weight) {
+    set_error("phi and weight are required");
+    return AFQMC_EINVAL;
+  }
+  const afqmc_params& p = s->p;
+  const size_t W = p.nwalkers, N = p.N, M = p.M;
+  AFQ_TRY(all_finite(phi, W * M * N * 2, "phi"));
+  AFQ_TRY(all_finite(weight, W * 2, "weight"));
+  std::vector<double> h(W * 2 * N * M);
+  for (size_t w = 0; w < W; ++w)
+    for (size_t c = 0; c < 2; ++c)
+      for (size_t i = 0; i < N; ++i)
+        for (size_t q = 0; q < M; ++q)
+          h[((w * 2 + c) * N + i) * M + q] = phi[((w * M + q) * N + i) * 2 + c];
+  AFQ_CUDA(cudaMemcpyAsync(s->b.phiT, h.data(), sizeof(double) * h.size(), cudaMemcpyHostToDevice, s->st));
+  AFQ_CUDA(cudaMemcpyAsync(s->b.wt, weight, sizeof(double) * 2 * W, cudaMemcpyHostToDevice, s->st));
+  AFQ_TRY(overlap_update(s, true));
+  s->t_fresh = false;
+  AFQ_CUDA(cudaStreamSynchronize(s->st));
+  return AFQMC_OK;
+}
+
+int afqmc_get_energy_log(afqmc_state* s, double* rec, int32_t cap, int32_t* n) {
+  AFQ_STATE(s);
+  if (!n || (cap > 0 && !rec) || cap < 0) {
+    set_error("bad arguments");
+    return AFQMC_EINVAL;
+  }
+  unsigned long long count = 0;
+  AFQ_CUDA(cudaMemcpyAsync(&count, s->b.counters + CTR_RECORDS, sizeof(count),
+                           cudaMemcpyDeviceToHost, s->st));
+  std::vector<double> all(4 * (size_t)s->p.max_records);
+  AFQ_CUDA(cudaMemcpyAsync(all.data(), s->b.records, sizeof(double) * all.size(),
+                           cudaMemcpyDeviceToHost, s->st));
+  AFQ_CUDA(cudaStreamSynchronize(s->st));
+  const unsigned long long R = (unsigned long long)s->p.max_records;
+  const unsigned long long have = count < R ? count : R;
+  const unsigned long long first = count - have;
+  const unsigned long long ncopy = have < (unsigned long long)cap ? have : (unsigned long long)cap;
+  for (unsigned long long i = 0; i < ncopy; ++i) {
+    const unsigned long long slot = (first + i) % R;
+    std::memcpy(rec + 4 * i, all.data() + 4 * slot, 4 * sizeof(double));
+  }
+  *n = (int32_t)ncopy;
+  return AFQMC_OK;
+}
+
+int afqmc_get_info(afqmc_state* s, afqmc_info* info) {
+  AFQ_STATE(s);
+  if (!info) {
+    set_error("info is NULL");
+    return AFQMC_EINVAL;
+  }
+  unsigned long long ctr[8];
+  std::vector<double> wt(2 * (size_t)s->p.nwalkers);
+  AFQ_CUDA(cudaMemcpyAsync(ctr, s->b.counters, sizeof(ctr), cudaMemcpyDeviceToHost, s->st));
+  AFQ_CUDA(cudaMemcpyAsync(wt.data(), s->b.wt, sizeof(double) * wt.size(), cudaMemcpyDeviceToHost, s->st));
+  AFQ_CUDA(cudaStreamSynchronize(s->st));
+  info->E_T = s->E_T;
+  info->H0p = s->H0p;
+  info->e_shift = s->e_shift;
+  info->wmax = s->wmax;
+  info->step = (int64_t)ctr[CTR_STEP];
+  info->nonfinite = (int64_t)ctr[CTR_NONFINITE];
+  info->launches = g_launches;
+  int alive = 0;
+  for (int w = 0; w < s->p.nwalkers; ++w) alive += (wt[2 * w] != 0.0 || wt[2 * w + 1] != 0.0);
+  info->alive = alive;
+  info->status = (int32_t)ctr[CTR_STATUS];
+  return AFQMC_OK;
+}
+
+namespace {
+struct CkptHeader {
+  uint64_t magic;
+  int32_t M, N, nchol, nwalkers;
+  int64_t step;
+  uint64_t records, nonfinite;
+  uint64_t seed;
+  int32_t max_records, reserved;
+};
+constexpr uint64_t kMagic = 0x31434D5146414731ull;
+}  // namespace
+
+int afqmc_save(afqmc_state* s, void* buf, size_t* bytes) {
+  AFQ_STATE(s);
+  if (!bytes) {
+    set_error("bytes is NULL");
+    return AFQMC_EINVAL;
+  }
+  const afqmc_params& p = s->p;
+  const size_t nw = (size_t)p.nwalkers * 2 * p.N * p.M;
+  const size_t need = sizeof(CkptHeader) +
+                      sizeof(double) * (2 * nw + 4 * (size_t)p.nwalkers + 4 * (size_t)p.max_records);
+  if (!buf) {
+    *bytes = need;
+    return AFQMC_OK;
+  }
+  if (*bytes < need) {
+    set_error("checkpoint buffer %zu < %zu", *bytes, need);
+    return AFQMC_ENOSPC;
+  }
+  unsigned long long ctr[8];
+  AFQ_CUDA(cudaMemcpyAsync(ctr, s->b.counters, sizeof(ctr), cudaMemcpyDeviceToHost, s->st));
+  char* o = static_cast<char*>(buf) + sizeof(CkptHeader);
+  double* d = reinterpret_cast<double*>(o);
+  AFQ_CUDA(cudaMemcpyAsync(d, s->b.phiT, sizeof(double) * nw, cudaMemcpyDeviceToHost, s->st));
+  AFQ_CUDA(cudaMemcpyAsync(d + nw, s->b.thetaT, sizeof(double) * nw, cudaMemcpyDeviceToHost, s->st));
+  AFQ_CUDA(cudaMemcpyAsync(d + 2 * nw, s->b.wt, sizeof(double) * 2 * p.nwalkers, cudaMemcpyDeviceToHost, s->st));
+  AFQ_CUDA(cudaMemcpyAsync(d + 2 * nw + 2 * p.nwalkers, s->b.ld, sizeof(double) * 2 * p.nwalkers,
+                           cudaMemcpyDeviceToHost, s->st));
+  AFQ_CUDA(cudaMemcpyAsync(d + 2 * nw + 4 * p.nwalkers, s->b.records,
+                           sizeof(double) * 4 * p.max_records, cudaMemcpyDeviceToHost, s->st));
+  AFQ_CUDA(cudaStreamSynchronize(s->st));
+  CkptHeader h{kMagic, p.M, p.N, p.nchol, p.nwalkers, s->h_step, ctr[CTR_RECORDS],
+               ctr[CTR_NONFINITE], p.seed, p.max_records, 0};
+  std::memcpy(buf, &h, sizeof(h));
+  *bytes = need;
+  return AFQMC_OK;
+}
+
+int afqmc_load(afqmc_state* s, const void* buf, size_t bytes) {
+  AFQ_STATE(s);
+  const afqmc_params& p = s->p;
+  if (!buf || bytes < sizeof(CkptHeader)) {
+    set_error("checkpoint too small");
+    return AFQMC_EINVAL;
+  }
+  CkptHeader h;
+  std::memcpy(&h, buf, sizeof(h));
+  const size_t nw = (size_t)p.nwalkers * 2 * p.N * p.M;
+  const size_t need = sizeof(CkptHeader) +
+                      sizeof(double) * (2 * nw + 4 * (size_t)p.nwalkers + 4 * (size_t)p.max_records);
+  if (h.magic != kMagic || h.M != p.M || h.N != p.N || h.nchol != p.nchol ||
+      h.nwalkers != p.nwalkers || h.max_records != p.max_records || h.seed != p.seed ||
+      bytes < need) {
+    set_error("checkpoint does not match this state");
+    return AFQMC_EINVAL;
+  }
+  const double* d = reinterpret_cast<const double*>(static_cast<const char*>(buf) + sizeof(CkptHeader));
+  AFQ_CUDA(cudaMemcpyAsync(s->b.phiT, d, sizeof(double) * nw, cudaMemcpyHostToDevice, s->st));
+  AFQ_CUDA(cudaMemcpyAsync(s->b.thetaT, d + nw, sizeof(double) * nw, cudaMemcpyHostToDevice, s->st));
+  AFQ_CUDA(cudaMemcpyAsync(s->b.wt, d + 2 * nw, sizeof(double) * 2 * p.nwalkers, cudaMemcpyHostToDevice, s->st));
+  AFQ_CUDA(cudaMemcpyAsync(s->b.ld, d + 2 * nw + 2 * p.nwalkers, sizeof(double) * 2 * p.nwalkers,
+                           cudaMemcpyHostToDevice, s->st));
+  AFQ_CUDA(cudaMemcpyAsync(s->b.records, d + 2 * nw + 4 * p.nwalkers, sizeof(double) * 4 * p.max_records,
+                           cudaMemcpyHostToDevice, s->st));
+  unsigned long long ctr[8] = {0};
+  ctr[CTR_STEP] = (unsigned long long)h.step;
+  ctr[CTR_RECORDS] = h.records;
+  ctr[CTR_NONFINITE] = h.nonfinite;
+  AFQ_CUDA(cudaMemcpyAsync(s->b.counters, ctr, sizeof(ctr), cudaMemcpyHostToDevice, s->st));
+  AFQ_CUDA(cudaStreamSynchronize(s->st));
+  s->h_step = h.step;
+  s->t_fresh = false;
+  return AFQMC_OK;
+}
+
+int afqmc_destroy(afqmc_state* s) {
+  if (!s) return AFQMC_OK;
+  s->valid = false;
+  delete s;
+  return AFQMC_OK;
+}
+
+const char* afqmc_last_error(void) { return g_err; }
+
+int64_t afqmc_launch_count(void) { return g_launches; }
+
+}  // extern "C"
+
+namespace afq {
+int launch_philox(uint64_t key, const uint32_t* ctr, long n, uint32_t* out, cudaStream_t st);
+int launch_fields(uint64_t seed, uint32_t step, int w0, int nw, int G, double* out,
+                  cudaStream_t st);
+}  // namespace afq
+
+extern "C" {
+int afqmc_philox4x32_10(uint64_t key, const uint32_t* d_ctr, int64_t n, uint32_t* d_out,
+                        void* stream) {
+  if (n < 0 || (n > 0 && (!d_ctr || !d_out))) {
+    afq::set_error("bad arguments");
+    return AFQMC_EINVAL;
+  }
+  return afq::launch_philox(key, d_ctr, (long)n, d_out, static_cast<cudaStream_t>(stream));
+}
+
+int afqmc_gaussian_fields(uint64_t seed, int64_t step, int32_t w0, int32_t nw, int32_t nchol,
+                          double* d_out, void* stream) {
+  if (step < 0 || step > 0xFFFFFFFFll || w0 < 0 || nw < 0 || nchol < 1 || (nw > 0 && !d_out)) {
+    afq::set_error("bad arguments");
+    return AFQMC_EINVAL;
+  }
+  return afq::launch_fields(seed, (uint32_t)step, w0, nw, nchol, d_out,
+                            static_cast<cudaStream_t>(stream));
+}
+}  // extern "C"
+
+extern "C" {
+int afqmc_profile_start(afqmc_state* s, int32_t max_steps) {
+  AFQ_STATE(s);
+  if (max_steps < 1) {
+    afq::set_error("max_steps must be positive");
+    return AFQMC_EINVAL;
+  }
+  afq::Profiler& P = s->prof;
+  for (cudaEvent_t e : P.ev) cudaEventDestroy(e);
+  P = afq::Profiler();
+  const int pairs = max_steps * (AFQMC_NPHASE + 2);
+  P.ev.resize(2 * (size_t)pairs);
+  for (auto& e : P.ev) AFQ_CUDA(cudaEventCreate(&e));
+  P.phase.assign(pairs, -1);
+  P.kern.assign(pairs, 0);
+  P.max_events = pairs;
+  P.on = true;
+  return AFQMC_OK;
+}
+
+int afqmc_profile_stop(afqmc_state* s, double* ms, int64_t* count, int64_t* kernels) {
+  AFQ_STATE(s);
+  afq::Profiler& P = s->prof;
+  if (!P.on) {
+    afq::set_error("profiling was not started");
+    return AFQMC_ESTATE;
+  }
+  AFQ_CUDA(cudaStreamSynchronize(s->st));
+  for (int i = 0; i < AFQMC_NPHASE; ++i) {
+    if (ms) ms[i] = 0.0;
+    if (count) count[i] = 0;
+    if (kernels) kernels[i] = 0;
+  }
+  for (int i = 0; i < P.used; ++i) {
+    float t = 0.f;
+    AFQ_CUDA(cudaEventElapsedTime(&t, P.ev[2 * i], P.ev[2 * i + 1]));
+    const int ph = P.phase[i];
+    if (ms) ms[ph] += t;
+    if (count) count[ph] += 1;
+    if (kernels) kernels[ph] += P.kern[i];
+  }
+  for (cudaEvent_t e : P.ev) cudaEventDestroy(e);
+  P = afq::Profiler();
+  return AFQMC_OK;
+}
+}  // extern "C"

@@ -1,0 +1,76 @@
+// Host-side state of one AFQMC run (internal header).
+#pragma once
+
+#include <vector>
+
+#include "kernels.cuh"
+
+namespace afq {
+
+enum { CTR_STEP = 0, CTR_RECORDS = 1, CTR_NONFINITE = 2, CTR_STATUS = 3 };
+
+// Device buffers carved out of the caller's workspace.
+struct Bufs {
+  // constants of the run
+  double *LpT, *Lh, *hh, *c, *Bh, *VTt, *h1;
+  // walkers
+  double *phiT, *thetaT, *ld, *ld_new, *wt, *S, *Sinv, *t, *x, *scal, *eloc, *part;
+  double *cum, *wtot, *last, *records;
+  int* parent;
+  unsigned long long* counters;  // CTR_*
+  // step scratch
+  double *Y, *T0, *T1, *acc, *tmp_ld;
+  // set-up scratch (aliases the step scratch)
+  double *Lfull, *L2, *cLp, *E0, *E1, *X, *red;
+  int P, nchunk, gc;
+};
+
+size_t plan(const afqmc_params& p, Bufs* b, char* base);
+
+}  // namespace afq
+
+namespace afq {
+// CUDA-event timing of the phases of a step (afqmc_profile_start/stop).
+struct Profiler {
+  bool on = false;
+  int max_events = 0, used = 0;
+  std::vector<cudaEvent_t> ev;  // pairs (begin, end)
+  std::vector<int> phase;       // phase of each pair
+  std::vector<int64_t> kern;    // kernels launched inside each pair
+  int open_phase = -1;
+  int64_t open_launch = 0;
+};
+}  // namespace afq
+
+struct afqmc_state {
+  afqmc_params p;
+  cudaStream_t st = nullptr;
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+  afq::Bufs b{};
+  double E_T = 0, H0p = 0, e_shift = 0, wmax = 0, sdt = 0, elo = 0, ehi = 0;
+  int64_t h_step = 0;
+  bool t_fresh = false;
+  bool valid = false;
+  afq::Profiler prof;
+};
+
+namespace afq {
+// Open / close a timed phase on the state's stream (no-ops unless profiling).
+inline void prof_begin(afqmc_state* s, int phase) {
+  Profiler& P = s->prof;
+  if (!P.on || P.used >= P.max_events) return;
+  cudaEventRecord(P.ev[2 * P.used], s->st);
+  P.open_phase = phase;
+  P.open_launch = g_launches;
+}
+inline void prof_end(afqmc_state* s) {
+  Profiler& P = s->prof;
+  if (!P.on || P.open_phase < 0) return;
+  cudaEventRecord(P.ev[2 * P.used + 1], s->st);
+  P.phase[P.used] = P.open_phase;
+  P.kern[P.used] = g_launches - P.open_launch;
+  P.used++;
+  P.open_phase = -1;
+}
+}  // namespace afq

@@ -1,0 +1,909 @@
+// Per-walker kernels of the float64 path and the set-up kernels.
+//
+// Layouts (W walkers, M orbitals, N electrons per spin, G Cholesky vectors,
+// P = M(M+1)/2):
+//   phiT, thetaT [W][2][N][M]  orbital-major walkers (re plane, im plane)
+//   t, x         [W][2][G]     force-bias traces / shifted fields
+//   Y            [W][2][P]     packed sum_g x_g L_g (upper triangle, row-major)
+//   weights      [W][2]        (re, im); phaseless walks keep im = 0
+#include "kernels.cuh"
+
+namespace afq {
+
+__host__ __device__ inline long packed_index(int p, int q, int M) {
+  // p <= q: rows of the upper triangle stored one after another
+  return (long)p * M - (long)p * (p - 1) / 2 + (q - p);
+}
+
+// ------------------------------------------------------------------ fields --
+// Force bias (Eq. fb with the mean-field background of Sec. 2.4):
+// xbar_g = -i sqrt(dt) (t_g - c_g), t_g = 2 Tr(Lh_g Theta); magnitude capped
+// at fb_cap with the phase kept (Appendix B).  Fields xi_g ~ N(0,1) from
+// Philox; x = xi - xbar.  Per-walker sums for the weight: sum xi xbar,
+// sum xbar^2 (Eq. hybrid-wt) and sum x c (the scalar of B(x - xbar)).
+__global__ void __launch_bounds__(256) k_field(FieldArgs a) {
+  __shared__ double sh[32];
+  const int w = blockIdx.x;
+  const bool alive = walker_alive(a.wt, w);
+  double s0 = 0, s1 = 0, s2 = 0, s3 = 0, s4 = 0, s5 = 0;
+  const long base = (long)w * 2 * a.G;
+  const double* tr = a.t + base;
+  const double* ti = tr + a.G;
+  double* xr = a.x + base;
+  double* xim = xr + a.G;
+  const int npair = (a.G + 1) / 2;
+  for (int k = threadIdx.x; k < npair; k += blockDim.x) {
+    double xa, xb;
+    field_pair(a.seed, (uint32_t)*a.dstep, (uint32_t)w, (uint32_t)k, &xa, &xb);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int g = 2 * k + h;
+      if (g >= a.G) break;
+      const double xi = h ? xb : xa;
+      double br = 0.0, bi = 0.0;
+      if (a.mode == AFQMC_PHASELESS) {
+        br = a.sdt * ti[g];
+        bi = -a.sdt * (tr[g] - a.c[g]);
+        if (a.fb_cap > 0.0) {
+          const double mag = hypot(br, bi);
+          if (mag > a.fb_cap) {
+            const double f = a.fb_cap / mag;
+            br *= f;
+            bi *= f;
+          }
+        }
+      }
+      double vr = xi - br, vi = -bi;
+      if (!alive) vr = vi = 0.0;
+      xr[g] = vr;
+      xim[g] = vi;
+      s0 += xi * br;
+      s1 += xi * bi;
+      s2 += br * br - bi * bi;
+      s3 += 2.0 * br * bi;
+      s4 += a.c[g] * vr;
+      s5 += a.c[g] * vi;
+    }
+  }
+  double r;
+  r = block_sum(s0, sh); if (threadIdx.x == 0) a.scal[8L * w + 0] = r;
+  r = block_sum(s1, sh); if (threadIdx.x == 0) a.scal[8L * w + 1] = r;
+  r = block_sum(s2, sh); if (threadIdx.x == 0) a.scal[8L * w + 2] = r;
+  r = block_sum(s3, sh); if (threadIdx.x == 0) a.scal[8L * w + 3] = r;
+  r = block_sum(s4, sh); if (threadIdx.x == 0) a.scal[8L * w + 4] = r;
+  r = block_sum(s5, sh); if (threadIdx.x == 0) a.scal[8L * w + 5] = r;
+}
+
+int launch_field(const FieldArgs& a, cudaStream_t st) {
+  AFQ_LAUNCH(k_field, a.W, 256, 0, st, a);
+  return AFQMC_OK;
+}
+
+// ------------------------------------------------------------ Taylor term --
+// One term of the truncated series T_n(V) Phi = sum_k V^k Phi / k!
+// (Sec. 3.4.2): out = V * in / k with V = i sqrt(dt) sum_g x_g L_g complex
+// symmetric, read from the packed Y = sum_g x_g L_g as
+// V = sqrt(dt) (-Im Y + i Re Y).  In transposed storage out^T = in^T V.
+namespace {
+constexpr int TT_P = 64, TT_Q = 16, TT_NMAX = 64;
+}
+__global__ void __launch_bounds__(256) k_taylor_term(TaylorArgs a) {
+  __shared__ double Ys[2][TT_Q][TT_P];
+  __shared__ double Ts[2][TT_NMAX][TT_Q + 1];
+  const int w = blockIdx.y;
+  if (!walker_alive(a.wt, w)) return;
+  const int p0 = blockIdx.x * TT_P;
+  const int tx = threadIdx.x % TT_P, ty = threadIdx.x / TT_P;  // 4 rows of i
+  const int M = a.M, N = a.N;
+  const double* Yr = a.Y + (long)w * 2 * a.P;
+  const double* Yi = Yr + a.P;
+  const long wo = (long)w * 2 * N * M;
+  const double* tin = a.tin + wo;
+  double accR[TT_NMAX / 4], accI[TT_NMAX / 4];
+#pragma unroll
+  for (int r = 0; r < TT_NMAX / 4; ++r) accR[r] = accI[r] = 0.0;
+  for (int q0 = 0; q0 < M; q0 += TT_Q) {
+    for (int idx = threadIdx.x; idx < TT_Q * TT_P; idx += blockDim.x) {
+      const int qq = idx / TT_P, pp = idx % TT_P;
+      const int q = q0 + qq, p = p0 + pp;
+      double vr = 0.0, vi = 0.0;
+      if (q < M && p < M) {
+        const long id = (q <= p) ? packed_index(q, p, M) : packed_index(p, q, M);
+        vr = Yr[id];
+        vi = Yi[id];
+      }
+      Ys[0][qq][pp] = vr;
+      Ys[1][qq][pp] = vi;
+    }
+    for (int idx = threadIdx.x; idx < 2 * N * TT_Q; idx += blockDim.x) {
+      const int c = idx / (N * TT_Q), rem = idx % (N * TT_Q);
+      const int i = rem / TT_Q, qq = rem % TT_Q;
+      const int q = q0 + qq;
+      Ts[c][i][qq] = (q < M) ? tin[((long)c * N + i) * M + q] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int qq = 0; qq < TT_Q; ++qq) {
+      const double yr = Ys[0][qq][tx], yi = Ys[1][qq][tx];
+#pragma unroll
+      for (int r = 0; r < TT_NMAX / 4; ++r) {
+        const int i = ty + 4 * r;
+        if (i < N) {
+          const double tr = Ts[0][i][qq], ti = Ts[1][i][qq];
+          accR[r] = fma(tr, yi, fma(ti, yr, accR[r]));
+          accI[r] = fma(tr, yr, fma(-ti, yi, accI[r]));
+        }
+      }
+    }
+    __syncthreads();
+  }
+  const int p = p0 + tx;
+  if (p >= M) return;
+#pragma unroll
+  for (int r = 0; r < TT_NMAX / 4; ++r) {
+    const int i = ty + 4 * r;
+    if (i >= N) break;
+    const double oR = -a.scale * accR[r], oI = a.scale * accI[r];
+    const long o0 = wo + (long)i * M + p, o1 = wo + ((long)N + i) * M + p;
+    a.tout[o0] = oR;
+    a.tout[o1] = oI;
+    if (a.k == 1) {
+      a.acc[o0] = tin[(long)i * M + p] + oR;
+      a.acc[o1] = tin[((long)N + i) * M + p] + oI;
+    } else {
+      a.acc[o0] += oR;
+      a.acc[o1] += oI;
+    }
+  }
+}
+
+int launch_taylor_term(const TaylorArgs& a, cudaStream_t st) {
+  if (a.N > TT_NMAX) {
+    set_error("taylor: N=%d above the supported %d", a.N, TT_NMAX);
+    return AFQMC_EUNSUPPORTED;
+  }
+  dim3 grid(cdiv(a.M, TT_P), a.W);
+  AFQ_LAUNCH(k_taylor_term, grid, 256, 0, st, a);
+  return AFQMC_OK;
+}
+
+// ------------------------------------------------------- LU / inverse ------
+// Overlap matrix S = V_T^T Phi (Theorem 1.1): Gauss-Jordan elimination with
+// partial pivoting (largest modulus in the column) gives S^-1 and
+// log det S = sum_k log p_k (+ i pi per row swap).  Stored per walker:
+// log <Psi_T|Psi> = 2 log det S (both spins): real part and phase wrapped to
+// (-pi, pi].
+__global__ void __launch_bounds__(128) k_lu_inv(LuArgs a) {
+  extern __shared__ double2 lu_sm[];
+  const int w = blockIdx.x;
+  if (a.wt && !walker_alive(a.wt, w)) return;
+  const int N = a.N;
+  double2* A = lu_sm;          // [N][N]
+  double2* Inv = lu_sm + N * N;  // [N][N]
+  __shared__ int piv;
+  __shared__ double logabs, phase;
+  __shared__ int swaps, singular;
+  const double* S = a.S + (long)w * 2 * N * N;
+  for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x) {
+    const int i = idx / N, j = idx % N;
+    A[idx] = make_double2(S[(long)j * N + i], S[(long)N * N + (long)j * N + i]);
+    Inv[idx] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+  }
+  if (threadIdx.x == 0) {
+    logabs = 0.0;
+    phase = 0.0;
+    swaps = 0;
+    singular = 0;
+  }
+  __syncthreads();
+  for (int k = 0; k < N; ++k) {
+    if (threadIdx.x == 0) {
+      int best = k;
+      double bv = -1.0;
+      for (int r = k; r < N; ++r) {
+        const double v = hypot(A[r * N + k].x, A[r * N + k].y);
+        if (v > bv) {
+          bv = v;
+          best = r;
+        }
+      }
+      piv = best;
+      if (!(bv > 0.0)) singular = 1;
+    }
+    __syncthreads();
+    if (singular) break;
+    if (piv != k) {
+      for (int j = threadIdx.x; j < N; j += blockDim.x) {
+        double2 t = A[k * N + j];
+        A[k * N + j] = A[piv * N + j];
+        A[piv * N + j] = t;
+        t = Inv[k * N + j];
+        Inv[k * N + j] = Inv[piv * N + j];
+        Inv[piv * N + j] = t;
+      }
+      if (threadIdx.x == 0) swaps++;
+    }
+    __syncthreads();
+    const double2 p = A[k * N + k];
+    const double den = p.x * p.x + p.y * p.y;
+    const double2 rp = make_double2(p.x / den, -p.y / den);  // 1/p
+    if (threadIdx.x == 0) {
+      logabs += 0.5 * log(den);
+      phase += atan2(p.y, p.x);
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+      const double2 v = A[k * N + j], u = Inv[k * N + j];
+      A[k * N + j] = make_double2(v.x * rp.x - v.y * rp.y, v.x * rp.y + v.y * rp.x);
+      Inv[k * N + j] = make_double2(u.x * rp.x - u.y * rp.y, u.x * rp.y + u.y * rp.x);
+    }
+    __syncthreads();
+    // eliminate column k from every other row; factors read before updates
+    for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x) {
+      const int r = idx / N, j = idx % N;
+      if (r == k || j == k) continue;
+      const double2 f = A[r * N + k];
+      const double2 v = A[k * N + j];
+      A[r * N + j].x -= f.x * v.x - f.y * v.y;
+      A[r * N + j].y -= f.x * v.y + f.y * v.x;
+    }
+    for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x) {
+      const int r = idx / N, j = idx % N;
+      if (r == k) continue;
+      const double2 f = A[r * N + k];
+      const double2 v = Inv[k * N + j];
+      Inv[r * N + j].x -= f.x * v.x - f.y * v.y;
+      Inv[r * N + j].y -= f.x * v.y + f.y * v.x;
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < N; r += blockDim.x)
+      if (r != k) A[r * N + k] = make_double2(0.0, 0.0);
+    __syncthreads();
+  }
+  double* out = a.Sinv + (long)w * 2 * N * N;
+  for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x) {
+    out[idx] = singular ? 0.0 : Inv[idx].x;
+    out[(long)N * N + idx] = singular ? 0.0 : Inv[idx].y;
+  }
+  if (threadIdx.x == 0) {
+    if (singular) {
+      a.logdet[2L * w] = -INFINITY;
+      a.logdet[2L * w + 1] = 0.0;
+    } else {
+      a.logdet[2L * w] = 2.0 * logabs;
+      a.logdet[2L * w + 1] = wrap_pi(2.0 * (phase + 3.141592653589793 * swaps));
+    }
+  }
+}
+
+int launch_lu_inv(const LuArgs& a, cudaStream_t st) {
+  const size_t smem = 2ull * a.N * a.N * sizeof(double2);
+  if (smem > 200 * 1024) {
+    set_error("lu: N=%d too large for the shared-memory LU", a.N);
+    return AFQMC_EUNSUPPORTED;
+  }
+  static bool attr = false;
+  if (!attr) {
+    AFQ_CUDA(cudaFuncSetAttribute(k_lu_inv, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  200 * 1024));
+    attr = true;
+  }
+  AFQ_LAUNCH(k_lu_inv, a.W, 128, smem, st, a);
+  return AFQMC_OK;
+}
+
+// ------------------------------------------------------------------ Theta --
+// Theta = Phi S^-1 (Eq. precomputing for one determinant), stored as
+// Theta^T[i][p] = sum_j S^-1[j][i] Phi^T[j][p].
+__global__ void __launch_bounds__(128) k_theta(ThetaArgs a) {
+  extern __shared__ double th_sm[];  // [2][N][N]
+  const int w = blockIdx.y;
+  if (!walker_alive(a.wt, w)) return;
+  const int N = a.N, M = a.M;
+  const double* Si = a.Sinv + (long)w * 2 * N * N;
+  for (int idx = threadIdx.x; idx < 2 * N * N; idx += blockDim.x) th_sm[idx] = Si[idx];
+  __syncthreads();
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= M) return;
+  const double* ph = a.phiT + (long)w * 2 * N * M;
+  double* th = a.thetaT + (long)w * 2 * N * M;
+  const double* SR = th_sm;
+  const double* SI = th_sm + N * N;
+  for (int i0 = 0; i0 < N; i0 += 16) {
+    double ar[16], ai[16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) ar[u] = ai[u] = 0.0;
+    for (int j = 0; j < N; ++j) {
+      const double fr = ph[(long)j * M + p], fi = ph[((long)N + j) * M + p];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        const int i = i0 + u;
+        if (i < N) {
+          const double sr = SR[j * N + i], si = SI[j * N + i];
+          ar[u] = fma(fr, sr, fma(-fi, si, ar[u]));
+          ai[u] = fma(fr, si, fma(fi, sr, ai[u]));
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      const int i = i0 + u;
+      if (i < N) {
+        th[(long)i * M + p] = ar[u];
+        th[((long)N + i) * M + p] = ai[u];
+      }
+    }
+  }
+}
+
+int launch_theta(const ThetaArgs& a, cudaStream_t st) {
+  dim3 grid(cdiv(a.M, 128), a.W);
+  static bool attr = false;
+  if (!attr) {
+    AFQ_CUDA(cudaFuncSetAttribute(k_theta, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
+    attr = true;
+  }
+  AFQ_LAUNCH(k_theta, grid, 128, 2ull * a.N * a.N * sizeof(double), st, a);
+  return AFQMC_OK;
+}
+
+// ---------------------------------------------------------------- weights --
+// Overlap ratio of the step, including the scalar of B(x - xbar):
+// log R = l' - l - dt (H0' - E_shift) - i sqrt(dt) sum_g x_g c_g.
+// Phaseless (Eqs. hybrid-wt, if_rle, weight_update_2):
+//   W <- min(W |I| max(0, cos dtheta), W_max), dtheta = Arg R,
+//   |I| = exp(Re log R + Re sum xi xbar - Re sum xbar^2 / 2).
+// Free projection (Eq. weight_update): W e^{i theta} <- W e^{i theta} R.
+__global__ void k_weight(WeightArgs a) {
+  const int w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w == 0 && a.dstep) *a.dstep += 1;
+  if (w >= a.W) return;
+  if (!walker_alive(a.wt, w)) return;
+  const double* s = a.scal + 8L * w;
+  const double lr = (a.ld_new[2 * w] - a.ld[2 * w]) - a.dt * (a.H0p - a.e_shift) + a.sdt * s[5];
+  const double li = (a.ld_new[2 * w + 1] - a.ld[2 * w + 1]) - a.sdt * s[4];
+  double wr, wi;
+  if (a.mode == AFQMC_PHASELESS) {
+    const double dth = wrap_pi(li);
+    wr = a.wt[2 * w] * exp(lr + s[0] - 0.5 * s[2]) * fmax(0.0, cos(dth));
+    if (!isnan(wr)) wr = fmin(wr, a.wmax);
+    wi = 0.0;
+  } else {
+    const double m = exp(lr);
+    double sn, cs;
+    sincos(li, &sn, &cs);
+    const double rr = m * cs, ri = m * sn;
+    const double w0r = a.wt[2 * w], w0i = a.wt[2 * w + 1];
+    wr = w0r * rr - w0i * ri;
+    wi = w0r * ri + w0i * rr;
+  }
+  if (!isfinite(wr) || !isfinite(wi)) {
+    wr = wi = 0.0;
+    atomicAdd(a.nonfinite, 1ull);
+  }
+  a.wt[2 * w] = wr;
+  a.wt[2 * w + 1] = wi;
+  a.ld[2 * w] = a.ld_new[2 * w];
+  a.ld[2 * w + 1] = a.ld_new[2 * w + 1];
+}
+
+int launch_weight(const WeightArgs& a, cudaStream_t st) {
+  AFQ_LAUNCH(k_weight, cdiv(a.W, 128), 128, 0, st, a);
+  return AFQMC_OK;
+}
+
+// -------------------------------------------------- modified Gram-Schmidt --
+// Sec. 3.4.5: sweep the orbitals k = 1..N; each is orthogonalised against the
+// finished ones one projection at a time (the projection uses the partially
+// updated vector), then normalised.  Each thread owns a fixed set of rows p,
+// so only the block sums need barriers.
+__global__ void __launch_bounds__(256) k_mgs(MgsArgs a) {
+  __shared__ double sh[32];
+  const int w = blockIdx.x;
+  if (!walker_alive(a.wt, w)) return;
+  const int M = a.M, N = a.N;
+  double* re = a.phiT + (long)w * 2 * N * M;
+  double* im = re + (long)N * M;
+  for (int k = 0; k < N; ++k) {
+    double* vr = re + (long)k * M;
+    double* vi = im + (long)k * M;
+    for (int j = 0; j < k; ++j) {
+      const double* qr = re + (long)j * M;
+      const double* qi = im + (long)j * M;
+      double sr = 0.0, si = 0.0;
+      for (int p = threadIdx.x; p < M; p += blockDim.x) {
+        sr += qr[p] * vr[p] + qi[p] * vi[p];
+        si += qr[p] * vi[p] - qi[p] * vr[p];
+      }
+      sr = block_sum(sr, sh);
+      si = block_sum(si, sh);
+      for (int p = threadIdx.x; p < M; p += blockDim.x) {
+        const double a_ = qr[p], b_ = qi[p];
+        vr[p] -= sr * a_ - si * b_;
+        vi[p] -= sr * b_ + si * a_;
+      }
+    }
+    double nn = 0.0;
+    for (int p = threadIdx.x; p < M; p += blockDim.x) nn += vr[p] * vr[p] + vi[p] * vi[p];
+    nn = block_sum(nn, sh);
+    const double inv = 1.0 / sqrt(nn);
+    for (int p = threadIdx.x; p < M; p += blockDim.x) {
+      vr[p] *= inv;
+      vi[p] *= inv;
+    }
+  }
+}
+
+int launch_mgs(const MgsArgs& a, cudaStream_t st) {
+  AFQ_LAUNCH(k_mgs, a.W, 256, 0, st, a);
+  return AFQMC_OK;
+}
+
+// --------------------------------------------------------------- exchange --
+// Exchange part of Eq. localenergy3: sum_g Tr(Lh_g Theta Lh_g Theta), with
+// T_g = Lh_g Theta (N x N) formed in registers for a chunk of g and never
+// written to global memory; per-chunk partial sums are reduced later in a
+// fixed order.
+namespace {
+constexpr int EX_T = 256, EX_K = 32, EX_P = 32;
+}
+int exchange_chunk(int N, int G) {
+  int gc = (EX_T * EX_K) / (2 * N * N);
+  if (gc < 1) gc = 1;
+  if (gc > G) gc = G;
+  return gc;
+}
+
+__global__ void __launch_bounds__(EX_T) k_exchange(ExchArgs a) {
+  extern __shared__ double ex_sm[];
+  const int chunk = blockIdx.x, w = blockIdx.y;
+  if (!walker_alive(a.wt, w)) return;
+  const int M = a.M, N = a.N;
+  const int g0 = chunk * a.gc;
+  const int gcount = min(a.gc, a.G - g0);
+  double* Ls = ex_sm;                       // [gc][N][EX_P]
+  double* Ts = ex_sm + (long)a.gc * N * EX_P;  // [2][N][EX_P + 1]
+  const int nout = gcount * 2 * N * N;
+  double acc[EX_K];
+#pragma unroll
+  for (int r = 0; r < EX_K; ++r) acc[r] = 0.0;
+  const double* th = a.thetaT + (long)w * 2 * N * M;
+  for (int p0 = 0; p0 < M; p0 += EX_P) {
+    for (int idx = threadIdx.x; idx < gcount * N * EX_P; idx += blockDim.x) {
+      const int gi = idx / EX_P, pp = idx % EX_P;
+      const int p = p0 + pp;
+      Ls[idx] = (p < M) ? a.Lh[((long)g0 * N + gi) * M + p] : 0.0;
+    }
+    for (int idx = threadIdx.x; idx < 2 * N * EX_P; idx += blockDim.x) {
+      const int cj = idx / EX_P, pp = idx % EX_P;
+      const int p = p0 + pp;
+      Ts[cj * (EX_P + 1) + pp] = (p < M) ? th[(long)cj * M + p] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < EX_K; ++r) {
+      const int o = threadIdx.x + r * EX_T;
+      if (o < nout) {
+        // o = ((g * 2 + c) * N + i) * N + j
+        const int j = o % N, i = (o / N) % N, gc2 = o / (N * N);
+        const int c = gc2 & 1, g = gc2 >> 1;
+        const double* lrow = Ls + ((long)g * N + i) * EX_P;
+        const double* trow = Ts + ((long)c * N + j) * (EX_P + 1);
+        double s = acc[r];
+#pragma unroll 8
+        for (int pp = 0; pp < EX_P; ++pp) s = fma(lrow[pp], trow[pp], s);
+        acc[r] = s;
+      }
+    }
+    __syncthreads();
+  }
+  // T_g[c][i][j] into shared memory, then sum_ij T_ij T_ji (complex)
+  double* Tm = ex_sm;
+#pragma unroll
+  for (int r = 0; r < EX_K; ++r) {
+    const int o = threadIdx.x + r * EX_T;
+    if (o < nout) Tm[o] = acc[r];
+  }
+  __syncthreads();
+  double er = 0.0, ei = 0.0;
+  for (int idx = threadIdx.x; idx < gcount * N * N; idx += blockDim.x) {
+    const int g = idx / (N * N), ij = idx % (N * N);
+    const int i = ij / N, j = ij % N;
+    const double* Tr = Tm + (long)(2 * g) * N * N;
+    const double* Ti = Tr + (long)N * N;
+    const double ar = Tr[i * N + j], ai = Ti[i * N + j];
+    const double br = Tr[j * N + i], bi = Ti[j * N + i];
+    er += ar * br - ai * bi;
+    ei += ar * bi + ai * br;
+  }
+  __shared__ double sh[32];
+  er = block_sum(er, sh);
+  ei = block_sum(ei, sh);
+  if (threadIdx.x == 0) {
+    double* o = a.part + ((long)w * a.nchunk + chunk) * 2;
+    o[0] = er;
+    o[1] = ei;
+  }
+}
+
+int launch_exchange(const ExchArgs& a, cudaStream_t st) {
+  if (2 * a.N * a.N > EX_T * EX_K) {
+    set_error("exchange: N=%d above the supported 64", a.N);
+    return AFQMC_EUNSUPPORTED;
+  }
+  size_t d1 = (size_t)a.gc * a.N * EX_P + 2ull * a.N * (EX_P + 1);
+  size_t d2 = (size_t)a.gc * 2 * a.N * a.N;
+  size_t smem = (d1 > d2 ? d1 : d2) * sizeof(double);
+  static bool attr = false;
+  if (!attr) {
+    AFQ_CUDA(cudaFuncSetAttribute(k_exchange, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  160 * 1024));
+    attr = true;
+  }
+  if (smem > 160 * 1024) {
+    set_error("exchange: shared memory %zu too large", smem);
+    return AFQMC_EUNSUPPORTED;
+  }
+  dim3 grid(a.nchunk, a.W);
+  AFQ_LAUNCH(k_exchange, grid, EX_T, smem, st, a);
+  return AFQMC_OK;
+}
+
+// ---------------------------------------------------------- local energy --
+// E_loc = H0 + 2 Tr(hh Theta) + 1/2 sum_g t_g^2 - sum_g Tr(T_g T_g)
+// (Eqs. localenergy2/3; the 1/2 is that of H_2 in Eq. bo_ham2).
+__global__ void __launch_bounds__(256) k_eloc(ElocArgs a) {
+  __shared__ double sh[32];
+  const int w = blockIdx.x;
+  const int M = a.M, N = a.N, G = a.G;
+  const double* th = a.thetaT + (long)w * 2 * N * M;
+  double e1r = 0.0, e1i = 0.0;
+  for (int idx = threadIdx.x; idx < N * M; idx += blockDim.x) {
+    const double hv = a.hh[idx];
+    e1r += hv * th[idx];
+    e1i += hv * th[(long)N * M + idx];
+  }
+  const double* tr = a.t + (long)w * 2 * G;
+  const double* ti = tr + G;
+  double cr = 0.0, ci = 0.0;
+  for (int g = threadIdx.x; g < G; g += blockDim.x) {
+    cr += tr[g] * tr[g] - ti[g] * ti[g];
+    ci += 2.0 * tr[g] * ti[g];
+  }
+  e1r = block_sum(e1r, sh);
+  e1i = block_sum(e1i, sh);
+  cr = block_sum(cr, sh);
+  ci = block_sum(ci, sh);
+  if (threadIdx.x == 0) {
+    double xr = 0.0, xi = 0.0;
+    const double* p = a.part + (long)w * a.nchunk * 2;
+    for (int c = 0; c < a.nchunk; ++c) {
+      xr += p[2 * c];
+      xi += p[2 * c + 1];
+    }
+    a.eloc[2 * w] = a.H0 + 2.0 * e1r + 0.5 * cr - xr;
+    a.eloc[2 * w + 1] = 2.0 * e1i + 0.5 * ci - xi;
+  }
+}
+
+int launch_eloc(const ElocArgs& a, cudaStream_t st) {
+  AFQ_LAUNCH(k_eloc, a.W, 256, 0, st, a);
+  return AFQMC_OK;
+}
+
+// Mixed estimator (Eq. localenergy) over live walkers, Re E_loc clamped to
+// [lo, hi] (Eq. cap) for phaseless walks; one record (step, E, sum W, live).
+__global__ void __launch_bounds__(256) k_record(RecordArgs a) {
+  __shared__ double sh[32];
+  double nr = 0.0, ni = 0.0, dr = 0.0, di = 0.0, na = 0.0;
+  for (int w = threadIdx.x; w < a.W; w += blockDim.x) {
+    if (!walker_alive(a.wt, w)) continue;
+    const double wr = a.wt[2 * w], wi = a.wt[2 * w + 1];
+    double er = a.eloc[2 * w], ei = a.eloc[2 * w + 1];
+    na += 1.0;
+    if (a.mode == AFQMC_PHASELESS) {
+      er = fmin(fmax(er, a.lo), a.hi);
+      nr += wr * er;
+      dr += wr;
+    } else {
+      nr += wr * er - wi * ei;
+      ni += wr * ei + wi * er;
+      dr += wr;
+      di += wi;
+    }
+  }
+  nr = block_sum(nr, sh);
+  ni = block_sum(ni, sh);
+  dr = block_sum(dr, sh);
+  di = block_sum(di, sh);
+  na = block_sum(na, sh);
+  if (threadIdx.x == 0) {
+    double E;
+    if (a.mode == AFQMC_PHASELESS) {
+      E = nr / dr;
+    } else {
+      const double den = dr * dr + di * di;
+      E = (nr * dr + ni * di) / den;
+    }
+    a.last[0] = nr;
+    a.last[1] = dr;
+    a.last[2] = ni;
+    a.last[3] = di;
+    a.last[4] = E;
+    a.last[5] = na;
+    if (a.records) {
+      const unsigned long long n = *a.rec_count;
+      double* r = a.records + 4 * (long)(n % (unsigned long long)a.max_records);
+      r[0] = (double)*a.step;
+      r[1] = E;
+      r[2] = dr;
+      r[3] = na;
+      *a.rec_count = n + 1;
+    }
+  }
+}
+
+int launch_record(const RecordArgs& a, cudaStream_t st) {
+  AFQ_LAUNCH(k_record, 1, 256, 0, st, a);
+  return AFQMC_OK;
+}
+
+// -------------------------------------------------------------------- comb --
+// Fixed-size comb (Sec. 3.4.4 asks for population control but gives no
+// scheme): W_tot and the cumulative weights C_j are sequential sums in walker
+// order; tooth k sits at ((k + u) W_tot) / N_w with u from Philox counter
+// (0, 0xffffffff, step, 0); it goes to the walker j with C_{j-1} <= tooth <
+// C_j (the last live walker if rounding puts it past C_{N_w-1}).  Copies land
+// in walker-index order and every new weight is W_tot / N_w.
+__global__ void __launch_bounds__(256) k_comb_plan(CombArgs a) {
+  __shared__ double s_u;
+  __shared__ int s_last, s_ok;
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    int last = -1;
+    for (int j = 0; j < a.W; ++j) {
+      const double wj = a.wt[2 * j];
+      s += wj;
+      a.cum[j] = s;
+      if (wj > 0.0) last = j;
+    }
+    a.wtot[0] = s;
+    s_last = last;
+    s_ok = (s > 0.0 && isfinite(s) && last >= 0) ? 1 : 0;
+    u32x4 c = {0u, 0xFFFFFFFFu, (uint32_t)(*a.dstep - 1), 0u};
+    u32x4 r = philox4x32_10(c, (uint32_t)a.seed, (uint32_t)(a.seed >> 32));
+    s_u = uniform53(r.x, r.y);
+  }
+  __syncthreads();
+  const double wtot = a.wtot[0];
+  for (int k = threadIdx.x; k < a.W; k += blockDim.x) {
+    if (!s_ok) {
+      a.parent[k] = -1;
+      continue;
+    }
+    const double tooth = (((double)k + s_u) * wtot) / (double)a.W;
+    int lo = 0, hi = a.W;  // first j with cum[j] > tooth
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (a.cum[mid] > tooth) hi = mid; else lo = mid + 1;
+    }
+    a.parent[k] = (lo >= a.W) ? s_last : lo;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_comb_gather(CombArgs a) {
+  const int k = blockIdx.x;
+  const int j = a.parent[k];
+  if (j < 0) return;
+  const long n = 2L * a.N * a.M;
+  const double* sp = a.phiT + (long)j * n;
+  const double* st_ = a.thetaT + (long)j * n;
+  double* dp = a.tmp_phi + (long)k * n;
+  double* dt_ = a.tmp_theta + (long)k * n;
+  for (long i = threadIdx.x; i < n; i += blockDim.x) {
+    dp[i] = sp[i];
+    dt_[i] = st_[i];
+  }
+  if (threadIdx.x == 0) {
+    a.tmp_ld[2 * k] = a.ld[2 * j];
+    a.tmp_ld[2 * k + 1] = a.ld[2 * j + 1];
+  }
+}
+
+__global__ void __launch_bounds__(256) k_comb_commit(CombArgs a) {
+  const int k = blockIdx.x;
+  if (a.parent[k] < 0) return;
+  const long n = 2L * a.N * a.M;
+  for (long i = threadIdx.x; i < n; i += blockDim.x) {
+    a.phiT[(long)k * n + i] = a.tmp_phi[(long)k * n + i];
+    a.thetaT[(long)k * n + i] = a.tmp_theta[(long)k * n + i];
+  }
+  if (threadIdx.x == 0) {
+    a.ld[2 * k] = a.tmp_ld[2 * k];
+    a.ld[2 * k + 1] = a.tmp_ld[2 * k + 1];
+    a.wt[2 * k] = a.wtot[0] / (double)a.W;
+    a.wt[2 * k + 1] = 0.0;
+  }
+}
+
+int launch_comb(const CombArgs& a, cudaStream_t st) {
+  AFQ_LAUNCH(k_comb_plan, 1, 256, 0, st, a);
+  AFQ_LAUNCH(k_comb_gather, a.W, 256, 0, st, a);
+  AFQ_LAUNCH(k_comb_commit, a.W, 256, 0, st, a);
+  return AFQMC_OK;
+}
+
+// ---------------------------------------------------------------- set-up ----
+// L[g][p][q] -> LpT[packed(p,q)][g] for p <= q (transposed packed vectors).
+__global__ void k_pack_transpose(const double* L, double* LpT, int G, int M) {
+  __shared__ double tile[32][33];
+  const int g0 = blockIdx.x * 32, p = blockIdx.y, q0 = blockIdx.z * 32;
+  if (q0 + 31 < p) return;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int g = g0 + r, q = q0 + threadIdx.x;
+    tile[r][threadIdx.x] = (g < G && q < M && q >= p) ? L[((long)g * M + p) * M + q] : 0.0;
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int q = q0 + r, g = g0 + threadIdx.x;
+    if (q < M && q >= p && g < G) LpT[packed_index(p, q, M) * G + g] = tile[threadIdx.x][r];
+  }
+}
+
+int launch_pack_transpose(const double* L, double* LpT, int G, int M, cudaStream_t st) {
+  dim3 grid(cdiv(G, 32), M, cdiv(M, 32));
+  AFQ_LAUNCH(k_pack_transpose, grid, dim3(32, 8), 0, st, L, LpT, G, M);
+  return AFQMC_OK;
+}
+
+__global__ void __launch_bounds__(256) k_rowdot(const double* A, const double* b, double* out,
+                                                int len, double scale) {
+  __shared__ double sh[32];
+  const double* a = A + (long)blockIdx.x * len;
+  double s = 0.0;
+  for (int j = threadIdx.x; j < len; j += blockDim.x) s += a[j] * b[j];
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) out[blockIdx.x] = scale * s;
+}
+
+int launch_rowdot(const double* A, const double* b, double* out, int rows, int len,
+                  double scale, cudaStream_t st) {
+  AFQ_LAUNCH(k_rowdot, rows, 256, 0, st, A, b, out, len, scale);
+  return AFQMC_OK;
+}
+
+// X = scale * (h - 1/2 sum_g L_g^2 + sum_g c_g L_g): the mean-field-shifted
+// one-body operator v0' of Sec. 2.4 (Eq. mcd1), times -dt/2.
+__global__ void k_v0p(const double* h1, const double* L2, const double* cLp, double* X, int M,
+                      double scale) {
+  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long)M * M) return;
+  const int p = (int)(idx / M), q = (int)(idx % M);
+  const long pk = (p <= q) ? packed_index(p, q, M) : packed_index(q, p, M);
+  X[idx] = scale * (h1[idx] - 0.5 * L2[idx] + cLp[pk]);
+}
+
+int launch_v0p(const double* h1, const double* L2, const double* cLp, double* X, int M,
+               double scale, cudaStream_t st) {
+  AFQ_LAUNCH(k_v0p, cdiv((size_t)M * M, 256), 256, 0, st, h1, L2, cLp, X, M, scale);
+  return AFQMC_OK;
+}
+
+__global__ void __launch_bounds__(256) k_norm1(const double* X, double* out, int M) {
+  __shared__ double sh[256];
+  double best = 0.0;
+  for (int q = threadIdx.x; q < M; q += blockDim.x) {
+    double s = 0.0;
+    for (int p = 0; p < M; ++p) s += fabs(X[(long)p * M + q]);
+    best = fmax(best, s);
+  }
+  sh[threadIdx.x] = best;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] = fmax(sh[threadIdx.x], sh[threadIdx.x + o]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[0] = sh[0];
+}
+
+int launch_norm1(const double* X, double* out, int M, cudaStream_t st) {
+  AFQ_LAUNCH(k_norm1, 1, 256, 0, st, X, out, M);
+  return AFQMC_OK;
+}
+
+__global__ void k_fill_identity(double* X, int M, double d) {
+  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long)M * M) return;
+  X[idx] = (idx / M == idx % M) ? d : 0.0;
+}
+
+int launch_fill_identity(double* X, int M, double d, cudaStream_t st) {
+  AFQ_LAUNCH(k_fill_identity, cdiv((size_t)M * M, 256), 256, 0, st, X, M, d);
+  return AFQMC_OK;
+}
+
+__global__ void k_scale(double* X, long n, double s) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) X[i] *= s;
+}
+
+int launch_scale(double* X, long n, double s, cudaStream_t st) {
+  AFQ_LAUNCH(k_scale, cdiv(n, 256), 256, 0, st, X, n, s);
+  return AFQMC_OK;
+}
+
+// Every walker at {V_T, W = 1} (algorithm outline, step 1).
+__global__ void k_init_walkers(const double* VTt, double* phiT, double* wt, int W, int N, int M) {
+  const long n = (long)N * M;
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int w = blockIdx.y;
+  if (i < n) {
+    phiT[(long)w * 2 * n + i] = VTt[i];
+    phiT[(long)w * 2 * n + n + i] = 0.0;
+  }
+  if (i == 0) {
+    wt[2 * w] = 1.0;
+    wt[2 * w + 1] = 0.0;
+  }
+}
+
+int launch_init_walkers(const double* VTt, double* phiT, double* wt, int W, int N, int M,
+                        cudaStream_t st) {
+  dim3 grid(cdiv((size_t)N * M, 256), W);
+  AFQ_LAUNCH(k_init_walkers, grid, 256, 0, st, VTt, phiT, wt, W, N, M);
+  return AFQMC_OK;
+}
+
+__global__ void __launch_bounds__(256) k_sumsq(const double* v, double* out, int n) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += v[i] * v[i];
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) out[0] = s;
+}
+
+int launch_sumsq(const double* v, double* out, int n, cudaStream_t st) {
+  AFQ_LAUNCH(k_sumsq, 1, 256, 0, st, v, out, n);
+  return AFQMC_OK;
+}
+
+}  // namespace afq
+
+// ------------------------------------------------------- generator access --
+namespace afq {
+__global__ void k_philox(uint64_t key, const uint32_t* ctr, long n, uint32_t* out) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  u32x4 c = {ctr[4 * i], ctr[4 * i + 1], ctr[4 * i + 2], ctr[4 * i + 3]};
+  u32x4 r = philox4x32_10(c, (uint32_t)key, (uint32_t)(key >> 32));
+  out[4 * i] = r.x;
+  out[4 * i + 1] = r.y;
+  out[4 * i + 2] = r.z;
+  out[4 * i + 3] = r.w;
+}
+
+__global__ void k_fields(uint64_t seed, uint32_t step, int w0, int nw, int G, double* out) {
+  const int npair = (G + 1) / 2;
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long)nw * npair) return;
+  const int w = (int)(i / npair), k = (int)(i % npair);
+  double a, b;
+  field_pair(seed, step, (uint32_t)(w0 + w), (uint32_t)k, &a, &b);
+  out[(long)w * G + 2 * k] = a;
+  if (2 * k + 1 < G) out[(long)w * G + 2 * k + 1] = b;
+}
+
+int launch_philox(uint64_t key, const uint32_t* ctr, long n, uint32_t* out, cudaStream_t st) {
+  if (n <= 0) return AFQMC_OK;
+  AFQ_LAUNCH(k_philox, cdiv(n, 256), 256, 0, st, key, ctr, n, out);
+  return AFQMC_OK;
+}
+
+int launch_fields(uint64_t seed, uint32_t step, int w0, int nw, int G, double* out,
+                  cudaStream_t st) {
+  const long n = (long)nw * ((G + 1) / 2);
+  if (n <= 0) return AFQMC_OK;
+  AFQ_LAUNCH(k_fields, cdiv(n, 256), 256, 0, st, seed, step, w0, nw, G, out);
+  return AFQMC_OK;
+}
+}  // namespace afq

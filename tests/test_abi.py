@@ -1,0 +1,69 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every symbol its
+header declares (no GPU needed: no compute call is made)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "afqmc.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"AFQMC_API\s+[\w\s\*]+?\b(afqmc_\w+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def built():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_1711_02242_gb300 as pkg
+
+    return pkg
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("afqmc_init", "afqmc_propagate", "afqmc_energy", "afqmc_workspace_size"):
+        assert required in names
+    assert len(names) >= 17
+
+
+def test_library_exports_every_declared_symbol(built):
+    lib = ctypes.CDLL(built.LIB_PATH)
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+    assert sorted(built.EXPORTED) == declared_functions()
+
+
+def test_params_struct_matches_header_defaults(built):
+    p = built.default_params(12, 3, 48, 32)
+    assert (p.dt, p.taylor_order, p.qr_period, p.pc_period) == (0.005, 6, 5, 0)
+    assert p.ecap_C == 2.0 and p.fb_cap == 1.0 and p.max_records == 4096
+    assert p.e_shift != p.e_shift and p.wmax != p.wmax  # NaN defaults
+    assert ctypes.sizeof(built.Params) == 104
+
+
+def test_workspace_size_and_validation_without_gpu(built):
+    p = built.default_params(300, 25, 1800, 512)
+    n = built.afqmc_workspace_size(p)
+    # packed Cholesky vectors alone are 1800 * 45150 doubles
+    assert n > 1800 * 45150 * 8
+    assert n % 256 == 0
+    with pytest.raises(built.AfqmcError, match="EINVAL"):
+        built.afqmc_workspace_size(built.default_params(10, 11, 5, 4))
+    with pytest.raises(built.AfqmcError, match="EINVAL"):
+        built.afqmc_workspace_size(built.default_params(10, 2, 5, 4, dt=-1.0))
+
+
+def test_library_has_no_oracle_dependency():
+    """The product path never imports or links the oracle."""
+    pkgdir = os.path.join(ROOT, "paper_1711_02242_gb300")
+    for dirpath, _, files in os.walk(pkgdir):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in txt and "from oracle" not in txt, f
