@@ -254,6 +254,25 @@ AFQMC_API int afqmc_profile_start(afqmc_state* s, int32_t max_steps);
 AFQMC_API int afqmc_profile_stop(afqmc_state* s, double* ms, int64_t* count, int64_t* kernels);
 
 /*
+ * The dense contraction of the mixed-precision path on the tcgen05 tensor
+ * cores, C[m][n] = alpha * sum_k A[m][k] B[n][k], FP32 accumulation.  The
+ * force-bias traces (Eq. precomputing2), V = sum_g x_g L_g (Sec. 3.4.2) and
+ * the T_g = Lh_g Theta products of Eq. localenergy3 are all of this form.
+ *   dtype   0: A, B are BF16; 1: A, B are FP32 read as TF32
+ *   dA, dB  DEVICE row-major operands with row pitches lda, ldb (elements;
+ *           pitch * element size a multiple of 16 bytes, bases 16-byte
+ *           aligned); entries past column k are not read
+ *   dC      DEVICE row-major FP32 output with pitch ldc
+ *   d_status DEVICE int: left unchanged on success, set non-zero if a
+ *           bounded wait inside the kernel timed out (the result is then
+ *           invalid)
+ * Asynchronous on `stream`.
+ */
+AFQMC_API int afqmc_contract(int32_t dtype, int64_t m, int64_t n, int64_t k, const void* dA,
+                             int64_t lda, const void* dB, int64_t ldb, float alpha, float* dC,
+                             int64_t ldc, int* d_status, void* stream);
+
+/*
  * The counter-based generator behind the auxiliary fields: Philox4x32 with
  * 10 rounds (J. K. Salmon et al., "Parallel random numbers: as easy as 1, 2,
  * 3", SC'11), key = (key & 0xffffffff, key >> 32).

@@ -29,7 +29,8 @@ EXPORTED = ["afqmc_default_params", "afqmc_workspace_size", "afqmc_init", "afqmc
             "afqmc_energy", "afqmc_local_energies", "afqmc_get_walkers", "afqmc_set_walkers",
             "afqmc_get_energy_log", "afqmc_get_info", "afqmc_save", "afqmc_load",
             "afqmc_destroy", "afqmc_last_error", "afqmc_launch_count",
-            "afqmc_philox4x32_10", "afqmc_gaussian_fields"]
+            "afqmc_philox4x32_10", "afqmc_gaussian_fields", "afqmc_contract",
+            "afqmc_profile_start", "afqmc_profile_stop"]
 
 
 class Params(ctypes.Structure):
@@ -89,6 +90,11 @@ def lib():
         "afqmc_philox4x32_10": (ctypes.c_int, [ctypes.c_uint64, vp, ctypes.c_int64, vp, vp]),
         "afqmc_gaussian_fields": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_int64, ctypes.c_int32,
                                                  ctypes.c_int32, ctypes.c_int32, vp, vp]),
+        "afqmc_contract": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int64, ctypes.c_int64,
+                                          ctypes.c_int64, vp, ctypes.c_int64, vp, ctypes.c_int64,
+                                          ctypes.c_float, vp, ctypes.c_int64, vp, vp]),
+        "afqmc_profile_start": (ctypes.c_int, [vp, ctypes.c_int32]),
+        "afqmc_profile_stop": (ctypes.c_int, [vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)

@@ -69,7 +69,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     lib64 = os.path.join(_cuda_home(nvcc), "lib64")
     tmp = OUT + ".tmp"
     cmd = [nvcc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs,
-           "-Xlinker", "-rpath", "-Xlinker", lib64, "-lcuda"]
+           "-Xlinker", "-rpath", "-Xlinker", lib64]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -7,6 +7,7 @@
 
 #include "kernels.cuh"
 #include "state.cuh"
+#include "tc.cuh"
 
 namespace afq {
 
@@ -40,7 +41,15 @@ size_t plan(const afqmc_params& p, Bufs* b, char* base) {
   if (!b) b = &tmp;
   const size_t M = p.M, N = p.N, G = p.nchol, W = p.nwalkers;
   const size_t P = M * (M + 1) / 2;
-  const size_t nchunk = (G + exchange_chunk(p.N, p.nchol) - 1) / exchange_chunk(p.N, p.nchol);
+  const bool mixed = p.precision != AFQMC_FP64;
+  size_t nchunk = (G + exchange_chunk(p.N, p.nchol) - 1) / exchange_chunk(p.N, p.nchol);
+  if (mixed) {
+    int RG, CW;
+    exchange_tile(p.N, &RG, &CW);
+    nchunk = (G + RG - 1) / RG;
+  }
+  const size_t lo = (p.precision == AFQMC_MIXED_BF16) ? 2 : 4;
+  const size_t Gp = (G + 7) / 8 * 8, Mp = (M + 7) / 8 * 8, Pp = (P + 3) / 4 * 4;
   Bump a{base};
   // constants
   b->LpT = a.take<double>(P * G);
@@ -69,13 +78,36 @@ size_t plan(const afqmc_params& p, Bufs* b, char* base) {
   b->last = a.take<double>(8);
   b->records = a.take<double>(4 * (size_t)(p.max_records > 0 ? p.max_records : 1));
   b->counters = a.take<unsigned long long>(8);
+  b->mixed = mixed;
+  b->lo_kind = mixed ? (lo == 2 ? LO_BF16 : LO_TF32) : LO_NONE;
+  b->lo_bytes = (int)lo;
+  b->Gp = (int)Gp;
+  b->Mp = (int)Mp;
+  b->Pp = (long)Pp;
+  if (mixed) {
+    b->LpT_lo = a.take<char>(P * Gp * lo);
+    b->Lh_lo = a.take<char>(G * N * Mp * lo);
+    b->x_lo = a.take<char>(W * 2 * Gp * lo);
+    b->th_lo = a.take<char>(W * 2 * N * Mp * lo);
+    b->t32 = a.take<float>(W * 2 * G);
+    b->Bh32 = a.take<float>(M * M);
+  }
   // scratch: the set-up and the step never run at the same time
   const size_t scratch_at = (a.off + 255) & ~size_t(255);
   Bump s1{base, scratch_at};
-  b->Y = s1.take<double>(W * 2 * P);
-  b->T0 = s1.take<double>(W * 2 * N * M);
+  if (mixed) {
+    b->Y = nullptr;
+    b->acc = nullptr;
+    b->Y32 = s1.take<float>(W * 2 * Pp);
+    b->T0f = s1.take<float>(W * 2 * N * M);
+    b->T1f = s1.take<float>(W * 2 * N * M);
+    b->accf = s1.take<float>(W * 2 * N * M);
+  } else {
+    b->Y = s1.take<double>(W * 2 * P);
+    b->acc = s1.take<double>(W * 2 * N * M);
+  }
+  b->T0 = s1.take<double>(W * 2 * N * M);  // Taylor terms (FP64) / comb copies
   b->T1 = s1.take<double>(W * 2 * N * M);
-  b->acc = s1.take<double>(W * 2 * N * M);
   b->tmp_ld = s1.take<double>(2 * W);
   Bump s2{base, scratch_at};
   b->Lfull = s2.take<double>(G * M * M);
@@ -88,6 +120,7 @@ size_t plan(const afqmc_params& p, Bufs* b, char* base) {
   b->P = (int)P;
   b->nchunk = (int)nchunk;
   b->gc = exchange_chunk(p.N, p.nchol);
+  b->status = reinterpret_cast<int*>(b->counters + CTR_STATUS);
   return ((s1.off > s2.off ? s1.off : s2.off) + 255) & ~size_t(255);
 }
 
@@ -122,7 +155,8 @@ static int check_params(const afqmc_params* p) {
     set_error("the comb needs real weights: pc_period must be 0 for free projection");
     return AFQMC_EINVAL;
   }
-  if (p->precision != AFQMC_FP64) {
+  if (p->precision != AFQMC_FP64 && p->precision != AFQMC_MIXED_TF32 &&
+      p->precision != AFQMC_MIXED_BF16) {
     set_error("precision %d is not available in this build", p->precision);
     return AFQMC_EUNSUPPORTED;
   }
@@ -165,6 +199,11 @@ int overlap_update(afqmc_state* s, bool into_ld) {
   LuArgs lu{p.nwalkers, p.N, b.S, b.Sinv, into_ld ? b.ld : b.ld_new, b.wt};
   AFQ_TRY(launch_lu_inv(lu, s->st));
   ThetaArgs th{p.nwalkers, p.M, p.N, b.Sinv, b.phiT, b.thetaT, b.wt};
+  if (b.mixed) {
+    th.th_lo = b.th_lo;
+    th.lo_kind = b.lo_kind;
+    th.Mp = b.Mp;
+  }
   AFQ_TRY(launch_theta(th, s->st));
   return AFQMC_OK;
 }
@@ -172,6 +211,22 @@ int overlap_update(afqmc_state* s, bool into_ld) {
 int force_bias_gemm(afqmc_state* s) {
   const afqmc_params& p = s->p;
   const Bufs& b = s->b;
+  if (b.mixed) {
+    // t[(w,c)][g] = 2 sum_(i,p) Theta^T_lo[(w,c)][(i,p)] Lh_lo[g][(i,p)] on tcgen05
+    TcGemm g;
+    g.m = 2 * p.nwalkers;
+    g.n = p.nchol;
+    g.k = p.N * b.Mp;
+    g.A = b.th_lo;
+    g.lda = (long)p.N * b.Mp;
+    g.B = b.Lh_lo;
+    g.ldb = (long)p.N * b.Mp;
+    g.tf32 = b.lo_kind == LO_TF32;
+    g.err = b.status;
+    AFQ_TRY(tc_gemm_store(g, b.t32, p.nchol, 2.0f, s->st));
+    s->t_fresh = true;
+    return AFQMC_OK;
+  }
   GemmF64 g;
   g.m = 2 * p.nwalkers;
   g.n = p.nchol;
@@ -192,9 +247,25 @@ int energy_eval(afqmc_state* s, bool append) {
   const afqmc_params& p = s->p;
   const Bufs& b = s->b;
   if (!s->t_fresh) AFQ_TRY(force_bias_gemm(s));
-  ExchArgs ex{p.nwalkers, p.M, p.N, p.nchol, b.gc, b.nchunk, b.Lh, b.thetaT, b.part, b.wt};
-  AFQ_TRY(launch_exchange(ex, s->st));
+  if (b.mixed) {
+    // T_g = Lh_g Theta for all (g, w) on tcgen05, sum_ij T_ij T_ji in the epilogue
+    TcGemm g;
+    g.m = p.nchol * p.N;
+    g.n = 2 * p.N * p.nwalkers;
+    g.k = p.M;
+    g.A = b.Lh_lo;
+    g.lda = b.Mp;
+    g.B = b.th_lo;
+    g.ldb = b.Mp;
+    g.tf32 = b.lo_kind == LO_TF32;
+    g.err = b.status;
+    AFQ_TRY(tc_exchange(g, p.nchol, p.nwalkers, p.N, b.part, b.nchunk, s->st));
+  } else {
+    ExchArgs ex{p.nwalkers, p.M, p.N, p.nchol, b.gc, b.nchunk, b.Lh, b.thetaT, b.part, b.wt};
+    AFQ_TRY(launch_exchange(ex, s->st));
+  }
   ElocArgs el{p.nwalkers, p.M, p.N, p.nchol, b.nchunk, p.H0, b.hh, b.thetaT, b.t, b.part, b.eloc, b.wt};
+  el.t32 = b.mixed ? b.t32 : nullptr;
   AFQ_TRY(launch_eloc(el, s->st));
   RecordArgs rc;
   rc.W = p.nwalkers;
@@ -212,17 +283,12 @@ int energy_eval(afqmc_state* s, bool append) {
   return AFQMC_OK;
 }
 
-static int step_once(afqmc_state* s) {
+// Float64 propagation: Phi <- B_half T_n(V) B_half Phi, V = i sqrt(dt) sum_g x_g L_g
+// (Eqs. primitive and hs2; Sec. 3.4.2).
+static int propagate_f64(afqmc_state* s) {
   const afqmc_params& p = s->p;
   const Bufs& b = s->b;
   const int W = p.nwalkers, N = p.N, M = p.M, G = p.nchol;
-  // force bias traces t = 2 Tr(Lh_g Theta) for every walker (Eq. precomputing2)
-  if (!s->t_fresh) {
-    prof_begin(s, AFQMC_PH_FORCE_BIAS);
-    AFQ_TRY(force_bias_gemm(s));
-    prof_end(s);
-  }
-  // fields and shifted fields
   FieldArgs fa{W, G, p.mode, p.seed, s->sdt, p.fb_cap, b.t, b.c, b.wt, b.x, b.scal,
                reinterpret_cast<const int64_t*>(b.counters + CTR_STEP)};
   prof_begin(s, AFQMC_PH_FIELDS);
@@ -230,19 +296,17 @@ static int step_once(afqmc_state* s) {
   prof_end(s);
   // Y = sum_g x_g L_g (packed), the dense contraction with K = N_gamma
   prof_begin(s, AFQMC_PH_V);
-  {
-    GemmF64 g;
-    g.m = 2 * W;
-    g.n = b.P;
-    g.k = G;
-    g.A = b.x;
-    g.lda = G;
-    g.B = b.LpT;
-    g.ldb = G;
-    g.C = b.Y;
-    g.ldc = b.P;
-    AFQ_TRY(gemm_nt_f64(g, s->st));
-  }
+  GemmF64 g;
+  g.m = 2 * W;
+  g.n = b.P;
+  g.k = G;
+  g.A = b.x;
+  g.lda = G;
+  g.B = b.LpT;
+  g.ldb = G;
+  g.C = b.Y;
+  g.ldc = b.P;
+  AFQ_TRY(gemm_nt_f64(g, s->st));
   prof_end(s);
   // Phi <- B_half Phi  (Phi^T <- Phi^T B_half, B_half symmetric)
   prof_begin(s, AFQMC_PH_BHALF);
@@ -258,12 +322,12 @@ static int step_once(afqmc_state* s) {
   bh.ldc = M;
   AFQ_TRY(gemm_nt_f64(bh, s->st));
   prof_end(s);
-  // truncated Taylor series of exp(V) (Sec. 3.4.2)
+  // truncated Taylor series of exp(V)
   prof_begin(s, AFQMC_PH_TAYLOR);
   double* tin = b.T0;
   double* tout = b.T1;
   for (int k = 1; k <= p.taylor_order; ++k) {
-    TaylorArgs ta{W, M, N, b.P, k, s->sdt / k, b.Y, tin, tout, b.acc, b.wt};
+    TaylorArgsT<double> ta{W, M, N, b.P, k, (long)b.P, s->sdt / k, b.Y, tin, tout, b.acc};
     AFQ_TRY(launch_taylor_term(ta, s->st));
     double* t_ = tin;
     tin = tout;
@@ -278,6 +342,93 @@ static int step_once(afqmc_state* s) {
   bh.mask_rows = 2 * N;
   AFQ_TRY(gemm_nt_f64(bh, s->st));
   prof_end(s);
+  return AFQMC_OK;
+}
+
+// Mixed propagation: the same sequence with x and the Cholesky vectors in
+// BF16/TF32 on the tensor cores (FP32 accumulation) and the B_half products
+// and Taylor terms in FP32 on the CUDA cores; the orbitals stay float64.
+static int propagate_mixed(afqmc_state* s) {
+  const afqmc_params& p = s->p;
+  const Bufs& b = s->b;
+  const int W = p.nwalkers, N = p.N, M = p.M, G = p.nchol;
+  FieldArgs fa{W, G, p.mode, p.seed, s->sdt, p.fb_cap, nullptr, b.c, b.wt, nullptr, b.scal,
+               reinterpret_cast<const int64_t*>(b.counters + CTR_STEP)};
+  fa.t32 = b.t32;
+  fa.x_lo = b.x_lo;
+  fa.lo_kind = b.lo_kind;
+  fa.Gp = b.Gp;
+  prof_begin(s, AFQMC_PH_FIELDS);
+  AFQ_TRY(launch_field(fa, s->st));
+  prof_end(s);
+  prof_begin(s, AFQMC_PH_V);
+  TcGemm g;
+  g.m = 2 * W;
+  g.n = b.P;
+  g.k = G;
+  g.A = b.x_lo;
+  g.lda = b.Gp;
+  g.B = b.LpT_lo;
+  g.ldb = b.Gp;
+  g.tf32 = b.lo_kind == LO_TF32;
+  g.err = b.status;
+  AFQ_TRY(tc_gemm_store(g, b.Y32, b.Pp, 1.0f, s->st));
+  prof_end(s);
+  prof_begin(s, AFQMC_PH_BHALF);
+  GemmNT<double, float, float> b1;
+  b1.m = 2 * N * W;
+  b1.n = M;
+  b1.k = M;
+  b1.A = b.phiT;
+  b1.lda = M;
+  b1.B = b.Bh32;
+  b1.ldb = M;
+  b1.C = b.T0f;
+  b1.ldc = M;
+  AFQ_TRY(gemm_nt_dff(b1, s->st));
+  prof_end(s);
+  prof_begin(s, AFQMC_PH_TAYLOR);
+  float* tin = b.T0f;
+  float* tout = b.T1f;
+  for (int k = 1; k <= p.taylor_order; ++k) {
+    TaylorArgsT<float> ta{W, M, N, b.P, k, b.Pp, s->sdt / k, b.Y32, tin, tout, b.accf};
+    AFQ_TRY(launch_taylor_term(ta, s->st));
+    float* t_ = tin;
+    tin = tout;
+    tout = t_;
+  }
+  prof_end(s);
+  prof_begin(s, AFQMC_PH_BHALF);
+  GemmNT<float, float, double> b2;
+  b2.m = 2 * N * W;
+  b2.n = M;
+  b2.k = M;
+  b2.A = b.accf;
+  b2.lda = M;
+  b2.B = b.Bh32;
+  b2.ldb = M;
+  b2.C = b.phiT;
+  b2.ldc = M;
+  b2.mask = b.wt;
+  b2.mask_rows = 2 * N;
+  AFQ_TRY(gemm_nt_ffd(b2, s->st));
+  prof_end(s);
+  return AFQMC_OK;
+}
+
+static int step_once(afqmc_state* s) {
+  const afqmc_params& p = s->p;
+  const Bufs& b = s->b;
+  const int W = p.nwalkers, N = p.N, M = p.M, G = p.nchol;
+  // force bias traces t = 2 Tr(Lh_g Theta) for every walker (Eq. precomputing2)
+  if (!s->t_fresh) {
+    prof_begin(s, AFQMC_PH_FORCE_BIAS);
+    AFQ_TRY(force_bias_gemm(s));
+    prof_end(s);
+  }
+  // fields, the force bias and x = xi - xbar; then exp(-dt v0'/2) T_n(V)
+  // exp(-dt v0'/2) applied to every walker's orbitals
+  AFQ_TRY(b.mixed ? propagate_mixed(s) : propagate_f64(s));
   // new overlap, log det, Theta; then the weights (and step += 1)
   prof_begin(s, AFQMC_PH_OVERLAP);
   AFQ_TRY(overlap_update(s, false));
@@ -450,6 +601,14 @@ static int setup_device(afqmc_state* s, const double* h1, const double* L, const
   AFQ_CUDA(cudaMemcpyAsync(&sumc2, b.red + 1, sizeof(double), cudaMemcpyDeviceToHost, st));
   AFQ_TRY(expm_device(s));  // synchronises once
   s->H0p = p.H0 - 0.5 * sumc2;
+  if (b.mixed) {
+    // BF16 / TF32 copies of the contraction operands (zero-padded pitches)
+    AFQ_TRY(launch_convert_lo(b.LpT, b.P, G, G, b.LpT_lo, b.Gp, b.lo_kind, st));
+    AFQ_TRY(launch_convert_lo(b.Lh, (long)G * N, M, M, b.Lh_lo, b.Mp, b.lo_kind, st));
+    AFQ_CUDA(cudaMemsetAsync(b.th_lo, 0, (size_t)W * 2 * N * b.Mp * b.lo_bytes, st));
+    AFQ_CUDA(cudaMemsetAsync(b.x_lo, 0, (size_t)W * 2 * b.Gp * b.lo_bytes, st));
+    AFQ_TRY(launch_convert_f32(b.Bh, b.Bh32, (long)M * M, st));
+  }
   // walkers at the trial, their overlaps, and the trial energy
   AFQ_TRY(launch_init_walkers(b.VTt, b.phiT, b.wt, W, N, M, st));
   AFQ_TRY(overlap_update(s, true));

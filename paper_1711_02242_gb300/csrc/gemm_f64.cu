@@ -1,13 +1,15 @@
-// FP64 "NT" GEMM for the float64 path:
+// SIMT "NT" GEMM on the CUDA cores:
 //   C[m][n] = alpha * sum_{b < kb} sum_{k < K} A_b[m][k] * B_b[n][k] + beta * C[m][n]
 // batched over blockIdx.z.  Both operands are read along K (contiguous), which
 // is how every contraction of the step is laid out (walkers are stored
 // orbital-major, Phi^T, so X * Phi becomes Phi^T X^T with symmetric X).
 //
-// GB300 executes float64 at ~1.2 TFLOP/s (measured DFMA throughput), about
-// 1/60 of its FP32 rate, so this kernel is bound by the FP64 pipe whatever the
-// tiling: a 64x64 tile with a 4x4 register block per thread keeps it busy
-// with a few resident warps per SM.
+// Float64 instance: GB300 executes float64 at ~1.2 TFLOP/s (measured DFMA
+// throughput), about 1/60 of its FP32 rate, so the kernel is bound by the
+// FP64 pipe whatever the tiling; a 64x64 tile with a 4x4 register block per
+// thread keeps it busy with a few resident warps per SM.
+// Mixed instances (FP32 accumulation) multiply the exp(-dt v0'/2) factor
+// into float64 or float32 walkers and store float32 or float64.
 #include "kernels.cuh"
 
 namespace afq {
@@ -15,38 +17,39 @@ namespace afq {
 namespace {
 constexpr int BM = 64, BN = 64, BK = 16, TPB = 256;
 
-__global__ void __launch_bounds__(TPB) k_gemm_nt_f64(GemmF64 g) {
-  __shared__ double As[BK][BM + 1];
-  __shared__ double Bs[BK][BN + 1];
+template <typename TA, typename TB, typename TC, typename ACC>
+__global__ void __launch_bounds__(TPB) k_gemm_nt(GemmNT<TA, TB, TC> g) {
+  __shared__ ACC As[BK][BM + 1];
+  __shared__ ACC Bs[BK][BN + 1];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
   const long z = blockIdx.z;
-  const double* A = g.A + z * g.sAb;
-  const double* B = g.B + z * g.sBb;
-  double* C = g.C + z * g.sCb;
-  double acc[4][4];
+  const TA* A = g.A + z * g.sAb;
+  const TB* B = g.B + z * g.sBb;
+  TC* C = g.C + z * g.sCb;
+  ACC acc[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+    for (int j = 0; j < 4; ++j) acc[i][j] = ACC(0);
 
   for (int b = 0; b < g.kb; ++b) {
-    const double* Ab = A + (long)b * g.sAk;
-    const double* Bb = B + (long)b * g.sBk;
+    const TA* Ab = A + (long)b * g.sAk;
+    const TB* Bb = B + (long)b * g.sBk;
     for (int k0 = 0; k0 < g.k; k0 += BK) {
 #pragma unroll
       for (int r = 0; r < (BM * BK) / TPB; ++r) {
         int idx = threadIdx.x + r * TPB;
         int row = idx / BK, col = idx % BK;
         int gm = m0 + row, gk = k0 + col;
-        As[col][row] = (gm < g.m && gk < g.k) ? Ab[(long)gm * g.lda + gk] : 0.0;
+        As[col][row] = (gm < g.m && gk < g.k) ? ACC(Ab[(long)gm * g.lda + gk]) : ACC(0);
         int gn = n0 + row;
-        Bs[col][row] = (gn < g.n && gk < g.k) ? Bb[(long)gn * g.ldb + gk] : 0.0;
+        Bs[col][row] = (gn < g.n && gk < g.k) ? ACC(Bb[(long)gn * g.ldb + gk]) : ACC(0);
       }
       __syncthreads();
 #pragma unroll
       for (int kk = 0; kk < BK; ++kk) {
-        double a[4], bv[4];
+        ACC a[4], bv[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
 #pragma unroll
@@ -68,32 +71,41 @@ __global__ void __launch_bounds__(TPB) k_gemm_nt_f64(GemmF64 g) {
     for (int j = 0; j < 4; ++j) {
       int gn = n0 + tx + 16 * j;
       if (gn >= g.n) continue;
-      double* c = C + (long)gm * g.ldc + gn;
-      double v = g.alpha * acc[i][j];
-      if (g.beta != 0.0) v = fma(g.beta, *c, v);
-      *c = v;
+      TC* c = C + (long)gm * g.ldc + gn;
+      ACC v = ACC(g.alpha) * acc[i][j];
+      if (g.beta != 0.0) v = fma(ACC(g.beta), ACC(*c), v);
+      *c = TC(v);
     }
   }
 }
 }  // namespace
 
-int gemm_nt_f64(const GemmF64& g, cudaStream_t st) {
+template <typename TA, typename TB, typename TC, typename ACC>
+static int launch_gemm(const GemmNT<TA, TB, TC>& g, cudaStream_t st) {
   if (g.m <= 0 || g.n <= 0 || g.batch <= 0) return AFQMC_OK;
   if (g.k < 0 || g.kb < 1) {
-    set_error("gemm_nt_f64: bad k=%d kb=%d", g.k, g.kb);
+    set_error("gemm_nt: bad k=%d kb=%d", g.k, g.kb);
     return AFQMC_EINVAL;
   }
   if (g.mask && g.mask_rows <= 0) {
-    set_error("gemm_nt_f64: mask_rows must be positive");
+    set_error("gemm_nt: mask_rows must be positive");
     return AFQMC_EINVAL;
   }
   dim3 grid(cdiv(g.n, BN), cdiv(g.m, BM), g.batch);
   if (grid.y > 65535u || grid.z > 65535u) {
-    set_error("gemm_nt_f64: grid too large (m=%d batch=%d)", g.m, g.batch);
+    set_error("gemm_nt: grid too large (m=%d batch=%d)", g.m, g.batch);
     return AFQMC_EINVAL;
   }
-  AFQ_LAUNCH(k_gemm_nt_f64, grid, TPB, 0, st, g);
+  AFQ_LAUNCH((k_gemm_nt<TA, TB, TC, ACC>), grid, TPB, 0, st, g);
   return AFQMC_OK;
+}
+
+int gemm_nt_f64(const GemmF64& g, cudaStream_t st) { return launch_gemm<double, double, double, double>(g, st); }
+int gemm_nt_dff(const GemmNT<double, float, float>& g, cudaStream_t st) {
+  return launch_gemm<double, float, float, float>(g, st);
+}
+int gemm_nt_ffd(const GemmNT<float, float, double>& g, cudaStream_t st) {
+  return launch_gemm<float, float, double, float>(g, st);
 }
 
 }  // namespace afq

@@ -1,0 +1,460 @@
+// Tensor-core contraction for the mixed-precision path (sm_103a, tcgen05).
+//
+//   D[m][n] = alpha * sum_k A[m][k] * B[n][k]     (A, B K-major; FP32 accumulate)
+//
+// A and B are BF16 (tcgen05.mma kind::f16) or TF32 (kind::tf32) row-major
+// matrices with a row pitch that is a multiple of 16 bytes.  Per CTA one
+// 128 x BN output tile:
+//   warp 0  one thread issues TMA loads (128-byte swizzle) into a STAGES-deep
+//           shared-memory ring, completion tracked by mbarriers;
+//   warp 1  allocates BN TMEM columns; one thread issues tcgen05.mma
+//           (M=128, N=BN, K=32 bytes per instruction) into the TMEM
+//           accumulator and frees ring slots with tcgen05.commit;
+//   warps 2-5 read the accumulator with tcgen05.ld (each warp its 32-lane
+//           quarter) and run the epilogue.
+// Every mbarrier wait is bounded; on time-out the kernel records an error
+// in *err and stops issuing work, and TMEM is always freed before exit.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include "kernels.cuh"
+#include "tc.cuh"
+
+namespace afq {
+namespace tc {
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait: false (and *err set) when the phase never completes.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err, int code) {
+  for (uint32_t i = 0; i < (1u << 22); ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  atomicCAS(err, 0, code);
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x,
+                                            int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, "
+      "%3}], [%4];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand in the 128-byte swizzle
+// layout written by TMA (8 rows x 128 B atoms, 1024 B apart).
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)1 << 16;                    // leading byte offset (unused for SW128 K-major)
+  d |= (uint64_t)((1024 >> 4) & 0x3FFF) << 32;  // stride byte offset: 8 rows x 128 B
+  d |= (uint64_t)1 << 46;                    // descriptor version for tcgen05
+  d |= (uint64_t)2 << 61;                    // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor: FP32 accumulator, A/B format (1 = BF16, 2 = TF32),
+// both K-major, M = 128, N = n.
+__host__ __device__ constexpr uint32_t instr_desc(uint32_t fmt, uint32_t n) {
+  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((n >> 3) << 17) | ((128u >> 4) << 24);
+}
+
+template <bool TF32>
+__device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                    uint32_t accum) {
+  if constexpr (TF32) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accum));
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accum));
+  }
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+constexpr int BM = 128;
+constexpr int BKB = 128;  // bytes of K per stage and row (one swizzle atom)
+
+template <int BN, int STAGES>
+struct Smem {
+  static constexpr int A_BYTES = BM * BKB;
+  static constexpr int B_BYTES = BN * BKB;
+  static constexpr int STAGE = A_BYTES + B_BYTES;
+  static constexpr int RING = STAGES * STAGE;
+  static constexpr int TOTAL = RING + 1024 /*align*/ + 256 /*barriers*/;
+};
+
+template <int BN, int STAGES, bool TF32, class Epi>
+__global__ void __launch_bounds__(192, 1)
+    k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+              int M, int N, int K, Epi epi, int* err) {
+  extern __shared__ uint8_t smem_raw[];
+  using S = Smem<BN, STAGES>;
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + S::RING);
+  uint64_t* empty = full + STAGES;
+  uint64_t* accum = empty + STAGES;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
+  int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = epi.m_origin(blockIdx.x), n0 = epi.n_origin(blockIdx.y);
+  constexpr int ELEM = TF32 ? 4 : 2;
+  constexpr int BK = BKB / ELEM;          // K elements per stage
+  constexpr int KSTEPS = BKB / 32;        // MMAs per stage (32 bytes of K each)
+  const int nk = (K + BK - 1) / BK;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(accum, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"((uint32_t)BN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // TMA producer
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % STAGES;
+      if (kb >= STAGES) {
+        if (!mbar_wait(&empty[s], ((kb / STAGES) - 1) & 1, err, 1)) {
+          *abort_flag = 1;
+          break;
+        }
+      }
+      if (*(volatile int*)abort_flag) break;
+      uint8_t* a = smem + s * S::STAGE;
+      uint8_t* b = a + S::A_BYTES;
+      mbar_expect_tx(&full[s], S::STAGE);
+      tma_load_2d(a, &tmA, &full[s], kb * BK, m0);
+      tma_load_2d(b, &tmB, &full[s], kb * BK, n0);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer
+    constexpr uint32_t idesc = instr_desc(TF32 ? 2u : 1u, (uint32_t)BN);
+    bool ok = true;
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % STAGES;
+      if (!mbar_wait(&full[s], (kb / STAGES) & 1, err, 2)) {
+        ok = false;
+        *abort_flag = 1;
+        break;
+      }
+      fence_after();
+      const uint32_t a = smem_u32(smem + s * S::STAGE);
+      const uint32_t b = a + S::A_BYTES;
+#pragma unroll
+      for (int k = 0; k < KSTEPS; ++k)
+        mma<TF32>(tmem, sw128_desc(a + 32 * k), sw128_desc(b + 32 * k), idesc,
+                  (kb > 0 || k > 0) ? 1u : 0u);
+      mma_commit(&empty[s]);
+    }
+    (void)ok;
+    mma_commit(accum);  // arrives once every issued MMA has completed
+  } else if (warp >= 2) {
+    // epilogue: TMEM lane quarter q = warp % 4 holds rows m0 + 32q + lane
+    const int q = warp & 3;
+    if (!mbar_wait(accum, 0, err, 3)) *(volatile int*)abort_flag = 1;
+    fence_after();
+    asm volatile("bar.sync 1, 128;" ::: "memory");  // one decision for all 4 warps
+    if (!*(volatile int*)abort_flag)
+      epi.template run<BN>(tmem, q, lane, warp - 2, m0, n0, M, N, reinterpret_cast<float*>(smem));
+  }
+  // wait (bounded) for any TMA still in flight on an abort path, then free TMEM
+  if (warp == 0 && lane == 0 && *(volatile int*)abort_flag) {
+    for (int s = 0; s < STAGES; ++s) {
+      for (uint32_t i = 0; i < (1u << 20); ++i)
+        if (mbar_try_wait(&full[s], 0) || mbar_try_wait(&full[s], 1)) break;
+    }
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"((uint32_t)BN));
+  }
+}
+
+// ------------------------------------------------------------ epilogues -----
+// Plain FP32 store of alpha * D to C[m * ldc + n].
+struct EpiStore {
+  float* C;
+  long ldc;
+  float alpha;
+  __device__ __forceinline__ int m_origin(int bx) const { return bx * BM; }
+  __device__ __forceinline__ int n_origin(int by) const { return by * 256; }
+  template <int BN>
+  __device__ __forceinline__ void run(uint32_t tmem, int q, int lane, int, int m0, int n0, int M,
+                                      int N, float*) const {
+    const int row = m0 + 32 * q + lane;
+#pragma unroll 1
+    for (int c0 = 0; c0 < BN; c0 += 16) {
+      float v[16];
+      tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c0, v);
+      if (row >= M) continue;
+      const int col = n0 + c0;
+      float* c = C + (long)row * ldc + col;
+      if (col + 16 <= N && (ldc % 4 == 0)) {
+#pragma unroll
+        for (int i = 0; i < 16; i += 4)
+          *reinterpret_cast<float4*>(c + i) =
+              make_float4(alpha * v[i], alpha * v[i + 1], alpha * v[i + 2], alpha * v[i + 3]);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 16; ++i)
+          if (col + i < N) c[i] = alpha * v[i];
+      }
+    }
+  }
+};
+
+// Exchange part of Eq. localenergy3 fused into the T_g = Lh_g Theta
+// contraction.  Rows of the product are (g, i) = Lh rows, columns (w, c, j)
+// = Theta^T rows (c = re/im plane).  A CTA covers RG whole Cholesky vectors
+// (RG*N <= 128 rows) and CW whole walkers (CW*2N <= 256 columns), so every
+// T_g,w block lies inside its tile: the accumulator is copied to shared
+// memory and sum_ij T_ij T_ji (complex) is formed there; T never reaches
+// global memory.  part[w][tile row][2] receives the sum over the tile's g.
+struct EpiExchange {
+  double* part;
+  int G, W, N, RG, CW, nchunk;
+  __device__ __forceinline__ int m_origin(int bx) const { return bx * RG * N; }
+  __device__ __forceinline__ int n_origin(int by) const { return by * CW * 2 * N; }
+  template <int BN>
+  __device__ __forceinline__ void run(uint32_t tmem, int q, int lane, int ew, int, int, int, int,
+                                      float* sm) const {
+    constexpr int LD = BN + 1;
+    const int r = 32 * q + lane;
+#pragma unroll 1
+    for (int c0 = 0; c0 < BN; c0 += 16) {
+      float v[16];
+      tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c0, v);
+#pragma unroll
+      for (int i = 0; i < 16; ++i) sm[r * LD + c0 + i] = v[i];
+    }
+    asm volatile("bar.sync 1, 128;" ::: "memory");
+    double* red = reinterpret_cast<double*>(sm + 128 * LD);  // [RG][CW][2]
+    const int g0 = blockIdx.x * RG, w0 = blockIdx.y * CW;
+    for (int pi = ew; pi < RG * CW; pi += 4) {
+      const int g = pi / CW, wl = pi % CW;
+      double er = 0.0, ei = 0.0;
+      if (g0 + g < G && w0 + wl < W) {
+        const float* Dg = sm + (g * N) * LD + wl * 2 * N;
+        for (int ij = lane; ij < N * N; ij += 32) {
+          const int i = ij / N, j = ij % N;
+          const float ar = Dg[i * LD + j], ai = Dg[i * LD + N + j];
+          const float br = Dg[j * LD + i], bi = Dg[j * LD + N + i];
+          er += (double)ar * br - (double)ai * bi;
+          ei += (double)ar * bi + (double)ai * br;
+        }
+      }
+      er = warp_sum(er);
+      ei = warp_sum(ei);
+      if (lane == 0) {
+        red[2 * pi] = er;
+        red[2 * pi + 1] = ei;
+      }
+    }
+    asm volatile("bar.sync 1, 128;" ::: "memory");
+    const int t = ew * 32 + lane;
+    if (t < CW && w0 + t < W) {
+      double sr = 0.0, si = 0.0;
+      for (int g = 0; g < RG; ++g) {
+        sr += red[2 * (g * CW + t)];
+        si += red[2 * (g * CW + t) + 1];
+      }
+      double* o = part + ((long)(w0 + t) * nchunk + blockIdx.x) * 2;
+      o[0] = sr;
+      o[1] = si;
+    }
+  }
+};
+
+}  // namespace tc
+
+// ------------------------------------------------------------------- host ----
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+// 2-D row-major [rows][pitch] operand, box = rows_box x 128 bytes, 128B swizzle.
+int make_tmap(CUtensorMap* m, const void* base, int elem_bytes, long rows, long cols, long pitch,
+              int box_rows) {
+  auto fn = encode_fn();
+  if (!fn) {
+    set_error("cuTensorMapEncodeTiled is not available");
+    return AFQMC_ECUDA;
+  }
+  if ((reinterpret_cast<uintptr_t>(base) % 16) || (pitch * elem_bytes) % 16) {
+    set_error("tensor map: base or pitch not 16-byte aligned");
+    return AFQMC_EINVAL;
+  }
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(pitch * elem_bytes)};
+  cuuint32_t box[2] = {(cuuint32_t)(128 / elem_bytes), (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(m, elem_bytes == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                  2, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return AFQMC_ECUDA;
+  }
+  return AFQMC_OK;
+}
+
+template <int BN, int STAGES, bool TF32, class Epi>
+static int launch_tc(const TcGemm& g, const Epi& epi, dim3 grid, cudaStream_t st) {
+  using S = tc::Smem<BN, STAGES>;
+  const int eb = TF32 ? 4 : 2;
+  CUtensorMap ta, tb;
+  AFQ_TRY(make_tmap(&ta, g.A, eb, g.m, g.k, g.lda, tc::BM));
+  AFQ_TRY(make_tmap(&tb, g.B, eb, g.n, g.k, g.ldb, BN));
+  auto kern = tc::k_tc_gemm<BN, STAGES, TF32, Epi>;
+  static bool attr = false;
+  if (!attr) {
+    AFQ_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, S::TOTAL));
+    attr = true;
+  }
+  if (grid.y > 65535u) {
+    set_error("tc gemm: n too large");
+    return AFQMC_EINVAL;
+  }
+  AFQ_LAUNCH(kern, grid, 192, S::TOTAL, st, ta, tb, g.m, g.n, g.k, epi, g.err);
+  return AFQMC_OK;
+}
+
+int tc_gemm_store(const TcGemm& g, float* C, long ldc, float alpha, cudaStream_t st) {
+  if (g.m <= 0 || g.n <= 0) return AFQMC_OK;
+  if (g.k <= 0) {
+    set_error("tc gemm: k must be positive");
+    return AFQMC_EINVAL;
+  }
+  tc::EpiStore e{C, ldc, alpha};
+  dim3 grid(cdiv(g.m, tc::BM), cdiv(g.n, 256));
+  if (g.tf32) return launch_tc<256, 4, true>(g, e, grid, st);
+  return launch_tc<256, 4, false>(g, e, grid, st);
+}
+
+// Exchange blocking: RG Cholesky vectors x CW walkers per 128 x 256 tile.
+void exchange_tile(int N, int* RG, int* CW) {
+  int rg = 128 / N, cw = 256 / (2 * N);
+  *RG = rg < 32 ? rg : 32;
+  *CW = cw < 32 ? cw : 32;
+}
+
+int tc_exchange(const TcGemm& g, int G, int W, int N, double* part, int nchunk, cudaStream_t st) {
+  int RG, CW;
+  exchange_tile(N, &RG, &CW);
+  if (RG < 1 || CW < 1 || nchunk != (G + RG - 1) / RG) {
+    set_error("tc exchange: bad blocking N=%d", N);
+    return AFQMC_EINVAL;
+  }
+  tc::EpiExchange e{part, G, W, N, RG, CW, nchunk};
+  dim3 grid(cdiv(G, RG), cdiv(W, CW));
+  if (g.tf32) return launch_tc<256, 4, true>(g, e, grid, st);
+  return launch_tc<256, 4, false>(g, e, grid, st);
+}
+
+}  // namespace afq
+
+extern "C" int afqmc_contract(int32_t dtype, int64_t m, int64_t n, int64_t k, const void* dA,
+                              int64_t lda, const void* dB, int64_t ldb, float alpha, float* dC,
+                              int64_t ldc, int* d_status, void* stream) {
+  if ((dtype != 0 && dtype != 1) || m < 0 || n < 0 || k < 1 || !dA || !dB || !dC || !d_status ||
+      lda < k || ldb < k || ldc < n || m > (1ll << 31) - 1 || n > (1ll << 31) - 1 ||
+      k > (1ll << 31) - 1) {
+    afq::set_error("afqmc_contract: bad arguments");
+    return AFQMC_EINVAL;
+  }
+  afq::TcGemm g;
+  g.m = (int)m;
+  g.n = (int)n;
+  g.k = (int)k;
+  g.A = dA;
+  g.lda = lda;
+  g.B = dB;
+  g.ldb = ldb;
+  g.tf32 = dtype == 1;
+  g.err = d_status;
+  return afq::tc_gemm_store(g, dC, ldc, alpha, static_cast<cudaStream_t>(stream));
+}

@@ -1,6 +1,8 @@
 // Internal launchers of the AFQMC kernels (not part of the C ABI).
 #pragma once
 
+#include <cuda_bf16.h>
+
 #include "common.cuh"
 
 namespace afq {
@@ -11,19 +13,41 @@ __device__ __forceinline__ bool walker_alive(const double* w2, long w) {
   return w2[2 * w] != 0.0 || w2[2 * w + 1] != 0.0;
 }
 
-struct GemmF64 {
+// Operand copies for the tensor-core contractions of the mixed path.
+enum { LO_NONE = 0, LO_BF16 = 1, LO_TF32 = 2 };
+
+// FP32 -> TF32 with round-to-nearest (ties away), kept in an FP32 container.
+__device__ __forceinline__ float round_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+__device__ __forceinline__ void store_lo(void* base, int kind, long idx, double v) {
+  if (kind == LO_BF16)
+    reinterpret_cast<__nv_bfloat16*>(base)[idx] = __double2bfloat16(v);
+  else
+    reinterpret_cast<float*>(base)[idx] = round_tf32((float)v);
+}
+
+template <typename TA, typename TB, typename TC>
+struct GemmNT {
   int m = 0, n = 0, k = 0, kb = 1, batch = 1;
   double alpha = 1.0, beta = 0.0;
-  const double* A = nullptr;
+  const TA* A = nullptr;
   long lda = 0, sAk = 0, sAb = 0;
-  const double* B = nullptr;
+  const TB* B = nullptr;
   long ldb = 0, sBk = 0, sBb = 0;
-  double* C = nullptr;
+  TC* C = nullptr;
   long ldc = 0, sCb = 0;
   const double* mask = nullptr;  // weights [W][2]: skip rows of dead walkers
   int mask_rows = 1;             // rows of C per walker
 };
+using GemmF64 = GemmNT<double, double, double>;
 int gemm_nt_f64(const GemmF64& g, cudaStream_t st);
+// FP32 accumulation: float64 A -> float32 C, and float32 A -> float64 C
+int gemm_nt_dff(const GemmNT<double, float, float>& g, cudaStream_t st);
+int gemm_nt_ffd(const GemmNT<float, float, double>& g, cudaStream_t st);
 
 // ---- step kernels (float64) -------------------------------------------------
 struct FieldArgs {
@@ -36,19 +60,26 @@ struct FieldArgs {
   double* x;         // [W][2][G]  x = xi - xbar
   double* scal;      // [W][8]: sum xi xbar, sum xbar^2, sum x c (complex each)
   const int64_t* dstep;  // device step counter (the step being taken)
+  // mixed path: t read as float, x written as a BF16/TF32 copy with pitch Gp
+  const float* t32 = nullptr;
+  void* x_lo = nullptr;
+  int lo_kind = LO_NONE, Gp = 0;
 };
 int launch_field(const FieldArgs& a, cudaStream_t st);
 
-struct TaylorArgs {
+template <typename T>
+struct TaylorArgsT {
   int W, M, N, P, k;  // k: order of the term produced (1..n)
+  long ldy;           // pitch of one (walker, re/im) row of Y
   double scale;       // sqrt(dt) / k
-  const double* Y;    // [W][2][P] packed sum_g x_g L_g (re, im)
-  const double* tin;  // [W][2][N][M] previous term (transposed orbitals)
-  double* tout;       // [W][2][N][M] new term
-  double* acc;        // [W][2][N][M] running sum (k == 1: acc = tin + tout)
-  const double* wt;
+  const T* Y;         // [W][2][ldy] packed sum_g x_g L_g (re, im)
+  const T* tin;       // [W][2][N][M] previous term (transposed orbitals)
+  T* tout;            // [W][2][N][M] new term
+  T* acc;             // [W][2][N][M] running sum (k == 1: acc = tin + tout)
 };
-int launch_taylor_term(const TaylorArgs& a, cudaStream_t st);
+using TaylorArgs = TaylorArgsT<double>;
+int launch_taylor_term(const TaylorArgsT<double>& a, cudaStream_t st);
+int launch_taylor_term(const TaylorArgsT<float>& a, cudaStream_t st);
 
 struct LuArgs {
   int W, N;
@@ -65,6 +96,8 @@ struct ThetaArgs {
   const double* phiT;  // [W][2][N][M]
   double* thetaT;      // [W][2][N][M]
   const double* wt;
+  void* th_lo = nullptr;  // mixed path: BF16/TF32 copy [W][2][N][Mp]
+  int lo_kind = LO_NONE, Mp = 0;
 };
 int launch_theta(const ThetaArgs& a, cudaStream_t st);
 
@@ -106,6 +139,7 @@ struct ElocArgs {
   const double* part;    // [W][nchunk][2]
   double* eloc;          // [W][2]
   const double* wt;
+  const float* t32 = nullptr;  // mixed path: t as float
 };
 int launch_eloc(const ElocArgs& a, cudaStream_t st);
 
@@ -150,5 +184,9 @@ int launch_scale(double* X, long n, double s, cudaStream_t st);
 int launch_init_walkers(const double* VTt, double* phiT, double* wt, int W, int N, int M,
                         cudaStream_t st);
 int launch_sumsq(const double* v, double* out, int n, cudaStream_t st);
+// dst[r][c] = lo(src[r][c]) for c < cols, 0 for cols <= c < ldd
+int launch_convert_lo(const double* src, long rows, long cols, long lds, void* dst, long ldd,
+                      int kind, cudaStream_t st);
+int launch_convert_f32(const double* src, float* dst, long n, cudaStream_t st);
 
 }  // namespace afq

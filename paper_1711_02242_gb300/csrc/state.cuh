@@ -23,6 +23,14 @@ struct Bufs {
   // set-up scratch (aliases the step scratch)
   double *Lfull, *L2, *cLp, *E0, *E1, *X, *red;
   int P, nchunk, gc;
+  // mixed path: BF16 / TF32 operand copies and FP32 step buffers
+  bool mixed = false;
+  int lo_kind = 0, lo_bytes = 0, Gp = 0, Mp = 0;
+  long Pp = 0;
+  void *LpT_lo = nullptr, *Lh_lo = nullptr, *x_lo = nullptr, *th_lo = nullptr;
+  float *t32 = nullptr, *Y32 = nullptr, *Bh32 = nullptr, *T0f = nullptr, *T1f = nullptr,
+        *accf = nullptr;
+  int* status = nullptr;  // device status word (tensor-core waits)
 };
 
 size_t plan(const afqmc_params& p, Bufs* b, char* base);

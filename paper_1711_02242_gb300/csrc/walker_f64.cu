@@ -27,10 +27,13 @@ __global__ void __launch_bounds__(256) k_field(FieldArgs a) {
   const bool alive = walker_alive(a.wt, w);
   double s0 = 0, s1 = 0, s2 = 0, s3 = 0, s4 = 0, s5 = 0;
   const long base = (long)w * 2 * a.G;
-  const double* tr = a.t + base;
-  const double* ti = tr + a.G;
-  double* xr = a.x + base;
-  double* xim = xr + a.G;
+  const double* tr = a.t ? a.t + base : nullptr;
+  const double* ti = tr ? tr + a.G : nullptr;
+  const float* tr32 = a.t32 ? a.t32 + base : nullptr;
+  const float* ti32 = tr32 ? tr32 + a.G : nullptr;
+  double* xr = a.x ? a.x + base : nullptr;
+  double* xim = xr ? xr + a.G : nullptr;
+  const long xl = (long)w * 2 * a.Gp;
   const int npair = (a.G + 1) / 2;
   for (int k = threadIdx.x; k < npair; k += blockDim.x) {
     double xa, xb;
@@ -42,8 +45,10 @@ __global__ void __launch_bounds__(256) k_field(FieldArgs a) {
       const double xi = h ? xb : xa;
       double br = 0.0, bi = 0.0;
       if (a.mode == AFQMC_PHASELESS) {
-        br = a.sdt * ti[g];
-        bi = -a.sdt * (tr[g] - a.c[g]);
+        const double tre = tr32 ? (double)tr32[g] : tr[g];
+        const double tim = ti32 ? (double)ti32[g] : ti[g];
+        br = a.sdt * tim;
+        bi = -a.sdt * (tre - a.c[g]);
         if (a.fb_cap > 0.0) {
           const double mag = hypot(br, bi);
           if (mag > a.fb_cap) {
@@ -55,8 +60,14 @@ __global__ void __launch_bounds__(256) k_field(FieldArgs a) {
       }
       double vr = xi - br, vi = -bi;
       if (!alive) vr = vi = 0.0;
-      xr[g] = vr;
-      xim[g] = vi;
+      if (xr) {
+        xr[g] = vr;
+        xim[g] = vi;
+      }
+      if (a.x_lo) {
+        store_lo(a.x_lo, a.lo_kind, xl + g, vr);
+        store_lo(a.x_lo, a.lo_kind, xl + a.Gp + g, vi);
+      }
       s0 += xi * br;
       s1 += xi * bi;
       s2 += br * br - bi * bi;
@@ -87,26 +98,28 @@ int launch_field(const FieldArgs& a, cudaStream_t st) {
 namespace {
 constexpr int TT_P = 64, TT_Q = 16, TT_NMAX = 64;
 }
-__global__ void __launch_bounds__(256) k_taylor_term(TaylorArgs a) {
-  __shared__ double Ys[2][TT_Q][TT_P];
-  __shared__ double Ts[2][TT_NMAX][TT_Q + 1];
+template <typename T>
+__global__ void __launch_bounds__(256) k_taylor_term(TaylorArgsT<T> a) {
+  __shared__ T Ys[2][TT_Q][TT_P];
+  __shared__ T Ts[2][TT_NMAX][TT_Q + 1];
+  // every walker is computed (the work does not depend on the weights); the
+  // result of a dead walker is never stored into its orbitals
   const int w = blockIdx.y;
-  if (!walker_alive(a.wt, w)) return;
   const int p0 = blockIdx.x * TT_P;
   const int tx = threadIdx.x % TT_P, ty = threadIdx.x / TT_P;  // 4 rows of i
   const int M = a.M, N = a.N;
-  const double* Yr = a.Y + (long)w * 2 * a.P;
-  const double* Yi = Yr + a.P;
+  const T* Yr = a.Y + (long)w * 2 * a.ldy;
+  const T* Yi = Yr + a.ldy;
   const long wo = (long)w * 2 * N * M;
-  const double* tin = a.tin + wo;
-  double accR[TT_NMAX / 4], accI[TT_NMAX / 4];
+  const T* tin = a.tin + wo;
+  T accR[TT_NMAX / 4], accI[TT_NMAX / 4];
 #pragma unroll
-  for (int r = 0; r < TT_NMAX / 4; ++r) accR[r] = accI[r] = 0.0;
+  for (int r = 0; r < TT_NMAX / 4; ++r) accR[r] = accI[r] = T(0);
   for (int q0 = 0; q0 < M; q0 += TT_Q) {
     for (int idx = threadIdx.x; idx < TT_Q * TT_P; idx += blockDim.x) {
       const int qq = idx / TT_P, pp = idx % TT_P;
       const int q = q0 + qq, p = p0 + pp;
-      double vr = 0.0, vi = 0.0;
+      T vr = T(0), vi = T(0);
       if (q < M && p < M) {
         const long id = (q <= p) ? packed_index(q, p, M) : packed_index(p, q, M);
         vr = Yr[id];
@@ -119,17 +132,17 @@ __global__ void __launch_bounds__(256) k_taylor_term(TaylorArgs a) {
       const int c = idx / (N * TT_Q), rem = idx % (N * TT_Q);
       const int i = rem / TT_Q, qq = rem % TT_Q;
       const int q = q0 + qq;
-      Ts[c][i][qq] = (q < M) ? tin[((long)c * N + i) * M + q] : 0.0;
+      Ts[c][i][qq] = (q < M) ? tin[((long)c * N + i) * M + q] : T(0);
     }
     __syncthreads();
 #pragma unroll 4
     for (int qq = 0; qq < TT_Q; ++qq) {
-      const double yr = Ys[0][qq][tx], yi = Ys[1][qq][tx];
+      const T yr = Ys[0][qq][tx], yi = Ys[1][qq][tx];
 #pragma unroll
       for (int r = 0; r < TT_NMAX / 4; ++r) {
         const int i = ty + 4 * r;
         if (i < N) {
-          const double tr = Ts[0][i][qq], ti = Ts[1][i][qq];
+          const T tr = Ts[0][i][qq], ti = Ts[1][i][qq];
           accR[r] = fma(tr, yi, fma(ti, yr, accR[r]));
           accI[r] = fma(tr, yr, fma(-ti, yi, accI[r]));
         }
@@ -143,7 +156,7 @@ __global__ void __launch_bounds__(256) k_taylor_term(TaylorArgs a) {
   for (int r = 0; r < TT_NMAX / 4; ++r) {
     const int i = ty + 4 * r;
     if (i >= N) break;
-    const double oR = -a.scale * accR[r], oI = a.scale * accI[r];
+    const T oR = -T(a.scale) * accR[r], oI = T(a.scale) * accI[r];
     const long o0 = wo + (long)i * M + p, o1 = wo + ((long)N + i) * M + p;
     a.tout[o0] = oR;
     a.tout[o1] = oI;
@@ -157,15 +170,18 @@ __global__ void __launch_bounds__(256) k_taylor_term(TaylorArgs a) {
   }
 }
 
-int launch_taylor_term(const TaylorArgs& a, cudaStream_t st) {
+template <typename T>
+static int launch_taylor(const TaylorArgsT<T>& a, cudaStream_t st) {
   if (a.N > TT_NMAX) {
     set_error("taylor: N=%d above the supported %d", a.N, TT_NMAX);
     return AFQMC_EUNSUPPORTED;
   }
   dim3 grid(cdiv(a.M, TT_P), a.W);
-  AFQ_LAUNCH(k_taylor_term, grid, 256, 0, st, a);
+  AFQ_LAUNCH(k_taylor_term<T>, grid, 256, 0, st, a);
   return AFQMC_OK;
 }
+int launch_taylor_term(const TaylorArgsT<double>& a, cudaStream_t st) { return launch_taylor(a, st); }
+int launch_taylor_term(const TaylorArgsT<float>& a, cudaStream_t st) { return launch_taylor(a, st); }
 
 // ------------------------------------------------------- LU / inverse ------
 // Overlap matrix S = V_T^T Phi (Theorem 1.1): Gauss-Jordan elimination with
@@ -176,7 +192,7 @@ int launch_taylor_term(const TaylorArgs& a, cudaStream_t st) {
 __global__ void __launch_bounds__(128) k_lu_inv(LuArgs a) {
   extern __shared__ double2 lu_sm[];
   const int w = blockIdx.x;
-  if (a.wt && !walker_alive(a.wt, w)) return;
+  const bool live = !a.wt || walker_alive(a.wt, w);  // log det stored for live walkers
   const int N = a.N;
   double2* A = lu_sm;          // [N][N]
   double2* Inv = lu_sm + N * N;  // [N][N]
@@ -265,7 +281,7 @@ __global__ void __launch_bounds__(128) k_lu_inv(LuArgs a) {
     out[idx] = singular ? 0.0 : Inv[idx].x;
     out[(long)N * N + idx] = singular ? 0.0 : Inv[idx].y;
   }
-  if (threadIdx.x == 0) {
+  if (threadIdx.x == 0 && live) {
     if (singular) {
       a.logdet[2L * w] = -INFINITY;
       a.logdet[2L * w + 1] = 0.0;
@@ -298,7 +314,7 @@ int launch_lu_inv(const LuArgs& a, cudaStream_t st) {
 __global__ void __launch_bounds__(128) k_theta(ThetaArgs a) {
   extern __shared__ double th_sm[];  // [2][N][N]
   const int w = blockIdx.y;
-  if (!walker_alive(a.wt, w)) return;
+  const bool live = walker_alive(a.wt, w);  // Theta is stored for live walkers only
   const int N = a.N, M = a.M;
   const double* Si = a.Sinv + (long)w * 2 * N * N;
   for (int idx = threadIdx.x; idx < 2 * N * N; idx += blockDim.x) th_sm[idx] = Si[idx];
@@ -325,12 +341,15 @@ __global__ void __launch_bounds__(128) k_theta(ThetaArgs a) {
         }
       }
     }
+    if (!live) continue;
 #pragma unroll
     for (int u = 0; u < 16; ++u) {
       const int i = i0 + u;
       if (i < N) {
         th[(long)i * M + p] = ar[u];
         th[((long)N + i) * M + p] = ai[u];
+        if (a.th_lo) store_lo(a.th_lo, a.lo_kind, ((long)w * 2 * N + i) * a.Mp + p, ar[u]);
+        if (a.th_lo) store_lo(a.th_lo, a.lo_kind, ((long)w * 2 * N + N + i) * a.Mp + p, ai[u]);
       }
     }
   }
@@ -456,8 +475,7 @@ int exchange_chunk(int N, int G) {
 
 __global__ void __launch_bounds__(EX_T) k_exchange(ExchArgs a) {
   extern __shared__ double ex_sm[];
-  const int chunk = blockIdx.x, w = blockIdx.y;
-  if (!walker_alive(a.wt, w)) return;
+  const int chunk = blockIdx.x, w = blockIdx.y;  // every walker (dead ones too)
   const int M = a.M, N = a.N;
   const int g0 = chunk * a.gc;
   const int gcount = min(a.gc, a.G - g0);
@@ -563,12 +581,18 @@ __global__ void __launch_bounds__(256) k_eloc(ElocArgs a) {
     e1r += hv * th[idx];
     e1i += hv * th[(long)N * M + idx];
   }
-  const double* tr = a.t + (long)w * 2 * G;
-  const double* ti = tr + G;
   double cr = 0.0, ci = 0.0;
   for (int g = threadIdx.x; g < G; g += blockDim.x) {
-    cr += tr[g] * tr[g] - ti[g] * ti[g];
-    ci += 2.0 * tr[g] * ti[g];
+    double re, imv;
+    if (a.t32) {
+      re = a.t32[(long)w * 2 * G + g];
+      imv = a.t32[(long)w * 2 * G + G + g];
+    } else {
+      re = a.t[(long)w * 2 * G + g];
+      imv = a.t[(long)w * 2 * G + G + g];
+    }
+    cr += re * re - imv * imv;
+    ci += 2.0 * re * imv;
   }
   e1r = block_sum(e1r, sh);
   e1i = block_sum(e1i, sh);
@@ -867,6 +891,38 @@ int launch_sumsq(const double* v, double* out, int n, cudaStream_t st) {
   return AFQMC_OK;
 }
 
+}  // namespace afq
+
+// ------------------------------------------------- low-precision copies ----
+namespace afq {
+__global__ void k_convert_lo(const double* src, long rows, long cols, long lds, void* dst,
+                             long ldd, int kind) {
+  const long n = rows * ldd;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long)gridDim.x * blockDim.x) {
+    const long r = i / ldd, c = i % ldd;
+    store_lo(dst, kind, i, c < cols ? src[r * lds + c] : 0.0);
+  }
+}
+
+int launch_convert_lo(const double* src, long rows, long cols, long lds, void* dst, long ldd,
+                      int kind, cudaStream_t st) {
+  if (rows <= 0) return AFQMC_OK;
+  AFQ_LAUNCH(k_convert_lo, 152 * 8, 256, 0, st, src, rows, cols, lds, dst, ldd, kind);
+  return AFQMC_OK;
+}
+
+__global__ void k_convert_f32(const double* src, float* dst, long n) {
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long)gridDim.x * blockDim.x)
+    dst[i] = (float)src[i];
+}
+
+int launch_convert_f32(const double* src, float* dst, long n, cudaStream_t st) {
+  if (n <= 0) return AFQMC_OK;
+  AFQ_LAUNCH(k_convert_f32, 152 * 4, 256, 0, st, src, dst, n);
+  return AFQMC_OK;
+}
 }  // namespace afq
 
 // ------------------------------------------------------- generator access --

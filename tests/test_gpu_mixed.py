@@ -1,0 +1,94 @@
+"""Mixed-precision path (tcgen05 BF16/TF32 contractions, FP32 propagation,
+FP64 overlaps/weights/QR) against the FP64 path on identical fields.
+
+The FP64 path is itself held to the oracle at 1e-10 (test_gpu_parity), so
+these tolerances measure the rounding of the mixed path only: BF16 inputs
+carry a relative error of 2^-9, TF32 inputs 2^-11, FP32 propagation 2^-24.
+"""
+import numpy as np
+import pytest
+
+import workloads
+from oracle import scf
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_1711_02242_gb300 as p
+
+    return p
+
+
+def runs(pkg, w, precisions, nwalkers=None, **kw):
+    h1, L, _ = w.hamiltonian()
+    C, _, _, _ = scf.rhf(h1, L, w.N)
+    out = {}
+    for prec in precisions:
+        p = pkg.default_params(w.M, w.N, w.nchol, nwalkers or w.nwalkers, dt=w.dt, seed=w.seed,
+                               qr_period=w.qr_period, precision=prec, **kw)
+        out[prec] = pkg.AfqmcRun(h1, L, C, p)
+    return out
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("prec,tol", [(2, 3e-3), (1, 4e-4)])
+def test_trial_energy_mixed_vs_fp64(pkg, prec, tol):
+    """E_loc at the trial (Eqs. localenergy2/3): force bias and exchange
+    contractions on the tensor cores, ragged tiles (N=10: 12 vectors and 12
+    walkers per tile; 500 vectors, 1024 walkers)."""
+    w = workloads.config("c1")
+    r = runs(pkg, w, [0, prec], energy_period=0)
+    e64 = r[0].local_energies()
+    emx = r[prec].local_energies()
+    assert np.max(np.abs(emx - e64) / np.abs(e64)) < tol
+    assert r[prec].info().status == 0
+
+
+@pytest.mark.parametrize("prec,tol_phi,tol_e", [(2, 3e-2, 5e-3), (1, 5e-3, 5e-4)])
+def test_one_step_mixed_vs_fp64(pkg, prec, tol_phi, tol_e):
+    """One full step of the 12-orbital workload on identical Philox fields."""
+    w = workloads.config("c0")
+    r = runs(pkg, w, [0, prec], energy_period=1)
+    for x in r.values():
+        x.propagate(1)
+    p64, w64, _ = r[0].get_walkers()
+    pmx, wmx, _ = r[prec].get_walkers()
+    alive = np.nonzero(w64 != 0)[0]
+    assert alive.size > w.nwalkers // 2
+    assert rel(pmx[alive], p64[alive]) < tol_phi
+    e64 = r[0].energy_log()[-1, 1]
+    emx = r[prec].energy_log()[-1, 1]
+    assert abs(emx - e64) < tol_e * abs(e64)
+    assert r[prec].info().status == 0
+
+
+def test_mixed_full_size_runs_clean(pkg):
+    """M=300, N=25, 1800 vectors, 512 walkers: set-up and two steps in BF16
+    with an energy evaluation; the tensor-core status word stays 0 and the
+    trial energy matches the FP64 set-up to BF16 accuracy."""
+    w = workloads.config("c2")
+    h1, L, _ = w.hamiltonian()
+    C = np.linalg.eigh(h1)[1][:, :w.N]
+    p = pkg.default_params(w.M, w.N, w.nchol, w.nwalkers, dt=w.dt, seed=w.seed, precision=2,
+                           energy_period=2)
+    run = pkg.AfqmcRun(h1, L, C, p)
+    e_mixed_trial = run.local_energies()[0]
+    run.propagate(2)
+    info = run.info()
+    assert info.status == 0 and info.step == 2
+    assert run.energy_log().shape[0] == 1
+    p64 = pkg.default_params(w.M, w.N, w.nchol, 4, dt=w.dt, seed=w.seed, energy_period=0)
+    r64 = pkg.AfqmcRun(h1, L, C, p64)
+    e64 = r64.local_energies()[0]
+    assert abs(e_mixed_trial - e64) < 5e-3 * abs(e64)
