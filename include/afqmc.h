@@ -293,6 +293,40 @@ AFQMC_API int afqmc_philox4x32_10(uint64_t key, const uint32_t* d_ctr, int64_t n
 AFQMC_API int afqmc_gaussian_fields(uint64_t seed, int64_t step, int32_t w0, int32_t nw,
                                     int32_t nchol, double* d_out, void* stream);
 
+/*
+ * Local energies for callers that cannot allocate device memory.
+ *
+ * The paper has no counterpart: this is the float64 local-energy evaluation
+ * of afqmc_local_energies() packaged for callers that own no workspace and may
+ * not create one - for example a host program whose device memory all belongs
+ * to another framework's pool, or code that must not call cudaMalloc because
+ * the allocation would synchronise the device in the middle of its own stream
+ * work.  The caller passes only inputs and outputs (all DEVICE float64):
+ *   d_Lh     [nchol][N][M]      half-rotated Cholesky vectors V_T^T L_g
+ *   d_hh     [N][M]             V_T^T h
+ *   d_thetaT [nwalkers][2][N][M] Theta^T = (Phi S^-1)^T, real plane then
+ *                               imaginary plane per walker
+ *   d_eloc   [nwalkers][2]      output: E_loc (real, imaginary), H0 included
+ * The intermediate results (force-bias traces and exchange partial sums,
+ * nwalkers * (2 nchol + 2 ceil(nchol / chunk)) float64, chunk = the number of
+ * Cholesky vectors one exchange block handles) live in one fixed 16 MiB array
+ * inside the library, which every GPU that loads the library reserves until
+ * the process exits.  Calls needing more return AFQMC_ENOSPC and launch
+ * nothing (split the walkers over several calls).  Nothing is allocated:
+ * no cudaMalloc, no cudaFree, no allocating library routine.
+ * The first call on a device looks up the array's device address with
+ * cudaGetSymbolAddress (with that device current); make that first call
+ * before any stream capture.  Every call writes all of the array it later
+ * reads, so nothing needs clearing, but all calls share the one array: calls
+ * that may overlap on the GPU (different streams, or different host threads
+ * on the same device) race and must be serialised by the caller.
+ * Asynchronous on `stream`.
+ */
+AFQMC_API int afqmc_local_energies_noalloc(int32_t M, int32_t N, int32_t nchol,
+                                           int32_t nwalkers, const double* d_Lh,
+                                           const double* d_hh, const double* d_thetaT,
+                                           double H0, double* d_eloc, void* stream);
+
 /* Message for the calling thread's last failed call (never NULL). */
 AFQMC_API const char* afqmc_last_error(void);
 

@@ -30,7 +30,7 @@ EXPORTED = ["afqmc_default_params", "afqmc_workspace_size", "afqmc_init", "afqmc
             "afqmc_get_energy_log", "afqmc_get_info", "afqmc_save", "afqmc_load",
             "afqmc_destroy", "afqmc_last_error", "afqmc_launch_count",
             "afqmc_philox4x32_10", "afqmc_gaussian_fields", "afqmc_contract",
-            "afqmc_profile_start", "afqmc_profile_stop"]
+            "afqmc_profile_start", "afqmc_profile_stop", "afqmc_local_energies_noalloc"]
 
 
 class Params(ctypes.Structure):
@@ -95,6 +95,8 @@ def lib():
                                           ctypes.c_float, vp, ctypes.c_int64, vp, vp]),
         "afqmc_profile_start": (ctypes.c_int, [vp, ctypes.c_int32]),
         "afqmc_profile_stop": (ctypes.c_int, [vp, vp, vp, vp]),
+        "afqmc_local_energies_noalloc": (ctypes.c_int, [ctypes.c_int32] * 4 + [vp] * 3 +
+                                         [ctypes.c_double, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
