@@ -90,7 +90,8 @@ size_t plan(const afqmc_params& p, Bufs* b, char* base) {
     b->x_lo = a.take<char>(W * 2 * Gp * lo);
     b->th_lo = a.take<char>(W * 2 * N * Mp * lo);
     b->t32 = a.take<float>(W * 2 * G);
-    b->Bh32 = a.take<float>(M * M);
+    b->Bh_lo = a.take<char>(M * Mp * lo);
+    b->Bh_tf = a.take<float>(M * Mp);
   }
   // scratch: the set-up and the step never run at the same time
   const size_t scratch_at = (a.off + 255) & ~size_t(255);
@@ -99,9 +100,11 @@ size_t plan(const afqmc_params& p, Bufs* b, char* base) {
     b->Y = nullptr;
     b->acc = nullptr;
     b->Y32 = s1.take<float>(W * 2 * Pp);
-    b->T0f = s1.take<float>(W * 2 * N * M);
-    b->T1f = s1.take<float>(W * 2 * N * M);
-    b->accf = s1.take<float>(W * 2 * N * M);
+    b->V_lo = s1.take<char>(W * M * 2 * Mp * lo);
+    b->phi_lo = s1.take<char>(W * 2 * N * Mp * lo);
+    b->acc32 = s1.take<float>(W * 2 * N * Mp);
+    b->Tb0 = s1.take<char>(W * 2 * N * 2 * Mp * lo);
+    b->Tb1 = s1.take<char>(W * 2 * N * 2 * Mp * lo);
   } else {
     b->Y = s1.take<double>(W * 2 * P);
     b->acc = s1.take<double>(W * 2 * N * M);
@@ -185,26 +188,14 @@ static int all_finite(const double* v, size_t n, const char* what) {
 int overlap_update(afqmc_state* s, bool into_ld) {
   const afqmc_params& p = s->p;
   const Bufs& b = s->b;
-  GemmF64 g;
-  g.m = 2 * p.N * p.nwalkers;
-  g.n = p.N;
-  g.k = p.M;
-  g.A = b.phiT;
-  g.lda = p.M;
-  g.B = b.VTt;
-  g.ldb = p.M;
-  g.C = b.S;
-  g.ldc = p.N;
-  AFQ_TRY(gemm_nt_f64(g, s->st));
-  LuArgs lu{p.nwalkers, p.N, b.S, b.Sinv, into_ld ? b.ld : b.ld_new, b.wt};
-  AFQ_TRY(launch_lu_inv(lu, s->st));
-  ThetaArgs th{p.nwalkers, p.M, p.N, b.Sinv, b.phiT, b.thetaT, b.wt};
+  // S = V_T^T Phi, S^-1, log det and Theta in one float64 kernel per walker
+  OverlapArgs ov{p.nwalkers, p.M, p.N, b.VTt, b.phiT, b.thetaT, into_ld ? b.ld : b.ld_new, b.wt};
   if (b.mixed) {
-    th.th_lo = b.th_lo;
-    th.lo_kind = b.lo_kind;
-    th.Mp = b.Mp;
+    ov.th_lo = b.th_lo;
+    ov.lo_kind = b.lo_kind;
+    ov.Mp = b.Mp;
   }
-  AFQ_TRY(launch_theta(th, s->st));
+  AFQ_TRY(launch_overlap(ov, s->st));
   return AFQMC_OK;
 }
 
@@ -374,44 +365,60 @@ static int propagate_mixed(afqmc_state* s) {
   g.err = b.status;
   AFQ_TRY(tc_gemm_store(g, b.Y32, b.Pp, 1.0f, s->st));
   prof_end(s);
-  prof_begin(s, AFQMC_PH_BHALF);
-  GemmNT<double, float, float> b1;
-  b1.m = 2 * N * W;
-  b1.n = M;
-  b1.k = M;
-  b1.A = b.phiT;
-  b1.lda = M;
-  b1.B = b.Bh32;
-  b1.ldb = M;
-  b1.C = b.T0f;
-  b1.ldc = M;
-  AFQ_TRY(gemm_nt_dff(b1, s->st));
-  prof_end(s);
+  // [Re V | Im V] operand rows for the Taylor terms
   prof_begin(s, AFQMC_PH_TAYLOR);
-  float* tin = b.T0f;
-  float* tout = b.T1f;
+  AFQ_TRY(launch_unpack_v(b.Y32, b.Pp, W, M, b.Mp, s->sdt, b.V_lo, b.lo_kind, s->st));
+  prof_end(s);
+  // first half step: acc = (B_half Phi)^T, Tb0 = the 0th Taylor term
+  prof_begin(s, AFQMC_PH_BHALF);
+  AFQ_TRY(launch_convert_lo(b.phiT, 2L * N * W, M, M, b.phi_lo, b.Mp, b.lo_kind, s->st));
+  TcGemm h1;
+  h1.m = 2 * N * W;
+  h1.n = M;
+  h1.k = M;
+  h1.A = b.phi_lo;
+  h1.lda = b.Mp;
+  h1.B = b.Bh_lo;
+  h1.ldb = b.Mp;
+  h1.tf32 = b.lo_kind == LO_TF32;
+  h1.err = b.status;
+  AFQ_TRY(tc_prop_first(h1, b.acc32, b.Tb0, b.lo_kind, N, M, b.Mp, s->st));
+  prof_end(s);
+  // terms k = 1..n: T_k = V T_{k-1} / k, acc += T_k
+  prof_begin(s, AFQMC_PH_TAYLOR);
+  void* tin = b.Tb0;
+  void* tout = b.Tb1;
   for (int k = 1; k <= p.taylor_order; ++k) {
-    TaylorArgsT<float> ta{W, M, N, b.P, k, b.Pp, s->sdt / k, b.Y32, tin, tout, b.accf};
-    AFQ_TRY(launch_taylor_term(ta, s->st));
-    float* t_ = tin;
+    TcGemm tg;
+    tg.m = W * M;
+    tg.n = W * 2 * N;
+    tg.k = 2 * b.Mp;
+    tg.A = b.V_lo;
+    tg.lda = 2L * b.Mp;
+    tg.B = tin;
+    tg.ldb = 2L * b.Mp;
+    tg.tf32 = b.lo_kind == LO_TF32;
+    tg.err = b.status;
+    AFQ_TRY(tc_taylor_term(tg, b.acc32, k < p.taylor_order ? tout : nullptr, b.lo_kind, W, N, M,
+                           b.Mp, 1.0f / (float)k, s->st));
+    void* t_ = tin;
     tin = tout;
     tout = t_;
   }
   prof_end(s);
+  // last half step (TF32 on the FP32 series sum): Phi <- B_half acc, live walkers
   prof_begin(s, AFQMC_PH_BHALF);
-  GemmNT<float, float, double> b2;
-  b2.m = 2 * N * W;
-  b2.n = M;
-  b2.k = M;
-  b2.A = b.accf;
-  b2.lda = M;
-  b2.B = b.Bh32;
-  b2.ldb = M;
-  b2.C = b.phiT;
-  b2.ldc = M;
-  b2.mask = b.wt;
-  b2.mask_rows = 2 * N;
-  AFQ_TRY(gemm_nt_ffd(b2, s->st));
+  TcGemm h2;
+  h2.m = 2 * N * W;
+  h2.n = M;
+  h2.k = M;
+  h2.A = b.acc32;
+  h2.lda = b.Mp;
+  h2.B = b.Bh_tf;
+  h2.ldb = b.Mp;
+  h2.tf32 = true;
+  h2.err = b.status;
+  AFQ_TRY(tc_prop_last(h2, b.phiT, b.wt, N, M, s->st));
   prof_end(s);
   return AFQMC_OK;
 }
@@ -607,7 +614,8 @@ static int setup_device(afqmc_state* s, const double* h1, const double* L, const
     AFQ_TRY(launch_convert_lo(b.Lh, (long)G * N, M, M, b.Lh_lo, b.Mp, b.lo_kind, st));
     AFQ_CUDA(cudaMemsetAsync(b.th_lo, 0, (size_t)W * 2 * N * b.Mp * b.lo_bytes, st));
     AFQ_CUDA(cudaMemsetAsync(b.x_lo, 0, (size_t)W * 2 * b.Gp * b.lo_bytes, st));
-    AFQ_TRY(launch_convert_f32(b.Bh, b.Bh32, (long)M * M, st));
+    AFQ_TRY(launch_convert_lo(b.Bh, M, M, M, b.Bh_lo, b.Mp, b.lo_kind, st));
+    AFQ_TRY(launch_convert_lo(b.Bh, M, M, M, b.Bh_tf, b.Mp, LO_TF32, st));
   }
   // walkers at the trial, their overlaps, and the trial energy
   AFQ_TRY(launch_init_walkers(b.VTt, b.phiT, b.wt, W, N, M, st));
@@ -620,6 +628,14 @@ static int setup_device(afqmc_state* s, const double* h1, const double* L, const
   AFQ_CUDA(cudaMemcpyAsync(e0, b.eloc, sizeof(e0), cudaMemcpyDeviceToHost, st));
   AFQ_CUDA(cudaStreamSynchronize(st));
   s->E_T = e0[0];
+  if (b.mixed) {
+    // the tensor-core operands read their padded columns: clear them once, now
+    // that the set-up scratch these buffers alias is no longer needed
+    AFQ_CUDA(cudaMemsetAsync(b.acc32, 0, sizeof(float) * (size_t)W * 2 * N * b.Mp, st));
+    AFQ_CUDA(cudaMemsetAsync(b.Tb0, 0, (size_t)W * 2 * N * 2 * b.Mp * b.lo_bytes, st));
+    AFQ_CUDA(cudaMemsetAsync(b.Tb1, 0, (size_t)W * 2 * N * 2 * b.Mp * b.lo_bytes, st));
+    AFQ_CUDA(cudaStreamSynchronize(st));
+  }
   s->e_shift = std::isnan(p.e_shift) ? s->E_T : p.e_shift;
   s->wmax = std::isnan(p.wmax) ? std::fmax(100.0, W / 10.0) : p.wmax;
   if (p.ecap_C > 0.0) {

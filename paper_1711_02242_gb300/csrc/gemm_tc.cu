@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(192, 1)
   int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = epi.m_origin(blockIdx.x), n0 = epi.n_origin(blockIdx.y);
+  const int m0 = epi.m_origin(blockIdx.x, blockIdx.y), n0 = epi.n_origin(blockIdx.x, blockIdx.y);
   constexpr int ELEM = TF32 ? 4 : 2;
   constexpr int BK = BKB / ELEM;          // K elements per stage
   constexpr int KSTEPS = BKB / 32;        // MMAs per stage (32 bytes of K each)
@@ -250,8 +250,8 @@ struct EpiStore {
   float* C;
   long ldc;
   float alpha;
-  __device__ __forceinline__ int m_origin(int bx) const { return bx * BM; }
-  __device__ __forceinline__ int n_origin(int by) const { return by * 256; }
+  __device__ __forceinline__ int m_origin(int bx, int) const { return bx * BM; }
+  __device__ __forceinline__ int n_origin(int, int by) const { return by * 256; }
   template <int BN>
   __device__ __forceinline__ void run(uint32_t tmem, int q, int lane, int, int m0, int n0, int M,
                                       int N, float*) const {
@@ -287,8 +287,8 @@ struct EpiStore {
 struct EpiExchange {
   double* part;
   int G, W, N, RG, CW, nchunk;
-  __device__ __forceinline__ int m_origin(int bx) const { return bx * RG * N; }
-  __device__ __forceinline__ int n_origin(int by) const { return by * CW * 2 * N; }
+  __device__ __forceinline__ int m_origin(int bx, int) const { return bx * RG * N; }
+  __device__ __forceinline__ int n_origin(int, int by) const { return by * CW * 2 * N; }
   template <int BN>
   __device__ __forceinline__ void run(uint32_t tmem, int q, int lane, int ew, int, int, int, int,
                                       float* sm) const {
@@ -304,24 +304,26 @@ struct EpiExchange {
     asm volatile("bar.sync 1, 128;" ::: "memory");
     double* red = reinterpret_cast<double*>(sm + 128 * LD);  // [RG][CW][2]
     const int g0 = blockIdx.x * RG, w0 = blockIdx.y * CW;
+    // FP32 sums per lane (the products come from FP32 accumulators; GB300's
+    // float64 pipe is ~60x slower, so float64 here would dominate the kernel)
     for (int pi = ew; pi < RG * CW; pi += 4) {
       const int g = pi / CW, wl = pi % CW;
-      double er = 0.0, ei = 0.0;
+      float er = 0.f, ei = 0.f;
       if (g0 + g < G && w0 + wl < W) {
         const float* Dg = sm + (g * N) * LD + wl * 2 * N;
         for (int ij = lane; ij < N * N; ij += 32) {
           const int i = ij / N, j = ij % N;
           const float ar = Dg[i * LD + j], ai = Dg[i * LD + N + j];
           const float br = Dg[j * LD + i], bi = Dg[j * LD + N + i];
-          er += (double)ar * br - (double)ai * bi;
-          ei += (double)ar * bi + (double)ai * br;
+          er = fmaf(ar, br, fmaf(-ai, bi, er));
+          ei = fmaf(ar, bi, fmaf(ai, br, ei));
         }
       }
       er = warp_sum(er);
       ei = warp_sum(ei);
       if (lane == 0) {
-        red[2 * pi] = er;
-        red[2 * pi + 1] = ei;
+        red[2 * pi] = (double)er;
+        red[2 * pi + 1] = (double)ei;
       }
     }
     asm volatile("bar.sync 1, 128;" ::: "memory");
@@ -335,6 +337,114 @@ struct EpiExchange {
       double* o = part + ((long)(w0 + t) * nchunk + blockIdx.x) * 2;
       o[0] = sr;
       o[1] = si;
+    }
+  }
+};
+
+// ---- propagation epilogues (Eq. primitive and Sec. 3.4.2 on tcgen05) --------
+// A Taylor term T (M x N complex) is kept as the K-major operand
+//   Tb = [[Tr^T, -Ti^T], [Ti^T, Tr^T]]  (2N rows x 2Mp columns),
+// so that V T = [Vr | Vi] Tb^T: real output columns are rows i of Tb, imaginary
+// ones rows N + i.  These helpers write one element of T into Tb.
+__device__ __forceinline__ void put_term(void* tb, int kind, long wrow, int N, int Mp, int c,
+                                         int i, int p, float v) {
+  const long rr = (wrow + i) * 2L * Mp, ri = (wrow + N + i) * 2L * Mp;
+  if (c == 0) {
+    store_lo(tb, kind, rr + p, v);
+    store_lo(tb, kind, ri + Mp + p, v);
+  } else {
+    store_lo(tb, kind, rr + Mp + p, -v);
+    store_lo(tb, kind, ri + p, v);
+  }
+}
+
+// First half step: rows (w,c,i) of Phi^T, columns p; D = (B_half Phi)^T.
+// acc[(w,c,i)][p] = D (FP32, pitch Mp) and Tb holds the 0th Taylor term.
+struct EpiProp0 {
+  float* acc;
+  void* tb;
+  int lo_kind, N, M, Mp, rows;
+  __device__ __forceinline__ int m_origin(int bx, int) const { return bx * BM; }
+  __device__ __forceinline__ int n_origin(int, int by) const { return by * 256; }
+  template <int BN>
+  __device__ __forceinline__ void run(uint32_t tmem, int q, int lane, int, int m0, int n0, int,
+                                      int, float*) const {
+    const int row = m0 + 32 * q + lane;
+#pragma unroll 1
+    for (int c0 = 0; c0 < BN; c0 += 16) {
+      float v[16];
+      tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c0, v);
+      if (row >= rows) continue;
+      const int w = row / (2 * N), rem = row % (2 * N), c = rem / N, i = rem % N;
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        const int p = n0 + c0 + u;
+        if (p < M) {
+          acc[(long)row * Mp + p] = v[u];
+          put_term(tb, lo_kind, (long)w * 2 * N, N, Mp, c, i, p, v[u]);
+        }
+      }
+    }
+  }
+};
+
+// Taylor term k for walker w = blockIdx.y: rows p of [Vr | Vi] (a 128-row tile),
+// columns n < 2N of Tb_{k-1}; T_k = D / k is added to acc and, unless it is
+// the last term, written as the next operand.
+struct EpiTaylor {
+  float* acc;
+  void* tb_out;
+  int lo_kind, N, M, Mp;
+  float scale;
+  __device__ __forceinline__ int m_origin(int bx, int by) const { return by * M + bx * BM; }
+  __device__ __forceinline__ int n_origin(int, int by) const { return by * 2 * N; }
+  template <int BN>
+  __device__ __forceinline__ void run(uint32_t tmem, int q, int lane, int, int, int, int, int,
+                                      float*) const {
+    const int w = blockIdx.y;
+    const int p = blockIdx.x * BM + 32 * q + lane;
+#pragma unroll 1
+    for (int c0 = 0; c0 < BN; c0 += 16) {
+      float v[16];
+      tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c0, v);
+      if (p >= M) continue;
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        const int n = c0 + u;
+        if (n < 2 * N) {
+          const int c = n / N, i = n % N;
+          const float val = v[u] * scale;
+          acc[((long)w * 2 * N + c * N + i) * Mp + p] += val;
+          if (tb_out) put_term(tb_out, lo_kind, (long)w * 2 * N, N, Mp, c, i, p, val);
+        }
+      }
+    }
+  }
+};
+
+// Last half step: rows (w,c,i) of the series sum, columns p; the product is
+// stored as the new float64 orbitals of live walkers.
+struct EpiPhi {
+  double* phiT;
+  const double* wt;
+  int N, M, rows;
+  __device__ __forceinline__ int m_origin(int bx, int) const { return bx * BM; }
+  __device__ __forceinline__ int n_origin(int, int by) const { return by * 256; }
+  template <int BN>
+  __device__ __forceinline__ void run(uint32_t tmem, int q, int lane, int, int m0, int n0, int,
+                                      int, float*) const {
+    const int row = m0 + 32 * q + lane;
+    const bool ok = row < rows && walker_alive(wt, row / (2 * N));
+#pragma unroll 1
+    for (int c0 = 0; c0 < BN; c0 += 16) {
+      float v[16];
+      tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c0, v);
+      if (!ok) continue;
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        const int p = n0 + c0 + u;
+        if (p < M) phiT[(long)row * M + p] = (double)v[u];
+      }
     }
   }
 };
@@ -411,6 +521,34 @@ int tc_gemm_store(const TcGemm& g, float* C, long ldc, float alpha, cudaStream_t
   }
   tc::EpiStore e{C, ldc, alpha};
   dim3 grid(cdiv(g.m, tc::BM), cdiv(g.n, 256));
+  if (g.tf32) return launch_tc<256, 4, true>(g, e, grid, st);
+  return launch_tc<256, 4, false>(g, e, grid, st);
+}
+
+int tc_prop_first(const TcGemm& g, float* acc, void* tb, int lo_kind, int N, int M, int Mp,
+                  cudaStream_t st) {
+  tc::EpiProp0 e{acc, tb, lo_kind, N, M, Mp, g.m};
+  dim3 grid(cdiv(g.m, tc::BM), cdiv(M, 256));
+  if (g.tf32) return launch_tc<256, 4, true>(g, e, grid, st);
+  return launch_tc<256, 4, false>(g, e, grid, st);
+}
+
+int tc_taylor_term(const TcGemm& g, float* acc, void* tb_out, int lo_kind, int W, int N, int M,
+                   int Mp, float scale, cudaStream_t st) {
+  if (2 * N > 64) {
+    set_error("tc taylor: 2N=%d above the 64-column tile", 2 * N);
+    return AFQMC_EUNSUPPORTED;
+  }
+  tc::EpiTaylor e{acc, tb_out, lo_kind, N, M, Mp, scale};
+  dim3 grid(cdiv(M, tc::BM), W);
+  if (g.tf32) return launch_tc<64, 4, true>(g, e, grid, st);
+  return launch_tc<64, 4, false>(g, e, grid, st);
+}
+
+int tc_prop_last(const TcGemm& g, double* phiT, const double* wt, int N, int M,
+                 cudaStream_t st) {
+  tc::EpiPhi e{phiT, wt, N, M, g.m};
+  dim3 grid(cdiv(g.m, tc::BM), cdiv(M, 256));
   if (g.tf32) return launch_tc<256, 4, true>(g, e, grid, st);
   return launch_tc<256, 4, false>(g, e, grid, st);
 }

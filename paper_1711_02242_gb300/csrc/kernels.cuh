@@ -90,6 +90,19 @@ struct LuArgs {
 };
 int launch_lu_inv(const LuArgs& a, cudaStream_t st);
 
+// Fused overlap: S = V_T^T Phi, Gauss-Jordan S^-1 and log det, Theta = Phi S^-1.
+struct OverlapArgs {
+  int W, M, N;
+  const double* VTt;   // [N][M]
+  const double* phiT;  // [W][2][N][M]
+  double* thetaT;      // [W][2][N][M] (live walkers)
+  double* logdet;      // [W][2] (live walkers)
+  const double* wt;    // alive mask (nullptr: all)
+  void* th_lo = nullptr;
+  int lo_kind = LO_NONE, Mp = 0;
+};
+int launch_overlap(const OverlapArgs& a, cudaStream_t st);
+
 struct ThetaArgs {
   int W, M, N;
   const double* Sinv;  // [W][2][N][N]
@@ -188,5 +201,8 @@ int launch_sumsq(const double* v, double* out, int n, cudaStream_t st);
 int launch_convert_lo(const double* src, long rows, long cols, long lds, void* dst, long ldd,
                       int kind, cudaStream_t st);
 int launch_convert_f32(const double* src, float* dst, long n, cudaStream_t st);
+// [Re V | Im V] rows (pitch 2 Mp) for the tensor-core Taylor terms, from packed Y
+int launch_unpack_v(const float* Y, long ldy, int W, int M, int Mp, double sdt, void* V, int kind,
+                    cudaStream_t st);
 
 }  // namespace afq

@@ -28,8 +28,12 @@ struct Bufs {
   int lo_kind = 0, lo_bytes = 0, Gp = 0, Mp = 0;
   long Pp = 0;
   void *LpT_lo = nullptr, *Lh_lo = nullptr, *x_lo = nullptr, *th_lo = nullptr;
-  float *t32 = nullptr, *Y32 = nullptr, *Bh32 = nullptr, *T0f = nullptr, *T1f = nullptr,
-        *accf = nullptr;
+  float *t32 = nullptr, *Y32 = nullptr;
+  // tensor-core propagation: exp(-dt v0'/2) as BF16/TF32 and TF32 [M][Mp],
+  // V operand [W*M][2Mp], orbitals [W*2N][Mp], series sum [W*2N][Mp] FP32,
+  // two Taylor-term operands [W*2N][2Mp]
+  void *Bh_lo = nullptr, *V_lo = nullptr, *phi_lo = nullptr, *Tb0 = nullptr, *Tb1 = nullptr;
+  float *Bh_tf = nullptr, *acc32 = nullptr;
   int* status = nullptr;  // device status word (tensor-core waits)
 };
 

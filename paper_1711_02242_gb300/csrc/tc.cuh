@@ -22,6 +22,15 @@ int tc_gemm_store(const TcGemm& g, float* C, long ldc, float alpha, cudaStream_t
 
 // Exchange energy contraction (rows (g,i) of Lh, columns (w,c,j) of Theta^T)
 // with the fused sum_ij T_ij T_ji epilogue; part [W][nchunk][2] (float64).
+// Propagation on tcgen05 (mixed path): first half step, Taylor terms, last
+// half step (see the epilogues in gemm_tc.cu for the operand layouts).
+int tc_prop_first(const TcGemm& g, float* acc, void* tb, int lo_kind, int N, int M, int Mp,
+                  cudaStream_t st);
+int tc_taylor_term(const TcGemm& g, float* acc, void* tb_out, int lo_kind, int W, int N, int M,
+                   int Mp, float scale, cudaStream_t st);
+int tc_prop_last(const TcGemm& g, double* phiT, const double* wt, int N, int M,
+                 cudaStream_t st);
+
 void exchange_tile(int N, int* RG, int* CW);
 int tc_exchange(const TcGemm& g, int G, int W, int N, double* part, int nchunk, cudaStream_t st);
 

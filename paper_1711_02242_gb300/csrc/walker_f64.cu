@@ -366,6 +366,170 @@ int launch_theta(const ThetaArgs& a, cudaStream_t st) {
   return AFQMC_OK;
 }
 
+// ------------------------------------------------------- fused overlap ------
+// One block per walker, float64 throughout (Theorem 1.1, Eq. precomputing):
+//   1. S = V_T^T Phi (N x N complex, each entry a length-M dot product);
+//   2. Gauss-Jordan elimination with partial pivoting (largest modulus):
+//      S^-1 and log det S = sum log p_k (+ i pi per row swap);
+//   3. Theta^T[i][p] = sum_j S^-1[j][i] Phi^T[j][p].
+// log <Psi_T|Psi> = 2 log det S (both spins), phase wrapped to (-pi, pi].
+// Every walker is computed; Theta and log det are stored for live walkers.
+__global__ void __launch_bounds__(256) k_overlap(OverlapArgs a) {
+  extern __shared__ double2 ov_sm[];
+  const int w = blockIdx.x;
+  const bool live = !a.wt || walker_alive(a.wt, w);
+  const int N = a.N, M = a.M;
+  double2* A = ov_sm;            // [N][N]
+  double2* Inv = ov_sm + N * N;  // [N][N]
+  __shared__ int piv, swaps, singular;
+  __shared__ double logabs, phase;
+  const double* fr = a.phiT + (long)w * 2 * N * M;
+  const double* fi = fr + (long)N * M;
+  for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x) {
+    const int i = idx / N, j = idx % N;
+    const double* v = a.VTt + (long)i * M;
+    const double* xr = fr + (long)j * M;
+    const double* xi = fi + (long)j * M;
+    double sr = 0.0, si = 0.0;
+    for (int p = 0; p < M; ++p) {
+      sr = fma(v[p], xr[p], sr);
+      si = fma(v[p], xi[p], si);
+    }
+    A[idx] = make_double2(sr, si);
+    Inv[idx] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+  }
+  if (threadIdx.x == 0) {
+    logabs = 0.0;
+    phase = 0.0;
+    swaps = 0;
+    singular = 0;
+  }
+  __syncthreads();
+  for (int k = 0; k < N; ++k) {
+    if (threadIdx.x == 0) {
+      int best = k;
+      double bv = -1.0;
+      for (int r = k; r < N; ++r) {
+        const double v = hypot(A[r * N + k].x, A[r * N + k].y);
+        if (v > bv) {
+          bv = v;
+          best = r;
+        }
+      }
+      piv = best;
+      if (!(bv > 0.0)) singular = 1;
+    }
+    __syncthreads();
+    if (singular) break;
+    if (piv != k) {
+      for (int j = threadIdx.x; j < N; j += blockDim.x) {
+        double2 t = A[k * N + j];
+        A[k * N + j] = A[piv * N + j];
+        A[piv * N + j] = t;
+        t = Inv[k * N + j];
+        Inv[k * N + j] = Inv[piv * N + j];
+        Inv[piv * N + j] = t;
+      }
+      if (threadIdx.x == 0) swaps++;
+    }
+    __syncthreads();
+    const double2 pv = A[k * N + k];
+    const double den = pv.x * pv.x + pv.y * pv.y;
+    const double2 rp = make_double2(pv.x / den, -pv.y / den);
+    if (threadIdx.x == 0) {
+      logabs += 0.5 * log(den);
+      phase += atan2(pv.y, pv.x);
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+      const double2 v = A[k * N + j], u = Inv[k * N + j];
+      A[k * N + j] = make_double2(v.x * rp.x - v.y * rp.y, v.x * rp.y + v.y * rp.x);
+      Inv[k * N + j] = make_double2(u.x * rp.x - u.y * rp.y, u.x * rp.y + u.y * rp.x);
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x) {
+      const int r = idx / N, j = idx % N;
+      if (r == k || j == k) continue;
+      const double2 f = A[r * N + k];
+      const double2 v = A[k * N + j];
+      A[r * N + j].x -= f.x * v.x - f.y * v.y;
+      A[r * N + j].y -= f.x * v.y + f.y * v.x;
+    }
+    for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x) {
+      const int r = idx / N, j = idx % N;
+      if (r == k) continue;
+      const double2 f = A[r * N + k];
+      const double2 v = Inv[k * N + j];
+      Inv[r * N + j].x -= f.x * v.x - f.y * v.y;
+      Inv[r * N + j].y -= f.x * v.y + f.y * v.x;
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < N; r += blockDim.x)
+      if (r != k) A[r * N + k] = make_double2(0.0, 0.0);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && live) {
+    if (singular) {
+      a.logdet[2L * w] = -INFINITY;
+      a.logdet[2L * w + 1] = 0.0;
+    } else {
+      a.logdet[2L * w] = 2.0 * logabs;
+      a.logdet[2L * w + 1] = wrap_pi(2.0 * (phase + 3.141592653589793 * swaps));
+    }
+  }
+  if (singular || !live) return;
+  // Theta^T = S^-T Phi^T: work items (p, block of 8 orbitals i)
+  constexpr int IB = 8;
+  const int nib = (N + IB - 1) / IB;
+  double* tr = a.thetaT + (long)w * 2 * N * M;
+  double* ti = tr + (long)N * M;
+  for (int item = threadIdx.x; item < M * nib; item += blockDim.x) {
+    const int p = item % M, i0 = (item / M) * IB;
+    double ar[IB], ai[IB];
+#pragma unroll
+    for (int u = 0; u < IB; ++u) ar[u] = ai[u] = 0.0;
+    for (int j = 0; j < N; ++j) {
+      const double xr = fr[(long)j * M + p], xi = fi[(long)j * M + p];
+#pragma unroll
+      for (int u = 0; u < IB; ++u) {
+        if (i0 + u < N) {
+          const double2 s = Inv[j * N + i0 + u];
+          ar[u] = fma(xr, s.x, fma(-xi, s.y, ar[u]));
+          ai[u] = fma(xr, s.y, fma(xi, s.x, ai[u]));
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < IB; ++u) {
+      const int i = i0 + u;
+      if (i < N) {
+        tr[(long)i * M + p] = ar[u];
+        ti[(long)i * M + p] = ai[u];
+        if (a.th_lo) {
+          store_lo(a.th_lo, a.lo_kind, ((long)w * 2 * N + i) * a.Mp + p, ar[u]);
+          store_lo(a.th_lo, a.lo_kind, ((long)w * 2 * N + N + i) * a.Mp + p, ai[u]);
+        }
+      }
+    }
+  }
+}
+
+int launch_overlap(const OverlapArgs& a, cudaStream_t st) {
+  const size_t smem = 2ull * a.N * a.N * sizeof(double2);
+  if (smem > 200 * 1024) {
+    set_error("overlap: N=%d too large", a.N);
+    return AFQMC_EUNSUPPORTED;
+  }
+  static bool attr = false;
+  if (!attr) {
+    AFQ_CUDA(cudaFuncSetAttribute(k_overlap, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  200 * 1024));
+    attr = true;
+  }
+  AFQ_LAUNCH(k_overlap, a.W, 256, smem, st, a);
+  return AFQMC_OK;
+}
+
 // ---------------------------------------------------------------- weights --
 // Overlap ratio of the step, including the scalar of B(x - xbar):
 // log R = l' - l - dt (H0' - E_shift) - i sqrt(dt) sum_g x_g c_g.
@@ -895,6 +1059,61 @@ int launch_sumsq(const double* v, double* out, int n, cudaStream_t st) {
 
 // ------------------------------------------------- low-precision copies ----
 namespace afq {
+// Operand of the tensor-core Taylor terms from the packed Y = sum_g x_g L_g
+// (FP32, pitch ldy per walker component): row (w, p) of V holds
+// [Re V[p][0..M), 0.. | Im V[p][0..M), 0..] (pitch 2 Mp) with V = i sqrt(dt) Y,
+// i.e. Re V = -sqrt(dt) Im Y and Im V = sqrt(dt) Re Y.  32x32 tiles of (p, q):
+// tiles above the diagonal read packed rows p, tiles below read rows q and are
+// transposed in shared memory, so both loads and stores are contiguous.
+__global__ void __launch_bounds__(256) k_unpack_v(const float* Y, long ldy, int M, int Mp,
+                                                  float sdt, void* V, int kind) {
+  __shared__ float sr[32][33], si[32][33];
+  const int w = blockIdx.z, p0 = blockIdx.y * 32, q0 = blockIdx.x * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const float* Yr = Y + (long)w * 2 * ldy;
+  const float* Yi = Yr + ldy;
+  if (p0 < q0 + 32) {  // diagonal or upper tile: element (p, q) at packed(min, max)
+    for (int r = ty; r < 32; r += 8) {
+      const int p = p0 + r, q = q0 + tx;
+      float a = 0.f, b = 0.f;
+      if (p < M && q < M) {
+        const long id = (p <= q) ? packed_index(p, q, M) : packed_index(q, p, M);
+        a = Yr[id];
+        b = Yi[id];
+      }
+      sr[r][tx] = a;
+      si[r][tx] = b;
+    }
+  } else {  // lower tile: (p, q) with q < p is stored in packed row q
+    for (int r = ty; r < 32; r += 8) {
+      const int q = q0 + r, p = p0 + tx;
+      float a = 0.f, b = 0.f;
+      if (p < M && q < M) {
+        const long id = packed_index(q, p, M);
+        a = Yr[id];
+        b = Yi[id];
+      }
+      sr[tx][r] = a;
+      si[tx][r] = b;
+    }
+  }
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    const int p = p0 + r, q = q0 + tx;
+    if (p >= M || q >= Mp) continue;
+    const long row = ((long)w * M + p) * 2 * Mp;
+    store_lo(V, kind, row + q, -sdt * si[r][tx]);
+    store_lo(V, kind, row + Mp + q, sdt * sr[r][tx]);
+  }
+}
+
+int launch_unpack_v(const float* Y, long ldy, int W, int M, int Mp, double sdt, void* V, int kind,
+                    cudaStream_t st) {
+  dim3 grid(cdiv(Mp, 32), cdiv(M, 32), W);
+  AFQ_LAUNCH(k_unpack_v, grid, 256, 0, st, Y, ldy, M, Mp, (float)sdt, V, kind);
+  return AFQMC_OK;
+}
+
 __global__ void k_convert_lo(const double* src, long rows, long cols, long lds, void* dst,
                              long ldd, int kind) {
   const long n = rows * ldd;
