@@ -157,10 +157,15 @@ def run_gpu(args, w: workloads.Workload):
     h1, L, H0, C, conv, grad = make_inputs(w)
     p = pkg.default_params(w.M, w.N, w.nchol, w.nwalkers, dt=w.dt, seed=w.seed + 1000 * rank,
                            qr_period=w.qr_period, energy_period=w.energy_period,
-                           taylor_order=w.taylor_order, precision=prec, H0=H0)
+                           taylor_order=w.taylor_order, precision=prec, H0=H0,
+                           use_graph=0 if args.no_graph else 1)
     stream = torch.cuda.Stream(device=dev)
     run = pkg.AfqmcRun(h1, L, C, p, device=dev, stream=stream)
-    K, Wm = args.steps, args.warmup
+    K = args.steps
+    # warm-up: at least one whole graph block (capture + first replay)
+    blk = math.lcm(*[x for x in (w.qr_period, w.pc_period, w.energy_period) if x]) or 1
+    Wm = max(args.warmup, blk)
+    Wm = -(-Wm // blk) * blk
     run.propagate(Wm)
     stream.synchronize()
 
@@ -173,7 +178,6 @@ def run_gpu(args, w: workloads.Workload):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     lib = pkg.lib()
-    lib.afqmc_profile_start(run.s, K)
     launches0 = pkg.afqmc_launch_count()
     barrier()
     torch.cuda.synchronize(dev)
@@ -188,10 +192,26 @@ def run_gpu(args, w: workloads.Workload):
     ms_total = e0.elapsed_time(e1)
     import ctypes
 
+    # the same K steps again, launched one by one with CUDA events around
+    # every phase on the state's stream: phase times and the dominant kernel
     ph_ms = (ctypes.c_double * 10)()
     ph_n = (ctypes.c_int64 * 10)()
     ph_k = (ctypes.c_int64 * 10)()
+    pkg._check(lib.afqmc_profile_start(run.s, K))
+    p0 = torch.cuda.Event(enable_timing=True)
+    p1 = torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    run.propagate(K)
+    p1.record(stream)
     pkg._check(lib.afqmc_profile_stop(run.s, ph_ms, ph_n, ph_k))
+    ms_profiled = p0.elapsed_time(p1)
+    # energy evaluations: afqmc_energy (local energies of every walker, the
+    # estimator, and the 2-double read back)
+    n_e = 5
+    t0 = time.perf_counter()
+    for _ in range(n_e):
+        run.energy()
+    s_energy = (time.perf_counter() - t0) / n_e
     if ws > 1:
         import torch.distributed as dist
 
@@ -220,28 +240,45 @@ def run_gpu(args, w: workloads.Workload):
               for i in range(10)}
     return dict(ms_total=ms_total, phases=phases, launches=launches, info=info, E=E, wsum=wsum,
                 clocks=clk.summary(), e2e_s=t_e2e, trial_converged=conv, trial_grad=grad,
-                h2d_bytes=h1.nbytes + L.nbytes + C.nbytes, world=ws, rank=rank)
+                h2d_bytes=h1.nbytes + L.nbytes + C.nbytes, world=ws, rank=rank, warmup=Wm,
+                ms_profiled=ms_profiled, s_energy=s_energy, graph=not args.no_graph)
 
 
-def cpu_sample(w: workloads.Workload, n_walkers=8, n_steps=2):
-    """Time the oracle as it stands on a bounded sample of the workload:
-    n_walkers walkers of the population for n_steps steps (set-up excluded,
-    as the GPU number excludes afqmc_init)."""
-    from oracle import afqmc
+class OracleSampler:
+    """The oracle as it stands, stepping a bounded sample of the workload's
+    walkers.  At the M=300 scale the sampled walkers die within a step (their
+    weights overflow) and the oracle then skips them, so every timed step
+    starts again from the initial walkers: each timed step is a full step of
+    the sampled walkers (the set-up, like afqmc_init on the GPU, is untimed)."""
 
-    h1, L, H0, C, _, _ = make_inputs(w)
-    p = afqmc.Params(dt=w.dt, seed=w.seed, qr_period=w.qr_period, energy_period=w.energy_period,
-                     taylor_order=w.taylor_order)
-    orc = afqmc.Oracle(h1, L, C, w.nwalkers, p, H0=H0)
-    orc.weight[n_walkers:] = 0.0  # the oracle skips zero-weight walkers
-    t0 = time.perf_counter()
-    for _ in range(n_steps):
-        orc.step()
-    dt = time.perf_counter() - t0
+    def __init__(self, w: workloads.Workload, n_walkers: int):
+        from oracle import afqmc
+
+        h1, L, H0, C, _, _ = make_inputs(w)
+        p = afqmc.Params(dt=w.dt, seed=w.seed, qr_period=w.qr_period,
+                         energy_period=w.energy_period, taylor_order=w.taylor_order)
+        self.orc = afqmc.Oracle(h1, L, C, w.nwalkers, p, H0=H0)
+        self.orc.weight[n_walkers:] = 0.0  # the oracle skips zero-weight walkers
+        self.init = {k: getattr(self.orc, k).copy() for k in ("phi", "weight", "logdet", "theta")}
+        self.n = n_walkers
+
+    def step(self):
+        for k, v in self.init.items():
+            setattr(self.orc, k, v.copy())
+        self.orc.step_count = 0
+        t0 = time.perf_counter()
+        self.orc.step()
+        return time.perf_counter() - t0
+
+
+def cpu_sample(w: workloads.Workload, n_walkers=32, n_steps=3):
+    """Oracle walker-steps/s on n_steps full steps of n_walkers walkers."""
+    s = OracleSampler(w, n_walkers)
+    dt = sum(s.step() for _ in range(n_steps))
     cores = len(os.sched_getaffinity(0))
     return dict(value=n_walkers * n_steps / dt, unit="walker-steps/s", cores=cores, kind="oracle",
-                sample=f"{n_walkers} of {w.nwalkers} walkers x {n_steps} steps of the M=300 "
-                       f"workload (set-up excluded), numpy float64, {cores} host threads",
+                sample=f"{n_steps} full steps of {n_walkers} of the {w.nwalkers} walkers of the "
+                       f"M=300 workload (set-up untimed), numpy float64, {cores} host threads",
                 seconds=dt)
 
 
@@ -249,20 +286,11 @@ def run_reference(args, w):
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
-    from oracle import afqmc
-
-    h1, L, H0, C, _, _ = make_inputs(w)
-    p = afqmc.Params(dt=w.dt, seed=w.seed, qr_period=w.qr_period, energy_period=w.energy_period,
-                     taylor_order=w.taylor_order)
-    orc = afqmc.Oracle(h1, L, C, w.nwalkers, p, H0=H0)
     sample = args.ref_walkers
-    orc.weight[sample:] = 0.0
+    s = OracleSampler(w, sample)
     for _ in range(args.warmup):
-        orc.step()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        orc.step()
-    dt = time.perf_counter() - t0
+        s.step()
+    dt = sum(s.step() for _ in range(args.steps))
     cores = len(os.sched_getaffinity(0))
     val = sample * args.steps / dt
     line = {
@@ -291,7 +319,8 @@ def main():
     ap.add_argument("--config", default="c2", choices=sorted(workloads.CONFIGS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end pass")
-    ap.add_argument("--ref-walkers", type=int, default=4)
+    ap.add_argument("--no-graph", action="store_true", help="launch kernels one by one")
+    ap.add_argument("--ref-walkers", type=int, default=16)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -325,7 +354,7 @@ def main():
     roof["launch_ms"] = v_ms
     line = {
         "metric": "walker-steps/s at M=300", "value": value, "unit": "walker-steps/s",
-        "n_gpus": N, "steps": K, "warmup": args.warmup, "ms_per_step": ms_step,
+        "n_gpus": N, "steps": K, "warmup": r["warmup"], "ms_per_step": ms_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp64": "f64", "tf32": "tf32/f32/f64", "bf16": "bf16/f32/f64"}[args.precision],
         "data": "synthetic",
@@ -336,6 +365,11 @@ def main():
                    "trial": f"RHF (25 iterations, converged={r['trial_converged']}, "
                             f"|FD-DF|={r['trial_grad']:.2e})"},
         "roofline": roof,
+        "launch_mode": "CUDA graph per block of steps" if r["graph"] else "kernel by kernel",
+        "energy_evals_per_s": w.nwalkers / r["s_energy"],
+        "profiled_pass": {"ms_per_step": r["ms_profiled"] / K,
+                          "note": "same K steps launched kernel by kernel with CUDA events "
+                                  "around each phase; source of phases and roofline"},
         "phases_ms_per_step": {k: round(v["ms"] / K, 4) for k, v in r["phases"].items()},
         "gpu_launches": r["launches"],
         "clocks": r["clocks"],

@@ -98,12 +98,15 @@ typedef struct afqmc_params {
   double fb_cap;         /* force-bias magnitude cap v_max; <= 0: off          */
   double wmax;           /* weight cap; NaN -> max(100, nwalkers / 10)         */
   int32_t max_records;   /* capacity of the device energy log (>= 1)           */
-  int32_t reserved;      /* must be 0                                          */
+  int32_t use_graph;     /* 1: afqmc_propagate captures one block of steps      */
+                         /* (the least common multiple of the non-zero periods) */
+                         /* as a CUDA graph and replays it; 0: launches kernels */
+                         /* one by one.  Results are identical either way.     */
 } afqmc_params;
 
 /* Fill *p with the defaults: dt 0.005, e_shift NaN, H0 0, seed 1,
  * taylor_order 6, qr_period 5, pc_period 0, energy_period 1, FP64,
- * phaseless, ecap_C 2, fb_cap 1, wmax NaN, max_records 4096.  The sizes
+ * phaseless, ecap_C 2, fb_cap 1, wmax NaN, max_records 4096, use_graph 0.  The sizes
  * (M, N, nchol, nwalkers) are set to 0 and must be filled in. */
 AFQMC_API void afqmc_default_params(afqmc_params* p);
 

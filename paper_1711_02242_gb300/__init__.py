@@ -42,7 +42,7 @@ class Params(ctypes.Structure):
                 ("energy_period", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("mode", ctypes.c_int32), ("ecap_C", ctypes.c_double),
                 ("fb_cap", ctypes.c_double), ("wmax", ctypes.c_double),
-                ("max_records", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("max_records", ctypes.c_int32), ("use_graph", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):

@@ -146,8 +146,8 @@ static int check_params(const afqmc_params* p) {
     return AFQMC_EINVAL;
   }
   if (p->taylor_order < 1 || p->qr_period < 0 || p->pc_period < 0 || p->energy_period < 0 ||
-      p->max_records < 1 || p->reserved != 0) {
-    set_error("bad taylor_order / periods / max_records / reserved");
+      p->max_records < 1 || (p->use_graph != 0 && p->use_graph != 1)) {
+    set_error("bad taylor_order / periods / max_records / use_graph");
     return AFQMC_EINVAL;
   }
   if (p->mode != AFQMC_PHASELESS && p->mode != AFQMC_FREE) {
@@ -634,6 +634,30 @@ static int setup_device(afqmc_state* s, const double* h1, const double* L, const
     AFQ_CUDA(cudaMemsetAsync(b.acc32, 0, sizeof(float) * (size_t)W * 2 * N * b.Mp, st));
     AFQ_CUDA(cudaMemsetAsync(b.Tb0, 0, (size_t)W * 2 * N * 2 * b.Mp * b.lo_bytes, st));
     AFQ_CUDA(cudaMemsetAsync(b.Tb1, 0, (size_t)W * 2 * N * 2 * b.Mp * b.lo_bytes, st));
+    // autotune the tile width of the two plain contractions for this shape
+    TcGemm gv;
+    gv.m = 2 * W;
+    gv.n = b.P;
+    gv.k = G;
+    gv.A = b.x_lo;
+    gv.lda = b.Gp;
+    gv.B = b.LpT_lo;
+    gv.ldb = b.Gp;
+    gv.tf32 = b.lo_kind == LO_TF32;
+    gv.err = b.status;
+    AFQ_TRY(tc_tune_store(gv, b.Y32, b.Pp, 1.0f, st, &s->bn_v));
+    TcGemm gf;
+    gf.m = 2 * W;
+    gf.n = G;
+    gf.k = N * b.Mp;
+    gf.A = b.th_lo;
+    gf.lda = (long)N * b.Mp;
+    gf.B = b.Lh_lo;
+    gf.ldb = (long)N * b.Mp;
+    gf.tf32 = b.lo_kind == LO_TF32;
+    gf.err = b.status;
+    AFQ_TRY(tc_tune_store(gf, b.t32, G, 2.0f, st, &s->bn_fb));
+    s->t_fresh = false;
     AFQ_CUDA(cudaStreamSynchronize(st));
   }
   s->e_shift = std::isnan(p.e_shift) ? s->E_T : p.e_shift;
@@ -730,6 +754,21 @@ int afqmc_init(const afqmc_params* p, const double* h1, const double* L, const d
     delete s;
     return r;
   }
+  // graph block: least common multiple of the non-zero periods (at most 64 steps)
+  {
+    long blk = 1;
+    for (int per : {p->qr_period, p->pc_period, p->energy_period}) {
+      if (per <= 0) continue;
+      long a = blk, bb = per;
+      while (bb) {
+        const long t = a % bb;
+        a = bb;
+        bb = t;
+      }
+      blk = blk / a * per;
+    }
+    s->graph_block = blk <= 64 ? (int)blk : 0;
+  }
   s->valid = true;
   *out = s;
   return AFQMC_OK;
@@ -749,7 +788,50 @@ int afqmc_propagate(afqmc_state* s, int32_t nsteps) {
     set_error("nsteps < 0");
     return AFQMC_EINVAL;
   }
-  for (int i = 0; i < nsteps; ++i) AFQ_TRY(step_once(s));
+  const int blk = s->graph_block;
+  while (nsteps > 0) {
+    // whole blocks that start on a block boundary replay the captured graph;
+    // the rest (and every step while profiling) launches kernels one by one
+    if (s->p.use_graph && blk > 0 && s->h_step % blk == 0 && nsteps >= blk && !s->prof.on) {
+      s->t_fresh = false;  // the block recomputes the force-bias traces itself
+      if (!s->graph) {
+        const int64_t l0 = g_launches;
+        const int64_t h0 = s->h_step;
+        AFQ_CUDA(cudaStreamBeginCapture(s->st, cudaStreamCaptureModeThreadLocal));
+        int r = AFQMC_OK;
+        for (int i = 0; i < blk && r == AFQMC_OK; ++i) r = step_once(s);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(s->st, &g);
+        s->h_step = h0;  // nothing ran yet: the launch below takes the steps
+        if (r != AFQMC_OK) {
+          if (g) cudaGraphDestroy(g);
+          return r;
+        }
+        if (e != cudaSuccess) {
+          set_error("graph capture failed: %s", cudaGetErrorString(e));
+          return AFQMC_ECUDA;
+        }
+        e = cudaGraphInstantiate(&s->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+          s->graph = nullptr;
+          set_error("graph instantiation failed: %s", cudaGetErrorString(e));
+          return AFQMC_ECUDA;
+        }
+        s->graph_kernels = g_launches - l0;
+        g_launches = l0;
+      }
+      AFQ_CUDA(cudaGraphLaunch(s->graph, s->st));
+      g_launches += s->graph_kernels;
+      s->h_step += blk;
+      // the block ends with an energy evaluation iff the energy period divides blk
+      s->t_fresh = s->p.energy_period > 0 && blk % s->p.energy_period == 0;
+      nsteps -= blk;
+    } else {
+      AFQ_TRY(step_once(s));
+      --nsteps;
+    }
+  }
   return AFQMC_OK;
 }
 
@@ -963,6 +1045,8 @@ int afqmc_load(afqmc_state* s, const void* buf, size_t bytes) {
 int afqmc_destroy(afqmc_state* s) {
   if (!s) return AFQMC_OK;
   s->valid = false;
+  if (s->graph) cudaGraphExecDestroy(s->graph);
+  for (cudaEvent_t e : s->prof.ev) cudaEventDestroy(e);
   delete s;
   return AFQMC_OK;
 }

@@ -17,6 +17,9 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <map>
+#include <mutex>
+
 #include "kernels.cuh"
 #include "tc.cuh"
 
@@ -250,8 +253,9 @@ struct EpiStore {
   float* C;
   long ldc;
   float alpha;
+  int bn;  // tile width (the kernel's BN)
   __device__ __forceinline__ int m_origin(int bx, int) const { return bx * BM; }
-  __device__ __forceinline__ int n_origin(int, int by) const { return by * 256; }
+  __device__ __forceinline__ int n_origin(int, int by) const { return by * bn; }
   template <int BN>
   __device__ __forceinline__ void run(uint32_t tmem, int q, int lane, int, int m0, int n0, int M,
                                       int N, float*) const {
@@ -513,16 +517,86 @@ static int launch_tc(const TcGemm& g, const Epi& epi, dim3 grid, cudaStream_t st
   return AFQMC_OK;
 }
 
+// ---- plain-store contraction with an autotuned tile width --------------------
+// Candidates: BN = 256 (4 stages, one CTA per SM), 128 (3 stages) and 64
+// (4 stages), the last two small enough for two CTAs per SM.  tc_tune_store()
+// times each once on the caller's buffers and remembers the fastest for the
+// shape; tc_gemm_store() uses the remembered choice (256 when untuned).
+namespace {
+struct ShapeKey {
+  int m, n, k;
+  bool tf32;
+  bool operator<(const ShapeKey& o) const {
+    if (m != o.m) return m < o.m;
+    if (n != o.n) return n < o.n;
+    if (k != o.k) return k < o.k;
+    return tf32 < o.tf32;
+  }
+};
+std::mutex g_tune_mu;
+std::map<ShapeKey, int> g_tuned_bn;
+}  // namespace
+
+static int launch_store_bn(const TcGemm& g, float* C, long ldc, float alpha, int bn,
+                           cudaStream_t st) {
+  tc::EpiStore e{C, ldc, alpha, bn};
+  dim3 grid(cdiv(g.m, tc::BM), cdiv(g.n, bn));
+  if (bn == 64) {
+    if (g.tf32) return launch_tc<64, 4, true>(g, e, grid, st);
+    return launch_tc<64, 4, false>(g, e, grid, st);
+  }
+  if (bn == 128) {
+    if (g.tf32) return launch_tc<128, 3, true>(g, e, grid, st);
+    return launch_tc<128, 3, false>(g, e, grid, st);
+  }
+  if (g.tf32) return launch_tc<256, 4, true>(g, e, grid, st);
+  return launch_tc<256, 4, false>(g, e, grid, st);
+}
+
 int tc_gemm_store(const TcGemm& g, float* C, long ldc, float alpha, cudaStream_t st) {
   if (g.m <= 0 || g.n <= 0) return AFQMC_OK;
   if (g.k <= 0) {
     set_error("tc gemm: k must be positive");
     return AFQMC_EINVAL;
   }
-  tc::EpiStore e{C, ldc, alpha};
-  dim3 grid(cdiv(g.m, tc::BM), cdiv(g.n, 256));
-  if (g.tf32) return launch_tc<256, 4, true>(g, e, grid, st);
-  return launch_tc<256, 4, false>(g, e, grid, st);
+  int bn = 256;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tuned_bn.find(ShapeKey{g.m, g.n, g.k, g.tf32});
+    if (it != g_tuned_bn.end()) bn = it->second;
+  }
+  return launch_store_bn(g, C, ldc, alpha, bn, st);
+}
+
+int tc_tune_store(const TcGemm& g, float* C, long ldc, float alpha, cudaStream_t st, int* chosen) {
+  if (g.m <= 0 || g.n <= 0 || g.k <= 0) return AFQMC_OK;
+  cudaEvent_t e0, e1;
+  AFQ_CUDA(cudaEventCreate(&e0));
+  AFQ_CUDA(cudaEventCreate(&e1));
+  int best = 256;
+  float best_ms = 1e30f;
+  for (int bn : {256, 128, 64}) {
+    AFQ_TRY(launch_store_bn(g, C, ldc, alpha, bn, st));  // warm-up (and first-use set-up)
+    AFQ_CUDA(cudaEventRecord(e0, st));
+    AFQ_TRY(launch_store_bn(g, C, ldc, alpha, bn, st));
+    AFQ_TRY(launch_store_bn(g, C, ldc, alpha, bn, st));
+    AFQ_CUDA(cudaEventRecord(e1, st));
+    AFQ_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    AFQ_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = bn;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuned_bn[ShapeKey{g.m, g.n, g.k, g.tf32}] = best;
+  }
+  if (chosen) *chosen = best;
+  return AFQMC_OK;
 }
 
 int tc_prop_first(const TcGemm& g, float* acc, void* tb, int lo_kind, int N, int M, int Mp,

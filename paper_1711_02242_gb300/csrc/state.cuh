@@ -65,6 +65,12 @@ struct afqmc_state {
   bool t_fresh = false;
   bool valid = false;
   afq::Profiler prof;
+  // CUDA graph of one block of steps (afqmc_params.use_graph)
+  cudaGraphExec_t graph = nullptr;
+  int graph_block = 0;
+  int64_t graph_kernels = 0;
+  // tile widths the autotuner chose for the V and force-bias contractions
+  int bn_v = 0, bn_fb = 0;
 };
 
 namespace afq {

@@ -19,6 +19,9 @@ struct TcGemm {
 };
 
 int tc_gemm_store(const TcGemm& g, float* C, long ldc, float alpha, cudaStream_t st);
+// Time the tile-width candidates for this shape on the given buffers (not
+// under stream capture) and remember the fastest for tc_gemm_store().
+int tc_tune_store(const TcGemm& g, float* C, long ldc, float alpha, cudaStream_t st, int* chosen);
 
 // Exchange energy contraction (rows (g,i) of Lh, columns (w,c,j) of Theta^T)
 // with the fused sum_ij T_ij T_ji epilogue; part [W][nchunk][2] (float64).

@@ -1,0 +1,68 @@
+"""A single contraction of the M=300 step, for kernel profiling.
+
+    python -m paper_1711_02242_gb300.profile_case [--case v|fb] [--dtype bf16|tf32] [--reps 3]
+
+Case "v": V = sum_g x_g L_g as afqmc_contract with the M=300 shapes
+(A = 1024 x 1800 fields, B = 45150 x 1800 packed Cholesky vectors, C FP32):
+about 350 MB on the device, B alone (162 MB BF16) larger than the 129 MB L2.
+Case "fb": the force-bias contraction (A = 1024 x 7600, B = 1800 x 7600).
+Random operands; prints the mean time per launch from CUDA events.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+
+import paper_1711_02242_gb300 as pkg
+
+
+def main():
+    import torch
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--case", default="v", choices=["v", "fb"])
+    ap.add_argument("--dtype", default="bf16", choices=["bf16", "tf32"])
+    ap.add_argument("--reps", type=int, default=3)
+    a = ap.parse_args()
+    from paper_1711_02242_gb300 import build as b
+
+    b.build()
+    if a.case == "v":
+        m, n, k, pitch = 1024, 45150, 1800, 1800
+    else:
+        m, n, k, pitch = 1024, 1800, 25 * 304, 25 * 304
+    dt = torch.bfloat16 if a.dtype == "bf16" else torch.float32
+    g = torch.Generator(device="cuda").manual_seed(0)
+    A = torch.randn((m, pitch), generator=g, device="cuda").to(dt)
+    B = torch.randn((n, pitch), generator=g, device="cuda").to(dt)
+    ldc = (n + 3) // 4 * 4
+    C = torch.empty((m, ldc), dtype=torch.float32, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+    lib = pkg.lib()
+
+    def call():
+        pkg._check(lib.afqmc_contract(0 if a.dtype == "bf16" else 1, m, n, k,
+                                      ctypes.c_void_p(A.data_ptr()), pitch,
+                                      ctypes.c_void_p(B.data_ptr()), pitch, ctypes.c_float(1.0),
+                                      ctypes.c_void_p(C.data_ptr()), ldc,
+                                      ctypes.c_void_p(st.data_ptr()),
+                                      ctypes.c_void_p(stream.cuda_stream)))
+
+    call()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(a.reps):
+        call()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / a.reps
+    flops = 2.0 * m * n * k
+    print(f"case {a.case} {a.dtype}: m={m} n={n} k={k}: {ms:.4f} ms/launch, "
+          f"{flops / ms / 1e9:.1f} TFLOP/s, status {int(st.item())}")
+    assert int(st.item()) == 0
+
+
+if __name__ == "__main__":
+    main()
