@@ -309,8 +309,169 @@ def run_reference(args, w):
     return 0
 
 
+def _inputs_parallel(ws, trial_iters=0):
+    """Hamiltonians (and trials: core orbitals, or a few RHF iterations) for
+    many workloads, generated on host threads."""
+    import concurrent.futures as cf
+
+    from paper_1711_02242_gb300.rhf import rhf_trial
+
+    def one(w):
+        h1, L, H0 = w.hamiltonian()
+        if trial_iters:
+            C, _, _ = rhf_trial(h1, L, w.N, max_iter=trial_iters)
+        else:
+            C = np.linalg.eigh(h1)[1][:, :w.N]
+        return h1, L, H0, C
+
+    with cf.ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 4)) as ex:
+        return list(ex.map(one, ws))
+
+
+def run_batched(args):
+    """16 uneven systems (M in {40..200}, N = M/8, nchol = 5M, walkers in
+    {64..1024}) advanced by one CUDA graph launch per block of steps."""
+    import torch
+
+    import paper_1711_02242_gb300 as pkg
+    from paper_1711_02242_gb300 import build as b
+
+    b.build()
+    prec = {"fp64": 0, "tf32": 1, "bf16": 2}[args.precision]
+    ws_ = workloads.batched_systems()
+    inputs = _inputs_parallel(ws_, trial_iters=10)
+    runs = []
+    for w, (h1, L, H0, C) in zip(ws_, inputs):
+        p = pkg.default_params(w.M, w.N, w.nchol, w.nwalkers, dt=w.dt, seed=w.seed, H0=H0,
+                               qr_period=w.qr_period, energy_period=w.energy_period,
+                               precision=prec, use_graph=1)
+        runs.append(pkg.AfqmcRun(h1, L, C, p, stream=torch.cuda.Stream()))
+    g = pkg.AfqmcGroup(runs)
+    blk = 10
+    K = -(-args.steps // blk) * blk
+    g.propagate(blk)  # capture + first replay
+    g.synchronize()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = pkg.afqmc_launch_count()
+    with ClockSampler(0) as clk:
+        e0.record(g.stream)
+        g.propagate(K)
+        e1.record(g.stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    launches = pkg.afqmc_launch_count() - l0
+    total_ws = sum(w.nwalkers for w in ws_)
+    # the same systems one after the other, each with its own graph replay
+    torch.cuda.synchronize()
+    s0 = torch.cuda.Event(enable_timing=True)
+    s1 = torch.cuda.Event(enable_timing=True)
+    st = torch.cuda.current_stream()
+    s0.record(st)
+    for r in runs:
+        r.stream.wait_stream(st)
+        r.propagate(K)
+        st.wait_stream(r.stream)
+    s1.record(st)
+    torch.cuda.synchronize()
+    ms_seq = s0.elapsed_time(s1)
+    line = {
+        "metric": "walker-steps/s, 16 uneven systems in one graph launch per block",
+        "value": total_ws * K / (ms * 1e-3), "unit": "walker-steps/s", "n_gpus": 1, "steps": K,
+        "warmup": blk, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": {"fp64": "f64", "tf32": "tf32/f32/f64",
+                                       "bf16": "bf16/f32/f64"}[args.precision],
+        "data": "synthetic",
+        "config": {"workload": "16 systems, M in {40..200}, N=M/8, nchol=5M, walkers in {64..1024}",
+                   "systems": [[w.M, w.N, w.nchol, w.nwalkers] for w in ws_],
+                   "trial": "RHF, 10 DIIS iterations"},
+        "one_by_one": {"value": total_ws * K / (ms_seq * 1e-3), "ms_per_step": ms_seq / K,
+                       "note": "same systems propagated one after another (own graphs)"},
+        "gpu_launches": launches, "clocks": clk.summary(),
+        "e2e": None,
+    }
+    print(json.dumps(line))
+    g.close()
+    return 0
+
+
+def run_serve(args):
+    """A Poisson stream of AFQMC run requests (M uniform in [20, 300],
+    N uniform in [2, M/8], nchol = 5M, 128-2048 walkers) served with
+    continuous batching; p50/p99 run latency and aggregate throughput."""
+    import torch
+
+    import paper_1711_02242_gb300 as pkg
+    from paper_1711_02242_gb300 import build as b
+    from paper_1711_02242_gb300.serve import Request, Server, latency_stats
+
+    b.build()
+    prec = {"fp64": 0, "tf32": 1, "bf16": 2}[args.precision]
+    stream = workloads.request_stream(count=args.requests, rate=args.rate, blocks=args.blocks,
+                                      steps_per_block=args.steps_per_block)
+    inputs = _inputs_parallel([w for _, w in stream])
+    reqs = [Request(rid=i, arrival=t, h1=h1, L=L, trial=C, nwalkers=w.nwalkers, nsteps=w.nsteps,
+                    seed=w.seed, energy_period=w.energy_period)
+            for i, ((t, w), (h1, L, H0, C)) in enumerate(zip(stream, inputs))]
+    free, _ = torch.cuda.mem_get_info()
+    pool = int(min(0.6 * free, 120e9))
+    srv = Server(pool, precision=prec, chunk_steps=args.steps_per_block)
+    t0 = time.perf_counter()
+    with ClockSampler(0) as clk:
+        done = srv.run(reqs, realtime=True)
+    makespan = time.perf_counter() - t0
+    ws_total = sum(r.nwalkers * r.nsteps for r in done)
+    lat = latency_stats(done)
+    # FP64 one at a time: the first requests timed alone, the rest extrapolated
+    # by algorithmic FLOPs (the FP64 path is bound by the FP64 pipe)
+    n_fp = min(3, len(reqs))
+    fl = lambda r: flops_per_walker_step(workloads.Workload(  # noqa: E731
+        "r", M=r.trial.shape[0], N=r.trial.shape[1], nchol=r.L.shape[0], nwalkers=r.nwalkers,
+        qr_period=5, energy_period=r.energy_period))["total"] * r.nwalkers * r.nsteps
+    srv64 = Server(pool, precision=0, chunk_steps=args.steps_per_block)
+    t1 = time.perf_counter()
+    for r in reqs[:n_fp]:
+        srv64.run([dataclasses_replace(r)], realtime=False)
+    t_fp = time.perf_counter() - t1
+    fp_rate = sum(fl(r) for r in reqs[:n_fp]) / t_fp
+    t_fp_all = sum(fl(r) for r in reqs) / fp_rate
+    line = {
+        "metric": "p50/p99 run latency and walker-steps/s, served request stream",
+        "value": ws_total / makespan, "unit": "walker-steps/s", "n_gpus": 1,
+        "steps": int(np.mean([r.nsteps for r in reqs])), "warmup": 0,
+        "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp64": "f64", "tf32": "tf32/f32/f64", "bf16": "bf16/f32/f64"}[args.precision],
+        "data": "synthetic",
+        "config": {"workload": f"{len(reqs)} requests, Poisson {args.rate}/s, M in [20,300], "
+                               f"N in [2,M/8], nchol=5M, walkers in [128,2048], "
+                               f"{args.blocks} blocks x {args.steps_per_block} steps",
+                   "pool_GB": pool / 1e9, "trial": "core-Hamiltonian orbitals"},
+        "latency": lat, "makespan_s": makespan,
+        "offered_walker_steps_per_s": ws_total / max(1e-9, max(r.arrival for r in reqs)),
+        "fp64_one_at_a_time": {"measured_requests": n_fp, "seconds_measured": t_fp,
+                               "estimated_seconds_all": t_fp_all,
+                               "walker_steps_per_s": ws_total / t_fp_all},
+        "clocks": clk.summary(), "gpu_launches": None, "e2e": None,
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def dataclasses_replace(r):
+    import dataclasses
+
+    return dataclasses.replace(r, arrival=0.0, energies=None)
+
+
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", default="c2", choices=["c2", "batched", "serve"],
+                    help="c2: the M=300 walker-steps/s line; batched / serve: the grouped and "
+                         "served forms (their own JSON lines)")
+    ap.add_argument("--requests", type=int, default=40)
+    ap.add_argument("--rate", type=float, default=20.0)
+    ap.add_argument("--blocks", type=int, default=4)
+    ap.add_argument("--steps-per-block", type=int, default=25)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
@@ -324,6 +485,10 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.workload == "batched":
+        return run_batched(args)
+    if args.workload == "serve":
+        return run_serve(args)
     w = workloads.config(args.config)
     if args.impl == "reference":
         return run_reference(args, w)

@@ -102,6 +102,8 @@ typedef struct afqmc_params {
                          /* (the least common multiple of the non-zero periods) */
                          /* as a CUDA graph and replays it; 0: launches kernels */
                          /* one by one.  Results are identical either way.     */
+                         /* 1 needs a stream created by the caller (the legacy */
+                         /* default stream cannot be captured): else EINVAL.   */
 } afqmc_params;
 
 /* Fill *p with the defaults: dt 0.005, e_shift NaN, H0 0, seed 1,
@@ -210,6 +212,26 @@ AFQMC_API int afqmc_get_info(afqmc_state* s, afqmc_info* info);
  */
 AFQMC_API int afqmc_save(afqmc_state* s, void* buf, size_t* bytes);
 AFQMC_API int afqmc_load(afqmc_state* s, const void* buf, size_t bytes);
+
+/*
+ * Groups: many independent runs (different molecules and sizes, each its own
+ * state, workspace and stream) advanced together.  Walkers of different
+ * states never interact (Sec. 3.5: walkers are independent), so the group's
+ * block of steps - one graph block of every state, the least common multiple
+ * of its periods - is captured once as ONE CUDA graph whose branches are the
+ * states' streams (fork/join on `stream`), and afqmc_group_propagate replays
+ * it with one launch per block.  All states need use_graph = 1 and the same
+ * graph block length, must be on the current device, and must stay valid
+ * while the group exists.  Each state's results are bit-identical to
+ * stepping it alone.
+ */
+typedef struct afqmc_group afqmc_group; /* opaque */
+AFQMC_API int afqmc_group_create(afqmc_state* const* states, int32_t n, void* stream,
+                                 afqmc_group** out);
+/* nsteps must be a multiple of the block length and every state must sit on
+ * a block boundary.  Asynchronous on `stream` (which joins all branches). */
+AFQMC_API int afqmc_group_propagate(afqmc_group* g, int32_t nsteps);
+AFQMC_API int afqmc_group_destroy(afqmc_group* g);
 
 /* Release the host side of a state (the workspace stays the caller's). */
 AFQMC_API int afqmc_destroy(afqmc_state* s);

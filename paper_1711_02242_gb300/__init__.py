@@ -30,7 +30,8 @@ EXPORTED = ["afqmc_default_params", "afqmc_workspace_size", "afqmc_init", "afqmc
             "afqmc_get_energy_log", "afqmc_get_info", "afqmc_save", "afqmc_load",
             "afqmc_destroy", "afqmc_last_error", "afqmc_launch_count",
             "afqmc_philox4x32_10", "afqmc_gaussian_fields", "afqmc_contract",
-            "afqmc_profile_start", "afqmc_profile_stop", "afqmc_local_energies_noalloc"]
+            "afqmc_profile_start", "afqmc_profile_stop", "afqmc_local_energies_noalloc",
+            "afqmc_group_create", "afqmc_group_propagate", "afqmc_group_destroy"]
 
 
 class Params(ctypes.Structure):
@@ -97,6 +98,9 @@ def lib():
         "afqmc_profile_stop": (ctypes.c_int, [vp, vp, vp, vp]),
         "afqmc_local_energies_noalloc": (ctypes.c_int, [ctypes.c_int32] * 4 + [vp] * 3 +
                                          [ctypes.c_double, vp, vp]),
+        "afqmc_group_create": (ctypes.c_int, [P(vp), ctypes.c_int32, vp, P(vp)]),
+        "afqmc_group_propagate": (ctypes.c_int, [vp, ctypes.c_int32]),
+        "afqmc_group_destroy": (ctypes.c_int, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -175,7 +179,11 @@ class AfqmcRun:
         self.ws = workspace
         base = workspace.data_ptr()
         off = (-base) % 256
-        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        if stream is None:
+            # graph capture needs a created stream (the default stream cannot be captured)
+            stream = (torch.cuda.Stream(device=self.device) if params.use_graph
+                      else torch.cuda.current_stream(self.device))
+        self.stream = stream
         h1 = np.ascontiguousarray(h1, np.float64)
         L = np.ascontiguousarray(L, np.float64)
         trial = np.ascontiguousarray(trial, np.float64)
@@ -247,6 +255,42 @@ class AfqmcRun:
         if getattr(self, "s", None):
             lib().afqmc_destroy(self.s)
             self.s = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class AfqmcGroup:
+    """Independent runs advanced together by one CUDA graph launch per block
+    of steps (afqmc_group_*).  Every run needs use_graph=1, its own stream and
+    the same graph block length."""
+
+    def __init__(self, runs, stream=None):
+        import torch
+
+        self.runs = list(runs)
+        dev = self.runs[0].device
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=dev)
+        arr = (ctypes.c_void_p * len(self.runs))(*[r.s.value for r in self.runs])
+        g = ctypes.c_void_p()
+        with torch.cuda.device(dev):
+            _check(lib().afqmc_group_create(arr, len(self.runs),
+                                            ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(g)))
+        self.g = g
+
+    def propagate(self, nsteps: int):
+        _check(lib().afqmc_group_propagate(self.g, int(nsteps)))
+
+    def synchronize(self):
+        self.stream.synchronize()
+
+    def close(self):
+        if getattr(self, "g", None):
+            lib().afqmc_group_destroy(self.g)
+            self.g = None
 
     def __del__(self):
         try:

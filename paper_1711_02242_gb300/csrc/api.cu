@@ -471,6 +471,12 @@ static int step_once(afqmc_state* s) {
   return AFQMC_OK;
 }
 
+// One graph block of steps launched kernel by kernel (captured by groups).
+int step_block(afqmc_state* s) {
+  for (int i = 0; i < s->graph_block; ++i) AFQ_TRY(step_once(s));
+  return AFQMC_OK;
+}
+
 // B_half = exp(X), X = -dt v0'/2, by scaling and squaring of a degree-18
 // Taylor polynomial evaluated by Horner's rule (all float64 GEMMs).
 static int expm_device(afqmc_state* s) {
@@ -727,6 +733,11 @@ int afqmc_init(const afqmc_params* p, const double* h1, const double* L, const d
   }
   if (reinterpret_cast<uintptr_t>(d_workspace) % 256) {
     set_error("workspace must be 256-byte aligned");
+    return AFQMC_EINVAL;
+  }
+  if (p->use_graph && (stream == nullptr || stream == (void*)cudaStreamLegacy ||
+                       stream == (void*)cudaStreamPerThread)) {
+    set_error("use_graph needs a stream created by the caller (default streams cannot be captured)");
     return AFQMC_EINVAL;
   }
   const size_t need = plan(*p, nullptr, nullptr);
