@@ -238,10 +238,14 @@ def run_gpu(args, w: workloads.Workload):
 
     phases = {PHASES[i]: {"ms": ph_ms[i], "count": int(ph_n[i]), "kernels": int(ph_k[i])}
               for i in range(10)}
+    prec_rep = None
+    if prec != 0 and rank == 0 and not args.no_precision_report:
+        prec_rep = precision_report(w, prec, h1, L, C, H0)
     return dict(ms_total=ms_total, phases=phases, launches=launches, info=info, E=E, wsum=wsum,
                 clocks=clk.summary(), e2e_s=t_e2e, trial_converged=conv, trial_grad=grad,
                 h2d_bytes=h1.nbytes + L.nbytes + C.nbytes, world=ws, rank=rank, warmup=Wm,
-                ms_profiled=ms_profiled, s_energy=s_energy, graph=not args.no_graph)
+                ms_profiled=ms_profiled, s_energy=s_energy, graph=not args.no_graph,
+                precision_report=prec_rep)
 
 
 class OracleSampler:
@@ -269,6 +273,46 @@ class OracleSampler:
         t0 = time.perf_counter()
         self.orc.step()
         return time.perf_counter() - t0
+
+
+def precision_report(w: workloads.Workload, prec: int, h1, L, C, H0, nwalk=32):
+    """Mixed path against the FP64 path on identical inputs: trial energy,
+    local energies of identical perturbed walkers (Eqs. localenergy2/3), and
+    the orbitals after one step on identical Philox fields."""
+    import torch
+
+    import paper_1711_02242_gb300 as pkg
+
+    runs = {}
+    for pr in (0, prec):
+        p = pkg.default_params(w.M, w.N, w.nchol, nwalk, dt=w.dt, seed=w.seed, H0=H0,
+                               qr_period=w.qr_period, energy_period=0, precision=pr)
+        runs[pr] = pkg.AfqmcRun(h1, L, C, p)
+    e_t = {pr: r.info().E_T for pr, r in runs.items()}
+    rng = np.random.default_rng(11)
+    phi = C[None] + 0.05 * (rng.standard_normal((nwalk,) + C.shape)
+                            + 1j * rng.standard_normal((nwalk,) + C.shape))
+    for r in runs.values():
+        r.set_walkers(phi, np.ones(nwalk))
+    el = {pr: r.local_energies() for pr, r in runs.items()}
+    d = np.abs(el[prec] - el[0])
+    for r in runs.values():
+        r.set_walkers(np.broadcast_to(C, (nwalk,) + C.shape), np.ones(nwalk))
+        r.propagate(1)
+    p64 = runs[0].get_walkers()[0]
+    pmx = runs[prec].get_walkers()[0]
+    rel = float(np.linalg.norm(pmx - p64) / np.linalg.norm(p64))
+    out = {"trial_energy_Ha": e_t[0], "dE_trial_mHa": 1e3 * (e_t[prec] - e_t[0]),
+           "dEloc_mean_abs_mHa": 1e3 * float(d.mean()), "dEloc_max_mHa": 1e3 * float(d.max()),
+           "dEloc_rel_mean": float((d / np.abs(el[0])).mean()),
+           "phi_rel_err_one_step": rel, "walkers": nwalk,
+           "note": "mixed minus FP64 on identical walkers and fields; the FP64 path is held "
+                   "to the oracle at 1e-10"}
+    for r in runs.values():
+        r.close()
+    del runs
+    torch.cuda.empty_cache()
+    return out
 
 
 def cpu_sample(w: workloads.Workload, n_walkers=32, n_steps=3):
@@ -481,6 +525,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end pass")
     ap.add_argument("--no-graph", action="store_true", help="launch kernels one by one")
+    ap.add_argument("--no-precision-report", action="store_true")
     ap.add_argument("--ref-walkers", type=int, default=16)
     args = ap.parse_args()
     if args.warmup < 3:
@@ -546,6 +591,8 @@ def main():
                    "E_T": r["info"].E_T, "nonfinite": int(r["info"].nonfinite)},
         "flops_per_walker_step": fl["total"],
     }
+    if r["precision_report"]:
+        line["precision_vs_fp64"] = r["precision_report"]
     if N == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_sample(w)
     print(json.dumps(line))

@@ -631,7 +631,11 @@ namespace {
 constexpr int EX_T = 256, EX_K = 32, EX_P = 32;
 }
 int exchange_chunk(int N, int G) {
+  // outputs per block <= EX_T * EX_K, and the staged Lh rows
+  // (gc * N * EX_P doubles) plus Theta rows fit in 160 KB of shared memory
   int gc = (EX_T * EX_K) / (2 * N * N);
+  const int smem_cap = (160 * 1024 / 8 - 2 * N * (EX_P + 1)) / (N * EX_P);
+  if (gc > smem_cap) gc = smem_cap;
   if (gc < 1) gc = 1;
   if (gc > G) gc = G;
   return gc;
