@@ -28,6 +28,7 @@ def requests(n=5):
     sizes = [(12, 3, 48, 32), (30, 3, 150, 64), (20, 2, 100, 128), (40, 5, 200, 48), (16, 2, 80, 16)]
     for i, (M, N, G, W) in enumerate(sizes[:n]):
         h1, L, _ = workloads.hamiltonian(M, G, 4000 + i)
+        L = 0.3 * L  # milder vectors keep walkers alive through the run
         trial = np.linalg.eigh(h1)[1][:, :N]
         out.append(Request(rid=i, arrival=0.02 * i, h1=h1, L=L, trial=trial, nwalkers=W,
                            nsteps=40, seed=77 + i, energy_period=10))
@@ -50,7 +51,8 @@ def test_results_alone_equal_results_in_the_mix(pkg, prec):
     for r in requests():
         alone = Server(int(1.1 * srv.footprint(r)), precision=prec).run([r], realtime=False)[0]
         mixed = next(d for d in done if d.rid == r.rid)
-        assert np.array_equal(alone.energies, mixed.energies)
+        assert np.array_equal(alone.energies, mixed.energies, equal_nan=True)
+        assert np.isfinite(alone.energies[:, 1]).all()
         assert alone.energies.shape[0] == 4
 
 
