@@ -114,6 +114,28 @@ def dist_env():
     return ws, rank, local
 
 
+def replica_seed(base: int, rank: int) -> int:
+    """Each rank runs an independent replica: its own Philox key."""
+    return base + 1000 * rank
+
+
+def max_over_ranks(value: float, device="cpu") -> float:
+    """The slowest rank's time (the job's time), via all_reduce(MAX)."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(walkers_per_rank: int, steps: int, ms_max: float, world: int) -> float:
+    """Walker-steps of all ranks per second of the slowest rank."""
+    return world * walkers_per_rank * steps / (ms_max * 1e-3)
+
+
 def flops_per_walker_step(w: workloads.Workload, s=1):
     """Algorithmic FLOPs per walker-step (packed symmetric V, real Lh, s spin
     blocks run): force bias, V, Taylor, B_half, overlap/Theta, QR/q,
@@ -155,7 +177,7 @@ def run_gpu(args, w: workloads.Workload):
     prec = {"fp64": pkg.AFQMC_FP64, "tf32": pkg.AFQMC_MIXED_TF32, "bf16": pkg.AFQMC_MIXED_BF16}[
         args.precision]
     h1, L, H0, C, conv, grad = make_inputs(w)
-    p = pkg.default_params(w.M, w.N, w.nchol, w.nwalkers, dt=w.dt, seed=w.seed + 1000 * rank,
+    p = pkg.default_params(w.M, w.N, w.nchol, w.nwalkers, dt=w.dt, seed=replica_seed(w.seed, rank),
                            qr_period=w.qr_period, energy_period=w.energy_period,
                            taylor_order=w.taylor_order, precision=prec, H0=H0,
                            use_graph=0 if args.no_graph else 1)
@@ -212,12 +234,7 @@ def run_gpu(args, w: workloads.Workload):
     for _ in range(n_e):
         run.energy()
     s_energy = (time.perf_counter() - t0) / n_e
-    if ws > 1:
-        import torch.distributed as dist
-
-        t = torch.tensor([ms_total], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = max_over_ranks(ms_total, device=dev)
     info = run.info()
     E, wsum = run.energy()
     run.close()
@@ -459,7 +476,8 @@ def run_serve(args):
             for i, ((t, w), (h1, L, H0, C)) in enumerate(zip(stream, inputs))]
     free, _ = torch.cuda.mem_get_info()
     pool = int(min(0.6 * free, 120e9))
-    srv = Server(pool, precision=prec, chunk_steps=args.steps_per_block)
+    srv = Server(pool, precision=prec, chunk_steps=args.steps_per_block,
+                 max_active=args.slots or None)
     t0 = time.perf_counter()
     with ClockSampler(0) as clk:
         done = srv.run(reqs, realtime=True)
@@ -489,7 +507,8 @@ def run_serve(args):
         "config": {"workload": f"{len(reqs)} requests, Poisson {args.rate}/s, M in [20,300], "
                                f"N in [2,M/8], nchol=5M, walkers in [128,2048], "
                                f"{args.blocks} blocks x {args.steps_per_block} steps",
-                   "pool_GB": pool / 1e9, "trial": "core-Hamiltonian orbitals"},
+                   "pool_GB": pool / 1e9, "trial": "core-Hamiltonian orbitals",
+                   "slots": args.slots},
         "latency": lat, "makespan_s": makespan,
         "offered_walker_steps_per_s": ws_total / max(1e-9, max(r.arrival for r in reqs)),
         "fp64_one_at_a_time": {"measured_requests": n_fp, "seconds_measured": t_fp,
@@ -516,6 +535,7 @@ def main():
     ap.add_argument("--rate", type=float, default=20.0)
     ap.add_argument("--blocks", type=int, default=4)
     ap.add_argument("--steps-per-block", type=int, default=25)
+    ap.add_argument("--slots", type=int, default=8, help="serve: runs advanced per tick (0: memory only)")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
@@ -543,7 +563,7 @@ def main():
     K = args.steps
     N = r["world"]
     ms_step = r["ms_total"] / K
-    value = N * w.nwalkers * K / (r["ms_total"] * 1e-3)
+    value = job_throughput(w.nwalkers, K, r["ms_total"], N)
     fl = flops_per_walker_step(w)
     pk, pk_kind = peaks()
     # dominant kernel: the V contraction (one launch per step)

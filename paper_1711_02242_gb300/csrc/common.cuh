@@ -110,6 +110,22 @@ __device__ inline void field_pair(uint64_t seed, uint32_t step, uint32_t walker,
   *xb = rad * s;
 }
 
+// The same pair from the same Philox words with the Box-Muller transform taken
+// in FP32 (mixed path: the fields only feed BF16/TF32 contractions, and
+// float64 log/sincos run on GB300's slow FP64 pipe).
+__device__ inline void field_pair_f32(uint64_t seed, uint32_t step, uint32_t walker, uint32_t k,
+                                      double* xa, double* xb) {
+  u32x4 c = {k, walker, step, 0u};
+  u32x4 r = philox4x32_10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
+  const float u1 = (float)uniform53(r.x, r.y);
+  const float u2 = (float)uniform53(r.z, r.w);
+  const float rad = sqrtf(-2.f * logf(u1));
+  float s, co;
+  sincospif(2.f * u2, &s, &co);
+  *xa = (double)(rad * co);
+  *xb = (double)(rad * s);
+}
+
 // ------------------------------------------------------------ reductions --
 template <typename T>
 __device__ inline T warp_sum(T v) {

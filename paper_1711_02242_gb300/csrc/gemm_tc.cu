@@ -362,8 +362,30 @@ __device__ __forceinline__ void put_term(void* tb, int kind, long wrow, int N, i
   }
 }
 
+// 16 consecutive values (times sign) into a BF16 or TF32 row at element idx
+// (idx a multiple of 8 elements, 16-byte aligned): two or four vector stores.
+__device__ __forceinline__ void store16_lo(void* base, int kind, long idx, const float* v,
+                                           float sign) {
+  if (kind == LO_BF16) {
+    uint4 w[2];
+    __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(w);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) h[i] = __floats2bfloat162_rn(sign * v[2 * i], sign * v[2 * i + 1]);
+    uint4* d = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(base) + idx);
+    d[0] = w[0];
+    d[1] = w[1];
+  } else {
+    float4* d = reinterpret_cast<float4*>(reinterpret_cast<float*>(base) + idx);
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      d[i] = make_float4(round_tf32(sign * v[4 * i]), round_tf32(sign * v[4 * i + 1]),
+                         round_tf32(sign * v[4 * i + 2]), round_tf32(sign * v[4 * i + 3]));
+  }
+}
+
 // First half step: rows (w,c,i) of Phi^T, columns p; D = (B_half Phi)^T.
 // acc[(w,c,i)][p] = D (FP32, pitch Mp) and Tb holds the 0th Taylor term.
+// Each thread owns one row and 16 consecutive p per chunk: vector stores.
 struct EpiProp0 {
   float* acc;
   void* tb;
@@ -380,12 +402,28 @@ struct EpiProp0 {
       tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c0, v);
       if (row >= rows) continue;
       const int w = row / (2 * N), rem = row % (2 * N), c = rem / N, i = rem % N;
+      const int pb = n0 + c0;
+      if (pb >= M) continue;
+      if (pb + 16 <= M) {
+        float4* a4 = reinterpret_cast<float4*>(acc + (long)row * Mp + pb);
 #pragma unroll
-      for (int u = 0; u < 16; ++u) {
-        const int p = n0 + c0 + u;
-        if (p < M) {
-          acc[(long)row * Mp + p] = v[u];
-          put_term(tb, lo_kind, (long)w * 2 * N, N, Mp, c, i, p, v[u]);
+        for (int k = 0; k < 4; ++k) a4[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+        const long rr = ((long)w * 2 * N + i) * 2L * Mp, ri = ((long)w * 2 * N + N + i) * 2L * Mp;
+        if (c == 0) {
+          store16_lo(tb, lo_kind, rr + pb, v, 1.f);
+          store16_lo(tb, lo_kind, ri + Mp + pb, v, 1.f);
+        } else {
+          store16_lo(tb, lo_kind, rr + Mp + pb, v, -1.f);
+          store16_lo(tb, lo_kind, ri + pb, v, 1.f);
+        }
+      } else {
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+          const int p = pb + u;
+          if (p < M) {
+            acc[(long)row * Mp + p] = v[u];
+            put_term(tb, lo_kind, (long)w * 2 * N, N, Mp, c, i, p, v[u]);
+          }
         }
       }
     }
@@ -407,19 +445,24 @@ struct EpiTaylor {
                                       float*) const {
     const int w = blockIdx.y;
     const int p = blockIdx.x * BM + 32 * q + lane;
+    float* accw = acc + (long)w * 2 * N * Mp + p;  // column p of this walker's rows
 #pragma unroll 1
     for (int c0 = 0; c0 < BN; c0 += 16) {
       float v[16];
       tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c0, v);
-      if (p >= M) continue;
+      if (p >= M || c0 >= 2 * N) continue;
+      // all loads of the running sum first (the stores below could alias them
+      // as far as the compiler knows), then the stores
+      float old[16];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) old[u] = (c0 + u < 2 * N) ? accw[(long)(c0 + u) * Mp] : 0.f;
 #pragma unroll
       for (int u = 0; u < 16; ++u) {
         const int n = c0 + u;
         if (n < 2 * N) {
-          const int c = n / N, i = n % N;
           const float val = v[u] * scale;
-          acc[((long)w * 2 * N + c * N + i) * Mp + p] += val;
-          if (tb_out) put_term(tb_out, lo_kind, (long)w * 2 * N, N, Mp, c, i, p, val);
+          accw[(long)n * Mp] = old[u] + val;
+          if (tb_out) put_term(tb_out, lo_kind, (long)w * 2 * N, N, Mp, n / N, n % N, p, val);
         }
       }
     }

@@ -37,7 +37,10 @@ __global__ void __launch_bounds__(256) k_field(FieldArgs a) {
   const int npair = (a.G + 1) / 2;
   for (int k = threadIdx.x; k < npair; k += blockDim.x) {
     double xa, xb;
-    field_pair(a.seed, (uint32_t)*a.dstep, (uint32_t)w, (uint32_t)k, &xa, &xb);
+    if (a.x_lo)
+      field_pair_f32(a.seed, (uint32_t)*a.dstep, (uint32_t)w, (uint32_t)k, &xa, &xb);
+    else
+      field_pair(a.seed, (uint32_t)*a.dstep, (uint32_t)w, (uint32_t)k, &xa, &xb);
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int g = 2 * k + h;
@@ -1072,10 +1075,12 @@ namespace afq {
 __global__ void __launch_bounds__(256) k_unpack_v(const float* Y, long ldy, int M, int Mp,
                                                   float sdt, void* V, int kind) {
   __shared__ float sr[32][33], si[32][33];
-  const int w = blockIdx.z, p0 = blockIdx.y * 32, q0 = blockIdx.x * 32;
+  const int w = blockIdx.y, p0 = blockIdx.x * 32;  // one 32-row strip of one walker
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const float* Yr = Y + (long)w * 2 * ldy;
   const float* Yi = Yr + ldy;
+  for (int q0 = 0; q0 < Mp; q0 += 32) {
+  __syncthreads();  // the previous tile's shared-memory reads are done
   if (p0 < q0 + 32) {  // diagonal or upper tile: element (p, q) at packed(min, max)
     for (int r = ty; r < 32; r += 8) {
       const int p = p0 + r, q = q0 + tx;
@@ -1109,11 +1114,12 @@ __global__ void __launch_bounds__(256) k_unpack_v(const float* Y, long ldy, int 
     store_lo(V, kind, row + q, -sdt * si[r][tx]);
     store_lo(V, kind, row + Mp + q, sdt * sr[r][tx]);
   }
+  }
 }
 
 int launch_unpack_v(const float* Y, long ldy, int W, int M, int Mp, double sdt, void* V, int kind,
                     cudaStream_t st) {
-  dim3 grid(cdiv(Mp, 32), cdiv(M, 32), W);
+  dim3 grid(cdiv(M, 32), W);
   AFQ_LAUNCH(k_unpack_v, grid, 256, 0, st, Y, ldy, M, Mp, (float)sdt, V, kind);
   return AFQMC_OK;
 }

@@ -80,7 +80,10 @@ class Request:
 
 class Server:
     def __init__(self, pool_bytes: int, precision: int = 2, chunk_steps: int = 10,
-                 device="cuda:0", qr_period: int = 5, dt: float = 0.005):
+                 device="cuda:0", qr_period: int = 5, dt: float = 0.005,
+                 max_active: int | None = None):
+        """max_active bounds the runs advanced per tick (slots); None: memory only."""
+        self.max_active = max_active
         self.pool = DevicePool(pool_bytes, device)
         self.precision = precision
         self.chunk = chunk_steps
@@ -115,8 +118,8 @@ class Server:
             now = clock()
             while pending and pending[0].arrival <= now:
                 queue.append(pending.pop(0))
-            # admission in arrival order while the footprint fits
-            while queue:
+            # admission in arrival order while a slot is free and the footprint fits
+            while queue and (self.max_active is None or len(active) < self.max_active):
                 r = queue[0]
                 blk = self.pool.alloc(self.footprint(r))
                 if blk is None:
