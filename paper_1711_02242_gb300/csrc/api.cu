@@ -43,11 +43,7 @@ size_t plan(const afqmc_params& p, Bufs* b, char* base) {
   const size_t P = M * (M + 1) / 2;
   const bool mixed = p.precision != AFQMC_FP64;
   size_t nchunk = (G + exchange_chunk(p.N, p.nchol) - 1) / exchange_chunk(p.N, p.nchol);
-  if (mixed) {
-    int RG, CW;
-    exchange_tile(p.N, &RG, &CW);
-    nchunk = (G + RG - 1) / RG;
-  }
+  if (mixed) nchunk = G;  // the tensor-core exchange leaves one partial per vector
   const size_t lo = (p.precision == AFQMC_MIXED_BF16) ? 2 : 4;
   const size_t Gp = (G + 7) / 8 * 8, Mp = (M + 7) / 8 * 8, Pp = (P + 3) / 4 * 4;
   Bump a{base};
@@ -426,7 +422,7 @@ static int propagate_mixed(afqmc_state* s) {
 static int step_once(afqmc_state* s) {
   const afqmc_params& p = s->p;
   const Bufs& b = s->b;
-  const int W = p.nwalkers, N = p.N, M = p.M, G = p.nchol;
+  const int W = p.nwalkers, N = p.N, M = p.M;
   // force bias traces t = 2 Tr(Lh_g Theta) for every walker (Eq. precomputing2)
   if (!s->t_fresh) {
     prof_begin(s, AFQMC_PH_FORCE_BIAS);

@@ -229,7 +229,8 @@ __global__ void __launch_bounds__(192, 1)
     fence_after();
     asm volatile("bar.sync 1, 128;" ::: "memory");  // one decision for all 4 warps
     if (!*(volatile int*)abort_flag)
-      epi.template run<BN>(tmem, q, lane, warp - 2, m0, n0, M, N, reinterpret_cast<float*>(smem));
+      epi.template run<BN>(tmem, q, lane, warp - 2, blockIdx.x, blockIdx.y, m0, n0, M, N,
+                           reinterpret_cast<float*>(smem));
   }
   // wait (bounded) for any TMA still in flight on an abort path, then free TMEM
   if (warp == 0 && lane == 0 && *(volatile int*)abort_flag) {
@@ -247,9 +248,140 @@ __global__ void __launch_bounds__(192, 1)
   }
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Persistent variant for epilogues that need no shared memory: one CTA per SM
+// walks the output tiles t = blockIdx.x, blockIdx.x + gridDim.x, ... (tile
+// (bx, by) = (t % gx, t / gx), so CTAs running together share B tiles in L2).
+// Two TMEM accumulators of BN columns: the epilogue warps drain tile j while
+// the MMA thread fills tile j + 1 (tfull / tempty mbarriers per accumulator).
+template <int BN, int STAGES, bool TF32, class Epi>
+__global__ void __launch_bounds__(192, 1)
+    k_tc_gemm_persistent(const __grid_constant__ CUtensorMap tmA,
+                         const __grid_constant__ CUtensorMap tmB, int M, int N, int K, int gx,
+                         int ntiles, Epi epi, int* err) {
+  extern __shared__ uint8_t smem_raw[];
+  using S = Smem<BN, STAGES>;
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + S::RING);
+  uint64_t* empty = full + STAGES;
+  uint64_t* tfull = empty + STAGES;  // [2]
+  uint64_t* tempty = tfull + 2;      // [2]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
+  int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  constexpr int ELEM = TF32 ? 4 : 2;
+  constexpr int BK = BKB / ELEM;
+  constexpr int KSTEPS = BKB / 32;
+  const int nk = (K + BK - 1) / BK;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&tfull[a], 1);
+      mbar_init(&tempty[a], 4);  // one arrival per epilogue warp
+    }
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"((uint32_t)(2 * BN)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    int it = 0;
+    for (int t = blockIdx.x; t < ntiles && !*(volatile int*)abort_flag; t += gridDim.x) {
+      const int bx = t % gx, by = t / gx;
+      const int m0 = epi.m_origin(bx, by), n0 = epi.n_origin(bx, by);
+      for (int kb = 0; kb < nk; ++kb, ++it) {
+        const int s = it % STAGES;
+        if (it >= STAGES && !mbar_wait(&empty[s], ((it / STAGES) - 1) & 1, err, 11)) {
+          *(volatile int*)abort_flag = 1;
+          break;
+        }
+        uint8_t* a = smem + s * S::STAGE;
+        mbar_expect_tx(&full[s], S::STAGE);
+        tma_load_2d(a, &tmA, &full[s], kb * BK, m0);
+        tma_load_2d(a + S::A_BYTES, &tmB, &full[s], kb * BK, n0);
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    constexpr uint32_t idesc = instr_desc(TF32 ? 2u : 1u, (uint32_t)BN);
+    int it = 0, j = 0;
+    for (int t = blockIdx.x; t < ntiles && !*(volatile int*)abort_flag; t += gridDim.x, ++j) {
+      const int acc = j & 1;
+      if (j >= 2 && !mbar_wait(&tempty[acc], ((j / 2) - 1) & 1, err, 12)) {
+        *(volatile int*)abort_flag = 1;
+        break;
+      }
+      fence_after();
+      const uint32_t d = tmem + (uint32_t)(acc * BN);
+      bool ok = true;
+      for (int kb = 0; kb < nk; ++kb, ++it) {
+        const int s = it % STAGES;
+        if (!mbar_wait(&full[s], (it / STAGES) & 1, err, 13)) {
+          ok = false;
+          break;
+        }
+        fence_after();
+        const uint32_t a = smem_u32(smem + s * S::STAGE);
+        const uint32_t b = a + S::A_BYTES;
+#pragma unroll
+        for (int k = 0; k < KSTEPS; ++k)
+          mma<TF32>(d, sw128_desc(a + 32 * k), sw128_desc(b + 32 * k), idesc,
+                    (kb > 0 || k > 0) ? 1u : 0u);
+        mma_commit(&empty[s]);
+      }
+      mma_commit(&tfull[acc]);
+      if (!ok) {
+        *(volatile int*)abort_flag = 1;
+        break;
+      }
+    }
+  } else if (warp >= 2) {
+    const int q = warp & 3;
+    float* esm = Epi::kSmemBytes ? reinterpret_cast<float*>(smem + S::RING + 256) : nullptr;
+    int j = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++j) {
+      const int acc = j & 1;
+      if (!mbar_wait(&tfull[acc], (j / 2) & 1, err, 14)) *(volatile int*)abort_flag = 1;
+      fence_after();
+      asm volatile("bar.sync 1, 128;" ::: "memory");  // one decision for all 4 warps
+      if (*(volatile int*)abort_flag) break;
+      const int bx = t % gx, by = t / gx;
+      epi.template run<BN>(tmem + (uint32_t)(acc * BN), q, lane, warp - 2, bx, by,
+                           epi.m_origin(bx, by), epi.n_origin(bx, by), M, N, esm);
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[acc]);
+    }
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"((uint32_t)(2 * BN)));
+  }
+}
+
 // ------------------------------------------------------------ epilogues -----
 // Plain FP32 store of alpha * D to C[m * ldc + n].
 struct EpiStore {
+  static constexpr int kSmemBytes = 0;
   float* C;
   long ldc;
   float alpha;
@@ -257,8 +389,8 @@ struct EpiStore {
   __device__ __forceinline__ int m_origin(int bx, int) const { return bx * BM; }
   __device__ __forceinline__ int n_origin(int, int by) const { return by * bn; }
   template <int BN>
-  __device__ __forceinline__ void run(uint32_t tmem, int q, int lane, int, int m0, int n0, int M,
-                                      int N, float*) const {
+  __device__ __forceinline__ void run(uint32_t tmem, int q, int lane, int, int, int, int m0, int n0,
+                                      int M, int N, float*) const {
     const int row = m0 + 32 * q + lane;
 #pragma unroll 1
     for (int c0 = 0; c0 < BN; c0 += 16) {
@@ -283,19 +415,21 @@ struct EpiStore {
 
 // Exchange part of Eq. localenergy3 fused into the T_g = Lh_g Theta
 // contraction.  Rows of the product are (g, i) = Lh rows, columns (w, c, j)
-// = Theta^T rows (c = re/im plane).  A CTA covers RG whole Cholesky vectors
+// = Theta^T rows (c = re/im plane).  A tile covers RG whole Cholesky vectors
 // (RG*N <= 128 rows) and CW whole walkers (CW*2N <= 256 columns), so every
-// T_g,w block lies inside its tile: the accumulator is copied to shared
-// memory and sum_ij T_ij T_ji (complex) is formed there; T never reaches
-// global memory.  part[w][tile row][2] receives the sum over the tile's g.
+// T_g,w block lies inside it: the accumulator is copied to this epilogue's
+// own shared memory and sum_ij T_ij T_ji (complex) is formed there; T never
+// reaches global memory.  part[w][g][2] receives one partial per (g, w)
+// (nchunk = G), summed later in a fixed order.
 struct EpiExchange {
+  static constexpr int kSmemBytes = 128 * 257 * 4;  // one 128 x 256 FP32 tile
   double* part;
   int G, W, N, RG, CW, nchunk;
   __device__ __forceinline__ int m_origin(int bx, int) const { return bx * RG * N; }
   __device__ __forceinline__ int n_origin(int, int by) const { return by * CW * 2 * N; }
   template <int BN>
-  __device__ __forceinline__ void run(uint32_t tmem, int q, int lane, int ew, int, int, int, int,
-                                      float* sm) const {
+  __device__ __forceinline__ void run(uint32_t tmem, int q, int lane, int ew, int bx, int by, int,
+                                      int, int, int, float* sm) const {
     constexpr int LD = BN + 1;
     const int r = 32 * q + lane;
 #pragma unroll 1
@@ -306,8 +440,7 @@ struct EpiExchange {
       for (int i = 0; i < 16; ++i) sm[r * LD + c0 + i] = v[i];
     }
     asm volatile("bar.sync 1, 128;" ::: "memory");
-    double* red = reinterpret_cast<double*>(sm + 128 * LD);  // [RG][CW][2]
-    const int g0 = blockIdx.x * RG, w0 = blockIdx.y * CW;
+    const int g0 = bx * RG, w0 = by * CW;
     // FP32 sums per lane (the products come from FP32 accumulators; GB300's
     // float64 pipe is ~60x slower, so float64 here would dominate the kernel)
     for (int pi = ew; pi < RG * CW; pi += 4) {
@@ -325,23 +458,15 @@ struct EpiExchange {
       }
       er = warp_sum(er);
       ei = warp_sum(ei);
-      if (lane == 0) {
-        red[2 * pi] = (double)er;
-        red[2 * pi + 1] = (double)ei;
+      // one partial per (Cholesky vector, walker): part[w][g][2]
+      if (lane == 0 && g0 + g < G && w0 + wl < W) {
+        double* o = part + ((long)(w0 + wl) * nchunk + g0 + g) * 2;
+        o[0] = (double)er;
+        o[1] = (double)ei;
       }
     }
+    // the next tile's copy into sm must wait until every warp is done reading
     asm volatile("bar.sync 1, 128;" ::: "memory");
-    const int t = ew * 32 + lane;
-    if (t < CW && w0 + t < W) {
-      double sr = 0.0, si = 0.0;
-      for (int g = 0; g < RG; ++g) {
-        sr += red[2 * (g * CW + t)];
-        si += red[2 * (g * CW + t) + 1];
-      }
-      double* o = part + ((long)(w0 + t) * nchunk + blockIdx.x) * 2;
-      o[0] = sr;
-      o[1] = si;
-    }
   }
 };
 
@@ -387,14 +512,15 @@ __device__ __forceinline__ void store16_lo(void* base, int kind, long idx, const
 // acc[(w,c,i)][p] = D (FP32, pitch Mp) and Tb holds the 0th Taylor term.
 // Each thread owns one row and 16 consecutive p per chunk: vector stores.
 struct EpiProp0 {
+  static constexpr int kSmemBytes = 0;
   float* acc;
   void* tb;
   int lo_kind, N, M, Mp, rows;
   __device__ __forceinline__ int m_origin(int bx, int) const { return bx * BM; }
   __device__ __forceinline__ int n_origin(int, int by) const { return by * 256; }
   template <int BN>
-  __device__ __forceinline__ void run(uint32_t tmem, int q, int lane, int, int m0, int n0, int,
-                                      int, float*) const {
+  __device__ __forceinline__ void run(uint32_t tmem, int q, int lane, int, int, int, int m0, int n0,
+                                      int, int, float*) const {
     const int row = m0 + 32 * q + lane;
 #pragma unroll 1
     for (int c0 = 0; c0 < BN; c0 += 16) {
@@ -434,6 +560,7 @@ struct EpiProp0 {
 // columns n < 2N of Tb_{k-1}; T_k = D / k is added to acc and, unless it is
 // the last term, written as the next operand.
 struct EpiTaylor {
+  static constexpr int kSmemBytes = 0;
   float* acc;
   void* tb_out;
   int lo_kind, N, M, Mp;
@@ -441,10 +568,10 @@ struct EpiTaylor {
   __device__ __forceinline__ int m_origin(int bx, int by) const { return by * M + bx * BM; }
   __device__ __forceinline__ int n_origin(int, int by) const { return by * 2 * N; }
   template <int BN>
-  __device__ __forceinline__ void run(uint32_t tmem, int q, int lane, int, int, int, int, int,
-                                      float*) const {
-    const int w = blockIdx.y;
-    const int p = blockIdx.x * BM + 32 * q + lane;
+  __device__ __forceinline__ void run(uint32_t tmem, int q, int lane, int, int bx, int by, int, int,
+                                      int, int, float*) const {
+    const int w = by;
+    const int p = bx * BM + 32 * q + lane;
     float* accw = acc + (long)w * 2 * N * Mp + p;  // column p of this walker's rows
 #pragma unroll 1
     for (int c0 = 0; c0 < BN; c0 += 16) {
@@ -472,14 +599,15 @@ struct EpiTaylor {
 // Last half step: rows (w,c,i) of the series sum, columns p; the product is
 // stored as the new float64 orbitals of live walkers.
 struct EpiPhi {
+  static constexpr int kSmemBytes = 0;
   double* phiT;
   const double* wt;
   int N, M, rows;
   __device__ __forceinline__ int m_origin(int bx, int) const { return bx * BM; }
   __device__ __forceinline__ int n_origin(int, int by) const { return by * 256; }
   template <int BN>
-  __device__ __forceinline__ void run(uint32_t tmem, int q, int lane, int, int m0, int n0, int,
-                                      int, float*) const {
+  __device__ __forceinline__ void run(uint32_t tmem, int q, int lane, int, int, int, int m0, int n0,
+                                      int, int, float*) const {
     const int row = m0 + 32 * q + lane;
     const bool ok = row < rows && walker_alive(wt, row / (2 * N));
 #pragma unroll 1
@@ -560,6 +688,42 @@ static int launch_tc(const TcGemm& g, const Epi& epi, dim3 grid, cudaStream_t st
   return AFQMC_OK;
 }
 
+static int sm_count() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1)
+      n = 148;
+  }
+  return n;
+}
+
+template <int BN, int STAGES, bool TF32, class Epi>
+static int launch_tc_persistent(const TcGemm& g, const Epi& epi, int gx, int gy, cudaStream_t st) {
+  constexpr int kTotal = tc::Smem<BN, STAGES>::TOTAL + Epi::kSmemBytes;
+  static_assert(kTotal <= 232448, "shared memory");
+  const int eb = TF32 ? 4 : 2;
+  CUtensorMap ta, tb;
+  AFQ_TRY(make_tmap(&ta, g.A, eb, g.m, g.k, g.lda, tc::BM));
+  AFQ_TRY(make_tmap(&tb, g.B, eb, g.n, g.k, g.ldb, BN));
+  auto kern = tc::k_tc_gemm_persistent<BN, STAGES, TF32, Epi>;
+  static bool attr = false;
+  if (!attr) {
+    AFQ_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kTotal));
+    attr = true;
+  }
+  const long ntiles = (long)gx * gy;
+  if (ntiles <= 0) return AFQMC_OK;
+  if (ntiles > 0x7fffffffL) {
+    set_error("tc gemm: too many tiles");
+    return AFQMC_EINVAL;
+  }
+  const int grid = (int)(ntiles < sm_count() ? ntiles : sm_count());
+  AFQ_LAUNCH(kern, grid, 192, kTotal, st, ta, tb, g.m, g.n, g.k, gx, (int)ntiles, epi, g.err);
+  return AFQMC_OK;
+}
+
 // ---- plain-store contraction with an autotuned tile width --------------------
 // Candidates: BN = 256 (4 stages, one CTA per SM), 128 (3 stages) and 64
 // (4 stages), the last two small enough for two CTAs per SM.  tc_tune_store()
@@ -583,17 +747,17 @@ std::map<ShapeKey, int> g_tuned_bn;
 static int launch_store_bn(const TcGemm& g, float* C, long ldc, float alpha, int bn,
                            cudaStream_t st) {
   tc::EpiStore e{C, ldc, alpha, bn};
-  dim3 grid(cdiv(g.m, tc::BM), cdiv(g.n, bn));
+  const int gx = cdiv(g.m, tc::BM), gy = cdiv(g.n, bn);
   if (bn == 64) {
-    if (g.tf32) return launch_tc<64, 4, true>(g, e, grid, st);
-    return launch_tc<64, 4, false>(g, e, grid, st);
+    if (g.tf32) return launch_tc_persistent<64, 8, true>(g, e, gx, gy, st);
+    return launch_tc_persistent<64, 8, false>(g, e, gx, gy, st);
   }
   if (bn == 128) {
-    if (g.tf32) return launch_tc<128, 3, true>(g, e, grid, st);
-    return launch_tc<128, 3, false>(g, e, grid, st);
+    if (g.tf32) return launch_tc_persistent<128, 6, true>(g, e, gx, gy, st);
+    return launch_tc_persistent<128, 6, false>(g, e, gx, gy, st);
   }
-  if (g.tf32) return launch_tc<256, 4, true>(g, e, grid, st);
-  return launch_tc<256, 4, false>(g, e, grid, st);
+  if (g.tf32) return launch_tc_persistent<256, 4, true>(g, e, gx, gy, st);
+  return launch_tc_persistent<256, 4, false>(g, e, gx, gy, st);
 }
 
 int tc_gemm_store(const TcGemm& g, float* C, long ldc, float alpha, cudaStream_t st) {
@@ -645,9 +809,9 @@ int tc_tune_store(const TcGemm& g, float* C, long ldc, float alpha, cudaStream_t
 int tc_prop_first(const TcGemm& g, float* acc, void* tb, int lo_kind, int N, int M, int Mp,
                   cudaStream_t st) {
   tc::EpiProp0 e{acc, tb, lo_kind, N, M, Mp, g.m};
-  dim3 grid(cdiv(g.m, tc::BM), cdiv(M, 256));
-  if (g.tf32) return launch_tc<256, 4, true>(g, e, grid, st);
-  return launch_tc<256, 4, false>(g, e, grid, st);
+  const int gx = cdiv(g.m, tc::BM), gy = cdiv(M, 256);
+  if (g.tf32) return launch_tc_persistent<256, 4, true>(g, e, gx, gy, st);
+  return launch_tc_persistent<256, 4, false>(g, e, gx, gy, st);
 }
 
 int tc_taylor_term(const TcGemm& g, float* acc, void* tb_out, int lo_kind, int W, int N, int M,
@@ -657,17 +821,16 @@ int tc_taylor_term(const TcGemm& g, float* acc, void* tb_out, int lo_kind, int W
     return AFQMC_EUNSUPPORTED;
   }
   tc::EpiTaylor e{acc, tb_out, lo_kind, N, M, Mp, scale};
-  dim3 grid(cdiv(M, tc::BM), W);
-  if (g.tf32) return launch_tc<64, 4, true>(g, e, grid, st);
-  return launch_tc<64, 4, false>(g, e, grid, st);
+  if (g.tf32) return launch_tc_persistent<64, 8, true>(g, e, cdiv(M, tc::BM), W, st);
+  return launch_tc_persistent<64, 8, false>(g, e, cdiv(M, tc::BM), W, st);
 }
 
 int tc_prop_last(const TcGemm& g, double* phiT, const double* wt, int N, int M,
                  cudaStream_t st) {
   tc::EpiPhi e{phiT, wt, N, M, g.m};
-  dim3 grid(cdiv(g.m, tc::BM), cdiv(M, 256));
-  if (g.tf32) return launch_tc<256, 4, true>(g, e, grid, st);
-  return launch_tc<256, 4, false>(g, e, grid, st);
+  const int gx = cdiv(g.m, tc::BM), gy = cdiv(M, 256);
+  if (g.tf32) return launch_tc_persistent<256, 4, true>(g, e, gx, gy, st);
+  return launch_tc_persistent<256, 4, false>(g, e, gx, gy, st);
 }
 
 // Exchange blocking: RG Cholesky vectors x CW walkers per 128 x 256 tile.
@@ -680,14 +843,15 @@ void exchange_tile(int N, int* RG, int* CW) {
 int tc_exchange(const TcGemm& g, int G, int W, int N, double* part, int nchunk, cudaStream_t st) {
   int RG, CW;
   exchange_tile(N, &RG, &CW);
-  if (RG < 1 || CW < 1 || nchunk != (G + RG - 1) / RG) {
+  if (RG < 1 || CW < 1 || nchunk != G) {
     set_error("tc exchange: bad blocking N=%d", N);
     return AFQMC_EINVAL;
   }
   tc::EpiExchange e{part, G, W, N, RG, CW, nchunk};
-  dim3 grid(cdiv(G, RG), cdiv(W, CW));
-  if (g.tf32) return launch_tc<256, 4, true>(g, e, grid, st);
-  return launch_tc<256, 4, false>(g, e, grid, st);
+  // K = M is a few k-blocks of L2-resident operands: a 2-deep ring leaves room
+  // for the epilogue's own 128 KB tile buffer
+  if (g.tf32) return launch_tc_persistent<256, 2, true>(g, e, cdiv(G, RG), cdiv(W, CW), st);
+  return launch_tc_persistent<256, 2, false>(g, e, cdiv(G, RG), cdiv(W, CW), st);
 }
 
 }  // namespace afq

@@ -765,17 +765,19 @@ __global__ void __launch_bounds__(256) k_eloc(ElocArgs a) {
     cr += re * re - imv * imv;
     ci += 2.0 * re * imv;
   }
+  double xr = 0.0, xi = 0.0;
+  const double* pp = a.part + (long)w * a.nchunk * 2;
+  for (int c = threadIdx.x; c < a.nchunk; c += blockDim.x) {
+    xr += pp[2 * c];
+    xi += pp[2 * c + 1];
+  }
   e1r = block_sum(e1r, sh);
   e1i = block_sum(e1i, sh);
   cr = block_sum(cr, sh);
   ci = block_sum(ci, sh);
+  xr = block_sum(xr, sh);
+  xi = block_sum(xi, sh);
   if (threadIdx.x == 0) {
-    double xr = 0.0, xi = 0.0;
-    const double* p = a.part + (long)w * a.nchunk * 2;
-    for (int c = 0; c < a.nchunk; ++c) {
-      xr += p[2 * c];
-      xi += p[2 * c + 1];
-    }
     a.eloc[2 * w] = a.H0 + 2.0 * e1r + 0.5 * cr - xr;
     a.eloc[2 * w + 1] = 2.0 * e1i + 0.5 * ci - xi;
   }
