@@ -352,6 +352,16 @@ AFQMC_API int afqmc_local_energies_noalloc(int32_t M, int32_t N, int32_t nchol,
                                            const double* d_hh, const double* d_thetaT,
                                            double H0, double* d_eloc, void* stream);
 
+/*
+ * Bounded device-side wait, the pattern every wait inside the library follows
+ * (the tensor-core pipelines' mbarrier waits): one thread polls the DEVICE
+ * int *d_flag up to max_polls times (about 1 us apart); if it never becomes
+ * non-zero the kernel writes AFQMC_ETIMEOUT to the DEVICE int *d_status and
+ * returns, so the context stays usable and the host reads the status.  Used
+ * by the failure-detection tests.  Asynchronous on `stream`.
+ */
+AFQMC_API int afqmc_wait_flag(const int* d_flag, int64_t max_polls, int* d_status, void* stream);
+
 /* Message for the calling thread's last failed call (never NULL). */
 AFQMC_API const char* afqmc_last_error(void);
 

@@ -31,7 +31,8 @@ EXPORTED = ["afqmc_default_params", "afqmc_workspace_size", "afqmc_init", "afqmc
             "afqmc_destroy", "afqmc_last_error", "afqmc_launch_count",
             "afqmc_philox4x32_10", "afqmc_gaussian_fields", "afqmc_contract",
             "afqmc_profile_start", "afqmc_profile_stop", "afqmc_local_energies_noalloc",
-            "afqmc_group_create", "afqmc_group_propagate", "afqmc_group_destroy"]
+            "afqmc_group_create", "afqmc_group_propagate", "afqmc_group_destroy",
+            "afqmc_wait_flag"]
 
 
 class Params(ctypes.Structure):
@@ -101,6 +102,7 @@ def lib():
         "afqmc_group_create": (ctypes.c_int, [P(vp), ctypes.c_int32, vp, P(vp)]),
         "afqmc_group_propagate": (ctypes.c_int, [vp, ctypes.c_int32]),
         "afqmc_group_destroy": (ctypes.c_int, [vp]),
+        "afqmc_wait_flag": (ctypes.c_int, [vp, ctypes.c_int64, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)

@@ -45,7 +45,9 @@ size_t plan(const afqmc_params& p, Bufs* b, char* base) {
   size_t nchunk = (G + exchange_chunk(p.N, p.nchol) - 1) / exchange_chunk(p.N, p.nchol);
   if (mixed) nchunk = G;  // the tensor-core exchange leaves one partial per vector
   const size_t lo = (p.precision == AFQMC_MIXED_BF16) ? 2 : 4;
-  const size_t Gp = (G + 7) / 8 * 8, Mp = (M + 7) / 8 * 8, Pp = (P + 3) / 4 * 4;
+  // pitches: 16-byte rows for TMA; Mp a multiple of 16 so that 16-column
+  // epilogue chunks of the flattened (p, q) index never straddle rows
+  const size_t Gp = (G + 7) / 8 * 8, Mp = (M + 15) / 16 * 16, Pp = (P + 3) / 4 * 4;
   Bump a{base};
   // constants
   b->LpT = a.take<double>(P * G);
@@ -81,7 +83,7 @@ size_t plan(const afqmc_params& p, Bufs* b, char* base) {
   b->Mp = (int)Mp;
   b->Pp = (long)Pp;
   if (mixed) {
-    b->LpT_lo = a.take<char>(P * Gp * lo);
+    b->LfT_lo = a.take<char>(M * Mp * Gp * lo);  // full vectors, rows (p, q) = p*Mp + q
     b->Lh_lo = a.take<char>(G * N * Mp * lo);
     b->x_lo = a.take<char>(W * 2 * Gp * lo);
     b->th_lo = a.take<char>(W * 2 * N * Mp * lo);
@@ -95,7 +97,6 @@ size_t plan(const afqmc_params& p, Bufs* b, char* base) {
   if (mixed) {
     b->Y = nullptr;
     b->acc = nullptr;
-    b->Y32 = s1.take<float>(W * 2 * Pp);
     b->V_lo = s1.take<char>(W * M * 2 * Mp * lo);
     b->phi_lo = s1.take<char>(W * 2 * N * Mp * lo);
     b->acc32 = s1.take<float>(W * 2 * N * Mp);
@@ -348,22 +349,20 @@ static int propagate_mixed(afqmc_state* s) {
   prof_begin(s, AFQMC_PH_FIELDS);
   AFQ_TRY(launch_field(fa, s->st));
   prof_end(s);
+  // V = i sqrt(dt) sum_g x_g L_g over the full (p, q) grid, written straight
+  // into the [Re V | Im V] operand rows of the Taylor terms
   prof_begin(s, AFQMC_PH_V);
   TcGemm g;
   g.m = 2 * W;
-  g.n = b.P;
+  g.n = M * b.Mp;
   g.k = G;
   g.A = b.x_lo;
   g.lda = b.Gp;
-  g.B = b.LpT_lo;
+  g.B = b.LfT_lo;
   g.ldb = b.Gp;
   g.tf32 = b.lo_kind == LO_TF32;
   g.err = b.status;
-  AFQ_TRY(tc_gemm_store(g, b.Y32, b.Pp, 1.0f, s->st));
-  prof_end(s);
-  // [Re V | Im V] operand rows for the Taylor terms
-  prof_begin(s, AFQMC_PH_TAYLOR);
-  AFQ_TRY(launch_unpack_v(b.Y32, b.Pp, W, M, b.Mp, s->sdt, b.V_lo, b.lo_kind, s->st));
+  AFQ_TRY(tc_v_full(g, b.V_lo, b.lo_kind, W, M, b.Mp, s->sdt, s->st));
   prof_end(s);
   // first half step: acc = (B_half Phi)^T, Tb0 = the 0th Taylor term
   prof_begin(s, AFQMC_PH_BHALF);
@@ -386,12 +385,12 @@ static int propagate_mixed(afqmc_state* s) {
   void* tout = b.Tb1;
   for (int k = 1; k <= p.taylor_order; ++k) {
     TcGemm tg;
-    tg.m = W * M;
-    tg.n = W * 2 * N;
+    tg.m = W * 2 * N;  // A: the term's operand rows (w, c, i)
+    tg.n = W * M;      // B: [Re V | Im V] rows (w, p)
     tg.k = 2 * b.Mp;
-    tg.A = b.V_lo;
+    tg.A = tin;
     tg.lda = 2L * b.Mp;
-    tg.B = tin;
+    tg.B = b.V_lo;
     tg.ldb = 2L * b.Mp;
     tg.tf32 = b.lo_kind == LO_TF32;
     tg.err = b.status;
@@ -612,7 +611,7 @@ static int setup_device(afqmc_state* s, const double* h1, const double* L, const
   s->H0p = p.H0 - 0.5 * sumc2;
   if (b.mixed) {
     // BF16 / TF32 copies of the contraction operands (zero-padded pitches)
-    AFQ_TRY(launch_convert_lo(b.LpT, b.P, G, G, b.LpT_lo, b.Gp, b.lo_kind, st));
+    AFQ_TRY(launch_pack_full_lo(b.Lfull, G, M, b.Mp, b.Gp, b.LfT_lo, b.lo_kind, st));
     AFQ_TRY(launch_convert_lo(b.Lh, (long)G * N, M, M, b.Lh_lo, b.Mp, b.lo_kind, st));
     AFQ_CUDA(cudaMemsetAsync(b.th_lo, 0, (size_t)W * 2 * N * b.Mp * b.lo_bytes, st));
     AFQ_CUDA(cudaMemsetAsync(b.x_lo, 0, (size_t)W * 2 * b.Gp * b.lo_bytes, st));
@@ -636,18 +635,7 @@ static int setup_device(afqmc_state* s, const double* h1, const double* L, const
     AFQ_CUDA(cudaMemsetAsync(b.acc32, 0, sizeof(float) * (size_t)W * 2 * N * b.Mp, st));
     AFQ_CUDA(cudaMemsetAsync(b.Tb0, 0, (size_t)W * 2 * N * 2 * b.Mp * b.lo_bytes, st));
     AFQ_CUDA(cudaMemsetAsync(b.Tb1, 0, (size_t)W * 2 * N * 2 * b.Mp * b.lo_bytes, st));
-    // autotune the tile width of the two plain contractions for this shape
-    TcGemm gv;
-    gv.m = 2 * W;
-    gv.n = b.P;
-    gv.k = G;
-    gv.A = b.x_lo;
-    gv.lda = b.Gp;
-    gv.B = b.LpT_lo;
-    gv.ldb = b.Gp;
-    gv.tf32 = b.lo_kind == LO_TF32;
-    gv.err = b.status;
-    AFQ_TRY(tc_tune_store(gv, b.Y32, b.Pp, 1.0f, st, &s->bn_v));
+    // autotune the tile width of the force-bias contraction for this shape
     TcGemm gf;
     gf.m = 2 * W;
     gf.n = G;
@@ -1066,11 +1054,21 @@ int64_t afqmc_launch_count(void) { return g_launches; }
 
 namespace afq {
 int launch_philox(uint64_t key, const uint32_t* ctr, long n, uint32_t* out, cudaStream_t st);
+int launch_wait_flag(const int* flag, long long max_polls, int* status, cudaStream_t st);
 int launch_fields(uint64_t seed, uint32_t step, int w0, int nw, int G, double* out,
                   cudaStream_t st);
 }  // namespace afq
 
 extern "C" {
+int afqmc_wait_flag(const int* d_flag, int64_t max_polls, int* d_status, void* stream) {
+  if (!d_flag || !d_status || max_polls < 0 || max_polls > (1ll << 32)) {
+    afq::set_error("bad arguments");
+    return AFQMC_EINVAL;
+  }
+  return afq::launch_wait_flag(d_flag, (long long)max_polls, d_status,
+                               static_cast<cudaStream_t>(stream));
+}
+
 int afqmc_philox4x32_10(uint64_t key, const uint32_t* d_ctr, int64_t n, uint32_t* d_out,
                         void* stream) {
   if (n < 0 || (n > 0 && (!d_ctr || !d_out))) {

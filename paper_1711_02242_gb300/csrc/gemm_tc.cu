@@ -290,10 +290,14 @@ __global__ void __launch_bounds__(192, 1)
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
+  // TMEM columns: a power of two holding two accumulators of BN columns
+  constexpr uint32_t TCOLS = (2 * BN <= 64) ? 64 : (2 * BN <= 128) ? 128 : (2 * BN <= 256) ? 256 : 512;
+  constexpr uint32_t ASTRIDE = TCOLS / 2;
+  static_assert(BN <= (int)ASTRIDE, "accumulator stride");
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(tmem_slot)),
-                 "r"((uint32_t)(2 * BN)));
+                 "r"(TCOLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   fence_before();
@@ -328,7 +332,7 @@ __global__ void __launch_bounds__(192, 1)
         break;
       }
       fence_after();
-      const uint32_t d = tmem + (uint32_t)(acc * BN);
+      const uint32_t d = tmem + (uint32_t)acc * ASTRIDE;
       bool ok = true;
       for (int kb = 0; kb < nk; ++kb, ++it) {
         const int s = it % STAGES;
@@ -362,7 +366,7 @@ __global__ void __launch_bounds__(192, 1)
       asm volatile("bar.sync 1, 128;" ::: "memory");  // one decision for all 4 warps
       if (*(volatile int*)abort_flag) break;
       const int bx = t % gx, by = t / gx;
-      epi.template run<BN>(tmem + (uint32_t)(acc * BN), q, lane, warp - 2, bx, by,
+      epi.template run<BN>(tmem + (uint32_t)acc * ASTRIDE, q, lane, warp - 2, bx, by,
                            epi.m_origin(bx, by), epi.n_origin(bx, by), M, N, esm);
       fence_before();
       __syncwarp();
@@ -374,7 +378,7 @@ __global__ void __launch_bounds__(192, 1)
   if (warp == 1) {
     fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                 "r"((uint32_t)(2 * BN)));
+                 "r"(TCOLS));
   }
 }
 
@@ -559,38 +563,95 @@ struct EpiProp0 {
 // Taylor term k for walker w = blockIdx.y: rows p of [Vr | Vi] (a 128-row tile),
 // columns n < 2N of Tb_{k-1}; T_k = D / k is added to acc and, unless it is
 // the last term, written as the next operand.
+// The MMA takes the term as A (rows n = (c, i) of Tb_{k-1}: a 128-row tile at
+// walker w = by, rows n >= 2N belong to the next walker and are ignored) and
+// [Vr | Vi] as B (columns p: tile bx of BN), so D[n][p] = (V T_{k-1})^T and
+// each epilogue thread owns one row n and 16 consecutive p per chunk: the
+// running sum and the next operand are written with 16-byte vectors.
 struct EpiTaylor {
   static constexpr int kSmemBytes = 0;
+  static constexpr int kBN = 160;  // two tiles cover p < 320
   float* acc;
   void* tb_out;
   int lo_kind, N, M, Mp;
   float scale;
-  __device__ __forceinline__ int m_origin(int bx, int by) const { return by * M + bx * BM; }
-  __device__ __forceinline__ int n_origin(int, int by) const { return by * 2 * N; }
+  __device__ __forceinline__ int m_origin(int, int by) const { return by * 2 * N; }
+  __device__ __forceinline__ int n_origin(int bx, int by) const { return by * M + bx * kBN; }
   template <int BN>
   __device__ __forceinline__ void run(uint32_t tmem, int q, int lane, int, int bx, int by, int, int,
                                       int, int, float*) const {
-    const int w = by;
-    const int p = bx * BM + 32 * q + lane;
-    float* accw = acc + (long)w * 2 * N * Mp + p;  // column p of this walker's rows
+    const int w = by, n = 32 * q + lane;
+    const bool valid = n < 2 * N;
+    const int c = valid ? n / N : 0, i = valid ? n % N : 0;
+    float* arow = acc + ((long)w * 2 * N + n) * Mp;
+    const long rr = ((long)w * 2 * N + i) * 2L * Mp, ri = ((long)w * 2 * N + N + i) * 2L * Mp;
 #pragma unroll 1
     for (int c0 = 0; c0 < BN; c0 += 16) {
       float v[16];
       tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c0, v);
-      if (p >= M || c0 >= 2 * N) continue;
-      // all loads of the running sum first (the stores below could alias them
-      // as far as the compiler knows), then the stores
-      float old[16];
+      const int pb = bx * BN + c0;
+      if (!valid || pb >= M) continue;
 #pragma unroll
-      for (int u = 0; u < 16; ++u) old[u] = (c0 + u < 2 * N) ? accw[(long)(c0 + u) * Mp] : 0.f;
+      for (int u = 0; u < 16; ++u) v[u] *= scale;
+      if (pb + 16 <= M) {
+        float4* a4 = reinterpret_cast<float4*>(arow + pb);
+        float4 o[4];
 #pragma unroll
-      for (int u = 0; u < 16; ++u) {
-        const int n = c0 + u;
-        if (n < 2 * N) {
-          const float val = v[u] * scale;
-          accw[(long)n * Mp] = old[u] + val;
-          if (tb_out) put_term(tb_out, lo_kind, (long)w * 2 * N, N, Mp, n / N, n % N, p, val);
+        for (int k = 0; k < 4; ++k) o[k] = a4[k];
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          a4[k] = make_float4(o[k].x + v[4 * k], o[k].y + v[4 * k + 1], o[k].z + v[4 * k + 2],
+                              o[k].w + v[4 * k + 3]);
+        if (tb_out) {
+          if (c == 0) {
+            store16_lo(tb_out, lo_kind, rr + pb, v, 1.f);
+            store16_lo(tb_out, lo_kind, ri + Mp + pb, v, 1.f);
+          } else {
+            store16_lo(tb_out, lo_kind, rr + Mp + pb, v, -1.f);
+            store16_lo(tb_out, lo_kind, ri + pb, v, 1.f);
+          }
         }
+      } else {
+        for (int u = 0; u < 16 && pb + u < M; ++u) {
+          arow[pb + u] += v[u];
+          if (tb_out) put_term(tb_out, lo_kind, (long)w * 2 * N, N, Mp, c, i, pb + u, v[u]);
+        }
+      }
+    }
+  }
+};
+
+// V = i sqrt(dt) sum_g x_g L_g straight into the Taylor operand: rows (w, c)
+// of the field matrix (c = 0: Re x, c = 1: Im x), columns (p, q) = p * Mp + q
+// of the full Cholesky vectors; Re V = -sqrt(dt) (Im x . L) and Im V =
+// sqrt(dt) (Re x . L) land in row (w, p) of [Re V | Im V] at column q or
+// Mp + q, 16 consecutive q per thread (pad columns come out zero).
+struct EpiV {
+  static constexpr int kSmemBytes = 0;
+  void* V;
+  int lo_kind, W, M, Mp;
+  float sdt;
+  __device__ __forceinline__ int m_origin(int bx, int) const { return bx * BM; }
+  __device__ __forceinline__ int n_origin(int, int by) const { return by * 256; }
+  template <int BN>
+  __device__ __forceinline__ void run(uint32_t tmem, int q, int lane, int, int, int, int m0, int n0,
+                                      int, int, float*) const {
+    const int row = m0 + 32 * q + lane;
+    const bool valid = row < 2 * W;
+    const int w = row >> 1, c = row & 1;
+    const float sign = c ? -sdt : sdt;
+#pragma unroll 1
+    for (int c0 = 0; c0 < BN; c0 += 16) {
+      float v[16];
+      tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c0, v);
+      const int col = n0 + c0;  // p * Mp + q0, q0 a multiple of 16 within row p
+      const int p = col / Mp, q0 = col % Mp;
+      if (!valid || p >= M) continue;
+      const long base = ((long)w * M + p) * 2L * Mp + (c ? 0 : Mp) + q0;
+      if (q0 + 16 <= Mp) {
+        store16_lo(V, lo_kind, base, v, sign);
+      } else {
+        for (int u = 0; u < Mp - q0; ++u) store_lo(V, lo_kind, base + u, sign * v[u]);
       }
     }
   }
@@ -816,13 +877,26 @@ int tc_prop_first(const TcGemm& g, float* acc, void* tb, int lo_kind, int N, int
 
 int tc_taylor_term(const TcGemm& g, float* acc, void* tb_out, int lo_kind, int W, int N, int M,
                    int Mp, float scale, cudaStream_t st) {
-  if (2 * N > 64) {
-    set_error("tc taylor: 2N=%d above the 64-column tile", 2 * N);
+  if (2 * N > tc::BM) {
+    set_error("tc taylor: 2N=%d above the 128-row tile", 2 * N);
     return AFQMC_EUNSUPPORTED;
   }
   tc::EpiTaylor e{acc, tb_out, lo_kind, N, M, Mp, scale};
-  if (g.tf32) return launch_tc_persistent<64, 8, true>(g, e, cdiv(M, tc::BM), W, st);
-  return launch_tc_persistent<64, 8, false>(g, e, cdiv(M, tc::BM), W, st);
+  constexpr int BN = tc::EpiTaylor::kBN;
+  if (g.tf32) return launch_tc_persistent<BN, 6, true>(g, e, cdiv(M, BN), W, st);
+  return launch_tc_persistent<BN, 6, false>(g, e, cdiv(M, BN), W, st);
+}
+
+int tc_v_full(const TcGemm& g, void* V, int lo_kind, int W, int M, int Mp, double sdt,
+              cudaStream_t st) {
+  if (Mp % 16) {
+    set_error("tc V: Mp=%d must be a multiple of 16", Mp);
+    return AFQMC_EINVAL;
+  }
+  tc::EpiV e{V, lo_kind, W, M, Mp, (float)sdt};
+  const int gx = cdiv(g.m, tc::BM), gy = cdiv(g.n, 256);
+  if (g.tf32) return launch_tc_persistent<256, 4, true>(g, e, gx, gy, st);
+  return launch_tc_persistent<256, 4, false>(g, e, gx, gy, st);
 }
 
 int tc_prop_last(const TcGemm& g, double* phiT, const double* wt, int N, int M,

@@ -201,6 +201,9 @@ int launch_sumsq(const double* v, double* out, int n, cudaStream_t st);
 int launch_convert_lo(const double* src, long rows, long cols, long lds, void* dst, long ldd,
                       int kind, cudaStream_t st);
 int launch_convert_f32(const double* src, float* dst, long n, cudaStream_t st);
+// full Cholesky vectors transposed, rows (p, q) = p * Mp + q, pitch Gp, low precision
+int launch_pack_full_lo(const double* L, int G, int M, int Mp, int Gp, void* out, int kind,
+                        cudaStream_t st);
 // [Re V | Im V] rows (pitch 2 Mp) for the tensor-core Taylor terms, from packed Y
 int launch_unpack_v(const float* Y, long ldy, int W, int M, int Mp, double sdt, void* V, int kind,
                     cudaStream_t st);

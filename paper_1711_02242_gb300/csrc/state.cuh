@@ -27,8 +27,9 @@ struct Bufs {
   bool mixed = false;
   int lo_kind = 0, lo_bytes = 0, Gp = 0, Mp = 0;
   long Pp = 0;
-  void *LpT_lo = nullptr, *Lh_lo = nullptr, *x_lo = nullptr, *th_lo = nullptr;
-  float *t32 = nullptr, *Y32 = nullptr;
+  // LfT_lo: full Cholesky vectors transposed, rows (p, q) = p * Mp + q, pitch Gp
+  void *LfT_lo = nullptr, *Lh_lo = nullptr, *x_lo = nullptr, *th_lo = nullptr;
+  float* t32 = nullptr;
   // tensor-core propagation: exp(-dt v0'/2) as BF16/TF32 and TF32 [M][Mp],
   // V operand [W*M][2Mp], orbitals [W*2N][Mp], series sum [W*2N][Mp] FP32,
   // two Taylor-term operands [W*2N][2Mp]

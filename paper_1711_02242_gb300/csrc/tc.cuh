@@ -33,6 +33,10 @@ int tc_taylor_term(const TcGemm& g, float* acc, void* tb_out, int lo_kind, int W
                    int Mp, float scale, cudaStream_t st);
 int tc_prop_last(const TcGemm& g, double* phiT, const double* wt, int N, int M,
                  cudaStream_t st);
+// V = i sqrt(dt) sum_g x_g L_g from the full transposed vectors (rows p*Mp+q)
+// written directly as [Re V | Im V] rows (pitch 2 Mp) of each walker.
+int tc_v_full(const TcGemm& g, void* V, int lo_kind, int W, int M, int Mp, double sdt,
+              cudaStream_t st);
 
 void exchange_tile(int N, int* RG, int* CW);
 int tc_exchange(const TcGemm& g, int G, int W, int N, double* part, int nchunk, cudaStream_t st);

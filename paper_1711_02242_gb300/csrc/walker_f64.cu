@@ -1149,9 +1149,51 @@ __global__ void k_convert_f32(const double* src, float* dst, long n) {
     dst[i] = (float)src[i];
 }
 
+// Full Cholesky vectors, transposed, in BF16/TF32 for the mixed V contraction:
+// row (p, q) = p * Mp + q holds L[g][p][q] over g (pitch Gp); rows with q >= M
+// and columns g >= G are zero.  32 x 32 tiles of (q, g) per block, one p.
+__global__ void k_pack_full_lo(const double* L, int G, int M, int Mp, int Gp, void* out, int kind) {
+  __shared__ double tile[32][33];
+  const int g0 = blockIdx.x * 32, p = blockIdx.y, q0 = blockIdx.z * 32;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int g = g0 + r, q = q0 + threadIdx.x;
+    tile[r][threadIdx.x] = (g < G && q < M) ? L[((long)g * M + p) * M + q] : 0.0;
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int q = q0 + r, g = g0 + threadIdx.x;
+    if (q < Mp && g < Gp) store_lo(out, kind, ((long)p * Mp + q) * Gp + g, tile[threadIdx.x][r]);
+  }
+}
+
+int launch_pack_full_lo(const double* L, int G, int M, int Mp, int Gp, void* out, int kind,
+                        cudaStream_t st) {
+  dim3 grid(cdiv(Gp, 32), M, cdiv(Mp, 32));
+  AFQ_LAUNCH(k_pack_full_lo, grid, dim3(32, 8), 0, st, L, G, M, Mp, Gp, out, kind);
+  return AFQMC_OK;
+}
+
 int launch_convert_f32(const double* src, float* dst, long n, cudaStream_t st) {
   if (n <= 0) return AFQMC_OK;
   AFQ_LAUNCH(k_convert_f32, 152 * 4, 256, 0, st, src, dst, n);
+  return AFQMC_OK;
+}
+}  // namespace afq
+
+// ------------------------------------------------------------ bounded wait --
+namespace afq {
+__global__ void k_wait_flag(const int* flag, long long max_polls, int* status) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const volatile int* f = flag;
+  for (long long i = 0; i < max_polls; ++i) {
+    if (*f) return;
+    __nanosleep(1000);
+  }
+  *status = AFQMC_ETIMEOUT;
+}
+
+int launch_wait_flag(const int* flag, long long max_polls, int* status, cudaStream_t st) {
+  AFQ_LAUNCH(k_wait_flag, 1, 32, 0, st, flag, max_polls, status);
   return AFQMC_OK;
 }
 }  // namespace afq
