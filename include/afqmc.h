@@ -298,6 +298,34 @@ AFQMC_API int afqmc_contract(int32_t dtype, int64_t m, int64_t n, int64_t k, con
                              int64_t ldc, int* d_status, void* stream);
 
 /*
+ * The truncated Taylor expansion of exp(V) of Sec. 3.4.2 as the mixed path
+ * applies it, on the tcgen05 tensor cores: for every walker w
+ *     acc_w <- acc_w + sum_{k=1..order} T_k,   T_k = V_w T_{k-1} / k,
+ * with T_0 given (acc_w holds T_0 on entry in the propagation step, so that
+ * it leaves with exp(V_w) T_0 to order `order`).  T_k is rounded to the
+ * operand type before it multiplies V; products accumulate in FP32.
+ *   dtype    0: BF16 operands; 1: FP32 containers holding TF32 values
+ *   Mp       padded orbital count, a multiple of 16, Mp >= M
+ *   dV       [nwalkers][M][2 Mp]   row p = [Re V[p][0..Mp) | Im V[p][0..Mp)]
+ *                                   (columns q >= M zero)
+ *   dT0      [nwalkers][2N][2 Mp]  the 0th term as operand rows:
+ *                                   row i      = [Re T_i | -Im T_i]
+ *                                   row N + i  = [Im T_i |  Re T_i]
+ *                                   with T_i[p] = T[p][i] (columns p >= M zero)
+ *   dT1      same shape as dT0: scratch of the per-term route (may be NULL
+ *            when the whole-series kernel runs); dT0 and dT1 are overwritten
+ *   dacc     [nwalkers][2N][Mp] FP32: row i = Re T_i, row N + i = Im T_i
+ *   per_term 0: one launch for the whole series when the term fits in shared
+ *            memory (else per term); 1: one launch per term
+ *   d_status DEVICE int, set non-zero if a bounded wait timed out
+ * All buffers DEVICE, caller-owned, 16-byte aligned.  Requires 2N <= 128.
+ * Returns AFQMC_EINVAL on bad sizes or pointers.  Asynchronous on `stream`.
+ */
+AFQMC_API int afqmc_taylor_series(int32_t dtype, int64_t nwalkers, int64_t N, int64_t M,
+                                  int64_t Mp, int32_t order, const void* dV, void* dT0, void* dT1,
+                                  float* dacc, int32_t per_term, int* d_status, void* stream);
+
+/*
  * The counter-based generator behind the auxiliary fields: Philox4x32 with
  * 10 rounds (J. K. Salmon et al., "Parallel random numbers: as easy as 1, 2,
  * 3", SC'11), key = (key & 0xffffffff, key >> 32).

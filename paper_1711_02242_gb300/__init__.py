@@ -32,7 +32,7 @@ EXPORTED = ["afqmc_default_params", "afqmc_workspace_size", "afqmc_init", "afqmc
             "afqmc_philox4x32_10", "afqmc_gaussian_fields", "afqmc_contract",
             "afqmc_profile_start", "afqmc_profile_stop", "afqmc_local_energies_noalloc",
             "afqmc_group_create", "afqmc_group_propagate", "afqmc_group_destroy",
-            "afqmc_wait_flag"]
+            "afqmc_wait_flag", "afqmc_taylor_series"]
 
 
 class Params(ctypes.Structure):
@@ -103,6 +103,8 @@ def lib():
         "afqmc_group_propagate": (ctypes.c_int, [vp, ctypes.c_int32]),
         "afqmc_group_destroy": (ctypes.c_int, [vp]),
         "afqmc_wait_flag": (ctypes.c_int, [vp, ctypes.c_int64, vp, vp]),
+        "afqmc_taylor_series": (ctypes.c_int, [ctypes.c_int32] + [ctypes.c_int64] * 4 +
+                                [ctypes.c_int32, vp, vp, vp, vp, ctypes.c_int32, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)

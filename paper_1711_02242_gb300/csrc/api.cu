@@ -333,9 +333,9 @@ static int propagate_f64(afqmc_state* s) {
   return AFQMC_OK;
 }
 
-// Mixed propagation: the same sequence with x and the Cholesky vectors in
-// BF16/TF32 on the tensor cores (FP32 accumulation) and the B_half products
-// and Taylor terms in FP32 on the CUDA cores; the orbitals stay float64.
+// Mixed propagation: the same sequence with every contraction on the tensor
+// cores (BF16 or TF32 operands, FP32 accumulation): V, the first half step,
+// the Taylor series and the last half step (TF32); the orbitals stay float64.
 static int propagate_mixed(afqmc_state* s) {
   const afqmc_params& p = s->p;
   const Bufs& b = s->b;
@@ -379,27 +379,11 @@ static int propagate_mixed(afqmc_state* s) {
   h1.err = b.status;
   AFQ_TRY(tc_prop_first(h1, b.acc32, b.Tb0, b.lo_kind, N, M, b.Mp, s->st));
   prof_end(s);
-  // terms k = 1..n: T_k = V T_{k-1} / k, acc += T_k
+  // terms k = 1..n: T_k = V T_{k-1} / k, acc += T_k; the whole series in one
+  // launch when the term fits in shared memory, else one launch per term
   prof_begin(s, AFQMC_PH_TAYLOR);
-  void* tin = b.Tb0;
-  void* tout = b.Tb1;
-  for (int k = 1; k <= p.taylor_order; ++k) {
-    TcGemm tg;
-    tg.m = W * 2 * N;  // A: the term's operand rows (w, c, i)
-    tg.n = W * M;      // B: [Re V | Im V] rows (w, p)
-    tg.k = 2 * b.Mp;
-    tg.A = tin;
-    tg.lda = 2L * b.Mp;
-    tg.B = b.V_lo;
-    tg.ldb = 2L * b.Mp;
-    tg.tf32 = b.lo_kind == LO_TF32;
-    tg.err = b.status;
-    AFQ_TRY(tc_taylor_term(tg, b.acc32, k < p.taylor_order ? tout : nullptr, b.lo_kind, W, N, M,
-                           b.Mp, 1.0f / (float)k, s->st));
-    void* t_ = tin;
-    tin = tout;
-    tout = t_;
-  }
+  AFQ_TRY(taylor_apply(b.V_lo, b.Tb0, b.Tb1, b.acc32, b.lo_kind, W, N, M, b.Mp, p.taylor_order,
+                       false, b.status, s->st));
   prof_end(s);
   // last half step (TF32 on the FP32 series sum): Phi <- B_half acc, live walkers
   prof_begin(s, AFQMC_PH_BHALF);

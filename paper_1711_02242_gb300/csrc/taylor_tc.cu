@@ -1,0 +1,377 @@
+// Whole Taylor series of exp(V) for one walker per CTA (Sec. 3.4.2, the
+// truncated expansion of the exponential of the one-body operator) on tcgen05.
+//
+// For walker w the terms T_k = V T_{k-1} / k, k = 1..n, are formed one after
+// another and added to the running sum acc (FP32, holds T_0 on entry); the
+// last half step then consumes acc.  Per-term launches would stream every
+// walker's V from HBM n times; here a CTA keeps the term in shared memory and
+// streams only V, which after the first term comes from L2.
+//
+//   A operand  [Re V | Im V] rows p of walker w (128-row tiles, K = 2 Mp),
+//              TMA ring of 128 x 128-byte boxes;
+//   B operand  the term T_{k-1} as K-major rows n = (c, i):
+//                 row (0, i) = [Re T_i | -Im T_i],  row (1, i) = [Im T_i | Re T_i]
+//              (NB = 2N rounded up to 16 rows), resident in shared memory in
+//              the 128-byte-swizzled layout TMA writes, one 1024-byte-aligned
+//              block of NB x 128 bytes per 128 bytes of K;
+//   D          TMEM lane p of p-tile pt, column pt * NB + n: (V T_{k-1})[p][n].
+//
+// The epilogue warps read D, add T_k = D / k to acc and, unless k = n, write
+// T_k into the B operand in place (every MMA of term k has completed by then),
+// then release the MMA thread for term k + 1.  Warp roles: warp 0 TMA
+// producer, warp 1 TMEM allocation and the MMA thread, warps 2-5 epilogue.
+// Every wait is bounded; on time-out the kernel records an error and stops.
+#include <cuda_bf16.h>
+
+#include "kernels.cuh"
+#include "tc.cuh"
+#include "tc_dev.cuh"
+
+namespace afq {
+namespace tc {
+
+constexpr int kVBox = BM * BKB;  // one V tile in the ring: 128 rows x 128 bytes
+
+struct SeriesArgs {
+  float* acc;   // [W][2N][Mp]
+  int W, M, N, Mp, order;
+  int nb;       // rows of the term operand (2N rounded up to 16) = MMA N
+  int kblocks;  // 128-byte K blocks covering 2 Mp
+  int ptiles;   // 128-row tiles covering p < M
+  int stages;   // depth of the V ring
+  uint32_t tcols;
+};
+
+// One element of the term operand (row r, K column kcol) in the swizzled layout.
+template <bool TF32>
+__device__ __forceinline__ void put_op(uint8_t* bop, int nb, int r, int kcol, float v) {
+  constexpr int ELEM = TF32 ? 4 : 2;
+  constexpr int BK = BKB / ELEM;
+  const int kb = kcol / BK;
+  const uint32_t byte = (uint32_t)(kcol - kb * BK) * ELEM;
+  const uint32_t off = (uint32_t)kb * (uint32_t)nb * BKB + (uint32_t)(r >> 3) * 1024u +
+                       (uint32_t)(r & 7) * 128u + ((((byte >> 4) ^ (uint32_t)(r & 7)) << 4) | (byte & 15u));
+  if constexpr (TF32)
+    *reinterpret_cast<float*>(bop + off) = round_tf32(v);
+  else
+    *reinterpret_cast<__nv_bfloat16*>(bop + off) = __float2bfloat16_rn(v);
+}
+
+// Named barrier over the 128 epilogue threads that also ORs a flag across them,
+// so every epilogue warp takes the same branch.
+__device__ __forceinline__ bool epi_sync_or(bool flag) {
+  uint32_t out;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 q, %1, 0;\n\t"
+      "bar.red.or.pred p, 1, 128, q;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(out)
+      : "r"((uint32_t)flag)
+      : "memory");
+  return out != 0;
+}
+
+template <bool TF32>
+__global__ void __launch_bounds__(192, 1)
+    k_taylor_series(const __grid_constant__ CUtensorMap tmV, const __grid_constant__ CUtensorMap tmT,
+                    SeriesArgs a, int* err) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                             ~uintptr_t(1023));
+  const uint32_t opk = (uint32_t)a.nb * BKB;  // bytes of one K block of the term operand
+  uint8_t* bop = smem;
+  uint8_t* ring = smem + (size_t)a.kblocks * opk;
+  uint64_t* full = reinterpret_cast<uint64_t*>(ring + (size_t)a.stages * kVBox);
+  uint64_t* empty = full + a.stages;
+  uint64_t* bfull = empty + a.stages;  // T_0 of the walker has landed
+  uint64_t* bfree = bfull + 1;         // the walker's last MMAs are done: operand space free
+  uint64_t* dfull = bfree + 1;         // a term's product is complete in TMEM
+  uint64_t* bnext = dfull + 1;         // epilogue done with a term (TMEM read, next term written)
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bnext + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  constexpr int ELEM = TF32 ? 4 : 2;
+  constexpr int BK = BKB / ELEM;
+  constexpr int KSTEPS = BKB / 32;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < a.stages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(bfull, 1);
+    mbar_init(bfree, 1);
+    mbar_init(dfull, 1);
+    mbar_init(bnext, 128);  // every epilogue thread arrives
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(a.tcols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // producer: per walker T_0 once, then the V tiles of every term
+    int it = 0, j = 0;
+    bool stop = false;
+    for (int w = blockIdx.x; w < a.W && !stop; w += gridDim.x, ++j) {
+      if (j > 0 && !mbar_wait(bfree, (j - 1) & 1, err, 31)) {
+        stop = true;
+        break;
+      }
+      mbar_expect_tx(bfull, (uint32_t)a.kblocks * opk);
+      for (int kb = 0; kb < a.kblocks; ++kb) tma_load_3d(bop + kb * opk, &tmT, bfull, kb * BK, 0, w);
+      for (int k = 1; k <= a.order && !stop; ++k)
+        for (int pt = 0; pt < a.ptiles && !stop; ++pt)
+          for (int kb = 0; kb < a.kblocks; ++kb, ++it) {
+            const int s = it % a.stages;
+            if ((it >= a.stages && !mbar_wait(&empty[s], ((it / a.stages) - 1) & 1, err, 32)) ||
+                *abort_flag) {
+              stop = true;
+              break;
+            }
+            mbar_expect_tx(&full[s], kVBox);
+            tma_load_3d(ring + s * kVBox, &tmV, &full[s], kb * BK, pt * BM, w);
+          }
+    }
+    if (stop) *abort_flag = 1;
+  } else if (warp == 1 && lane == 0) {
+    // MMA thread
+    const uint32_t idesc = instr_desc(TF32 ? 2u : 1u, (uint32_t)a.nb);
+    int it = 0, g = 0, j = 0;
+    bool stop = false;
+    for (int w = blockIdx.x; w < a.W && !stop; w += gridDim.x, ++j) {
+      for (int k = 1; k <= a.order; ++k, ++g) {
+        if ((k == 1 && !mbar_wait(bfull, j & 1, err, 33)) ||
+            (g > 0 && !mbar_wait(bnext, (g - 1) & 1, err, 34)) || *abort_flag) {
+          stop = true;
+          break;
+        }
+        fence_after();
+        for (int pt = 0; pt < a.ptiles && !stop; ++pt) {
+          const uint32_t d = tmem + (uint32_t)(pt * a.nb);
+          for (int kb = 0; kb < a.kblocks; ++kb, ++it) {
+            const int s = it % a.stages;
+            if (!mbar_wait(&full[s], (it / a.stages) & 1, err, 35)) {
+              *abort_flag = 1;
+              stop = true;
+              break;
+            }
+            fence_after();
+            const uint32_t av = smem_u32(ring + s * kVBox);
+            const uint32_t bv = smem_u32(bop + kb * opk);
+#pragma unroll
+            for (int kk = 0; kk < KSTEPS; ++kk)
+              mma<TF32>(d, sw128_desc(av + 32 * kk), sw128_desc(bv + 32 * kk), idesc,
+                        (kb > 0 || kk > 0) ? 1u : 0u);
+            mma_commit(&empty[s]);
+          }
+        }
+        mma_commit(dfull);
+        if (k == a.order) mma_commit(bfree);
+        if (stop) break;
+      }
+    }
+    if (stop) *abort_flag = 1;
+  } else if (warp >= 2) {
+    // epilogue: warp quarter q holds TMEM lanes (p within the tile) 32q .. 32q + 31
+    const int q = warp & 3, twoN = 2 * a.N;
+    int g = 0;
+    bool stop = false;
+    for (int w = blockIdx.x; w < a.W && !stop; w += gridDim.x) {
+      for (int k = 1; k <= a.order; ++k, ++g) {
+        bool bad = !mbar_wait(dfull, g & 1, err, 36) || *abort_flag;
+        fence_after();
+        if (epi_sync_or(bad)) {
+          stop = true;
+          break;
+        }
+        const float scale = 1.0f / (float)k;
+        const bool next = k < a.order;
+#pragma unroll 1
+        for (int pt = 0; pt < a.ptiles; ++pt) {
+          const int p = pt * BM + 32 * q + lane;
+          const bool pv = p < a.M;
+#pragma unroll 1
+          for (int c0 = 0; c0 < twoN; c0 += 16) {
+            float v[16];
+            tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(pt * a.nb + c0), v);
+            if (!pv) continue;
+            float* arow = a.acc + ((long)w * twoN + c0) * a.Mp + p;
+            float o[16];
+#pragma unroll
+            for (int u = 0; u < 16; ++u)
+              if (c0 + u < twoN) o[u] = arow[(long)u * a.Mp];
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+              const int n = c0 + u;
+              if (n >= twoN) break;
+              const float t = v[u] * scale;
+              arow[(long)u * a.Mp] = o[u] + t;
+              if (next) {
+                if (n < a.N) {
+                  put_op<TF32>(bop, a.nb, n, p, t);
+                  put_op<TF32>(bop, a.nb, a.N + n, a.Mp + p, t);
+                } else {
+                  put_op<TF32>(bop, a.nb, n - a.N, a.Mp + p, -t);
+                  put_op<TF32>(bop, a.nb, n, p, t);
+                }
+              }
+            }
+          }
+        }
+        // generic-proxy writes of the next term -> visible to the MMA (async proxy)
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        fence_before();
+        mbar_arrive(bnext);
+      }
+    }
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(a.tcols));
+  }
+}
+
+}  // namespace tc
+
+namespace {
+constexpr int kSmemMax = 232448;
+constexpr int kSmemFixed = 1024 /*align*/ + 256 /*barriers*/;
+
+bool series_plan(int lo_kind, int N, int M, int Mp, tc::SeriesArgs* sa, int* smem) {
+  if (N < 1 || M < 1 || Mp < M || Mp % 16) return false;
+  const int elem = lo_kind == LO_TF32 ? 4 : 2;
+  const int nb = (2 * N + 15) / 16 * 16;
+  const int kblocks = (2 * Mp * elem + tc::BKB - 1) / tc::BKB;
+  const int ptiles = (M + tc::BM - 1) / tc::BM;
+  if (nb > 256 || ptiles * nb > 512) return false;
+  const long op = (long)kblocks * nb * tc::BKB;
+  long room = kSmemMax - kSmemFixed - op;
+  int stages = (int)(room / tc::kVBox);
+  if (stages > 8) stages = 8;
+  if (stages < 2) return false;
+  uint32_t tcols = 32;
+  while (tcols < (uint32_t)(ptiles * nb)) tcols <<= 1;
+  if (sa) {
+    sa->nb = nb;
+    sa->kblocks = kblocks;
+    sa->ptiles = ptiles;
+    sa->stages = stages;
+    sa->tcols = tcols;
+  }
+  if (smem) *smem = (int)(op + (long)stages * tc::kVBox + kSmemFixed);
+  return true;
+}
+}  // namespace
+
+bool tc_taylor_series_fits(int lo_kind, int N, int M, int Mp) {
+  return series_plan(lo_kind, N, M, Mp, nullptr, nullptr);
+}
+
+int tc_taylor_series(const void* V, const void* T0, float* acc, int lo_kind, int W, int N, int M,
+                     int Mp, int order, int* err, cudaStream_t st) {
+  tc::SeriesArgs sa{};
+  int smem = 0;
+  if (!series_plan(lo_kind, N, M, Mp, &sa, &smem)) {
+    set_error("taylor series kernel: shape N=%d M=%d does not fit", N, M);
+    return AFQMC_EUNSUPPORTED;
+  }
+  if (W <= 0 || order <= 0) return AFQMC_OK;
+  sa.acc = acc;
+  sa.W = W;
+  sa.M = M;
+  sa.N = N;
+  sa.Mp = Mp;
+  sa.order = order;
+  const bool tf32 = lo_kind == LO_TF32;
+  const int eb = tf32 ? 4 : 2;
+  CUtensorMap tv, tt;
+  AFQ_TRY(make_tmap_3d(&tv, V, eb, W, M, 2L * Mp, 2L * Mp, (long)M * 2 * Mp, tc::BM));
+  AFQ_TRY(make_tmap_3d(&tt, T0, eb, W, 2L * N, 2L * Mp, 2L * Mp, 2L * N * 2 * Mp, sa.nb));
+  const int grid = W < tc_sm_count() ? W : tc_sm_count();
+  if (tf32) {
+    static bool attr = false;
+    if (!attr) {
+      AFQ_CUDA(cudaFuncSetAttribute(tc::k_taylor_series<true>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax));
+      attr = true;
+    }
+    AFQ_LAUNCH(tc::k_taylor_series<true>, grid, 192, smem, st, tv, tt, sa, err);
+  } else {
+    static bool attr = false;
+    if (!attr) {
+      AFQ_CUDA(cudaFuncSetAttribute(tc::k_taylor_series<false>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax));
+      attr = true;
+    }
+    AFQ_LAUNCH(tc::k_taylor_series<false>, grid, 192, smem, st, tv, tt, sa, err);
+  }
+  return AFQMC_OK;
+}
+
+int taylor_apply(const void* V, void* T0, void* T1, float* acc, int lo_kind, int W, int N, int M,
+                 int Mp, int order, bool per_term, int* err, cudaStream_t st) {
+  if (!per_term && tc_taylor_series_fits(lo_kind, N, M, Mp))
+    return tc_taylor_series(V, T0, acc, lo_kind, W, N, M, Mp, order, err, st);
+  // one launch per term, the term as the A operand (rows (w, c, i)); the
+  // operand alternates between T0 and T1
+  void* tin = T0;
+  void* tout = T1;
+  for (int k = 1; k <= order; ++k) {
+    TcGemm tg;
+    tg.m = W * 2 * N;
+    tg.n = W * M;
+    tg.k = 2 * Mp;
+    tg.A = tin;
+    tg.lda = 2L * Mp;
+    tg.B = V;
+    tg.ldb = 2L * Mp;
+    tg.tf32 = lo_kind == LO_TF32;
+    tg.err = err;
+    AFQ_TRY(tc_taylor_term(tg, acc, k < order ? tout : nullptr, lo_kind, W, N, M, Mp,
+                           1.0f / (float)k, st));
+    void* t_ = tin;
+    tin = tout;
+    tout = t_;
+  }
+  return AFQMC_OK;
+}
+
+}  // namespace afq
+
+extern "C" int afqmc_taylor_series(int32_t dtype, int64_t nwalkers, int64_t N, int64_t M,
+                                   int64_t Mp, int32_t order, const void* dV, void* dT0, void* dT1,
+                                   float* dacc, int32_t per_term, int* d_status, void* stream) {
+  using namespace afq;
+  const int lo_kind = dtype == 1 ? LO_TF32 : LO_BF16;
+  const bool bad_dims = (dtype != 0 && dtype != 1) || nwalkers < 0 || N < 1 || M < 1 || Mp < M ||
+                        Mp % 16 || order < 1 || order > 64 || 2 * N > 128 ||
+                        nwalkers * 2 * N * 2 * Mp > (1ll << 31) - 1 ||
+                        nwalkers * M * 2 * Mp > (1ll << 31) - 1;
+  if (bad_dims || !dV || !dT0 || !dacc || !d_status) {
+    set_error("afqmc_taylor_series: bad arguments");
+    return AFQMC_EINVAL;
+  }
+  const bool series = !per_term && tc_taylor_series_fits(lo_kind, (int)N, (int)M, (int)Mp);
+  if (!series && !dT1) {
+    set_error("afqmc_taylor_series: the per-term path needs dT1");
+    return AFQMC_EINVAL;
+  }
+  if ((reinterpret_cast<uintptr_t>(dV) | reinterpret_cast<uintptr_t>(dT0) |
+       reinterpret_cast<uintptr_t>(dT1) | reinterpret_cast<uintptr_t>(dacc)) % 16) {
+    set_error("afqmc_taylor_series: buffers must be 16-byte aligned");
+    return AFQMC_EINVAL;
+  }
+  return taylor_apply(dV, dT0, dT1, dacc, lo_kind, (int)nwalkers, (int)N, (int)M, (int)Mp, order,
+                      !series, d_status, static_cast<cudaStream_t>(stream));
+}

@@ -1,6 +1,8 @@
 // Tensor-core (tcgen05) contraction launchers (internal header).
 #pragma once
 
+#include <cuda.h>
+
 #include "common.cuh"
 
 namespace afq {
@@ -37,6 +39,29 @@ int tc_prop_last(const TcGemm& g, double* phiT, const double* wt, int N, int M,
 // written directly as [Re V | Im V] rows (pitch 2 Mp) of each walker.
 int tc_v_full(const TcGemm& g, void* V, int lo_kind, int W, int M, int Mp, double sdt,
               cudaStream_t st);
+
+// Whole Taylor series per walker in one launch (one CTA per walker at a time):
+// the term stays in shared memory and the walker's [Re V | Im V] rows are
+// streamed once per term (from L2 after the first).  T0: the 0th term operand
+// rows [W][2N][2Mp], V: [W][M][2Mp], acc: [W][2N][Mp] FP32 (holds T_0 on
+// entry, the series sum on exit).  tc_taylor_series_fits() says whether the
+// shape fits the kernel's shared memory and tensor memory.
+bool tc_taylor_series_fits(int lo_kind, int N, int M, int Mp);
+int tc_taylor_series(const void* V, const void* T0, float* acc, int lo_kind, int W, int N, int M,
+                     int Mp, int order, int* err, cudaStream_t st);
+
+// The series by whichever route fits: the whole-series kernel unless per_term
+// is set or the shape does not fit, else one launch per term (the operand
+// alternates between T0 and T1, so both are overwritten).
+int taylor_apply(const void* V, void* T0, void* T1, float* acc, int lo_kind, int W, int N, int M,
+                 int Mp, int order, bool per_term, int* err, cudaStream_t st);
+
+// tensor maps (128-byte swizzle, box = 128 bytes x box_rows)
+int make_tmap(CUtensorMap* m, const void* base, int elem_bytes, long rows, long cols, long pitch,
+              int box_rows);
+int make_tmap_3d(CUtensorMap* m, const void* base, int elem_bytes, long planes, long rows,
+                 long cols, long pitch, long plane_stride, int box_rows);
+int tc_sm_count();
 
 void exchange_tile(int N, int* RG, int* CW);
 int tc_exchange(const TcGemm& g, int G, int W, int N, double* part, int nchunk, cudaStream_t st);

@@ -1,0 +1,147 @@
+"""Taylor expansion of exp(V) on the tensor cores (afqmc_taylor_series).
+
+The reference repeats what the kernel is specified to do (Sec. 3.4.2 with the
+operands in BF16/TF32): T_k = V T_{k-1} / k formed from the rounded operands
+in float64, rounded to FP32 and then to the operand type before the next
+product, and summed into acc.  What is left between the two is FP32
+accumulation order (and the rare rounding flip it causes), so the bound is
+2e-5 relative; a dropped or mis-signed term moves acc by more than 1e-2 with
+|V| ~ 1.5.  Both routes (one launch for the whole series, one launch per
+term) are checked, including walker counts above one CTA per SM, so CTAs
+take several walkers in turn.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_1711_02242_gb300 as pkg
+
+    return torch, pkg
+
+
+def round_bf16(x):
+    u = np.asarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32)
+
+
+def round_tf32(x):
+    # round to nearest, ties away from zero, 10 explicit mantissa bits
+    u = np.asarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x1000) & 0xFFFFE000
+    return u.astype(np.uint32).view(np.float32)
+
+
+def operands(rng, W, N, M, Mp, rnd):
+    s = 0.75 / np.sqrt(M)
+    V = s * (rng.standard_normal((W, M, M)) + 1j * rng.standard_normal((W, M, M)))
+    T0 = (rng.standard_normal((W, M, N)) + 1j * rng.standard_normal((W, M, N))) / np.sqrt(M)
+    Vr, Vi = rnd(V.real), rnd(V.imag)
+    Tr, Ti = rnd(T0.real), rnd(T0.imag)
+    dV = np.zeros((W, M, 2 * Mp), np.float32)
+    dV[:, :, :M] = Vr
+    dV[:, :, Mp:Mp + M] = Vi
+    dT = np.zeros((W, 2 * N, 2 * Mp), np.float32)
+    trT, tiT = np.swapaxes(Tr, 1, 2), np.swapaxes(Ti, 1, 2)  # [W][N][M]
+    dT[:, :N, :M] = trT
+    dT[:, :N, Mp:Mp + M] = -tiT
+    dT[:, N:, :M] = tiT
+    dT[:, N:, Mp:Mp + M] = trT
+    acc = np.zeros((W, 2 * N, Mp), np.float32)
+    acc[:, :N, :M] = np.swapaxes(T0.real, 1, 2)
+    acc[:, N:, :M] = np.swapaxes(T0.imag, 1, 2)
+    Vlo = Vr.astype(np.float64) + 1j * Vi.astype(np.float64)
+    Tlo = Tr.astype(np.float64) + 1j * Ti.astype(np.float64)
+    return dV, dT, acc, Vlo, Tlo
+
+
+def reference(Vlo, Tlo, acc0, N, M, order, rnd):
+    acc = acc0.astype(np.float64)
+    T = Tlo
+    for k in range(1, order + 1):
+        D = Vlo @ T  # [W][M][N]
+        sc = np.float32(1.0 / np.float32(k))
+        tr = D.real.astype(np.float32) * sc
+        ti = D.imag.astype(np.float32) * sc
+        acc[:, :N, :M] += np.swapaxes(tr, 1, 2)
+        acc[:, N:2 * N, :M] += np.swapaxes(ti, 1, 2)
+        T = rnd(tr).astype(np.float64) + 1j * rnd(ti).astype(np.float64)
+    return acc
+
+
+def run(torch, pkg, dtype, dV, dT, acc, W, N, M, Mp, order, per_term):
+    dev = torch.device("cuda:0")
+    if dtype == 0:
+        tV = torch.from_numpy(dV).to(dev).to(torch.bfloat16).contiguous()
+        tT0 = torch.from_numpy(dT).to(dev).to(torch.bfloat16).contiguous()
+    else:
+        tV = torch.from_numpy(dV).to(dev)
+        tT0 = torch.from_numpy(dT).to(dev)
+    tT1 = torch.zeros_like(tT0)
+    tacc = torch.from_numpy(acc).to(dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    st = torch.cuda.current_stream(dev)
+    rc = pkg.lib().afqmc_taylor_series(
+        dtype, W, N, M, Mp, order, ctypes.c_void_p(tV.data_ptr()), ctypes.c_void_p(tT0.data_ptr()),
+        ctypes.c_void_p(tT1.data_ptr()), ctypes.c_void_p(tacc.data_ptr()), per_term,
+        ctypes.c_void_p(status.data_ptr()), ctypes.c_void_p(st.cuda_stream))
+    assert rc == 0, pkg.lib().afqmc_last_error()
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    return tacc.cpu().numpy().astype(np.float64)
+
+
+SHAPES = [  # dtype, W, N, M
+    (0, 3, 3, 12),
+    (0, 7, 10, 100),
+    (0, 5, 25, 300),    # three 128-row tiles of p, ragged K block
+    (1, 5, 25, 300),
+    (0, 3, 64, 200),    # 128 operand rows
+    (1, 3, 48, 300),    # TF32 term too large for shared memory: per-term route only
+    (0, 400, 5, 60),    # more walkers than SMs: CTAs take walkers in turn
+    (1, 333, 8, 130),
+]
+
+
+@pytest.mark.parametrize("dtype,W,N,M", SHAPES)
+def test_taylor_series_matches_reference(env, dtype, W, N, M):
+    torch, pkg = env
+    rnd = round_bf16 if dtype == 0 else round_tf32
+    Mp = (M + 15) // 16 * 16
+    order = 6
+    rng = np.random.default_rng(1000 + 7 * W + N + M + dtype)
+    dV, dT, acc, Vlo, Tlo = operands(rng, W, N, M, Mp, rnd)
+    ref = reference(Vlo, Tlo, acc, N, M, order, rnd)
+    # the series moves acc well above the tolerance, so a lost term shows
+    assert np.linalg.norm(ref - acc) > 0.3 * np.linalg.norm(acc)
+    for per_term in (0, 1):
+        got = run(torch, pkg, dtype, dV, dT, acc, W, N, M, Mp, order, per_term)
+        for w in range(W):
+            err = np.linalg.norm(got[w] - ref[w]) / np.linalg.norm(ref[w])
+            assert err < 2e-5, (per_term, w, err)
+        # padding columns are never written
+        assert np.all(got[:, :, M:] == 0)
+
+
+def test_taylor_series_rejects_bad_sizes(env):
+    torch, pkg = env
+    lib = pkg.lib()
+    buf = torch.zeros(1 << 16, dtype=torch.float32, device="cuda:0")
+    p = ctypes.c_void_p(buf.data_ptr())
+    st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    # Mp not a multiple of 16, Mp < M, 2N > 128, bad dtype, order 0
+    for args in [(0, 1, 2, 20, 20, 6), (0, 1, 2, 40, 32, 6), (0, 1, 65, 20, 32, 6),
+                 (3, 1, 2, 20, 32, 6), (0, 1, 2, 20, 32, 0)]:
+        assert lib.afqmc_taylor_series(*args, p, p, p, p, 0, p, st) == -1  # AFQMC_EINVAL
