@@ -4,9 +4,14 @@ The reference repeats what the kernel is specified to do (Sec. 3.4.2 with the
 operands in BF16/TF32): T_k = V T_{k-1} / k formed from the rounded operands
 in float64, rounded to FP32 and then to the operand type before the next
 product, and summed into acc.  What is left between the two is FP32
-accumulation order (and the rare rounding flip it causes), so the bound is
-2e-5 relative; a dropped or mis-signed term moves acc by more than 1e-2 with
-|V| ~ 1.5.  Both routes (one launch for the whole series, one launch per
+accumulation order and the operand-rounding flips it causes: a term element
+that lands on the other side of a BF16 (TF32) rounding boundary moves by one
+unit of 2^-8 (2^-11) and carries that into the later terms.  Replaying the
+reference with 3e-6 relative noise on every product (about FP32 accumulation
+over K = 2 Mp) moves acc by up to 9e-4 (BF16) and 1.2e-4 (TF32) per walker at
+these sizes, so the bound is 2.5e-3 (BF16) and 5e-4 (TF32) relative per
+walker; with |V| ~ 3 the last term alone is over 2e-2 of acc (checked), so a
+dropped or mis-signed term cannot pass.  Both routes (one launch for the whole series, one launch per
 term) are checked, including walker counts above one CTA per SM, so CTAs
 take several walkers in turn.
 """
@@ -45,7 +50,7 @@ def round_tf32(x):
 
 
 def operands(rng, W, N, M, Mp, rnd):
-    s = 0.75 / np.sqrt(M)
+    s = 1.5 / np.sqrt(M)
     V = s * (rng.standard_normal((W, M, M)) + 1j * rng.standard_normal((W, M, M)))
     T0 = (rng.standard_normal((W, M, N)) + 1j * rng.standard_normal((W, M, N))) / np.sqrt(M)
     Vr, Vi = rnd(V.real), rnd(V.imag)
@@ -68,8 +73,10 @@ def operands(rng, W, N, M, Mp, rnd):
 
 
 def reference(Vlo, Tlo, acc0, N, M, order, rnd):
+    """acc after the series, and the relative size of the last term per walker."""
     acc = acc0.astype(np.float64)
     T = Tlo
+    last = None
     for k in range(1, order + 1):
         D = Vlo @ T  # [W][M][N]
         sc = np.float32(1.0 / np.float32(k))
@@ -78,7 +85,8 @@ def reference(Vlo, Tlo, acc0, N, M, order, rnd):
         acc[:, :N, :M] += np.swapaxes(tr, 1, 2)
         acc[:, N:2 * N, :M] += np.swapaxes(ti, 1, 2)
         T = rnd(tr).astype(np.float64) + 1j * rnd(ti).astype(np.float64)
-    return acc
+        last = np.sqrt((tr.astype(np.float64) ** 2 + ti.astype(np.float64) ** 2).sum(axis=(1, 2)))
+    return acc, last / np.linalg.norm(acc.reshape(acc.shape[0], -1), axis=1)
 
 
 def run(torch, pkg, dtype, dV, dT, acc, W, N, M, Mp, order, per_term):
@@ -123,14 +131,14 @@ def test_taylor_series_matches_reference(env, dtype, W, N, M):
     order = 6
     rng = np.random.default_rng(1000 + 7 * W + N + M + dtype)
     dV, dT, acc, Vlo, Tlo = operands(rng, W, N, M, Mp, rnd)
-    ref = reference(Vlo, Tlo, acc, N, M, order, rnd)
-    # the series moves acc well above the tolerance, so a lost term shows
-    assert np.linalg.norm(ref - acc) > 0.3 * np.linalg.norm(acc)
+    ref, last = reference(Vlo, Tlo, acc, N, M, order, rnd)
+    tol = 2.5e-3 if dtype == 0 else 5e-4
+    # even the last term is well above the tolerance, so a lost term shows
+    assert np.all(last > 5 * tol), last.min()
     for per_term in (0, 1):
         got = run(torch, pkg, dtype, dV, dT, acc, W, N, M, Mp, order, per_term)
-        for w in range(W):
-            err = np.linalg.norm(got[w] - ref[w]) / np.linalg.norm(ref[w])
-            assert err < 2e-5, (per_term, w, err)
+        err = [np.linalg.norm(got[w] - ref[w]) / np.linalg.norm(ref[w]) for w in range(W)]
+        assert max(err) < tol, (per_term, int(np.argmax(err)), max(err))
         # padding columns are never written
         assert np.all(got[:, :, M:] == 0)
 
