@@ -300,10 +300,11 @@ AFQMC_API int afqmc_contract(int32_t dtype, int64_t m, int64_t n, int64_t k, con
 /*
  * The truncated Taylor expansion of exp(V) of Sec. 3.4.2 as the mixed path
  * applies it, on the tcgen05 tensor cores: for every walker w
- *     acc_w <- acc_w + sum_{k=1..order} T_k,   T_k = V_w T_{k-1} / k,
- * with T_0 given (acc_w holds T_0 on entry in the propagation step, so that
- * it leaves with exp(V_w) T_0 to order `order`).  T_k is rounded to the
- * operand type before it multiplies V; products accumulate in FP32.
+ *     S_w = T_1 + ... + T_order,   T_k = V_w T_{k-1} / k,
+ * with T_0 given, so that exp(V_w) T_0 = T_0 + S_w to order `order` (the
+ * propagation step then applies exp(-dt v0'/2) to T_0 + S_w).  T_k is rounded
+ * to the operand type before it multiplies V; products and S accumulate in
+ * FP32.
  *   dtype    0: BF16 operands; 1: FP32 containers holding TF32 values
  *   Mp       padded orbital count, a multiple of 16, Mp >= M
  *   dV       [nwalkers][M][2 Mp]   row p = [Re V[p][0..Mp) | Im V[p][0..Mp)]
@@ -314,16 +315,19 @@ AFQMC_API int afqmc_contract(int32_t dtype, int64_t m, int64_t n, int64_t k, con
  *                                   with T_i[p] = T[p][i] (columns p >= M zero)
  *   dT1      same shape as dT0: scratch of the per-term route (may be NULL
  *            when the whole-series kernel runs); dT0 and dT1 are overwritten
- *   dacc     [nwalkers][2N][Mp] FP32: row i = Re T_i, row N + i = Im T_i
- *   per_term 0: one launch for the whole series when the term fits in shared
- *            memory (else per term); 1: one launch per term
+ *   dS       [nwalkers][2N][ldS] FP32 output: row i = Re S_i, row N + i =
+ *            Im S_i (S_i[p] = S[p][i]); columns p >= M are not written;
+ *            ldS >= Mp, a multiple of 4
+ *   per_term 0: one launch for the whole series when the term and the sum fit
+ *            in shared and tensor memory (else per term); 1: one launch per term
  *   d_status DEVICE int, set non-zero if a bounded wait timed out
  * All buffers DEVICE, caller-owned, 16-byte aligned.  Requires 2N <= 128.
  * Returns AFQMC_EINVAL on bad sizes or pointers.  Asynchronous on `stream`.
  */
 AFQMC_API int afqmc_taylor_series(int32_t dtype, int64_t nwalkers, int64_t N, int64_t M,
                                   int64_t Mp, int32_t order, const void* dV, void* dT0, void* dT1,
-                                  float* dacc, int32_t per_term, int* d_status, void* stream);
+                                  float* dS, int64_t ldS, int32_t per_term, int* d_status,
+                                  void* stream);
 
 /*
  * The counter-based generator behind the auxiliary fields: Philox4x32 with

@@ -104,7 +104,8 @@ def lib():
         "afqmc_group_destroy": (ctypes.c_int, [vp]),
         "afqmc_wait_flag": (ctypes.c_int, [vp, ctypes.c_int64, vp, vp]),
         "afqmc_taylor_series": (ctypes.c_int, [ctypes.c_int32] + [ctypes.c_int64] * 4 +
-                                [ctypes.c_int32, vp, vp, vp, vp, ctypes.c_int32, vp, vp]),
+                                [ctypes.c_int32, vp, vp, vp, vp, ctypes.c_int64, ctypes.c_int32,
+                                 vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)

@@ -89,7 +89,7 @@ size_t plan(const afqmc_params& p, Bufs* b, char* base) {
     b->th_lo = a.take<char>(W * 2 * N * Mp * lo);
     b->t32 = a.take<float>(W * 2 * G);
     b->Bh_lo = a.take<char>(M * Mp * lo);
-    b->Bh_tf = a.take<float>(M * Mp);
+    b->Bh_tf = a.take<float>(M * 2 * Mp);
   }
   // scratch: the set-up and the step never run at the same time
   const size_t scratch_at = (a.off + 255) & ~size_t(255);
@@ -99,7 +99,7 @@ size_t plan(const afqmc_params& p, Bufs* b, char* base) {
     b->acc = nullptr;
     b->V_lo = s1.take<char>(W * M * 2 * Mp * lo);
     b->phi_lo = s1.take<char>(W * 2 * N * Mp * lo);
-    b->acc32 = s1.take<float>(W * 2 * N * Mp);
+    b->acc32 = s1.take<float>(W * 2 * N * 2 * Mp);
     b->Tb0 = s1.take<char>(W * 2 * N * 2 * Mp * lo);
     b->Tb1 = s1.take<char>(W * 2 * N * 2 * Mp * lo);
   } else {
@@ -364,7 +364,8 @@ static int propagate_mixed(afqmc_state* s) {
   g.err = b.status;
   AFQ_TRY(tc_v_full(g, b.V_lo, b.lo_kind, W, M, b.Mp, s->sdt, s->st));
   prof_end(s);
-  // first half step: acc = (B_half Phi)^T, Tb0 = the 0th Taylor term
+  // first half step: T_0 = (B_half Phi)^T into columns [0, Mp) of the FP32
+  // rows of acc (pitch 2 Mp) and, as the 0th Taylor operand, into Tb0
   prof_begin(s, AFQMC_PH_BHALF);
   AFQ_TRY(launch_convert_lo(b.phiT, 2L * N * W, M, M, b.phi_lo, b.Mp, b.lo_kind, s->st));
   TcGemm h1;
@@ -377,24 +378,26 @@ static int propagate_mixed(afqmc_state* s) {
   h1.ldb = b.Mp;
   h1.tf32 = b.lo_kind == LO_TF32;
   h1.err = b.status;
-  AFQ_TRY(tc_prop_first(h1, b.acc32, b.Tb0, b.lo_kind, N, M, b.Mp, s->st));
+  AFQ_TRY(tc_prop_first(h1, b.acc32, 2L * b.Mp, b.Tb0, b.lo_kind, N, M, b.Mp, s->st));
   prof_end(s);
-  // terms k = 1..n: T_k = V T_{k-1} / k, acc += T_k; the whole series in one
-  // launch when the term fits in shared memory, else one launch per term
+  // terms k = 1..n: T_k = V T_{k-1} / k, S = T_1 + ... + T_n into columns
+  // [Mp, 2 Mp) of acc; the whole series in one launch when the term fits in
+  // shared memory, else one launch per term
   prof_begin(s, AFQMC_PH_TAYLOR);
-  AFQ_TRY(taylor_apply(b.V_lo, b.Tb0, b.Tb1, b.acc32, b.lo_kind, W, N, M, b.Mp, p.taylor_order,
-                       false, b.status, s->st));
+  AFQ_TRY(taylor_apply(b.V_lo, b.Tb0, b.Tb1, b.acc32 + b.Mp, 2L * b.Mp, b.lo_kind, W, N, M, b.Mp,
+                       p.taylor_order, false, b.status, s->st));
   prof_end(s);
-  // last half step (TF32 on the FP32 series sum): Phi <- B_half acc, live walkers
+  // last half step (TF32): Phi <- B_half (T_0 + S) as one K = 2 Mp product of
+  // [T_0 | S] with [B_half | B_half]; stored for live walkers
   prof_begin(s, AFQMC_PH_BHALF);
   TcGemm h2;
   h2.m = 2 * N * W;
   h2.n = M;
-  h2.k = M;
+  h2.k = 2 * b.Mp;
   h2.A = b.acc32;
-  h2.lda = b.Mp;
+  h2.lda = 2L * b.Mp;
   h2.B = b.Bh_tf;
-  h2.ldb = b.Mp;
+  h2.ldb = 2L * b.Mp;
   h2.tf32 = true;
   h2.err = b.status;
   AFQ_TRY(tc_prop_last(h2, b.phiT, b.wt, N, M, s->st));
@@ -600,7 +603,11 @@ static int setup_device(afqmc_state* s, const double* h1, const double* L, const
     AFQ_CUDA(cudaMemsetAsync(b.th_lo, 0, (size_t)W * 2 * N * b.Mp * b.lo_bytes, st));
     AFQ_CUDA(cudaMemsetAsync(b.x_lo, 0, (size_t)W * 2 * b.Gp * b.lo_bytes, st));
     AFQ_TRY(launch_convert_lo(b.Bh, M, M, M, b.Bh_lo, b.Mp, b.lo_kind, st));
-    AFQ_TRY(launch_convert_lo(b.Bh, M, M, M, b.Bh_tf, b.Mp, LO_TF32, st));
+    // [B_half | B_half] so that one K = 2 Mp product applies it to T_0 + S
+    AFQ_TRY(launch_convert_lo(b.Bh, M, M, M, b.Bh_tf, 2L * b.Mp, LO_TF32, st));
+    AFQ_CUDA(cudaMemcpy2DAsync(b.Bh_tf + b.Mp, sizeof(float) * 2 * b.Mp, b.Bh_tf,
+                               sizeof(float) * 2 * b.Mp, sizeof(float) * b.Mp, M,
+                               cudaMemcpyDeviceToDevice, st));
   }
   // walkers at the trial, their overlaps, and the trial energy
   AFQ_TRY(launch_init_walkers(b.VTt, b.phiT, b.wt, W, N, M, st));
@@ -616,7 +623,7 @@ static int setup_device(afqmc_state* s, const double* h1, const double* L, const
   if (b.mixed) {
     // the tensor-core operands read their padded columns: clear them once, now
     // that the set-up scratch these buffers alias is no longer needed
-    AFQ_CUDA(cudaMemsetAsync(b.acc32, 0, sizeof(float) * (size_t)W * 2 * N * b.Mp, st));
+    AFQ_CUDA(cudaMemsetAsync(b.acc32, 0, sizeof(float) * (size_t)W * 2 * N * 2 * b.Mp, st));
     AFQ_CUDA(cudaMemsetAsync(b.Tb0, 0, (size_t)W * 2 * N * 2 * b.Mp * b.lo_bytes, st));
     AFQ_CUDA(cudaMemsetAsync(b.Tb1, 0, (size_t)W * 2 * N * 2 * b.Mp * b.lo_bytes, st));
     // autotune the tile width of the force-bias contraction for this shape

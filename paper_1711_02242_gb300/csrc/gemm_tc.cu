@@ -404,11 +404,12 @@ __device__ __forceinline__ void store16_lo(void* base, int kind, long idx, const
 }
 
 // First half step: rows (w,c,i) of Phi^T, columns p; D = (B_half Phi)^T.
-// acc[(w,c,i)][p] = D (FP32, pitch Mp) and Tb holds the 0th Taylor term.
+// acc[(w,c,i)][p] = D (FP32, pitch ldacc) and Tb holds the 0th Taylor term.
 // Each thread owns one row and 16 consecutive p per chunk: vector stores.
 struct EpiProp0 {
   static constexpr int kSmemBytes = 0;
   float* acc;
+  long ldacc;
   void* tb;
   int lo_kind, N, M, Mp, rows;
   __device__ __forceinline__ int m_origin(int bx, int) const { return bx * BM; }
@@ -426,7 +427,7 @@ struct EpiProp0 {
       const int pb = n0 + c0;
       if (pb >= M) continue;
       if (pb + 16 <= M) {
-        float4* a4 = reinterpret_cast<float4*>(acc + (long)row * Mp + pb);
+        float4* a4 = reinterpret_cast<float4*>(acc + (long)row * ldacc + pb);
 #pragma unroll
         for (int k = 0; k < 4; ++k) a4[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
         const long rr = ((long)w * 2 * N + i) * 2L * Mp, ri = ((long)w * 2 * N + N + i) * 2L * Mp;
@@ -442,7 +443,7 @@ struct EpiProp0 {
         for (int u = 0; u < 16; ++u) {
           const int p = pb + u;
           if (p < M) {
-            acc[(long)row * Mp + p] = v[u];
+            acc[(long)row * ldacc + p] = v[u];
             put_term(tb, lo_kind, (long)w * 2 * N, N, Mp, c, i, p, v[u]);
           }
         }
@@ -451,9 +452,9 @@ struct EpiProp0 {
   }
 };
 
-// Taylor term k for walker w = blockIdx.y: rows p of [Vr | Vi] (a 128-row tile),
-// columns n < 2N of Tb_{k-1}; T_k = D / k is added to acc and, unless it is
-// the last term, written as the next operand.
+// Taylor term k for walker w: T_k = D / k goes to the series sum S (stored
+// for k = 1, added after) and, unless it is the last term, is written as the
+// next operand.
 // The MMA takes the term as A (rows n = (c, i) of Tb_{k-1}: a 128-row tile at
 // walker w = by, rows n >= 2N belong to the next walker and are ignored) and
 // [Vr | Vi] as B (columns p: tile bx of BN), so D[n][p] = (V T_{k-1})^T and
@@ -462,7 +463,9 @@ struct EpiProp0 {
 struct EpiTaylor {
   static constexpr int kSmemBytes = 0;
   static constexpr int kBN = 160;  // two tiles cover p < 320
-  float* acc;
+  float* S;
+  long lds;
+  int first;
   void* tb_out;
   int lo_kind, N, M, Mp;
   float scale;
@@ -474,7 +477,7 @@ struct EpiTaylor {
     const int w = by, n = 32 * q + lane;
     const bool valid = n < 2 * N;
     const int c = valid ? n / N : 0, i = valid ? n % N : 0;
-    float* arow = acc + ((long)w * 2 * N + n) * Mp;
+    float* arow = S + ((long)w * 2 * N + n) * lds;
     const long rr = ((long)w * 2 * N + i) * 2L * Mp, ri = ((long)w * 2 * N + N + i) * 2L * Mp;
 #pragma unroll 1
     for (int c0 = 0; c0 < BN; c0 += 16) {
@@ -488,7 +491,7 @@ struct EpiTaylor {
         float4* a4 = reinterpret_cast<float4*>(arow + pb);
         float4 o[4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) o[k] = a4[k];
+        for (int k = 0; k < 4; ++k) o[k] = first ? make_float4(0.f, 0.f, 0.f, 0.f) : a4[k];
 #pragma unroll
         for (int k = 0; k < 4; ++k)
           a4[k] = make_float4(o[k].x + v[4 * k], o[k].y + v[4 * k + 1], o[k].z + v[4 * k + 2],
@@ -504,7 +507,7 @@ struct EpiTaylor {
         }
       } else {
         for (int u = 0; u < 16 && pb + u < M; ++u) {
-          arow[pb + u] += v[u];
+          arow[pb + u] = (first ? 0.f : arow[pb + u]) + v[u];
           if (tb_out) put_term(tb_out, lo_kind, (long)w * 2 * N, N, Mp, c, i, pb + u, v[u]);
         }
       }
@@ -787,21 +790,25 @@ int tc_tune_store(const TcGemm& g, float* C, long ldc, float alpha, cudaStream_t
   return AFQMC_OK;
 }
 
-int tc_prop_first(const TcGemm& g, float* acc, void* tb, int lo_kind, int N, int M, int Mp,
-                  cudaStream_t st) {
-  tc::EpiProp0 e{acc, tb, lo_kind, N, M, Mp, g.m};
+int tc_prop_first(const TcGemm& g, float* acc, long ldacc, void* tb, int lo_kind, int N, int M,
+                  int Mp, cudaStream_t st) {
+  tc::EpiProp0 e{acc, ldacc, tb, lo_kind, N, M, Mp, g.m};
   const int gx = cdiv(g.m, tc::BM), gy = cdiv(M, 256);
   if (g.tf32) return launch_tc_persistent<256, 4, true>(g, e, gx, gy, st);
   return launch_tc_persistent<256, 4, false>(g, e, gx, gy, st);
 }
 
-int tc_taylor_term(const TcGemm& g, float* acc, void* tb_out, int lo_kind, int W, int N, int M,
-                   int Mp, float scale, cudaStream_t st) {
+int tc_taylor_term(const TcGemm& g, float* S, long lds, bool first, void* tb_out, int lo_kind,
+                   int W, int N, int M, int Mp, float scale, cudaStream_t st) {
   if (2 * N > tc::BM) {
     set_error("tc taylor: 2N=%d above the 128-row tile", 2 * N);
     return AFQMC_EUNSUPPORTED;
   }
-  tc::EpiTaylor e{acc, tb_out, lo_kind, N, M, Mp, scale};
+  if (lds % 4) {
+    set_error("tc taylor: sum pitch %ld not a multiple of 4", lds);
+    return AFQMC_EINVAL;
+  }
+  tc::EpiTaylor e{S, lds, first ? 1 : 0, tb_out, lo_kind, N, M, Mp, scale};
   constexpr int BN = tc::EpiTaylor::kBN;
   if (g.tf32) return launch_tc_persistent<BN, 6, true>(g, e, cdiv(M, BN), W, st);
   return launch_tc_persistent<BN, 6, false>(g, e, cdiv(M, BN), W, st);

@@ -2,10 +2,11 @@
 // truncated expansion of the exponential of the one-body operator) on tcgen05.
 //
 // For walker w the terms T_k = V T_{k-1} / k, k = 1..n, are formed one after
-// another and added to the running sum acc (FP32, holds T_0 on entry); the
-// last half step then consumes acc.  Per-term launches would stream every
-// walker's V from HBM n times; here a CTA keeps the term in shared memory and
-// streams only V, which after the first term comes from L2.
+// another and summed, S = T_1 + ... + T_n (FP32); the last half step then
+// applies exp(-dt v0'/2) to T_0 + S.  Per-term launches would stream every
+// walker's V from HBM n times and read-modify-write the sum in global memory
+// per term; here a CTA keeps the term in shared memory and the sum in tensor
+// memory, streams only V (from L2 after the first term) and writes S once.
 //
 //   A operand  [Re V | Im V] rows p of walker w (128-row tiles, K = 2 Mp),
 //              TMA ring of 128 x 128-byte boxes;
@@ -14,11 +15,13 @@
 //              (NB = 2N rounded up to 16 rows), resident in shared memory in
 //              the 128-byte-swizzled layout TMA writes, one 1024-byte-aligned
 //              block of NB x 128 bytes per 128 bytes of K;
-//   D          TMEM lane p of p-tile pt, column pt * NB + n: (V T_{k-1})[p][n].
+//   D          TMEM lane p of p-tile pt, column pt * NB + n: (V T_{k-1})[p][n];
+//              the running sum S sits in the same layout PT * NB columns on.
 //
-// The epilogue warps read D, add T_k = D / k to acc and, unless k = n, write
-// T_k into the B operand in place (every MMA of term k has completed by then),
-// then release the MMA thread for term k + 1.  Warp roles: warp 0 TMA
+// The epilogue warps read D, add T_k = D / k to S (tcgen05.ld / st) and,
+// unless k = n, write T_k into the B operand in place (every MMA of term k has
+// completed by then), then release the MMA thread for term k + 1; after the
+// last term S goes to global memory with plain coalesced stores.  Warp roles: warp 0 TMA
 // producer, warp 1 TMEM allocation and the MMA thread, warps 2-5 epilogue.
 // Every wait is bounded; on time-out the kernel records an error and stops.
 #include <cuda_bf16.h>
@@ -33,7 +36,8 @@ namespace tc {
 constexpr int kVBox = BM * BKB;  // one V tile in the ring: 128 rows x 128 bytes
 
 struct SeriesArgs {
-  float* acc;   // [W][2N][Mp]
+  float* S;     // [W][2N][lds]: S = T_1 + ... + T_n, columns p < M
+  long lds;
   int W, M, N, Mp, order;
   int nb;       // rows of the term operand (2N rounded up to 16) = MMA N
   int kblocks;  // 128-byte K blocks covering 2 Mp
@@ -183,6 +187,8 @@ __global__ void __launch_bounds__(192, 1)
   } else if (warp >= 2) {
     // epilogue: warp quarter q holds TMEM lanes (p within the tile) 32q .. 32q + 31
     const int q = warp & 3, twoN = 2 * a.N;
+    const uint32_t tl = tmem + ((uint32_t)(32 * q) << 16);
+    const uint32_t soff = (uint32_t)(a.ptiles * a.nb);  // columns of the running sum
     int g = 0;
     bool stop = false;
     for (int w = blockIdx.x; w < a.W && !stop; w += gridDim.x) {
@@ -201,32 +207,45 @@ __global__ void __launch_bounds__(192, 1)
           const bool pv = p < a.M;
 #pragma unroll 1
           for (int c0 = 0; c0 < twoN; c0 += 16) {
-            float v[16];
-            tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(pt * a.nb + c0), v);
-            if (!pv) continue;
-            float* arow = a.acc + ((long)w * twoN + c0) * a.Mp + p;
-            float o[16];
+            const uint32_t col = (uint32_t)(pt * a.nb + c0);
+            float v[16], sum[16];
+            tmem_ld16(tl + col, v);
+            if (k > 1) {
+              tmem_ld16(tl + soff + col, sum);
+            } else {
 #pragma unroll
-            for (int u = 0; u < 16; ++u)
-              if (c0 + u < twoN) o[u] = arow[(long)u * a.Mp];
+              for (int u = 0; u < 16; ++u) sum[u] = 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+              v[u] *= scale;
+              sum[u] += v[u];
+            }
+            if (next) {
+              tmem_st16(tl + soff + col, sum);
+            } else if (pv) {
+              float* srow = a.S + ((long)w * twoN + c0) * a.lds + p;
+#pragma unroll
+              for (int u = 0; u < 16; ++u)
+                if (c0 + u < twoN) srow[(long)u * a.lds] = sum[u];
+            }
+            if (!next || !pv) continue;
 #pragma unroll
             for (int u = 0; u < 16; ++u) {
               const int n = c0 + u;
               if (n >= twoN) break;
-              const float t = v[u] * scale;
-              arow[(long)u * a.Mp] = o[u] + t;
-              if (next) {
-                if (n < a.N) {
-                  put_op<TF32>(bop, a.nb, n, p, t);
-                  put_op<TF32>(bop, a.nb, a.N + n, a.Mp + p, t);
-                } else {
-                  put_op<TF32>(bop, a.nb, n - a.N, a.Mp + p, -t);
-                  put_op<TF32>(bop, a.nb, n, p, t);
-                }
+              const float t = v[u];
+              if (n < a.N) {
+                put_op<TF32>(bop, a.nb, n, p, t);
+                put_op<TF32>(bop, a.nb, a.N + n, a.Mp + p, t);
+              } else {
+                put_op<TF32>(bop, a.nb, n - a.N, a.Mp + p, -t);
+                put_op<TF32>(bop, a.nb, n, p, t);
               }
             }
           }
         }
+        tmem_st_wait();
         // generic-proxy writes of the next term -> visible to the MMA (async proxy)
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         fence_before();
@@ -254,14 +273,15 @@ bool series_plan(int lo_kind, int N, int M, int Mp, tc::SeriesArgs* sa, int* sme
   const int nb = (2 * N + 15) / 16 * 16;
   const int kblocks = (2 * Mp * elem + tc::BKB - 1) / tc::BKB;
   const int ptiles = (M + tc::BM - 1) / tc::BM;
-  if (nb > 256 || ptiles * nb > 512) return false;
+  // the product and the running sum side by side in tensor memory
+  if (nb > 256 || 2 * ptiles * nb > 512) return false;
   const long op = (long)kblocks * nb * tc::BKB;
   long room = kSmemMax - kSmemFixed - op;
   int stages = (int)(room / tc::kVBox);
   if (stages > 8) stages = 8;
   if (stages < 2) return false;
   uint32_t tcols = 32;
-  while (tcols < (uint32_t)(ptiles * nb)) tcols <<= 1;
+  while (tcols < (uint32_t)(2 * ptiles * nb)) tcols <<= 1;
   if (sa) {
     sa->nb = nb;
     sa->kblocks = kblocks;
@@ -278,8 +298,8 @@ bool tc_taylor_series_fits(int lo_kind, int N, int M, int Mp) {
   return series_plan(lo_kind, N, M, Mp, nullptr, nullptr);
 }
 
-int tc_taylor_series(const void* V, const void* T0, float* acc, int lo_kind, int W, int N, int M,
-                     int Mp, int order, int* err, cudaStream_t st) {
+int tc_taylor_series(const void* V, const void* T0, float* S, long lds, int lo_kind, int W, int N,
+                     int M, int Mp, int order, int* err, cudaStream_t st) {
   tc::SeriesArgs sa{};
   int smem = 0;
   if (!series_plan(lo_kind, N, M, Mp, &sa, &smem)) {
@@ -287,7 +307,8 @@ int tc_taylor_series(const void* V, const void* T0, float* acc, int lo_kind, int
     return AFQMC_EUNSUPPORTED;
   }
   if (W <= 0 || order <= 0) return AFQMC_OK;
-  sa.acc = acc;
+  sa.S = S;
+  sa.lds = lds;
   sa.W = W;
   sa.M = M;
   sa.N = N;
@@ -319,10 +340,10 @@ int tc_taylor_series(const void* V, const void* T0, float* acc, int lo_kind, int
   return AFQMC_OK;
 }
 
-int taylor_apply(const void* V, void* T0, void* T1, float* acc, int lo_kind, int W, int N, int M,
-                 int Mp, int order, bool per_term, int* err, cudaStream_t st) {
+int taylor_apply(const void* V, void* T0, void* T1, float* S, long lds, int lo_kind, int W, int N,
+                 int M, int Mp, int order, bool per_term, int* err, cudaStream_t st) {
   if (!per_term && tc_taylor_series_fits(lo_kind, N, M, Mp))
-    return tc_taylor_series(V, T0, acc, lo_kind, W, N, M, Mp, order, err, st);
+    return tc_taylor_series(V, T0, S, lds, lo_kind, W, N, M, Mp, order, err, st);
   // one launch per term, the term as the A operand (rows (w, c, i)); the
   // operand alternates between T0 and T1
   void* tin = T0;
@@ -338,7 +359,7 @@ int taylor_apply(const void* V, void* T0, void* T1, float* acc, int lo_kind, int
     tg.ldb = 2L * Mp;
     tg.tf32 = lo_kind == LO_TF32;
     tg.err = err;
-    AFQ_TRY(tc_taylor_term(tg, acc, k < order ? tout : nullptr, lo_kind, W, N, M, Mp,
+    AFQ_TRY(tc_taylor_term(tg, S, lds, k == 1, k < order ? tout : nullptr, lo_kind, W, N, M, Mp,
                            1.0f / (float)k, st));
     void* t_ = tin;
     tin = tout;
@@ -351,14 +372,15 @@ int taylor_apply(const void* V, void* T0, void* T1, float* acc, int lo_kind, int
 
 extern "C" int afqmc_taylor_series(int32_t dtype, int64_t nwalkers, int64_t N, int64_t M,
                                    int64_t Mp, int32_t order, const void* dV, void* dT0, void* dT1,
-                                   float* dacc, int32_t per_term, int* d_status, void* stream) {
+                                   float* dS, int64_t ldS, int32_t per_term, int* d_status,
+                                   void* stream) {
   using namespace afq;
   const int lo_kind = dtype == 1 ? LO_TF32 : LO_BF16;
   const bool bad_dims = (dtype != 0 && dtype != 1) || nwalkers < 0 || N < 1 || M < 1 || Mp < M ||
                         Mp % 16 || order < 1 || order > 64 || 2 * N > 128 ||
                         nwalkers * 2 * N * 2 * Mp > (1ll << 31) - 1 ||
-                        nwalkers * M * 2 * Mp > (1ll << 31) - 1;
-  if (bad_dims || !dV || !dT0 || !dacc || !d_status) {
+                        nwalkers * M * 2 * Mp > (1ll << 31) - 1 || ldS < Mp || ldS % 4;
+  if (bad_dims || !dV || !dT0 || !dS || !d_status) {
     set_error("afqmc_taylor_series: bad arguments");
     return AFQMC_EINVAL;
   }
@@ -368,10 +390,10 @@ extern "C" int afqmc_taylor_series(int32_t dtype, int64_t nwalkers, int64_t N, i
     return AFQMC_EINVAL;
   }
   if ((reinterpret_cast<uintptr_t>(dV) | reinterpret_cast<uintptr_t>(dT0) |
-       reinterpret_cast<uintptr_t>(dT1) | reinterpret_cast<uintptr_t>(dacc)) % 16) {
+       reinterpret_cast<uintptr_t>(dT1) | reinterpret_cast<uintptr_t>(dS)) % 16) {
     set_error("afqmc_taylor_series: buffers must be 16-byte aligned");
     return AFQMC_EINVAL;
   }
-  return taylor_apply(dV, dT0, dT1, dacc, lo_kind, (int)nwalkers, (int)N, (int)M, (int)Mp, order,
-                      !series, d_status, static_cast<cudaStream_t>(stream));
+  return taylor_apply(dV, dT0, dT1, dS, ldS, lo_kind, (int)nwalkers, (int)N, (int)M, (int)Mp,
+                      order, !series, d_status, static_cast<cudaStream_t>(stream));
 }

@@ -29,10 +29,11 @@ int tc_tune_store(const TcGemm& g, float* C, long ldc, float alpha, cudaStream_t
 // with the fused sum_ij T_ij T_ji epilogue; part [W][nchunk][2] (float64).
 // Propagation on tcgen05 (mixed path): first half step, Taylor terms, last
 // half step (see the epilogues in gemm_tc.cu for the operand layouts).
-int tc_prop_first(const TcGemm& g, float* acc, void* tb, int lo_kind, int N, int M, int Mp,
-                  cudaStream_t st);
-int tc_taylor_term(const TcGemm& g, float* acc, void* tb_out, int lo_kind, int W, int N, int M,
-                   int Mp, float scale, cudaStream_t st);
+int tc_prop_first(const TcGemm& g, float* acc, long ldacc, void* tb, int lo_kind, int N, int M,
+                  int Mp, cudaStream_t st);
+// S = T_k (first) or S += T_k, T_k = scale * (V T_{k-1}); pitch lds
+int tc_taylor_term(const TcGemm& g, float* S, long lds, bool first, void* tb_out, int lo_kind,
+                   int W, int N, int M, int Mp, float scale, cudaStream_t st);
 int tc_prop_last(const TcGemm& g, double* phiT, const double* wt, int N, int M,
                  cudaStream_t st);
 // V = i sqrt(dt) sum_g x_g L_g from the full transposed vectors (rows p*Mp+q)
@@ -43,18 +44,18 @@ int tc_v_full(const TcGemm& g, void* V, int lo_kind, int W, int M, int Mp, doubl
 // Whole Taylor series per walker in one launch (one CTA per walker at a time):
 // the term stays in shared memory and the walker's [Re V | Im V] rows are
 // streamed once per term (from L2 after the first).  T0: the 0th term operand
-// rows [W][2N][2Mp], V: [W][M][2Mp], acc: [W][2N][Mp] FP32 (holds T_0 on
-// entry, the series sum on exit).  tc_taylor_series_fits() says whether the
-// shape fits the kernel's shared memory and tensor memory.
+// rows [W][2N][2Mp], V: [W][M][2Mp], S: [W][2N][lds] FP32 receives
+// T_1 + ... + T_order (columns p < M).  tc_taylor_series_fits() says whether
+// the shape fits the kernel's shared memory and tensor memory.
 bool tc_taylor_series_fits(int lo_kind, int N, int M, int Mp);
-int tc_taylor_series(const void* V, const void* T0, float* acc, int lo_kind, int W, int N, int M,
-                     int Mp, int order, int* err, cudaStream_t st);
+int tc_taylor_series(const void* V, const void* T0, float* S, long lds, int lo_kind, int W, int N,
+                     int M, int Mp, int order, int* err, cudaStream_t st);
 
 // The series by whichever route fits: the whole-series kernel unless per_term
 // is set or the shape does not fit, else one launch per term (the operand
 // alternates between T0 and T1, so both are overwritten).
-int taylor_apply(const void* V, void* T0, void* T1, float* acc, int lo_kind, int W, int N, int M,
-                 int Mp, int order, bool per_term, int* err, cudaStream_t st);
+int taylor_apply(const void* V, void* T0, void* T1, float* S, long lds, int lo_kind, int W, int N,
+                 int M, int Mp, int order, bool per_term, int* err, cudaStream_t st);
 
 // tensor maps (128-byte swizzle, box = 128 bytes x box_rows)
 int make_tmap(CUtensorMap* m, const void* base, int elem_bytes, long rows, long cols, long pitch,
