@@ -1,11 +1,14 @@
 """A single contraction of the M=300 step, for kernel profiling.
 
-    python -m paper_1711_02242_gb300.profile_case [--case v|fb] [--dtype bf16|tf32] [--reps 3]
+    python -m paper_1711_02242_gb300.profile_case [--case v|fb|taylor] [--dtype bf16|tf32]
+                                                  [--reps 3] [--walkers 512]
 
 Case "v": V = sum_g x_g L_g as afqmc_contract with the M=300 shapes
 (A = 1024 x 1800 fields, B = 45150 x 1800 packed Cholesky vectors, C FP32):
 about 350 MB on the device, B alone (162 MB BF16) larger than the 129 MB L2.
 Case "fb": the force-bias contraction (A = 1024 x 7600, B = 1800 x 7600).
+Case "taylor": the sixth-order Taylor series of exp(V) on 512 walkers with
+M = 300, N = 25 (afqmc_taylor_series; V is 187 MB in BF16).
 Random operands; prints the mean time per launch from CUDA events.
 """
 from __future__ import annotations
@@ -20,13 +23,16 @@ def main():
     import torch
 
     ap = argparse.ArgumentParser()
-    ap.add_argument("--case", default="v", choices=["v", "fb"])
+    ap.add_argument("--case", default="v", choices=["v", "fb", "taylor"])
+    ap.add_argument("--walkers", type=int, default=512)
     ap.add_argument("--dtype", default="bf16", choices=["bf16", "tf32"])
     ap.add_argument("--reps", type=int, default=3)
     a = ap.parse_args()
     from paper_1711_02242_gb300 import build as b
 
     b.build()
+    if a.case == "taylor":
+        return taylor(a)
     if a.case == "v":
         m, n, k, pitch = 1024, 45150, 1800, 1800
     else:
@@ -61,6 +67,50 @@ def main():
     flops = 2.0 * m * n * k
     print(f"case {a.case} {a.dtype}: m={m} n={n} k={k}: {ms:.4f} ms/launch, "
           f"{flops / ms / 1e9:.1f} TFLOP/s, status {int(st.item())}")
+    assert int(st.item()) == 0
+
+
+def taylor(a):
+    import torch
+
+    W, N, M, Mp, order = a.walkers, 25, 300, 304, 6
+    dt = torch.bfloat16 if a.dtype == "bf16" else torch.float32
+    g = torch.Generator(device="cuda").manual_seed(0)
+    V = torch.zeros((W, M, 2 * Mp), device="cuda")
+    V[:, :, :M] = torch.randn((W, M, M), generator=g, device="cuda") * (0.05 / M ** 0.5)
+    V[:, :, Mp:Mp + M] = torch.randn((W, M, M), generator=g, device="cuda") * (0.05 / M ** 0.5)
+    V = V.to(dt)
+    T0 = torch.zeros((W, 2 * N, 2 * Mp), device="cuda")
+    T0[:, :, :M] = torch.randn((W, 2 * N, M), generator=g, device="cuda")
+    T0 = T0.to(dt)
+    T1 = torch.empty_like(T0)
+    S = torch.empty((W, 2 * N, Mp), dtype=torch.float32, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+    lib = pkg.lib()
+
+    def call():
+        pkg._check(lib.afqmc_taylor_series(0 if a.dtype == "bf16" else 1, W, N, M, Mp, order,
+                                           ctypes.c_void_p(V.data_ptr()),
+                                           ctypes.c_void_p(T0.data_ptr()),
+                                           ctypes.c_void_p(T1.data_ptr()),
+                                           ctypes.c_void_p(S.data_ptr()), Mp, 0,
+                                           ctypes.c_void_p(st.data_ptr()),
+                                           ctypes.c_void_p(stream.cuda_stream)))
+
+    call()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(a.reps):
+        call()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / a.reps
+    vbytes = V.numel() * V.element_size()
+    print(f"case taylor {a.dtype}: W={W} N={N} M={M} order={order}: {ms:.4f} ms/launch, "
+          f"V {vbytes / 1e6:.0f} MB once from HBM: {vbytes / ms / 1e6:.0f} GB/s, "
+          f"V per term (L2): {order * vbytes / ms / 1e6:.0f} GB/s, status {int(st.item())}")
     assert int(st.item()) == 0
 
 
