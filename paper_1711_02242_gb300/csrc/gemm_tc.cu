@@ -210,7 +210,10 @@ __global__ void __launch_bounds__(192, 1)
         uint8_t* a = smem + s * S::STAGE;
         mbar_expect_tx(&full[s], S::STAGE);
         tma_load_2d(a, &tmA, &full[s], kb * BK, m0);
-        tma_load_2d(a + S::A_BYTES, &tmB, &full[s], kb * BK, n0);
+        if constexpr (Epi::kB3D)
+          tma_load_3d(a + S::A_BYTES, &tmB, &full[s], kb * BK, 0, epi.b_plane(bx, by));
+        else
+          tma_load_2d(a + S::A_BYTES, &tmB, &full[s], kb * BK, n0);
       }
     }
   } else if (warp == 1 && lane == 0) {
@@ -277,6 +280,7 @@ __global__ void __launch_bounds__(192, 1)
 // Plain FP32 store of alpha * D to C[m * ldc + n].
 struct EpiStore {
   static constexpr int kSmemBytes = 0;
+  static constexpr bool kB3D = false;  // B tile = one 2-D box at row n_origin
   float* C;
   long ldc;
   float alpha;
@@ -311,21 +315,27 @@ struct EpiStore {
 // Exchange part of Eq. localenergy3 fused into the T_g = Lh_g Theta
 // contraction.  Rows of the product are (g, i) = Lh rows, columns (w, c, j)
 // = Theta^T rows (c = re/im plane).  A tile covers RG whole Cholesky vectors
-// (RG*N <= 128 rows) and CW whole walkers (CW*2N <= 256 columns), so every
-// T_g,w block lies inside it: the accumulator is copied to this epilogue's
-// own shared memory and sum_ij T_ij T_ji (complex) is formed there; T never
-// reaches global memory.  part[w][g][2] receives one partial per (g, w)
-// (nchunk = G), summed later in a fixed order.
+// (RG*N <= 128 rows) and CW whole walkers; the B tile is one 3-D TMA box of
+// CW walkers x NPAD rows (the 2N rows of a walker, zero-padded to a power of
+// two), so walker wl of the tile owns accumulator columns [wl NPAD, wl NPAD +
+// 2N).  The accumulator is copied to this epilogue's own shared memory; the
+// thread of row (g, i) then forms e_i = sum_j T_ij T_ji (complex) from its own
+// row and column i of the block, the N values of a vector are summed, and
+// part[w][g][2] receives one partial per (g, w) (nchunk = G), summed later in
+// a fixed order.  T never reaches global memory.
 struct EpiExchange {
   static constexpr int kSmemBytes = 128 * 257 * 4;  // one 128 x 256 FP32 tile
+  static constexpr bool kB3D = true;
+  static constexpr int kMaxCW = 16;
   double* part;
-  int G, W, N, RG, CW, nchunk;
+  int G, W, N, RG, CW, NPAD, nchunk;
   __device__ __forceinline__ int m_origin(int bx, int) const { return bx * RG * N; }
-  __device__ __forceinline__ int n_origin(int, int by) const { return by * CW * 2 * N; }
+  __device__ __forceinline__ int n_origin(int, int by) const { return by * CW * NPAD; }
+  __device__ __forceinline__ int b_plane(int, int by) const { return by * CW; }
   template <int BN>
-  __device__ __forceinline__ void run(uint32_t tmem, int q, int lane, int ew, int bx, int by, int,
+  __device__ __forceinline__ void run(uint32_t tmem, int q, int lane, int, int bx, int by, int,
                                       int, int, int, float* sm) const {
-    constexpr int LD = BN + 1;
+    constexpr int LD = BN + 1;  // odd pitch: row and column walks are conflict-free
     const int r = 32 * q + lane;
 #pragma unroll 1
     for (int c0 = 0; c0 < BN; c0 += 16) {
@@ -335,30 +345,48 @@ struct EpiExchange {
       for (int i = 0; i < 16; ++i) sm[r * LD + c0 + i] = v[i];
     }
     asm volatile("bar.sync 1, 128;" ::: "memory");
-    const int g0 = bx * RG, w0 = by * CW;
-    // FP32 sums per lane (the products come from FP32 accumulators; GB300's
-    // float64 pipe is ~60x slower, so float64 here would dominate the kernel)
-    for (int pi = ew; pi < RG * CW; pi += 4) {
-      const int g = pi / CW, wl = pi % CW;
+    const int gl = r / N, i = r - gl * N;
+    const bool rv = gl < RG;
+    // FP32 sums (the products come from FP32 accumulators; GB300's float64
+    // pipe is ~60x slower than FP32 and would dominate the kernel)
+    float e[2 * kMaxCW];
+#pragma unroll
+    for (int wl = 0; wl < kMaxCW; ++wl) {
       float er = 0.f, ei = 0.f;
-      if (g0 + g < G && w0 + wl < W) {
-        const float* Dg = sm + (g * N) * LD + wl * 2 * N;
-        for (int ij = lane; ij < N * N; ij += 32) {
-          const int i = ij / N, j = ij % N;
-          const float ar = Dg[i * LD + j], ai = Dg[i * LD + N + j];
-          const float br = Dg[j * LD + i], bi = Dg[j * LD + N + i];
+      if (wl < CW && rv) {
+        const float* own = sm + r * LD + wl * NPAD;            // T_ij: [j], [N + j]
+        const float* col = sm + (gl * N) * LD + wl * NPAD + i;  // T_ji: [j LD], [j LD + N]
+#pragma unroll 4
+        for (int j = 0; j < N; ++j) {
+          const float ar = own[j], ai = own[N + j];
+          const float br = col[j * LD], bi = col[j * LD + N];
           er = fmaf(ar, br, fmaf(-ai, bi, er));
           ei = fmaf(ar, bi, fmaf(ai, br, ei));
         }
       }
-      er = warp_sum(er);
-      ei = warp_sum(ei);
-      // one partial per (Cholesky vector, walker): part[w][g][2]
-      if (lane == 0 && g0 + g < G && w0 + wl < W) {
-        double* o = part + ((long)(w0 + wl) * nchunk + g0 + g) * 2;
-        o[0] = (double)er;
-        o[1] = (double)ei;
+      e[2 * wl] = er;
+      e[2 * wl + 1] = ei;
+    }
+    asm volatile("bar.sync 1, 128;" ::: "memory");  // every read of the tile is done
+#pragma unroll
+    for (int wl = 0; wl < kMaxCW; ++wl)
+      if (wl < CW) {
+        sm[r * LD + 2 * wl] = e[2 * wl];
+        sm[r * LD + 2 * wl + 1] = e[2 * wl + 1];
       }
+    asm volatile("bar.sync 1, 128;" ::: "memory");
+    const int g0 = bx * RG, w0 = by * CW;
+    for (int item = r; item < RG * CW; item += 128) {
+      const int g = item / CW, wl = item - g * CW;
+      if (g0 + g >= G || w0 + wl >= W) continue;
+      float sr = 0.f, si = 0.f;
+      for (int i2 = 0; i2 < N; ++i2) {
+        sr += sm[(g * N + i2) * LD + 2 * wl];
+        si += sm[(g * N + i2) * LD + 2 * wl + 1];
+      }
+      double* o = part + ((long)(w0 + wl) * nchunk + g0 + g) * 2;
+      o[0] = (double)sr;
+      o[1] = (double)si;
     }
     // the next tile's copy into sm must wait until every warp is done reading
     asm volatile("bar.sync 1, 128;" ::: "memory");
@@ -408,6 +436,7 @@ __device__ __forceinline__ void store16_lo(void* base, int kind, long idx, const
 // Each thread owns one row and 16 consecutive p per chunk: vector stores.
 struct EpiProp0 {
   static constexpr int kSmemBytes = 0;
+  static constexpr bool kB3D = false;  // B tile = one 2-D box at row n_origin
   float* acc;
   long ldacc;
   void* tb;
@@ -462,6 +491,7 @@ struct EpiProp0 {
 // running sum and the next operand are written with 16-byte vectors.
 struct EpiTaylor {
   static constexpr int kSmemBytes = 0;
+  static constexpr bool kB3D = false;  // B tile = one 2-D box at row n_origin
   static constexpr int kBN = 160;  // two tiles cover p < 320
   float* S;
   long lds;
@@ -522,6 +552,7 @@ struct EpiTaylor {
 // Mp + q, 16 consecutive q per thread (pad columns come out zero).
 struct EpiV {
   static constexpr int kSmemBytes = 0;
+  static constexpr bool kB3D = false;  // B tile = one 2-D box at row n_origin
   void* V;
   int lo_kind, W, M, Mp;
   float sdt;
@@ -555,6 +586,7 @@ struct EpiV {
 // stored as the new float64 orbitals of live walkers.
 struct EpiPhi {
   static constexpr int kSmemBytes = 0;
+  static constexpr bool kB3D = false;  // B tile = one 2-D box at row n_origin
   double* phiT;
   const double* wt;
   int N, M, rows;
@@ -623,9 +655,11 @@ int make_tmap(CUtensorMap* m, const void* base, int elem_bytes, long rows, long 
 }
 
 // 3-D operand [planes][rows][pitch] (plane stride in elements), box = 128 bytes
-// x box_rows x 1, 128B swizzle; rows >= `rows` of a plane read as zero.
+// x box_rows x box_planes, 128B swizzle; rows >= `rows` of a plane and planes
+// >= `planes` read as zero, so a box lands as box_planes blocks of box_rows
+// (zero-padded) rows.
 int make_tmap_3d(CUtensorMap* m, const void* base, int elem_bytes, long planes, long rows,
-                 long cols, long pitch, long plane_stride, int box_rows) {
+                 long cols, long pitch, long plane_stride, int box_rows, int box_planes) {
   auto fn = encode_fn();
   if (!fn) {
     set_error("cuTensorMapEncodeTiled is not available");
@@ -638,7 +672,8 @@ int make_tmap_3d(CUtensorMap* m, const void* base, int elem_bytes, long planes, 
   }
   cuuint64_t dims[3] = {(cuuint64_t)cols, (cuuint64_t)rows, (cuuint64_t)planes};
   cuuint64_t strides[2] = {(cuuint64_t)(pitch * elem_bytes), (cuuint64_t)(plane_stride * elem_bytes)};
-  cuuint32_t box[3] = {(cuuint32_t)(128 / elem_bytes), (cuuint32_t)box_rows, 1};
+  cuuint32_t box[3] = {(cuuint32_t)(128 / elem_bytes), (cuuint32_t)box_rows,
+                       (cuuint32_t)box_planes};
   cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = fn(m, elem_bytes == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
                   3, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -684,13 +719,17 @@ int tc_sm_count() {
 }
 
 template <int BN, int STAGES, bool TF32, class Epi>
-static int launch_tc_persistent(const TcGemm& g, const Epi& epi, int gx, int gy, cudaStream_t st) {
+static int launch_tc_persistent(const TcGemm& g, const Epi& epi, int gx, int gy, cudaStream_t st,
+                                const CUtensorMap* tb_given = nullptr) {
   constexpr int kTotal = tc::Smem<BN, STAGES>::TOTAL + Epi::kSmemBytes;
   static_assert(kTotal <= 232448, "shared memory");
   const int eb = TF32 ? 4 : 2;
   CUtensorMap ta, tb;
   AFQ_TRY(make_tmap(&ta, g.A, eb, g.m, g.k, g.lda, tc::BM));
-  AFQ_TRY(make_tmap(&tb, g.B, eb, g.n, g.k, g.ldb, BN));
+  if (tb_given)
+    tb = *tb_given;
+  else
+    AFQ_TRY(make_tmap(&tb, g.B, eb, g.n, g.k, g.ldb, BN));
   auto kern = tc::k_tc_gemm_persistent<BN, STAGES, TF32, Epi>;
   static bool attr = false;
   if (!attr) {
@@ -835,24 +874,31 @@ int tc_prop_last(const TcGemm& g, double* phiT, const double* wt, int N, int M,
 }
 
 // Exchange blocking: RG Cholesky vectors x CW walkers per 128 x 256 tile.
-void exchange_tile(int N, int* RG, int* CW) {
-  int rg = 128 / N, cw = 256 / (2 * N);
-  *RG = rg < 32 ? rg : 32;
-  *CW = cw < 32 ? cw : 32;
+void exchange_tile(int N, int* RG, int* CW, int* NPAD) {
+  int npad = 16;
+  while (npad < 2 * N) npad <<= 1;
+  *NPAD = npad;
+  *CW = npad <= 256 ? 256 / npad : 0;
+  *RG = N <= 128 ? 128 / N : 0;
 }
 
 int tc_exchange(const TcGemm& g, int G, int W, int N, double* part, int nchunk, cudaStream_t st) {
-  int RG, CW;
-  exchange_tile(N, &RG, &CW);
-  if (RG < 1 || CW < 1 || nchunk != G) {
-    set_error("tc exchange: bad blocking N=%d", N);
-    return AFQMC_EINVAL;
+  int RG, CW, NPAD;
+  exchange_tile(N, &RG, &CW, &NPAD);
+  if (RG < 1 || CW < 1 || CW > tc::EpiExchange::kMaxCW || nchunk != G) {
+    set_error("tc exchange: N=%d not supported", N);
+    return AFQMC_EUNSUPPORTED;
   }
-  tc::EpiExchange e{part, G, W, N, RG, CW, nchunk};
+  // B: Theta^T rows as [W][2N][ldb], one box = CW walkers x NPAD rows
+  const int eb = g.tf32 ? 4 : 2;
+  CUtensorMap tb;
+  AFQ_TRY(make_tmap_3d(&tb, g.B, eb, W, 2L * N, g.k, g.ldb, 2L * N * g.ldb, NPAD, CW));
+  tc::EpiExchange e{part, G, W, N, RG, CW, NPAD, nchunk};
   // K = M is a few k-blocks of L2-resident operands: a 2-deep ring leaves room
   // for the epilogue's own 128 KB tile buffer
-  if (g.tf32) return launch_tc_persistent<256, 2, true>(g, e, cdiv(G, RG), cdiv(W, CW), st);
-  return launch_tc_persistent<256, 2, false>(g, e, cdiv(G, RG), cdiv(W, CW), st);
+  if (g.tf32)
+    return launch_tc_persistent<256, 2, true>(g, e, cdiv(G, RG), cdiv(W, CW), st, &tb);
+  return launch_tc_persistent<256, 2, false>(g, e, cdiv(G, RG), cdiv(W, CW), st, &tb);
 }
 
 }  // namespace afq

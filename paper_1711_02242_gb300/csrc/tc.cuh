@@ -61,10 +61,12 @@ int taylor_apply(const void* V, void* T0, void* T1, float* S, long lds, int lo_k
 int make_tmap(CUtensorMap* m, const void* base, int elem_bytes, long rows, long cols, long pitch,
               int box_rows);
 int make_tmap_3d(CUtensorMap* m, const void* base, int elem_bytes, long planes, long rows,
-                 long cols, long pitch, long plane_stride, int box_rows);
+                 long cols, long pitch, long plane_stride, int box_rows, int box_planes = 1);
 int tc_sm_count();
 
-void exchange_tile(int N, int* RG, int* CW);
+// Exchange blocking: RG Cholesky vectors x CW walkers per 128 x 256 tile, the
+// 2N columns of a walker padded to NPAD (a power of two >= 16).
+void exchange_tile(int N, int* RG, int* CW, int* NPAD);
 int tc_exchange(const TcGemm& g, int G, int W, int N, double* part, int nchunk, cudaStream_t st);
 
 }  // namespace afq
