@@ -707,6 +707,44 @@ static int launch_tc(const TcGemm& g, const Epi& epi, dim3 grid, cudaStream_t st
   return AFQMC_OK;
 }
 
+// Tensor map of any rank (2..5): dims innermost first, strides in bytes for
+// dims 1.., box sizes per dim; 128-byte swizzle, out-of-range elements read 0.
+int make_tmap_nd(CUtensorMap* m, const void* base, int elem_bytes, int rank, const long* dims,
+                 const long* stride_bytes, const int* box) {
+  auto fn = encode_fn();
+  if (!fn) {
+    set_error("cuTensorMapEncodeTiled is not available");
+    return AFQMC_ECUDA;
+  }
+  if (rank < 2 || rank > 5 || (reinterpret_cast<uintptr_t>(base) % 16)) {
+    set_error("tensor map: bad rank or base");
+    return AFQMC_EINVAL;
+  }
+  cuuint64_t d[5], sb[4];
+  cuuint32_t bx[5], es[5];
+  for (int i = 0; i < rank; ++i) {
+    d[i] = (cuuint64_t)dims[i];
+    bx[i] = (cuuint32_t)box[i];
+    es[i] = 1;
+    if (i > 0) {
+      if (stride_bytes[i - 1] % 16) {
+        set_error("tensor map: stride not a multiple of 16 bytes");
+        return AFQMC_EINVAL;
+      }
+      sb[i - 1] = (cuuint64_t)stride_bytes[i - 1];
+    }
+  }
+  CUresult r = fn(m, elem_bytes == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                  (cuuint32_t)rank, const_cast<void*>(base), d, sb, bx, es,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled (rank %d) failed (%d)", rank, (int)r);
+    return AFQMC_ECUDA;
+  }
+  return AFQMC_OK;
+}
+
 int tc_sm_count() {
   static int n = 0;
   if (!n) {

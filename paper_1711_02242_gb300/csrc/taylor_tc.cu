@@ -10,20 +10,27 @@
 //
 //   A operand  [Re V | Im V] rows p of walker w (128-row tiles, K = 2 Mp),
 //              TMA ring of 128 x 128-byte boxes;
-//   B operand  the term T_{k-1} as K-major rows n = (c, i):
-//                 row (0, i) = [Re T_i | -Im T_i],  row (1, i) = [Im T_i | Re T_i]
-//              (NB = 2N rounded up to 16 rows), resident in shared memory in
+//   B operand  the term T_{k-1} as K-major rows, NH = N rounded up to 16:
+//                 row i      = [Re T_i | -Im T_i]   (i < N)
+//                 row NH + i = [Im T_i |  Re T_i]
+//              (rows i >= N of each half zero), resident in shared memory in
 //              the 128-byte-swizzled layout TMA writes, one 1024-byte-aligned
-//              block of NB x 128 bytes per 128 bytes of K;
-//   D          TMEM lane p of p-tile pt, column pt * NB + n: (V T_{k-1})[p][n];
-//              the running sum S sits in the same layout PT * NB columns on.
+//              block of 2NH x 128 bytes per 128 bytes of K;
+//   D          TMEM lane p of p-tile pt, column pt * 2NH + n: (V T_{k-1})[p][n],
+//              n = c NH + i (c = 0: real part, 1: imaginary part of row i);
+//              the running sum S sits in the same layout PT * 2NH columns on.
 //
 // The epilogue warps read D, add T_k = D / k to S (tcgen05.ld / st) and,
 // unless k = n, write T_k into the B operand in place (every MMA of term k has
 // completed by then), then release the MMA thread for term k + 1; after the
-// last term S goes to global memory with plain coalesced stores.  Warp roles: warp 0 TMA
-// producer, warp 1 TMEM allocation and the MMA thread, warps 2-5 epilogue.
-// Every wait is bounded; on time-out the kernel records an error and stops.
+// last term S goes to global memory with plain coalesced stores.  With NH a
+// multiple of 16 every 16-column chunk of D is one half (real or imaginary)
+// and its rows share their position within the 8-row swizzle atoms, so each
+// thread computes the swizzled offsets of its two K columns (p and Mp + p)
+// once per tile and a store costs one add.  Warp roles: warp 0 TMA producer,
+// warp 1 TMEM allocation and the MMA thread, warps 2-9 epilogue (two warps
+// per 32-lane quarter of TMEM, splitting the chunks).  Every wait is bounded;
+// on time-out the kernel records an error and stops.
 #include <cuda_bf16.h>
 
 #include "kernels.cuh"
@@ -33,49 +40,59 @@
 namespace afq {
 namespace tc {
 
-constexpr int kVBox = BM * BKB;  // one V tile in the ring: 128 rows x 128 bytes
+constexpr int kVBox = BM * BKB;   // one V tile in the ring: 128 rows x 128 bytes
+constexpr int kEpiWarps = 8;      // epilogue warps (2 per TMEM lane quarter)
+constexpr int kEpiThreads = 32 * kEpiWarps;
+constexpr int kSeriesThreads = 64 + kEpiThreads;
 
 struct SeriesArgs {
   float* S;     // [W][2N][lds]: S = T_1 + ... + T_n, columns p < M
   long lds;
   int W, M, N, Mp, order;
-  int nb;       // rows of the term operand (2N rounded up to 16) = MMA N
+  int nh;       // N rounded up to 16: rows per half of the term operand
+  int nb;       // 2 nh = MMA N
   int kblocks;  // 128-byte K blocks covering 2 Mp
   int ptiles;   // 128-row tiles covering p < M
   int stages;   // depth of the V ring
   uint32_t tcols;
 };
 
-// One element of the term operand (row r, K column kcol) in the swizzled layout.
+// Byte offsets, within the term operand, of K column kcol in rows 0..7 of a
+// swizzle atom (add 1024 per further 8 rows).
 template <bool TF32>
-__device__ __forceinline__ void put_op(uint8_t* bop, int nb, int r, int kcol, float v) {
+__device__ __forceinline__ void column_offsets(int kcol, uint32_t opk, uint32_t* off) {
   constexpr int ELEM = TF32 ? 4 : 2;
   constexpr int BK = BKB / ELEM;
   const int kb = kcol / BK;
   const uint32_t byte = (uint32_t)(kcol - kb * BK) * ELEM;
-  const uint32_t off = (uint32_t)kb * (uint32_t)nb * BKB + (uint32_t)(r >> 3) * 1024u +
-                       (uint32_t)(r & 7) * 128u + ((((byte >> 4) ^ (uint32_t)(r & 7)) << 4) | (byte & 15u));
+#pragma unroll
+  for (int j = 0; j < 8; ++j)
+    off[j] = (uint32_t)kb * opk + (uint32_t)j * 128u + ((((byte >> 4) ^ (uint32_t)j) << 4) | (byte & 15u));
+}
+
+template <bool TF32>
+__device__ __forceinline__ void put_op(uint8_t* bop, uint32_t off, float v) {
   if constexpr (TF32)
     *reinterpret_cast<float*>(bop + off) = round_tf32(v);
   else
     *reinterpret_cast<__nv_bfloat16*>(bop + off) = __float2bfloat16_rn(v);
 }
 
-// Named barrier over the 128 epilogue threads that also ORs a flag across them,
+// Named barrier over the epilogue threads that also ORs a flag across them,
 // so every epilogue warp takes the same branch.
 __device__ __forceinline__ bool epi_sync_or(bool flag) {
   uint32_t out;
   asm volatile(
       "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 q, %1, 0;\n\t"
-      "bar.red.or.pred p, 1, 128, q;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
+      "bar.red.or.pred p, 1, %2, q;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
       : "=r"(out)
-      : "r"((uint32_t)flag)
+      : "r"((uint32_t)flag), "n"(kEpiThreads)
       : "memory");
   return out != 0;
 }
 
 template <bool TF32>
-__global__ void __launch_bounds__(192, 1)
+__global__ void __launch_bounds__(kSeriesThreads, 1)
     k_taylor_series(const __grid_constant__ CUtensorMap tmV, const __grid_constant__ CUtensorMap tmT,
                     SeriesArgs a, int* err) {
   extern __shared__ uint8_t smem_raw[];
@@ -106,7 +123,7 @@ __global__ void __launch_bounds__(192, 1)
     mbar_init(bfull, 1);
     mbar_init(bfree, 1);
     mbar_init(dfull, 1);
-    mbar_init(bnext, 128);  // every epilogue thread arrives
+    mbar_init(bnext, kEpiThreads);  // every epilogue thread arrives
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -122,7 +139,8 @@ __global__ void __launch_bounds__(192, 1)
   const uint32_t tmem = *tmem_slot;
 
   if (warp == 0 && lane == 0) {
-    // producer: per walker T_0 once, then the V tiles of every term
+    // producer: per walker T_0 once (rows (c, i) -> c NH + i by a 4-D box),
+    // then the V tiles of every term
     int it = 0, j = 0;
     bool stop = false;
     for (int w = blockIdx.x; w < a.W && !stop; w += gridDim.x, ++j) {
@@ -131,7 +149,8 @@ __global__ void __launch_bounds__(192, 1)
         break;
       }
       mbar_expect_tx(bfull, (uint32_t)a.kblocks * opk);
-      for (int kb = 0; kb < a.kblocks; ++kb) tma_load_3d(bop + kb * opk, &tmT, bfull, kb * BK, 0, w);
+      for (int kb = 0; kb < a.kblocks; ++kb)
+        tma_load_4d(bop + kb * opk, &tmT, bfull, kb * BK, 0, 0, w);
       for (int k = 1; k <= a.order && !stop; ++k)
         for (int pt = 0; pt < a.ptiles && !stop; ++pt)
           for (int kb = 0; kb < a.kblocks; ++kb, ++it) {
@@ -185,10 +204,13 @@ __global__ void __launch_bounds__(192, 1)
     }
     if (stop) *abort_flag = 1;
   } else if (warp >= 2) {
-    // epilogue: warp quarter q holds TMEM lanes (p within the tile) 32q .. 32q + 31
-    const int q = warp & 3, twoN = 2 * a.N;
+    // epilogue: warp quarter q holds TMEM lanes (p within the tile) 32q .. 32q + 31;
+    // the two warps of a quarter take alternate 16-column chunks
+    const int q = warp & 3, half = (warp - 2) >> 2;
     const uint32_t tl = tmem + ((uint32_t)(32 * q) << 16);
     const uint32_t soff = (uint32_t)(a.ptiles * a.nb);  // columns of the running sum
+    const int N = a.N, NH = a.nh;
+    const int nchunk = a.nb / 16;                      // chunks per p-tile
     int g = 0;
     bool stop = false;
     for (int w = blockIdx.x; w < a.W && !stop; w += gridDim.x) {
@@ -205,43 +227,47 @@ __global__ void __launch_bounds__(192, 1)
         for (int pt = 0; pt < a.ptiles; ++pt) {
           const int p = pt * BM + 32 * q + lane;
           const bool pv = p < a.M;
+          uint32_t offp[8], offq[8];  // K columns p and Mp + p
+          column_offsets<TF32>(p, opk, offp);
+          column_offsets<TF32>(a.Mp + p, opk, offq);
 #pragma unroll 1
-          for (int c0 = 0; c0 < twoN; c0 += 16) {
+          for (int ch = half; ch < nchunk; ch += 2) {
+            const int c0 = ch * 16;
+            const int cpart = c0 >= NH ? 1 : 0, i0 = c0 - cpart * NH;
+            if (i0 >= N) continue;  // a chunk of padding rows only
             const uint32_t col = (uint32_t)(pt * a.nb + c0);
+            uint32_t rd[16], rs[16];
             float v[16], sum[16];
-            tmem_ld16(tl + col, v);
-            if (k > 1) {
-              tmem_ld16(tl + soff + col, sum);
-            } else {
-#pragma unroll
-              for (int u = 0; u < 16; ++u) sum[u] = 0.f;
-            }
+            tmem_ld16_async(tl + col, rd);
+            if (k > 1) tmem_ld16_async(tl + soff + col, rs);
+            tmem_ld_wait();
 #pragma unroll
             for (int u = 0; u < 16; ++u) {
-              v[u] *= scale;
-              sum[u] += v[u];
+              v[u] = __uint_as_float(rd[u]) * scale;
+              sum[u] = (k > 1 ? __uint_as_float(rs[u]) : 0.f) + v[u];
             }
             if (next) {
               tmem_st16(tl + soff + col, sum);
             } else if (pv) {
-              float* srow = a.S + ((long)w * twoN + c0) * a.lds + p;
+              float* srow = a.S + ((long)w * 2 * N + cpart * N + i0) * a.lds + p;
 #pragma unroll
               for (int u = 0; u < 16; ++u)
-                if (c0 + u < twoN) srow[(long)u * a.lds] = sum[u];
+                if (i0 + u < N) srow[(long)u * a.lds] = sum[u];
             }
             if (!next || !pv) continue;
+            // row i gets column p (real half) or Mp + p negated (imaginary
+            // half); row NH + i gets the other column
+            const uint32_t ra = (uint32_t)(i0 >> 3) * 1024u;
+            const uint32_t rb = ra + (uint32_t)(NH >> 3) * 1024u;
+            const float sa = cpart ? -1.f : 1.f;
 #pragma unroll
             for (int u = 0; u < 16; ++u) {
-              const int n = c0 + u;
-              if (n >= twoN) break;
-              const float t = v[u];
-              if (n < a.N) {
-                put_op<TF32>(bop, a.nb, n, p, t);
-                put_op<TF32>(bop, a.nb, a.N + n, a.Mp + p, t);
-              } else {
-                put_op<TF32>(bop, a.nb, n - a.N, a.Mp + p, -t);
-                put_op<TF32>(bop, a.nb, n, p, t);
-              }
+              if (i0 + u >= N) break;
+              const uint32_t blk = (uint32_t)(u >> 3) * 1024u;
+              const uint32_t oa = cpart ? offq[u & 7] : offp[u & 7];
+              const uint32_t ob = cpart ? offp[u & 7] : offq[u & 7];
+              put_op<TF32>(bop, oa + ra + blk, sa * v[u]);
+              put_op<TF32>(bop, ob + rb + blk, v[u]);
             }
           }
         }
@@ -270,7 +296,8 @@ constexpr int kSmemFixed = 1024 /*align*/ + 256 /*barriers*/;
 bool series_plan(int lo_kind, int N, int M, int Mp, tc::SeriesArgs* sa, int* smem) {
   if (N < 1 || M < 1 || Mp < M || Mp % 16) return false;
   const int elem = lo_kind == LO_TF32 ? 4 : 2;
-  const int nb = (2 * N + 15) / 16 * 16;
+  const int nh = (N + 15) / 16 * 16;
+  const int nb = 2 * nh;
   const int kblocks = (2 * Mp * elem + tc::BKB - 1) / tc::BKB;
   const int ptiles = (M + tc::BM - 1) / tc::BM;
   // the product and the running sum side by side in tensor memory
@@ -283,6 +310,7 @@ bool series_plan(int lo_kind, int N, int M, int Mp, tc::SeriesArgs* sa, int* sme
   uint32_t tcols = 32;
   while (tcols < (uint32_t)(2 * ptiles * nb)) tcols <<= 1;
   if (sa) {
+    sa->nh = nh;
     sa->nb = nb;
     sa->kblocks = kblocks;
     sa->ptiles = ptiles;
@@ -318,7 +346,11 @@ int tc_taylor_series(const void* V, const void* T0, float* S, long lds, int lo_k
   const int eb = tf32 ? 4 : 2;
   CUtensorMap tv, tt;
   AFQ_TRY(make_tmap_3d(&tv, V, eb, W, M, 2L * Mp, 2L * Mp, (long)M * 2 * Mp, tc::BM));
-  AFQ_TRY(make_tmap_3d(&tt, T0, eb, W, 2L * N, 2L * Mp, 2L * Mp, 2L * N * 2 * Mp, sa.nb));
+  // T0 rows (w, c, i) -> operand rows c NH + i: dims (K, i, c, w), box (K block, NH, 2, 1)
+  const long tdims[4] = {2L * Mp, N, 2, W};
+  const long tstr[3] = {2L * Mp * eb, (long)N * 2 * Mp * eb, 2L * N * 2 * Mp * eb};
+  const int tbox[4] = {tc::BKB / eb, sa.nh, 2, 1};
+  AFQ_TRY(make_tmap_nd(&tt, T0, eb, 4, tdims, tstr, tbox));
   const int grid = W < tc_sm_count() ? W : tc_sm_count();
   if (tf32) {
     static bool attr = false;
@@ -327,7 +359,7 @@ int tc_taylor_series(const void* V, const void* T0, float* S, long lds, int lo_k
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax));
       attr = true;
     }
-    AFQ_LAUNCH(tc::k_taylor_series<true>, grid, 192, smem, st, tv, tt, sa, err);
+    AFQ_LAUNCH(tc::k_taylor_series<true>, grid, tc::kSeriesThreads, smem, st, tv, tt, sa, err);
   } else {
     static bool attr = false;
     if (!attr) {
@@ -335,7 +367,7 @@ int tc_taylor_series(const void* V, const void* T0, float* S, long lds, int lo_k
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax));
       attr = true;
     }
-    AFQ_LAUNCH(tc::k_taylor_series<false>, grid, 192, smem, st, tv, tt, sa, err);
+    AFQ_LAUNCH(tc::k_taylor_series<false>, grid, tc::kSeriesThreads, smem, st, tv, tt, sa, err);
   }
   return AFQMC_OK;
 }

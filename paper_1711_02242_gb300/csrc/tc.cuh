@@ -62,6 +62,8 @@ int make_tmap(CUtensorMap* m, const void* base, int elem_bytes, long rows, long 
               int box_rows);
 int make_tmap_3d(CUtensorMap* m, const void* base, int elem_bytes, long planes, long rows,
                  long cols, long pitch, long plane_stride, int box_rows, int box_planes = 1);
+int make_tmap_nd(CUtensorMap* m, const void* base, int elem_bytes, int rank, const long* dims,
+                 const long* stride_bytes, const int* box);
 int tc_sm_count();
 
 // Exchange blocking: RG Cholesky vectors x CW walkers per 128 x 256 tile, the

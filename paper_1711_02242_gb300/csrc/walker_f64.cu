@@ -88,8 +88,78 @@ __global__ void __launch_bounds__(256) k_field(FieldArgs a) {
   r = block_sum(s5, sh); if (threadIdx.x == 0) a.scal[8L * w + 5] = r;
 }
 
+// Mixed path: the same fields, force bias and sums with the force bias taken
+// in FP32 (t comes from an FP32 accumulator and x only feeds the BF16/TF32
+// V contraction; float64 hypot and division run on GB300's slow FP64 pipe).
+// Each thread sums its fields in FP32; the six per-walker sums are reduced in
+// float64 in a fixed order (warps, then the block's warps in turn).
+__global__ void __launch_bounds__(256) k_field_lo(FieldArgs a) {
+  __shared__ double sh[8][6];
+  const int w = blockIdx.x;
+  const bool alive = walker_alive(a.wt, w);
+  const long base = (long)w * 2 * a.G;
+  const float* tr = a.t32 + base;
+  const float* ti = tr + a.G;
+  const long xl = (long)w * 2 * a.Gp;
+  const float sdt = (float)a.sdt, cap = (float)a.fb_cap;
+  const bool phaseless = a.mode == AFQMC_PHASELESS;
+  const uint32_t step = (uint32_t)*a.dstep;
+  float s[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  const int npair = (a.G + 1) / 2;
+  for (int k = threadIdx.x; k < npair; k += blockDim.x) {
+    double xa, xb;
+    field_pair_f32(a.seed, step, (uint32_t)w, (uint32_t)k, &xa, &xb);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int g = 2 * k + h;
+      if (g >= a.G) break;
+      const float xi = (float)(h ? xb : xa);
+      const float cg = (float)a.c[g];
+      float br = 0.f, bi = 0.f;
+      if (phaseless) {
+        br = sdt * ti[g];
+        bi = -sdt * (tr[g] - cg);
+        if (cap > 0.f) {
+          const float mag = hypotf(br, bi);
+          if (mag > cap) {
+            const float f = cap / mag;
+            br *= f;
+            bi *= f;
+          }
+        }
+      }
+      float vr = xi - br, vi = -bi;
+      if (!alive) vr = vi = 0.f;
+      store_lo(a.x_lo, a.lo_kind, xl + g, vr);
+      store_lo(a.x_lo, a.lo_kind, xl + a.Gp + g, vi);
+      s[0] = fmaf(xi, br, s[0]);
+      s[1] = fmaf(xi, bi, s[1]);
+      s[2] += br * br - bi * bi;
+      s[3] += 2.f * br * bi;
+      s[4] = fmaf(cg, vr, s[4]);
+      s[5] = fmaf(cg, vi, s[5]);
+    }
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    const double d = warp_sum((double)s[i]);
+    if (lane == 0) sh[wid][i] = d;
+  }
+  __syncthreads();
+  if (threadIdx.x < 6) {
+    double r = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) r += sh[q][threadIdx.x];
+    a.scal[8L * w + threadIdx.x] = r;
+  }
+}
+
 int launch_field(const FieldArgs& a, cudaStream_t st) {
-  AFQ_LAUNCH(k_field, a.W, 256, 0, st, a);
+  if (a.x_lo && a.t32 && !a.x && !a.t) {
+    AFQ_LAUNCH(k_field_lo, a.W, 256, 0, st, a);
+  } else {
+    AFQ_LAUNCH(k_field, a.W, 256, 0, st, a);
+  }
   return AFQMC_OK;
 }
 

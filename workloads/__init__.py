@@ -13,9 +13,16 @@ paper, Sec. 2 "The AFQMC method", Eqs. bo_ham2 / bo_ham_matel):
   deviation) in row-major order, then mirrored.
 * each Cholesky vector ``L[g]`` (``g = 0 .. nchol-1``) is real symmetric
   ``M x M``: upper-triangle entries including the diagonal drawn
-  ``N(0, 0.5 * exp(-g / M))`` in row-major order, then mirrored.  The
+  ``N(0, a * exp(-g / M))`` in row-major order, then mirrored.  The
   two-electron tensor ``v_pqrs = sum_g L[g]_pr L[g]_qs`` (Sec. 2.3, Eq. chol)
   is then positive semi-definite by construction.
+* the amplitude ``a`` is 0.5 for the 12-orbital, 48-vector workload and, for
+  the others, 0.5 scaled so that ``sum_g ||L[g]||_F^2`` -- the variance of
+  the one-body operator ``sum_g x_g L[g]`` under unit Gaussian fields -- is
+  the same as there (``l_amplitude``).  Drawn with 0.5 at every size, the
+  300-orbital operator would have ``||sqrt(dt) sum_g x_g L[g]|| ~ 15``: its
+  sixth-order Taylor series diverges and every walker overflows within a
+  few steps, and the energies reach 2e5 Ha.
 * draws come from numpy's PCG64 generator seeded ``1000 + config_index``;
   ``h1`` is drawn first, then ``L[0]``, ``L[1]``, ...
 * the nuclear repulsion ``H0`` is 0.
@@ -32,6 +39,7 @@ __all__ = [
     "CONFIGS",
     "config",
     "hamiltonian",
+    "l_amplitude",
     "batched_systems",
     "request_stream",
 ]
@@ -56,7 +64,17 @@ class Workload:
     ham_seed: int = 1000  # PCG64 seed of the Hamiltonian draw
 
     def hamiltonian(self):
-        return hamiltonian(self.M, self.nchol, self.ham_seed)
+        return hamiltonian(self.M, self.nchol, self.ham_seed,
+                           l_scale=l_amplitude(self.M, self.nchol))
+
+
+def l_amplitude(M: int, nchol: int, decay: float | None = None) -> float:
+    """Amplitude of ``L[0]`` that gives ``sum_g ||L[g]||_F^2`` (expected) the
+    value it has for M = 12, nchol = 48, decay 12, amplitude 0.5."""
+    def spread(m, n, d):
+        return m * m * sum(math.exp(-2.0 * g / d) for g in range(n))
+
+    return 0.5 * math.sqrt(spread(12, 48, 12.0) / spread(M, nchol, float(decay or M)))
 
 
 # The five workloads of the phaseless-AFQMC hot path.  Index i uses PCG64
