@@ -433,9 +433,10 @@ static int step_once(afqmc_state* s) {
   const int64_t n = s->h_step;
   if (p.qr_period && n % p.qr_period == 0) {
     prof_begin(s, AFQMC_PH_QR);
-    MgsArgs ma{W, M, N, b.phiT, b.wt};
+    // Phi -> Q; Theta is unchanged and log det S drops by sum_k log r_kk,
+    // which the kernel applies to ld (no new overlap needed)
+    MgsArgs ma{W, M, N, b.phiT, b.wt, b.ld};
     AFQ_TRY(launch_mgs(ma, s->st));
-    AFQ_TRY(overlap_update(s, true));
     prof_end(s);
   }
   if (p.pc_period && n % p.pc_period == 0) {

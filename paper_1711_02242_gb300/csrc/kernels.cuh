@@ -130,6 +130,7 @@ struct MgsArgs {
   int W, M, N;
   double* phiT;  // [W][2][N][M] in place
   const double* wt;
+  double* ld;    // [W][2]: log <Psi_T|Psi> of live walkers, lowered by 2 sum_k log r_kk
 };
 int launch_mgs(const MgsArgs& a, cudaStream_t st);
 

@@ -286,18 +286,31 @@ __global__ void __launch_bounds__(128) k_lu_inv(LuArgs a) {
   }
   __syncthreads();
   for (int k = 0; k < N; ++k) {
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {
+      // pivot: the largest |a_rk|^2 over rows r >= k, the first such row on ties
       int best = k;
       double bv = -1.0;
-      for (int r = k; r < N; ++r) {
-        const double v = hypot(A[r * N + k].x, A[r * N + k].y);
+      for (int r = k + threadIdx.x; r < N; r += 32) {
+        const double2 x = A[r * N + k];
+        const double v = x.x * x.x + x.y * x.y;
         if (v > bv) {
           bv = v;
           best = r;
         }
       }
-      piv = best;
-      if (!(bv > 0.0)) singular = 1;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        const int ob = __shfl_xor_sync(0xffffffffu, best, o);
+        if (ov > bv || (ov == bv && ob < best)) {
+          bv = ov;
+          best = ob;
+        }
+      }
+      if (threadIdx.x == 0) {
+        piv = best;
+        if (!(bv > 0.0)) singular = 1;
+      }
     }
     __syncthreads();
     if (singular) break;
@@ -441,36 +454,74 @@ int launch_theta(const ThetaArgs& a, cudaStream_t st) {
 
 // ------------------------------------------------------- fused overlap ------
 // One block per walker, float64 throughout (Theorem 1.1, Eq. precomputing):
-//   1. S = V_T^T Phi (N x N complex, each entry a length-M dot product);
-//   2. Gauss-Jordan elimination with partial pivoting (largest modulus):
-//      S^-1 and log det S = sum log p_k (+ i pi per row swap);
+//   1. S = V_T^T Phi (N x N complex): V_T^T and Phi^T are staged through
+//      shared memory OV_P orbitals at a time (coalesced loads), each thread
+//      accumulating up to OV_R entries of S (re and im planes);
+//   2. Gauss-Jordan elimination with partial pivoting (largest modulus,
+//      searched by one warp): S^-1 and log det S = sum log p_k (+ i pi per
+//      row swap);
 //   3. Theta^T[i][p] = sum_j S^-1[j][i] Phi^T[j][p].
 // log <Psi_T|Psi> = 2 log det S (both spins), phase wrapped to (-pi, pi].
 // Every walker is computed; Theta and log det are stored for live walkers.
-__global__ void __launch_bounds__(256) k_overlap(OverlapArgs a) {
+namespace {
+constexpr int OV_P = 32, OV_R = 8, OV_T = 256;
+}
+__global__ void __launch_bounds__(OV_T) k_overlap(OverlapArgs a) {
   extern __shared__ double2 ov_sm[];
   const int w = blockIdx.x;
   const bool live = !a.wt || walker_alive(a.wt, w);
   const int N = a.N, M = a.M;
   double2* A = ov_sm;            // [N][N]
   double2* Inv = ov_sm + N * N;  // [N][N]
+  double* Vs = reinterpret_cast<double*>(ov_sm + 2 * N * N);  // [N][OV_P + 1]
+  double* Ps = Vs + N * (OV_P + 1);                           // [2N][OV_P + 1]
   __shared__ int piv, swaps, singular;
   __shared__ double logabs, phase;
   const double* fr = a.phiT + (long)w * 2 * N * M;
   const double* fi = fr + (long)N * M;
-  for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x) {
-    const int i = idx / N, j = idx % N;
-    const double* v = a.VTt + (long)i * M;
-    const double* xr = fr + (long)j * M;
-    const double* xi = fi + (long)j * M;
-    double sr = 0.0, si = 0.0;
-    for (int p = 0; p < M; ++p) {
-      sr = fma(v[p], xr[p], sr);
-      si = fma(v[p], xi[p], si);
+  const int nout = 2 * N * N;  // (i, c, j): S_c[i][j], c = re / im plane
+  for (int o0 = 0; o0 < nout; o0 += OV_T * OV_R) {
+    double acc[OV_R];
+#pragma unroll
+    for (int r = 0; r < OV_R; ++r) acc[r] = 0.0;
+    for (int p0 = 0; p0 < M; p0 += OV_P) {
+      for (int idx = threadIdx.x; idx < 3 * N * OV_P; idx += OV_T) {
+        const int row = idx / OV_P, pp = idx % OV_P, pc = p0 + pp;
+        double v = 0.0;
+        if (pc < M) v = row < N ? a.VTt[(long)row * M + pc] : fr[(long)(row - N) * M + pc];
+        if (row < N)
+          Vs[row * (OV_P + 1) + pp] = v;
+        else
+          Ps[(row - N) * (OV_P + 1) + pp] = v;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int r = 0; r < OV_R; ++r) {
+        const int o = o0 + threadIdx.x + r * OV_T;
+        if (o < nout) {
+          const int i = o / (2 * N), cj = o % (2 * N);
+          const double* vs = Vs + i * (OV_P + 1);
+          const double* ps = Ps + cj * (OV_P + 1);
+          double t = acc[r];
+#pragma unroll 8
+          for (int pp = 0; pp < OV_P; ++pp) t = fma(vs[pp], ps[pp], t);
+          acc[r] = t;
+        }
+      }
+      __syncthreads();
     }
-    A[idx] = make_double2(sr, si);
-    Inv[idx] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+#pragma unroll
+    for (int r = 0; r < OV_R; ++r) {
+      const int o = o0 + threadIdx.x + r * OV_T;
+      if (o < nout) {
+        const int i = o / (2 * N), cj = o % (2 * N), c = cj / N, j = cj % N;
+        double* d = reinterpret_cast<double*>(&A[i * N + j]);
+        d[c] = acc[r];
+      }
+    }
   }
+  for (int idx = threadIdx.x; idx < N * N; idx += OV_T)
+    Inv[idx] = make_double2(idx / N == idx % N ? 1.0 : 0.0, 0.0);
   if (threadIdx.x == 0) {
     logabs = 0.0;
     phase = 0.0;
@@ -479,18 +530,31 @@ __global__ void __launch_bounds__(256) k_overlap(OverlapArgs a) {
   }
   __syncthreads();
   for (int k = 0; k < N; ++k) {
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {
+      // pivot: the largest |a_rk|^2 over rows r >= k, the first such row on ties
       int best = k;
       double bv = -1.0;
-      for (int r = k; r < N; ++r) {
-        const double v = hypot(A[r * N + k].x, A[r * N + k].y);
+      for (int r = k + threadIdx.x; r < N; r += 32) {
+        const double2 x = A[r * N + k];
+        const double v = x.x * x.x + x.y * x.y;
         if (v > bv) {
           bv = v;
           best = r;
         }
       }
-      piv = best;
-      if (!(bv > 0.0)) singular = 1;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        const int ob = __shfl_xor_sync(0xffffffffu, best, o);
+        if (ov > bv || (ov == bv && ob < best)) {
+          bv = ov;
+          best = ob;
+        }
+      }
+      if (threadIdx.x == 0) {
+        piv = best;
+        if (!(bv > 0.0)) singular = 1;
+      }
     }
     __syncthreads();
     if (singular) break;
@@ -588,7 +652,7 @@ __global__ void __launch_bounds__(256) k_overlap(OverlapArgs a) {
 }
 
 int launch_overlap(const OverlapArgs& a, cudaStream_t st) {
-  const size_t smem = 2ull * a.N * a.N * sizeof(double2);
+  const size_t smem = 2ull * a.N * a.N * sizeof(double2) + 3ull * a.N * (OV_P + 1) * sizeof(double);
   if (smem > 200 * 1024) {
     set_error("overlap: N=%d too large", a.N);
     return AFQMC_EUNSUPPORTED;
@@ -599,7 +663,7 @@ int launch_overlap(const OverlapArgs& a, cudaStream_t st) {
                                   200 * 1024));
     attr = true;
   }
-  AFQ_LAUNCH(k_overlap, a.W, 256, smem, st, a);
+  AFQ_LAUNCH(k_overlap, a.W, OV_T, smem, st, a);
   return AFQMC_OK;
 }
 
@@ -649,49 +713,78 @@ int launch_weight(const WeightArgs& a, cudaStream_t st) {
 }
 
 // -------------------------------------------------- modified Gram-Schmidt --
-// Sec. 3.4.5: sweep the orbitals k = 1..N; each is orthogonalised against the
-// finished ones one projection at a time (the projection uses the partially
-// updated vector), then normalised.  Each thread owns a fixed set of rows p,
-// so only the block sums need barriers.
+// Sec. 3.4.5: orbitals k = 1..N in turn; column k is orthogonalised against
+// the finished columns one projection at a time (each projection uses the
+// partially updated vector), then normalised.  The projections are applied
+// as soon as a column is finished ("right-looking"): once q_k is normalised,
+// every later column j takes v_j -= <q_k|v_j> q_k, one warp per column, so
+// column j sees exactly the projections q_0, q_1, ... in order, as in the
+// column-by-column form, with two block barriers per k instead of two block
+// reductions per (j, k) pair.
+// Phi = Q R with R upper triangular and r_kk = |v_k| > 0, so S = V_T^T Phi
+// becomes S R^-1: Theta = Phi S^-1 is unchanged and log det S drops by
+// sum_k log r_kk (det R real and positive: the phase is unchanged).  The
+// kernel lowers log <Psi_T|Psi> = 2 log det S by 2 sum_k log r_kk; the
+// overlap need not be recomputed.
 __global__ void __launch_bounds__(256) k_mgs(MgsArgs a) {
+  extern __shared__ double2 q_sm[];  // the finished column q_k, [M]
   __shared__ double sh[32];
   const int w = blockIdx.x;
   if (!walker_alive(a.wt, w)) return;
   const int M = a.M, N = a.N;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   double* re = a.phiT + (long)w * 2 * N * M;
   double* im = re + (long)N * M;
+  double logr = 0.0;
   for (int k = 0; k < N; ++k) {
     double* vr = re + (long)k * M;
     double* vi = im + (long)k * M;
-    for (int j = 0; j < k; ++j) {
-      const double* qr = re + (long)j * M;
-      const double* qi = im + (long)j * M;
-      double sr = 0.0, si = 0.0;
-      for (int p = threadIdx.x; p < M; p += blockDim.x) {
-        sr += qr[p] * vr[p] + qi[p] * vi[p];
-        si += qr[p] * vi[p] - qi[p] * vr[p];
-      }
-      sr = block_sum(sr, sh);
-      si = block_sum(si, sh);
-      for (int p = threadIdx.x; p < M; p += blockDim.x) {
-        const double a_ = qr[p], b_ = qi[p];
-        vr[p] -= sr * a_ - si * b_;
-        vi[p] -= sr * b_ + si * a_;
-      }
-    }
     double nn = 0.0;
     for (int p = threadIdx.x; p < M; p += blockDim.x) nn += vr[p] * vr[p] + vi[p] * vi[p];
     nn = block_sum(nn, sh);
     const double inv = 1.0 / sqrt(nn);
+    logr += 0.5 * log(nn);
     for (int p = threadIdx.x; p < M; p += blockDim.x) {
-      vr[p] *= inv;
-      vi[p] *= inv;
+      const double qr = vr[p] * inv, qi = vi[p] * inv;
+      vr[p] = qr;
+      vi[p] = qi;
+      q_sm[p] = make_double2(qr, qi);
     }
+    __syncthreads();
+    for (int j = k + 1 + warp; j < N; j += nwarp) {
+      double* ur = re + (long)j * M;
+      double* ui = im + (long)j * M;
+      double sr = 0.0, si = 0.0;
+      for (int p = lane; p < M; p += 32) {
+        const double2 q = q_sm[p];
+        sr += q.x * ur[p] + q.y * ui[p];
+        si += q.x * ui[p] - q.y * ur[p];
+      }
+      sr = warp_sum(sr);
+      si = warp_sum(si);
+      for (int p = lane; p < M; p += 32) {
+        const double2 q = q_sm[p];
+        ur[p] -= sr * q.x - si * q.y;
+        ui[p] -= sr * q.y + si * q.x;
+      }
+    }
+    __syncthreads();
   }
+  if (threadIdx.x == 0 && a.ld) a.ld[2L * w] -= 2.0 * logr;
 }
 
 int launch_mgs(const MgsArgs& a, cudaStream_t st) {
-  AFQ_LAUNCH(k_mgs, a.W, 256, 0, st, a);
+  const size_t smem = sizeof(double2) * (size_t)a.M;
+  if (smem > 200 * 1024) {
+    set_error("mgs: M=%d too large", a.M);
+    return AFQMC_EUNSUPPORTED;
+  }
+  static bool attr = false;
+  if (!attr) {
+    AFQ_CUDA(cudaFuncSetAttribute(k_mgs, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    attr = true;
+  }
+  AFQ_LAUNCH(k_mgs, a.W, 256, smem, st, a);
   return AFQMC_OK;
 }
 
