@@ -346,16 +346,18 @@ __global__ void __launch_bounds__(128) k_lu_inv(LuArgs a) {
       if (r == k || j == k) continue;
       const double2 f = A[r * N + k];
       const double2 v = A[k * N + j];
-      A[r * N + j].x -= f.x * v.x - f.y * v.y;
-      A[r * N + j].y -= f.x * v.y + f.y * v.x;
+      double2& d = A[r * N + j];
+      d.x = fma(-f.x, v.x, fma(f.y, v.y, d.x));
+      d.y = fma(-f.x, v.y, fma(-f.y, v.x, d.y));
     }
     for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x) {
       const int r = idx / N, j = idx % N;
       if (r == k) continue;
       const double2 f = A[r * N + k];
       const double2 v = Inv[k * N + j];
-      Inv[r * N + j].x -= f.x * v.x - f.y * v.y;
-      Inv[r * N + j].y -= f.x * v.y + f.y * v.x;
+      double2& d = Inv[r * N + j];
+      d.x = fma(-f.x, v.x, fma(f.y, v.y, d.x));
+      d.y = fma(-f.x, v.y, fma(-f.y, v.x, d.y));
     }
     __syncthreads();
     for (int r = threadIdx.x; r < N; r += blockDim.x)
@@ -589,16 +591,18 @@ __global__ void __launch_bounds__(OV_T) k_overlap(OverlapArgs a) {
       if (r == k || j == k) continue;
       const double2 f = A[r * N + k];
       const double2 v = A[k * N + j];
-      A[r * N + j].x -= f.x * v.x - f.y * v.y;
-      A[r * N + j].y -= f.x * v.y + f.y * v.x;
+      double2& d = A[r * N + j];
+      d.x = fma(-f.x, v.x, fma(f.y, v.y, d.x));
+      d.y = fma(-f.x, v.y, fma(-f.y, v.x, d.y));
     }
     for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x) {
       const int r = idx / N, j = idx % N;
       if (r == k) continue;
       const double2 f = A[r * N + k];
       const double2 v = Inv[k * N + j];
-      Inv[r * N + j].x -= f.x * v.x - f.y * v.y;
-      Inv[r * N + j].y -= f.x * v.y + f.y * v.x;
+      double2& d = Inv[r * N + j];
+      d.x = fma(-f.x, v.x, fma(f.y, v.y, d.x));
+      d.y = fma(-f.x, v.y, fma(-f.y, v.x, d.y));
     }
     __syncthreads();
     for (int r = threadIdx.x; r < N; r += blockDim.x)
@@ -740,7 +744,7 @@ __global__ void __launch_bounds__(256) k_mgs(MgsArgs a) {
     double* vr = re + (long)k * M;
     double* vi = im + (long)k * M;
     double nn = 0.0;
-    for (int p = threadIdx.x; p < M; p += blockDim.x) nn += vr[p] * vr[p] + vi[p] * vi[p];
+    for (int p = threadIdx.x; p < M; p += blockDim.x) nn = fma(vr[p], vr[p], fma(vi[p], vi[p], nn));
     nn = block_sum(nn, sh);
     const double inv = 1.0 / sqrt(nn);
     logr += 0.5 * log(nn);
@@ -754,18 +758,21 @@ __global__ void __launch_bounds__(256) k_mgs(MgsArgs a) {
     for (int j = k + 1 + warp; j < N; j += nwarp) {
       double* ur = re + (long)j * M;
       double* ui = im + (long)j * M;
+      // <q_k|v_j> and v_j -= <q_k|v_j> q_k as chains of FMAs (the FP64 pipe
+      // is the bound: no separate multiplies or adds)
       double sr = 0.0, si = 0.0;
       for (int p = lane; p < M; p += 32) {
         const double2 q = q_sm[p];
-        sr += q.x * ur[p] + q.y * ui[p];
-        si += q.x * ui[p] - q.y * ur[p];
+        const double a_ = ur[p], b_ = ui[p];
+        sr = fma(q.x, a_, fma(q.y, b_, sr));
+        si = fma(q.x, b_, fma(-q.y, a_, si));
       }
       sr = warp_sum(sr);
       si = warp_sum(si);
       for (int p = lane; p < M; p += 32) {
         const double2 q = q_sm[p];
-        ur[p] -= sr * q.x - si * q.y;
-        ui[p] -= sr * q.y + si * q.x;
+        ur[p] = fma(-sr, q.x, fma(si, q.y, ur[p]));
+        ui[p] = fma(-sr, q.y, fma(-si, q.x, ui[p]));
       }
     }
     __syncthreads();
