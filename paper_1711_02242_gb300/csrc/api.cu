@@ -1,4 +1,5 @@
 // C ABI of the AFQMC library: workspace plan, set-up, step sequencing.
+#include <cmath>
 #include <cstdarg>
 #include <cstdlib>
 #include <cstring>
@@ -57,6 +58,8 @@ size_t plan(const afqmc_params& p, Bufs* b, char* base) {
   b->Bh = a.take<double>(M * M);
   b->VTt = a.take<double>(N * M);
   b->h1 = a.take<double>(M * M);
+  b->Qb = a.take<double>(M * M);
+  b->QTb = a.take<double>(M * M);
   // walkers
   b->phiT = a.take<double>(W * 2 * N * M);
   b->thetaT = a.take<double>(W * 2 * N * M);
@@ -117,6 +120,8 @@ size_t plan(const afqmc_params& p, Bufs* b, char* base) {
   b->E1 = s2.take<double>(M * M);
   b->X = s2.take<double>(M * M);
   b->red = s2.take<double>(8);
+  b->ych = (int)(G < 32 ? G : 32);
+  b->Ych = s2.take<double>((size_t)b->ych * M * M);
   b->P = (int)P;
   b->nchunk = (int)nchunk;
   b->gc = exchange_chunk(p.N, p.nchol);
@@ -187,6 +192,7 @@ int overlap_update(afqmc_state* s, bool into_ld) {
   const Bufs& b = s->b;
   // S = V_T^T Phi, S^-1, log det and Theta in one float64 kernel per walker
   OverlapArgs ov{p.nwalkers, p.M, p.N, b.VTt, b.phiT, b.thetaT, into_ld ? b.ld : b.ld_new, b.wt};
+  ov.unit_trial = 1;  // V_T' = [I_N; 0] in the trial-adapted basis
   if (b.mixed) {
     ov.th_lo = b.th_lo;
     ov.lo_kind = b.lo_kind;
@@ -518,18 +524,108 @@ static int expm_device(afqmc_state* s) {
   return AFQMC_OK;
 }
 
+// An orthogonal M x M matrix (row-major) whose first N columns are the trial
+// orbitals: the Householder QR of the trial (reflectors H_1 .. H_N) gives
+// Q_H = H_1 ... H_N, whose first N columns span the trial and whose other
+// columns are an orthonormal basis of the complement; the first N columns are
+// then set to the trial itself.
+static void complete_basis(const double* trial, int M, int N, std::vector<double>& q) {
+  std::vector<double> a(trial, trial + (size_t)M * N);  // [M][N]
+  std::vector<double> v((size_t)N * M, 0.0);           // reflector k: v[k][k .. M)
+  for (int k = 0; k < N; ++k) {
+    double nrm = 0.0;
+    for (int r = k; r < M; ++r) nrm += a[(size_t)r * N + k] * a[(size_t)r * N + k];
+    nrm = std::sqrt(nrm);
+    double* vk = &v[(size_t)k * M];
+    const double alpha = a[(size_t)k * N + k] >= 0.0 ? -nrm : nrm;
+    for (int r = k; r < M; ++r) vk[r] = a[(size_t)r * N + k];
+    vk[k] -= alpha;
+    double vn = 0.0;
+    for (int r = k; r < M; ++r) vn += vk[r] * vk[r];
+    vn = std::sqrt(vn);
+    if (vn > 0.0)
+      for (int r = k; r < M; ++r) vk[r] /= vn;
+    for (int j = k; j < N; ++j) {
+      double d = 0.0;
+      for (int r = k; r < M; ++r) d += vk[r] * a[(size_t)r * N + j];
+      for (int r = k; r < M; ++r) a[(size_t)r * N + j] -= 2.0 * d * vk[r];
+    }
+  }
+  q.assign((size_t)M * M, 0.0);
+  for (int i = 0; i < M; ++i) q[(size_t)i * M + i] = 1.0;
+  for (int k = N - 1; k >= 0; --k) {  // Q_H = H_1 (H_2 (... (H_N I)))
+    const double* vk = &v[(size_t)k * M];
+    for (int c = 0; c < M; ++c) {
+      double d = 0.0;
+      for (int r = k; r < M; ++r) d += vk[r] * q[(size_t)r * M + c];
+      for (int r = k; r < M; ++r) q[(size_t)r * M + c] -= 2.0 * d * vk[r];
+    }
+  }
+  for (int r = 0; r < M; ++r)
+    for (int i = 0; i < N; ++i) q[(size_t)r * M + i] = trial[(size_t)r * N + i];
+}
+
+// C = A B^T for M x M float64 matrices batched over `batch` (strides 0 = shared).
+static int gemm_sq(const double* A, long sA, const double* B, long sB, double* C, long sC, int M,
+                   int batch, cudaStream_t st) {
+  GemmF64 g;
+  g.m = g.n = g.k = M;
+  g.batch = batch;
+  g.A = A;
+  g.lda = M;
+  g.sAb = sA;
+  g.B = B;
+  g.ldb = M;
+  g.sBb = sB;
+  g.C = C;
+  g.ldc = M;
+  g.sCb = sC;
+  return gemm_nt_f64(g, st);
+}
+
+// The run works in the trial-adapted orthonormal basis {Q_p}: h' = Q^T h Q,
+// L'_g = Q^T L_g Q and V_T' = Q^T V_T = [I_N; 0].  Energies, overlap ratios,
+// weights and the fields' force bias are the same in any orthonormal basis;
+// what changes is that S = V_T'^T Phi' is the top N x N block of Phi' (no
+// product) and the top N rows of Theta' = Phi' S^-1 are the identity.
+// Walkers cross the API in the caller's basis: Phi = Q Phi'.
 static int setup_device(afqmc_state* s, const double* h1, const double* L, const double* trial) {
   const afqmc_params& p = s->p;
   const Bufs& b = s->b;
   const int M = p.M, N = p.N, G = p.nchol, W = p.nwalkers;
   cudaStream_t st = s->st;
-  std::vector<double> vtt((size_t)N * M);
+  // the trial's columns must be orthonormal
+  double dev = 0.0;
   for (int i = 0; i < N; ++i)
-    for (int q = 0; q < M; ++q) vtt[(size_t)i * M + q] = trial[(size_t)q * N + i];
+    for (int j = 0; j <= i; ++j) {
+      double d = 0.0;
+      for (int q = 0; q < M; ++q) d += trial[(size_t)q * N + i] * trial[(size_t)q * N + j];
+      dev = std::fmax(dev, std::fabs(d - (i == j ? 1.0 : 0.0)));
+    }
+  if (!(dev < 1e-8)) {
+    set_error("trial columns are not orthonormal (max |V^T V - I| = %.3g)", dev);
+    return AFQMC_EINVAL;
+  }
+  std::vector<double> qh, qt((size_t)M * M), vtt((size_t)N * M, 0.0);
+  complete_basis(trial, M, N, qh);
+  for (int r = 0; r < M; ++r)
+    for (int c = 0; c < M; ++c) qt[(size_t)c * M + r] = qh[(size_t)r * M + c];
+  for (int i = 0; i < N; ++i) vtt[(size_t)i * M + i] = 1.0;
+  AFQ_CUDA(cudaMemcpyAsync(b.Qb, qh.data(), sizeof(double) * M * M, cudaMemcpyHostToDevice, st));
+  AFQ_CUDA(cudaMemcpyAsync(b.QTb, qt.data(), sizeof(double) * M * M, cudaMemcpyHostToDevice, st));
   AFQ_CUDA(cudaMemcpyAsync(b.VTt, vtt.data(), sizeof(double) * N * M, cudaMemcpyHostToDevice, st));
-  AFQ_CUDA(cudaMemcpyAsync(b.h1, h1, sizeof(double) * M * M, cudaMemcpyHostToDevice, st));
+  AFQ_CUDA(cudaMemcpyAsync(b.X, h1, sizeof(double) * M * M, cudaMemcpyHostToDevice, st));
   AFQ_CUDA(cudaMemcpyAsync(b.Lfull, L, sizeof(double) * G * M * M, cudaMemcpyHostToDevice, st));
   AFQ_CUDA(cudaMemsetAsync(b.counters, 0, 8 * sizeof(unsigned long long), st));
+  // h' = Q^T h Q and L'_g = Q^T L_g Q (h, L_g symmetric: B = h reads h^T)
+  AFQ_TRY(gemm_sq(b.QTb, 0, b.X, 0, b.E0, 0, M, 1, st));
+  AFQ_TRY(gemm_sq(b.E0, 0, b.QTb, 0, b.h1, 0, M, 1, st));
+  for (int g0 = 0; g0 < G; g0 += b.ych) {
+    const int nb = G - g0 < b.ych ? G - g0 : b.ych;
+    double* Lg = b.Lfull + (size_t)g0 * M * M;
+    AFQ_TRY(gemm_sq(b.QTb, 0, Lg, (long)M * M, b.Ych, (long)M * M, M, nb, st));
+    AFQ_TRY(gemm_sq(b.Ych, (long)M * M, b.QTb, 0, Lg, (long)M * M, M, nb, st));
+  }
   // packed, transposed Cholesky vectors for the V contraction
   AFQ_TRY(launch_pack_transpose(b.Lfull, b.LpT, G, M, st));
   // half-rotated vectors Lh_g = V_T^T L_g and hh = V_T^T h (Eq. precomputing2)
@@ -851,8 +947,19 @@ int afqmc_get_walkers(afqmc_state* s, double* phi, double* weight, double* logov
   const afqmc_params& p = s->p;
   const size_t W = p.nwalkers, N = p.N, M = p.M;
   if (phi) {
+    // back to the caller's basis: Phi^T = Phi'^T Q^T
+    GemmF64 g;
+    g.m = (int)(W * 2 * N);
+    g.n = g.k = (int)M;
+    g.A = s->b.phiT;
+    g.lda = (long)M;
+    g.B = s->b.Qb;
+    g.ldb = (long)M;
+    g.C = s->b.T0;
+    g.ldc = (long)M;
+    AFQ_TRY(gemm_nt_f64(g, s->st));
     std::vector<double> h(W * 2 * N * M);
-    AFQ_CUDA(cudaMemcpyAsync(h.data(), s->b.phiT, sizeof(double) * h.size(),
+    AFQ_CUDA(cudaMemcpyAsync(h.data(), s->b.T0, sizeof(double) * h.size(),
                              cudaMemcpyDeviceToHost, s->st));
     AFQ_CUDA(cudaStreamSynchronize(s->st));
     for (size_t w = 0; w < W; ++w)
@@ -885,7 +992,18 @@ int afqmc_set_walkers(afqmc_state* s, const double* phi, const double* weight) {
       for (size_t i = 0; i < N; ++i)
         for (size_t q = 0; q < M; ++q)
           h[((w * 2 + c) * N + i) * M + q] = phi[((w * M + q) * N + i) * 2 + c];
-  AFQ_CUDA(cudaMemcpyAsync(s->b.phiT, h.data(), sizeof(double) * h.size(), cudaMemcpyHostToDevice, s->st));
+  AFQ_CUDA(cudaMemcpyAsync(s->b.T0, h.data(), sizeof(double) * h.size(), cudaMemcpyHostToDevice, s->st));
+  // into the trial-adapted basis: Phi'^T = Phi^T Q
+  GemmF64 g;
+  g.m = (int)(W * 2 * N);
+  g.n = g.k = (int)M;
+  g.A = s->b.T0;
+  g.lda = (long)M;
+  g.B = s->b.QTb;
+  g.ldb = (long)M;
+  g.C = s->b.phiT;
+  g.ldc = (long)M;
+  AFQ_TRY(gemm_nt_f64(g, s->st));
   AFQ_CUDA(cudaMemcpyAsync(s->b.wt, weight, sizeof(double) * 2 * W, cudaMemcpyHostToDevice, s->st));
   AFQ_TRY(overlap_update(s, true));
   s->t_fresh = false;

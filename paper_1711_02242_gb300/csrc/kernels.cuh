@@ -100,6 +100,7 @@ struct OverlapArgs {
   const double* wt;    // alive mask (nullptr: all)
   void* th_lo = nullptr;
   int lo_kind = LO_NONE, Mp = 0;
+  int unit_trial = 0;  // VTt = [I_N | 0]: S is the top block of Phi, Theta's top rows I
 };
 int launch_overlap(const OverlapArgs& a, cudaStream_t st);
 

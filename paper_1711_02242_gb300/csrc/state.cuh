@@ -11,8 +11,10 @@ enum { CTR_STEP = 0, CTR_RECORDS = 1, CTR_NONFINITE = 2, CTR_STATUS = 3 };
 
 // Device buffers carved out of the caller's workspace.
 struct Bufs {
-  // constants of the run
+  // constants of the run (all in the trial-adapted basis, see setup_device)
   double *LpT, *Lh, *hh, *c, *Bh, *VTt, *h1;
+  // basis rotation: Qb[p][q] = Q_pq with Q[:, :N] the trial, QTb = Q^T
+  double *Qb, *QTb;
   // walkers
   double *phiT, *thetaT, *ld, *ld_new, *wt, *S, *Sinv, *t, *x, *scal, *eloc, *part;
   double *cum, *wtot, *last, *records;
@@ -20,8 +22,9 @@ struct Bufs {
   unsigned long long* counters;  // CTR_*
   // step scratch
   double *Y, *T0, *T1, *acc, *tmp_ld;
-  // set-up scratch (aliases the step scratch)
-  double *Lfull, *L2, *cLp, *E0, *E1, *X, *red;
+  // set-up scratch (aliases the step scratch); Ych: ych vectors of Q^T L_g
+  double *Lfull, *L2, *cLp, *E0, *E1, *X, *red, *Ych;
+  int ych = 0;
   int P, nchunk, gc;
   // mixed path: BF16 / TF32 operand copies and FP32 step buffers
   bool mixed = false;

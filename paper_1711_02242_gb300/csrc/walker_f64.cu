@@ -482,7 +482,14 @@ __global__ void __launch_bounds__(OV_T) k_overlap(OverlapArgs a) {
   const double* fr = a.phiT + (long)w * 2 * N * M;
   const double* fi = fr + (long)N * M;
   const int nout = 2 * N * N;  // (i, c, j): S_c[i][j], c = re / im plane
-  for (int o0 = 0; o0 < nout; o0 += OV_T * OV_R) {
+  if (a.unit_trial) {
+    // V_T = [I_N; 0]: S[i][j] = Phi[i][j], the top block of the orbitals
+    for (int idx = threadIdx.x; idx < N * N; idx += OV_T) {
+      const int i = idx / N, j = idx % N;
+      A[idx] = make_double2(fr[(long)j * M + i], fi[(long)j * M + i]);
+    }
+  }
+  for (int o0 = 0; o0 < (a.unit_trial ? 0 : nout); o0 += OV_T * OV_R) {
     double acc[OV_R];
 #pragma unroll
     for (int r = 0; r < OV_R; ++r) acc[r] = 0.0;
@@ -629,6 +636,11 @@ __global__ void __launch_bounds__(OV_T) k_overlap(OverlapArgs a) {
     double ar[IB], ai[IB];
 #pragma unroll
     for (int u = 0; u < IB; ++u) ar[u] = ai[u] = 0.0;
+    // with V_T = [I_N; 0] rows p < N of Theta = Phi S^-1 are rows of S S^-1 = I
+    if (a.unit_trial && p < N) {
+#pragma unroll
+      for (int u = 0; u < IB; ++u) ar[u] = (i0 + u == p) ? 1.0 : 0.0;
+    } else
     for (int j = 0; j < N; ++j) {
       const double xr = fr[(long)j * M + p], xi = fi[(long)j * M + p];
 #pragma unroll
