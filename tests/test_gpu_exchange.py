@@ -4,7 +4,11 @@ sum_ij T_ij T_ji epilogue, Eq. localenergy3) on walkers that all differ.
 Expected values come from the oracle only: the float64 energies of
 oracle.afqmc.local_energy, and the same formula evaluated with the operands
 the mixed path feeds the tensor cores (the half-rotated vectors and Theta
-rounded to BF16 or TF32, products and sums exact).  The float64 path must
+rounded to BF16 or TF32, products and sums exact).  The library works in the
+orthonormal basis whose first N vectors are the trial orbitals and whose
+others complete them by the Householder QR of the trial; the operands are
+rounded in that basis (Lh_g Q and Q^T Theta), which complete_basis below
+rebuilds the same way.  The float64 path must
 match the first to 1e-9 and the mixed path the second to 2e-5 of the size of
 the energy's terms (|one-body| + |Coulomb| + |exchange|): what is left is FP32
 accumulation.  A (g, w) block taken from the wrong walker or vector moves
@@ -49,14 +53,39 @@ def round_tf32(x):
     return u.astype(np.uint32).view(np.float32).astype(np.float64)
 
 
-def energy_terms(setup, theta, rnd=None):
+def complete_basis(trial):
+    """Orthogonal Q with Q[:, :N] = trial: Householder QR of the trial
+    (reflectors H_1 .. H_N), Q = H_1 ... H_N with its first N columns set to
+    the trial."""
+    M, N = trial.shape
+    a = trial.copy()
+    vs = []
+    for k in range(N):
+        x = a[k:, k]
+        alpha = -np.linalg.norm(x) if x[0] >= 0 else np.linalg.norm(x)
+        v = x.copy()
+        v[0] -= alpha
+        nv = np.linalg.norm(v)
+        if nv > 0:
+            v /= nv
+        a[k:, k:] -= 2.0 * np.outer(v, v @ a[k:, k:])
+        vs.append(v)
+    q = np.eye(M)
+    for k in range(N - 1, -1, -1):
+        q[k:, :] -= 2.0 * np.outer(vs[k], vs[k] @ q[k:, :])
+    q[:, :N] = trial
+    return q
+
+
+def energy_terms(setup, theta, rnd=None, Q=None):
     """(E_loc, |one-body| + |Coulomb| + |exchange|, exchange) per walker; with
-    rnd, the two-body terms use the rounded Lh and Theta."""
+    rnd, the two-body terms use Lh Q and Q^T Theta rounded."""
     e1 = 2.0 * np.einsum("iq,wqi->w", setup.hh, theta)
     Lh, th = setup.Lh, theta
     if rnd is not None:
-        Lh = rnd(Lh)
-        th = rnd(theta.real) + 1j * rnd(theta.imag)
+        Lh = rnd(Lh @ Q)
+        th = np.einsum("pq,wpi->wqi", Q, theta)
+        th = rnd(th.real) + 1j * rnd(th.imag)
     t = 2.0 * np.einsum("giq,wqi->wg", Lh, th)
     G, N, M = Lh.shape
     Lh2 = Lh.reshape(G * N, M)
@@ -85,6 +114,7 @@ def test_mixed_local_energies_match_rounded_oracle(pkg, M, N, G, W):
     phi = trial[None] + (0.5 / np.sqrt(M)) * (rng.standard_normal((W, M, N))
                                               + 1j * rng.standard_normal((W, M, N)))
     setup = afqmc.Setup(h1, L, trial)
+    Q = complete_basis(trial)
     _, theta = afqmc.overlap(setup, phi)
     e_ref = afqmc.local_energy(setup, theta)
     _, scale, ex = energy_terms(setup, theta)
@@ -96,6 +126,6 @@ def test_mixed_local_energies_match_rounded_oracle(pkg, M, N, G, W):
         run.set_walkers(phi, np.ones(W))
         e = run.local_energies()
         assert run.info().status == 0
-        want = e_ref if rnd is None else energy_terms(setup, theta, rnd)[0]
+        want = e_ref if rnd is None else energy_terms(setup, theta, rnd, Q)[0]
         err = np.abs(e - want) / scale
         assert err.max() < tol, (prec, int(err.argmax()), err.max())
