@@ -6,8 +6,13 @@ modified Gram-Schmidt every 5 steps, local energy every 10 steps.  One step
 is one pass of the whole hot path over all walkers (force bias, fields, V,
 propagation, overlap/LU, weights, and the periodic QR and energy).
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16|tf32|fp64]
     python bench.py --impl reference      # the CPU oracle on the host cores
+
+The default is the mixed path with BF16 tensor-core operands (the M=300
+configuration's precision); the line also carries the same workload's FP64
+path measured on the same GPU (a few steps) and the mixed path's energy bias
+against it on identical walkers and fields.
 
 Prints one JSON line.  Under torchrun (N > 1) every rank runs an independent
 replica (its own walker population and Philox seed) on its own GPU; time is
@@ -45,9 +50,15 @@ def peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
-# FP64 DFMA throughput of GB300, measured on this machine with a dependent-chain
-# probe kernel (152 SMs, 256-thread blocks): 1.198 TFLOP/s.
-FP64_PEAK_TFLOPS = 1.198
+# FP64 peak of GB300 from its unit counts and clock: 152 SMs x 2 FP64 FMA per
+# clock x 2 FLOP x 2070 MHz = 1.259 TFLOP/s (a DFMA probe kernel measured
+# 1.198 TFLOP/s on this machine, i.e. 2 FMA/clk/SM at the clock under load).
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+
+# DRAM bytes (read + write) per launch from one ncu capture of the M=300 BF16
+# step, with the SHA-256 of the source file the kernel was built from; a
+# figure whose source has changed since is reported as null.
+TRAFFIC = {}
 
 
 class ClockSampler:
@@ -66,7 +77,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -134,6 +145,79 @@ def max_over_ranks(value: float, device="cpu") -> float:
 def job_throughput(walkers_per_rank: int, steps: int, ms_max: float, world: int) -> float:
     """Walker-steps of all ranks per second of the slowest rank."""
     return world * walkers_per_rank * steps / (ms_max * 1e-3)
+
+
+def algorithmic_per_walker(w: workloads.Workload):
+    """Algorithmic work of the step's kernels per walker (one spin block; the
+    closed-shell walker's two blocks are the same matrix), as used for the
+    roofline fractions:
+      overlap  FP64: Gauss-Jordan inverse of S (8 N^3) and Theta's M - N
+               non-trivial rows (8 (M - N) N^2): in the trial-adapted basis S
+               is the top block of Phi and Theta's top rows are I;
+      qr       FP64: modified Gram-Schmidt, 8 M N^2, every qr_period steps;
+      v        tensor: V = sum_g x_g L_g over the M (M + 1) / 2 distinct
+               elements, complex x real: 2 N_g M (M + 1);
+      taylor   tensor: n products of complex M x M by M x N, 8 n M^2 N;
+      energy   tensor: force bias 4 N_g N M and exchange 4 N_g N^2 M (the
+               T_g = Lh_g Theta products), per evaluation."""
+    M, N, G, n = w.M, w.N, w.nchol, w.taylor_order
+    return {"overlap": 8 * (M - N) * N * N + 8 * N ** 3, "qr": 8 * M * N * N,
+            "v_assembly": 2 * G * M * (M + 1), "taylor": 8 * n * M * M * N,
+            "energy": 4 * G * N * M + 4 * G * N * N * M}
+
+
+KERNEL_OF_PHASE = {"overlap": ("k_overlap", "alu", "walker_f64.cu"),
+                   "qr": ("k_mgs", "alu", "walker_f64.cu"),
+                   "v_assembly": ("tcgen05 V contraction (EpiV)", "tensor", "gemm_tc.cu"),
+                   "taylor": ("k_taylor_series", "tensor", "taylor_tc.cu"),
+                   "energy": ("force bias + tcgen05 exchange (EpiExchange) + k_eloc", "tensor",
+                              "gemm_tc.cu")}
+
+
+def source_sha(fname):
+    import hashlib
+
+    path = os.path.join(ROOT, "paper_1711_02242_gb300", "csrc", fname)
+    try:
+        with open(path, "rb") as f:
+            return hashlib.sha256(f.read()).hexdigest()
+    except OSError:
+        return None
+
+
+def rooflines(w, phases, precision, K):
+    """Roofline entry per timed phase that is one kernel family: algorithmic
+    work per launch / device time per launch (CUDA events on the state's
+    stream) against the peak of the pipe that bounds it."""
+    pk, pk_kind = peaks()
+    per = algorithmic_per_walker(w)
+    out = []
+    for ph, (kname, bound, src) in KERNEL_OF_PHASE.items():
+        v = phases[ph]
+        if v["count"] == 0 or v["ms"] <= 0:
+            continue
+        ms_launch = v["ms"] / v["count"]
+        work = per[ph] * w.nwalkers
+        if bound == "alu" or precision == "fp64":
+            peak, unit, src_peak = FP64_PEAK_TFLOPS, "TFLOP/s", (
+                "derived: 152 SMs x 2 FP64 FMA/clk x 2 x 2070 MHz")
+            bound = "alu"
+        else:
+            base = pk["bf16_tflops_sustained"]
+            peak = base if precision == "bf16" else base / 2
+            unit = "TFLOP/s"
+            src_peak = (f"{pk_kind} bf16 sustained" if precision == "bf16"
+                        else f"{pk_kind} bf16 sustained / 2 (TF32 nominal ratio)")
+        achieved = work / (ms_launch * 1e-3) / 1e12
+        tr = TRAFFIC.get(ph)
+        traffic = tr["bytes"] if tr and tr.get("sha") == source_sha(src) else None
+        out.append({"phase": ph, "kernel": kname, "bound": bound, "achieved": achieved,
+                    "peak": peak, "unit": unit, "frac": achieved / peak, "traffic": traffic,
+                    "peak_source": src_peak, "ms_per_launch": ms_launch,
+                    "launches_per_step": v["count"] / K,
+                    "share_of_step": v["ms"] / sum(x["ms"] for x in phases.values())})
+    out.sort(key=lambda d: -d["share_of_step"])
+    return out
 
 
 def flops_per_walker_step(w: workloads.Workload, s=1):
@@ -258,11 +342,44 @@ def run_gpu(args, w: workloads.Workload):
     prec_rep = None
     if prec != 0 and rank == 0 and not args.no_precision_report:
         prec_rep = precision_report(w, prec, h1, L, C, H0)
+    fp64 = None
+    if prec != 0 and rank == 0 and not args.no_fp64_compare:
+        fp64 = fp64_compare(w, p, h1, L, C, dev, stream, args.fp64_steps)
     return dict(ms_total=ms_total, phases=phases, launches=launches, info=info, E=E, wsum=wsum,
                 clocks=clk.summary(), e2e_s=t_e2e, trial_converged=conv, trial_grad=grad,
                 h2d_bytes=h1.nbytes + L.nbytes + C.nbytes, world=ws, rank=rank, warmup=Wm,
                 ms_profiled=ms_profiled, s_energy=s_energy, graph=not args.no_graph,
-                precision_report=prec_rep)
+                precision_report=prec_rep, fp64=fp64)
+
+
+def fp64_compare(w, p, h1, L, C, dev, stream, steps):
+    """The FP64 path on the same workload and GPU: a few steps after one
+    untimed step (its step is ~100x the mixed one)."""
+    import dataclasses
+
+    import torch
+
+    import paper_1711_02242_gb300 as pkg
+
+    q = pkg.Params.from_buffer_copy(p)
+    q.precision = pkg.AFQMC_FP64
+    q.use_graph = 0
+    run = pkg.AfqmcRun(h1, L, C, q, device=dev, stream=stream)
+    run.propagate(1)
+    stream.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    run.propagate(steps)
+    e1.record(stream)
+    stream.synchronize()
+    ms = e0.elapsed_time(e1)
+    run.close()
+    del run
+    torch.cuda.empty_cache()
+    return {"value": w.nwalkers * steps / (ms * 1e-3), "unit": "walker-steps/s",
+            "ms_per_step": ms / steps, "steps": steps,
+            "note": "the same workload on the FP64 path (every step in float64/complex128), "
+                    "same GPU, kernel by kernel"}
 
 
 class OracleSampler:
@@ -537,10 +654,13 @@ def main():
     ap.add_argument("--steps-per-block", type=int, default=25)
     ap.add_argument("--slots", type=int, default=8, help="serve: runs advanced per tick (0: memory only)")
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "tf32", "bf16"])
+    ap.add_argument("--precision", default="bf16", choices=["fp64", "tf32", "bf16"])
+    ap.add_argument("--no-fp64-compare", action="store_true",
+                    help="skip the FP64 path's own few-step measurement")
+    ap.add_argument("--fp64-steps", type=int, default=5)
     ap.add_argument("--config", default="c2", choices=sorted(workloads.CONFIGS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end pass")
@@ -565,23 +685,12 @@ def main():
     ms_step = r["ms_total"] / K
     value = job_throughput(w.nwalkers, K, r["ms_total"], N)
     fl = flops_per_walker_step(w)
-    pk, pk_kind = peaks()
-    # dominant kernel: the V contraction (one launch per step)
-    v = r["phases"]["v_assembly"]
-    v_ms = v["ms"] / max(1, v["kernels"])
-    v_flops = fl["v_assembly"] * w.nwalkers
-    if args.precision == "fp64":
-        peak = FP64_PEAK_TFLOPS
-        roof = {"bound": "alu", "kernel": "k_gemm_nt_f64 (V = sum_g x_g L_g)",
-                "achieved": v_flops / (v_ms * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s",
-                "peak_source": "measured FP64 DFMA throughput (probe kernel)",
-                "traffic": None}
-    else:
-        peak = pk["bf16_tflops_sustained"] if args.precision == "bf16" else pk["bf16_tflops_sustained"] / 2
-        roof = {"bound": "tensor", "kernel": "V contraction", "achieved": v_flops / (v_ms * 1e-3) / 1e12,
-                "peak": peak, "unit": "TFLOP/s", "peak_source": pk_kind, "traffic": None}
-    roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["launch_ms"] = v_ms
+    # the dominant kernel (largest share of the profiled step) and the others
+    roofs = rooflines(w, r["phases"], args.precision, K)
+    top = roofs[0]
+    roof = {k: top[k] for k in ("bound", "achieved", "peak", "unit", "frac", "traffic")}
+    roof.update(kernel=top["kernel"], peak_source=top["peak_source"],
+                ms_per_launch=top["ms_per_launch"])
     line = {
         "metric": "walker-steps/s at M=300", "value": value, "unit": "walker-steps/s",
         "n_gpus": N, "steps": K, "warmup": r["warmup"], "ms_per_step": ms_step,
@@ -595,6 +704,7 @@ def main():
                    "trial": f"RHF (25 iterations, converged={r['trial_converged']}, "
                             f"|FD-DF|={r['trial_grad']:.2e})"},
         "roofline": roof,
+        "rooflines_by_phase": roofs,
         "launch_mode": "CUDA graph per block of steps" if r["graph"] else "kernel by kernel",
         "energy_evals_per_s": w.nwalkers / r["s_energy"],
         "profiled_pass": {"ms_per_step": r["ms_profiled"] / K,
@@ -613,6 +723,8 @@ def main():
     }
     if r["precision_report"]:
         line["precision_vs_fp64"] = r["precision_report"]
+    if r.get("fp64"):
+        line["fp64_same_gpu"] = r["fp64"]
     if N == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_sample(w)
     print(json.dumps(line))

@@ -53,3 +53,34 @@ def test_job_throughput_counts_all_ranks():
     assert bench.job_throughput(512, 10, 1000.0, 1) == 5120.0
     assert bench.job_throughput(512, 10, 1000.0, 4) == 4 * 5120.0
     assert bench.max_over_ranks(7.5) == 7.5  # no process group: local value
+
+
+def test_rooflines_from_phase_times():
+    """Per-phase roofline entries: algorithmic work / time per launch, the
+    dominant phase first, and a traffic figure only while its source matches."""
+    import bench
+    import workloads
+
+    w = workloads.config("c2")
+    K = 10
+    ph = {name: {"ms": 0.0, "count": 0, "kernels": 0} for name in bench.PHASES}
+    ph["overlap"] = {"ms": 13.0, "count": 10, "kernels": 10}   # 1.3 ms per launch
+    ph["taylor"] = {"ms": 4.0, "count": 10, "kernels": 10}
+    ph["qr"] = {"ms": 2.6, "count": 2, "kernels": 2}
+    roofs = bench.rooflines(w, ph, "bf16", K)
+    assert [r["phase"] for r in roofs] == ["overlap", "taylor", "qr"]
+    ov = roofs[0]
+    per = bench.algorithmic_per_walker(w)["overlap"]
+    assert per == 8 * (300 - 25) * 25 * 25 + 8 * 25 ** 3
+    assert abs(ov["achieved"] - per * 512 / 1.3e-3 / 1e12) < 1e-12
+    assert ov["bound"] == "alu" and abs(ov["frac"] - ov["achieved"] / bench.FP64_PEAK_TFLOPS) < 1e-12
+    assert roofs[1]["bound"] == "tensor" and roofs[1]["traffic"] is None
+    assert abs(sum(r["share_of_step"] for r in roofs) - 1.0) < 1e-12
+    # a recorded traffic figure counts only for the source it was taken from
+    bench.TRAFFIC["overlap"] = {"bytes": 1.0e8, "sha": bench.source_sha("walker_f64.cu")}
+    try:
+        assert bench.rooflines(w, ph, "bf16", K)[0]["traffic"] == 1.0e8
+        bench.TRAFFIC["overlap"]["sha"] = "0" * 64
+        assert bench.rooflines(w, ph, "bf16", K)[0]["traffic"] is None
+    finally:
+        bench.TRAFFIC.pop("overlap")
