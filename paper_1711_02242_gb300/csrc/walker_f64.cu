@@ -468,6 +468,40 @@ int launch_theta(const ThetaArgs& a, cudaStream_t st) {
 namespace {
 constexpr int OV_P = 32, OV_R = 8, OV_T = 256;
 }
+
+// Theta^T[i][p] = sum_j S^-1[j][i] Phi^T[j][p] for p >= p0, IB orbitals i per
+// work item (IB divides N).
+template <int IB>
+__device__ __forceinline__ void theta_rows(const OverlapArgs& a, int w, const double2* Inv,
+                                           const double* fr, const double* fi, double* tr,
+                                           double* ti, int p0) {
+  const int N = a.N, M = a.M, np = M - p0, nib = N / IB;
+  for (int item = threadIdx.x; item < np * nib; item += blockDim.x) {
+    const int p = p0 + item % np, i0 = (item / np) * IB;
+    double ar[IB], ai[IB];
+#pragma unroll
+    for (int u = 0; u < IB; ++u) ar[u] = ai[u] = 0.0;
+    for (int j = 0; j < N; ++j) {
+      const double xr = fr[(long)j * M + p], xi = fi[(long)j * M + p];
+#pragma unroll
+      for (int u = 0; u < IB; ++u) {
+        const double2 sv = Inv[j * N + i0 + u];
+        ar[u] = fma(xr, sv.x, fma(-xi, sv.y, ar[u]));
+        ai[u] = fma(xr, sv.y, fma(xi, sv.x, ai[u]));
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < IB; ++u) {
+      const int i = i0 + u;
+      tr[(long)i * M + p] = ar[u];
+      ti[(long)i * M + p] = ai[u];
+      if (a.th_lo) {
+        store_lo(a.th_lo, a.lo_kind, ((long)w * 2 * N + i) * a.Mp + p, ar[u]);
+        store_lo(a.th_lo, a.lo_kind, ((long)w * 2 * N + N + i) * a.Mp + p, ai[u]);
+      }
+    }
+  }
+}
 __global__ void __launch_bounds__(OV_T) k_overlap(OverlapArgs a) {
   extern __shared__ double2 ov_sm[];
   const int w = blockIdx.x;
@@ -479,6 +513,7 @@ __global__ void __launch_bounds__(OV_T) k_overlap(OverlapArgs a) {
   double* Ps = Vs + N * (OV_P + 1);                           // [2N][OV_P + 1]
   __shared__ int piv, swaps, singular;
   __shared__ double logabs, phase;
+  __shared__ double2 rpiv;
   const double* fr = a.phiT + (long)w * 2 * N * M;
   const double* fi = fr + (long)N * M;
   const int nout = 2 * N * N;  // (i, c, j): S_c[i][j], c = re / im plane
@@ -579,14 +614,16 @@ __global__ void __launch_bounds__(OV_T) k_overlap(OverlapArgs a) {
       if (threadIdx.x == 0) swaps++;
     }
     __syncthreads();
-    const double2 pv = A[k * N + k];
-    const double den = pv.x * pv.x + pv.y * pv.y;
-    const double2 rp = make_double2(pv.x / den, -pv.y / den);
+    // 1 / pivot once (float64 division and log run long on the FP64 pipe)
     if (threadIdx.x == 0) {
+      const double2 pv = A[k * N + k];
+      const double den = pv.x * pv.x + pv.y * pv.y;
+      rpiv = make_double2(pv.x / den, -pv.y / den);
       logabs += 0.5 * log(den);
       phase += atan2(pv.y, pv.x);
     }
     __syncthreads();
+    const double2 rp = rpiv;
     for (int j = threadIdx.x; j < N; j += blockDim.x) {
       const double2 v = A[k * N + j], u = Inv[k * N + j];
       A[k * N + j] = make_double2(v.x * rp.x - v.y * rp.y, v.x * rp.y + v.y * rp.x);
@@ -626,44 +663,35 @@ __global__ void __launch_bounds__(OV_T) k_overlap(OverlapArgs a) {
     }
   }
   if (singular || !live) return;
-  // Theta^T = S^-T Phi^T: work items (p, block of 8 orbitals i)
-  constexpr int IB = 8;
-  const int nib = (N + IB - 1) / IB;
+  // Theta^T = S^-T Phi^T: work items (p, block of IB orbitals i), IB the
+  // largest divisor of N up to 8 (no padded lanes); with V_T = [I_N; 0] rows
+  // p < N are rows of S S^-1 = I
   double* tr = a.thetaT + (long)w * 2 * N * M;
   double* ti = tr + (long)N * M;
-  for (int item = threadIdx.x; item < M * nib; item += blockDim.x) {
-    const int p = item % M, i0 = (item / M) * IB;
-    double ar[IB], ai[IB];
-#pragma unroll
-    for (int u = 0; u < IB; ++u) ar[u] = ai[u] = 0.0;
-    // with V_T = [I_N; 0] rows p < N of Theta = Phi S^-1 are rows of S S^-1 = I
-    if (a.unit_trial && p < N) {
-#pragma unroll
-      for (int u = 0; u < IB; ++u) ar[u] = (i0 + u == p) ? 1.0 : 0.0;
-    } else
-    for (int j = 0; j < N; ++j) {
-      const double xr = fr[(long)j * M + p], xi = fi[(long)j * M + p];
-#pragma unroll
-      for (int u = 0; u < IB; ++u) {
-        if (i0 + u < N) {
-          const double2 s = Inv[j * N + i0 + u];
-          ar[u] = fma(xr, s.x, fma(-xi, s.y, ar[u]));
-          ai[u] = fma(xr, s.y, fma(xi, s.x, ai[u]));
-        }
+  const int p0 = a.unit_trial ? N : 0;
+  if (a.unit_trial) {
+    for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x) {
+      const int i = idx / N, p = idx % N;
+      const double v = i == p ? 1.0 : 0.0;
+      tr[(long)i * M + p] = v;
+      ti[(long)i * M + p] = 0.0;
+      if (a.th_lo) {
+        store_lo(a.th_lo, a.lo_kind, ((long)w * 2 * N + i) * a.Mp + p, v);
+        store_lo(a.th_lo, a.lo_kind, ((long)w * 2 * N + N + i) * a.Mp + p, 0.0);
       }
     }
-#pragma unroll
-    for (int u = 0; u < IB; ++u) {
-      const int i = i0 + u;
-      if (i < N) {
-        tr[(long)i * M + p] = ar[u];
-        ti[(long)i * M + p] = ai[u];
-        if (a.th_lo) {
-          store_lo(a.th_lo, a.lo_kind, ((long)w * 2 * N + i) * a.Mp + p, ar[u]);
-          store_lo(a.th_lo, a.lo_kind, ((long)w * 2 * N + N + i) * a.Mp + p, ai[u]);
-        }
-      }
-    }
+  }
+  int ib = 8;
+  while (N % ib) --ib;
+  switch (ib) {
+    case 8: theta_rows<8>(a, w, Inv, fr, fi, tr, ti, p0); break;
+    case 7: theta_rows<7>(a, w, Inv, fr, fi, tr, ti, p0); break;
+    case 6: theta_rows<6>(a, w, Inv, fr, fi, tr, ti, p0); break;
+    case 5: theta_rows<5>(a, w, Inv, fr, fi, tr, ti, p0); break;
+    case 4: theta_rows<4>(a, w, Inv, fr, fi, tr, ti, p0); break;
+    case 3: theta_rows<3>(a, w, Inv, fr, fi, tr, ti, p0); break;
+    case 2: theta_rows<2>(a, w, Inv, fr, fi, tr, ti, p0); break;
+    default: theta_rows<1>(a, w, Inv, fr, fi, tr, ti, p0); break;
   }
 }
 
@@ -745,6 +773,7 @@ int launch_weight(const WeightArgs& a, cudaStream_t st) {
 __global__ void __launch_bounds__(256) k_mgs(MgsArgs a) {
   extern __shared__ double2 q_sm[];  // the finished column q_k, [M]
   __shared__ double sh[32];
+  __shared__ double inv_sh;
   const int w = blockIdx.x;
   if (!walker_alive(a.wt, w)) return;
   const int M = a.M, N = a.N;
@@ -758,8 +787,13 @@ __global__ void __launch_bounds__(256) k_mgs(MgsArgs a) {
     double nn = 0.0;
     for (int p = threadIdx.x; p < M; p += blockDim.x) nn = fma(vr[p], vr[p], fma(vi[p], vi[p], nn));
     nn = block_sum(nn, sh);
-    const double inv = 1.0 / sqrt(nn);
-    logr += 0.5 * log(nn);
+    // 1 / |v_k| and log |v_k| once (long FP64 sequences), shared by the block
+    if (threadIdx.x == 0) {
+      inv_sh = 1.0 / sqrt(nn);
+      logr += 0.5 * log(nn);
+    }
+    __syncthreads();
+    const double inv = inv_sh;
     for (int p = threadIdx.x; p < M; p += blockDim.x) {
       const double qr = vr[p] * inv, qi = vi[p] * inv;
       vr[p] = qr;
