@@ -143,13 +143,26 @@ __global__ void __launch_bounds__(192, 1)
 }
 
 
+// Named barrier 1 over the W epilogue warps, returning the OR of a flag.
+template <int W>
+__device__ __forceinline__ bool epi_bar_or(bool flag) {
+  uint32_t out;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 q, %1, 0;\n\t"
+      "bar.red.or.pred p, 1, %2, q;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(out)
+      : "r"((uint32_t)flag), "n"(32 * W)
+      : "memory");
+  return out != 0;
+}
+
 // Persistent variant for epilogues that need no shared memory: one CTA per SM
 // walks the output tiles t = blockIdx.x, blockIdx.x + gridDim.x, ... (tile
 // (bx, by) = (t % gx, t / gx), so CTAs running together share B tiles in L2).
 // Two TMEM accumulators of BN columns: the epilogue warps drain tile j while
 // the MMA thread fills tile j + 1 (tfull / tempty mbarriers per accumulator).
 template <int BN, int STAGES, bool TF32, class Epi>
-__global__ void __launch_bounds__(192, 1)
+__global__ void __launch_bounds__(64 + 32 * Epi::kWarps, 1)
     k_tc_gemm_persistent(const __grid_constant__ CUtensorMap tmA,
                          const __grid_constant__ CUtensorMap tmB, int M, int N, int K, int gx,
                          int ntiles, Epi epi, int* err) {
@@ -176,7 +189,7 @@ __global__ void __launch_bounds__(192, 1)
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(&tfull[a], 1);
-      mbar_init(&tempty[a], 4);  // one arrival per epilogue warp
+      mbar_init(&tempty[a], Epi::kWarps);  // one arrival per epilogue warp
     }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -255,10 +268,13 @@ __global__ void __launch_bounds__(192, 1)
     int j = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++j) {
       const int acc = j & 1;
-      if (!mbar_wait(&tfull[acc], (j / 2) & 1, err, 14)) *(volatile int*)abort_flag = 1;
+      bool bad = !mbar_wait(&tfull[acc], (j / 2) & 1, err, 14);
       fence_after();
-      asm volatile("bar.sync 1, 128;" ::: "memory");  // one decision for all 4 warps
-      if (*(volatile int*)abort_flag) break;
+      // one decision for every epilogue warp (barrier 1 with an OR of the flags)
+      if (epi_bar_or<Epi::kWarps>(bad || *(volatile int*)abort_flag)) {
+        *(volatile int*)abort_flag = 1;
+        break;
+      }
       const int bx = t % gx, by = t / gx;
       epi.template run<BN>(tmem + (uint32_t)acc * ASTRIDE, q, lane, warp - 2, bx, by,
                            epi.m_origin(bx, by), epi.n_origin(bx, by), M, N, esm);
@@ -281,6 +297,7 @@ __global__ void __launch_bounds__(192, 1)
 struct EpiStore {
   static constexpr int kSmemBytes = 0;
   static constexpr bool kB3D = false;  // B tile = one 2-D box at row n_origin
+  static constexpr int kWarps = 4;      // epilogue warps
   float* C;
   long ldc;
   float alpha;
@@ -326,6 +343,7 @@ struct EpiStore {
 struct EpiExchange {
   static constexpr int kSmemBytes = 128 * 257 * 4;  // one 128 x 256 FP32 tile
   static constexpr bool kB3D = true;
+  static constexpr int kWarps = 8;  // two per TMEM lane quarter, splitting columns / walkers
   static constexpr int kMaxCW = 16;
   double* part;
   int G, W, N, RG, CW, NPAD, nchunk;
@@ -333,25 +351,27 @@ struct EpiExchange {
   __device__ __forceinline__ int n_origin(int, int by) const { return by * CW * NPAD; }
   __device__ __forceinline__ int b_plane(int, int by) const { return by * CW; }
   template <int BN>
-  __device__ __forceinline__ void run(uint32_t tmem, int q, int lane, int, int bx, int by, int,
+  __device__ __forceinline__ void run(uint32_t tmem, int q, int lane, int ew, int bx, int by, int,
                                       int, int, int, float* sm) const {
     constexpr int LD = BN + 1;  // odd pitch: row and column walks are conflict-free
-    const int r = 32 * q + lane;
+    const int r = 32 * q + lane, half = ew >> 2;
 #pragma unroll 1
-    for (int c0 = 0; c0 < BN; c0 += 16) {
+    for (int c0 = 16 * half; c0 < BN; c0 += 32) {
       float v[16];
       tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c0, v);
 #pragma unroll
       for (int i = 0; i < 16; ++i) sm[r * LD + c0 + i] = v[i];
     }
-    asm volatile("bar.sync 1, 128;" ::: "memory");
+    asm volatile("bar.sync 1, 256;" ::: "memory");
     const int gl = r / N, i = r - gl * N;
     const bool rv = gl < RG;
     // FP32 sums (the products come from FP32 accumulators; GB300's float64
-    // pipe is ~60x slower than FP32 and would dominate the kernel)
-    float e[2 * kMaxCW];
+    // pipe is ~60x slower than FP32 and would dominate the kernel); the two
+    // warps of a row take alternate walkers
+    float e[kMaxCW];
 #pragma unroll
-    for (int wl = 0; wl < kMaxCW; ++wl) {
+    for (int h = 0; h < kMaxCW / 2; ++h) {
+      const int wl = 2 * h + half;
       float er = 0.f, ei = 0.f;
       if (wl < CW && rv) {
         const float* own = sm + r * LD + wl * NPAD;            // T_ij: [j], [N + j]
@@ -364,19 +384,21 @@ struct EpiExchange {
           ei = fmaf(ar, bi, fmaf(ai, br, ei));
         }
       }
-      e[2 * wl] = er;
-      e[2 * wl + 1] = ei;
+      e[2 * h] = er;
+      e[2 * h + 1] = ei;
     }
-    asm volatile("bar.sync 1, 128;" ::: "memory");  // every read of the tile is done
+    asm volatile("bar.sync 1, 256;" ::: "memory");  // every read of the tile is done
 #pragma unroll
-    for (int wl = 0; wl < kMaxCW; ++wl)
+    for (int h = 0; h < kMaxCW / 2; ++h) {
+      const int wl = 2 * h + half;
       if (wl < CW) {
-        sm[r * LD + 2 * wl] = e[2 * wl];
-        sm[r * LD + 2 * wl + 1] = e[2 * wl + 1];
+        sm[r * LD + 2 * wl] = e[2 * h];
+        sm[r * LD + 2 * wl + 1] = e[2 * h + 1];
       }
-    asm volatile("bar.sync 1, 128;" ::: "memory");
+    }
+    asm volatile("bar.sync 1, 256;" ::: "memory");
     const int g0 = bx * RG, w0 = by * CW;
-    for (int item = r; item < RG * CW; item += 128) {
+    for (int item = r + 128 * half; item < RG * CW; item += 256) {
       const int g = item / CW, wl = item - g * CW;
       if (g0 + g >= G || w0 + wl >= W) continue;
       float sr = 0.f, si = 0.f;
@@ -389,7 +411,7 @@ struct EpiExchange {
       o[1] = (double)si;
     }
     // the next tile's copy into sm must wait until every warp is done reading
-    asm volatile("bar.sync 1, 128;" ::: "memory");
+    asm volatile("bar.sync 1, 256;" ::: "memory");
   }
 };
 
@@ -437,6 +459,7 @@ __device__ __forceinline__ void store16_lo(void* base, int kind, long idx, const
 struct EpiProp0 {
   static constexpr int kSmemBytes = 0;
   static constexpr bool kB3D = false;  // B tile = one 2-D box at row n_origin
+  static constexpr int kWarps = 4;      // epilogue warps
   float* acc;
   long ldacc;
   void* tb;
@@ -492,6 +515,7 @@ struct EpiProp0 {
 struct EpiTaylor {
   static constexpr int kSmemBytes = 0;
   static constexpr bool kB3D = false;  // B tile = one 2-D box at row n_origin
+  static constexpr int kWarps = 4;      // epilogue warps
   static constexpr int kBN = 160;  // two tiles cover p < 320
   float* S;
   long lds;
@@ -553,6 +577,7 @@ struct EpiTaylor {
 struct EpiV {
   static constexpr int kSmemBytes = 0;
   static constexpr bool kB3D = false;  // B tile = one 2-D box at row n_origin
+  static constexpr int kWarps = 4;      // epilogue warps
   void* V;
   int lo_kind, W, M, Mp;
   float sdt;
@@ -587,6 +612,7 @@ struct EpiV {
 struct EpiPhi {
   static constexpr int kSmemBytes = 0;
   static constexpr bool kB3D = false;  // B tile = one 2-D box at row n_origin
+  static constexpr int kWarps = 4;      // epilogue warps
   double* phiT;
   const double* wt;
   int N, M, rows;
@@ -781,7 +807,8 @@ static int launch_tc_persistent(const TcGemm& g, const Epi& epi, int gx, int gy,
     return AFQMC_EINVAL;
   }
   const int grid = (int)(ntiles < tc_sm_count() ? ntiles : tc_sm_count());
-  AFQ_LAUNCH(kern, grid, 192, kTotal, st, ta, tb, g.m, g.n, g.k, gx, (int)ntiles, epi, g.err);
+  AFQ_LAUNCH(kern, grid, 64 + 32 * Epi::kWarps, kTotal, st, ta, tb, g.m, g.n, g.k, gx, (int)ntiles,
+             epi, g.err);
   return AFQMC_OK;
 }
 
