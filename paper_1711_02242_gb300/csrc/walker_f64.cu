@@ -630,21 +630,18 @@ __global__ void __launch_bounds__(OV_T) k_overlap(OverlapArgs a) {
       Inv[k * N + j] = make_double2(u.x * rp.x - u.y * rp.y, u.x * rp.y + u.y * rp.x);
     }
     __syncthreads();
-    for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x) {
-      const int r = idx / N, j = idx % N;
-      if (r == k || j == k) continue;
+    // eliminate column k from the other rows.  Columns j < k of A are already
+    // unit vectors (row k holds 0 there), so A changes only in columns j > k;
+    // Inv changes in every column (row swaps can move any column forward)
+    const int na = N - 1 - k;  // A columns k+1 .. N-1
+    for (int idx = threadIdx.x; idx < (N - 1) * (na + N); idx += blockDim.x) {
+      const int rr = idx / (na + N), c = idx % (na + N);
+      const int r = rr < k ? rr : rr + 1;  // rows other than k
       const double2 f = A[r * N + k];
-      const double2 v = A[k * N + j];
-      double2& d = A[r * N + j];
-      d.x = fma(-f.x, v.x, fma(f.y, v.y, d.x));
-      d.y = fma(-f.x, v.y, fma(-f.y, v.x, d.y));
-    }
-    for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x) {
-      const int r = idx / N, j = idx % N;
-      if (r == k) continue;
-      const double2 f = A[r * N + k];
-      const double2 v = Inv[k * N + j];
-      double2& d = Inv[r * N + j];
+      const bool inA = c < na;
+      const int col = inA ? k + 1 + c : c - na;
+      const double2 v = inA ? A[k * N + col] : Inv[k * N + col];
+      double2& d = inA ? A[r * N + col] : Inv[r * N + col];
       d.x = fma(-f.x, v.x, fma(f.y, v.y, d.x));
       d.y = fma(-f.x, v.y, fma(-f.y, v.x, d.y));
     }
