@@ -16,13 +16,13 @@ paper, Sec. 2 "The AFQMC method", Eqs. bo_ham2 / bo_ham_matel):
   ``N(0, a * exp(-g / M))`` in row-major order, then mirrored.  The
   two-electron tensor ``v_pqrs = sum_g L[g]_pr L[g]_qs`` (Sec. 2.3, Eq. chol)
   is then positive semi-definite by construction.
-* the amplitude ``a`` is 0.5 up to M = 12 (the 12-orbital workload's value)
-  and ``0.5 * 12 / M`` above (``l_amplitude``), which keeps the propagator's
-  argument ``||sqrt(dt) sum_g x_g L[g]||`` near 0.5 at every size.  Drawn
-  with 0.5 at every size, the 300-orbital operator has
-  ``||sqrt(dt) sum_g x_g L[g]|| ~ 15``: its sixth-order Taylor series is far
-  from converged, every walker overflows within a few steps, and the
-  energies reach 2e5 Ha.
+* the amplitude ``a`` is 0.5 for the 12-orbital, 48-vector workload and, for
+  the others, 0.5 scaled so that ``sum_g ||L[g]||_F^2`` -- the variance of
+  the one-body operator ``sum_g x_g L[g]`` under unit Gaussian fields -- is
+  the same as there (``l_amplitude``).  Drawn with 0.5 at every size, the
+  300-orbital operator has ``||sqrt(dt) sum_g x_g L[g]|| ~ 15``: its
+  sixth-order Taylor series is far from converged, every walker overflows
+  within a few steps, and the energies reach 2e5 Ha.
 * draws come from numpy's PCG64 generator seeded ``1000 + config_index``;
   ``h1`` is drawn first, then ``L[0]``, ``L[1]``, ...
 * the nuclear repulsion ``H0`` is 0.
@@ -68,9 +68,13 @@ class Workload:
                            l_scale=l_amplitude(self.M, self.nchol))
 
 
-def l_amplitude(M: int, nchol: int = 0) -> float:
-    """Amplitude of ``L[0]``: 0.5 for M <= 12, 0.5 * 12 / M above."""
-    return 0.5 * min(1.0, 12.0 / M)
+def l_amplitude(M: int, nchol: int, decay: float | None = None) -> float:
+    """Amplitude of ``L[0]`` that gives ``sum_g ||L[g]||_F^2`` (expected) the
+    value it has for M = 12, nchol = 48, decay 12, amplitude 0.5."""
+    def spread(m, n, d):
+        return m * m * sum(math.exp(-2.0 * g / d) for g in range(n))
+
+    return 0.5 * math.sqrt(spread(12, 48, 12.0) / spread(M, nchol, float(decay or M)))
 
 
 # The five workloads of the phaseless-AFQMC hot path.  Index i uses PCG64
