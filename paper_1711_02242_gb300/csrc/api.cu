@@ -193,6 +193,7 @@ int overlap_update(afqmc_state* s, bool into_ld) {
   // S = V_T^T Phi, S^-1, log det and Theta in one float64 kernel per walker
   OverlapArgs ov{p.nwalkers, p.M, p.N, b.VTt, b.phiT, b.thetaT, into_ld ? b.ld : b.ld_new, b.wt};
   ov.unit_trial = 1;  // V_T' = [I_N; 0] in the trial-adapted basis
+  ov.Sinv = reinterpret_cast<double2*>(b.Sinv);
   if (b.mixed) {
     ov.th_lo = b.th_lo;
     ov.lo_kind = b.lo_kind;

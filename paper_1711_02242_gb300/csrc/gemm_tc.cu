@@ -3,15 +3,15 @@
 //   D[m][n] = alpha * sum_k A[m][k] * B[n][k]     (A, B K-major; FP32 accumulate)
 //
 // A and B are BF16 (tcgen05.mma kind::f16) or TF32 (kind::tf32) row-major
-// matrices with a row pitch that is a multiple of 16 bytes.  Per CTA one
-// 128 x BN output tile:
+// matrices with a row pitch that is a multiple of 16 bytes.  One persistent
+// CTA per SM walks 128 x BN output tiles:
 //   warp 0  one thread issues TMA loads (128-byte swizzle) into a STAGES-deep
 //           shared-memory ring, completion tracked by mbarriers;
-//   warp 1  allocates BN TMEM columns; one thread issues tcgen05.mma
-//           (M=128, N=BN, K=32 bytes per instruction) into the TMEM
-//           accumulator and frees ring slots with tcgen05.commit;
-//   warps 2-5 read the accumulator with tcgen05.ld (each warp its 32-lane
-//           quarter) and run the epilogue.
+//   warp 1  allocates two BN-column TMEM accumulators; one thread issues
+//           tcgen05.mma (M=128, N=BN, K=32 bytes per instruction) and frees
+//           ring slots with tcgen05.commit;
+//   warps 2.. read an accumulator with tcgen05.ld (each warp its 32-lane
+//           quarter) and run the epilogue while the other one fills.
 // Every mbarrier wait is bounded; on time-out the kernel records an error
 // in *err and stops issuing work, and TMEM is always freed before exit.
 #include <cuda.h>
@@ -36,112 +36,6 @@ struct Smem {
   static constexpr int RING = STAGES * STAGE;
   static constexpr int TOTAL = RING + 1024 /*align*/ + 256 /*barriers*/;
 };
-
-template <int BN, int STAGES, bool TF32, class Epi>
-__global__ void __launch_bounds__(192, 1)
-    k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-              int M, int N, int K, Epi epi, int* err) {
-  extern __shared__ uint8_t smem_raw[];
-  using S = Smem<BN, STAGES>;
-  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + S::RING);
-  uint64_t* empty = full + STAGES;
-  uint64_t* accum = empty + STAGES;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
-  int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
-
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = epi.m_origin(blockIdx.x, blockIdx.y), n0 = epi.n_origin(blockIdx.x, blockIdx.y);
-  constexpr int ELEM = TF32 ? 4 : 2;
-  constexpr int BK = BKB / ELEM;          // K elements per stage
-  constexpr int KSTEPS = BKB / 32;        // MMAs per stage (32 bytes of K each)
-  const int nk = (K + BK - 1) / BK;
-
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; ++s) {
-      mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 1);
-    }
-    mbar_init(accum, 1);
-    *abort_flag = 0;
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  if (warp == 1) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                     smem_u32(tmem_slot)),
-                 "r"((uint32_t)BN));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-  }
-  fence_before();
-  __syncthreads();
-  fence_after();
-  const uint32_t tmem = *tmem_slot;
-
-  if (warp == 0 && lane == 0) {
-    // TMA producer
-    for (int kb = 0; kb < nk; ++kb) {
-      const int s = kb % STAGES;
-      if (kb >= STAGES) {
-        if (!mbar_wait(&empty[s], ((kb / STAGES) - 1) & 1, err, 1)) {
-          *abort_flag = 1;
-          break;
-        }
-      }
-      if (*(volatile int*)abort_flag) break;
-      uint8_t* a = smem + s * S::STAGE;
-      uint8_t* b = a + S::A_BYTES;
-      mbar_expect_tx(&full[s], S::STAGE);
-      tma_load_2d(a, &tmA, &full[s], kb * BK, m0);
-      tma_load_2d(b, &tmB, &full[s], kb * BK, n0);
-    }
-  } else if (warp == 1 && lane == 0) {
-    // MMA issuer
-    constexpr uint32_t idesc = instr_desc(TF32 ? 2u : 1u, (uint32_t)BN);
-    bool ok = true;
-    for (int kb = 0; kb < nk; ++kb) {
-      const int s = kb % STAGES;
-      if (!mbar_wait(&full[s], (kb / STAGES) & 1, err, 2)) {
-        ok = false;
-        *abort_flag = 1;
-        break;
-      }
-      fence_after();
-      const uint32_t a = smem_u32(smem + s * S::STAGE);
-      const uint32_t b = a + S::A_BYTES;
-#pragma unroll
-      for (int k = 0; k < KSTEPS; ++k)
-        mma<TF32>(tmem, sw128_desc(a + 32 * k), sw128_desc(b + 32 * k), idesc,
-                  (kb > 0 || k > 0) ? 1u : 0u);
-      mma_commit(&empty[s]);
-    }
-    (void)ok;
-    mma_commit(accum);  // arrives once every issued MMA has completed
-  } else if (warp >= 2) {
-    // epilogue: TMEM lane quarter q = warp % 4 holds rows m0 + 32q + lane
-    const int q = warp & 3;
-    if (!mbar_wait(accum, 0, err, 3)) *(volatile int*)abort_flag = 1;
-    fence_after();
-    asm volatile("bar.sync 1, 128;" ::: "memory");  // one decision for all 4 warps
-    if (!*(volatile int*)abort_flag)
-      epi.template run<BN>(tmem, q, lane, warp - 2, blockIdx.x, blockIdx.y, m0, n0, M, N,
-                           reinterpret_cast<float*>(smem));
-  }
-  // wait (bounded) for any TMA still in flight on an abort path, then free TMEM
-  if (warp == 0 && lane == 0 && *(volatile int*)abort_flag) {
-    for (int s = 0; s < STAGES; ++s) {
-      for (uint32_t i = 0; i < (1u << 20); ++i)
-        if (mbar_try_wait(&full[s], 0) || mbar_try_wait(&full[s], 1)) break;
-    }
-  }
-  fence_before();
-  __syncthreads();
-  if (warp == 1) {
-    fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                 "r"((uint32_t)BN));
-  }
-}
-
 
 // Named barrier 1 over the W epilogue warps, returning the OR of a flag.
 template <int W>
@@ -712,26 +606,6 @@ int make_tmap_3d(CUtensorMap* m, const void* base, int elem_bytes, long planes, 
   return AFQMC_OK;
 }
 
-template <int BN, int STAGES, bool TF32, class Epi>
-static int launch_tc(const TcGemm& g, const Epi& epi, dim3 grid, cudaStream_t st) {
-  using S = tc::Smem<BN, STAGES>;
-  const int eb = TF32 ? 4 : 2;
-  CUtensorMap ta, tb;
-  AFQ_TRY(make_tmap(&ta, g.A, eb, g.m, g.k, g.lda, tc::BM));
-  AFQ_TRY(make_tmap(&tb, g.B, eb, g.n, g.k, g.ldb, BN));
-  auto kern = tc::k_tc_gemm<BN, STAGES, TF32, Epi>;
-  static bool attr = false;
-  if (!attr) {
-    AFQ_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, S::TOTAL));
-    attr = true;
-  }
-  if (grid.y > 65535u) {
-    set_error("tc gemm: n too large");
-    return AFQMC_EINVAL;
-  }
-  AFQ_LAUNCH(kern, grid, 192, S::TOTAL, st, ta, tb, g.m, g.n, g.k, epi, g.err);
-  return AFQMC_OK;
-}
 
 // Tensor map of any rank (2..5): dims innermost first, strides in bytes for
 // dims 1.., box sizes per dim; 128-byte swizzle, out-of-range elements read 0.

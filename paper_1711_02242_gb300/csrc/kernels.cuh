@@ -79,16 +79,6 @@ struct TaylorArgsT {
 };
 using TaylorArgs = TaylorArgsT<double>;
 int launch_taylor_term(const TaylorArgsT<double>& a, cudaStream_t st);
-int launch_taylor_term(const TaylorArgsT<float>& a, cudaStream_t st);
-
-struct LuArgs {
-  int W, N;
-  const double* S;   // [W][2][N][N]: S_c[i][j] at [w][c][j][i]
-  double* Sinv;      // [W][2][N][N]: row-major S^-1
-  double* logdet;    // [W][2]: 2 log|det S|, wrapped 2 arg det S
-  const double* wt;  // alive mask
-};
-int launch_lu_inv(const LuArgs& a, cudaStream_t st);
 
 // Fused overlap: S = V_T^T Phi, Gauss-Jordan S^-1 and log det, Theta = Phi S^-1.
 struct OverlapArgs {
@@ -101,19 +91,9 @@ struct OverlapArgs {
   void* th_lo = nullptr;
   int lo_kind = LO_NONE, Mp = 0;
   int unit_trial = 0;  // VTt = [I_N | 0]: S is the top block of Phi, Theta's top rows I
+  double2* Sinv = nullptr;  // [W][N][N] scratch: S^-1 of live walkers
 };
 int launch_overlap(const OverlapArgs& a, cudaStream_t st);
-
-struct ThetaArgs {
-  int W, M, N;
-  const double* Sinv;  // [W][2][N][N]
-  const double* phiT;  // [W][2][N][M]
-  double* thetaT;      // [W][2][N][M]
-  const double* wt;
-  void* th_lo = nullptr;  // mixed path: BF16/TF32 copy [W][2][N][Mp]
-  int lo_kind = LO_NONE, Mp = 0;
-};
-int launch_theta(const ThetaArgs& a, cudaStream_t st);
 
 struct WeightArgs {
   int W, mode;
@@ -206,8 +186,5 @@ int launch_convert_f32(const double* src, float* dst, long n, cudaStream_t st);
 // full Cholesky vectors transposed, rows (p, q) = p * Mp + q, pitch Gp, low precision
 int launch_pack_full_lo(const double* L, int G, int M, int Mp, int Gp, void* out, int kind,
                         cudaStream_t st);
-// [Re V | Im V] rows (pitch 2 Mp) for the tensor-core Taylor terms, from packed Y
-int launch_unpack_v(const float* Y, long ldy, int W, int M, int Mp, double sdt, void* V, int kind,
-                    cudaStream_t st);
 
 }  // namespace afq

@@ -254,254 +254,24 @@ static int launch_taylor(const TaylorArgsT<T>& a, cudaStream_t st) {
   return AFQMC_OK;
 }
 int launch_taylor_term(const TaylorArgsT<double>& a, cudaStream_t st) { return launch_taylor(a, st); }
-int launch_taylor_term(const TaylorArgsT<float>& a, cudaStream_t st) { return launch_taylor(a, st); }
 
-// ------------------------------------------------------- LU / inverse ------
-// Overlap matrix S = V_T^T Phi (Theorem 1.1): Gauss-Jordan elimination with
-// partial pivoting (largest modulus in the column) gives S^-1 and
-// log det S = sum_k log p_k (+ i pi per row swap).  Stored per walker:
-// log <Psi_T|Psi> = 2 log det S (both spins): real part and phase wrapped to
-// (-pi, pi].
-__global__ void __launch_bounds__(128) k_lu_inv(LuArgs a) {
-  extern __shared__ double2 lu_sm[];
-  const int w = blockIdx.x;
-  const bool live = !a.wt || walker_alive(a.wt, w);  // log det stored for live walkers
-  const int N = a.N;
-  double2* A = lu_sm;          // [N][N]
-  double2* Inv = lu_sm + N * N;  // [N][N]
-  __shared__ int piv;
-  __shared__ double logabs, phase;
-  __shared__ int swaps, singular;
-  const double* S = a.S + (long)w * 2 * N * N;
-  for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x) {
-    const int i = idx / N, j = idx % N;
-    A[idx] = make_double2(S[(long)j * N + i], S[(long)N * N + (long)j * N + i]);
-    Inv[idx] = make_double2(i == j ? 1.0 : 0.0, 0.0);
-  }
-  if (threadIdx.x == 0) {
-    logabs = 0.0;
-    phase = 0.0;
-    swaps = 0;
-    singular = 0;
-  }
-  __syncthreads();
-  for (int k = 0; k < N; ++k) {
-    if (threadIdx.x < 32) {
-      // pivot: the largest |a_rk|^2 over rows r >= k, the first such row on ties
-      int best = k;
-      double bv = -1.0;
-      for (int r = k + threadIdx.x; r < N; r += 32) {
-        const double2 x = A[r * N + k];
-        const double v = x.x * x.x + x.y * x.y;
-        if (v > bv) {
-          bv = v;
-          best = r;
-        }
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
-        const int ob = __shfl_xor_sync(0xffffffffu, best, o);
-        if (ov > bv || (ov == bv && ob < best)) {
-          bv = ov;
-          best = ob;
-        }
-      }
-      if (threadIdx.x == 0) {
-        piv = best;
-        if (!(bv > 0.0)) singular = 1;
-      }
-    }
-    __syncthreads();
-    if (singular) break;
-    if (piv != k) {
-      for (int j = threadIdx.x; j < N; j += blockDim.x) {
-        double2 t = A[k * N + j];
-        A[k * N + j] = A[piv * N + j];
-        A[piv * N + j] = t;
-        t = Inv[k * N + j];
-        Inv[k * N + j] = Inv[piv * N + j];
-        Inv[piv * N + j] = t;
-      }
-      if (threadIdx.x == 0) swaps++;
-    }
-    __syncthreads();
-    const double2 p = A[k * N + k];
-    const double den = p.x * p.x + p.y * p.y;
-    const double2 rp = make_double2(p.x / den, -p.y / den);  // 1/p
-    if (threadIdx.x == 0) {
-      logabs += 0.5 * log(den);
-      phase += atan2(p.y, p.x);
-    }
-    __syncthreads();
-    for (int j = threadIdx.x; j < N; j += blockDim.x) {
-      const double2 v = A[k * N + j], u = Inv[k * N + j];
-      A[k * N + j] = make_double2(v.x * rp.x - v.y * rp.y, v.x * rp.y + v.y * rp.x);
-      Inv[k * N + j] = make_double2(u.x * rp.x - u.y * rp.y, u.x * rp.y + u.y * rp.x);
-    }
-    __syncthreads();
-    // eliminate column k from every other row; factors read before updates
-    for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x) {
-      const int r = idx / N, j = idx % N;
-      if (r == k || j == k) continue;
-      const double2 f = A[r * N + k];
-      const double2 v = A[k * N + j];
-      double2& d = A[r * N + j];
-      d.x = fma(-f.x, v.x, fma(f.y, v.y, d.x));
-      d.y = fma(-f.x, v.y, fma(-f.y, v.x, d.y));
-    }
-    for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x) {
-      const int r = idx / N, j = idx % N;
-      if (r == k) continue;
-      const double2 f = A[r * N + k];
-      const double2 v = Inv[k * N + j];
-      double2& d = Inv[r * N + j];
-      d.x = fma(-f.x, v.x, fma(f.y, v.y, d.x));
-      d.y = fma(-f.x, v.y, fma(-f.y, v.x, d.y));
-    }
-    __syncthreads();
-    for (int r = threadIdx.x; r < N; r += blockDim.x)
-      if (r != k) A[r * N + k] = make_double2(0.0, 0.0);
-    __syncthreads();
-  }
-  double* out = a.Sinv + (long)w * 2 * N * N;
-  for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x) {
-    out[idx] = singular ? 0.0 : Inv[idx].x;
-    out[(long)N * N + idx] = singular ? 0.0 : Inv[idx].y;
-  }
-  if (threadIdx.x == 0 && live) {
-    if (singular) {
-      a.logdet[2L * w] = -INFINITY;
-      a.logdet[2L * w + 1] = 0.0;
-    } else {
-      a.logdet[2L * w] = 2.0 * logabs;
-      a.logdet[2L * w + 1] = wrap_pi(2.0 * (phase + 3.141592653589793 * swaps));
-    }
-  }
-}
-
-int launch_lu_inv(const LuArgs& a, cudaStream_t st) {
-  const size_t smem = 2ull * a.N * a.N * sizeof(double2);
-  if (smem > 200 * 1024) {
-    set_error("lu: N=%d too large for the shared-memory LU", a.N);
-    return AFQMC_EUNSUPPORTED;
-  }
-  static bool attr = false;
-  if (!attr) {
-    AFQ_CUDA(cudaFuncSetAttribute(k_lu_inv, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  200 * 1024));
-    attr = true;
-  }
-  AFQ_LAUNCH(k_lu_inv, a.W, 128, smem, st, a);
-  return AFQMC_OK;
-}
-
-// ------------------------------------------------------------------ Theta --
-// Theta = Phi S^-1 (Eq. precomputing for one determinant), stored as
-// Theta^T[i][p] = sum_j S^-1[j][i] Phi^T[j][p].
-__global__ void __launch_bounds__(128) k_theta(ThetaArgs a) {
-  extern __shared__ double th_sm[];  // [2][N][N]
-  const int w = blockIdx.y;
-  const bool live = walker_alive(a.wt, w);  // Theta is stored for live walkers only
-  const int N = a.N, M = a.M;
-  const double* Si = a.Sinv + (long)w * 2 * N * N;
-  for (int idx = threadIdx.x; idx < 2 * N * N; idx += blockDim.x) th_sm[idx] = Si[idx];
-  __syncthreads();
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= M) return;
-  const double* ph = a.phiT + (long)w * 2 * N * M;
-  double* th = a.thetaT + (long)w * 2 * N * M;
-  const double* SR = th_sm;
-  const double* SI = th_sm + N * N;
-  for (int i0 = 0; i0 < N; i0 += 16) {
-    double ar[16], ai[16];
-#pragma unroll
-    for (int u = 0; u < 16; ++u) ar[u] = ai[u] = 0.0;
-    for (int j = 0; j < N; ++j) {
-      const double fr = ph[(long)j * M + p], fi = ph[((long)N + j) * M + p];
-#pragma unroll
-      for (int u = 0; u < 16; ++u) {
-        const int i = i0 + u;
-        if (i < N) {
-          const double sr = SR[j * N + i], si = SI[j * N + i];
-          ar[u] = fma(fr, sr, fma(-fi, si, ar[u]));
-          ai[u] = fma(fr, si, fma(fi, sr, ai[u]));
-        }
-      }
-    }
-    if (!live) continue;
-#pragma unroll
-    for (int u = 0; u < 16; ++u) {
-      const int i = i0 + u;
-      if (i < N) {
-        th[(long)i * M + p] = ar[u];
-        th[((long)N + i) * M + p] = ai[u];
-        if (a.th_lo) store_lo(a.th_lo, a.lo_kind, ((long)w * 2 * N + i) * a.Mp + p, ar[u]);
-        if (a.th_lo) store_lo(a.th_lo, a.lo_kind, ((long)w * 2 * N + N + i) * a.Mp + p, ai[u]);
-      }
-    }
-  }
-}
-
-int launch_theta(const ThetaArgs& a, cudaStream_t st) {
-  dim3 grid(cdiv(a.M, 128), a.W);
-  static bool attr = false;
-  if (!attr) {
-    AFQ_CUDA(cudaFuncSetAttribute(k_theta, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
-    attr = true;
-  }
-  AFQ_LAUNCH(k_theta, grid, 128, 2ull * a.N * a.N * sizeof(double), st, a);
-  return AFQMC_OK;
-}
-
-// ------------------------------------------------------- fused overlap ------
-// One block per walker, float64 throughout (Theorem 1.1, Eq. precomputing):
-//   1. S = V_T^T Phi (N x N complex): V_T^T and Phi^T are staged through
-//      shared memory OV_P orbitals at a time (coalesced loads), each thread
+// ------------------------------------------------------------- overlap ------
+// Float64 throughout (Theorem 1.1, Eq. precomputing).  k_overlap, one block
+// per walker:
+//   1. S = V_T^T Phi (N x N complex): with V_T = [I_N; 0] (the trial-adapted
+//      basis) the top block of Phi; otherwise V_T^T and Phi^T are staged
+//      through shared memory OV_P orbitals at a time, each thread
 //      accumulating up to OV_R entries of S (re and im planes);
 //   2. Gauss-Jordan elimination with partial pivoting (largest modulus,
 //      searched by one warp): S^-1 and log det S = sum log p_k (+ i pi per
-//      row swap);
-//   3. Theta^T[i][p] = sum_j S^-1[j][i] Phi^T[j][p].
+//      row swap), S^-1 written for k_theta_rows;
+// then k_theta_rows forms Theta^T[i][p] = sum_j S^-1[j][i] Phi^T[j][p].
 // log <Psi_T|Psi> = 2 log det S (both spins), phase wrapped to (-pi, pi].
 // Every walker is computed; Theta and log det are stored for live walkers.
 namespace {
 constexpr int OV_P = 32, OV_R = 8, OV_T = 256;
 }
 
-// Theta^T[i][p] = sum_j S^-1[j][i] Phi^T[j][p] for p >= p0, IB orbitals i per
-// work item (IB divides N).
-template <int IB>
-__device__ __forceinline__ void theta_rows(const OverlapArgs& a, int w, const double2* Inv,
-                                           const double* fr, const double* fi, double* tr,
-                                           double* ti, int p0) {
-  const int N = a.N, M = a.M, np = M - p0, nib = N / IB;
-  for (int item = threadIdx.x; item < np * nib; item += blockDim.x) {
-    const int p = p0 + item % np, i0 = (item / np) * IB;
-    double ar[IB], ai[IB];
-#pragma unroll
-    for (int u = 0; u < IB; ++u) ar[u] = ai[u] = 0.0;
-    for (int j = 0; j < N; ++j) {
-      const double xr = fr[(long)j * M + p], xi = fi[(long)j * M + p];
-#pragma unroll
-      for (int u = 0; u < IB; ++u) {
-        const double2 sv = Inv[j * N + i0 + u];
-        ar[u] = fma(xr, sv.x, fma(-xi, sv.y, ar[u]));
-        ai[u] = fma(xr, sv.y, fma(xi, sv.x, ai[u]));
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < IB; ++u) {
-      const int i = i0 + u;
-      tr[(long)i * M + p] = ar[u];
-      ti[(long)i * M + p] = ai[u];
-      if (a.th_lo) {
-        store_lo(a.th_lo, a.lo_kind, ((long)w * 2 * N + i) * a.Mp + p, ar[u]);
-        store_lo(a.th_lo, a.lo_kind, ((long)w * 2 * N + N + i) * a.Mp + p, ai[u]);
-      }
-    }
-  }
-}
 __global__ void __launch_bounds__(OV_T) k_overlap(OverlapArgs a) {
   extern __shared__ double2 ov_sm[];
   const int w = blockIdx.x;
@@ -659,37 +429,77 @@ __global__ void __launch_bounds__(OV_T) k_overlap(OverlapArgs a) {
       a.logdet[2L * w + 1] = wrap_pi(2.0 * (phase + 3.141592653589793 * swaps));
     }
   }
+  // S^-1 of live, non-singular walkers for the Theta kernel
   if (singular || !live) return;
-  // Theta^T = S^-T Phi^T: work items (p, block of IB orbitals i), IB the
-  // largest divisor of N up to 8 (no padded lanes); with V_T = [I_N; 0] rows
-  // p < N are rows of S S^-1 = I
+  double2* si = a.Sinv + (long)w * N * N;
+  for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x) si[idx] = Inv[idx];
+}
+
+// Theta^T[i][p] = sum_j S^-1[j][i] Phi^T[j][p]: block (x, w) takes rows
+// p in [x TH_P, (x + 1) TH_P) of walker w in work items (p, block of IB
+// orbitals i), IB the largest divisor of N up to 8 (no padded lanes), so the
+// FP64 work of all walkers spreads evenly over the SMs.  With V_T = [I_N; 0]
+// rows p < N are rows of S S^-1 = I.  Dead and singular walkers keep Theta.
+namespace {
+constexpr int TH_P = 64, TH_T = 128;
+}
+template <int IB>
+__global__ void __launch_bounds__(TH_T) k_theta_rows(OverlapArgs a) {
+  extern __shared__ double2 th_sinv[];  // [N][N]
+  const int w = blockIdx.y, N = a.N, M = a.M;
+  if ((a.wt && !walker_alive(a.wt, w)) || !(a.logdet[2L * w] > -INFINITY)) return;
+  const double2* si = a.Sinv + (long)w * N * N;
+  for (int idx = threadIdx.x; idx < N * N; idx += TH_T) th_sinv[idx] = si[idx];
+  __syncthreads();
+  const double* fr = a.phiT + (long)w * 2 * N * M;
+  const double* fi = fr + (long)N * M;
   double* tr = a.thetaT + (long)w * 2 * N * M;
   double* ti = tr + (long)N * M;
-  const int p0 = a.unit_trial ? N : 0;
-  if (a.unit_trial) {
-    for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x) {
-      const int i = idx / N, p = idx % N;
-      const double v = i == p ? 1.0 : 0.0;
-      tr[(long)i * M + p] = v;
-      ti[(long)i * M + p] = 0.0;
+  const int pb = blockIdx.x * TH_P, pe = min(M, pb + TH_P), np = pe - pb, nib = N / IB;
+  for (int item = threadIdx.x; item < np * nib; item += TH_T) {
+    const int p = pb + item % np, i0 = (item / np) * IB;
+    double ar[IB], ai[IB];
+#pragma unroll
+    for (int u = 0; u < IB; ++u) ar[u] = ai[u] = 0.0;
+    if (a.unit_trial && p < N) {
+#pragma unroll
+      for (int u = 0; u < IB; ++u) ar[u] = (i0 + u == p) ? 1.0 : 0.0;
+    } else {
+      for (int j = 0; j < N; ++j) {
+        const double xr = fr[(long)j * M + p], xi = fi[(long)j * M + p];
+#pragma unroll
+        for (int u = 0; u < IB; ++u) {
+          const double2 sv = th_sinv[j * N + i0 + u];
+          ar[u] = fma(xr, sv.x, fma(-xi, sv.y, ar[u]));
+          ai[u] = fma(xr, sv.y, fma(xi, sv.x, ai[u]));
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < IB; ++u) {
+      const int i = i0 + u;
+      tr[(long)i * M + p] = ar[u];
+      ti[(long)i * M + p] = ai[u];
       if (a.th_lo) {
-        store_lo(a.th_lo, a.lo_kind, ((long)w * 2 * N + i) * a.Mp + p, v);
-        store_lo(a.th_lo, a.lo_kind, ((long)w * 2 * N + N + i) * a.Mp + p, 0.0);
+        store_lo(a.th_lo, a.lo_kind, ((long)w * 2 * N + i) * a.Mp + p, ar[u]);
+        store_lo(a.th_lo, a.lo_kind, ((long)w * 2 * N + N + i) * a.Mp + p, ai[u]);
       }
     }
   }
-  int ib = 8;
-  while (N % ib) --ib;
-  switch (ib) {
-    case 8: theta_rows<8>(a, w, Inv, fr, fi, tr, ti, p0); break;
-    case 7: theta_rows<7>(a, w, Inv, fr, fi, tr, ti, p0); break;
-    case 6: theta_rows<6>(a, w, Inv, fr, fi, tr, ti, p0); break;
-    case 5: theta_rows<5>(a, w, Inv, fr, fi, tr, ti, p0); break;
-    case 4: theta_rows<4>(a, w, Inv, fr, fi, tr, ti, p0); break;
-    case 3: theta_rows<3>(a, w, Inv, fr, fi, tr, ti, p0); break;
-    case 2: theta_rows<2>(a, w, Inv, fr, fi, tr, ti, p0); break;
-    default: theta_rows<1>(a, w, Inv, fr, fi, tr, ti, p0); break;
+}
+
+template <int IB>
+static int launch_theta_rows(const OverlapArgs& a, cudaStream_t st) {
+  static bool attr = false;
+  const size_t smem = sizeof(double2) * (size_t)a.N * a.N;
+  if (!attr) {
+    AFQ_CUDA(cudaFuncSetAttribute(k_theta_rows<IB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  100 * 1024));
+    attr = true;
   }
+  dim3 grid(cdiv(a.M, TH_P), a.W);
+  AFQ_LAUNCH(k_theta_rows<IB>, grid, TH_T, smem, st, a);
+  return AFQMC_OK;
 }
 
 int launch_overlap(const OverlapArgs& a, cudaStream_t st) {
@@ -705,7 +515,18 @@ int launch_overlap(const OverlapArgs& a, cudaStream_t st) {
     attr = true;
   }
   AFQ_LAUNCH(k_overlap, a.W, OV_T, smem, st, a);
-  return AFQMC_OK;
+  int ib = 8;
+  while (a.N % ib) --ib;
+  switch (ib) {
+    case 8: return launch_theta_rows<8>(a, st);
+    case 7: return launch_theta_rows<7>(a, st);
+    case 6: return launch_theta_rows<6>(a, st);
+    case 5: return launch_theta_rows<5>(a, st);
+    case 4: return launch_theta_rows<4>(a, st);
+    case 3: return launch_theta_rows<3>(a, st);
+    case 2: return launch_theta_rows<2>(a, st);
+    default: return launch_theta_rows<1>(a, st);
+  }
 }
 
 // ---------------------------------------------------------------- weights --
@@ -1281,64 +1102,6 @@ int launch_sumsq(const double* v, double* out, int n, cudaStream_t st) {
 
 // ------------------------------------------------- low-precision copies ----
 namespace afq {
-// Operand of the tensor-core Taylor terms from the packed Y = sum_g x_g L_g
-// (FP32, pitch ldy per walker component): row (w, p) of V holds
-// [Re V[p][0..M), 0.. | Im V[p][0..M), 0..] (pitch 2 Mp) with V = i sqrt(dt) Y,
-// i.e. Re V = -sqrt(dt) Im Y and Im V = sqrt(dt) Re Y.  32x32 tiles of (p, q):
-// tiles above the diagonal read packed rows p, tiles below read rows q and are
-// transposed in shared memory, so both loads and stores are contiguous.
-__global__ void __launch_bounds__(256) k_unpack_v(const float* Y, long ldy, int M, int Mp,
-                                                  float sdt, void* V, int kind) {
-  __shared__ float sr[32][33], si[32][33];
-  const int w = blockIdx.y, p0 = blockIdx.x * 32;  // one 32-row strip of one walker
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  const float* Yr = Y + (long)w * 2 * ldy;
-  const float* Yi = Yr + ldy;
-  for (int q0 = 0; q0 < Mp; q0 += 32) {
-  __syncthreads();  // the previous tile's shared-memory reads are done
-  if (p0 < q0 + 32) {  // diagonal or upper tile: element (p, q) at packed(min, max)
-    for (int r = ty; r < 32; r += 8) {
-      const int p = p0 + r, q = q0 + tx;
-      float a = 0.f, b = 0.f;
-      if (p < M && q < M) {
-        const long id = (p <= q) ? packed_index(p, q, M) : packed_index(q, p, M);
-        a = Yr[id];
-        b = Yi[id];
-      }
-      sr[r][tx] = a;
-      si[r][tx] = b;
-    }
-  } else {  // lower tile: (p, q) with q < p is stored in packed row q
-    for (int r = ty; r < 32; r += 8) {
-      const int q = q0 + r, p = p0 + tx;
-      float a = 0.f, b = 0.f;
-      if (p < M && q < M) {
-        const long id = packed_index(q, p, M);
-        a = Yr[id];
-        b = Yi[id];
-      }
-      sr[tx][r] = a;
-      si[tx][r] = b;
-    }
-  }
-  __syncthreads();
-  for (int r = ty; r < 32; r += 8) {
-    const int p = p0 + r, q = q0 + tx;
-    if (p >= M || q >= Mp) continue;
-    const long row = ((long)w * M + p) * 2 * Mp;
-    store_lo(V, kind, row + q, -sdt * si[r][tx]);
-    store_lo(V, kind, row + Mp + q, sdt * sr[r][tx]);
-  }
-  }
-}
-
-int launch_unpack_v(const float* Y, long ldy, int W, int M, int Mp, double sdt, void* V, int kind,
-                    cudaStream_t st) {
-  dim3 grid(cdiv(M, 32), W);
-  AFQ_LAUNCH(k_unpack_v, grid, 256, 0, st, Y, ldy, M, Mp, (float)sdt, V, kind);
-  return AFQMC_OK;
-}
-
 __global__ void k_convert_lo(const double* src, long rows, long cols, long lds, void* dst,
                              long ldd, int kind) {
   const long n = rows * ldd;
