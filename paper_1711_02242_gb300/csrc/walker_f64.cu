@@ -256,93 +256,155 @@ static int launch_taylor(const TaylorArgsT<T>& a, cudaStream_t st) {
 int launch_taylor_term(const TaylorArgsT<double>& a, cudaStream_t st) { return launch_taylor(a, st); }
 
 // ------------------------------------------------------------- overlap ------
-// Float64 throughout (Theorem 1.1, Eq. precomputing), in the trial-adapted
-// basis where V_T = [I_N; 0].  k_overlap, one warp per walker:
-//   1. S = V_T^T Phi is the top N x N block of Phi (a gather);
-//   2. Gauss-Jordan elimination with partial pivoting (largest |s_rk|^2, the
-//      first row on ties): S^-1 and log det S = sum log p_k (+ i pi per row
-//      swap).  The warp works without block barriers, so the FP64 pipe stays
-//      busy with other walkers' warps while one waits on its pivot;
+// Float64 throughout (Theorem 1.1, Eq. precomputing).  k_overlap, one block
+// per walker:
+//   1. S = V_T^T Phi (N x N complex): with V_T = [I_N; 0] (the trial-adapted
+//      basis) the top block of Phi; otherwise V_T^T and Phi^T are staged
+//      through shared memory OV_P orbitals at a time, each thread
+//      accumulating up to OV_R entries of S (re and im planes);
+//   2. Gauss-Jordan elimination with partial pivoting (largest modulus,
+//      searched by one warp): S^-1 and log det S = sum log p_k (+ i pi per
+//      row swap), S^-1 written for k_theta_rows;
 // then k_theta_rows forms Theta^T[i][p] = sum_j S^-1[j][i] Phi^T[j][p].
 // log <Psi_T|Psi> = 2 log det S (both spins), phase wrapped to (-pi, pi].
-// Every walker is computed; S^-1 and log det are stored for live walkers.
-__global__ void __launch_bounds__(32) k_overlap(OverlapArgs a) {
+// Every walker is computed; Theta and log det are stored for live walkers.
+namespace {
+constexpr int OV_P = 32, OV_R = 8, OV_T = 256;
+}
+
+__global__ void __launch_bounds__(OV_T) k_overlap(OverlapArgs a) {
   extern __shared__ double2 ov_sm[];
-  const int w = blockIdx.x, lane = threadIdx.x;
+  const int w = blockIdx.x;
   const bool live = !a.wt || walker_alive(a.wt, w);
   const int N = a.N, M = a.M;
   double2* A = ov_sm;            // [N][N]
   double2* Inv = ov_sm + N * N;  // [N][N]
+  double* Vs = reinterpret_cast<double*>(ov_sm + 2 * N * N);  // [N][OV_P + 1]
+  double* Ps = Vs + N * (OV_P + 1);                           // [2N][OV_P + 1]
+  __shared__ int piv, swaps, singular;
+  __shared__ double logabs, phase;
+  __shared__ double2 rpiv;
   const double* fr = a.phiT + (long)w * 2 * N * M;
   const double* fi = fr + (long)N * M;
-  for (int idx = lane; idx < N * N; idx += 32) {
-    const int i = idx / N, j = idx % N;
-    A[idx] = make_double2(fr[(long)j * M + i], fi[(long)j * M + i]);
-    Inv[idx] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+  const int nout = 2 * N * N;  // (i, c, j): S_c[i][j], c = re / im plane
+  if (a.unit_trial) {
+    // V_T = [I_N; 0]: S[i][j] = Phi[i][j], the top block of the orbitals
+    for (int idx = threadIdx.x; idx < N * N; idx += OV_T) {
+      const int i = idx / N, j = idx % N;
+      A[idx] = make_double2(fr[(long)j * M + i], fi[(long)j * M + i]);
+    }
   }
-  __syncwarp();
-  double logabs = 0.0, phase = 0.0;
-  int swaps = 0;
-  bool singular = false;
-  for (int k = 0; k < N; ++k) {
-    int best = k;
-    double bv = -1.0;
-    for (int r = k + lane; r < N; r += 32) {
-      const double2 x = A[r * N + k];
-      const double v = x.x * x.x + x.y * x.y;
-      if (v > bv) {
-        bv = v;
-        best = r;
+  for (int o0 = 0; o0 < (a.unit_trial ? 0 : nout); o0 += OV_T * OV_R) {
+    double acc[OV_R];
+#pragma unroll
+    for (int r = 0; r < OV_R; ++r) acc[r] = 0.0;
+    for (int p0 = 0; p0 < M; p0 += OV_P) {
+      for (int idx = threadIdx.x; idx < 3 * N * OV_P; idx += OV_T) {
+        const int row = idx / OV_P, pp = idx % OV_P, pc = p0 + pp;
+        double v = 0.0;
+        if (pc < M) v = row < N ? a.VTt[(long)row * M + pc] : fr[(long)(row - N) * M + pc];
+        if (row < N)
+          Vs[row * (OV_P + 1) + pp] = v;
+        else
+          Ps[(row - N) * (OV_P + 1) + pp] = v;
       }
+      __syncthreads();
+#pragma unroll
+      for (int r = 0; r < OV_R; ++r) {
+        const int o = o0 + threadIdx.x + r * OV_T;
+        if (o < nout) {
+          const int i = o / (2 * N), cj = o % (2 * N);
+          const double* vs = Vs + i * (OV_P + 1);
+          const double* ps = Ps + cj * (OV_P + 1);
+          double t = acc[r];
+#pragma unroll 8
+          for (int pp = 0; pp < OV_P; ++pp) t = fma(vs[pp], ps[pp], t);
+          acc[r] = t;
+        }
+      }
+      __syncthreads();
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {  // every lane ends with the same pivot
-      const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
-      const int ob = __shfl_xor_sync(0xffffffffu, best, o);
-      if (ov > bv || (ov == bv && ob < best)) {
-        bv = ov;
-        best = ob;
+    for (int r = 0; r < OV_R; ++r) {
+      const int o = o0 + threadIdx.x + r * OV_T;
+      if (o < nout) {
+        const int i = o / (2 * N), cj = o % (2 * N), c = cj / N, j = cj % N;
+        double* d = reinterpret_cast<double*>(&A[i * N + j]);
+        d[c] = acc[r];
       }
     }
-    if (!(bv > 0.0)) {
-      singular = true;
-      break;
+  }
+  for (int idx = threadIdx.x; idx < N * N; idx += OV_T)
+    Inv[idx] = make_double2(idx / N == idx % N ? 1.0 : 0.0, 0.0);
+  if (threadIdx.x == 0) {
+    logabs = 0.0;
+    phase = 0.0;
+    swaps = 0;
+    singular = 0;
+  }
+  __syncthreads();
+  for (int k = 0; k < N; ++k) {
+    if (threadIdx.x < 32) {
+      // pivot: the largest |a_rk|^2 over rows r >= k, the first such row on ties
+      int best = k;
+      double bv = -1.0;
+      for (int r = k + threadIdx.x; r < N; r += 32) {
+        const double2 x = A[r * N + k];
+        const double v = x.x * x.x + x.y * x.y;
+        if (v > bv) {
+          bv = v;
+          best = r;
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        const int ob = __shfl_xor_sync(0xffffffffu, best, o);
+        if (ov > bv || (ov == bv && ob < best)) {
+          bv = ov;
+          best = ob;
+        }
+      }
+      if (threadIdx.x == 0) {
+        piv = best;
+        if (!(bv > 0.0)) singular = 1;
+      }
     }
-    if (best != k) {
-      for (int j = lane; j < N; j += 32) {
+    __syncthreads();
+    if (singular) break;
+    if (piv != k) {
+      for (int j = threadIdx.x; j < N; j += blockDim.x) {
         double2 t = A[k * N + j];
-        A[k * N + j] = A[best * N + j];
-        A[best * N + j] = t;
+        A[k * N + j] = A[piv * N + j];
+        A[piv * N + j] = t;
         t = Inv[k * N + j];
-        Inv[k * N + j] = Inv[best * N + j];
-        Inv[best * N + j] = t;
+        Inv[k * N + j] = Inv[piv * N + j];
+        Inv[piv * N + j] = t;
       }
-      ++swaps;
-      __syncwarp();
+      if (threadIdx.x == 0) swaps++;
     }
-    // 1 / pivot on one lane (float64 division and log are long FP64 sequences)
-    double rpx = 0.0, rpy = 0.0;
-    if (lane == 0) {
+    __syncthreads();
+    // 1 / pivot once (float64 division and log run long on the FP64 pipe)
+    if (threadIdx.x == 0) {
       const double2 pv = A[k * N + k];
       const double den = pv.x * pv.x + pv.y * pv.y;
-      rpx = pv.x / den;
-      rpy = -pv.y / den;
+      rpiv = make_double2(pv.x / den, -pv.y / den);
       logabs += 0.5 * log(den);
       phase += atan2(pv.y, pv.x);
     }
-    rpx = __shfl_sync(0xffffffffu, rpx, 0);
-    rpy = __shfl_sync(0xffffffffu, rpy, 0);
-    for (int j = lane; j < N; j += 32) {
+    __syncthreads();
+    const double2 rp = rpiv;
+    for (int j = threadIdx.x; j < N; j += blockDim.x) {
       const double2 v = A[k * N + j], u = Inv[k * N + j];
-      A[k * N + j] = make_double2(fma(v.x, rpx, -v.y * rpy), fma(v.x, rpy, v.y * rpx));
-      Inv[k * N + j] = make_double2(fma(u.x, rpx, -u.y * rpy), fma(u.x, rpy, u.y * rpx));
+      A[k * N + j] = make_double2(v.x * rp.x - v.y * rp.y, v.x * rp.y + v.y * rp.x);
+      Inv[k * N + j] = make_double2(u.x * rp.x - u.y * rp.y, u.x * rp.y + u.y * rp.x);
     }
-    __syncwarp();
+    __syncthreads();
     // eliminate column k from the other rows.  Columns j < k of A are already
     // unit vectors (row k holds 0 there), so A changes only in columns j > k;
     // Inv changes in every column (row swaps can move any column forward)
     const int na = N - 1 - k;  // A columns k+1 .. N-1
-    for (int idx = lane; idx < (N - 1) * (na + N); idx += 32) {
+    for (int idx = threadIdx.x; idx < (N - 1) * (na + N); idx += blockDim.x) {
       const int rr = idx / (na + N), c = idx % (na + N);
       const int r = rr < k ? rr : rr + 1;  // rows other than k
       const double2 f = A[r * N + k];
@@ -353,12 +415,12 @@ __global__ void __launch_bounds__(32) k_overlap(OverlapArgs a) {
       d.x = fma(-f.x, v.x, fma(f.y, v.y, d.x));
       d.y = fma(-f.x, v.y, fma(-f.y, v.x, d.y));
     }
-    __syncwarp();
-    for (int r = lane; r < N; r += 32)
+    __syncthreads();
+    for (int r = threadIdx.x; r < N; r += blockDim.x)
       if (r != k) A[r * N + k] = make_double2(0.0, 0.0);
-    __syncwarp();
+    __syncthreads();
   }
-  if (lane == 0 && live) {
+  if (threadIdx.x == 0 && live) {
     if (singular) {
       a.logdet[2L * w] = -INFINITY;
       a.logdet[2L * w + 1] = 0.0;
@@ -370,7 +432,7 @@ __global__ void __launch_bounds__(32) k_overlap(OverlapArgs a) {
   // S^-1 of live, non-singular walkers for the Theta kernel
   if (singular || !live) return;
   double2* si = a.Sinv + (long)w * N * N;
-  for (int idx = lane; idx < N * N; idx += 32) si[idx] = Inv[idx];
+  for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x) si[idx] = Inv[idx];
 }
 
 // Theta^T[i][p] = sum_j S^-1[j][i] Phi^T[j][p]: block (x, w) takes rows
@@ -441,11 +503,7 @@ static int launch_theta_rows(const OverlapArgs& a, cudaStream_t st) {
 }
 
 int launch_overlap(const OverlapArgs& a, cudaStream_t st) {
-  const size_t smem = 2ull * a.N * a.N * sizeof(double2);
-  if (!a.unit_trial || !a.Sinv) {
-    set_error("overlap: the trial-adapted basis (V_T = [I; 0]) and S^-1 scratch are required");
-    return AFQMC_EINVAL;
-  }
+  const size_t smem = 2ull * a.N * a.N * sizeof(double2) + 3ull * a.N * (OV_P + 1) * sizeof(double);
   if (smem > 200 * 1024) {
     set_error("overlap: N=%d too large", a.N);
     return AFQMC_EUNSUPPORTED;
@@ -456,7 +514,7 @@ int launch_overlap(const OverlapArgs& a, cudaStream_t st) {
                                   200 * 1024));
     attr = true;
   }
-  AFQ_LAUNCH(k_overlap, a.W, 32, smem, st, a);
+  AFQ_LAUNCH(k_overlap, a.W, OV_T, smem, st, a);
   int ib = 8;
   while (a.N % ib) --ib;
   switch (ib) {
