@@ -39,7 +39,7 @@ sys.path.insert(0, ROOT)
 import workloads  # noqa: E402
 
 PHASES = ["force_bias", "fields", "v_assembly", "bhalf", "taylor", "overlap", "weight", "qr",
-          "comb", "energy"]
+          "comb", "energy", "theta"]
 
 
 def peaks():
@@ -58,7 +58,13 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # DRAM bytes (read + write) per launch from one ncu capture of the M=300 BF16
 # step, with the SHA-256 of the source file the kernel was built from; a
 # figure whose source has changed since is reported as null.
-TRAFFIC = {}
+TRAFFIC = {
+    "theta": {"bytes": (64.496128 + 30.346240) * 1e6, "sha": "004a95623cddb44574b90f88ec68835a3b661bb5614f289f67f091d90d5c8b4d"},
+    "overlap": {"bytes": 8.258816e6, "sha": "004a95623cddb44574b90f88ec68835a3b661bb5614f289f67f091d90d5c8b4d"},
+    "qr": {"bytes": (61.484800 + 26.066176) * 1e6, "sha": "004a95623cddb44574b90f88ec68835a3b661bb5614f289f67f091d90d5c8b4d"},
+    "taylor": {"bytes": (218.395392 + 20.219648) * 1e6, "sha": "7d84c2b3465f764bb47983565617111a70bc45f2b5fbc4a888a139d84b0bbc1f"},
+    "v_assembly": {"bytes": (332.216320 + 154.316032) * 1e6, "sha": "2a0d3c3691ec05bb86922022bf9219e589e16cc3c047a97f45a1de565fe02fb6"},
+}
 
 
 class ClockSampler:
@@ -151,9 +157,10 @@ def algorithmic_per_walker(w: workloads.Workload):
     """Algorithmic work of the step's kernels per walker (one spin block; the
     closed-shell walker's two blocks are the same matrix), as used for the
     roofline fractions:
-      overlap  FP64: Gauss-Jordan inverse of S (8 N^3) and Theta's M - N
-               non-trivial rows (8 (M - N) N^2): in the trial-adapted basis S
-               is the top block of Phi and Theta's top rows are I;
+      overlap  FP64: Gauss-Jordan inverse of S, 8 N^3 (in the trial-adapted
+               basis S is the top block of Phi);
+      theta    FP64: Theta's M - N non-trivial rows, 8 (M - N) N^2 (the top
+               N rows are I);
       qr       FP64: modified Gram-Schmidt, 8 M N^2, every qr_period steps;
       v        tensor: V = sum_g x_g L_g over the M (M + 1) / 2 distinct
                elements, complex x real: 2 N_g M (M + 1);
@@ -161,12 +168,13 @@ def algorithmic_per_walker(w: workloads.Workload):
       energy   tensor: force bias 4 N_g N M and exchange 4 N_g N^2 M (the
                T_g = Lh_g Theta products), per evaluation."""
     M, N, G, n = w.M, w.N, w.nchol, w.taylor_order
-    return {"overlap": 8 * (M - N) * N * N + 8 * N ** 3, "qr": 8 * M * N * N,
+    return {"overlap": 8 * N ** 3, "theta": 8 * (M - N) * N * N, "qr": 8 * M * N * N,
             "v_assembly": 2 * G * M * (M + 1), "taylor": 8 * n * M * M * N,
             "energy": 4 * G * N * M + 4 * G * N * N * M}
 
 
 KERNEL_OF_PHASE = {"overlap": ("k_overlap", "alu", "walker_f64.cu"),
+                   "theta": ("k_theta_rows", "alu", "walker_f64.cu"),
                    "qr": ("k_mgs", "alu", "walker_f64.cu"),
                    "v_assembly": ("tcgen05 V contraction (EpiV)", "tensor", "gemm_tc.cu"),
                    "taylor": ("k_taylor_series", "tensor", "taylor_tc.cu"),
@@ -300,9 +308,10 @@ def run_gpu(args, w: workloads.Workload):
 
     # the same K steps again, launched one by one with CUDA events around
     # every phase on the state's stream: phase times and the dominant kernel
-    ph_ms = (ctypes.c_double * 10)()
-    ph_n = (ctypes.c_int64 * 10)()
-    ph_k = (ctypes.c_int64 * 10)()
+    nph = len(PHASES)
+    ph_ms = (ctypes.c_double * nph)()
+    ph_n = (ctypes.c_int64 * nph)()
+    ph_k = (ctypes.c_int64 * nph)()
     pkg._check(lib.afqmc_profile_start(run.s, K))
     p0 = torch.cuda.Event(enable_timing=True)
     p1 = torch.cuda.Event(enable_timing=True)
@@ -338,7 +347,7 @@ def run_gpu(args, w: workloads.Workload):
         run2.close()
 
     phases = {PHASES[i]: {"ms": ph_ms[i], "count": int(ph_n[i]), "kernels": int(ph_k[i])}
-              for i in range(10)}
+              for i in range(len(PHASES))}
     prec_rep = None
     if prec != 0 and rank == 0 and not args.no_precision_report:
         prec_rep = precision_report(w, prec, h1, L, C, H0)

@@ -243,11 +243,12 @@ AFQMC_API int afqmc_destroy(afqmc_state* s);
  *   V           sum_g x_g L_g contraction (A(x) of Sec. 3.4.2)
  *   BHALF       the two exp(-dt v0'/2) products (Eq. primitive)
  *   TAYLOR      the truncated exp(V) series
- *   OVERLAP     S = V_T^T Phi, LU, log det, Theta (Theorem 1.1)
+ *   OVERLAP     S = V_T^T Phi, its inverse and log det (Theorem 1.1)
  *   WEIGHT      overlap ratio, phaseless / free weight update
- *   QR          modified Gram-Schmidt and the overlap after it
+ *   QR          modified Gram-Schmidt (and the log det update it implies)
  *   COMB        population control
  *   ENERGY      local energies (exchange contraction) and the estimator
+ *   THETA       Theta = Phi S^-1 (Eq. precomputing), after OVERLAP
  */
 enum {
   AFQMC_PH_FORCE_BIAS = 0,
@@ -260,6 +261,7 @@ enum {
   AFQMC_PH_QR,
   AFQMC_PH_COMB,
   AFQMC_PH_ENERGY,
+  AFQMC_PH_THETA,
   AFQMC_NPHASE
 };
 

@@ -187,7 +187,7 @@ static int all_finite(const double* v, size_t n, const char* what) {
 }
 
 // ------------------------------------------------------------ step pieces ---
-int overlap_update(afqmc_state* s, bool into_ld) {
+int overlap_update(afqmc_state* s, bool into_ld, bool timed) {
   const afqmc_params& p = s->p;
   const Bufs& b = s->b;
   // S = V_T^T Phi, S^-1, log det and Theta in one float64 kernel per walker
@@ -199,7 +199,14 @@ int overlap_update(afqmc_state* s, bool into_ld) {
     ov.lo_kind = b.lo_kind;
     ov.Mp = b.Mp;
   }
+  if (timed) prof_begin(s, AFQMC_PH_OVERLAP);
   AFQ_TRY(launch_overlap(ov, s->st));
+  if (timed) {
+    prof_end(s);
+    prof_begin(s, AFQMC_PH_THETA);
+  }
+  AFQ_TRY(launch_theta(ov, s->st));
+  if (timed) prof_end(s);
   return AFQMC_OK;
 }
 
@@ -426,9 +433,7 @@ static int step_once(afqmc_state* s) {
   // exp(-dt v0'/2) applied to every walker's orbitals
   AFQ_TRY(b.mixed ? propagate_mixed(s) : propagate_f64(s));
   // new overlap, log det, Theta; then the weights (and step += 1)
-  prof_begin(s, AFQMC_PH_OVERLAP);
-  AFQ_TRY(overlap_update(s, false));
-  prof_end(s);
+  AFQ_TRY(overlap_update(s, false, true));
   WeightArgs wa{W, p.mode, p.dt, s->sdt, s->H0p, s->e_shift, s->wmax, b.ld_new, b.ld, b.scal,
                 b.wt, b.counters + CTR_NONFINITE,
                 reinterpret_cast<int64_t*>(b.counters + CTR_STEP)};
@@ -709,7 +714,7 @@ static int setup_device(afqmc_state* s, const double* h1, const double* L, const
   }
   // walkers at the trial, their overlaps, and the trial energy
   AFQ_TRY(launch_init_walkers(b.VTt, b.phiT, b.wt, W, N, M, st));
-  AFQ_TRY(overlap_update(s, true));
+  AFQ_TRY(overlap_update(s, true, false));
   s->t_fresh = false;
   s->elo = -INFINITY;
   s->ehi = INFINITY;
@@ -1006,7 +1011,7 @@ int afqmc_set_walkers(afqmc_state* s, const double* phi, const double* weight) {
   g.ldc = (long)M;
   AFQ_TRY(gemm_nt_f64(g, s->st));
   AFQ_CUDA(cudaMemcpyAsync(s->b.wt, weight, sizeof(double) * 2 * W, cudaMemcpyHostToDevice, s->st));
-  AFQ_TRY(overlap_update(s, true));
+  AFQ_TRY(overlap_update(s, true, false));
   s->t_fresh = false;
   AFQ_CUDA(cudaStreamSynchronize(s->st));
   return AFQMC_OK;

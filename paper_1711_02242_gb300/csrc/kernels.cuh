@@ -93,7 +93,9 @@ struct OverlapArgs {
   int unit_trial = 0;  // VTt = [I_N | 0]: S is the top block of Phi, Theta's top rows I
   double2* Sinv = nullptr;  // [W][N][N] scratch: S^-1 of live walkers
 };
+// S^-1 and log det (k_overlap), then Theta (k_theta_rows)
 int launch_overlap(const OverlapArgs& a, cudaStream_t st);
+int launch_theta(const OverlapArgs& a, cudaStream_t st);
 
 struct WeightArgs {
   int W, mode;

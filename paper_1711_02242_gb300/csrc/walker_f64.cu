@@ -515,6 +515,10 @@ int launch_overlap(const OverlapArgs& a, cudaStream_t st) {
     attr = true;
   }
   AFQ_LAUNCH(k_overlap, a.W, OV_T, smem, st, a);
+  return AFQMC_OK;
+}
+
+int launch_theta(const OverlapArgs& a, cudaStream_t st) {
   int ib = 8;
   while (a.N % ib) --ib;
   switch (ib) {

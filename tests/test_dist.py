@@ -71,7 +71,8 @@ def test_rooflines_from_phase_times():
     assert [r["phase"] for r in roofs] == ["overlap", "taylor", "qr"]
     ov = roofs[0]
     per = bench.algorithmic_per_walker(w)["overlap"]
-    assert per == 8 * (300 - 25) * 25 * 25 + 8 * 25 ** 3
+    assert per == 8 * 25 ** 3
+    assert bench.algorithmic_per_walker(w)["theta"] == 8 * (300 - 25) * 25 * 25
     assert abs(ov["achieved"] - per * 512 / 1.3e-3 / 1e12) < 1e-12
     assert ov["bound"] == "alu" and abs(ov["frac"] - ov["achieved"] / bench.FP64_PEAK_TFLOPS) < 1e-12
     assert roofs[1]["bound"] == "tensor" and roofs[1]["traffic"] is None
