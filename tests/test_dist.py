@@ -75,13 +75,15 @@ def test_rooflines_from_phase_times():
     assert bench.algorithmic_per_walker(w)["theta"] == 8 * (300 - 25) * 25 * 25
     assert abs(ov["achieved"] - per * 512 / 1.3e-3 / 1e12) < 1e-12
     assert ov["bound"] == "alu" and abs(ov["frac"] - ov["achieved"] / bench.FP64_PEAK_TFLOPS) < 1e-12
-    assert roofs[1]["bound"] == "tensor" and roofs[1]["traffic"] is None
+    assert roofs[1]["bound"] == "tensor"
     assert abs(sum(r["share_of_step"] for r in roofs) - 1.0) < 1e-12
     # a recorded traffic figure counts only for the source it was taken from
-    bench.TRAFFIC["overlap"] = {"bytes": 1.0e8, "sha": bench.source_sha("walker_f64.cu")}
+    saved = dict(bench.TRAFFIC)
     try:
+        bench.TRAFFIC["overlap"] = {"bytes": 1.0e8, "sha": bench.source_sha("walker_f64.cu")}
         assert bench.rooflines(w, ph, "bf16", K)[0]["traffic"] == 1.0e8
-        bench.TRAFFIC["overlap"]["sha"] = "0" * 64
+        bench.TRAFFIC["overlap"] = {"bytes": 1.0e8, "sha": "0" * 64}
         assert bench.rooflines(w, ph, "bf16", K)[0]["traffic"] is None
     finally:
-        bench.TRAFFIC.pop("overlap")
+        bench.TRAFFIC.clear()
+        bench.TRAFFIC.update(saved)
