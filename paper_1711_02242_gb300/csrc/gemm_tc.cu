@@ -358,8 +358,9 @@ struct EpiProp0 {
   long ldacc;
   void* tb;
   int lo_kind, N, M, Mp, rows;
+  int bn;  // tile width (the kernel's BN)
   __device__ __forceinline__ int m_origin(int bx, int) const { return bx * BM; }
-  __device__ __forceinline__ int n_origin(int, int by) const { return by * 256; }
+  __device__ __forceinline__ int n_origin(int, int by) const { return by * bn; }
   template <int BN>
   __device__ __forceinline__ void run(uint32_t tmem, int q, int lane, int, int, int, int m0, int n0,
                                       int, int, float*) const {
@@ -510,8 +511,9 @@ struct EpiPhi {
   double* phiT;
   const double* wt;
   int N, M, rows;
+  int bn;  // tile width (the kernel's BN)
   __device__ __forceinline__ int m_origin(int bx, int) const { return bx * BM; }
-  __device__ __forceinline__ int n_origin(int, int by) const { return by * 256; }
+  __device__ __forceinline__ int n_origin(int, int by) const { return by * bn; }
   template <int BN>
   __device__ __forceinline__ void run(uint32_t tmem, int q, int lane, int, int, int, int m0, int n0,
                                       int, int, float*) const {
@@ -522,10 +524,16 @@ struct EpiPhi {
       float v[16];
       tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c0, v);
       if (!ok) continue;
+      const int pb = n0 + c0;
+      double* o = phiT + (long)row * M + pb;
+      if (pb + 16 <= M && (((long)row * M + pb) & 1) == 0) {
 #pragma unroll
-      for (int u = 0; u < 16; ++u) {
-        const int p = n0 + c0 + u;
-        if (p < M) phiT[(long)row * M + p] = (double)v[u];
+        for (int u = 0; u < 16; u += 2)
+          *reinterpret_cast<double2*>(o + u) = make_double2((double)v[u], (double)v[u + 1]);
+      } else {
+#pragma unroll
+        for (int u = 0; u < 16; ++u)
+          if (pb + u < M) o[u] = (double)v[u];
       }
     }
   }
@@ -768,10 +776,21 @@ int tc_tune_store(const TcGemm& g, float* C, long ldc, float alpha, cudaStream_t
   return AFQMC_OK;
 }
 
+// Tile width for an output of n columns: 160 or 256, whichever pads less.
+static int half_step_bn(int n) {
+  const int pad160 = cdiv(n, 160) * 160 - n, pad256 = cdiv(n, 256) * 256 - n;
+  return pad160 < pad256 ? 160 : 256;
+}
+
 int tc_prop_first(const TcGemm& g, float* acc, long ldacc, void* tb, int lo_kind, int N, int M,
                   int Mp, cudaStream_t st) {
-  tc::EpiProp0 e{acc, ldacc, tb, lo_kind, N, M, Mp, g.m};
-  const int gx = cdiv(g.m, tc::BM), gy = cdiv(M, 256);
+  const int bn = half_step_bn(M);
+  tc::EpiProp0 e{acc, ldacc, tb, lo_kind, N, M, Mp, g.m, bn};
+  const int gx = cdiv(g.m, tc::BM), gy = cdiv(M, bn);
+  if (bn == 160) {
+    if (g.tf32) return launch_tc_persistent<160, 6, true>(g, e, gx, gy, st);
+    return launch_tc_persistent<160, 6, false>(g, e, gx, gy, st);
+  }
   if (g.tf32) return launch_tc_persistent<256, 4, true>(g, e, gx, gy, st);
   return launch_tc_persistent<256, 4, false>(g, e, gx, gy, st);
 }
@@ -806,8 +825,13 @@ int tc_v_full(const TcGemm& g, void* V, int lo_kind, int W, int M, int Mp, doubl
 
 int tc_prop_last(const TcGemm& g, double* phiT, const double* wt, int N, int M,
                  cudaStream_t st) {
-  tc::EpiPhi e{phiT, wt, N, M, g.m};
-  const int gx = cdiv(g.m, tc::BM), gy = cdiv(M, 256);
+  const int bn = half_step_bn(M);
+  tc::EpiPhi e{phiT, wt, N, M, g.m, bn};
+  const int gx = cdiv(g.m, tc::BM), gy = cdiv(M, bn);
+  if (bn == 160) {
+    if (g.tf32) return launch_tc_persistent<160, 6, true>(g, e, gx, gy, st);
+    return launch_tc_persistent<160, 6, false>(g, e, gx, gy, st);
+  }
   if (g.tf32) return launch_tc_persistent<256, 4, true>(g, e, gx, gy, st);
   return launch_tc_persistent<256, 4, false>(g, e, gx, gy, st);
 }
