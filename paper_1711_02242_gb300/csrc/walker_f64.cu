@@ -503,7 +503,9 @@ static int launch_theta_rows(const OverlapArgs& a, cudaStream_t st) {
 }
 
 int launch_overlap(const OverlapArgs& a, cudaStream_t st) {
-  const size_t smem = 2ull * a.N * a.N * sizeof(double2) + 3ull * a.N * (OV_P + 1) * sizeof(double);
+  // the S tiles are only staged when V_T is a general matrix
+  const size_t smem = 2ull * a.N * a.N * sizeof(double2) +
+                      (a.unit_trial ? 0ull : 3ull * a.N * (OV_P + 1) * sizeof(double));
   if (smem > 200 * 1024) {
     set_error("overlap: N=%d too large", a.N);
     return AFQMC_EUNSUPPORTED;
@@ -583,7 +585,7 @@ int launch_weight(const WeightArgs& a, cudaStream_t st) {
 // the finished columns one projection at a time (each projection uses the
 // partially updated vector), then normalised.  The projections are applied
 // as soon as a column is finished ("right-looking"): once q_k is normalised,
-// every later column j takes v_j -= <q_k|v_j> q_k, one warp per column, so
+// every later column j takes v_j -= <q_k|v_j> q_k, 8 lanes per column, so
 // column j sees exactly the projections q_0, q_1, ... in order, as in the
 // column-by-column form, with two block barriers per k instead of two block
 // reductions per (j, k) pair.
@@ -623,25 +625,35 @@ __global__ void __launch_bounds__(256) k_mgs(MgsArgs a) {
       q_sm[p] = make_double2(qr, qi);
     }
     __syncthreads();
-    for (int j = k + 1 + warp; j < N; j += nwarp) {
-      double* ur = re + (long)j * M;
-      double* ui = im + (long)j * M;
-      // <q_k|v_j> and v_j -= <q_k|v_j> q_k as chains of FMAs (the FP64 pipe
-      // is the bound: no separate multiplies or adds)
+    // one group of 8 lanes per later column (4 columns per warp): the dot
+    // product is reduced over 8 lanes (3 shuffle levels) instead of 32, which
+    // keeps the FP64 pipe - the bound of this kernel - on the projections
+    const int grp = lane >> 3, gl = lane & 7, ngrp = 4 * nwarp;
+    for (int j0 = k + 1; j0 < N; j0 += ngrp) {
+      const int j = j0 + 4 * warp + grp;
+      const bool act = j < N;
+      double* ur = re + (long)(act ? j : k) * M;
+      double* ui = im + (long)(act ? j : k) * M;
+      // <q_k|v_j> and v_j -= <q_k|v_j> q_k as chains of FMAs
       double sr = 0.0, si = 0.0;
-      for (int p = lane; p < M; p += 32) {
-        const double2 q = q_sm[p];
-        const double a_ = ur[p], b_ = ui[p];
-        sr = fma(q.x, a_, fma(q.y, b_, sr));
-        si = fma(q.x, b_, fma(-q.y, a_, si));
+      if (act)
+        for (int p = gl; p < M; p += 8) {
+          const double2 q = q_sm[p];
+          const double a_ = ur[p], b_ = ui[p];
+          sr = fma(q.x, a_, fma(q.y, b_, sr));
+          si = fma(q.x, b_, fma(-q.y, a_, si));
+        }
+#pragma unroll
+      for (int o = 4; o > 0; o >>= 1) {
+        sr += __shfl_xor_sync(0xffffffffu, sr, o);
+        si += __shfl_xor_sync(0xffffffffu, si, o);
       }
-      sr = warp_sum(sr);
-      si = warp_sum(si);
-      for (int p = lane; p < M; p += 32) {
-        const double2 q = q_sm[p];
-        ur[p] = fma(-sr, q.x, fma(si, q.y, ur[p]));
-        ui[p] = fma(-sr, q.y, fma(-si, q.x, ui[p]));
-      }
+      if (act)
+        for (int p = gl; p < M; p += 8) {
+          const double2 q = q_sm[p];
+          ur[p] = fma(-sr, q.x, fma(si, q.y, ur[p]));
+          ui[p] = fma(-sr, q.y, fma(-si, q.x, ui[p]));
+        }
     }
     __syncthreads();
   }
