@@ -229,9 +229,9 @@ struct EpiStore {
 // (RG*N <= 128 rows) and CW whole walkers; the B tile is one 3-D TMA box of
 // CW walkers x NPAD rows (the 2N rows of a walker, zero-padded to a power of
 // two), so walker wl of the tile owns accumulator columns [wl NPAD, wl NPAD +
-// 2N).  The accumulator is copied to this epilogue's own shared memory, all
-// 256 columns at once (NPART = 1) or in two halves of whole walkers
-// (NPART = 2, half the shared memory, so the operand ring can be deeper); the
+// 2N).  The accumulator is copied to this epilogue's own shared memory in
+// NPART parts of whole walkers (two halves: half the shared memory of the
+// whole tile, so the operand ring can be three deep); the
 // thread of row (g, i) forms e_i = sum_j T_ij T_ji (complex) from its own row
 // and column i of the block, the N values of a vector are summed, and
 // part[w][g][2] receives one partial per (g, w) (nchunk = G), summed later in
@@ -857,7 +857,7 @@ void exchange_tile(int N, int* RG, int* CW, int* NPAD) {
 int tc_exchange(const TcGemm& g, int G, int W, int N, double* part, int nchunk, cudaStream_t st) {
   int RG, CW, NPAD;
   exchange_tile(N, &RG, &CW, &NPAD);
-  if (RG < 1 || CW < 1 || CW > tc::EpiExchangeT<1>::kMaxCW || nchunk != G) {
+  if (RG < 1 || CW < 2 || CW > tc::EpiExchangeT<2>::kMaxCW || NPAD > 128 || nchunk != G) {
     set_error("tc exchange: N=%d not supported", N);
     return AFQMC_EUNSUPPORTED;
   }
@@ -865,18 +865,11 @@ int tc_exchange(const TcGemm& g, int G, int W, int N, double* part, int nchunk, 
   const int eb = g.tf32 ? 4 : 2;
   CUtensorMap tb;
   AFQ_TRY(make_tmap_3d(&tb, g.B, eb, W, 2L * N, g.k, g.ldb, 2L * N * g.ldb, NPAD, CW));
-  if (NPAD <= 128) {
-    // two staged halves (66 KB) leave room for a 3-deep operand ring
-    tc::EpiExchangeT<2> e{part, G, W, N, RG, CW, NPAD, nchunk};
-    if (g.tf32)
-      return launch_tc_persistent<256, 3, true>(g, e, cdiv(G, RG), cdiv(W, CW), st, &tb);
-    return launch_tc_persistent<256, 3, false>(g, e, cdiv(G, RG), cdiv(W, CW), st, &tb);
-  }
-  // one walker per tile: the whole 128 KB tile staged, a 2-deep ring
-  tc::EpiExchangeT<1> e{part, G, W, N, RG, CW, NPAD, nchunk};
+  // two staged halves (66 KB) leave room for a 3-deep operand ring
+  tc::EpiExchangeT<2> e{part, G, W, N, RG, CW, NPAD, nchunk};
   if (g.tf32)
-    return launch_tc_persistent<256, 2, true>(g, e, cdiv(G, RG), cdiv(W, CW), st, &tb);
-  return launch_tc_persistent<256, 2, false>(g, e, cdiv(G, RG), cdiv(W, CW), st, &tb);
+    return launch_tc_persistent<256, 3, true>(g, e, cdiv(G, RG), cdiv(W, CW), st, &tb);
+  return launch_tc_persistent<256, 3, false>(g, e, cdiv(G, RG), cdiv(W, CW), st, &tb);
 }
 
 }  // namespace afq

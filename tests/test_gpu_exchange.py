@@ -16,8 +16,8 @@ E_loc by the spread of the exchange energies across walkers, above that
 bound on every shape (checked).  How far the rounded operands themselves move
 the energy (the mixed path's bias) is reported by the benchmark, not bounded
 here.  Shapes cover every column padding of the exchange tile (2N padded to
-16, 32, 64, 128, 256: 16, 8, 4, 2, 1 walkers per tile), a single electron
-pair, ragged vector and walker counts, and N = 64 and 66.
+16, 32, 64, 128: 16, 8, 4, 2 walkers per tile), a single electron pair,
+ragged vector and walker counts, and N = 64 (the largest N a state takes).
 """
 import numpy as np
 import pytest
@@ -103,7 +103,6 @@ SHAPES = [  # M, N, nchol, nwalkers
     (40, 16, 80, 40),
     (80, 33, 100, 20),
     (140, 64, 60, 9),
-    (150, 66, 40, 7),   # 2N padded to 256: one walker per tile, the whole tile staged
 ]
 
 
