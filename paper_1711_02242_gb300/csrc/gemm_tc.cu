@@ -229,17 +229,13 @@ struct EpiStore {
 // (RG*N <= 128 rows) and CW whole walkers; the B tile is one 3-D TMA box of
 // CW walkers x NPAD rows (the 2N rows of a walker, zero-padded to a power of
 // two), so walker wl of the tile owns accumulator columns [wl NPAD, wl NPAD +
-// 2N).  The accumulator is copied to this epilogue's own shared memory in
-// NPART parts of whole walkers (two halves: half the shared memory of the
-// whole tile, so the operand ring can be three deep); the
-// thread of row (g, i) forms e_i = sum_j T_ij T_ji (complex) from its own row
-// and column i of the block, the N values of a vector are summed, and
+// 2N).  The accumulator is copied to this epilogue's own shared memory; the
+// thread of row (g, i) then forms e_i = sum_j T_ij T_ji (complex) from its own
+// row and column i of the block, the N values of a vector are summed, and
 // part[w][g][2] receives one partial per (g, w) (nchunk = G), summed later in
 // a fixed order.  T never reaches global memory.
-template <int NPART>
-struct EpiExchangeT {
-  static constexpr int kCols = 256 / NPART;  // accumulator columns staged at a time
-  static constexpr int kSmemBytes = 128 * (kCols + 1) * 4;
+struct EpiExchange {
+  static constexpr int kSmemBytes = 128 * 257 * 4;  // one 128 x 256 FP32 tile
   static constexpr bool kB3D = true;
   static constexpr int kWarps = 8;  // two per TMEM lane quarter, splitting columns / walkers
   static constexpr int kMaxCW = 16;
@@ -251,70 +247,65 @@ struct EpiExchangeT {
   template <int BN>
   __device__ __forceinline__ void run(uint32_t tmem, int q, int lane, int ew, int bx, int by, int,
                                       int, int, int, float* sm) const {
-    static_assert(BN == 256, "exchange tile");
-    constexpr int LD = kCols + 1;  // odd pitch: row and column walks are conflict-free
+    constexpr int LD = BN + 1;  // odd pitch: row and column walks are conflict-free
     const int r = 32 * q + lane, half = ew >> 2;
+#pragma unroll 1
+    for (int c0 = 16 * half; c0 < BN; c0 += 32) {
+      float v[16];
+      tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c0, v);
+#pragma unroll
+      for (int i = 0; i < 16; ++i) sm[r * LD + c0 + i] = v[i];
+    }
+    asm volatile("bar.sync 1, 256;" ::: "memory");
     const int gl = r / N, i = r - gl * N;
     const bool rv = gl < RG;
-    const int cwp = CW / NPART;  // walkers per staged part
-    const int g0 = bx * RG;
-    for (int pt = 0; pt < NPART; ++pt) {
-#pragma unroll 1
-      for (int c0 = 16 * half; c0 < kCols; c0 += 32) {
-        float v[16];
-        tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(pt * kCols + c0), v);
+    // FP32 sums (the products come from FP32 accumulators; GB300's float64
+    // pipe is ~60x slower than FP32 and would dominate the kernel); the two
+    // warps of a row take alternate walkers
+    float e[kMaxCW];
 #pragma unroll
-        for (int u = 0; u < 16; ++u) sm[r * LD + c0 + u] = v[u];
-      }
-      asm volatile("bar.sync 1, 256;" ::: "memory");
-      // FP32 sums (the products come from FP32 accumulators; GB300's float64
-      // pipe is ~60x slower than FP32 and would dominate the kernel); the two
-      // warps of a row take alternate walkers
-      float e[kMaxCW];
-#pragma unroll
-      for (int h = 0; h < kMaxCW / 2; ++h) {
-        const int wl = 2 * h + half;
-        float er = 0.f, ei = 0.f;
-        if (wl < cwp && rv) {
-          const float* own = sm + r * LD + wl * NPAD;            // T_ij: [j], [N + j]
-          const float* col = sm + (gl * N) * LD + wl * NPAD + i;  // T_ji: [j LD], [j LD + N]
+    for (int h = 0; h < kMaxCW / 2; ++h) {
+      const int wl = 2 * h + half;
+      float er = 0.f, ei = 0.f;
+      if (wl < CW && rv) {
+        const float* own = sm + r * LD + wl * NPAD;            // T_ij: [j], [N + j]
+        const float* col = sm + (gl * N) * LD + wl * NPAD + i;  // T_ji: [j LD], [j LD + N]
 #pragma unroll 4
-          for (int j = 0; j < N; ++j) {
-            const float ar = own[j], ai = own[N + j];
-            const float br = col[j * LD], bi = col[j * LD + N];
-            er = fmaf(ar, br, fmaf(-ai, bi, er));
-            ei = fmaf(ar, bi, fmaf(ai, br, ei));
-          }
-        }
-        e[2 * h] = er;
-        e[2 * h + 1] = ei;
-      }
-      asm volatile("bar.sync 1, 256;" ::: "memory");  // every read of the tile is done
-#pragma unroll
-      for (int h = 0; h < kMaxCW / 2; ++h) {
-        const int wl = 2 * h + half;
-        if (wl < cwp) {
-          sm[r * LD + 2 * wl] = e[2 * h];
-          sm[r * LD + 2 * wl + 1] = e[2 * h + 1];
+        for (int j = 0; j < N; ++j) {
+          const float ar = own[j], ai = own[N + j];
+          const float br = col[j * LD], bi = col[j * LD + N];
+          er = fmaf(ar, br, fmaf(-ai, bi, er));
+          ei = fmaf(ar, bi, fmaf(ai, br, ei));
         }
       }
-      asm volatile("bar.sync 1, 256;" ::: "memory");
-      const int w0 = by * CW + pt * cwp;
-      for (int item = r + 128 * half; item < RG * cwp; item += 256) {
-        const int g = item / cwp, wl = item - g * cwp;
-        if (g0 + g >= G || w0 + wl >= W) continue;
-        float sr = 0.f, si = 0.f;
-        for (int i2 = 0; i2 < N; ++i2) {
-          sr += sm[(g * N + i2) * LD + 2 * wl];
-          si += sm[(g * N + i2) * LD + 2 * wl + 1];
-        }
-        double* o = part + ((long)(w0 + wl) * nchunk + g0 + g) * 2;
-        o[0] = (double)sr;
-        o[1] = (double)si;
-      }
-      // the next copy into sm must wait until every warp is done reading
-      asm volatile("bar.sync 1, 256;" ::: "memory");
+      e[2 * h] = er;
+      e[2 * h + 1] = ei;
     }
+    asm volatile("bar.sync 1, 256;" ::: "memory");  // every read of the tile is done
+#pragma unroll
+    for (int h = 0; h < kMaxCW / 2; ++h) {
+      const int wl = 2 * h + half;
+      if (wl < CW) {
+        sm[r * LD + 2 * wl] = e[2 * h];
+        sm[r * LD + 2 * wl + 1] = e[2 * h + 1];
+      }
+    }
+    asm volatile("bar.sync 1, 256;" ::: "memory");
+    const int g0 = bx * RG, w0 = by * CW;
+    for (int item = r + 128 * half; item < RG * CW; item += 256) {
+      const int g = item / CW, wl = item - g * CW;
+      if (g0 + g >= G || w0 + wl >= W) continue;
+      float sr = 0.f, si = 0.f;
+      for (int i2 = 0; i2 < N; ++i2) {
+        sr += sm[(g * N + i2) * LD + 2 * wl];
+        si += sm[(g * N + i2) * LD + 2 * wl + 1];
+      }
+      double* o = part + ((long)(w0 + wl) * nchunk + g0 + g) * 2;
+      o[0] = (double)sr;
+      o[1] = (double)si;
+    }
+    // the next tile's copy into sm must wait until every warp is done reading
+    asm volatile("bar.sync 1, 256;" ::: "memory");
   }
 };
 
@@ -857,7 +848,7 @@ void exchange_tile(int N, int* RG, int* CW, int* NPAD) {
 int tc_exchange(const TcGemm& g, int G, int W, int N, double* part, int nchunk, cudaStream_t st) {
   int RG, CW, NPAD;
   exchange_tile(N, &RG, &CW, &NPAD);
-  if (RG < 1 || CW < 2 || CW > tc::EpiExchangeT<2>::kMaxCW || NPAD > 128 || nchunk != G) {
+  if (RG < 1 || CW < 1 || CW > tc::EpiExchange::kMaxCW || nchunk != G) {
     set_error("tc exchange: N=%d not supported", N);
     return AFQMC_EUNSUPPORTED;
   }
@@ -865,11 +856,12 @@ int tc_exchange(const TcGemm& g, int G, int W, int N, double* part, int nchunk, 
   const int eb = g.tf32 ? 4 : 2;
   CUtensorMap tb;
   AFQ_TRY(make_tmap_3d(&tb, g.B, eb, W, 2L * N, g.k, g.ldb, 2L * N * g.ldb, NPAD, CW));
-  // two staged halves (66 KB) leave room for a 3-deep operand ring
-  tc::EpiExchangeT<2> e{part, G, W, N, RG, CW, NPAD, nchunk};
+  tc::EpiExchange e{part, G, W, N, RG, CW, NPAD, nchunk};
+  // K = M is a few k-blocks of L2-resident operands: a 2-deep ring leaves room
+  // for the epilogue's own 128 KB tile buffer
   if (g.tf32)
-    return launch_tc_persistent<256, 3, true>(g, e, cdiv(G, RG), cdiv(W, CW), st, &tb);
-  return launch_tc_persistent<256, 3, false>(g, e, cdiv(G, RG), cdiv(W, CW), st, &tb);
+    return launch_tc_persistent<256, 2, true>(g, e, cdiv(G, RG), cdiv(W, CW), st, &tb);
+  return launch_tc_persistent<256, 2, false>(g, e, cdiv(G, RG), cdiv(W, CW), st, &tb);
 }
 
 }  // namespace afq
