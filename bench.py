@@ -465,8 +465,13 @@ def cpu_sample(w: workloads.Workload, n_walkers=32, n_steps=3):
     cores = len(os.sched_getaffinity(0))
     return dict(value=n_walkers * n_steps / dt, unit="walker-steps/s", cores=cores, kind="oracle",
                 sample=f"{n_steps} full steps of {n_walkers} of the {w.nwalkers} walkers of the "
-                       f"M=300 workload (set-up untimed), numpy float64, {cores} host threads",
+                       f"M={w.M} workload (set-up untimed), numpy float64, {cores} host threads",
                 seconds=dt)
+
+
+def workload_desc(w: workloads.Workload) -> str:
+    return (f"M={w.M} N_up=N_dn={w.N} nchol={w.nchol} walkers={w.nwalkers} dt={w.dt} "
+            f"qr/{w.qr_period} energy/{w.energy_period} taylor {w.taylor_order}")
 
 
 def run_reference(args, w):
@@ -481,12 +486,12 @@ def run_reference(args, w):
     cores = len(os.sched_getaffinity(0))
     val = sample * args.steps / dt
     line = {
-        "impl": "reference", "metric": "walker-steps/s at M=300", "value": val,
+        "impl": "reference", "metric": f"walker-steps/s at M={w.M}", "value": val,
         "unit": "walker-steps/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "M=300 N=25 nchol=1800 512 walkers dt=0.005 (oracle sample)",
-                   "sampled_walkers": sample},
+        "config": {"workload": workload_desc(w), "sampled_walkers": sample,
+                   "note": "the float64 oracle on the host cores, a bounded sample of the walkers"},
         "cpu_baseline": {"value": val, "unit": "walker-steps/s", "cores": cores, "kind": "oracle",
                          "sample": f"{sample} walkers x {args.steps} steps per run"},
         "e2e": {"value": val, "unit": "walker-steps/s", "h2d_bytes_per_step": 0,
@@ -701,13 +706,12 @@ def main():
     roof.update(kernel=top["kernel"], peak_source=top["peak_source"],
                 ms_per_launch=top["ms_per_launch"])
     line = {
-        "metric": "walker-steps/s at M=300", "value": value, "unit": "walker-steps/s",
+        "metric": f"walker-steps/s at M={w.M}", "value": value, "unit": "walker-steps/s",
         "n_gpus": N, "steps": K, "warmup": r["warmup"], "ms_per_step": ms_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp64": "f64", "tf32": "tf32/f32/f64", "bf16": "bf16/f32/f64"}[args.precision],
         "data": "synthetic",
-        "config": {"workload": f"M={w.M} N_up=N_dn={w.N} nchol={w.nchol} walkers={w.nwalkers} "
-                               f"dt={w.dt} qr/{w.qr_period} energy/{w.energy_period} taylor {w.taylor_order}",
+        "config": {"workload": workload_desc(w),
                    "precision": args.precision, "l2": "inputs larger than L2 (packed L "
                    f"{w.M * (w.M + 1) // 2 * w.nchol * 8 / 1e6:.0f} MB float64)",
                    "trial": f"RHF (25 iterations, converged={r['trial_converged']}, "
