@@ -28,9 +28,9 @@ namespace afq {
 namespace tc {
 
 
-template <int BN, int STAGES>
+template <int BN, int STAGES, int MT = 1>
 struct Smem {
-  static constexpr int A_BYTES = BM * BKB;
+  static constexpr int A_BYTES = MT * BM * BKB;  // MT 128-row A tiles per stage
   static constexpr int B_BYTES = BN * BKB;
   static constexpr int STAGE = A_BYTES + B_BYTES;
   static constexpr int RING = STAGES * STAGE;
@@ -55,13 +55,17 @@ __device__ __forceinline__ bool epi_bar_or(bool flag) {
 // (bx, by) = (t % gx, t / gx), so CTAs running together share B tiles in L2).
 // Two TMEM accumulators of BN columns: the epilogue warps drain tile j while
 // the MMA thread fills tile j + 1 (tfull / tempty mbarriers per accumulator).
+// With Epi::kMT = 2 a tile is 256 rows: one 256-row A box per stage feeds two
+// M=128 MMAs against the same B tile (half the B traffic per output), and when
+// two such tiles do not fit in tensor memory a single accumulator is used.
 template <int BN, int STAGES, bool TF32, class Epi>
 __global__ void __launch_bounds__(64 + 32 * Epi::kWarps, 1)
     k_tc_gemm_persistent(const __grid_constant__ CUtensorMap tmA,
                          const __grid_constant__ CUtensorMap tmB, int M, int N, int K, int gx,
                          int ntiles, Epi epi, int* err) {
   extern __shared__ uint8_t smem_raw[];
-  using S = Smem<BN, STAGES>;
+  constexpr int MT = Epi::kMT;
+  using S = Smem<BN, STAGES, MT>;
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + S::RING);
   uint64_t* empty = full + STAGES;
@@ -88,10 +92,12 @@ __global__ void __launch_bounds__(64 + 32 * Epi::kWarps, 1)
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  // TMEM columns: a power of two holding two accumulators of BN columns
-  constexpr uint32_t TCOLS = (2 * BN <= 64) ? 64 : (2 * BN <= 128) ? 128 : (2 * BN <= 256) ? 256 : 512;
-  constexpr uint32_t ASTRIDE = TCOLS / 2;
-  static_assert(BN <= (int)ASTRIDE, "accumulator stride");
+  // TMEM columns: a power of two holding NBUF accumulators of MT x BN columns
+  constexpr int NBUF = (2 * MT * BN <= 512) ? 2 : 1;
+  constexpr int NEED = NBUF * MT * BN;
+  constexpr uint32_t TCOLS = (NEED <= 64) ? 64 : (NEED <= 128) ? 128 : (NEED <= 256) ? 256 : 512;
+  constexpr uint32_t ASTRIDE = TCOLS / NBUF;
+  static_assert(MT * BN <= (int)ASTRIDE && NEED <= 512, "accumulator stride");
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(tmem_slot)),
@@ -127,8 +133,8 @@ __global__ void __launch_bounds__(64 + 32 * Epi::kWarps, 1)
     constexpr uint32_t idesc = instr_desc(TF32 ? 2u : 1u, (uint32_t)BN);
     int it = 0, j = 0;
     for (int t = blockIdx.x; t < ntiles && !*(volatile int*)abort_flag; t += gridDim.x, ++j) {
-      const int acc = j & 1;
-      if (j >= 2 && !mbar_wait(&tempty[acc], ((j / 2) - 1) & 1, err, 12)) {
+      const int acc = NBUF == 2 ? (j & 1) : 0;
+      if (j >= NBUF && !mbar_wait(&tempty[acc], ((j / NBUF) - 1) & 1, err, 12)) {
         *(volatile int*)abort_flag = 1;
         break;
       }
@@ -146,8 +152,10 @@ __global__ void __launch_bounds__(64 + 32 * Epi::kWarps, 1)
         const uint32_t b = a + S::A_BYTES;
 #pragma unroll
         for (int k = 0; k < KSTEPS; ++k)
-          mma<TF32>(d, sw128_desc(a + 32 * k), sw128_desc(b + 32 * k), idesc,
-                    (kb > 0 || k > 0) ? 1u : 0u);
+#pragma unroll
+          for (int mt = 0; mt < MT; ++mt)
+            mma<TF32>(d + (uint32_t)(mt * BN), sw128_desc(a + mt * BM * BKB + 32 * k),
+                      sw128_desc(b + 32 * k), idesc, (kb > 0 || k > 0) ? 1u : 0u);
         mma_commit(&empty[s]);
       }
       mma_commit(&tfull[acc]);
@@ -161,8 +169,8 @@ __global__ void __launch_bounds__(64 + 32 * Epi::kWarps, 1)
     float* esm = Epi::kSmemBytes ? reinterpret_cast<float*>(smem + S::RING + 256) : nullptr;
     int j = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++j) {
-      const int acc = j & 1;
-      bool bad = !mbar_wait(&tfull[acc], (j / 2) & 1, err, 14);
+      const int acc = NBUF == 2 ? (j & 1) : 0;
+      bool bad = !mbar_wait(&tfull[acc], (j / NBUF) & 1, err, 14);
       fence_after();
       // one decision for every epilogue warp (barrier 1 with an OR of the flags)
       if (epi_bar_or<Epi::kWarps>(bad || *(volatile int*)abort_flag)) {
@@ -170,8 +178,11 @@ __global__ void __launch_bounds__(64 + 32 * Epi::kWarps, 1)
         break;
       }
       const int bx = t % gx, by = t / gx;
-      epi.template run<BN>(tmem + (uint32_t)acc * ASTRIDE, q, lane, warp - 2, bx, by,
-                           epi.m_origin(bx, by), epi.n_origin(bx, by), M, N, esm);
+#pragma unroll
+      for (int mt = 0; mt < MT; ++mt)
+        epi.template run<BN>(tmem + (uint32_t)acc * ASTRIDE + (uint32_t)(mt * BN), q, lane,
+                             warp - 2, bx, by, epi.m_origin(bx, by) + mt * BM,
+                             epi.n_origin(bx, by), M, N, esm);
       fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&tempty[acc]);
@@ -192,6 +203,7 @@ struct EpiStore {
   static constexpr int kSmemBytes = 0;
   static constexpr bool kB3D = false;  // B tile = one 2-D box at row n_origin
   static constexpr int kWarps = 4;      // epilogue warps
+  static constexpr int kMT = 1;         // 128-row A tiles per output tile
   float* C;
   long ldc;
   float alpha;
@@ -238,6 +250,7 @@ struct EpiExchange {
   static constexpr int kSmemBytes = 128 * 257 * 4;  // one 128 x 256 FP32 tile
   static constexpr bool kB3D = true;
   static constexpr int kWarps = 8;  // two per TMEM lane quarter, splitting columns / walkers
+  static constexpr int kMT = 1;
   static constexpr int kMaxCW = 16;
   double* part;
   int G, W, N, RG, CW, NPAD, nchunk;
@@ -354,6 +367,7 @@ struct EpiProp0 {
   static constexpr int kSmemBytes = 0;
   static constexpr bool kB3D = false;  // B tile = one 2-D box at row n_origin
   static constexpr int kWarps = 4;      // epilogue warps
+  static constexpr int kMT = 1;         // 128-row A tiles per output tile
   float* acc;
   long ldacc;
   void* tb;
@@ -411,6 +425,7 @@ struct EpiTaylor {
   static constexpr int kSmemBytes = 0;
   static constexpr bool kB3D = false;  // B tile = one 2-D box at row n_origin
   static constexpr int kWarps = 4;      // epilogue warps
+  static constexpr int kMT = 1;         // 128-row A tiles per output tile
   static constexpr int kBN = 160;  // two tiles cover p < 320
   float* S;
   long lds;
@@ -473,10 +488,11 @@ struct EpiV {
   static constexpr int kSmemBytes = 0;
   static constexpr bool kB3D = false;  // B tile = one 2-D box at row n_origin
   static constexpr int kWarps = 4;      // epilogue warps
+  static constexpr int kMT = 2;         // 256-row tiles: each Cholesky tile serves 128 walkers
   void* V;
   int lo_kind, W, M, Mp;
   float sdt;
-  __device__ __forceinline__ int m_origin(int bx, int) const { return bx * BM; }
+  __device__ __forceinline__ int m_origin(int bx, int) const { return bx * BM * kMT; }
   __device__ __forceinline__ int n_origin(int, int by) const { return by * 256; }
   template <int BN>
   __device__ __forceinline__ void run(uint32_t tmem, int q, int lane, int, int, int, int m0, int n0,
@@ -508,6 +524,7 @@ struct EpiPhi {
   static constexpr int kSmemBytes = 0;
   static constexpr bool kB3D = false;  // B tile = one 2-D box at row n_origin
   static constexpr int kWarps = 4;      // epilogue warps
+  static constexpr int kMT = 1;         // 128-row A tiles per output tile
   double* phiT;
   const double* wt;
   int N, M, rows;
@@ -667,11 +684,11 @@ int tc_sm_count() {
 template <int BN, int STAGES, bool TF32, class Epi>
 static int launch_tc_persistent(const TcGemm& g, const Epi& epi, int gx, int gy, cudaStream_t st,
                                 const CUtensorMap* tb_given = nullptr) {
-  constexpr int kTotal = tc::Smem<BN, STAGES>::TOTAL + Epi::kSmemBytes;
+  constexpr int kTotal = tc::Smem<BN, STAGES, Epi::kMT>::TOTAL + Epi::kSmemBytes;
   static_assert(kTotal <= 232448, "shared memory");
   const int eb = TF32 ? 4 : 2;
   CUtensorMap ta, tb;
-  AFQ_TRY(make_tmap(&ta, g.A, eb, g.m, g.k, g.lda, tc::BM));
+  AFQ_TRY(make_tmap(&ta, g.A, eb, g.m, g.k, g.lda, tc::BM * Epi::kMT));
   if (tb_given)
     tb = *tb_given;
   else
@@ -818,9 +835,9 @@ int tc_v_full(const TcGemm& g, void* V, int lo_kind, int W, int M, int Mp, doubl
     return AFQMC_EINVAL;
   }
   tc::EpiV e{V, lo_kind, W, M, Mp, (float)sdt};
-  const int gx = cdiv(g.m, tc::BM), gy = cdiv(g.n, 256);
-  if (g.tf32) return launch_tc_persistent<256, 4, true>(g, e, gx, gy, st);
-  return launch_tc_persistent<256, 4, false>(g, e, gx, gy, st);
+  const int gx = cdiv(g.m, tc::BM * tc::EpiV::kMT), gy = cdiv(g.n, 256);
+  if (g.tf32) return launch_tc_persistent<256, 3, true>(g, e, gx, gy, st);
+  return launch_tc_persistent<256, 3, false>(g, e, gx, gy, st);
 }
 
 int tc_prop_last(const TcGemm& g, double* phiT, const double* wt, int N, int M,

@@ -56,16 +56,19 @@ def test_trial_energy_mixed_vs_fp64(pkg, prec, tol):
 
 
 @pytest.mark.parametrize("prec,tol_phi,tol_e", [(2, 3e-2, 5e-3), (1, 5e-3, 5e-4)])
-def test_one_step_mixed_vs_fp64(pkg, prec, tol_phi, tol_e):
-    """One full step of the 12-orbital workload on identical Philox fields."""
+@pytest.mark.parametrize("nwalkers", [32, 200])
+def test_one_step_mixed_vs_fp64(pkg, prec, tol_phi, tol_e, nwalkers):
+    """One full step of the 12-orbital workload on identical Philox fields;
+    200 walkers put field rows in both halves of a 256-row V tile and in a
+    ragged last tile."""
     w = workloads.config("c0")
-    r = runs(pkg, w, [0, prec], energy_period=1)
+    r = runs(pkg, w, [0, prec], nwalkers=nwalkers, energy_period=1)
     for x in r.values():
         x.propagate(1)
     p64, w64, _ = r[0].get_walkers()
     pmx, wmx, _ = r[prec].get_walkers()
     alive = np.nonzero(w64 != 0)[0]
-    assert alive.size > w.nwalkers // 2
+    assert alive.size > nwalkers // 2
     assert rel(pmx[alive], p64[alive]) < tol_phi
     e64 = r[0].energy_log()[-1, 1]
     emx = r[prec].energy_log()[-1, 1]
