@@ -256,22 +256,18 @@ static int launch_taylor(const TaylorArgsT<T>& a, cudaStream_t st) {
 int launch_taylor_term(const TaylorArgsT<double>& a, cudaStream_t st) { return launch_taylor(a, st); }
 
 // ------------------------------------------------------------- overlap ------
-// Float64 throughout (Theorem 1.1, Eq. precomputing).  k_overlap, one block
-// per walker:
-//   1. S = V_T^T Phi (N x N complex): with V_T = [I_N; 0] (the trial-adapted
-//      basis) the top block of Phi; otherwise V_T^T and Phi^T are staged
-//      through shared memory OV_P orbitals at a time, each thread
-//      accumulating up to OV_R entries of S (re and im planes);
-//   2. Gauss-Jordan elimination with partial pivoting (largest modulus,
-//      searched by one warp): S^-1 and log det S = sum log p_k (+ i pi per
-//      row swap), S^-1 written for k_theta_rows;
+// Float64 throughout (Theorem 1.1, Eq. precomputing), in the trial-adapted
+// basis where V_T = [I_N; 0].  k_overlap, one block per walker:
+//   1. S = V_T^T Phi is the top N x N block of Phi (a gather);
+//   2. Gauss-Jordan elimination with partial pivoting (largest |s_rk|^2, the
+//      first row on ties, searched by one warp): S^-1 and log det S = sum log
+//      p_k (+ i pi per row swap), S^-1 written for k_theta_rows;
 // then k_theta_rows forms Theta^T[i][p] = sum_j S^-1[j][i] Phi^T[j][p].
 // log <Psi_T|Psi> = 2 log det S (both spins), phase wrapped to (-pi, pi].
-// Every walker is computed; Theta and log det are stored for live walkers.
+// Every walker is computed; S^-1 and log det are stored for live walkers.
 namespace {
-constexpr int OV_P = 32, OV_R = 8, OV_T = 256;
+constexpr int OV_T = 256;
 }
-
 __global__ void __launch_bounds__(OV_T) k_overlap(OverlapArgs a) {
   extern __shared__ double2 ov_sm[];
   const int w = blockIdx.x;
@@ -279,60 +275,15 @@ __global__ void __launch_bounds__(OV_T) k_overlap(OverlapArgs a) {
   const int N = a.N, M = a.M;
   double2* A = ov_sm;            // [N][N]
   double2* Inv = ov_sm + N * N;  // [N][N]
-  double* Vs = reinterpret_cast<double*>(ov_sm + 2 * N * N);  // [N][OV_P + 1]
-  double* Ps = Vs + N * (OV_P + 1);                           // [2N][OV_P + 1]
   __shared__ int piv, swaps, singular;
   __shared__ double logabs, phase;
   __shared__ double2 rpiv;
   const double* fr = a.phiT + (long)w * 2 * N * M;
   const double* fi = fr + (long)N * M;
-  const int nout = 2 * N * N;  // (i, c, j): S_c[i][j], c = re / im plane
-  if (a.unit_trial) {
-    // V_T = [I_N; 0]: S[i][j] = Phi[i][j], the top block of the orbitals
-    for (int idx = threadIdx.x; idx < N * N; idx += OV_T) {
-      const int i = idx / N, j = idx % N;
-      A[idx] = make_double2(fr[(long)j * M + i], fi[(long)j * M + i]);
-    }
-  }
-  for (int o0 = 0; o0 < (a.unit_trial ? 0 : nout); o0 += OV_T * OV_R) {
-    double acc[OV_R];
-#pragma unroll
-    for (int r = 0; r < OV_R; ++r) acc[r] = 0.0;
-    for (int p0 = 0; p0 < M; p0 += OV_P) {
-      for (int idx = threadIdx.x; idx < 3 * N * OV_P; idx += OV_T) {
-        const int row = idx / OV_P, pp = idx % OV_P, pc = p0 + pp;
-        double v = 0.0;
-        if (pc < M) v = row < N ? a.VTt[(long)row * M + pc] : fr[(long)(row - N) * M + pc];
-        if (row < N)
-          Vs[row * (OV_P + 1) + pp] = v;
-        else
-          Ps[(row - N) * (OV_P + 1) + pp] = v;
-      }
-      __syncthreads();
-#pragma unroll
-      for (int r = 0; r < OV_R; ++r) {
-        const int o = o0 + threadIdx.x + r * OV_T;
-        if (o < nout) {
-          const int i = o / (2 * N), cj = o % (2 * N);
-          const double* vs = Vs + i * (OV_P + 1);
-          const double* ps = Ps + cj * (OV_P + 1);
-          double t = acc[r];
-#pragma unroll 8
-          for (int pp = 0; pp < OV_P; ++pp) t = fma(vs[pp], ps[pp], t);
-          acc[r] = t;
-        }
-      }
-      __syncthreads();
-    }
-#pragma unroll
-    for (int r = 0; r < OV_R; ++r) {
-      const int o = o0 + threadIdx.x + r * OV_T;
-      if (o < nout) {
-        const int i = o / (2 * N), cj = o % (2 * N), c = cj / N, j = cj % N;
-        double* d = reinterpret_cast<double*>(&A[i * N + j]);
-        d[c] = acc[r];
-      }
-    }
+  // S[i][j] = Phi[i][j], the top block of the orbitals
+  for (int idx = threadIdx.x; idx < N * N; idx += OV_T) {
+    const int i = idx / N, j = idx % N;
+    A[idx] = make_double2(fr[(long)j * M + i], fi[(long)j * M + i]);
   }
   for (int idx = threadIdx.x; idx < N * N; idx += OV_T)
     Inv[idx] = make_double2(idx / N == idx % N ? 1.0 : 0.0, 0.0);
@@ -503,9 +454,11 @@ static int launch_theta_rows(const OverlapArgs& a, cudaStream_t st) {
 }
 
 int launch_overlap(const OverlapArgs& a, cudaStream_t st) {
-  // the S tiles are only staged when V_T is a general matrix
-  const size_t smem = 2ull * a.N * a.N * sizeof(double2) +
-                      (a.unit_trial ? 0ull : 3ull * a.N * (OV_P + 1) * sizeof(double));
+  const size_t smem = 2ull * a.N * a.N * sizeof(double2);
+  if (!a.unit_trial || !a.Sinv) {
+    set_error("overlap: the trial-adapted basis (V_T = [I; 0]) and S^-1 scratch are required");
+    return AFQMC_EINVAL;
+  }
   if (smem > 200 * 1024) {
     set_error("overlap: N=%d too large", a.N);
     return AFQMC_EUNSUPPORTED;
