@@ -187,6 +187,17 @@ static int all_finite(const double* v, size_t n, const char* what) {
 }
 
 // ------------------------------------------------------------ step pieces ---
+// The mixed path keeps phi_lo = BF16/TF32 copy of the orbitals (pitch Mp)
+// current: the last half step writes both; every other change of the
+// orbitals (Gram-Schmidt, comb, set-up, set_walkers, load) calls this.
+int refresh_phi_lo(afqmc_state* s) {
+  const Bufs& b = s->b;
+  if (!b.mixed) return AFQMC_OK;
+  const afqmc_params& p = s->p;
+  return launch_convert_lo(b.phiT, 2L * p.N * p.nwalkers, p.M, p.M, b.phi_lo, b.Mp, b.lo_kind,
+                           s->st);
+}
+
 int overlap_update(afqmc_state* s, bool into_ld, bool timed) {
   const afqmc_params& p = s->p;
   const Bufs& b = s->b;
@@ -381,7 +392,6 @@ static int propagate_mixed(afqmc_state* s) {
   // first half step: T_0 = (B_half Phi)^T into columns [0, Mp) of the FP32
   // rows of acc (pitch 2 Mp) and, as the 0th Taylor operand, into Tb0
   prof_begin(s, AFQMC_PH_BHALF);
-  AFQ_TRY(launch_convert_lo(b.phiT, 2L * N * W, M, M, b.phi_lo, b.Mp, b.lo_kind, s->st));
   TcGemm h1;
   h1.m = 2 * N * W;
   h1.n = M;
@@ -414,7 +424,7 @@ static int propagate_mixed(afqmc_state* s) {
   h2.ldb = 2L * b.Mp;
   h2.tf32 = true;
   h2.err = b.status;
-  AFQ_TRY(tc_prop_last(h2, b.phiT, b.wt, N, M, s->st));
+  AFQ_TRY(tc_prop_last(h2, b.phiT, b.wt, N, M, b.phi_lo, b.lo_kind, b.Mp, s->st));
   prof_end(s);
   return AFQMC_OK;
 }
@@ -449,6 +459,7 @@ static int step_once(afqmc_state* s) {
     // which the kernel applies to ld (no new overlap needed)
     MgsArgs ma{W, M, N, b.phiT, b.wt, b.ld};
     AFQ_TRY(launch_mgs(ma, s->st));
+    AFQ_TRY(refresh_phi_lo(s));
     prof_end(s);
   }
   if (p.pc_period && n % p.pc_period == 0) {
@@ -456,6 +467,7 @@ static int step_once(afqmc_state* s) {
     CombArgs ca{W, M, N, p.seed, reinterpret_cast<const int64_t*>(b.counters + CTR_STEP),
                 b.wt, b.cum, b.parent, b.phiT, b.thetaT, b.ld, b.T0, b.T1, b.tmp_ld, b.wtot};
     AFQ_TRY(launch_comb(ca, s->st));
+    AFQ_TRY(refresh_phi_lo(s));
     prof_end(s);
   }
   if (p.energy_period && n % p.energy_period == 0) {
@@ -714,6 +726,7 @@ static int setup_device(afqmc_state* s, const double* h1, const double* L, const
   }
   // walkers at the trial, their overlaps, and the trial energy
   AFQ_TRY(launch_init_walkers(b.VTt, b.phiT, b.wt, W, N, M, st));
+  AFQ_TRY(refresh_phi_lo(s));
   AFQ_TRY(overlap_update(s, true, false));
   s->t_fresh = false;
   s->elo = -INFINITY;
@@ -1010,6 +1023,7 @@ int afqmc_set_walkers(afqmc_state* s, const double* phi, const double* weight) {
   g.C = s->b.phiT;
   g.ldc = (long)M;
   AFQ_TRY(gemm_nt_f64(g, s->st));
+  AFQ_TRY(refresh_phi_lo(s));
   AFQ_CUDA(cudaMemcpyAsync(s->b.wt, weight, sizeof(double) * 2 * W, cudaMemcpyHostToDevice, s->st));
   AFQ_TRY(overlap_update(s, true, false));
   s->t_fresh = false;
@@ -1136,6 +1150,7 @@ int afqmc_load(afqmc_state* s, const void* buf, size_t bytes) {
   }
   const double* d = reinterpret_cast<const double*>(static_cast<const char*>(buf) + sizeof(CkptHeader));
   AFQ_CUDA(cudaMemcpyAsync(s->b.phiT, d, sizeof(double) * nw, cudaMemcpyHostToDevice, s->st));
+  AFQ_TRY(refresh_phi_lo(s));
   AFQ_CUDA(cudaMemcpyAsync(s->b.thetaT, d + nw, sizeof(double) * nw, cudaMemcpyHostToDevice, s->st));
   AFQ_CUDA(cudaMemcpyAsync(s->b.wt, d + 2 * nw, sizeof(double) * 2 * p.nwalkers, cudaMemcpyHostToDevice, s->st));
   AFQ_CUDA(cudaMemcpyAsync(s->b.ld, d + 2 * nw + 2 * p.nwalkers, sizeof(double) * 2 * p.nwalkers,

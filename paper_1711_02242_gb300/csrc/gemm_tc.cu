@@ -529,6 +529,8 @@ struct EpiPhi {
   const double* wt;
   int N, M, rows;
   int bn;  // tile width (the kernel's BN)
+  void* phi_lo;  // BF16/TF32 copy of the orbitals (pitch Mp) for the next first half step
+  int lo_kind, Mp;
   __device__ __forceinline__ int m_origin(int bx, int) const { return bx * BM; }
   __device__ __forceinline__ int n_origin(int, int by) const { return by * bn; }
   template <int BN>
@@ -551,6 +553,11 @@ struct EpiPhi {
 #pragma unroll
         for (int u = 0; u < 16; ++u)
           if (pb + u < M) o[u] = (double)v[u];
+      }
+      if (pb + 16 <= M) {
+        store16_lo(phi_lo, lo_kind, (long)row * Mp + pb, v, 1.f);
+      } else {
+        for (int u = 0; u < 16 && pb + u < M; ++u) store_lo(phi_lo, lo_kind, (long)row * Mp + pb + u, v[u]);
       }
     }
   }
@@ -840,10 +847,10 @@ int tc_v_full(const TcGemm& g, void* V, int lo_kind, int W, int M, int Mp, doubl
   return launch_tc_persistent<256, 3, false>(g, e, gx, gy, st);
 }
 
-int tc_prop_last(const TcGemm& g, double* phiT, const double* wt, int N, int M,
-                 cudaStream_t st) {
+int tc_prop_last(const TcGemm& g, double* phiT, const double* wt, int N, int M, void* phi_lo,
+                 int lo_kind, int Mp, cudaStream_t st) {
   const int bn = half_step_bn(M);
-  tc::EpiPhi e{phiT, wt, N, M, g.m, bn};
+  tc::EpiPhi e{phiT, wt, N, M, g.m, bn, phi_lo, lo_kind, Mp};
   const int gx = cdiv(g.m, tc::BM), gy = cdiv(M, bn);
   if (bn == 160) {
     if (g.tf32) return launch_tc_persistent<160, 6, true>(g, e, gx, gy, st);

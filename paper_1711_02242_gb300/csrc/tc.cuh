@@ -34,8 +34,9 @@ int tc_prop_first(const TcGemm& g, float* acc, long ldacc, void* tb, int lo_kind
 // S = T_k (first) or S += T_k, T_k = scale * (V T_{k-1}); pitch lds
 int tc_taylor_term(const TcGemm& g, float* S, long lds, bool first, void* tb_out, int lo_kind,
                    int W, int N, int M, int Mp, float scale, cudaStream_t st);
-int tc_prop_last(const TcGemm& g, double* phiT, const double* wt, int N, int M,
-                 cudaStream_t st);
+// also writes the BF16/TF32 copy of the new orbitals (pitch Mp) for live walkers
+int tc_prop_last(const TcGemm& g, double* phiT, const double* wt, int N, int M, void* phi_lo,
+                 int lo_kind, int Mp, cudaStream_t st);
 // V = i sqrt(dt) sum_g x_g L_g from the full transposed vectors (rows p*Mp+q)
 // written directly as [Re V | Im V] rows (pitch 2 Mp) of each walker.
 int tc_v_full(const TcGemm& g, void* V, int lo_kind, int W, int M, int Mp, double sdt,
