@@ -396,6 +396,45 @@ AFQMC_API int afqmc_local_energies_noalloc(int32_t M, int32_t N, int32_t nchol,
  */
 AFQMC_API int afqmc_wait_flag(const int* d_flag, int64_t max_polls, int* d_status, void* stream);
 
+/*
+ * Modified Cholesky decomposition of the two-electron interaction (Sec. 2.3,
+ * Eqs. chol and chol2), the step that produces the Cholesky vectors L that
+ * afqmc_init takes.
+ *   dim      size of V: M*M for an interaction over M orbitals
+ *   d_V      [dim][dim] DEVICE float64, row-major, symmetric positive
+ *            semi-definite: V[p*M + r][q*M + s] = v_pqrs.  Read only: its
+ *            diagonal, then row nu0 of every pivot nu0 (V is taken to be
+ *            symmetric; a non-finite value in a row read stops the call)
+ *   delta    threshold: vectors are added until every residual diagonal is
+ *            below delta (then every residual element is, by Cauchy-Schwarz)
+ *   max_vectors  room in d_L (1 .. 16384)
+ *   d_L      [max_vectors][dim] DEVICE float64 output: vector g in row g
+ *            (as L[g][p][r] for afqmc_init); rows >= *nvec are not written.
+ *            Later iterations read the rows already written back
+ *   d_piv    [max_vectors] DEVICE int32 output, may be NULL: the pivot index
+ *            nu0 of each vector
+ *   nvec     HOST output: number of vectors found
+ *   residual HOST output, may be NULL: largest residual diagonal left; the
+ *            decomposition converged iff *residual < delta (otherwise
+ *            max_vectors vectors were found first)
+ *   d_work   DEVICE workspace of afqmc_mcd_workspace_size() bytes, 256-byte
+ *            aligned, caller-owned (about 8.8 dim + 8 max_vectors bytes)
+ * Each iteration pivots on the largest residual diagonal Delta_max (the
+ * smallest index among equal values), zeroes every index whose
+ * sqrt(|Delta_mm| Delta_max) <= min(1e-9, delta) (damped prescreening: a
+ * zeroed index stays zero in every later vector) and takes
+ * L_mu = (V[mu][nu0] - sum_g L[g][mu] L[g][nu0]) / sqrt(Delta_max).
+ * Runs on `stream` and returns when the decomposition is done (it reads a
+ * few bytes of state back between groups of launches).  Returns
+ * AFQMC_EINVAL on bad arguments, AFQMC_ENOSPC if the workspace is too small,
+ * AFQMC_ENONFINITE if V's diagonal or a row it read holds a non-finite value.
+ */
+AFQMC_API int afqmc_mcd_workspace_size(int64_t dim, int32_t max_vectors, size_t* bytes);
+AFQMC_API int afqmc_modified_cholesky(int64_t dim, const double* d_V, double delta,
+                                      int32_t max_vectors, double* d_L, int32_t* d_piv,
+                                      int32_t* nvec, double* residual, void* d_work,
+                                      size_t work_bytes, void* stream);
+
 /* Message for the calling thread's last failed call (never NULL). */
 AFQMC_API const char* afqmc_last_error(void);
 

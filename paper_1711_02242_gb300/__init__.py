@@ -32,7 +32,8 @@ EXPORTED = ["afqmc_default_params", "afqmc_workspace_size", "afqmc_init", "afqmc
             "afqmc_philox4x32_10", "afqmc_gaussian_fields", "afqmc_contract",
             "afqmc_profile_start", "afqmc_profile_stop", "afqmc_local_energies_noalloc",
             "afqmc_group_create", "afqmc_group_propagate", "afqmc_group_destroy",
-            "afqmc_wait_flag", "afqmc_taylor_series"]
+            "afqmc_wait_flag", "afqmc_taylor_series", "afqmc_mcd_workspace_size",
+            "afqmc_modified_cholesky"]
 
 
 class Params(ctypes.Structure):
@@ -106,6 +107,11 @@ def lib():
         "afqmc_taylor_series": (ctypes.c_int, [ctypes.c_int32] + [ctypes.c_int64] * 4 +
                                 [ctypes.c_int32, vp, vp, vp, vp, ctypes.c_int64, ctypes.c_int32,
                                  vp, vp]),
+        "afqmc_mcd_workspace_size": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32,
+                                                    P(ctypes.c_size_t)]),
+        "afqmc_modified_cholesky": (ctypes.c_int, [ctypes.c_int64, vp, ctypes.c_double,
+                                                   ctypes.c_int32, vp, vp, P(ctypes.c_int32),
+                                                   dp, vp, ctypes.c_size_t, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -163,6 +169,32 @@ def afqmc_gaussian_fields(seed: int, step: int, w0: int, nw: int, nchol: int, de
     _check(lib().afqmc_gaussian_fields(seed, step, w0, nw, nchol, ctypes.c_void_p(out.data_ptr()),
                                        ctypes.c_void_p(st.cuda_stream)))
     return out
+
+
+def afqmc_modified_cholesky(V, delta: float, max_vectors: int, workspace=None):
+    """Modified Cholesky vectors of the symmetric PSD CUDA float64 matrix V
+    (Sec. 2.3, Eqs. chol/chol2): returns (L [nvec][dim], pivots [nvec], the
+    largest residual diagonal left).  Converged iff that residual < delta."""
+    import torch
+
+    V = V.contiguous()
+    dim = V.shape[0]
+    nbytes = ctypes.c_size_t(0)
+    _check(lib().afqmc_mcd_workspace_size(dim, max_vectors, ctypes.byref(nbytes)))
+    if workspace is None or workspace.numel() < nbytes.value:
+        workspace = torch.empty(nbytes.value, dtype=torch.uint8, device=V.device)
+    L = torch.empty((max_vectors, dim), dtype=torch.float64, device=V.device)
+    piv = torch.empty(max_vectors, dtype=torch.int32, device=V.device)
+    nvec = ctypes.c_int32(0)
+    resid = ctypes.c_double(0.0)
+    st = torch.cuda.current_stream(V.device)
+    _check(lib().afqmc_modified_cholesky(
+        dim, ctypes.c_void_p(V.data_ptr()), float(delta), max_vectors,
+        ctypes.c_void_p(L.data_ptr()), ctypes.c_void_p(piv.data_ptr()), ctypes.byref(nvec),
+        ctypes.byref(resid), ctypes.c_void_p(workspace.data_ptr()), workspace.numel(),
+        ctypes.c_void_p(st.cuda_stream)))
+    n = nvec.value
+    return L[:n], piv[:n], resid.value
 
 
 def afqmc_launch_count() -> int:

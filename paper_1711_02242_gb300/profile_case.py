@@ -1,7 +1,7 @@
 """A single contraction of the M=300 step, for kernel profiling.
 
-    python -m paper_1711_02242_gb300.profile_case [--case v|fb|taylor] [--dtype bf16|tf32]
-                                                  [--reps 3] [--walkers 512]
+    python -m paper_1711_02242_gb300.profile_case [--case v|fb|taylor|mcd] [--dtype bf16|tf32]
+                                                  [--reps 3] [--walkers 512] [--orbitals 300]
 
 Case "v": V = sum_g x_g L_g as afqmc_contract with the M=300 shapes
 (A = 1024 x 1800 fields, B = 45150 x 1800 packed Cholesky vectors, C FP32):
@@ -9,6 +9,10 @@ about 350 MB on the device, B alone (162 MB BF16) larger than the 129 MB L2.
 Case "fb": the force-bias contraction (A = 1024 x 7600, B = 1800 x 7600).
 Case "taylor": the sixth-order Taylor series of exp(V) on 512 walkers with
 M = 300, N = 25 (afqmc_taylor_series; V is 187 MB in BF16).
+Case "mcd": the modified Cholesky decomposition (afqmc_modified_cholesky,
+delta = 1e-6) of the interaction of the seeded Hamiltonian with `--orbitals`
+M orbitals and 5M vectors (the M^2 x M^2 matrix is 65 GB at M = 300, 5.2 GB
+at M = 160); one launch per vector.
 Random operands; prints the mean time per launch from CUDA events.
 """
 from __future__ import annotations
@@ -23,7 +27,8 @@ def main():
     import torch
 
     ap = argparse.ArgumentParser()
-    ap.add_argument("--case", default="v", choices=["v", "fb", "taylor"])
+    ap.add_argument("--case", default="v", choices=["v", "fb", "taylor", "mcd"])
+    ap.add_argument("--orbitals", type=int, default=300)
     ap.add_argument("--walkers", type=int, default=512)
     ap.add_argument("--dtype", default="bf16", choices=["bf16", "tf32"])
     ap.add_argument("--reps", type=int, default=3)
@@ -33,6 +38,8 @@ def main():
     b.build()
     if a.case == "taylor":
         return taylor(a)
+    if a.case == "mcd":
+        return mcd(a)
     if a.case == "v":
         m, n, k, pitch = 1024, 45150, 1800, 1800
     else:
@@ -114,5 +121,30 @@ def taylor(a):
     assert int(st.item()) == 0
 
 
+def mcd(a):
+    import torch
+
+    import workloads
+
+    M = a.orbitals
+    G = 5 * M
+    _, L, _ = workloads.hamiltonian(M, G, 5000 + M, l_scale=workloads.l_amplitude(M, G))
+    V = workloads.interaction_matrix_device(L)
+    del L
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(a.reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        Lv, piv, resid = pkg.afqmc_modified_cholesky(V, 1e-6, G + 16)
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    n = Lv.shape[0]
+    print(f"case mcd M={M} dim={M * M} vectors={n} residual={resid:.3e} "
+          f"ms={min(times):.3f} per-vector-us={1e3 * min(times) / n:.2f}")
+
+
 if __name__ == "__main__":
     main()
+

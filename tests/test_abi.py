@@ -67,3 +67,20 @@ def test_library_has_no_oracle_dependency():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt, f
+
+
+def test_mcd_workspace_size_and_validation_without_gpu(built):
+    """The decomposition's workspace holds the residual diagonal, the pivot's
+    components and one partial result per 32 indices (the vectors themselves
+    live in the caller's output); bad sizes are refused before any device
+    call."""
+    lib = built.lib()
+    n = ctypes.c_size_t(0)
+    assert lib.afqmc_mcd_workspace_size(90000, 1800, ctypes.byref(n)) == 0
+    want = 90000 * 8 + 1800 * 8 + 2813 * 24
+    assert want <= n.value < want + 4096 and n.value % 256 == 0
+    for dim, mv in ((0, 10), (10, 0), (10, 16385), (1 << 31, 10)):
+        assert lib.afqmc_mcd_workspace_size(dim, mv, ctypes.byref(n)) == -1
+    nv = ctypes.c_int32(0)
+    assert lib.afqmc_modified_cholesky(10, None, 1e-6, 10, None, None, ctypes.byref(nv), None,
+                                       None, 0, None) == -1

@@ -42,6 +42,8 @@ __all__ = [
     "l_amplitude",
     "batched_systems",
     "request_stream",
+    "interaction_matrix",
+    "interaction_matrix_device",
 ]
 
 
@@ -121,6 +123,42 @@ def hamiltonian(M: int, nchol: int, ham_seed: int, decay: float | None = None,
     for g in range(nchol):
         L[g] = _sym_from_upper(rng, M, l_scale * math.exp(-g / decay), True)
     return h1, L, 0.0
+
+
+def interaction_matrix(L: np.ndarray) -> np.ndarray:
+    """The two-electron matrix V[(p, r)][(q, s)] = v_pqrs = sum_g L[g]_pr L[g]_qs
+    of Cholesky vectors ``L`` (nchol, M, M), as an (M*M) x (M*M) float64 array
+    with row index p*M + r; symmetrised so that V == V.T exactly.  The input of
+    the modified Cholesky decomposition (Sec. 2.3)."""
+    G, M, _ = L.shape
+    Lm = np.ascontiguousarray(L.reshape(G, M * M))
+    V = Lm.T @ Lm
+    V += V.T
+    V *= 0.5
+    return V
+
+
+def interaction_matrix_device(L: np.ndarray, device="cuda:0"):
+    """``interaction_matrix(L)`` built on a CUDA device with PyTorch (for
+    interactions too large to form on the host, e.g. M = 300: 65 GB).  The
+    products run over the M(M+1)/2 index pairs p <= r, whose rows and columns
+    are then repeated for (r, p), so rows (p, r) and (r, p) are identical;
+    the result is symmetric to rounding, then symmetrised exactly."""
+    import torch
+
+    G, M, _ = L.shape
+    iu = np.triu_indices(M)
+    Lp = torch.from_numpy(np.ascontiguousarray(L[:, iu[0], iu[1]])).to(device)
+    W = Lp.T @ Lp
+    del Lp
+    W = (W + W.T) * 0.5
+    pair = np.zeros((M, M), np.int64)
+    pair[iu] = np.arange(iu[0].size)
+    pair = pair + np.triu(pair, 1).T
+    idx = torch.from_numpy(pair.reshape(-1)).to(device)
+    V = W.index_select(0, idx)
+    del W
+    return V.index_select(1, idx)
 
 
 def batched_systems(seed: int = 3000, count: int = 16):
