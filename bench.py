@@ -8,6 +8,9 @@ propagation, overlap/LU, weights, and the periodic QR and energy).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16|tf32|fp64]
     python bench.py --impl reference      # the CPU oracle on the host cores
+    python bench.py --workload mcd [--config c2] [--impl reference]
+        # modified Cholesky decomposition (Sec. 2.3) of the workload's
+        # interaction over index pairs: Cholesky vectors per second
 
 The default is the mixed path with BF16 tensor-core operands (the M=300
 configuration's precision); the line also carries the same workload's FP64
@@ -651,6 +654,158 @@ def run_serve(args):
     return 0
 
 
+def mcd_flops_bytes(npair: int, nvec: int):
+    """Algorithmic FP64 work of a decomposition into nvec vectors over npair
+    indices: iteration k (k earlier vectors) takes npair k fused multiply-adds
+    (2 npair k FLOP) and streams the k earlier vectors' components and one row
+    of V, 8 npair (k + 1) bytes, plus the residual diagonal (read and write)
+    and the new vector (write), 24 npair bytes."""
+    ks = nvec * (nvec - 1) / 2
+    return 2.0 * npair * ks, 8.0 * npair * (ks + nvec) + 24.0 * npair * nvec
+
+
+def mcd_oracle_sample(W, nvec_sample, delta):
+    """The oracle's decomposition of the host pair matrix, stopped after
+    nvec_sample vectors (0: not stopped): seconds, vectors."""
+    from oracle import mcd as omcd
+
+    t0 = time.perf_counter()
+    Lo, piv, dmax, resid, conv = omcd.modified_cholesky(W, delta, max_vectors=nvec_sample or None)
+    return time.perf_counter() - t0, len(piv)
+
+
+def run_mcd(args):
+    """Modified Cholesky decomposition (Sec. 2.3, Eqs. chol and chol2) of the
+    interaction v_pqrs = sum_g L_g[p,r] L_g[q,s] of the chosen workload's
+    Cholesky vectors, over the M(M+1)/2 index pairs (afqmc_modified_cholesky_pairs),
+    delta = 1e-6.  One step is one whole decomposition."""
+    import torch
+
+    w = workloads.config(args.config)
+    M = w.M
+    npair = M * (M + 1) // 2
+    delta = 1e-6
+    maxv = w.nchol + 64
+    _, L, _ = w.hamiltonian()
+    cores = len(os.sched_getaffinity(0))
+    desc = (f"modified Cholesky (delta {delta:g}) of the M={M} interaction built from the "
+            f"{w.nchol} Cholesky vectors of the walker-steps workload; {npair} index pairs "
+            f"p<=r, pair matrix {npair * npair * 8 / 1e9:.1f} GB float64")
+    ws_, rank, _ = dist_env()
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        if not torch.cuda.is_available():
+            print(json.dumps({"impl": "reference", "unavailable": "the pair matrix is built on "
+                              "the GPU (numpy would take minutes)"}))
+            return 0
+        W = workloads.interaction_pairs_device(L).cpu().numpy()
+        nv = args.mcd_cpu_vectors
+        secs = []
+        for _ in range(args.steps):
+            t, n = mcd_oracle_sample(W, nv, delta)
+            secs.append(t)
+        val = n / statistics.mean(secs)
+        line = {"impl": "reference", "metric": f"Cholesky vectors/s, mCD at M={M}",
+                "value": val, "unit": "vectors/s", "n_gpus": ws_, "steps": args.steps,
+                "warmup": 0, "ms_per_step": 1e3 * statistics.mean(secs),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64", "data": "synthetic",
+                "config": {"workload": desc, "sampled_vectors": n},
+                "cpu_baseline": {"value": val, "unit": "vectors/s", "cores": cores,
+                                 "kind": "oracle",
+                                 "sample": f"{n} vectors of the decomposition (the whole "
+                                           f"one unless --mcd-cpu-vectors caps it)"},
+                "e2e": {"value": val, "unit": "vectors/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return 0
+
+    import ctypes
+
+    import paper_1711_02242_gb300 as pkg
+    from paper_1711_02242_gb300 import build as b
+
+    b.build()
+    dev = torch.device("cuda", 0)
+    W = workloads.interaction_pairs_device(L, dev)
+    torch.cuda.synchronize()
+    nbytes = ctypes.c_size_t(0)
+    pkg._check(pkg.lib().afqmc_mcd_pairs_workspace_size(M, maxv, ctypes.byref(nbytes)))
+    work = torch.empty(nbytes.value, dtype=torch.uint8, device=dev)
+    st = torch.cuda.current_stream(dev)
+    for _ in range(args.warmup):
+        Lv, piv, resid = pkg.afqmc_modified_cholesky_pairs(W, M, delta, maxv, workspace=work)
+    torch.cuda.synchronize()
+    K = args.steps
+    l0 = pkg.afqmc_launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clk:
+        e0.record(st)
+        for _ in range(K):
+            Lv, piv, resid = pkg.afqmc_modified_cholesky_pairs(W, M, delta, maxv, workspace=work)
+        e1.record(st)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / K
+    launches = (pkg.afqmc_launch_count() - l0) // K
+    nvec = Lv.shape[0]
+    flops, byts = mcd_flops_bytes(npair, nvec)
+    # end to end: pair matrix from pinned host memory, decomposition, vectors
+    # back to pinned host memory
+    e2e = None
+    if not args.no_e2e:
+        Wh = torch.empty(W.shape, dtype=W.dtype, pin_memory=True)
+        Wh.copy_(W)
+        Wd = torch.empty_like(W)
+        Lh = torch.empty((nvec, M, M), dtype=torch.float64, pin_memory=True)
+        del W
+        torch.cuda.synchronize()
+        ke = max(1, K // 2)
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            Wd.copy_(Wh, non_blocking=True)
+            Lv, piv, resid = pkg.afqmc_modified_cholesky_pairs(Wd, M, delta, maxv, workspace=work)
+            Lh.copy_(Lv, non_blocking=True)
+            torch.cuda.synchronize()
+        s_e2e = (time.perf_counter() - t0) / ke
+        e2e = {"value": nvec / s_e2e, "unit": "vectors/s", "h2d_bytes_per_step": Wh.nbytes,
+               "d2h_bytes_per_step": Lh.nbytes,
+               "includes": "pair matrix host->device, decomposition, vectors device->host "
+                           "(pinned buffers)"}
+        W = Wd
+    pk_fp64 = FP64_PEAK_TFLOPS
+    hbm = peaks()[0]["hbm_gbs"]
+    line = {
+        "metric": f"Cholesky vectors/s, mCD at M={M}", "value": nvec / (ms * 1e-3),
+        "unit": "vectors/s", "n_gpus": 1, "steps": K, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": desc, "vectors": nvec, "residual": resid,
+                   "l2": f"input larger than L2 (pair matrix {npair * npair * 8 / 1e9:.1f} GB)"},
+        "roofline": {"bound": "alu", "achieved": flops / (ms * 1e-3) / 1e12, "peak": pk_fp64,
+                     "unit": "TFLOP/s", "frac": flops / (ms * 1e-3) / 1e12 / pk_fp64,
+                     "traffic": None, "kernel": "k_mcd_step",
+                     "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 x 2070 MHz",
+                     "ms_per_launch": ms / max(1, launches),
+                     "note": "one FMA per streamed float64 puts the step kernel on the FP64 "
+                             "pipe (8 B/FMA x 0.6 TFMA/s = 4.8 TB/s < HBM); whole "
+                             "decomposition time, launch gaps included"},
+        "hbm_view": {"achieved": byts / (ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+                     "frac": byts / (ms * 1e-3) / 1e9 / hbm},
+        "gpu_launches": launches, "clocks": clk.summary(), "e2e": e2e,
+    }
+    if not args.no_cpu_baseline:
+        Wc = W.cpu().numpy()
+        t, n = mcd_oracle_sample(Wc, args.mcd_cpu_vectors, delta)
+        line["cpu_baseline"] = {"value": n / t, "unit": "vectors/s", "cores": cores,
+                                "kind": "oracle", "seconds": t,
+                                "sample": (f"the first {n} of the {nvec} vectors" if n < nvec
+                                           else "the whole decomposition") +
+                                          " of the same pair matrix (numpy float64)"}
+    print(json.dumps(line))
+    return 0
+
+
 def dataclasses_replace(r):
     import dataclasses
 
@@ -659,9 +814,13 @@ def dataclasses_replace(r):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", default="c2", choices=["c2", "batched", "serve"],
+    ap.add_argument("--workload", default="c2", choices=["c2", "batched", "serve", "mcd"],
                     help="c2: the M=300 walker-steps/s line; batched / serve: the grouped and "
-                         "served forms (their own JSON lines)")
+                         "served forms; mcd: the modified Cholesky decomposition of the "
+                         "workload's interaction (their own JSON lines)")
+    ap.add_argument("--mcd-cpu-vectors", type=int, default=0,
+                    help="mcd: stop the oracle's sample after this many vectors (0: the whole "
+                         "decomposition, about 10 s of CPU at M=300)")
     ap.add_argument("--requests", type=int, default=40)
     ap.add_argument("--rate", type=float, default=20.0)
     ap.add_argument("--blocks", type=int, default=4)
@@ -688,6 +847,8 @@ def main():
         return run_batched(args)
     if args.workload == "serve":
         return run_serve(args)
+    if args.workload == "mcd":
+        return run_mcd(args)
     w = workloads.config(args.config)
     if args.impl == "reference":
         return run_reference(args, w)

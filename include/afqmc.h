@@ -435,6 +435,31 @@ AFQMC_API int afqmc_modified_cholesky(int64_t dim, const double* d_V, double del
                                       int32_t* nvec, double* residual, void* d_work,
                                       size_t work_bytes, void* stream);
 
+/*
+ * The same decomposition for the interaction of real orbitals, whose rows
+ * (p, r) and (r, p) of V are equal (v_pqrs = v_rqps), taken over the
+ * M (M + 1) / 2 index pairs p <= r: half the arithmetic and a quarter of
+ * the matrix.  Pair index P(p, r) = p M - p (p - 1) / 2 + (r - p), p <= r.
+ *   M        orbitals (1 .. 2048)
+ *   d_Vpair  [npair][npair] DEVICE float64, npair = M (M + 1) / 2:
+ *            Vpair[P(p, r)][P(q, s)] = v_pqrs for p <= r, q <= s
+ *   d_L      [max_vectors][M][M] DEVICE float64 output: L[g][p][r] =
+ *            L[g][r][p]; rows >= *nvec are not written
+ *   d_piv    [max_vectors] DEVICE int32 output, may be NULL: pivots as
+ *            p M + r with p <= r
+ *   d_work   afqmc_mcd_pairs_workspace_size() bytes (about
+ *            8 npair (max_vectors + 2) bytes), 256-byte aligned
+ * Pivots, vectors and residual are those afqmc_modified_cholesky gives on
+ * the full M^2 x M^2 matrix (pivots on the lower index p M + r of a pair,
+ * equal rows carrying equal vectors), up to the order of the sums.  Other
+ * arguments and the return values as for afqmc_modified_cholesky.
+ */
+AFQMC_API int afqmc_mcd_pairs_workspace_size(int32_t M, int32_t max_vectors, size_t* bytes);
+AFQMC_API int afqmc_modified_cholesky_pairs(int32_t M, const double* d_Vpair, double delta,
+                                            int32_t max_vectors, double* d_L, int32_t* d_piv,
+                                            int32_t* nvec, double* residual, void* d_work,
+                                            size_t work_bytes, void* stream);
+
 /* Message for the calling thread's last failed call (never NULL). */
 AFQMC_API const char* afqmc_last_error(void);
 

@@ -33,7 +33,8 @@ EXPORTED = ["afqmc_default_params", "afqmc_workspace_size", "afqmc_init", "afqmc
             "afqmc_profile_start", "afqmc_profile_stop", "afqmc_local_energies_noalloc",
             "afqmc_group_create", "afqmc_group_propagate", "afqmc_group_destroy",
             "afqmc_wait_flag", "afqmc_taylor_series", "afqmc_mcd_workspace_size",
-            "afqmc_modified_cholesky"]
+            "afqmc_modified_cholesky", "afqmc_mcd_pairs_workspace_size",
+            "afqmc_modified_cholesky_pairs"]
 
 
 class Params(ctypes.Structure):
@@ -112,6 +113,11 @@ def lib():
         "afqmc_modified_cholesky": (ctypes.c_int, [ctypes.c_int64, vp, ctypes.c_double,
                                                    ctypes.c_int32, vp, vp, P(ctypes.c_int32),
                                                    dp, vp, ctypes.c_size_t, vp]),
+        "afqmc_mcd_pairs_workspace_size": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32,
+                                                          P(ctypes.c_size_t)]),
+        "afqmc_modified_cholesky_pairs": (ctypes.c_int, [ctypes.c_int32, vp, ctypes.c_double,
+                                                         ctypes.c_int32, vp, vp, P(ctypes.c_int32),
+                                                         dp, vp, ctypes.c_size_t, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -190,6 +196,32 @@ def afqmc_modified_cholesky(V, delta: float, max_vectors: int, workspace=None):
     st = torch.cuda.current_stream(V.device)
     _check(lib().afqmc_modified_cholesky(
         dim, ctypes.c_void_p(V.data_ptr()), float(delta), max_vectors,
+        ctypes.c_void_p(L.data_ptr()), ctypes.c_void_p(piv.data_ptr()), ctypes.byref(nvec),
+        ctypes.byref(resid), ctypes.c_void_p(workspace.data_ptr()), workspace.numel(),
+        ctypes.c_void_p(st.cuda_stream)))
+    n = nvec.value
+    return L[:n], piv[:n], resid.value
+
+
+def afqmc_modified_cholesky_pairs(Vpair, M: int, delta: float, max_vectors: int,
+                                  workspace=None):
+    """The decomposition over index pairs p <= r of a real-orbital interaction
+    (CUDA float64 Vpair, npair x npair): returns (L [nvec][M][M], pivots as
+    p*M + r, the largest residual diagonal left)."""
+    import torch
+
+    Vpair = Vpair.contiguous()
+    nbytes = ctypes.c_size_t(0)
+    _check(lib().afqmc_mcd_pairs_workspace_size(M, max_vectors, ctypes.byref(nbytes)))
+    if workspace is None or workspace.numel() < nbytes.value:
+        workspace = torch.empty(nbytes.value, dtype=torch.uint8, device=Vpair.device)
+    L = torch.empty((max_vectors, M, M), dtype=torch.float64, device=Vpair.device)
+    piv = torch.empty(max_vectors, dtype=torch.int32, device=Vpair.device)
+    nvec = ctypes.c_int32(0)
+    resid = ctypes.c_double(0.0)
+    st = torch.cuda.current_stream(Vpair.device)
+    _check(lib().afqmc_modified_cholesky_pairs(
+        M, ctypes.c_void_p(Vpair.data_ptr()), float(delta), max_vectors,
         ctypes.c_void_p(L.data_ptr()), ctypes.c_void_p(piv.data_ptr()), ctypes.byref(nvec),
         ctypes.byref(resid), ctypes.c_void_p(workspace.data_ptr()), workspace.numel(),
         ctypes.c_void_p(st.cuda_stream)))

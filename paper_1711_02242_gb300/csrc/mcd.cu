@@ -26,7 +26,6 @@
 #include <type_traits>
 
 #include "kernels.cuh"
-#include "tc.cuh"
 
 namespace afq {
 namespace {
@@ -355,6 +354,96 @@ int mcd_check(int64_t dim, int32_t max_vectors) {
   return AFQMC_OK;
 }
 
+// The decomposition of the dim x dim matrix V into the rows of L (pitch
+// dim), with the workspace laid out by mcd_layout(dim, max_vectors) at base.
+int run_mcd(int64_t dim, const double* d_V, double delta, int32_t max_vectors, double* d_L,
+            int32_t* d_piv, int32_t* nvec, double* residual, char* base, const McdLayout& lay,
+            cudaStream_t s, const char* who) {
+  McdState* st = reinterpret_cast<McdState*>(base + lay.state);
+  McdTree tree{reinterpret_cast<McdPartial*>(base + lay.part),
+               reinterpret_cast<McdPartial*>(base + lay.spart),
+               reinterpret_cast<uint32_t*>(base + lay.sticket)};
+  double* d = reinterpret_cast<double*>(base + lay.d);
+  double* apiv = reinterpret_cast<double*>(base + lay.apiv);
+  const double tau = delta < kScreen ? delta : kScreen;
+  // two indices per lane (16-byte accesses) when dim is even and V, L are
+  // 16-byte aligned
+  const int vec = dim % 2 == 0 && reinterpret_cast<uintptr_t>(d_V) % 16 == 0 &&
+                          reinterpret_cast<uintptr_t>(d_L) % 16 == 0
+                      ? 2
+                      : 1;
+  const size_t smem_max = sizeof(double) * (size_t)max_vectors;
+  auto step = vec == 2 ? k_mcd_step<2> : k_mcd_step<1>;
+  AFQ_CUDA(cudaFuncSetAttribute(step, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem_max));
+  const unsigned grid = (unsigned)((dim + 32 * vec - 1) / (32 * vec));
+  int64_t grid0 = (dim + kThreads - 1) / kThreads;
+  if (grid0 > kInitGrid) grid0 = kInitGrid;
+
+  AFQ_CUDA(cudaMemsetAsync(st, 0, sizeof(McdState), s));
+  AFQ_CUDA(cudaMemsetAsync(base + lay.sticket, 0, lay.d - lay.sticket, s));
+  AFQ_LAUNCH(k_mcd_init, (unsigned)grid0, kThreads, 0, s, d_V, dim, d, delta, max_vectors, tree,
+             st);
+  // Launch iterations in chunks and read the state between chunks; launches
+  // after convergence return at once.  A launch after `launched` others
+  // finds k <= launched earlier vectors, which sizes its shared memory.
+  McdState hs{};
+  int launched = 0;
+  for (;;) {
+    AFQ_CUDA(cudaMemcpyAsync(&hs, st, sizeof hs, cudaMemcpyDeviceToHost, s));
+    AFQ_CUDA(cudaStreamSynchronize(s));
+    if (hs.done || launched >= max_vectors) break;
+    int chunk = launched < 64 ? 16 : 64;
+    if (chunk > max_vectors - launched) chunk = max_vectors - launched;
+    for (int c = 0; c < chunk; ++c) {
+      const size_t smem = sizeof(double) * (size_t)(launched + 1);
+      AFQ_LAUNCH(step, grid, kThreads, smem, s, d_V, dim, d, d_L, apiv, d_piv, delta, tau,
+                 max_vectors, tree, st);
+      ++launched;
+    }
+  }
+  *nvec = hs.n;
+  if (residual) *residual = hs.dmax;
+  if (hs.done == 3) {
+    set_error("%s: non-finite residual after %d vectors", who, hs.n);
+    return AFQMC_ENONFINITE;
+  }
+  return AFQMC_OK;
+}
+
+// Pair index of p <= r: row-major order of the upper triangle.
+__host__ __device__ inline int64_t pair_index(int64_t p, int64_t r, int64_t M) {
+  return p * M - p * (p - 1) / 2 + (r - p);
+}
+
+// L[g][p][r] = L[g][r][p] = Lp[g][pair(min, max)] for the first nvec vectors.
+__global__ void k_mcd_expand(const double* __restrict__ Lp, int64_t npair, int M,
+                             double* __restrict__ L) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= M * M) return;
+  const int p = t / M, r = t - p * M;
+  const int a = p < r ? p : r, b = p < r ? r : p;
+  const int64_t g = blockIdx.y;
+  L[g * M * M + t] = Lp[g * npair + pair_index(a, b, M)];
+}
+
+// Pivots from pair index to p M + r (p <= r).
+__global__ void k_mcd_pivots_full(int32_t* piv, int n, int M) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t P = piv[i];
+  int p = 0;
+  while (p + 1 < M && pair_index(p + 1, p + 1, M) <= P) ++p;
+  piv[i] = (int32_t)(p * (int64_t)M + p + (P - pair_index(p, p, M)));
+}
+
+int64_t npair_of(int64_t M) { return M * (M + 1) / 2; }
+
+size_t mcd_pairs_bytes(int64_t M, int32_t max_vectors) {
+  const int64_t np = npair_of(M);
+  return mcd_layout(np, max_vectors).total + align256(sizeof(double) * (size_t)np * max_vectors);
+}
+
 }  // namespace
 }  // namespace afq
 
@@ -389,56 +478,61 @@ extern "C" AFQMC_API int afqmc_modified_cholesky(int64_t dim, const double* d_V,
     set_error("afqmc_modified_cholesky: workspace %zu bytes, needs %zu", work_bytes, lay.total);
     return AFQMC_ENOSPC;
   }
-  char* base = static_cast<char*>(d_work);
-  McdState* st = reinterpret_cast<McdState*>(base + lay.state);
-  McdTree tree{reinterpret_cast<McdPartial*>(base + lay.part),
-               reinterpret_cast<McdPartial*>(base + lay.spart),
-               reinterpret_cast<uint32_t*>(base + lay.sticket)};
-  double* d = reinterpret_cast<double*>(base + lay.d);
-  double* apiv = reinterpret_cast<double*>(base + lay.apiv);
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const double tau = delta < kScreen ? delta : kScreen;
-  // two indices per lane (16-byte accesses) when dim is even and V, L are
-  // 16-byte aligned
-  const int vec = dim % 2 == 0 && reinterpret_cast<uintptr_t>(d_V) % 16 == 0 &&
-                          reinterpret_cast<uintptr_t>(d_L) % 16 == 0
-                      ? 2
-                      : 1;
-  const unsigned grid = (unsigned)((dim + 32 * vec - 1) / (32 * vec));
-  const size_t smem_max = sizeof(double) * (size_t)max_vectors;
-  auto step = vec == 2 ? k_mcd_step<2> : k_mcd_step<1>;
-  AFQ_CUDA(cudaFuncSetAttribute(step, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem_max));
-  int64_t grid0 = (dim + kThreads - 1) / kThreads;
-  if (grid0 > kInitGrid) grid0 = kInitGrid;
+  return run_mcd(dim, d_V, delta, max_vectors, d_L, d_piv, nvec, residual,
+                 static_cast<char*>(d_work), lay, static_cast<cudaStream_t>(stream),
+                 "afqmc_modified_cholesky");
+}
 
-  AFQ_CUDA(cudaMemsetAsync(st, 0, sizeof(McdState), s));
-  AFQ_CUDA(cudaMemsetAsync(base + lay.sticket, 0, lay.d - lay.sticket, s));
-  AFQ_LAUNCH(k_mcd_init, (unsigned)grid0, kThreads, 0, s, d_V, dim, d, delta, max_vectors, tree,
-             st);
-  // Launch iterations in chunks and read the state between chunks; launches
-  // after convergence return at once.  A launch after `launched` others
-  // finds k <= launched earlier vectors, which sizes its shared memory.
-  McdState hs{};
-  int launched = 0;
-  for (;;) {
-    AFQ_CUDA(cudaMemcpyAsync(&hs, st, sizeof hs, cudaMemcpyDeviceToHost, s));
-    AFQ_CUDA(cudaStreamSynchronize(s));
-    if (hs.done || launched >= max_vectors) break;
-    int chunk = launched < 64 ? 16 : 64;
-    if (chunk > max_vectors - launched) chunk = max_vectors - launched;
-    for (int c = 0; c < chunk; ++c) {
-      const size_t smem = sizeof(double) * (size_t)(launched + 1);
-      AFQ_LAUNCH(step, grid, kThreads, smem, s, d_V, dim, d, d_L, apiv, d_piv, delta, tau,
-                 max_vectors, tree, st);
-      ++launched;
-    }
+extern "C" AFQMC_API int afqmc_mcd_pairs_workspace_size(int32_t M, int32_t max_vectors,
+                                                        size_t* bytes) {
+  using namespace afq;
+  if (!bytes || M < 1 || M > 2048) {
+    set_error("afqmc_mcd_pairs_workspace_size: NULL bytes or M outside [1, 2048]");
+    return AFQMC_EINVAL;
   }
-  *nvec = hs.n;
-  if (residual) *residual = hs.dmax;
-  if (hs.done == 3) {
-    set_error("afqmc_modified_cholesky: non-finite residual after %d vectors", hs.n);
-    return AFQMC_ENONFINITE;
-  }
+  AFQ_TRY(mcd_check(npair_of(M), max_vectors));
+  *bytes = mcd_pairs_bytes(M, max_vectors);
   return AFQMC_OK;
+}
+
+extern "C" AFQMC_API int afqmc_modified_cholesky_pairs(int32_t M, const double* d_Vpair,
+                                                       double delta, int32_t max_vectors,
+                                                       double* d_L, int32_t* d_piv,
+                                                       int32_t* nvec, double* residual,
+                                                       void* d_work, size_t work_bytes,
+                                                       void* stream) {
+  using namespace afq;
+  if (M < 1 || M > 2048) {
+    set_error("afqmc_modified_cholesky_pairs: M=%d outside [1, 2048]", M);
+    return AFQMC_EINVAL;
+  }
+  const int64_t np = npair_of(M);
+  AFQ_TRY(mcd_check(np, max_vectors));
+  if (!d_Vpair || !d_L || !nvec || !d_work || !(delta > 0.0) || !std::isfinite(delta)) {
+    set_error("afqmc_modified_cholesky_pairs: NULL pointer or delta not a positive finite number");
+    return AFQMC_EINVAL;
+  }
+  if (reinterpret_cast<uintptr_t>(d_work) % 256) {
+    set_error("afqmc_modified_cholesky_pairs: workspace not 256-byte aligned");
+    return AFQMC_EINVAL;
+  }
+  if (work_bytes < mcd_pairs_bytes(M, max_vectors)) {
+    set_error("afqmc_modified_cholesky_pairs: workspace %zu bytes, needs %zu", work_bytes,
+              mcd_pairs_bytes(M, max_vectors));
+    return AFQMC_ENOSPC;
+  }
+  const McdLayout lay = mcd_layout(np, max_vectors);
+  char* base = static_cast<char*>(d_work);
+  double* Lp = reinterpret_cast<double*>(base + lay.total);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int rc = run_mcd(np, d_Vpair, delta, max_vectors, Lp, d_piv, nvec, residual, base, lay, s,
+                         "afqmc_modified_cholesky_pairs");
+  if (rc != AFQMC_OK) return rc;
+  if (*nvec > 0) {
+    AFQ_LAUNCH(k_mcd_expand, dim3(cdiv((size_t)M * M, 256), (unsigned)*nvec), 256, 0, s, Lp, np,
+               M, d_L);
+    if (d_piv) AFQ_LAUNCH(k_mcd_pivots_full, cdiv(*nvec, 256), 256, 0, s, d_piv, *nvec, M);
+  }
+  AFQ_CUDA(cudaStreamSynchronize(s));
+  return rc;
 }

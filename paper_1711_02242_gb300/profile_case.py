@@ -9,10 +9,10 @@ about 350 MB on the device, B alone (162 MB BF16) larger than the 129 MB L2.
 Case "fb": the force-bias contraction (A = 1024 x 7600, B = 1800 x 7600).
 Case "taylor": the sixth-order Taylor series of exp(V) on 512 walkers with
 M = 300, N = 25 (afqmc_taylor_series; V is 187 MB in BF16).
-Case "mcd": the modified Cholesky decomposition (afqmc_modified_cholesky,
-delta = 1e-6) of the interaction of the seeded Hamiltonian with `--orbitals`
-M orbitals and 5M vectors (the M^2 x M^2 matrix is 65 GB at M = 300, 5.2 GB
-at M = 160); one launch per vector.
+Case "mcd": the modified Cholesky decomposition over index pairs
+(afqmc_modified_cholesky_pairs, delta = 1e-6) of the interaction of the seeded
+Hamiltonian with `--orbitals` M orbitals and 6M vectors (the pair matrix is
+16.3 GB at M = 300, 1.3 GB at M = 160); one launch per vector.
 Random operands; prints the mean time per launch from CUDA events.
 """
 from __future__ import annotations
@@ -127,21 +127,21 @@ def mcd(a):
     import workloads
 
     M = a.orbitals
-    G = 5 * M
+    G = 6 * M
     _, L, _ = workloads.hamiltonian(M, G, 5000 + M, l_scale=workloads.l_amplitude(M, G))
-    V = workloads.interaction_matrix_device(L)
+    W = workloads.interaction_pairs_device(L)
     del L
     torch.cuda.synchronize()
     times = []
     for _ in range(a.reps):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        Lv, piv, resid = pkg.afqmc_modified_cholesky(V, 1e-6, G + 16)
+        Lv, piv, resid = pkg.afqmc_modified_cholesky_pairs(W, M, 1e-6, G + 16)
         e1.record()
         torch.cuda.synchronize()
         times.append(e0.elapsed_time(e1))
     n = Lv.shape[0]
-    print(f"case mcd M={M} dim={M * M} vectors={n} residual={resid:.3e} "
+    print(f"case mcd M={M} pairs={W.shape[0]} vectors={n} residual={resid:.3e} "
           f"ms={min(times):.3f} per-vector-us={1e3 * min(times) / n:.2f}")
 
 

@@ -71,9 +71,9 @@ def test_library_has_no_oracle_dependency():
 
 def test_mcd_workspace_size_and_validation_without_gpu(built):
     """The decomposition's workspace holds the residual diagonal, the pivot's
-    components and one partial result per 32 indices (the vectors themselves
-    live in the caller's output); bad sizes are refused before any device
-    call."""
+    components and the reduction tree (one result per 32 indices; the vectors
+    themselves live in the caller's output); bad sizes are refused before any
+    device call."""
     lib = built.lib()
     n = ctypes.c_size_t(0)
     assert lib.afqmc_mcd_workspace_size(90000, 1800, ctypes.byref(n)) == 0
@@ -84,3 +84,14 @@ def test_mcd_workspace_size_and_validation_without_gpu(built):
     nv = ctypes.c_int32(0)
     assert lib.afqmc_modified_cholesky(10, None, 1e-6, 10, None, None, ctypes.byref(nv), None,
                                        None, 0, None) == -1
+
+
+def test_mcd_pairs_workspace_size_without_gpu(built):
+    lib = built.lib()
+    n = ctypes.c_size_t(0)
+    assert lib.afqmc_mcd_pairs_workspace_size(300, 1800, ctypes.byref(n)) == 0
+    npair = 300 * 301 // 2
+    assert n.value >= npair * 8 * (1800 + 1) and n.value % 256 == 0
+    assert n.value < npair * 8 * (1800 + 1) + 17 * npair + (4 << 20)
+    for M, mv in ((0, 10), (2049, 10), (10, 0)):
+        assert lib.afqmc_mcd_pairs_workspace_size(M, mv, ctypes.byref(n)) == -1

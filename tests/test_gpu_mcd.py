@@ -9,7 +9,9 @@ vector).  Cases: random positive semi-definite matrices of full and deficient
 rank, the interaction of the 100-orbital, 500-vector workload (dimension 1e4,
 several indices per warp, the launch shape of the benchmark), damped
 prescreening of a tiny diagonal, the vector cap, one-element and zero
-matrices, a non-finite diagonal and argument errors.
+matrices, a non-finite diagonal and argument errors; and the decomposition
+over index pairs p <= r (afqmc_modified_cholesky_pairs) against the oracle
+on the full matrix, with odd and even pair counts.
 """
 import numpy as np
 import pytest
@@ -152,3 +154,23 @@ def test_argument_errors(env):
     assert lib.afqmc_modified_cholesky(*args(8, 1e-6, 8, n.value)) == 0
     torch.cuda.synchronize()
     assert nv.value == 8 and np.allclose(out.cpu().numpy(), np.eye(8)[[0, 1, 2, 3, 4, 5, 6, 7]])
+
+
+@pytest.mark.parametrize("M,G,delta", [(10, 30, 1e-8), (24, 120, 1e-6), (100, 500, 1e-6)])
+def test_pair_space_matches_full_oracle(env, M, G, delta):
+    """afqmc_modified_cholesky_pairs on the pair matrix gives the vectors and
+    pivots the oracle finds on the full M^2 x M^2 matrix (rows (p, r) and
+    (r, p) equal), the vectors exactly symmetric."""
+    torch, pkg = env
+    _, L, _ = workloads.hamiltonian(M, G, 3000 + M, l_scale=workloads.l_amplitude(M, G))
+    W = workloads.interaction_pairs(L)
+    idx = workloads.pair_expansion(M)
+    want = mcd.modified_cholesky(W[idx][:, idx], delta)
+    Lg, piv, resid = pkg.afqmc_modified_cholesky_pairs(torch.from_numpy(W).cuda(), M, delta,
+                                                       G + 16)
+    torch.cuda.synchronize()
+    Lg = Lg.cpu().numpy()
+    assert np.array_equal(Lg, Lg.transpose(0, 2, 1))
+    piv = piv.cpu().numpy().astype(np.int64)
+    assert np.all(piv // M <= piv % M)  # the lower index p*M + r of each pair
+    compare((Lg.reshape(len(piv), M * M), piv, resid), want, M=M)

@@ -44,6 +44,9 @@ __all__ = [
     "request_stream",
     "interaction_matrix",
     "interaction_matrix_device",
+    "interaction_pairs",
+    "interaction_pairs_device",
+    "pair_expansion",
 ]
 
 
@@ -138,6 +141,45 @@ def interaction_matrix(L: np.ndarray) -> np.ndarray:
     return V
 
 
+def pair_expansion(M: int) -> np.ndarray:
+    """Index map (M*M,) from (p, r), row p*M + r, to its pair p' <= r' (row-major
+    order of the upper triangle), so that V = Vpair[idx][:, idx]."""
+    iu = np.triu_indices(M)
+    pair = np.zeros((M, M), np.int64)
+    pair[iu] = np.arange(iu[0].size)
+    pair = pair + np.triu(pair, 1).T
+    return pair.reshape(-1)
+
+
+def interaction_pairs(L: np.ndarray) -> np.ndarray:
+    """The two-electron matrix over index pairs p <= r (row-major upper
+    triangle): Vpair[(p, r)][(q, s)] = sum_g L[g]_pr L[g]_qs, symmetrised so
+    that Vpair == Vpair.T exactly.  Vpair[idx][:, idx] with idx =
+    pair_expansion(M) is the full matrix, rows (p, r) and (r, p) equal."""
+    M = L.shape[1]
+    iu = np.triu_indices(M)
+    Lp = np.ascontiguousarray(L[:, iu[0], iu[1]])
+    W = Lp.T @ Lp
+    W += W.T
+    W *= 0.5
+    return W
+
+
+def interaction_pairs_device(L: np.ndarray, device="cuda:0"):
+    """``interaction_pairs(L)`` built on a CUDA device with PyTorch (16 GB at
+    M = 300)."""
+    import torch
+
+    M = L.shape[1]
+    iu = np.triu_indices(M)
+    Lp = torch.from_numpy(np.ascontiguousarray(L[:, iu[0], iu[1]])).to(device)
+    W = Lp.T @ Lp
+    del Lp
+    W += W.T.clone()
+    W *= 0.5
+    return W
+
+
 def interaction_matrix_device(L: np.ndarray, device="cuda:0"):
     """``interaction_matrix(L)`` built on a CUDA device with PyTorch (for
     interactions too large to form on the host, e.g. M = 300: 65 GB).  The
@@ -152,10 +194,7 @@ def interaction_matrix_device(L: np.ndarray, device="cuda:0"):
     W = Lp.T @ Lp
     del Lp
     W = (W + W.T) * 0.5
-    pair = np.zeros((M, M), np.int64)
-    pair[iu] = np.arange(iu[0].size)
-    pair = pair + np.triu(pair, 1).T
-    idx = torch.from_numpy(pair.reshape(-1)).to(device)
+    idx = torch.from_numpy(pair_expansion(M)).to(device)
     V = W.index_select(0, idx)
     del W
     return V.index_select(1, idx)
