@@ -48,6 +48,15 @@ Readings of the paper taken here (each also listed in the design notes):
   * population control (Sec. 3.4.4, scheme not given in the paper): a
     fixed-size comb, see ``comb``.
   * dead walkers (W = 0) are skipped (algorithm outline, step 2).
+  * back-propagation (Sec. "Computing ground-state properties", Eqs. bp1,
+    Bprod-bp, bp, bp_dets): a window opened at step n keeps Psi_n and the
+    shifted fields x = xi - xbar of every later step; at step n + m,
+    Phi_m = B^+(x_n) ... B^+(x_{n+m-1}) Psi_T with B(x)^+ = B(-conj(x)); the
+    denominator <Psi_{m,w}|Psi_{n,w}> printed in Eq. bp reads
+    <Phi_{m,w}|Psi_{n,w}>.  BP-PRes multiplies W_{n+m} by, per step k of the
+    window, exp(-i dt Im E_loc(Psi_k)) / max(0, cos dtheta_k) (0 where the
+    projection zeroed the walker; the weight cap is not undone).  Windows
+    need population control off.
 """
 from __future__ import annotations
 
@@ -213,6 +222,15 @@ def comb(weights, u):
     return parent, wtot / n
 
 
+def one_body_density(phi_bra, psi):
+    """Spin-summed one-body density <Phi|a+_p a_q|Psi>/<Phi|Psi> between
+    closed-shell determinants (both spin blocks the same M x N matrix), per
+    walker: rho_pq = 2 [Psi (Phi^H Psi)^-1 Phi^H]_qp, shape (W, M, M)."""
+    S = np.conj(np.swapaxes(phi_bra, 1, 2)) @ psi  # Phi^H Psi, (W, N, N)
+    G = psi @ np.linalg.inv(S) @ np.conj(np.swapaxes(phi_bra, 1, 2))  # (W, M, M)
+    return 2.0 * np.swapaxes(G, 1, 2)
+
+
 class Oracle:
     """A population of walkers stepped by the phaseless AFQMC algorithm."""
 
@@ -236,6 +254,7 @@ class Oracle:
         self.wmax = max(100.0, self.W / 10.0) if math.isnan(p.wmax) else float(p.wmax)
         self.records = []  # (step, sum W Re E_loc, sum W)
         self.nonfinite = 0
+        self.bp = None  # back-propagation window (bp_begin .. bp_end)
 
     # --- one step of the random walk (algorithm outline, steps 2-7) -------
     def step(self):
@@ -279,6 +298,22 @@ class Oracle:
             self.logdet[alive] = logdet_new
             self.theta[alive] = theta_new
             self.weight[alive] = w_new
+            if self.bp is not None:
+                xs = np.zeros((self.W, st.nchol), np.complex128)
+                xs[alive] = x
+                self.bp["fields"].append(xs)
+                if p.mode == "phaseless":
+                    # path restoration (BP-PRes): give back the phase of the
+                    # importance function, exp(-i dt Im E_loc(Psi_k)), and undo
+                    # the cosine projection of this step
+                    e_new = local_energy(st, theta_new)
+                    cosd = np.cos(dtheta)
+                    keep = (cosd > 0.0) & ~bad
+                    f = np.where(keep, np.exp(-1j * p.dt * e_new.imag)
+                                 / np.where(keep, cosd, 1.0), 0.0)
+                    self.bp["factor"][alive] *= f
+        elif self.bp is not None:
+            self.bp["fields"].append(np.zeros((self.W, st.nchol), np.complex128))
         self.step_count += 1
         n = self.step_count
         if p.qr_period and n % p.qr_period == 0:
@@ -312,6 +347,37 @@ class Oracle:
         self.logdet = self.logdet[parent].copy()
         self.theta = self.theta[parent].copy()
         self.weight = np.full(self.W, wnew)
+
+    # --- back-propagation (Sec. "Computing ground-state properties") --------
+    def bp_begin(self):
+        """Open a back-propagation window at the current step n: keep Psi_n of
+        every walker and, at every later step, the shifted fields x - xbar that
+        built B (Eq. bp_dets) and the BP-PRes factor of the weight."""
+        if self.p.pc_period:
+            raise ValueError("back-propagation windows need population control off")
+        self.bp = {"psi_n": self.phi.copy(), "fields": [],
+                   "factor": np.ones(self.W, np.complex128)}
+
+    def bp_end(self):
+        """Close the window after m steps: Phi_m = B^+(x_n) ... B^+(x_{n+m-1}) Psi_T
+        (Eq. bp_dets, with B(x)^+ = B(-conj(x)): L_g real symmetric and the Taylor
+        polynomial has real coefficients), and the weighted averages of Eq. bp of
+        the spin-summed one-body density <Phi_m|a+_p a_q|Psi_n>/<Phi_m|Psi_n>:
+        returns (rho BP-PRes with weights W_{n+m} prod_k factor_k, rho BP-PhL
+        with W_{n+m}, the two weight sums, Phi_m)."""
+        st, p = self.setup, self.p
+        bp, self.bp = self.bp, None
+        phi = np.array(np.broadcast_to(st.VT, (self.W, st.M, st.N)), np.complex128)
+        for x in reversed(bp["fields"]):
+            V = assemble_V(st, -np.conj(x))
+            phi = st.Bhalf @ taylor(V, st.Bhalf @ phi, p.taylor_order)
+        alive = np.nonzero(self.weight != 0)[0]
+        rho = one_body_density(phi[alive], bp["psi_n"][alive])
+        w = self.weight[alive]
+        wp = w * bp["factor"][alive]
+        rho_pres = np.einsum("w,wpq->pq", wp, rho) / np.sum(wp)
+        rho_phl = np.einsum("w,wpq->pq", w, rho) / np.sum(w)
+        return rho_pres, rho_phl, complex(np.sum(wp)), complex(np.sum(w)), phi
 
     # --- estimators (Eq. localenergy, Eq. cap) ------------------------------
     def local_energies(self):
