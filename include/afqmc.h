@@ -104,11 +104,15 @@ typedef struct afqmc_params {
                          /* one by one.  Results are identical either way.     */
                          /* 1 needs a stream created by the caller (the legacy */
                          /* default stream cannot be captured): else EINVAL.   */
+  int32_t bp_steps;      /* capacity (steps) of a back-propagation window,      */
+                         /* afqmc_bp_begin / afqmc_bp_end; 0: none.  Float64    */
+                         /* path only (else EUNSUPPORTED)                        */
+  int32_t reserved;      /* must be 0                                          */
 } afqmc_params;
 
 /* Fill *p with the defaults: dt 0.005, e_shift NaN, H0 0, seed 1,
  * taylor_order 6, qr_period 5, pc_period 0, energy_period 1, FP64,
- * phaseless, ecap_C 2, fb_cap 1, wmax NaN, max_records 4096, use_graph 0.  The sizes
+ * phaseless, ecap_C 2, fb_cap 1, wmax NaN, max_records 4096, use_graph 0, bp_steps 0.  The sizes
  * (M, N, nchol, nwalkers) are set to 0 and must be filled in. */
 AFQMC_API void afqmc_default_params(afqmc_params* p);
 
@@ -395,6 +399,39 @@ AFQMC_API int afqmc_local_energies_noalloc(int32_t M, int32_t N, int32_t nchol,
  * by the failure-detection tests.  Asynchronous on `stream`.
  */
 AFQMC_API int afqmc_wait_flag(const int* d_flag, int64_t max_polls, int* d_status, void* stream);
+
+/*
+ * Back-propagation estimator of the one-body density (Sec. "Computing
+ * ground-state properties: the backpropagation algorithm", Eqs. bp1, bp,
+ * bp_dets), on a state created with bp_steps > 0, precision AFQMC_FP64 and
+ * pc_period 0.
+ *
+ * afqmc_bp_begin opens a window at the current step n: it keeps Psi_n of
+ * every walker; each later afqmc_propagate step records the shifted fields
+ * x - xbar of B and, for a phaseless walk, the path-restoration factor
+ * exp(-i dt Im E_loc(Psi_k)) / max(0, cos dtheta_k) (BP-PRes; the local
+ * energies are evaluated every step while the window is open, and the steps
+ * launch kernel by kernel).  At most bp_steps steps fit (afqmc_propagate
+ * returns AFQMC_ENOSPC beyond).  Enqueued on the state's stream.
+ *
+ * afqmc_bp_end closes the window after m steps: the trial is propagated
+ * backwards, Phi_m = B^+(x_n) ... B^+(x_{n+m-1}) Psi_T with
+ * B(x)^+ = B(-conj(x)), and with rho_w,pq = sum_sigma
+ * <Phi_m|a+_p,sigma a_q,sigma|Psi_n> / <Phi_m|Psi_n> it returns (HOST,
+ * row-major, caller-owned)
+ *   rho      [2][M][M]  BP-PRes: sum_w W_w F_w rho_w / sum_w W_w F_w, F_w the
+ *                       product of the window's restoration factors (F = 1
+ *                       in free projection), real plane then imaginary plane
+ *   rho_phl  [2][M][M]  BP-PhL: the same with W_w alone (may be NULL)
+ *   wsums    [4]        sum W F (re, im), sum W (re, im) (may be NULL)
+ *   nsteps   m (may be NULL)
+ * with W_w the weights at step n + m; walkers with W = 0 are left out.  The
+ * walk itself is unchanged and continues with its own weights.  Synchronises
+ * the stream.  AFQMC_ESTATE if no window is open (end) or one is (begin).
+ */
+AFQMC_API int afqmc_bp_begin(afqmc_state* s);
+AFQMC_API int afqmc_bp_end(afqmc_state* s, double* rho, double* rho_phl, double* wsums,
+                           int32_t* nsteps);
 
 /*
  * Modified Cholesky decomposition of the two-electron interaction (Sec. 2.3,

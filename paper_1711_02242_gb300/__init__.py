@@ -34,7 +34,7 @@ EXPORTED = ["afqmc_default_params", "afqmc_workspace_size", "afqmc_init", "afqmc
             "afqmc_group_create", "afqmc_group_propagate", "afqmc_group_destroy",
             "afqmc_wait_flag", "afqmc_taylor_series", "afqmc_mcd_workspace_size",
             "afqmc_modified_cholesky", "afqmc_mcd_pairs_workspace_size",
-            "afqmc_modified_cholesky_pairs"]
+            "afqmc_modified_cholesky_pairs", "afqmc_bp_begin", "afqmc_bp_end"]
 
 
 class Params(ctypes.Structure):
@@ -46,7 +46,8 @@ class Params(ctypes.Structure):
                 ("energy_period", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("mode", ctypes.c_int32), ("ecap_C", ctypes.c_double),
                 ("fb_cap", ctypes.c_double), ("wmax", ctypes.c_double),
-                ("max_records", ctypes.c_int32), ("use_graph", ctypes.c_int32)]
+                ("max_records", ctypes.c_int32), ("use_graph", ctypes.c_int32),
+                ("bp_steps", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
@@ -113,6 +114,8 @@ def lib():
         "afqmc_modified_cholesky": (ctypes.c_int, [ctypes.c_int64, vp, ctypes.c_double,
                                                    ctypes.c_int32, vp, vp, P(ctypes.c_int32),
                                                    dp, vp, ctypes.c_size_t, vp]),
+        "afqmc_bp_begin": (ctypes.c_int, [vp]),
+        "afqmc_bp_end": (ctypes.c_int, [vp, dp, dp, dp, P(ctypes.c_int32)]),
         "afqmc_mcd_pairs_workspace_size": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32,
                                                           P(ctypes.c_size_t)]),
         "afqmc_modified_cholesky_pairs": (ctypes.c_int, [ctypes.c_int32, vp, ctypes.c_double,
@@ -280,6 +283,22 @@ class AfqmcRun:
         out = np.empty((self.p.nwalkers, 2))
         _check(lib().afqmc_local_energies(self.s, _dptr(out)))
         return out[:, 0] + 1j * out[:, 1]
+
+    def bp_begin(self):
+        """Open a back-propagation window at the current step."""
+        _check(lib().afqmc_bp_begin(self.s))
+
+    def bp_end(self):
+        """Close the window: (rho BP-PRes, rho BP-PhL) as complex M x M arrays,
+        (sum W F, sum W) and the window's length in steps."""
+        M = self.p.M
+        rho = np.empty((2, M, M))
+        phl = np.empty((2, M, M))
+        ws = np.empty(4)
+        n = ctypes.c_int32(0)
+        _check(lib().afqmc_bp_end(self.s, _dptr(rho), _dptr(phl), _dptr(ws), ctypes.byref(n)))
+        return (rho[0] + 1j * rho[1], phl[0] + 1j * phl[1], complex(ws[0], ws[1]),
+                complex(ws[2], ws[3]), n.value)
 
     def get_walkers(self):
         W, M, N = self.p.nwalkers, self.p.M, self.p.N

@@ -79,6 +79,17 @@ size_t plan(const afqmc_params& p, Bufs* b, char* base) {
   b->last = a.take<double>(8);
   b->records = a.take<double>(4 * (size_t)(p.max_records > 0 ? p.max_records : 1));
   b->counters = a.take<unsigned long long>(8);
+  if (p.bp_steps > 0 && !mixed) {
+    b->bp_hist = a.take<double>((size_t)p.bp_steps * W * 2 * G);
+    b->bp_psi = a.take<double>(W * 2 * N * M);
+    b->bp_phi = a.take<double>(W * 2 * N * M);
+    b->bp_f = a.take<double>(2 * W);
+    b->bp_cos = a.take<double>(W);
+    b->bp_part = a.take<double>(4 * W);
+    b->bp_red = a.take<double>((size_t)kBpSlices * 2 * M * M);
+    b->bp_R = a.take<double>(4 * M * M);
+    b->bp_out = a.take<double>(4 * M * M + 4);
+  }
   b->mixed = mixed;
   b->lo_kind = mixed ? (lo == 2 ? LO_BF16 : LO_TF32) : LO_NONE;
   b->lo_bytes = (int)lo;
@@ -163,6 +174,14 @@ static int check_params(const afqmc_params* p) {
   if (p->precision != AFQMC_FP64 && p->precision != AFQMC_MIXED_TF32 &&
       p->precision != AFQMC_MIXED_BF16) {
     set_error("precision %d is not available in this build", p->precision);
+    return AFQMC_EUNSUPPORTED;
+  }
+  if (p->bp_steps < 0 || p->reserved != 0) {
+    set_error("bp_steps < 0 or reserved != 0");
+    return AFQMC_EINVAL;
+  }
+  if (p->bp_steps > 0 && p->precision != AFQMC_FP64) {
+    set_error("back-propagation windows run on the float64 path (precision AFQMC_FP64)");
     return AFQMC_EUNSUPPORTED;
   }
   const double P = 0.5 * p->M * (p->M + 1.0);
@@ -256,7 +275,7 @@ int force_bias_gemm(afqmc_state* s) {
   return AFQMC_OK;
 }
 
-int energy_eval(afqmc_state* s, bool append) {
+int energy_eval(afqmc_state* s, bool append, bool record = true) {
   const afqmc_params& p = s->p;
   const Bufs& b = s->b;
   if (!s->t_fresh) AFQ_TRY(force_bias_gemm(s));
@@ -280,6 +299,7 @@ int energy_eval(afqmc_state* s, bool append) {
   ElocArgs el{p.nwalkers, p.M, p.N, p.nchol, b.nchunk, p.H0, b.hh, b.thetaT, b.t, b.part, b.eloc, b.wt};
   el.t32 = b.mixed ? b.t32 : nullptr;
   AFQ_TRY(launch_eloc(el, s->st));
+  if (!record) return AFQMC_OK;
   RecordArgs rc;
   rc.W = p.nwalkers;
   rc.mode = p.mode;
@@ -307,6 +327,7 @@ static int propagate_f64(afqmc_state* s) {
   prof_begin(s, AFQMC_PH_FIELDS);
   AFQ_TRY(launch_field(fa, s->st));
   prof_end(s);
+  if (s->bp_on) AFQ_TRY(bp_record_fields(s));
   // Y = sum_g x_g L_g (packed), the dense contraction with K = N_gamma
   prof_begin(s, AFQMC_PH_V);
   GemmF64 g;
@@ -447,6 +468,7 @@ static int step_once(afqmc_state* s) {
   WeightArgs wa{W, p.mode, p.dt, s->sdt, s->H0p, s->e_shift, s->wmax, b.ld_new, b.ld, b.scal,
                 b.wt, b.counters + CTR_NONFINITE,
                 reinterpret_cast<int64_t*>(b.counters + CTR_STEP)};
+  if (s->bp_on) wa.cosd = b.bp_cos;
   prof_begin(s, AFQMC_PH_WEIGHT);
   AFQ_TRY(launch_weight(wa, s->st));
   prof_end(s);
@@ -470,10 +492,17 @@ static int step_once(afqmc_state* s) {
     AFQ_TRY(refresh_phi_lo(s));
     prof_end(s);
   }
-  if (p.energy_period && n % p.energy_period == 0) {
+  const bool e_due = p.energy_period && n % p.energy_period == 0;
+  if (e_due) {
     prof_begin(s, AFQMC_PH_ENERGY);
     AFQ_TRY(energy_eval(s, true));
     prof_end(s);
+  }
+  if (s->bp_on) {
+    // a back-propagation window needs E_loc of every step (BP-PRes factor)
+    if (!e_due) AFQ_TRY(energy_eval(s, false, false));
+    AFQ_TRY(bp_step_factor(s));
+    s->bp_m += 1;
   }
   return AFQMC_OK;
 }
@@ -773,7 +802,7 @@ static int setup_device(afqmc_state* s, const double* h1, const double* L, const
 
 }  // namespace afq
 
-static_assert(sizeof(afqmc_params) == 104, "afqmc_params layout");
+static_assert(sizeof(afqmc_params) == 112, "afqmc_params layout");
 static_assert(sizeof(afqmc_info) == 64, "afqmc_info layout");
 
 using namespace afq;
@@ -890,11 +919,16 @@ int afqmc_propagate(afqmc_state* s, int32_t nsteps) {
     set_error("nsteps < 0");
     return AFQMC_EINVAL;
   }
+  if (s->bp_on && s->bp_m + (int64_t)nsteps > s->p.bp_steps) {
+    set_error("back-propagation window: %d steps recorded, room for %d", s->bp_m, s->p.bp_steps);
+    return AFQMC_ENOSPC;
+  }
   const int blk = s->graph_block;
   while (nsteps > 0) {
     // whole blocks that start on a block boundary replay the captured graph;
     // the rest (and every step while profiling) launches kernels one by one
-    if (s->p.use_graph && blk > 0 && s->h_step % blk == 0 && nsteps >= blk && !s->prof.on) {
+    if (s->p.use_graph && blk > 0 && s->h_step % blk == 0 && nsteps >= blk && !s->prof.on &&
+        !s->bp_on) {
       s->t_fresh = false;  // the block recomputes the force-bias traces itself
       if (!s->graph) {
         const int64_t l0 = g_launches;
@@ -958,6 +992,49 @@ int afqmc_local_energies(afqmc_state* s, double* eloc) {
   AFQ_CUDA(cudaMemcpyAsync(eloc, s->b.eloc, sizeof(double) * 2 * s->p.nwalkers,
                            cudaMemcpyDeviceToHost, s->st));
   AFQ_CUDA(cudaStreamSynchronize(s->st));
+  return AFQMC_OK;
+}
+
+int afqmc_bp_begin(afqmc_state* s) {
+  AFQ_STATE(s);
+  if (s->p.bp_steps <= 0) {
+    set_error("afqmc_bp_begin: the state has no back-propagation buffers (bp_steps = 0)");
+    return AFQMC_EINVAL;
+  }
+  if (s->p.pc_period) {
+    set_error("afqmc_bp_begin: population control must be off (pc_period = 0)");
+    return AFQMC_EUNSUPPORTED;
+  }
+  if (s->bp_on) {
+    set_error("afqmc_bp_begin: a window is already open");
+    return AFQMC_ESTATE;
+  }
+  return bp_open(s);
+}
+
+int afqmc_bp_end(afqmc_state* s, double* rho, double* rho_phl, double* wsums, int32_t* nsteps) {
+  AFQ_STATE(s);
+  if (!s->bp_on) {
+    set_error("afqmc_bp_end: no open window");
+    return AFQMC_ESTATE;
+  }
+  if (!rho) {
+    set_error("afqmc_bp_end: rho is NULL");
+    return AFQMC_EINVAL;
+  }
+  const int m = s->bp_m;
+  AFQ_TRY(bp_close(s));
+  const size_t MM = (size_t)s->p.M * s->p.M;
+  const Bufs& b = s->b;
+  AFQ_CUDA(cudaMemcpyAsync(rho, b.bp_out, 2 * MM * sizeof(double), cudaMemcpyDeviceToHost, s->st));
+  if (rho_phl)
+    AFQ_CUDA(cudaMemcpyAsync(rho_phl, b.bp_out + 2 * MM, 2 * MM * sizeof(double),
+                             cudaMemcpyDeviceToHost, s->st));
+  if (wsums)
+    AFQ_CUDA(cudaMemcpyAsync(wsums, b.bp_out + 4 * MM, 4 * sizeof(double),
+                             cudaMemcpyDeviceToHost, s->st));
+  AFQ_CUDA(cudaStreamSynchronize(s->st));
+  if (nsteps) *nsteps = m;
   return AFQMC_OK;
 }
 

@@ -109,8 +109,9 @@ extern "C" int afqmc_group_propagate(afqmc_group* g, int32_t nsteps) {
     return AFQMC_EINVAL;
   }
   for (afqmc_state* s : g->states)
-    if (!s->valid || s->h_step % g->blk || s->prof.on) {
-      set_error("group: a state is invalid, profiling, or off a block boundary");
+    if (!s->valid || s->h_step % g->blk || s->prof.on || s->bp_on) {
+      set_error("group: a state is invalid, profiling, in a back-propagation window, or off a "
+                "block boundary");
       return AFQMC_ESTATE;
     }
   for (int done = 0; done < nsteps; done += g->blk) {

@@ -106,6 +106,7 @@ struct WeightArgs {
   double* wt;            // [W][2]
   unsigned long long* nonfinite;
   int64_t* dstep;  // incremented once per step
+  double* cosd = nullptr;  // [W]: cos dtheta of the step (phaseless), when non-null
 };
 int launch_weight(const WeightArgs& a, cudaStream_t st);
 

@@ -39,7 +39,17 @@ struct Bufs {
   void *Bh_lo = nullptr, *V_lo = nullptr, *phi_lo = nullptr, *Tb0 = nullptr, *Tb1 = nullptr;
   float *Bh_tf = nullptr, *acc32 = nullptr;
   int* status = nullptr;  // device status word (tensor-core waits)
+  // back-propagation window (float64 path, afqmc_params.bp_steps > 0):
+  // recorded fields [bp_steps][W][2][G], Psi_n and the back-propagated
+  // orbitals [W][2][N][M], BP-PRes factors [W][2], cos dtheta [W], per-walker
+  // weights [W][4], estimator slices [kBpSlices][2][M][M], R [4][M][M] and
+  // the results [2][2][M][M] + 4 weight sums
+  double *bp_hist = nullptr, *bp_psi = nullptr, *bp_phi = nullptr, *bp_f = nullptr;
+  double *bp_cos = nullptr, *bp_part = nullptr, *bp_red = nullptr, *bp_R = nullptr;
+  double* bp_out = nullptr;
 };
+
+constexpr int kBpSlices = 8;
 
 size_t plan(const afqmc_params& p, Bufs* b, char* base);
 
@@ -75,7 +85,17 @@ struct afqmc_state {
   int64_t graph_kernels = 0;
   // tile widths the autotuner chose for the V and force-bias contractions
   int bn_v = 0, bn_fb = 0;
+  // back-propagation window: open, and steps recorded since it opened
+  bool bp_on = false;
+  int bp_m = 0;
 };
+
+namespace afq {
+int bp_open(afqmc_state* s);
+int bp_close(afqmc_state* s);
+int bp_record_fields(afqmc_state* s);
+int bp_step_factor(afqmc_state* s);
+}  // namespace afq
 
 namespace afq {
 // Open / close a timed phase on the state's stream (no-ops unless profiling).

@@ -506,7 +506,9 @@ __global__ void k_weight(WeightArgs a) {
   double wr, wi;
   if (a.mode == AFQMC_PHASELESS) {
     const double dth = wrap_pi(li);
-    wr = a.wt[2 * w] * exp(lr + s[0] - 0.5 * s[2]) * fmax(0.0, cos(dth));
+    const double cd = cos(dth);
+    if (a.cosd) a.cosd[w] = cd;
+    wr = a.wt[2 * w] * exp(lr + s[0] - 0.5 * s[2]) * fmax(0.0, cd);
     if (!isnan(wr)) wr = fmin(wr, a.wmax);
     wi = 0.0;
   } else {

@@ -44,7 +44,8 @@ def test_params_struct_matches_header_defaults(built):
     assert (p.dt, p.taylor_order, p.qr_period, p.pc_period) == (0.005, 6, 5, 0)
     assert p.ecap_C == 2.0 and p.fb_cap == 1.0 and p.max_records == 4096
     assert p.e_shift != p.e_shift and p.wmax != p.wmax  # NaN defaults
-    assert ctypes.sizeof(built.Params) == 104
+    assert ctypes.sizeof(built.Params) == 112
+    assert p.bp_steps == 0 and p.reserved == 0
 
 
 def test_workspace_size_and_validation_without_gpu(built):

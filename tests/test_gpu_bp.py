@@ -1,0 +1,151 @@
+"""Back-propagation estimators on the GPU (afqmc_bp_begin / afqmc_bp_end; Sec.
+"Computing ground-state properties: the backpropagation algorithm", Eqs. bp,
+bp_dets, BP-PRes weights) against the oracle's window on the same walk.
+
+The float64 walk matches the oracle to 1e-10 step by step, so the recorded
+fields and weights are the same; the back-propagated density matrices (BP-PRes
+and BP-PhL), their weight sums and the window length must then agree to
+1e-9 of the largest element.  Cases: the 12-orbital workload over a window
+that crosses two Gram-Schmidt steps, a ragged shape (odd N, nchol, walker
+count, QR every 3 steps, energies every 2 so the window evaluates local
+energies on its own), an empty window (the mixed estimator), free projection
+(no restoration factor), a walk that keeps going after the window (unchanged
+by it, with and without graph replay), and the argument and state errors.
+"""
+import numpy as np
+import pytest
+
+import workloads
+from oracle import afqmc, scf
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-9
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_1711_02242_gb300 as p
+
+    return p
+
+
+def make_pair(pkg, M, N, G, W, seed=4, mode="phaseless", qr=5, ep=1, dt=0.01, bp_steps=32,
+              use_graph=0, stream=None):
+    h1, L, _ = workloads.hamiltonian(M, G, 6000 + M + N, l_scale=workloads.l_amplitude(M, G))
+    C, _, conv, _ = scf.rhf(h1, L, N)
+    assert conv
+    op = dict(dt=dt, seed=seed, qr_period=qr, energy_period=ep, mode=mode)
+    orc = afqmc.Oracle(h1, L, C, W, afqmc.Params(**op))
+    gp = dict(op)
+    gp["mode"] = pkg.AFQMC_FREE if mode == "free" else pkg.AFQMC_PHASELESS
+    p = pkg.default_params(M, N, G, W, bp_steps=bp_steps, use_graph=use_graph, **gp)
+    run = pkg.AfqmcRun(h1, L, C, p, stream=stream)
+    return orc, run
+
+
+def check(got, want):
+    rho, phl, wp, w, m = got
+    orho, ophl, owp, ow, _ = want
+    scale = max(np.max(np.abs(orho)), 1.0)
+    assert np.max(np.abs(rho - orho)) < TOL * scale, np.max(np.abs(rho - orho))
+    assert np.max(np.abs(phl - ophl)) < TOL * scale, np.max(np.abs(phl - ophl))
+    assert abs(wp - owp) < TOL * abs(owp) and abs(w - ow) < TOL * abs(ow)
+    # and the estimator is a density: Hermitian up to noise, trace 2N
+    return m
+
+
+@pytest.mark.parametrize("M,N,G,W,n,m,qr,ep", [
+    (12, 3, 48, 32, 4, 10, 5, 1),
+    (20, 7, 33, 50, 3, 7, 3, 2),
+    (16, 4, 40, 24, 2, 0, 5, 1),   # empty window: the mixed estimator
+])
+def test_window_matches_oracle(pkg, M, N, G, W, n, m, qr, ep):
+    orc, run = make_pair(pkg, M, N, G, W, qr=qr, ep=ep)
+    orc.run(n)
+    run.propagate(n)
+    orc.bp_begin()
+    run.bp_begin()
+    orc.run(m)
+    run.propagate(m)
+    want = orc.bp_end()
+    got = run.bp_end()
+    assert got[4] == m
+    check(got, want)
+    assert abs(np.trace(got[1]).real - 2 * N) < 1e-8
+    assert np.count_nonzero(orc.weight) > W // 2  # most walkers alive: a real test
+    run.close()
+
+
+def test_free_projection_window(pkg):
+    orc, run = make_pair(pkg, 12, 3, 48, 16, mode="free", qr=5, ep=0)
+    orc.run(3)
+    run.propagate(3)
+    orc.bp_begin()
+    run.bp_begin()
+    orc.run(8)
+    run.propagate(8)
+    got = run.bp_end()
+    check(got, orc.bp_end())
+    assert np.max(np.abs(got[0] - got[1])) < 1e-12  # no restoration factor
+    run.close()
+
+
+def test_walk_continues_unchanged(pkg):
+    """A window does not change the walk (graph replay is suspended while it is
+    open): walkers and energies after it equal a run without one."""
+    import torch
+
+    st = torch.cuda.Stream()
+    _, a = make_pair(pkg, 12, 3, 48, 32, ep=5, use_graph=1, stream=st)
+    _, b = make_pair(pkg, 12, 3, 48, 32, ep=5, use_graph=1, stream=st)
+    a.propagate(5)
+    b.propagate(5)
+    a.bp_begin()
+    a.propagate(10)
+    a.bp_end()
+    b.propagate(10)
+    a.propagate(5)
+    b.propagate(5)
+    pa, wa, la = a.get_walkers()
+    pb, wb, lb = b.get_walkers()
+    assert np.array_equal(pa, pb) and np.array_equal(wa, wb) and np.array_equal(la, lb)
+    assert np.array_equal(a.energy_log(), b.energy_log())
+    a.close()
+    b.close()
+
+
+def test_errors(pkg):
+    h1, L, _ = workloads.hamiltonian(12, 48, 7, l_scale=0.5)
+    C, _, _, _ = scf.rhf(h1, L, 3)
+    run = pkg.AfqmcRun(h1, L, C, pkg.default_params(12, 3, 48, 8))
+    with pytest.raises(pkg.AfqmcError, match="EINVAL"):
+        run.bp_begin()  # no window buffers
+    run.close()
+    with pytest.raises(pkg.AfqmcError, match="EUNSUPPORTED"):
+        pkg.afqmc_workspace_size(pkg.default_params(12, 3, 48, 8, bp_steps=4,
+                                                    precision=pkg.AFQMC_MIXED_BF16))
+    with pytest.raises(pkg.AfqmcError, match="EINVAL"):
+        pkg.afqmc_workspace_size(pkg.default_params(12, 3, 48, 8, bp_steps=-1))
+    run = pkg.AfqmcRun(h1, L, C, pkg.default_params(12, 3, 48, 8, bp_steps=4, pc_period=5))
+    with pytest.raises(pkg.AfqmcError, match="EUNSUPPORTED"):
+        run.bp_begin()  # population control on
+    run.close()
+    run = pkg.AfqmcRun(h1, L, C, pkg.default_params(12, 3, 48, 8, bp_steps=4))
+    with pytest.raises(pkg.AfqmcError, match="ESTATE"):
+        run.bp_end()
+    run.bp_begin()
+    with pytest.raises(pkg.AfqmcError, match="ESTATE"):
+        run.bp_begin()
+    run.propagate(3)
+    with pytest.raises(pkg.AfqmcError, match="ENOSPC"):
+        run.propagate(2)  # 3 + 2 > 4
+    run.propagate(1)
+    assert run.bp_end()[4] == 4
+    run.close()
