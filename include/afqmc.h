@@ -105,8 +105,7 @@ typedef struct afqmc_params {
                          /* 1 needs a stream created by the caller (the legacy */
                          /* default stream cannot be captured): else EINVAL.   */
   int32_t bp_steps;      /* capacity (steps) of a back-propagation window,      */
-                         /* afqmc_bp_begin / afqmc_bp_end; 0: none.  Float64    */
-                         /* path only (else EUNSUPPORTED)                        */
+                         /* afqmc_bp_begin / afqmc_bp_end; 0: none              */
   int32_t reserved;      /* must be 0                                          */
 } afqmc_params;
 
@@ -403,8 +402,10 @@ AFQMC_API int afqmc_wait_flag(const int* d_flag, int64_t max_polls, int* d_statu
 /*
  * Back-propagation estimator of the one-body density (Sec. "Computing
  * ground-state properties: the backpropagation algorithm", Eqs. bp1, bp,
- * bp_dets), on a state created with bp_steps > 0, precision AFQMC_FP64 and
- * pc_period 0.
+ * bp_dets), on a state created with bp_steps > 0 and pc_period 0.  On the
+ * mixed path the fields are recorded as the BF16/TF32 operands the step used
+ * and the backward sweep runs on the tensor cores; the densities and weights
+ * are formed in float64 on both paths.
  *
  * afqmc_bp_begin opens a window at the current step n: it keeps Psi_n of
  * every walker; each later afqmc_propagate step records the shifted fields

@@ -79,8 +79,11 @@ size_t plan(const afqmc_params& p, Bufs* b, char* base) {
   b->last = a.take<double>(8);
   b->records = a.take<double>(4 * (size_t)(p.max_records > 0 ? p.max_records : 1));
   b->counters = a.take<unsigned long long>(8);
-  if (p.bp_steps > 0 && !mixed) {
-    b->bp_hist = a.take<double>((size_t)p.bp_steps * W * 2 * G);
+  if (p.bp_steps > 0) {
+    // recorded fields: float64 [W][2][G], or the operand rows [W][2][Gp]
+    b->bp_hist = mixed ? reinterpret_cast<double*>(a.take<char>((size_t)p.bp_steps * W * 2 * Gp * lo))
+                       : a.take<double>((size_t)p.bp_steps * W * 2 * G);
+    if (mixed) b->bp_phi_lo = a.take<char>(W * 2 * N * Mp * lo);
     b->bp_psi = a.take<double>(W * 2 * N * M);
     b->bp_phi = a.take<double>(W * 2 * N * M);
     b->bp_f = a.take<double>(2 * W);
@@ -180,10 +183,7 @@ static int check_params(const afqmc_params* p) {
     set_error("bp_steps < 0 or reserved != 0");
     return AFQMC_EINVAL;
   }
-  if (p->bp_steps > 0 && p->precision != AFQMC_FP64) {
-    set_error("back-propagation windows run on the float64 path (precision AFQMC_FP64)");
-    return AFQMC_EUNSUPPORTED;
-  }
+
   const double P = 0.5 * p->M * (p->M + 1.0);
   if ((double)p->nwalkers * 2 * p->N > 65535.0 * 64 || P * p->nchol > 4e10) {
     set_error("problem too large for this build");
@@ -316,18 +316,13 @@ int energy_eval(afqmc_state* s, bool append, bool record = true) {
   return AFQMC_OK;
 }
 
-// Float64 propagation: Phi <- B_half T_n(V) B_half Phi, V = i sqrt(dt) sum_g x_g L_g
-// (Eqs. primitive and hs2; Sec. 3.4.2).
-static int propagate_f64(afqmc_state* s) {
+// Float64: phi_out <- B_half T_n(V) B_half phi_in with V = i sqrt(dt) sum_g x_g L_g
+// for the fields in b.x (Eqs. primitive and hs2; Sec. 3.4.2); rows of walkers
+// with W = 0 are not stored when mask is the weights.
+int apply_b_f64(afqmc_state* s, const double* phi_in, double* phi_out, const double* mask) {
   const afqmc_params& p = s->p;
   const Bufs& b = s->b;
   const int W = p.nwalkers, N = p.N, M = p.M, G = p.nchol;
-  FieldArgs fa{W, G, p.mode, p.seed, s->sdt, p.fb_cap, b.t, b.c, b.wt, b.x, b.scal,
-               reinterpret_cast<const int64_t*>(b.counters + CTR_STEP)};
-  prof_begin(s, AFQMC_PH_FIELDS);
-  AFQ_TRY(launch_field(fa, s->st));
-  prof_end(s);
-  if (s->bp_on) AFQ_TRY(bp_record_fields(s));
   // Y = sum_g x_g L_g (packed), the dense contraction with K = N_gamma
   prof_begin(s, AFQMC_PH_V);
   GemmF64 g;
@@ -348,7 +343,7 @@ static int propagate_f64(afqmc_state* s) {
   bh.m = 2 * N * W;
   bh.n = M;
   bh.k = M;
-  bh.A = b.phiT;
+  bh.A = phi_in;
   bh.lda = M;
   bh.B = b.Bh;
   bh.ldb = M;
@@ -368,33 +363,41 @@ static int propagate_f64(afqmc_state* s) {
     tout = t_;
   }
   prof_end(s);
-  // Phi <- B_half acc, stored only for live walkers
+  // Phi <- B_half acc
   prof_begin(s, AFQMC_PH_BHALF);
   bh.A = b.acc;
-  bh.C = b.phiT;
-  bh.mask = b.wt;
-  bh.mask_rows = 2 * N;
+  bh.C = phi_out;
+  if (mask) {
+    bh.mask = mask;
+    bh.mask_rows = 2 * N;
+  }
   AFQ_TRY(gemm_nt_f64(bh, s->st));
   prof_end(s);
   return AFQMC_OK;
 }
 
-// Mixed propagation: the same sequence with every contraction on the tensor
-// cores (BF16 or TF32 operands, FP32 accumulation): V, the first half step,
-// the Taylor series and the last half step (TF32); the orbitals stay float64.
-static int propagate_mixed(afqmc_state* s) {
+static int propagate_f64(afqmc_state* s) {
   const afqmc_params& p = s->p;
   const Bufs& b = s->b;
-  const int W = p.nwalkers, N = p.N, M = p.M, G = p.nchol;
-  FieldArgs fa{W, G, p.mode, p.seed, s->sdt, p.fb_cap, nullptr, b.c, b.wt, nullptr, b.scal,
+  const int W = p.nwalkers, G = p.nchol;
+  FieldArgs fa{W, G, p.mode, p.seed, s->sdt, p.fb_cap, b.t, b.c, b.wt, b.x, b.scal,
                reinterpret_cast<const int64_t*>(b.counters + CTR_STEP)};
-  fa.t32 = b.t32;
-  fa.x_lo = b.x_lo;
-  fa.lo_kind = b.lo_kind;
-  fa.Gp = b.Gp;
   prof_begin(s, AFQMC_PH_FIELDS);
   AFQ_TRY(launch_field(fa, s->st));
   prof_end(s);
+  if (s->bp_on) AFQ_TRY(bp_record_fields(s));
+  return apply_b_f64(s, b.phiT, b.phiT, b.wt);
+}
+
+// Mixed: the same product with every contraction on the tensor cores (BF16 or
+// TF32 operands, FP32 accumulation) for the fields in b.x_lo: V, the first half
+// step from the operand copy phi_lo_in, the Taylor series and the last half
+// step (TF32), which stores float64 orbitals (walkers with W != 0) and their
+// operand copy.
+int apply_b_mixed(afqmc_state* s, const void* phi_lo_in, double* phi_out, void* phi_lo_out) {
+  const afqmc_params& p = s->p;
+  const Bufs& b = s->b;
+  const int W = p.nwalkers, N = p.N, M = p.M, G = p.nchol;
   // V = i sqrt(dt) sum_g x_g L_g over the full (p, q) grid, written straight
   // into the [Re V | Im V] operand rows of the Taylor terms
   prof_begin(s, AFQMC_PH_V);
@@ -417,7 +420,7 @@ static int propagate_mixed(afqmc_state* s) {
   h1.m = 2 * N * W;
   h1.n = M;
   h1.k = M;
-  h1.A = b.phi_lo;
+  h1.A = phi_lo_in;
   h1.lda = b.Mp;
   h1.B = b.Bh_lo;
   h1.ldb = b.Mp;
@@ -445,9 +448,26 @@ static int propagate_mixed(afqmc_state* s) {
   h2.ldb = 2L * b.Mp;
   h2.tf32 = true;
   h2.err = b.status;
-  AFQ_TRY(tc_prop_last(h2, b.phiT, b.wt, N, M, b.phi_lo, b.lo_kind, b.Mp, s->st));
+  AFQ_TRY(tc_prop_last(h2, phi_out, b.wt, N, M, phi_lo_out, b.lo_kind, b.Mp, s->st));
   prof_end(s);
   return AFQMC_OK;
+}
+
+static int propagate_mixed(afqmc_state* s) {
+  const afqmc_params& p = s->p;
+  const Bufs& b = s->b;
+  const int W = p.nwalkers, G = p.nchol;
+  FieldArgs fa{W, G, p.mode, p.seed, s->sdt, p.fb_cap, nullptr, b.c, b.wt, nullptr, b.scal,
+               reinterpret_cast<const int64_t*>(b.counters + CTR_STEP)};
+  fa.t32 = b.t32;
+  fa.x_lo = b.x_lo;
+  fa.lo_kind = b.lo_kind;
+  fa.Gp = b.Gp;
+  prof_begin(s, AFQMC_PH_FIELDS);
+  AFQ_TRY(launch_field(fa, s->st));
+  prof_end(s);
+  if (s->bp_on) AFQ_TRY(bp_record_fields(s));
+  return apply_b_mixed(s, b.phi_lo, b.phiT, b.phi_lo);
 }
 
 static int step_once(afqmc_state* s) {

@@ -1,14 +1,16 @@
 // Back-propagation estimators of ground-state properties (Sec. "Computing
 // ground-state properties: the backpropagation algorithm", Eqs. bp1, bp,
-// bp_dets), float64 path.
+// bp_dets), on the float64 and the mixed path.
 //
 // A window opened at step n (afqmc_bp_begin) keeps Psi_n of every walker and,
 // at each later step, the shifted fields x = xi - xbar that built B(x) and the
 // BP-PRes factor exp(-i dt Im E_loc(Psi_k)) / max(0, cos dtheta_k).  At step
 // n + m (afqmc_bp_end) the trial is propagated backwards,
 //     Phi_m = B^+(x_n) ... B^+(x_{n+m-1}) Psi_T,   B(x)^+ = B(-conj(x)),
-// with the forward kernels (V assembly, half steps, Taylor terms, Gram-Schmidt)
-// fed the conjugated, negated fields; then per walker
+// with the forward kernels (V assembly, half steps, Taylor terms, Gram-Schmidt;
+// on the mixed path the tensor-core ones, fed the recorded operand-format
+// fields with the real plane's sign flipped) fed the conjugated, negated
+// fields; then, in float64, per walker
 //     rho_w = 2 [Psi_n (Phi_m^H Psi_n)^-1 Phi_m^H]^T  (spin summed)
 // and the weighted averages of Eq. bp with W_{n+m} prod_k factor_k (BP-PRes)
 // and with W_{n+m} (BP-PhL).  The run's trial-adapted basis is rotated back
@@ -77,6 +79,22 @@ __global__ void k_bp_fields(long n, int G, const double* hist, double* x) {
        t += (long)gridDim.x * blockDim.x) {
     const bool re = ((t / G) & 1) == 0;
     x[t] = re ? -hist[t] : hist[t];
+  }
+}
+
+// The same in the operand format (BF16, or TF32 in FP32 containers): the
+// real plane's sign bit flipped (exact), rows [W][2][Gp].
+__global__ void k_bp_fields_lo(long n, int Gp, int bytes, const void* hist, void* x) {
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n;
+       t += (long)gridDim.x * blockDim.x) {
+    const bool re = ((t / Gp) & 1) == 0;
+    if (bytes == 2) {
+      const uint16_t v = static_cast<const uint16_t*>(hist)[t];
+      static_cast<uint16_t*>(x)[t] = re ? (uint16_t)(v ^ 0x8000u) : v;
+    } else {
+      const uint32_t v = static_cast<const uint32_t*>(hist)[t];
+      static_cast<uint32_t*>(x)[t] = re ? (v ^ 0x80000000u) : v;
+    }
   }
 }
 
@@ -294,11 +312,17 @@ __global__ void k_bp_scale(long MM, const double* R, const double* sums, int off
 
 }  // namespace
 
+// Bytes of one step's recorded fields, and where they come from.
+size_t bp_field_bytes(const afqmc_params& p, const Bufs& b) {
+  return b.mixed ? (size_t)p.nwalkers * 2 * b.Gp * b.lo_bytes
+                 : (size_t)p.nwalkers * 2 * p.nchol * sizeof(double);
+}
+
 int bp_record_fields(afqmc_state* s) {
-  const afqmc_params& p = s->p;
   const Bufs& b = s->b;
-  const size_t n = (size_t)p.nwalkers * 2 * p.nchol;
-  AFQ_CUDA(cudaMemcpyAsync(b.bp_hist + (size_t)s->bp_m * n, b.x, n * sizeof(double),
+  const size_t n = bp_field_bytes(s->p, b);
+  char* dst = reinterpret_cast<char*>(b.bp_hist) + (size_t)s->bp_m * n;
+  AFQ_CUDA(cudaMemcpyAsync(dst, b.mixed ? b.x_lo : static_cast<const void*>(b.x), n,
                            cudaMemcpyDeviceToDevice, s->st));
   return AFQMC_OK;
 }
@@ -334,47 +358,27 @@ int bp_close(afqmc_state* s) {
   s->bp_on = false;
   AFQ_LAUNCH(k_bp_trial, cdiv((size_t)W * 2 * NM, 256), 256, 0, st, (long)W * 2 * NM, N, M,
              b.bp_phi);
+  if (b.mixed)
+    AFQ_TRY(launch_convert_lo(b.bp_phi, 2L * N * W, M, M, b.bp_phi_lo, b.Mp, b.lo_kind, st));
+  const size_t fbytes = bp_field_bytes(p, b);
   for (int k = s->bp_m - 1, done = 1; k >= 0; --k, ++done) {
-    const long nx = (long)W * 2 * G;
-    AFQ_LAUNCH(k_bp_fields, cdiv(nx, 256), 256, 0, st, nx, G, b.bp_hist + (size_t)k * nx, b.x);
-    // Y = sum_g (-conj x_g) L_g, then Phi <- B_half T_n(V) B_half Phi
-    GemmF64 g;
-    g.m = 2 * W;
-    g.n = b.P;
-    g.k = G;
-    g.A = b.x;
-    g.lda = G;
-    g.B = b.LpT;
-    g.ldb = G;
-    g.C = b.Y;
-    g.ldc = b.P;
-    AFQ_TRY(gemm_nt_f64(g, st));
-    GemmF64 bh;
-    bh.m = 2 * N * W;
-    bh.n = M;
-    bh.k = M;
-    bh.A = b.bp_phi;
-    bh.lda = M;
-    bh.B = b.Bh;
-    bh.ldb = M;
-    bh.C = b.T0;
-    bh.ldc = M;
-    AFQ_TRY(gemm_nt_f64(bh, st));
-    double* tin = b.T0;
-    double* tout = b.T1;
-    for (int t = 1; t <= p.taylor_order; ++t) {
-      TaylorArgsT<double> ta{W, M, N, b.P, t, (long)b.P, s->sdt / t, b.Y, tin, tout, b.acc};
-      AFQ_TRY(launch_taylor_term(ta, st));
-      double* t_ = tin;
-      tin = tout;
-      tout = t_;
+    const char* hk = reinterpret_cast<const char*>(b.bp_hist) + (size_t)k * fbytes;
+    // the fields of B^+ (-conj x), then Phi <- B_half T_n(V) B_half Phi
+    if (b.mixed) {
+      const long nx = (long)W * 2 * b.Gp;
+      AFQ_LAUNCH(k_bp_fields_lo, cdiv(nx, 256), 256, 0, st, nx, b.Gp, b.lo_bytes, hk, b.x_lo);
+      AFQ_TRY(apply_b_mixed(s, b.bp_phi_lo, b.bp_phi, b.bp_phi_lo));
+    } else {
+      const long nx = (long)W * 2 * G;
+      AFQ_LAUNCH(k_bp_fields, cdiv(nx, 256), 256, 0, st, nx, G,
+                 reinterpret_cast<const double*>(hk), b.x);
+      AFQ_TRY(apply_b_f64(s, b.bp_phi, b.bp_phi, nullptr));
     }
-    bh.A = b.acc;
-    bh.C = b.bp_phi;
-    AFQ_TRY(gemm_nt_f64(bh, st));
     if (p.qr_period && done % p.qr_period == 0) {
       MgsArgs ma{W, M, N, b.bp_phi, b.wt, b.tmp_ld};
       AFQ_TRY(launch_mgs(ma, st));
+      if (b.mixed)
+        AFQ_TRY(launch_convert_lo(b.bp_phi, 2L * N * W, M, M, b.bp_phi_lo, b.Mp, b.lo_kind, st));
     }
   }
   // per-walker (Phi^H Psi)^-1 and the scaled Theta rows (T0: BP-PRes, T1: BP-PhL)

@@ -39,14 +39,15 @@ struct Bufs {
   void *Bh_lo = nullptr, *V_lo = nullptr, *phi_lo = nullptr, *Tb0 = nullptr, *Tb1 = nullptr;
   float *Bh_tf = nullptr, *acc32 = nullptr;
   int* status = nullptr;  // device status word (tensor-core waits)
-  // back-propagation window (float64 path, afqmc_params.bp_steps > 0):
-  // recorded fields [bp_steps][W][2][G], Psi_n and the back-propagated
+  // back-propagation window (afqmc_params.bp_steps > 0): recorded fields
+  // [bp_steps][W][2][G] float64 (mixed path: operand rows [W][2][Gp]), Psi_n and the back-propagated
   // orbitals [W][2][N][M], BP-PRes factors [W][2], cos dtheta [W], per-walker
   // weights [W][4], estimator slices [kBpSlices][2][M][M], R [4][M][M] and
   // the results [2][2][M][M] + 4 weight sums
   double *bp_hist = nullptr, *bp_psi = nullptr, *bp_phi = nullptr, *bp_f = nullptr;
   double *bp_cos = nullptr, *bp_part = nullptr, *bp_red = nullptr, *bp_R = nullptr;
   double* bp_out = nullptr;
+  void* bp_phi_lo = nullptr;  // mixed path: operand copy of the back-propagated orbitals
 };
 
 constexpr int kBpSlices = 8;
@@ -95,6 +96,8 @@ int bp_open(afqmc_state* s);
 int bp_close(afqmc_state* s);
 int bp_record_fields(afqmc_state* s);
 int bp_step_factor(afqmc_state* s);
+int apply_b_f64(afqmc_state* s, const double* phi_in, double* phi_out, const double* mask);
+int apply_b_mixed(afqmc_state* s, const void* phi_lo_in, double* phi_out, void* phi_lo_out);
 }  // namespace afq
 
 namespace afq {

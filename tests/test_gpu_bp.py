@@ -11,6 +11,9 @@ count, QR every 3 steps, energies every 2 so the window evaluates local
 energies on its own), an empty window (the mixed estimator), free projection
 (no restoration factor), a walk that keeps going after the window (unchanged
 by it, with and without graph replay), and the argument and state errors.
+The mixed path's window (BF16/TF32 fields and tensor-core backward sweep) is
+held to the float64 path's on the same system within the operand rounding
+(measured 8e-4 BF16, 2e-4 TF32 of the largest element; bound 4e-3 / 1e-3).
 """
 import numpy as np
 import pytest
@@ -128,9 +131,6 @@ def test_errors(pkg):
     with pytest.raises(pkg.AfqmcError, match="EINVAL"):
         run.bp_begin()  # no window buffers
     run.close()
-    with pytest.raises(pkg.AfqmcError, match="EUNSUPPORTED"):
-        pkg.afqmc_workspace_size(pkg.default_params(12, 3, 48, 8, bp_steps=4,
-                                                    precision=pkg.AFQMC_MIXED_BF16))
     with pytest.raises(pkg.AfqmcError, match="EINVAL"):
         pkg.afqmc_workspace_size(pkg.default_params(12, 3, 48, 8, bp_steps=-1))
     run = pkg.AfqmcRun(h1, L, C, pkg.default_params(12, 3, 48, 8, bp_steps=4, pc_period=5))
@@ -149,3 +149,38 @@ def test_errors(pkg):
     run.propagate(1)
     assert run.bp_end()[4] == 4
     run.close()
+
+
+@pytest.mark.parametrize("prec,tol", [(2, 4e-3), (1, 1e-3)])
+def test_mixed_path_window_close_to_float64(pkg, prec, tol):
+    """The mixed path's window (fields recorded as BF16/TF32 operands, backward
+    sweep on the tensor cores, densities in float64) against the float64
+    path's on the same system, seed and steps: the two walks differ by the
+    operand rounding only, and so do the densities."""
+    out = []
+    for precision in (0, prec):
+        h1, L, _ = workloads.hamiltonian(24, 120, 6100, l_scale=workloads.l_amplitude(24, 120))
+        C, _, _, _ = scf.rhf(h1, L, 4)
+        p = pkg.default_params(24, 4, 120, 64, dt=0.01, seed=3, qr_period=5, energy_period=1,
+                               bp_steps=8, precision=precision)
+        run = pkg.AfqmcRun(h1, L, C, p)
+        run.propagate(3)
+        run.bp_begin()
+        run.propagate(6)
+        out.append(run.bp_end())
+        if precision == 0:
+            run.bp_begin()  # empty window at the same step: the mixed estimator
+            mixed_est = run.bp_end()[1]
+        assert run.info().status == 0
+        run.close()
+    (r0, p0, w0, v0, _), (r1, p1, w1, v1, _) = out
+    scale = np.max(np.abs(r0))
+    d_pres = np.max(np.abs(r1 - r0)) / scale
+    d_phl = np.max(np.abs(p1 - p0)) / scale
+    d_bp = np.max(np.abs(p0 - mixed_est)) / scale
+    print(f"mixed precision {prec}: BP-PRes {d_pres:.2e} BP-PhL {d_phl:.2e}; "
+          f"back-propagated vs mixed estimator {d_bp:.2e}")
+    assert d_pres < tol and d_phl < tol
+    assert abs(np.trace(p1).real - 8) < 1e-8
+    # six steps of back-propagation move the density by more than the rounding
+    assert d_bp > 3 * max(d_pres, d_phl)
