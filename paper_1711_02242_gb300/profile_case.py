@@ -1,7 +1,8 @@
 """A single contraction of the M=300 step, for kernel profiling.
 
-    python -m paper_1711_02242_gb300.profile_case [--case v|fb|taylor|mcd] [--dtype bf16|tf32]
+    python -m paper_1711_02242_gb300.profile_case [--case v|fb|taylor|mcd|bp] [--dtype bf16|tf32|fp64]
                                                   [--reps 3] [--walkers 512] [--orbitals 300]
+                                                  [--window 20]
 
 Case "v": V = sum_g x_g L_g as afqmc_contract with the M=300 shapes
 (A = 1024 x 1800 fields, B = 45150 x 1800 packed Cholesky vectors, C FP32):
@@ -13,12 +14,17 @@ Case "mcd": the modified Cholesky decomposition over index pairs
 (afqmc_modified_cholesky_pairs, delta = 1e-6) of the interaction of the seeded
 Hamiltonian with `--orbitals` M orbitals and 6M vectors (the pair matrix is
 16.3 GB at M = 300, 1.3 GB at M = 160); one launch per vector.
+Case "bp": the M=300 walk (512 walkers, 1800 vectors, RHF trial) with a
+back-propagation window of `--window` steps: time per step without and with
+the window open, and the time of afqmc_bp_end (backward sweep and densities).
 Random operands; prints the mean time per launch from CUDA events.
 """
 from __future__ import annotations
 
 import argparse
 import ctypes
+
+import numpy as np
 
 import paper_1711_02242_gb300 as pkg
 
@@ -27,10 +33,11 @@ def main():
     import torch
 
     ap = argparse.ArgumentParser()
-    ap.add_argument("--case", default="v", choices=["v", "fb", "taylor", "mcd"])
+    ap.add_argument("--case", default="v", choices=["v", "fb", "taylor", "mcd", "bp"])
+    ap.add_argument("--window", type=int, default=20)
     ap.add_argument("--orbitals", type=int, default=300)
     ap.add_argument("--walkers", type=int, default=512)
-    ap.add_argument("--dtype", default="bf16", choices=["bf16", "tf32"])
+    ap.add_argument("--dtype", default="bf16", choices=["bf16", "tf32", "fp64"])
     ap.add_argument("--reps", type=int, default=3)
     a = ap.parse_args()
     from paper_1711_02242_gb300 import build as b
@@ -40,6 +47,8 @@ def main():
         return taylor(a)
     if a.case == "mcd":
         return mcd(a)
+    if a.case == "bp":
+        return bp(a)
     if a.case == "v":
         m, n, k, pitch = 1024, 45150, 1800, 1800
     else:
@@ -143,6 +152,48 @@ def mcd(a):
     n = Lv.shape[0]
     print(f"case mcd M={M} pairs={W.shape[0]} vectors={n} residual={resid:.3e} "
           f"ms={min(times):.3f} per-vector-us={1e3 * min(times) / n:.2f}")
+
+
+def bp(a):
+    import time
+
+    import torch
+
+    import workloads
+    from paper_1711_02242_gb300.rhf import rhf_trial
+
+    w = workloads.config("c2")
+    h1, L, H0 = w.hamiltonian()
+    C, _, _ = rhf_trial(h1, L, w.N, max_iter=25)
+    prec = {"fp64": 0, "tf32": 1, "bf16": 2}[a.dtype]
+    m = a.window
+    p = pkg.default_params(w.M, w.N, w.nchol, w.nwalkers, dt=w.dt, seed=w.seed, H0=H0,
+                           qr_period=w.qr_period, energy_period=w.energy_period, precision=prec,
+                           bp_steps=m)
+    st = torch.cuda.Stream()
+    run = pkg.AfqmcRun(h1, L, C, p, stream=st)
+    run.propagate(10)
+    st.synchronize()
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        fn()
+        e1.record(st)
+        st.synchronize()
+        return e0.elapsed_time(e1)
+
+    t_plain = timed(lambda: run.propagate(m))
+    run.bp_begin()
+    t_window = timed(lambda: run.propagate(m))
+    t0 = time.perf_counter()
+    rho, phl, wp, wsum, n = run.bp_end()
+    t_end = 1e3 * (time.perf_counter() - t0)
+    print(f"case bp {a.dtype} M={w.M} walkers={w.nwalkers} window={n}: "
+          f"ms/step plain={t_plain / m:.3f} window-open={t_window / m:.3f}; "
+          f"bp_end ms={t_end:.2f}; trace(rho_PRes)={np.trace(rho).real:.6f} "
+          f"|sum W F|/sum W={abs(wp) / abs(wsum):.4f}; status={run.info().status}")
+    run.close()
 
 
 if __name__ == "__main__":
