@@ -59,14 +59,16 @@ def peaks():
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 
 # DRAM bytes (read + write) per launch from one ncu capture of the M=300 BF16
-# step, with the SHA-256 of the source file the kernel was built from; a
-# figure whose source has changed since is reported as null.
+# step (energy: the exchange contraction, the phase's main kernel), with the
+# SHA-256 of the source file the kernel was built from; a figure whose source
+# has changed since is reported as null.
 TRAFFIC = {
-    "theta": {"bytes": (64.496128 + 30.346240) * 1e6, "sha": "004a95623cddb44574b90f88ec68835a3b661bb5614f289f67f091d90d5c8b4d"},
-    "overlap": {"bytes": 8.258816e6, "sha": "004a95623cddb44574b90f88ec68835a3b661bb5614f289f67f091d90d5c8b4d"},
-    "qr": {"bytes": (61.484800 + 26.066176) * 1e6, "sha": "004a95623cddb44574b90f88ec68835a3b661bb5614f289f67f091d90d5c8b4d"},
-    "taylor": {"bytes": (218.395392 + 20.219648) * 1e6, "sha": "7d84c2b3465f764bb47983565617111a70bc45f2b5fbc4a888a139d84b0bbc1f"},
-    "v_assembly": {"bytes": (332.216320 + 154.316032) * 1e6, "sha": "2a0d3c3691ec05bb86922022bf9219e589e16cc3c047a97f45a1de565fe02fb6"},
+    "theta": {"bytes": (64.455168 + 30.120960) * 1e6, "sha": "a5d4696939acc04c20f26f3758050afa1bf5ec5d00500917703b04c95e24fe6c"},
+    "overlap": {"bytes": (8.237824 + 0.000000) * 1e6, "sha": "a5d4696939acc04c20f26f3758050afa1bf5ec5d00500917703b04c95e24fe6c"},
+    "qr": {"bytes": (61.481472 + 34.750720) * 1e6, "sha": "a5d4696939acc04c20f26f3758050afa1bf5ec5d00500917703b04c95e24fe6c"},
+    "taylor": {"bytes": (218.370560 + 19.842816) * 1e6, "sha": "7d84c2b3465f764bb47983565617111a70bc45f2b5fbc4a888a139d84b0bbc1f"},
+    "v_assembly": {"bytes": (332.382976 + 149.079296) * 1e6, "sha": "ae969ee56811ec9bc4c2b56e7d5c69d033e3462e42e4082180d39f310ded3dac"},
+    "energy": {"bytes": (42.972160 + 0.425216) * 1e6, "sha": "ae969ee56811ec9bc4c2b56e7d5c69d033e3462e42e4082180d39f310ded3dac"},
 }
 
 
