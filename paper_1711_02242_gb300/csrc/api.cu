@@ -100,7 +100,9 @@ size_t plan(const afqmc_params& p, Bufs* b, char* base) {
   b->Mp = (int)Mp;
   b->Pp = (long)Pp;
   if (mixed) {
-    b->LfT_lo = a.take<char>(M * Mp * Gp * lo);  // full vectors, rows (p, q) = p*Mp + q
+    // Cholesky operand of V: the upper 16 x 16 blocks of each vector, 256 rows per block
+    b->nblkV = (int)((Mp / 16) * (Mp / 16 + 1) / 2);
+    b->LbT_lo = a.take<char>((size_t)b->nblkV * 256 * Gp * lo);
     b->Lh_lo = a.take<char>(G * N * Mp * lo);
     b->x_lo = a.take<char>(W * 2 * Gp * lo);
     b->th_lo = a.take<char>(W * 2 * N * Mp * lo);
@@ -398,16 +400,17 @@ int apply_b_mixed(afqmc_state* s, const void* phi_lo_in, double* phi_out, void* 
   const afqmc_params& p = s->p;
   const Bufs& b = s->b;
   const int W = p.nwalkers, N = p.N, M = p.M, G = p.nchol;
-  // V = i sqrt(dt) sum_g x_g L_g over the full (p, q) grid, written straight
-  // into the [Re V | Im V] operand rows of the Taylor terms
+  // V = i sqrt(dt) sum_g x_g L_g over the upper 16 x 16 blocks of the (p, q)
+  // grid (V is symmetric), each block and its mirror written straight into
+  // the [Re V | Im V] operand rows of the Taylor terms
   prof_begin(s, AFQMC_PH_V);
   TcGemm g;
   g.m = 2 * W;
-  g.n = M * b.Mp;
+  g.n = b.nblkV * 256;
   g.k = G;
   g.A = b.x_lo;
   g.lda = b.Gp;
-  g.B = b.LfT_lo;
+  g.B = b.LbT_lo;
   g.ldb = b.Gp;
   g.tf32 = b.lo_kind == LO_TF32;
   g.err = b.status;
@@ -762,7 +765,7 @@ static int setup_device(afqmc_state* s, const double* h1, const double* L, const
   s->H0p = p.H0 - 0.5 * sumc2;
   if (b.mixed) {
     // BF16 / TF32 copies of the contraction operands (zero-padded pitches)
-    AFQ_TRY(launch_pack_full_lo(b.Lfull, G, M, b.Mp, b.Gp, b.LfT_lo, b.lo_kind, st));
+    AFQ_TRY(launch_pack_blocks_lo(b.Lfull, G, M, b.Mp, b.Gp, b.LbT_lo, b.lo_kind, st));
     AFQ_TRY(launch_convert_lo(b.Lh, (long)G * N, M, M, b.Lh_lo, b.Mp, b.lo_kind, st));
     AFQ_CUDA(cudaMemsetAsync(b.th_lo, 0, (size_t)W * 2 * N * b.Mp * b.lo_bytes, st));
     AFQ_CUDA(cudaMemsetAsync(b.x_lo, 0, (size_t)W * 2 * b.Gp * b.lo_bytes, st));

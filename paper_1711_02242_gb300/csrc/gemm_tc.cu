@@ -360,6 +360,23 @@ __device__ __forceinline__ void store16_lo(void* base, int kind, long idx, const
   }
 }
 
+__device__ __forceinline__ void store8_lo(void* base, int kind, long idx, const float* v,
+                                          float sign) {
+  if (kind == LO_BF16) {
+    uint4 w;
+    __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(&w);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) h[i] = __floats2bfloat162_rn(sign * v[2 * i], sign * v[2 * i + 1]);
+    *reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(base) + idx) = w;
+  } else {
+    float4* d = reinterpret_cast<float4*>(reinterpret_cast<float*>(base) + idx);
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+      d[i] = make_float4(round_tf32(sign * v[4 * i]), round_tf32(sign * v[4 * i + 1]),
+                         round_tf32(sign * v[4 * i + 2]), round_tf32(sign * v[4 * i + 3]));
+  }
+}
+
 // First half step: rows (w,c,i) of Phi^T, columns p; D = (B_half Phi)^T.
 // acc[(w,c,i)][p] = D (FP32, pitch ldacc) and Tb holds the 0th Taylor term.
 // Each thread owns one row and 16 consecutive p per chunk: vector stores.
@@ -494,25 +511,55 @@ struct EpiV {
   float sdt;
   __device__ __forceinline__ int m_origin(int bx, int) const { return bx * BM * kMT; }
   __device__ __forceinline__ int n_origin(int, int by) const { return by * 256; }
+  // Output tile by = one 16 x 16 block (P, Q), P <= Q, of the symmetric V:
+  // column pp * 16 + qq of the tile is V[16 P + pp][16 Q + qq].  The thread of
+  // row (w, c) writes the block's 16 rows (16 contiguous q each) and, off the
+  // diagonal, the mirrored block's 16 rows (V[q][p] = V[p][q]) in two halves
+  // of 8 contiguous p.
   template <int BN>
   __device__ __forceinline__ void run(uint32_t tmem, int q, int lane, int, int, int, int m0, int n0,
                                       int, int, float*) const {
+    static_assert(BN == 256, "one 16 x 16 block per tile");
     const int row = m0 + 32 * q + lane;
     const bool valid = row < 2 * W;
     const int w = row >> 1, c = row & 1;
     const float sign = c ? -sdt : sdt;
+    const int nb = Mp / 16;
+    int P = 0, rem = n0 / 256;
+    while (rem >= nb - P) {
+      rem -= nb - P;
+      ++P;
+    }
+    const int Q = P + rem;
+    const long vb = (long)w * M * 2L * Mp + (c ? 0 : Mp);
 #pragma unroll 1
-    for (int c0 = 0; c0 < BN; c0 += 16) {
-      float v[16];
-      tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c0, v);
-      const int col = n0 + c0;  // p * Mp + q0, q0 a multiple of 16 within row p
-      const int p = col / Mp, q0 = col % Mp;
-      if (!valid || p >= M) continue;
-      const long base = ((long)w * M + p) * 2L * Mp + (c ? 0 : Mp) + q0;
-      if (q0 + 16 <= Mp) {
-        store16_lo(V, lo_kind, base, v, sign);
-      } else {
-        for (int u = 0; u < Mp - q0; ++u) store_lo(V, lo_kind, base + u, sign * v[u]);
+    for (int h = 0; h < 2; ++h) {
+      uint32_t r[8][16];
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        tmem_ld16_async(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)((8 * h + u) * 16), r[u]);
+      tmem_ld_wait();
+      if (!valid) continue;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int p = 16 * P + 8 * h + u;
+        if (p < M) {
+          float v[16];
+#pragma unroll
+          for (int t = 0; t < 16; ++t) v[t] = __uint_as_float(r[u][t]);
+          store16_lo(V, lo_kind, vb + (long)p * 2 * Mp + 16 * Q, v, sign);
+        }
+      }
+      if (P == Q) continue;
+#pragma unroll
+      for (int t = 0; t < 16; ++t) {
+        const int qr = 16 * Q + t;
+        if (qr < M) {
+          float v[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) v[u] = __uint_as_float(r[u][t]);
+          store8_lo(V, lo_kind, vb + (long)qr * 2 * Mp + 16 * P + 8 * h, v, sign);
+        }
       }
     }
   }
@@ -841,8 +888,14 @@ int tc_v_full(const TcGemm& g, void* V, int lo_kind, int W, int M, int Mp, doubl
     set_error("tc V: Mp=%d must be a multiple of 16", Mp);
     return AFQMC_EINVAL;
   }
+  const int nb = Mp / 16;
+  if (g.n != nb * (nb + 1) / 2 * 256) {
+    set_error("tc V: %d operand rows, the %d upper 16 x 16 blocks of Mp=%d need %d", g.n,
+              nb * (nb + 1) / 2, Mp, nb * (nb + 1) / 2 * 256);
+    return AFQMC_EINVAL;
+  }
   tc::EpiV e{V, lo_kind, W, M, Mp, (float)sdt};
-  const int gx = cdiv(g.m, tc::BM * tc::EpiV::kMT), gy = cdiv(g.n, 256);
+  const int gx = cdiv(g.m, tc::BM * tc::EpiV::kMT), gy = nb * (nb + 1) / 2;
   if (g.tf32) return launch_tc_persistent<256, 3, true>(g, e, gx, gy, st);
   return launch_tc_persistent<256, 3, false>(g, e, gx, gy, st);
 }

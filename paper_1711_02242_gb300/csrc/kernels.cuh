@@ -187,7 +187,7 @@ int launch_convert_lo(const double* src, long rows, long cols, long lds, void* d
                       int kind, cudaStream_t st);
 int launch_convert_f32(const double* src, float* dst, long n, cudaStream_t st);
 // full Cholesky vectors transposed, rows (p, q) = p * Mp + q, pitch Gp, low precision
-int launch_pack_full_lo(const double* L, int G, int M, int Mp, int Gp, void* out, int kind,
-                        cudaStream_t st);
+int launch_pack_blocks_lo(const double* L, int G, int M, int Mp, int Gp, void* out, int kind,
+                          cudaStream_t st);
 
 }  // namespace afq

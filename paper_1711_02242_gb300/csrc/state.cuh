@@ -30,8 +30,10 @@ struct Bufs {
   bool mixed = false;
   int lo_kind = 0, lo_bytes = 0, Gp = 0, Mp = 0;
   long Pp = 0;
-  // LfT_lo: full Cholesky vectors transposed, rows (p, q) = p * Mp + q, pitch Gp
-  void *LfT_lo = nullptr, *Lh_lo = nullptr, *x_lo = nullptr, *th_lo = nullptr;
+  // LbT_lo: Cholesky vectors transposed over the upper 16 x 16 blocks (P <= Q)
+  // of each Mp x Mp vector, rows blk * 256 + pp * 16 + qq, pitch Gp
+  void *LbT_lo = nullptr, *Lh_lo = nullptr, *x_lo = nullptr, *th_lo = nullptr;
+  int nblkV = 0;
   float* t32 = nullptr;
   // tensor-core propagation: exp(-dt v0'/2) as BF16/TF32 and TF32 [M][Mp],
   // V operand [W*M][2Mp], orbitals [W*2N][Mp], series sum [W*2N][Mp] FP32,

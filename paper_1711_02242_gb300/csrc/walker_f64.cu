@@ -1099,24 +1099,41 @@ __global__ void k_convert_f32(const double* src, float* dst, long n) {
 // Full Cholesky vectors, transposed, in BF16/TF32 for the mixed V contraction:
 // row (p, q) = p * Mp + q holds L[g][p][q] over g (pitch Gp); rows with q >= M
 // and columns g >= G are zero.  32 x 32 tiles of (q, g) per block, one p.
-__global__ void k_pack_full_lo(const double* L, int G, int M, int Mp, int Gp, void* out, int kind) {
-  __shared__ double tile[32][33];
-  const int g0 = blockIdx.x * 32, p = blockIdx.y, q0 = blockIdx.z * 32;
-  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-    const int g = g0 + r, q = q0 + threadIdx.x;
-    tile[r][threadIdx.x] = (g < G && q < M) ? L[((long)g * M + p) * M + q] : 0.0;
+// The Cholesky operand of the V contraction: the upper 16 x 16 blocks (P, Q),
+// P <= Q, of each Mp x Mp vector L[g] (zero beyond M), row-major over the
+// blocks; row blk * 256 + pp * 16 + qq of out holds L[g][16 P + pp][16 Q + qq]
+// for g < Gp (zero for g >= G).  Block (x, y): 32 vectors, one (blk, pp) row.
+__global__ void k_pack_blocks_lo(const double* L, int G, int M, int Mp, int Gp, void* out,
+                                 int kind) {
+  __shared__ double tile[32][17];
+  const int g0 = blockIdx.x * 32;
+  const int blk = blockIdx.y >> 4, pp = blockIdx.y & 15;
+  const int nb = Mp / 16;
+  int P = 0, rem = blk;
+  while (rem >= nb - P) {
+    rem -= nb - P;
+    ++P;
+  }
+  const int Q = P + rem;
+  const int p = 16 * P + pp, q0 = 16 * Q;
+  for (int e = threadIdx.x; e < 32 * 16; e += blockDim.x) {
+    const int r = e >> 4, c = e & 15;
+    const int g = g0 + r, q = q0 + c;
+    tile[r][c] = (g < G && p < M && q < M) ? L[((long)g * M + p) * M + q] : 0.0;
   }
   __syncthreads();
-  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-    const int q = q0 + r, g = g0 + threadIdx.x;
-    if (q < Mp && g < Gp) store_lo(out, kind, ((long)p * Mp + q) * Gp + g, tile[threadIdx.x][r]);
+  const long n0 = (long)blk * 256 + pp * 16;
+  for (int e = threadIdx.x; e < 32 * 16; e += blockDim.x) {
+    const int c = e >> 5, r = e & 31;
+    if (g0 + r < Gp) store_lo(out, kind, (n0 + c) * Gp + g0 + r, tile[r][c]);
   }
 }
 
-int launch_pack_full_lo(const double* L, int G, int M, int Mp, int Gp, void* out, int kind,
-                        cudaStream_t st) {
-  dim3 grid(cdiv(Gp, 32), M, cdiv(Mp, 32));
-  AFQ_LAUNCH(k_pack_full_lo, grid, dim3(32, 8), 0, st, L, G, M, Mp, Gp, out, kind);
+int launch_pack_blocks_lo(const double* L, int G, int M, int Mp, int Gp, void* out, int kind,
+                          cudaStream_t st) {
+  const int nb = Mp / 16;
+  dim3 grid(cdiv(Gp, 32), nb * (nb + 1) / 2 * 16);
+  AFQ_LAUNCH(k_pack_blocks_lo, grid, 256, 0, st, L, G, M, Mp, Gp, out, kind);
   return AFQMC_OK;
 }
 
