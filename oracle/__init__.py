@@ -6,4 +6,4 @@ space results and library routines in ``tests/``.  It shares no code with the
 GPU library.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
 ``cpu_baseline`` leg of ``bench.py`` may import it.
 """
-from . import afqmc, mcd, philox, scf  # noqa: F401
+from . import afqmc, mcd, multidet, philox, scf  # noqa: F401
