@@ -106,12 +106,15 @@ typedef struct afqmc_params {
                          /* default stream cannot be captured): else EINVAL.   */
   int32_t bp_steps;      /* capacity (steps) of a back-propagation window,      */
                          /* afqmc_bp_begin / afqmc_bp_end; 0: none              */
-  int32_t reserved;      /* must be 0                                          */
+  int32_t ndet;          /* determinants of a multi-determinant trial          */
+                         /* (afqmc_init_multidet); 0: the single RHF trial of  */
+                         /* afqmc_init                                          */
 } afqmc_params;
 
 /* Fill *p with the defaults: dt 0.005, e_shift NaN, H0 0, seed 1,
  * taylor_order 6, qr_period 5, pc_period 0, energy_period 1, FP64,
- * phaseless, ecap_C 2, fb_cap 1, wmax NaN, max_records 4096, use_graph 0, bp_steps 0.  The sizes
+ * phaseless, ecap_C 2, fb_cap 1, wmax NaN, max_records 4096, use_graph 0, bp_steps 0,
+ * ndet 0.  The sizes
  * (M, N, nchol, nwalkers) are set to 0 and must be filled in. */
 AFQMC_API void afqmc_default_params(afqmc_params* p);
 
@@ -140,6 +143,28 @@ typedef struct afqmc_state afqmc_state; /* opaque */
 AFQMC_API int afqmc_init(const afqmc_params* p, const double* h1, const double* L,
                const double* trial, void* d_workspace, size_t ws_bytes,
                void* stream, afqmc_state** out);
+
+/*
+ * The same with a multi-determinant trial Psi_T = sum_d A_d Psi_d (Sec. 3.4,
+ * Eqs. usesherman, precomputing2, localenergy2/3), p->ndet = ndet >= 1:
+ *   coef      [ndet][2]     A_d (real, imaginary)
+ *   trial_up  [ndet][M][N]  spin-up orbitals of each determinant, and
+ *   trial_dn  [ndet][M][N]  spin-down orbitals, orthonormal columns each
+ * all host, row-major float64.  Walkers stay closed shell (both spin blocks
+ * the same orbitals; the propagator keeps them so) and start at the leading
+ * spin-up orbitals trial_up[0]; the overlap is
+ * sum_d A_d^* det(V_du^T Phi) det(V_dd^T Phi), the force bias and the local
+ * energy are the determinant-weighted sums of Eqs. precomputing2 and
+ * localenergy3; the mean-field background comes from determinant 0,
+ * c_g = Tr(L_g (P_0u + P_0d)), and E_T is the local energy of the initial
+ * walkers.  Float64 path, phaseless, population control off, no
+ * back-propagation window (else AFQMC_EUNSUPPORTED).  Everything else as
+ * afqmc_init.
+ */
+AFQMC_API int afqmc_init_multidet(const afqmc_params* p, const double* h1, const double* L,
+                                  int32_t ndet, const double* coef, const double* trial_up,
+                                  const double* trial_dn, void* d_workspace, size_t ws_bytes,
+                                  void* stream, afqmc_state** out);
 
 /*
  * Enqueue nsteps steps of the random walk (algorithm outline, steps 2-9):

@@ -29,10 +29,17 @@ Readings (the paper leaves them open):
     c_g = Tr(L_g (P_0u + P_0d)), P_0s = V_0s V_0s^T (any c_g keeps the
     Hamiltonian exact; Sec. 2.4).
   * the walkers start at phi = V_0u, and E_T is the mixed local energy there.
-  * a determinant with det(V_ds^T phi) = 0 has weight 0 and no Theta.
-  * the Sherman-Morrison-Woodbury speed-up for determinants that differ by a
-    few orbitals is not used: every determinant is handled in full (the
-    results are the same).
+  * a determinant with det(V_ds^T phi) = 0 has weight 0 and no Theta.  This
+    is the right limit only when H does not connect Psi_d to the walker; for a
+    determinant orthogonal (or nearly so) to a walker, w_d E_d and w_d Tr(...)
+    are 0/0 limits that this per-determinant evaluation does not resolve, so
+    the method is meant for non-orthogonal determinants (e.g. different
+    rotations of a reference), not for CI expansions about the walkers' own
+    determinant.
+  * the Sherman-Morrison-Woodbury evaluation relative to a reference
+    determinant (which resolves those limits and is faster for determinants
+    that differ by a few orbitals) is not used: every determinant is handled
+    in full.
 
 The walk itself (fields, propagation, phaseless weights, Gram-Schmidt, energy
 records) follows oracle.afqmc.Oracle step for step.

@@ -34,7 +34,8 @@ EXPORTED = ["afqmc_default_params", "afqmc_workspace_size", "afqmc_init", "afqmc
             "afqmc_group_create", "afqmc_group_propagate", "afqmc_group_destroy",
             "afqmc_wait_flag", "afqmc_taylor_series", "afqmc_mcd_workspace_size",
             "afqmc_modified_cholesky", "afqmc_mcd_pairs_workspace_size",
-            "afqmc_modified_cholesky_pairs", "afqmc_bp_begin", "afqmc_bp_end"]
+            "afqmc_modified_cholesky_pairs", "afqmc_bp_begin", "afqmc_bp_end",
+            "afqmc_init_multidet"]
 
 
 class Params(ctypes.Structure):
@@ -47,7 +48,7 @@ class Params(ctypes.Structure):
                 ("mode", ctypes.c_int32), ("ecap_C", ctypes.c_double),
                 ("fb_cap", ctypes.c_double), ("wmax", ctypes.c_double),
                 ("max_records", ctypes.c_int32), ("use_graph", ctypes.c_int32),
-                ("bp_steps", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("bp_steps", ctypes.c_int32), ("ndet", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
@@ -114,6 +115,8 @@ def lib():
         "afqmc_modified_cholesky": (ctypes.c_int, [ctypes.c_int64, vp, ctypes.c_double,
                                                    ctypes.c_int32, vp, vp, P(ctypes.c_int32),
                                                    dp, vp, ctypes.c_size_t, vp]),
+        "afqmc_init_multidet": (ctypes.c_int, [P(Params), dp, dp, ctypes.c_int32, dp, dp, dp, vp,
+                                               ctypes.c_size_t, vp, P(vp)]),
         "afqmc_bp_begin": (ctypes.c_int, [vp]),
         "afqmc_bp_end": (ctypes.c_int, [vp, dp, dp, dp, P(ctypes.c_int32)]),
         "afqmc_mcd_pairs_workspace_size": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32,
@@ -241,6 +244,9 @@ class AfqmcRun:
 
     def __init__(self, h1, L, trial, params: Params, device="cuda:0", stream=None,
                  workspace=None):
+        """trial: the RHF orbitals [M][N], or for a multi-determinant trial
+        (params.ndet >= 1) a tuple (coefficients [ndet] complex, spin-up orbitals
+        [ndet][M][N], spin-down orbitals [ndet][M][N])."""
         import torch
 
         self.p = params
@@ -258,15 +264,32 @@ class AfqmcRun:
         self.stream = stream
         h1 = np.ascontiguousarray(h1, np.float64)
         L = np.ascontiguousarray(L, np.float64)
-        trial = np.ascontiguousarray(trial, np.float64)
-        if h1.shape != (params.M, params.M) or L.shape != (params.nchol, params.M, params.M) \
-                or trial.shape != (params.M, params.N):
+        if h1.shape != (params.M, params.M) or L.shape != (params.nchol, params.M, params.M):
             raise AfqmcError("input shapes do not match the parameters")
         st = ctypes.c_void_p()
-        with torch.cuda.device(self.device):
-            rc = lib().afqmc_init(ctypes.byref(params), _dptr(h1), _dptr(L), _dptr(trial),
-                                  ctypes.c_void_p(base + off), ctypes.c_size_t(workspace.numel() - off),
-                                  ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(st))
+        ws_ptr = ctypes.c_void_p(base + off)
+        ws_len = ctypes.c_size_t(workspace.numel() - off)
+        sptr = ctypes.c_void_p(self.stream.cuda_stream)
+        if params.ndet > 0:
+            coef, up, dn = trial
+            nd = params.ndet
+            coef = np.asarray(coef, np.complex128).reshape(nd)
+            cf = np.ascontiguousarray(np.stack([coef.real, coef.imag], -1))
+            up = np.ascontiguousarray(up, np.float64)
+            dn = np.ascontiguousarray(dn, np.float64)
+            if up.shape != (nd, params.M, params.N) or dn.shape != up.shape:
+                raise AfqmcError("trial orbitals must be [ndet][M][N]")
+            with torch.cuda.device(self.device):
+                rc = lib().afqmc_init_multidet(ctypes.byref(params), _dptr(h1), _dptr(L), nd,
+                                               _dptr(cf), _dptr(up), _dptr(dn), ws_ptr, ws_len,
+                                               sptr, ctypes.byref(st))
+        else:
+            trial = np.ascontiguousarray(trial, np.float64)
+            if trial.shape != (params.M, params.N):
+                raise AfqmcError("input shapes do not match the parameters")
+            with torch.cuda.device(self.device):
+                rc = lib().afqmc_init(ctypes.byref(params), _dptr(h1), _dptr(L), _dptr(trial),
+                                      ws_ptr, ws_len, sptr, ctypes.byref(st))
         _check(rc)
         self.s = st
 

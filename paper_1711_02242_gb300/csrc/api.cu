@@ -79,6 +79,18 @@ size_t plan(const afqmc_params& p, Bufs* b, char* base) {
   b->last = a.take<double>(8);
   b->records = a.take<double>(4 * (size_t)(p.max_records > 0 ? p.max_records : 1));
   b->counters = a.take<unsigned long long>(8);
+  if (p.ndet > 0) {
+    const size_t nd2 = 2 * (size_t)p.ndet;
+    b->md_V = a.take<double>(nd2 * N * M);
+    b->md_Lh = a.take<double>(nd2 * G * N * M);
+    b->md_hh = a.take<double>(nd2 * N * M);
+    b->md_theta = a.take<double>(nd2 * W * 2 * N * M);
+    b->md_ld = a.take<double>(W * nd2 * 2);
+    b->md_w = a.take<double>(W * (size_t)p.ndet * 2);
+    b->md_C = a.take<double>(nd2 * 2 * W * G);
+    b->md_part = a.take<double>(nd2 * W * nchunk * 2);
+    b->md_logA = a.take<double>(nd2);
+  }
   if (p.bp_steps > 0) {
     // recorded fields: float64 [W][2][G], or the operand rows [W][2][Gp]
     b->bp_hist = mixed ? reinterpret_cast<double*>(a.take<char>((size_t)p.bp_steps * W * 2 * Gp * lo))
@@ -181,9 +193,15 @@ static int check_params(const afqmc_params* p) {
     set_error("precision %d is not available in this build", p->precision);
     return AFQMC_EUNSUPPORTED;
   }
-  if (p->bp_steps < 0 || p->reserved != 0) {
-    set_error("bp_steps < 0 or reserved != 0");
+  if (p->bp_steps < 0 || p->ndet < 0) {
+    set_error("bp_steps < 0 or ndet < 0");
     return AFQMC_EINVAL;
+  }
+  if (p->ndet > 0 && (p->precision != AFQMC_FP64 || p->pc_period || p->bp_steps ||
+                      p->mode != AFQMC_PHASELESS)) {
+    set_error("a multi-determinant trial runs on the float64 path, phaseless, without population "
+              "control or back-propagation");
+    return AFQMC_EUNSUPPORTED;
   }
 
   const double P = 0.5 * p->M * (p->M + 1.0);
@@ -222,6 +240,12 @@ int refresh_phi_lo(afqmc_state* s) {
 int overlap_update(afqmc_state* s, bool into_ld, bool timed) {
   const afqmc_params& p = s->p;
   const Bufs& b = s->b;
+  if (p.ndet > 0) {
+    if (timed) prof_begin(s, AFQMC_PH_OVERLAP);
+    AFQ_TRY(md_overlap_update(s, into_ld));
+    if (timed) prof_end(s);
+    return AFQMC_OK;
+  }
   // S = V_T^T Phi, S^-1, log det and Theta in one float64 kernel per walker
   OverlapArgs ov{p.nwalkers, p.M, p.N, b.VTt, b.phiT, b.thetaT, into_ld ? b.ld : b.ld_new, b.wt};
   ov.unit_trial = 1;  // V_T' = [I_N; 0] in the trial-adapted basis
@@ -245,6 +269,11 @@ int overlap_update(afqmc_state* s, bool into_ld, bool timed) {
 int force_bias_gemm(afqmc_state* s) {
   const afqmc_params& p = s->p;
   const Bufs& b = s->b;
+  if (p.ndet > 0) {
+    AFQ_TRY(md_force_bias(s));
+    s->t_fresh = true;
+    return AFQMC_OK;
+  }
   if (b.mixed) {
     // t[(w,c)][g] = 2 sum_(i,p) Theta^T_lo[(w,c)][(i,p)] Lh_lo[g][(i,p)] on tcgen05
     TcGemm g;
@@ -281,7 +310,9 @@ int energy_eval(afqmc_state* s, bool append, bool record = true) {
   const afqmc_params& p = s->p;
   const Bufs& b = s->b;
   if (!s->t_fresh) AFQ_TRY(force_bias_gemm(s));
-  if (b.mixed) {
+  if (p.ndet > 0) {
+    AFQ_TRY(md_local_energies(s));
+  } else if (b.mixed) {
     // T_g = Lh_g Theta for all (g, w) on tcgen05, sum_ij T_ij T_ji in the epilogue
     TcGemm g;
     g.m = p.nchol * p.N;
@@ -298,9 +329,12 @@ int energy_eval(afqmc_state* s, bool append, bool record = true) {
     ExchArgs ex{p.nwalkers, p.M, p.N, p.nchol, b.gc, b.nchunk, b.Lh, b.thetaT, b.part, b.wt};
     AFQ_TRY(launch_exchange(ex, s->st));
   }
-  ElocArgs el{p.nwalkers, p.M, p.N, p.nchol, b.nchunk, p.H0, b.hh, b.thetaT, b.t, b.part, b.eloc, b.wt};
-  el.t32 = b.mixed ? b.t32 : nullptr;
-  AFQ_TRY(launch_eloc(el, s->st));
+  if (p.ndet == 0) {
+    ElocArgs el{p.nwalkers, p.M, p.N, p.nchol, b.nchunk, p.H0, b.hh, b.thetaT, b.t, b.part, b.eloc,
+                b.wt};
+    el.t32 = b.mixed ? b.t32 : nullptr;
+    AFQ_TRY(launch_eloc(el, s->st));
+  }
   if (!record) return AFQMC_OK;
   RecordArgs rc;
   rc.W = p.nwalkers;
@@ -659,25 +693,60 @@ static int gemm_sq(const double* A, long sA, const double* B, long sB, double* C
 // what changes is that S = V_T'^T Phi' is the top N x N block of Phi' (no
 // product) and the top N rows of Theta' = Phi' S^-1 are the identity.
 // Walkers cross the API in the caller's basis: Phi = Q Phi'.
-static int setup_device(afqmc_state* s, const double* h1, const double* L, const double* trial) {
-  const afqmc_params& p = s->p;
-  const Bufs& b = s->b;
-  const int M = p.M, N = p.N, G = p.nchol, W = p.nwalkers;
-  cudaStream_t st = s->st;
-  // the trial's columns must be orthonormal
+// max |V^T V - I| of an M x N row-major matrix
+static double orthonormality_error(const double* V, int M, int N) {
   double dev = 0.0;
   for (int i = 0; i < N; ++i)
     for (int j = 0; j <= i; ++j) {
       double d = 0.0;
-      for (int q = 0; q < M; ++q) d += trial[(size_t)q * N + i] * trial[(size_t)q * N + j];
+      for (int q = 0; q < M; ++q) d += V[(size_t)q * N + i] * V[(size_t)q * N + j];
       dev = std::fmax(dev, std::fabs(d - (i == j ? 1.0 : 0.0)));
     }
-  if (!(dev < 1e-8)) {
-    set_error("trial columns are not orthonormal (max |V^T V - I| = %.3g)", dev);
-    return AFQMC_EINVAL;
+  return dev;
+}
+
+// md_coef / md_up / md_dn: a multi-determinant trial (p.ndet >= 1), whose
+// leading spin-up orbitals md_up[0] are then the trial of the basis and of
+// the initial walkers.
+static int setup_device(afqmc_state* s, const double* h1, const double* L, const double* trial,
+                        const double* md_coef = nullptr, const double* md_up = nullptr,
+                        const double* md_dn = nullptr) {
+  const afqmc_params& p = s->p;
+  const Bufs& b = s->b;
+  const int M = p.M, N = p.N, G = p.nchol, W = p.nwalkers;
+  cudaStream_t st = s->st;
+  const bool md = p.ndet > 0;
+  if (md) trial = md_up;
+  // the trial's columns must be orthonormal
+  for (int ds = 0; ds < (md ? 2 * p.ndet : 1); ++ds) {
+    const double* V = md ? ((ds & 1) ? md_dn : md_up) + (size_t)(ds >> 1) * M * N : trial;
+    const double dev = orthonormality_error(V, M, N);
+    if (!(dev < 1e-8)) {
+      set_error("trial columns are not orthonormal (determinant %d spin %d: max |V^T V - I| = "
+                "%.3g)", ds >> 1, ds & 1, dev);
+      return AFQMC_EINVAL;
+    }
   }
   std::vector<double> qh, qt((size_t)M * M), vtt((size_t)N * M, 0.0);
   complete_basis(trial, M, N, qh);
+  if (md) {
+    // the determinants' orbitals in the run's basis, V' = Q^T V, stored as
+    // rows i = column i: [2 ndet][N][M]
+    std::vector<double> mv((size_t)2 * p.ndet * N * M, 0.0);
+    for (int ds = 0; ds < 2 * p.ndet; ++ds) {
+      const double* V = ((ds & 1) ? md_dn : md_up) + (size_t)(ds >> 1) * M * N;
+      double* o = mv.data() + (size_t)ds * N * M;
+      for (int r = 0; r < M; ++r)
+        for (int i = 0; i < N; ++i) {
+          const double v = V[(size_t)r * N + i];
+          if (v == 0.0) continue;
+          for (int q = 0; q < M; ++q) o[(size_t)i * M + q] += v * qh[(size_t)r * M + q];
+        }
+    }
+    AFQ_CUDA(cudaMemcpyAsync(b.md_V, mv.data(), sizeof(double) * mv.size(),
+                             cudaMemcpyHostToDevice, st));
+    AFQ_CUDA(cudaStreamSynchronize(st));
+  }
   for (int r = 0; r < M; ++r)
     for (int c = 0; c < M; ++c) qt[(size_t)c * M + r] = qh[(size_t)r * M + c];
   for (int i = 0; i < N; ++i) vtt[(size_t)i * M + i] = 1.0;
@@ -726,8 +795,12 @@ static int setup_device(afqmc_state* s, const double* h1, const double* L, const
     h.ldc = M;
     AFQ_TRY(gemm_nt_f64(h, st));
   }
-  // c_g = 2 Tr(L_g P) = 2 Tr(Lh_g V_T): vbar_g = i c_g (Sec. 2.4)
-  AFQ_TRY(launch_rowdot(b.Lh, b.VTt, b.c, G, N * M, 2.0, st));
+  // c_g = 2 Tr(L_g P) = 2 Tr(Lh_g V_T): vbar_g = i c_g (Sec. 2.4); with a
+  // multi-determinant trial the leading determinant's Tr(L_g (P_0u + P_0d))
+  if (md)
+    AFQ_TRY(md_setup(s, md_coef));
+  else
+    AFQ_TRY(launch_rowdot(b.Lh, b.VTt, b.c, G, N * M, 2.0, st));
   // sum_g L_g L_g
   {
     GemmF64 g;
@@ -862,18 +935,14 @@ int afqmc_workspace_size(const afqmc_params* p, size_t* bytes) {
   return AFQMC_OK;
 }
 
-int afqmc_init(const afqmc_params* p, const double* h1, const double* L, const double* trial,
-               void* d_workspace, size_t ws_bytes, void* stream, afqmc_state** out) {
-  if (!out) {
-    set_error("out is NULL");
-    return AFQMC_EINVAL;
-  }
-  *out = nullptr;
-  AFQ_TRY(check_params(p));
-  if (!h1 || !L || !trial || !d_workspace) {
-    set_error("h1, L, trial and d_workspace are required");
-    return AFQMC_EINVAL;
-  }
+}  // extern "C"
+
+// Workspace checks, the state, the device set-up and the graph block, for
+// afqmc_init (trial) and afqmc_init_multidet (md_*).
+static int init_state(const afqmc_params* p, const double* h1, const double* L,
+                      const double* trial, const double* md_coef, const double* md_up,
+                      const double* md_dn, void* d_workspace, size_t ws_bytes, void* stream,
+                      afqmc_state** out) {
   if (reinterpret_cast<uintptr_t>(d_workspace) % 256) {
     set_error("workspace must be 256-byte aligned");
     return AFQMC_EINVAL;
@@ -889,8 +958,15 @@ int afqmc_init(const afqmc_params* p, const double* h1, const double* L, const d
     return AFQMC_ENOSPC;
   }
   const size_t M = p->M, N = p->N, G = p->nchol;
+  const size_t nd = p->ndet > 0 ? p->ndet : 0;
   AFQ_TRY(all_finite(h1, M * M, "h1"));
-  AFQ_TRY(all_finite(trial, M * N, "trial"));
+  if (nd) {
+    AFQ_TRY(all_finite(md_coef, 2 * nd, "coef"));
+    AFQ_TRY(all_finite(md_up, nd * M * N, "trial_up"));
+    AFQ_TRY(all_finite(md_dn, nd * M * N, "trial_dn"));
+  } else {
+    AFQ_TRY(all_finite(trial, M * N, "trial"));
+  }
   AFQ_TRY(all_finite(L, G * M * M, "L"));
   afqmc_state* s = new (std::nothrow) afqmc_state();
   if (!s) {
@@ -903,7 +979,7 @@ int afqmc_init(const afqmc_params* p, const double* h1, const double* L, const d
   s->ws_bytes = ws_bytes;
   plan(*p, &s->b, s->ws);
   s->sdt = std::sqrt(p->dt);
-  int r = setup_device(s, h1, L, trial);
+  int r = setup_device(s, h1, L, trial, md_coef, md_up, md_dn);
   if (r != AFQMC_OK) {
     delete s;
     return r;
@@ -926,6 +1002,50 @@ int afqmc_init(const afqmc_params* p, const double* h1, const double* L, const d
   s->valid = true;
   *out = s;
   return AFQMC_OK;
+}
+
+extern "C" {
+
+int afqmc_init(const afqmc_params* p, const double* h1, const double* L, const double* trial,
+               void* d_workspace, size_t ws_bytes, void* stream, afqmc_state** out) {
+  if (!out) {
+    set_error("out is NULL");
+    return AFQMC_EINVAL;
+  }
+  *out = nullptr;
+  AFQ_TRY(check_params(p));
+  if (p->ndet != 0) {
+    set_error("ndet = %d: a multi-determinant trial is set up by afqmc_init_multidet", p->ndet);
+    return AFQMC_EINVAL;
+  }
+  if (!h1 || !L || !trial || !d_workspace) {
+    set_error("h1, L, trial and d_workspace are required");
+    return AFQMC_EINVAL;
+  }
+  return init_state(p, h1, L, trial, nullptr, nullptr, nullptr, d_workspace, ws_bytes, stream,
+                    out);
+}
+
+int afqmc_init_multidet(const afqmc_params* p, const double* h1, const double* L, int32_t ndet,
+                        const double* coef, const double* trial_up, const double* trial_dn,
+                        void* d_workspace, size_t ws_bytes, void* stream, afqmc_state** out) {
+  if (!out) {
+    set_error("out is NULL");
+    return AFQMC_EINVAL;
+  }
+  *out = nullptr;
+  AFQ_TRY(check_params(p));
+  if (ndet < 1 || p->ndet != ndet) {
+    set_error("afqmc_init_multidet: ndet = %d must be >= 1 and equal params.ndet = %d", ndet,
+              p->ndet);
+    return AFQMC_EINVAL;
+  }
+  if (!h1 || !L || !coef || !trial_up || !trial_dn || !d_workspace) {
+    set_error("h1, L, coef, trial_up, trial_dn and d_workspace are required");
+    return AFQMC_EINVAL;
+  }
+  return init_state(p, h1, L, nullptr, coef, trial_up, trial_dn, d_workspace, ws_bytes, stream,
+                    out);
 }
 
 #define AFQ_STATE(s)                       \

@@ -1,6 +1,7 @@
 // Host-side state of one AFQMC run (internal header).
 #pragma once
 
+#include <cmath>
 #include <vector>
 
 #include "kernels.cuh"
@@ -50,6 +51,14 @@ struct Bufs {
   double *bp_cos = nullptr, *bp_part = nullptr, *bp_red = nullptr, *bp_R = nullptr;
   double* bp_out = nullptr;
   void* bp_phi_lo = nullptr;  // mixed path: operand copy of the back-propagated orbitals
+  // multi-determinant trial (afqmc_params.ndet >= 1), index ds = 2 d + spin:
+  // orbitals V_ds^T [2nd][N][M], half-rotated vectors [2nd][G][N][M] and
+  // one-body matrices [2nd][N][M], Theta_ds [2nd][W][2][N][M], log det S_ds
+  // [W][2nd][2], weights w_d [W][nd][2], traces [2nd][2W][G], exchange
+  // partials [2nd][W][nchunk][2], log A_d^* [nd][2]
+  double *md_V = nullptr, *md_Lh = nullptr, *md_hh = nullptr, *md_theta = nullptr;
+  double *md_ld = nullptr, *md_w = nullptr, *md_C = nullptr, *md_part = nullptr;
+  double* md_logA = nullptr;
 };
 
 constexpr int kBpSlices = 8;
@@ -100,6 +109,10 @@ int bp_record_fields(afqmc_state* s);
 int bp_step_factor(afqmc_state* s);
 int apply_b_f64(afqmc_state* s, const double* phi_in, double* phi_out, const double* mask);
 int apply_b_mixed(afqmc_state* s, const void* phi_lo_in, double* phi_out, void* phi_lo_out);
+int md_overlap_update(afqmc_state* s, bool into_ld);
+int md_force_bias(afqmc_state* s);
+int md_local_energies(afqmc_state* s);
+int md_setup(afqmc_state* s, const double* coef);
 }  // namespace afq
 
 namespace afq {

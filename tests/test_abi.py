@@ -45,7 +45,7 @@ def test_params_struct_matches_header_defaults(built):
     assert p.ecap_C == 2.0 and p.fb_cap == 1.0 and p.max_records == 4096
     assert p.e_shift != p.e_shift and p.wmax != p.wmax  # NaN defaults
     assert ctypes.sizeof(built.Params) == 112
-    assert p.bp_steps == 0 and p.reserved == 0
+    assert p.bp_steps == 0 and p.ndet == 0
 
 
 def test_workspace_size_and_validation_without_gpu(built):

@@ -6,7 +6,9 @@ trial with different spin-up and spin-down orbitals and complex coefficients
 are checked against brute-force Fock space; a one-determinant trial reproduces
 the single-determinant oracle (set-up, estimators and a short walk) exactly;
 scaling every coefficient by one complex number leaves the estimators alone; a
-determinant orthogonal to the walker drops out without non-finite values.
+determinant orthogonal to the walker drops out without non-finite values (it
+differs from the walker in two orbitals of each spin, so H does not connect
+them either and the single-determinant energy is the exact mixed one).
 """
 import numpy as np
 
