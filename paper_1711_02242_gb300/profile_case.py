@@ -1,6 +1,6 @@
 """A single contraction of the M=300 step, for kernel profiling.
 
-    python -m paper_1711_02242_gb300.profile_case [--case v|fb|taylor|mcd|bp] [--dtype bf16|tf32|fp64]
+    python -m paper_1711_02242_gb300.profile_case [--case v|fb|taylor|mcd|bp|md] [--dtype bf16|tf32|fp64]
                                                   [--reps 3] [--walkers 512] [--orbitals 300]
                                                   [--window 20]
 
@@ -14,6 +14,9 @@ Case "mcd": the modified Cholesky decomposition over index pairs
 (afqmc_modified_cholesky_pairs, delta = 1e-6) of the interaction of the seeded
 Hamiltonian with `--orbitals` M orbitals and 6M vectors (the pair matrix is
 16.3 GB at M = 300, 1.3 GB at M = 160); one launch per vector.
+Case "md": the float64 walk of the M=100 workload (10+10 electrons, 500
+vectors, 1024 walkers) with a trial of 1, 2 and 4 non-orthogonal determinants
+(rotations of the RHF determinant): time per step and per energy evaluation.
 Case "bp": the M=300 walk (512 walkers, 1800 vectors, RHF trial) with a
 back-propagation window of `--window` steps: time per step without and with
 the window open, and the time of afqmc_bp_end (backward sweep and densities).
@@ -33,7 +36,7 @@ def main():
     import torch
 
     ap = argparse.ArgumentParser()
-    ap.add_argument("--case", default="v", choices=["v", "fb", "taylor", "mcd", "bp"])
+    ap.add_argument("--case", default="v", choices=["v", "fb", "taylor", "mcd", "bp", "md"])
     ap.add_argument("--window", type=int, default=20)
     ap.add_argument("--orbitals", type=int, default=300)
     ap.add_argument("--walkers", type=int, default=512)
@@ -49,6 +52,8 @@ def main():
         return mcd(a)
     if a.case == "bp":
         return bp(a)
+    if a.case == "md":
+        return md(a)
     if a.case == "v":
         m, n, k, pitch = 1024, 45150, 1800, 1800
     else:
@@ -194,6 +199,52 @@ def bp(a):
           f"bp_end ms={t_end:.2f}; trace(rho_PRes)={np.trace(rho).real:.6f} "
           f"|sum W F|/sum W={abs(wp) / abs(wsum):.4f}; status={run.info().status}")
     run.close()
+
+
+def md(a):
+    import scipy.linalg as sla
+    import torch
+
+    import workloads
+    from paper_1711_02242_gb300.rhf import rhf_trial
+
+    w = workloads.config("c1")
+    h1, L, H0 = w.hamiltonian()
+    C, _, _ = rhf_trial(h1, L, w.N, max_iter=25)
+    rng = np.random.default_rng(11)
+    q, _ = np.linalg.qr(np.hstack([C, rng.standard_normal((w.M, w.M - w.N))]))
+    basis = np.hstack([C, q[:, w.N:]])
+
+    def rotated():
+        K = 0.02 * rng.standard_normal((w.M, w.M))
+        return basis @ sla.expm(K - K.T)[:, :w.N]
+
+    st = torch.cuda.Stream()
+    steps = 10
+    for nd in (1, 2, 4):
+        up = np.array([C] + [rotated() for _ in range(nd - 1)])
+        dn = np.array([C] + [rotated() for _ in range(nd - 1)])
+        coef = np.array([1.0] + [0.3 / nd] * (nd - 1), np.complex128)
+        p = pkg.default_params(w.M, w.N, w.nchol, w.nwalkers, dt=w.dt, seed=w.seed, H0=H0,
+                               qr_period=w.qr_period, energy_period=0, ndet=nd)
+        run = pkg.AfqmcRun(h1, L, (coef, up, dn), p, stream=st)
+        run.propagate(2)
+        st.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        run.propagate(steps)
+        e1.record(st)
+        st.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        import time
+
+        t0 = time.perf_counter()
+        run.local_energies()
+        te = 1e3 * (time.perf_counter() - t0)
+        print(f"case md fp64 M={w.M} N={w.N} nchol={w.nchol} walkers={w.nwalkers} ndet={nd}: "
+              f"ms/step={ms:.2f} walker-steps/s={w.nwalkers / ms * 1e3:.0f} energy-eval ms={te:.2f} "
+              f"status={run.info().status} alive={run.info().alive}")
+        run.close()
 
 
 if __name__ == "__main__":
