@@ -63,12 +63,12 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # SHA-256 of the source file the kernel was built from; a figure whose source
 # has changed since is reported as null.
 TRAFFIC = {
-    "theta": {"bytes": (64.455168 + 30.120960) * 1e6, "sha": "a5d4696939acc04c20f26f3758050afa1bf5ec5d00500917703b04c95e24fe6c"},
-    "overlap": {"bytes": (8.237824 + 0.000000) * 1e6, "sha": "a5d4696939acc04c20f26f3758050afa1bf5ec5d00500917703b04c95e24fe6c"},
-    "qr": {"bytes": (61.481472 + 34.750720) * 1e6, "sha": "a5d4696939acc04c20f26f3758050afa1bf5ec5d00500917703b04c95e24fe6c"},
-    "taylor": {"bytes": (218.370560 + 19.842816) * 1e6, "sha": "7d84c2b3465f764bb47983565617111a70bc45f2b5fbc4a888a139d84b0bbc1f"},
-    "v_assembly": {"bytes": (332.382976 + 149.079296) * 1e6, "sha": "ae969ee56811ec9bc4c2b56e7d5c69d033e3462e42e4082180d39f310ded3dac"},
-    "energy": {"bytes": (42.972160 + 0.425216) * 1e6, "sha": "ae969ee56811ec9bc4c2b56e7d5c69d033e3462e42e4082180d39f310ded3dac"},
+    "theta": {"bytes": (64.544512 + 30.260480) * 1e6, "sha": "33719648246e485b7a441bb83f88a827089bc4b9d9aeb90658da27bacb7275fc"},
+    "overlap": {"bytes": (8.236800 + 0.000000) * 1e6, "sha": "33719648246e485b7a441bb83f88a827089bc4b9d9aeb90658da27bacb7275fc"},
+    "qr": {"bytes": (61.481984 + 34.477824) * 1e6, "sha": "33719648246e485b7a441bb83f88a827089bc4b9d9aeb90658da27bacb7275fc"},
+    "taylor": {"bytes": (218.600448 + 20.028672) * 1e6, "sha": "7d84c2b3465f764bb47983565617111a70bc45f2b5fbc4a888a139d84b0bbc1f"},
+    "v_assembly": {"bytes": (229.882624 + 184.216576) * 1e6, "sha": "ebefa405f32f3e93f694d160ec40a4f1211014674d6f73d7de534f53b4d1f9a3"},
+    "energy": {"bytes": (42.972416 + 0.417024) * 1e6, "sha": "ebefa405f32f3e93f694d160ec40a4f1211014674d6f73d7de534f53b4d1f9a3"},
 }
 
 
