@@ -276,8 +276,8 @@ __global__ void __launch_bounds__(OV_T) k_overlap(OverlapArgs a) {
   double2* A = ov_sm;            // [N][N]
   double2* Inv = ov_sm + N * N;  // [N][N]
   __shared__ int piv, swaps, singular;
-  __shared__ double logabs, phase;
   __shared__ double2 rpiv;
+  __shared__ double2 pivots[64];  // the pivots, for log det after the elimination
   const double* fr = a.phiT + (long)w * 2 * N * M;
   const double* fi = fr + (long)N * M;
   // S[i][j] = Phi[i][j], the top block of the orbitals
@@ -288,8 +288,6 @@ __global__ void __launch_bounds__(OV_T) k_overlap(OverlapArgs a) {
   for (int idx = threadIdx.x; idx < N * N; idx += OV_T)
     Inv[idx] = make_double2(idx / N == idx % N ? 1.0 : 0.0, 0.0);
   if (threadIdx.x == 0) {
-    logabs = 0.0;
-    phase = 0.0;
     swaps = 0;
     singular = 0;
   }
@@ -335,13 +333,13 @@ __global__ void __launch_bounds__(OV_T) k_overlap(OverlapArgs a) {
       if (threadIdx.x == 0) swaps++;
     }
     __syncthreads();
-    // 1 / pivot once (float64 division and log run long on the FP64 pipe)
+    // 1 / pivot once (a float64 division runs long on the FP64 pipe); the
+    // pivot's log and phase are taken after the loop, all pivots at once
     if (threadIdx.x == 0) {
       const double2 pv = A[k * N + k];
       const double den = pv.x * pv.x + pv.y * pv.y;
       rpiv = make_double2(pv.x / den, -pv.y / den);
-      logabs += 0.5 * log(den);
-      phase += atan2(pv.y, pv.x);
+      pivots[k] = pv;
     }
     __syncthreads();
     const double2 rp = rpiv;
@@ -371,13 +369,34 @@ __global__ void __launch_bounds__(OV_T) k_overlap(OverlapArgs a) {
       if (r != k) A[r * N + k] = make_double2(0.0, 0.0);
     __syncthreads();
   }
+  // log det = sum_k log |p_k| + i (sum_k arg p_k + pi swaps), the N logs and
+  // phases in parallel, summed in a fixed order (warps 0 and 1: N <= 64)
+  double la = 0.0, ph = 0.0;
+  if (!singular && threadIdx.x < N) {
+    const double2 pv = pivots[threadIdx.x];
+    la = 0.5 * log(pv.x * pv.x + pv.y * pv.y);
+    ph = atan2(pv.y, pv.x);
+  }
+  __shared__ double red[4];
+  if (threadIdx.x < 64) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      la += __shfl_xor_sync(0xffffffffu, la, o);
+      ph += __shfl_xor_sync(0xffffffffu, ph, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+      red[2 * (threadIdx.x >> 5)] = la;
+      red[2 * (threadIdx.x >> 5) + 1] = ph;
+    }
+  }
+  __syncthreads();
   if (threadIdx.x == 0 && live) {
     if (singular) {
       a.logdet[2L * w] = -INFINITY;
       a.logdet[2L * w + 1] = 0.0;
     } else {
-      a.logdet[2L * w] = 2.0 * logabs;
-      a.logdet[2L * w + 1] = wrap_pi(2.0 * (phase + 3.141592653589793 * swaps));
+      a.logdet[2L * w] = 2.0 * (red[0] + red[2]);
+      a.logdet[2L * w + 1] = wrap_pi(2.0 * ((red[1] + red[3]) + 3.141592653589793 * swaps));
     }
   }
   // S^-1 of live, non-singular walkers for the Theta kernel
@@ -553,23 +572,24 @@ __global__ void __launch_bounds__(256) k_mgs(MgsArgs a) {
   extern __shared__ double2 q_sm[];  // the finished column q_k, [M]
   __shared__ double sh[32];
   __shared__ double inv_sh;
+  __shared__ double norms[64];  // |v_k|^2, for log det R after the sweep
   const int w = blockIdx.x;
   if (!walker_alive(a.wt, w)) return;
   const int M = a.M, N = a.N;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   double* re = a.phiT + (long)w * 2 * N * M;
   double* im = re + (long)N * M;
-  double logr = 0.0;
   for (int k = 0; k < N; ++k) {
     double* vr = re + (long)k * M;
     double* vi = im + (long)k * M;
     double nn = 0.0;
     for (int p = threadIdx.x; p < M; p += blockDim.x) nn = fma(vr[p], vr[p], fma(vi[p], vi[p], nn));
     nn = block_sum(nn, sh);
-    // 1 / |v_k| and log |v_k| once (long FP64 sequences), shared by the block
+    // 1 / |v_k| once (a long FP64 sequence), shared by the block; the logs of
+    // the norms are taken after the sweep, all at once
     if (threadIdx.x == 0) {
       inv_sh = 1.0 / sqrt(nn);
-      logr += 0.5 * log(nn);
+      norms[k] = nn;
     }
     __syncthreads();
     const double inv = inv_sh;
@@ -612,7 +632,15 @@ __global__ void __launch_bounds__(256) k_mgs(MgsArgs a) {
     }
     __syncthreads();
   }
-  if (threadIdx.x == 0 && a.ld) a.ld[2L * w] -= 2.0 * logr;
+  // log det R = sum_k log |v_k|, the N logs in parallel, summed in a fixed order
+  double lr = threadIdx.x < N ? 0.5 * log(norms[threadIdx.x]) : 0.0;
+  if (threadIdx.x < 64) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) lr += __shfl_xor_sync(0xffffffffu, lr, o);
+    if (lane == 0) sh[warp] = lr;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && a.ld) a.ld[2L * w] -= 2.0 * (sh[0] + sh[1]);
 }
 
 int launch_mgs(const MgsArgs& a, cudaStream_t st) {
