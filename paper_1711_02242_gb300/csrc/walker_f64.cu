@@ -273,11 +273,12 @@ __global__ void __launch_bounds__(OV_T) k_overlap(OverlapArgs a) {
   const int w = blockIdx.x;
   const bool live = !a.wt || walker_alive(a.wt, w);
   const int N = a.N, M = a.M;
-  double2* A = ov_sm;            // [N][N]
-  double2* Inv = ov_sm + N * N;  // [N][N]
-  __shared__ int piv, swaps, singular;
+  double2* A = ov_sm;  // [N][N], inverted in place
+  __shared__ int swaps, singular;
   __shared__ double2 rpiv;
   __shared__ double2 pivots[64];  // the pivots, for log det after the elimination
+  __shared__ double2 fac[64];     // a_rk / p of the current pivot column
+  __shared__ int order[64], pos[64];
   const double* fr = a.phiT + (long)w * 2 * N * M;
   const double* fi = fr + (long)N * M;
   // S[i][j] = Phi[i][j], the top block of the orbitals
@@ -285,13 +286,18 @@ __global__ void __launch_bounds__(OV_T) k_overlap(OverlapArgs a) {
     const int i = idx / N, j = idx % N;
     A[idx] = make_double2(fr[(long)j * M + i], fi[(long)j * M + i]);
   }
-  for (int idx = threadIdx.x; idx < N * N; idx += OV_T)
-    Inv[idx] = make_double2(idx / N == idx % N ? 1.0 : 0.0, 0.0);
+  if (threadIdx.x < N) order[threadIdx.x] = threadIdx.x;
   if (threadIdx.x == 0) {
     swaps = 0;
     singular = 0;
   }
   __syncthreads();
+  // In-place Gauss-Jordan with partial pivoting: at pivot k (after the row
+  // swap), with p = a_kk, a_ij -= a_ik a_kj / p (i, j != k), then
+  // a_kj /= p, a_ik = -a_ik / p, a_kk = 1 / p: (N - 1)^2 updates per pivot.
+  // Warp 0 picks the pivot, swaps the rows, takes 1 / p once and the factors
+  // a_rk / p.  The row interchanges leave the inverse with its columns in the
+  // rows' final order, undone when it is stored.
   for (int k = 0; k < N; ++k) {
     if (threadIdx.x < 32) {
       // pivot: the largest |a_rk|^2 over rows r >= k, the first such row on ties
@@ -314,61 +320,69 @@ __global__ void __launch_bounds__(OV_T) k_overlap(OverlapArgs a) {
           best = ob;
         }
       }
-      if (threadIdx.x == 0) {
-        piv = best;
-        if (!(bv > 0.0)) singular = 1;
+      if (bv > 0.0) {
+        if (best != k) {
+          for (int j = threadIdx.x; j < N; j += 32) {
+            const double2 t = A[k * N + j];
+            A[k * N + j] = A[best * N + j];
+            A[best * N + j] = t;
+          }
+          if (threadIdx.x == 0) {
+            const int t = order[k];
+            order[k] = order[best];
+            order[best] = t;
+            swaps++;
+          }
+          __syncwarp();
+        }
+        // 1 / pivot once per lane (a float64 division runs long on the FP64 pipe)
+        const double2 pv = A[k * N + k];
+        const double den = pv.x * pv.x + pv.y * pv.y;
+        const double2 rp = make_double2(pv.x / den, -pv.y / den);
+        for (int r = threadIdx.x; r < N; r += 32) {
+          const double2 x = A[r * N + k];
+          fac[r] = make_double2(x.x * rp.x - x.y * rp.y, x.x * rp.y + x.y * rp.x);
+        }
+        if (threadIdx.x == 0) {
+          rpiv = rp;
+          pivots[k] = pv;
+        }
+      } else if (threadIdx.x == 0) {
+        singular = 1;
       }
     }
     __syncthreads();
     if (singular) break;
-    if (piv != k) {
-      for (int j = threadIdx.x; j < N; j += blockDim.x) {
-        double2 t = A[k * N + j];
-        A[k * N + j] = A[piv * N + j];
-        A[piv * N + j] = t;
-        t = Inv[k * N + j];
-        Inv[k * N + j] = Inv[piv * N + j];
-        Inv[piv * N + j] = t;
-      }
-      if (threadIdx.x == 0) swaps++;
-    }
-    __syncthreads();
-    // 1 / pivot once (a float64 division runs long on the FP64 pipe); the
-    // pivot's log and phase are taken after the loop, all pivots at once
-    if (threadIdx.x == 0) {
-      const double2 pv = A[k * N + k];
-      const double den = pv.x * pv.x + pv.y * pv.y;
-      rpiv = make_double2(pv.x / den, -pv.y / den);
-      pivots[k] = pv;
-    }
-    __syncthreads();
-    const double2 rp = rpiv;
-    for (int j = threadIdx.x; j < N; j += blockDim.x) {
-      const double2 v = A[k * N + j], u = Inv[k * N + j];
-      A[k * N + j] = make_double2(v.x * rp.x - v.y * rp.y, v.x * rp.y + v.y * rp.x);
-      Inv[k * N + j] = make_double2(u.x * rp.x - u.y * rp.y, u.x * rp.y + u.y * rp.x);
-    }
-    __syncthreads();
-    // eliminate column k from the other rows.  Columns j < k of A are already
-    // unit vectors (row k holds 0 there), so A changes only in columns j > k;
-    // Inv changes in every column (row swaps can move any column forward)
-    const int na = N - 1 - k;  // A columns k+1 .. N-1
-    for (int idx = threadIdx.x; idx < (N - 1) * (na + N); idx += blockDim.x) {
-      const int rr = idx / (na + N), c = idx % (na + N);
-      const int r = rr < k ? rr : rr + 1;  // rows other than k
-      const double2 f = A[r * N + k];
-      const bool inA = c < na;
-      const int col = inA ? k + 1 + c : c - na;
-      const double2 v = inA ? A[k * N + col] : Inv[k * N + col];
-      double2& d = inA ? A[r * N + col] : Inv[r * N + col];
+    // a_ij -= (a_ik / p) a_kj for i, j != k
+    const int n1 = N - 1;
+    for (int idx = threadIdx.x; idx < n1 * n1; idx += blockDim.x) {
+      const int ii = idx / n1, jj = idx - (idx / n1) * n1;
+      const int i = ii < k ? ii : ii + 1, j = jj < k ? jj : jj + 1;
+      const double2 f = fac[i], v = A[k * N + j];
+      double2& d = A[i * N + j];
       d.x = fma(-f.x, v.x, fma(f.y, v.y, d.x));
       d.y = fma(-f.x, v.y, fma(-f.y, v.x, d.y));
     }
     __syncthreads();
-    for (int r = threadIdx.x; r < N; r += blockDim.x)
-      if (r != k) A[r * N + k] = make_double2(0.0, 0.0);
+    // pivot row / p, pivot column -a_ik / p, a_kk = 1 / p
+    const double2 rp = rpiv;
+    for (int t = threadIdx.x; t < 2 * N - 1; t += blockDim.x) {
+      if (t < N) {
+        double2& d = A[k * N + t];
+        if (t == k) {
+          d = rp;
+        } else {
+          const double2 v = d;
+          d = make_double2(v.x * rp.x - v.y * rp.y, v.x * rp.y + v.y * rp.x);
+        }
+      } else {
+        const int i = t - N < k ? t - N : t - N + 1;
+        A[i * N + k] = make_double2(-fac[i].x, -fac[i].y);
+      }
+    }
     __syncthreads();
   }
+  if (threadIdx.x < N) pos[order[threadIdx.x]] = threadIdx.x;
   // log det = sum_k log |p_k| + i (sum_k arg p_k + pi swaps), the N logs and
   // phases in parallel, summed in a fixed order (warps 0 and 1: N <= 64)
   double la = 0.0, ph = 0.0;
@@ -399,10 +413,14 @@ __global__ void __launch_bounds__(OV_T) k_overlap(OverlapArgs a) {
       a.logdet[2L * w + 1] = wrap_pi(2.0 * ((red[1] + red[3]) + 3.141592653589793 * swaps));
     }
   }
-  // S^-1 of live, non-singular walkers for the Theta kernel
+  // S^-1 of live, non-singular walkers for the Theta kernel: column c of the
+  // inverse is column pos[c] of A (the row interchanges undone)
   if (singular || !live) return;
   double2* si = a.Sinv + (long)w * N * N;
-  for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x) si[idx] = Inv[idx];
+  for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x) {
+    const int r = idx / N, c = idx - (idx / N) * N;
+    si[idx] = A[r * N + pos[c]];
+  }
 }
 
 // Theta^T[i][p] = sum_j S^-1[j][i] Phi^T[j][p]: block (x, w) takes rows
