@@ -427,7 +427,8 @@ AFQMC_API int afqmc_wait_flag(const int* d_flag, int64_t max_polls, int* d_statu
 /*
  * Back-propagation estimator of the one-body density (Sec. "Computing
  * ground-state properties: the backpropagation algorithm", Eqs. bp1, bp,
- * bp_dets), on a state created with bp_steps > 0 and pc_period 0.  On the
+ * bp_dets), on a state created with bp_steps > 0 (a comb inside the window
+ * gives each copy its parent's recorded path).  On the
  * mixed path the fields are recorded as the BF16/TF32 operands the step used
  * and the backward sweep runs on the tensor cores; the densities and weights
  * are formed in float64 on both paths.

@@ -55,8 +55,8 @@ Readings of the paper taken here (each also listed in the design notes):
     denominator <Psi_{m,w}|Psi_{n,w}> printed in Eq. bp reads
     <Phi_{m,w}|Psi_{n,w}>.  BP-PRes multiplies W_{n+m} by, per step k of the
     window, exp(-i dt Im E_loc(Psi_k)) / max(0, cos dtheta_k) (0 where the
-    projection zeroed the walker; the weight cap is not undone).  Windows
-    need population control off.
+    projection zeroed the walker; the weight cap is not undone).  The comb
+    gives each copy its parent's path (Psi_n, fields, factor).
 """
 from __future__ import annotations
 
@@ -347,14 +347,18 @@ class Oracle:
         self.logdet = self.logdet[parent].copy()
         self.theta = self.theta[parent].copy()
         self.weight = np.full(self.W, wnew)
+        if self.bp is not None:
+            # a copy carries its parent's path: Psi_n, fields and restoration factor
+            self.bp["psi_n"] = self.bp["psi_n"][parent].copy()
+            self.bp["factor"] = self.bp["factor"][parent].copy()
+            self.bp["fields"] = [f[parent].copy() for f in self.bp["fields"]]
 
     # --- back-propagation (Sec. "Computing ground-state properties") --------
     def bp_begin(self):
         """Open a back-propagation window at the current step n: keep Psi_n of
         every walker and, at every later step, the shifted fields x - xbar that
-        built B (Eq. bp_dets) and the BP-PRes factor of the weight."""
-        if self.p.pc_period:
-            raise ValueError("back-propagation windows need population control off")
+        built B (Eq. bp_dets) and the BP-PRes factor of the weight; a comb
+        inside the window copies these with the walkers."""
         self.bp = {"psi_n": self.phi.copy(), "fields": [],
                    "factor": np.ones(self.W, np.complex128)}
 

@@ -104,6 +104,10 @@ size_t plan(const afqmc_params& p, Bufs* b, char* base) {
     b->bp_red = a.take<double>((size_t)kBpSlices * 2 * M * M);
     b->bp_R = a.take<double>(4 * M * M);
     b->bp_out = a.take<double>(4 * M * M + 4);
+    size_t row = sizeof(double) * 2 * N * M;
+    const size_t frow = mixed ? 2 * Gp * lo : sizeof(double) * 2 * G;
+    if (frow > row) row = frow;
+    b->bp_tmp = a.take<char>(row * W);
   }
   b->mixed = mixed;
   b->lo_kind = mixed ? (lo == 2 ? LO_BF16 : LO_TF32) : LO_NONE;
@@ -532,6 +536,14 @@ static int step_once(afqmc_state* s) {
   s->t_fresh = false;
   s->h_step += 1;
   const int64_t n = s->h_step;
+  if (s->bp_on) {
+    // back-propagation window: this step's BP-PRes factor needs E_loc(Psi_k)
+    // of every walker, taken before Gram-Schmidt (which leaves it unchanged)
+    // and before a comb (which then copies factor and path together)
+    AFQ_TRY(energy_eval(s, false, false));
+    AFQ_TRY(bp_step_factor(s));
+    s->bp_m += 1;
+  }
   if (p.qr_period && n % p.qr_period == 0) {
     prof_begin(s, AFQMC_PH_QR);
     // Phi -> Q; Theta is unchanged and log det S drops by sum_k log r_kk,
@@ -547,6 +559,8 @@ static int step_once(afqmc_state* s) {
                 b.wt, b.cum, b.parent, b.phiT, b.thetaT, b.ld, b.T0, b.T1, b.tmp_ld, b.wtot};
     AFQ_TRY(launch_comb(ca, s->st));
     AFQ_TRY(refresh_phi_lo(s));
+    if (s->bp_on) AFQ_TRY(bp_after_comb(s));
+    s->t_fresh = false;  // the walkers moved: their force-bias traces are stale
     prof_end(s);
   }
   const bool e_due = p.energy_period && n % p.energy_period == 0;
@@ -554,12 +568,6 @@ static int step_once(afqmc_state* s) {
     prof_begin(s, AFQMC_PH_ENERGY);
     AFQ_TRY(energy_eval(s, true));
     prof_end(s);
-  }
-  if (s->bp_on) {
-    // a back-propagation window needs E_loc of every step (BP-PRes factor)
-    if (!e_due) AFQ_TRY(energy_eval(s, false, false));
-    AFQ_TRY(bp_step_factor(s));
-    s->bp_m += 1;
   }
   return AFQMC_OK;
 }
@@ -1143,10 +1151,6 @@ int afqmc_bp_begin(afqmc_state* s) {
   if (s->p.bp_steps <= 0) {
     set_error("afqmc_bp_begin: the state has no back-propagation buffers (bp_steps = 0)");
     return AFQMC_EINVAL;
-  }
-  if (s->p.pc_period) {
-    set_error("afqmc_bp_begin: population control must be off (pc_period = 0)");
-    return AFQMC_EUNSUPPORTED;
   }
   if (s->bp_on) {
     set_error("afqmc_bp_begin: a window is already open");

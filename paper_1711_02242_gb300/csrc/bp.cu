@@ -98,6 +98,15 @@ __global__ void k_bp_fields_lo(long n, int Gp, int bytes, const void* hist, void
   }
 }
 
+// dst row k = src row parent[k] (own row where the comb did nothing), rows
+// of `words` 8-byte words.
+__global__ void k_bp_gather(int W, long words, const int* parent, const uint64_t* src,
+                            uint64_t* dst) {
+  const int k = blockIdx.x;
+  const int j = parent[k] < 0 ? k : parent[k];
+  for (long t = threadIdx.x; t < words; t += blockDim.x) dst[k * words + t] = src[j * words + t];
+}
+
 __device__ inline double2 cmul(double2 a, double2 b) {
   return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
@@ -324,6 +333,28 @@ int bp_record_fields(afqmc_state* s) {
   char* dst = reinterpret_cast<char*>(b.bp_hist) + (size_t)s->bp_m * n;
   AFQ_CUDA(cudaMemcpyAsync(dst, b.mixed ? b.x_lo : static_cast<const void*>(b.x), n,
                            cudaMemcpyDeviceToDevice, s->st));
+  return AFQMC_OK;
+}
+
+// After a comb inside the window: every copy takes its parent's Psi_n,
+// restoration factor and recorded fields (rows gathered by the comb's parent
+// index through a scratch buffer).
+int bp_after_comb(afqmc_state* s) {
+  const afqmc_params& p = s->p;
+  const Bufs& b = s->b;
+  const int W = p.nwalkers;
+  auto gather = [&](void* buf, size_t row_bytes) -> int {
+    const long words = (long)(row_bytes / 8);
+    AFQ_LAUNCH(k_bp_gather, W, 256, 0, s->st, W, words, b.parent,
+               static_cast<const uint64_t*>(buf), reinterpret_cast<uint64_t*>(b.bp_tmp));
+    AFQ_CUDA(cudaMemcpyAsync(buf, b.bp_tmp, row_bytes * W, cudaMemcpyDeviceToDevice, s->st));
+    return AFQMC_OK;
+  };
+  AFQ_TRY(gather(b.bp_psi, sizeof(double) * 2 * (size_t)p.N * p.M));
+  AFQ_TRY(gather(b.bp_f, sizeof(double) * 2));
+  const size_t fbytes = bp_field_bytes(p, b);
+  for (int k = 0; k < s->bp_m; ++k)
+    AFQ_TRY(gather(reinterpret_cast<char*>(b.bp_hist) + (size_t)k * fbytes, fbytes / W));
   return AFQMC_OK;
 }
 

@@ -51,6 +51,7 @@ struct Bufs {
   double *bp_cos = nullptr, *bp_part = nullptr, *bp_red = nullptr, *bp_R = nullptr;
   double* bp_out = nullptr;
   void* bp_phi_lo = nullptr;  // mixed path: operand copy of the back-propagated orbitals
+  void* bp_tmp = nullptr;     // gather scratch: W rows of the largest recorded row
   // multi-determinant trial (afqmc_params.ndet >= 1), index ds = 2 d + spin:
   // orbitals V_ds^T [2nd][N][M], half-rotated vectors [2nd][G][N][M] and
   // one-body matrices [2nd][N][M], Theta_ds [2nd][W][2][N][M], log det S_ds
@@ -107,6 +108,7 @@ int bp_open(afqmc_state* s);
 int bp_close(afqmc_state* s);
 int bp_record_fields(afqmc_state* s);
 int bp_step_factor(afqmc_state* s);
+int bp_after_comb(afqmc_state* s);
 int apply_b_f64(afqmc_state* s, const double* phi_in, double* phi_out, const double* mask);
 int apply_b_mixed(afqmc_state* s, const void* phi_lo_in, double* phi_out, void* phi_lo_out);
 int md_overlap_update(afqmc_state* s, bool into_ld);

@@ -159,3 +159,24 @@ def test_free_projection_back_propagation_is_exact(fci_bp):
     # the back-propagated density is not the mixed one: the test can tell
     mixed = rho_bp(n * dt + m * dt, 0.0)
     assert np.max(np.abs(mixed.real - exact.real) / (err + 1e-4)) > 8.0
+
+
+def test_comb_inside_the_window_keeps_each_path_whole():
+    """With population control inside the window every copy carries its
+    parent's Psi_n and fields: propagating the recorded Psi_n with the recorded
+    fields gives the walker's current orbitals (same Theta = Phi S^-1, which
+    the Gram-Schmidt steps leave unchanged)."""
+    h1, L, C = small_system()
+    o = afqmc.Oracle(h1, L, C, 16, afqmc.Params(dt=0.02, seed=12, qr_period=4, pc_period=3))
+    o.run(2)
+    o.bp_begin()
+    rec = o.bp
+    o.run(8)  # two combs (steps 3, 6, 9) inside the window
+    st = o.setup
+    fwd = rec["psi_n"].copy()
+    for x in rec["fields"]:
+        fwd = st.Bhalf @ afqmc.taylor(afqmc.assemble_V(st, x), st.Bhalf @ fwd, 6)
+    _, th_fwd = afqmc.overlap(st, fwd)
+    assert np.max(np.abs(th_fwd - o.theta)) < 1e-10 * np.max(np.abs(o.theta))
+    rho, phl, wp, w, _ = o.bp_end()
+    assert abs(np.trace(phl) - 2 * C.shape[1]) < 1e-10

@@ -8,7 +8,8 @@ and BP-PhL), their weight sums and the window length must then agree to
 1e-9 of the largest element.  Cases: the 12-orbital workload over a window
 that crosses two Gram-Schmidt steps, a ragged shape (odd N, nchol, walker
 count, QR every 3 steps, energies every 2 so the window evaluates local
-energies on its own), an empty window (the mixed estimator), free projection
+energies on its own), an empty window (the mixed estimator), a window with
+population control inside it (copies carry their parents' paths), free projection
 (no restoration factor), a walk that keeps going after the window (unchanged
 by it, with and without graph replay), and the argument and state errors.
 The mixed path's window (BF16/TF32 fields and tensor-core backward sweep) is
@@ -40,11 +41,11 @@ def pkg():
 
 
 def make_pair(pkg, M, N, G, W, seed=4, mode="phaseless", qr=5, ep=1, dt=0.01, bp_steps=32,
-              use_graph=0, stream=None):
+              use_graph=0, stream=None, pc=0):
     h1, L, _ = workloads.hamiltonian(M, G, 6000 + M + N, l_scale=workloads.l_amplitude(M, G))
     C, _, conv, _ = scf.rhf(h1, L, N)
     assert conv
-    op = dict(dt=dt, seed=seed, qr_period=qr, energy_period=ep, mode=mode)
+    op = dict(dt=dt, seed=seed, qr_period=qr, energy_period=ep, mode=mode, pc_period=pc)
     orc = afqmc.Oracle(h1, L, C, W, afqmc.Params(**op))
     gp = dict(op)
     gp["mode"] = pkg.AFQMC_FREE if mode == "free" else pkg.AFQMC_PHASELESS
@@ -64,13 +65,14 @@ def check(got, want):
     return m
 
 
-@pytest.mark.parametrize("M,N,G,W,n,m,qr,ep", [
-    (12, 3, 48, 32, 4, 10, 5, 1),
-    (20, 7, 33, 50, 3, 7, 3, 2),
-    (16, 4, 40, 24, 2, 0, 5, 1),   # empty window: the mixed estimator
+@pytest.mark.parametrize("M,N,G,W,n,m,qr,ep,pc", [
+    (12, 3, 48, 32, 4, 10, 5, 1, 0),
+    (20, 7, 33, 50, 3, 7, 3, 2, 0),
+    (16, 4, 40, 24, 2, 0, 5, 1, 0),   # empty window: the mixed estimator
+    (12, 3, 48, 32, 2, 9, 4, 1, 3),   # combs inside the window carry the paths
 ])
-def test_window_matches_oracle(pkg, M, N, G, W, n, m, qr, ep):
-    orc, run = make_pair(pkg, M, N, G, W, qr=qr, ep=ep)
+def test_window_matches_oracle(pkg, M, N, G, W, n, m, qr, ep, pc):
+    orc, run = make_pair(pkg, M, N, G, W, qr=qr, ep=ep, pc=pc)
     orc.run(n)
     run.propagate(n)
     orc.bp_begin()
@@ -133,10 +135,6 @@ def test_errors(pkg):
     run.close()
     with pytest.raises(pkg.AfqmcError, match="EINVAL"):
         pkg.afqmc_workspace_size(pkg.default_params(12, 3, 48, 8, bp_steps=-1))
-    run = pkg.AfqmcRun(h1, L, C, pkg.default_params(12, 3, 48, 8, bp_steps=4, pc_period=5))
-    with pytest.raises(pkg.AfqmcError, match="EUNSUPPORTED"):
-        run.bp_begin()  # population control on
-    run.close()
     run = pkg.AfqmcRun(h1, L, C, pkg.default_params(12, 3, 48, 8, bp_steps=4))
     with pytest.raises(pkg.AfqmcError, match="ESTATE"):
         run.bp_end()
