@@ -157,9 +157,11 @@ AFQMC_API int afqmc_init(const afqmc_params* p, const double* h1, const double* 
  * energy are the determinant-weighted sums of Eqs. precomputing2 and
  * localenergy3; the mean-field background comes from determinant 0,
  * c_g = Tr(L_g (P_0u + P_0d)), and E_T is the local energy of the initial
- * walkers.  Float64 path, phaseless, population control off, no
- * back-propagation window (else AFQMC_EUNSUPPORTED).  Everything else as
- * afqmc_init.
+ * walkers.  Either precision: the mixed paths run the per-determinant
+ * force-bias traces and exchange on the tensor cores (BF16/TF32 operands)
+ * and keep overlaps, weights and their combinations in float64.  Phaseless,
+ * population control off, no back-propagation window (else
+ * AFQMC_EUNSUPPORTED).  Everything else as afqmc_init.
  */
 AFQMC_API int afqmc_init_multidet(const afqmc_params* p, const double* h1, const double* L,
                                   int32_t ndet, const double* coef, const double* trial_up,

@@ -90,6 +90,11 @@ size_t plan(const afqmc_params& p, Bufs* b, char* base) {
     b->md_C = a.take<double>(nd2 * 2 * W * G);
     b->md_part = a.take<double>(nd2 * W * nchunk * 2);
     b->md_logA = a.take<double>(nd2);
+    if (mixed) {
+      b->md_theta_lo = a.take<char>(nd2 * W * 2 * N * Mp * lo);
+      b->md_Lh_lo = a.take<char>(nd2 * G * N * Mp * lo);
+      b->md_C32 = a.take<float>(nd2 * 2 * W * G);
+    }
   }
   if (p.bp_steps > 0) {
     // recorded fields: float64 [W][2][G], or the operand rows [W][2][Gp]
@@ -201,10 +206,9 @@ static int check_params(const afqmc_params* p) {
     set_error("bp_steps < 0 or ndet < 0");
     return AFQMC_EINVAL;
   }
-  if (p->ndet > 0 && (p->precision != AFQMC_FP64 || p->pc_period || p->bp_steps ||
-                      p->mode != AFQMC_PHASELESS)) {
-    set_error("a multi-determinant trial runs on the float64 path, phaseless, without population "
-              "control or back-propagation");
+  if (p->ndet > 0 && (p->pc_period || p->bp_steps || p->mode != AFQMC_PHASELESS)) {
+    set_error("a multi-determinant trial runs phaseless, without population control or "
+              "back-propagation");
     return AFQMC_EUNSUPPORTED;
   }
 
@@ -434,7 +438,8 @@ static int propagate_f64(afqmc_state* s) {
 // step from the operand copy phi_lo_in, the Taylor series and the last half
 // step (TF32), which stores float64 orbitals (walkers with W != 0) and their
 // operand copy.
-int apply_b_mixed(afqmc_state* s, const void* phi_lo_in, double* phi_out, void* phi_lo_out) {
+int apply_b_mixed(afqmc_state* s, const double* phi_in, const void* phi_lo_in, double* phi_out,
+                  void* phi_lo_out) {
   const afqmc_params& p = s->p;
   const Bufs& b = s->b;
   const int W = p.nwalkers, N = p.N, M = p.M, G = p.nchol;
@@ -454,8 +459,10 @@ int apply_b_mixed(afqmc_state* s, const void* phi_lo_in, double* phi_out, void* 
   g.err = b.status;
   AFQ_TRY(tc_v_full(g, b.V_lo, b.lo_kind, W, M, b.Mp, s->sdt, s->st));
   prof_end(s);
-  // first half step: T_0 = (B_half Phi)^T into columns [0, Mp) of the FP32
-  // rows of acc (pitch 2 Mp) and, as the 0th Taylor operand, into Tb0
+  // first half step: T_0 = (B_half Phi)^T = Phi^T + (Phi_lo D_B)^T, D_B =
+  // B_half - I (the identity part added in float64 orbitals by the epilogue),
+  // into columns [0, Mp) of the FP32 rows of acc (pitch 2 Mp) and, as the 0th
+  // Taylor operand, into Tb0
   prof_begin(s, AFQMC_PH_BHALF);
   TcGemm h1;
   h1.m = 2 * N * W;
@@ -467,7 +474,7 @@ int apply_b_mixed(afqmc_state* s, const void* phi_lo_in, double* phi_out, void* 
   h1.ldb = b.Mp;
   h1.tf32 = b.lo_kind == LO_TF32;
   h1.err = b.status;
-  AFQ_TRY(tc_prop_first(h1, b.acc32, 2L * b.Mp, b.Tb0, b.lo_kind, N, M, b.Mp, s->st));
+  AFQ_TRY(tc_prop_first(h1, b.acc32, 2L * b.Mp, b.Tb0, phi_in, b.lo_kind, N, M, b.Mp, s->st));
   prof_end(s);
   // terms k = 1..n: T_k = V T_{k-1} / k, S = T_1 + ... + T_n into columns
   // [Mp, 2 Mp) of acc; the whole series in one launch when the term fits in
@@ -476,8 +483,9 @@ int apply_b_mixed(afqmc_state* s, const void* phi_lo_in, double* phi_out, void* 
   AFQ_TRY(taylor_apply(b.V_lo, b.Tb0, b.Tb1, b.acc32 + b.Mp, 2L * b.Mp, b.lo_kind, W, N, M, b.Mp,
                        p.taylor_order, false, b.status, s->st));
   prof_end(s);
-  // last half step (TF32): Phi <- B_half (T_0 + S) as one K = 2 Mp product of
-  // [T_0 | S] with [B_half | B_half]; stored for live walkers
+  // last half step (TF32): Phi <- B_half (T_0 + S) = (T_0 + S) + [T_0 | S]
+  // [D_B | D_B] (one K = 2 Mp product; T_0 + S added in the epilogue); stored
+  // for live walkers
   prof_begin(s, AFQMC_PH_BHALF);
   TcGemm h2;
   h2.m = 2 * N * W;
@@ -489,7 +497,7 @@ int apply_b_mixed(afqmc_state* s, const void* phi_lo_in, double* phi_out, void* 
   h2.ldb = 2L * b.Mp;
   h2.tf32 = true;
   h2.err = b.status;
-  AFQ_TRY(tc_prop_last(h2, phi_out, b.wt, N, M, phi_lo_out, b.lo_kind, b.Mp, s->st));
+  AFQ_TRY(tc_prop_last(h2, phi_out, b.wt, N, M, phi_lo_out, b.lo_kind, b.Mp, b.acc32, s->st));
   prof_end(s);
   return AFQMC_OK;
 }
@@ -508,7 +516,7 @@ static int propagate_mixed(afqmc_state* s) {
   AFQ_TRY(launch_field(fa, s->st));
   prof_end(s);
   if (s->bp_on) AFQ_TRY(bp_record_fields(s));
-  return apply_b_mixed(s, b.phi_lo, b.phiT, b.phi_lo);
+  return apply_b_mixed(s, b.phiT, b.phi_lo, b.phiT, b.phi_lo);
 }
 
 static int step_once(afqmc_state* s) {
@@ -850,9 +858,10 @@ static int setup_device(afqmc_state* s, const double* h1, const double* L, const
     AFQ_TRY(launch_convert_lo(b.Lh, (long)G * N, M, M, b.Lh_lo, b.Mp, b.lo_kind, st));
     AFQ_CUDA(cudaMemsetAsync(b.th_lo, 0, (size_t)W * 2 * N * b.Mp * b.lo_bytes, st));
     AFQ_CUDA(cudaMemsetAsync(b.x_lo, 0, (size_t)W * 2 * b.Gp * b.lo_bytes, st));
-    AFQ_TRY(launch_convert_lo(b.Bh, M, M, M, b.Bh_lo, b.Mp, b.lo_kind, st));
-    // [B_half | B_half] so that one K = 2 Mp product applies it to T_0 + S
-    AFQ_TRY(launch_convert_lo(b.Bh, M, M, M, b.Bh_tf, 2L * b.Mp, LO_TF32, st));
+    // D_B = B_half - I: the half steps apply the identity part exactly
+    AFQ_TRY(launch_convert_lo(b.Bh, M, M, M, b.Bh_lo, b.Mp, b.lo_kind, st, 1.0));
+    // [D_B | D_B] so that one K = 2 Mp product applies it to T_0 + S
+    AFQ_TRY(launch_convert_lo(b.Bh, M, M, M, b.Bh_tf, 2L * b.Mp, LO_TF32, st, 1.0));
     AFQ_CUDA(cudaMemcpy2DAsync(b.Bh_tf + b.Mp, sizeof(float) * 2 * b.Mp, b.Bh_tf,
                                sizeof(float) * 2 * b.Mp, sizeof(float) * b.Mp, M,
                                cudaMemcpyDeviceToDevice, st));

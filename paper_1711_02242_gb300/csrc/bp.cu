@@ -398,7 +398,7 @@ int bp_close(afqmc_state* s) {
     if (b.mixed) {
       const long nx = (long)W * 2 * b.Gp;
       AFQ_LAUNCH(k_bp_fields_lo, cdiv(nx, 256), 256, 0, st, nx, b.Gp, b.lo_bytes, hk, b.x_lo);
-      AFQ_TRY(apply_b_mixed(s, b.bp_phi_lo, b.bp_phi, b.bp_phi_lo));
+      AFQ_TRY(apply_b_mixed(s, b.bp_phi, b.bp_phi_lo, b.bp_phi, b.bp_phi_lo));
     } else {
       const long nx = (long)W * 2 * G;
       AFQ_LAUNCH(k_bp_fields, cdiv(nx, 256), 256, 0, st, nx, G,

@@ -377,9 +377,14 @@ __device__ __forceinline__ void store8_lo(void* base, int kind, long idx, const 
   }
 }
 
-// First half step: rows (w,c,i) of Phi^T, columns p; D = (B_half Phi)^T.
-// acc[(w,c,i)][p] = D (FP32, pitch ldacc) and Tb holds the 0th Taylor term.
-// Each thread owns one row and 16 consecutive p per chunk: vector stores.
+// First half step: rows (w,c,i) of Phi^T, columns p.  B_half = I + D_B is
+// applied as Phi + Phi D_B: the product runs with the BF16/TF32 copies of Phi
+// and D_B = B_half - I, and the epilogue adds the float64 orbitals phi_id
+// (pitch M, same rows) so that the identity part is exact (rounding B_half's
+// diagonal, close to 1, to BF16/TF32 would scale every walker's orbitals by
+// the same factor each step).  acc[(w,c,i)][p] = (B_half Phi)^T (FP32, pitch
+// ldacc) and Tb holds the 0th Taylor term.  Each thread owns one row and 16
+// consecutive p per chunk: vector stores.
 struct EpiProp0 {
   static constexpr int kSmemBytes = 0;
   static constexpr bool kB3D = false;  // B tile = one 2-D box at row n_origin
@@ -388,6 +393,7 @@ struct EpiProp0 {
   float* acc;
   long ldacc;
   void* tb;
+  const double* phi_id;
   int lo_kind, N, M, Mp, rows;
   int bn;  // tile width (the kernel's BN)
   __device__ __forceinline__ int m_origin(int bx, int) const { return bx * BM; }
@@ -404,6 +410,19 @@ struct EpiProp0 {
       const int w = row / (2 * N), rem = row % (2 * N), c = rem / N, i = rem % N;
       const int pb = n0 + c0;
       if (pb >= M) continue;
+      const double* f = phi_id + (long)row * M + pb;
+      if (pb + 16 <= M && (((long)row * M + pb) & 1) == 0) {
+#pragma unroll
+        for (int u = 0; u < 16; u += 2) {
+          const double2 d = __ldg(reinterpret_cast<const double2*>(f + u));
+          v[u] += (float)d.x;
+          v[u + 1] += (float)d.y;
+        }
+      } else {
+#pragma unroll
+        for (int u = 0; u < 16; ++u)
+          if (pb + u < M) v[u] += (float)__ldg(f + u);
+      }
       if (pb + 16 <= M) {
         float4* a4 = reinterpret_cast<float4*>(acc + (long)row * ldacc + pb);
 #pragma unroll
@@ -487,7 +506,9 @@ struct EpiTaylor {
           }
         }
       } else {
-        for (int u = 0; u < 16 && pb + u < M; ++u) {
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+          if (pb + u >= M) continue;
           arow[pb + u] = (first ? 0.f : arow[pb + u]) + v[u];
           if (tb_out) put_term(tb_out, lo_kind, (long)w * 2 * N, N, Mp, c, i, pb + u, v[u]);
         }
@@ -578,6 +599,9 @@ struct EpiPhi {
   int bn;  // tile width (the kernel's BN)
   void* phi_lo;  // BF16/TF32 copy of the orbitals (pitch Mp) for the next first half step
   int lo_kind, Mp;
+  // FP32 rows [T_0 | S] (pitch 2 Mp): the product is [T_0 | S] [D_B | D_B]
+  // with D_B = B_half - I, and the identity part T_0 + S is added here exactly
+  const float* acc_id;
   __device__ __forceinline__ int m_origin(int bx, int) const { return bx * BM; }
   __device__ __forceinline__ int n_origin(int, int by) const { return by * bn; }
   template <int BN>
@@ -591,6 +615,23 @@ struct EpiPhi {
       tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c0, v);
       if (!ok) continue;
       const int pb = n0 + c0;
+      if (pb >= M) continue;
+      const float* t0 = acc_id + (long)row * 2 * Mp + pb;
+      if (pb + 16 <= M) {
+#pragma unroll
+        for (int u = 0; u < 16; u += 4) {
+          const float4 a = __ldg(reinterpret_cast<const float4*>(t0 + u));
+          const float4 b = __ldg(reinterpret_cast<const float4*>(t0 + Mp + u));
+          v[u] += a.x + b.x;
+          v[u + 1] += a.y + b.y;
+          v[u + 2] += a.z + b.z;
+          v[u + 3] += a.w + b.w;
+        }
+      } else {
+#pragma unroll
+        for (int u = 0; u < 16; ++u)
+          if (pb + u < M) v[u] += __ldg(t0 + u) + __ldg(t0 + Mp + u);
+      }
       double* o = phiT + (long)row * M + pb;
       if (pb + 16 <= M && (((long)row * M + pb) & 1) == 0) {
 #pragma unroll
@@ -604,7 +645,9 @@ struct EpiPhi {
       if (pb + 16 <= M) {
         store16_lo(phi_lo, lo_kind, (long)row * Mp + pb, v, 1.f);
       } else {
-        for (int u = 0; u < 16 && pb + u < M; ++u) store_lo(phi_lo, lo_kind, (long)row * Mp + pb + u, v[u]);
+#pragma unroll
+        for (int u = 0; u < 16; ++u)
+          if (pb + u < M) store_lo(phi_lo, lo_kind, (long)row * Mp + pb + u, v[u]);
       }
     }
   }
@@ -853,10 +896,10 @@ static int half_step_bn(int n) {
   return pad160 < pad256 ? 160 : 256;
 }
 
-int tc_prop_first(const TcGemm& g, float* acc, long ldacc, void* tb, int lo_kind, int N, int M,
-                  int Mp, cudaStream_t st) {
+int tc_prop_first(const TcGemm& g, float* acc, long ldacc, void* tb, const double* phi_id,
+                  int lo_kind, int N, int M, int Mp, cudaStream_t st) {
   const int bn = half_step_bn(M);
-  tc::EpiProp0 e{acc, ldacc, tb, lo_kind, N, M, Mp, g.m, bn};
+  tc::EpiProp0 e{acc, ldacc, tb, phi_id, lo_kind, N, M, Mp, g.m, bn};
   const int gx = cdiv(g.m, tc::BM), gy = cdiv(M, bn);
   if (bn == 160) {
     if (g.tf32) return launch_tc_persistent<160, 6, true>(g, e, gx, gy, st);
@@ -901,9 +944,13 @@ int tc_v_full(const TcGemm& g, void* V, int lo_kind, int W, int M, int Mp, doubl
 }
 
 int tc_prop_last(const TcGemm& g, double* phiT, const double* wt, int N, int M, void* phi_lo,
-                 int lo_kind, int Mp, cudaStream_t st) {
+                 int lo_kind, int Mp, const float* acc_id, cudaStream_t st) {
+  if (g.lda != 2L * Mp) {
+    set_error("tc last half step: operand pitch %ld, want 2 Mp = %d", g.lda, 2 * Mp);
+    return AFQMC_EINVAL;
+  }
   const int bn = half_step_bn(M);
-  tc::EpiPhi e{phiT, wt, N, M, g.m, bn, phi_lo, lo_kind, Mp};
+  tc::EpiPhi e{phiT, wt, N, M, g.m, bn, phi_lo, lo_kind, Mp, acc_id};
   const int gx = cdiv(g.m, tc::BM), gy = cdiv(M, bn);
   if (bn == 160) {
     if (g.tf32) return launch_tc_persistent<160, 6, true>(g, e, gx, gy, st);

@@ -183,8 +183,9 @@ int launch_init_walkers(const double* VTt, double* phiT, double* wt, int W, int 
                         cudaStream_t st);
 int launch_sumsq(const double* v, double* out, int n, cudaStream_t st);
 // dst[r][c] = lo(src[r][c]) for c < cols, 0 for cols <= c < ldd
+// dst[r][c] = lo(src[r][c] - (r == c ? minus_diag : 0)), zero for cols <= c < ldd
 int launch_convert_lo(const double* src, long rows, long cols, long lds, void* dst, long ldd,
-                      int kind, cudaStream_t st);
+                      int kind, cudaStream_t st, double minus_diag = 0.0);
 int launch_convert_f32(const double* src, float* dst, long n, cudaStream_t st);
 // full Cholesky vectors transposed, rows (p, q) = p * Mp + q, pitch Gp, low precision
 int launch_pack_blocks_lo(const double* L, int G, int M, int Mp, int Gp, void* out, int kind,

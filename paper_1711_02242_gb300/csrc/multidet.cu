@@ -1,5 +1,5 @@
 // Multi-determinant trial (Sec. 3.4, Eqs. usesherman, precomputing,
-// precomputing2, localenergy2, localenergy3), float64 path.
+// precomputing2, localenergy2, localenergy3).
 //
 // Psi_T = sum_d A_d Psi_d with per-determinant spin-up and spin-down orbitals
 // V_ds; the walkers stay closed shell (both spin blocks phi).  Per walker and
@@ -11,11 +11,15 @@
 //   E_loc = H0 + sum_d w_d [sum_s Tr(hh_ds Theta_ds)
 //           + 1/2 sum_g (sum_s Tr(Lh_dsg Theta_ds))^2 - 1/2 sum_s sum_g Tr(T_dsg T_dsg)],
 //   T_dsg = Lh_dsg Theta_ds (the float64 exchange kernel, once per (d, s)).
+// On the mixed path the traces and the exchange of each (d, s) run on the
+// tensor cores from BF16/TF32 copies of Lh_ds and Theta_ds (written by the
+// overlap kernel); overlaps, weights and the combinations stay float64.
 // Every determinant is handled in full (the Sherman-Morrison-Woodbury
 // shortcut for determinants differing by a few orbitals is not used).  All in
 // the run's orthonormal basis, whose first N vectors are the leading spin-up
 // determinant's orbitals.
 #include "state.cuh"
+#include "tc.cuh"
 
 namespace afq {
 namespace {
@@ -29,7 +33,7 @@ __device__ inline double2 zmul(double2 a, double2 b) {
 // skipped; a singular S leaves log det = -inf and Theta = 0.
 __global__ void __launch_bounds__(256)
     k_md_overlap(int W, int M, int N, const double* __restrict__ Vt, const double* __restrict__ phi,
-                 const double* wt, double* theta, double* ldds) {
+                 const double* wt, double* theta, double* ldds, void* th_lo, int lo_kind, int Mp) {
   extern __shared__ double2 aug[];  // [N][2N]
   __shared__ double2 fac[64];
   __shared__ int prow, singular, swaps;
@@ -110,8 +114,13 @@ __global__ void __launch_bounds__(256)
     __syncthreads();
   }
   double* ld = ldds + ((long)w * gridDim.x + ds) * 2;
+  // the operand copy of Theta for the mixed path: rows (c, j) of pitch Mp
+  const long lo_row0 = ((long)ds * W + w) * 2 * N;
   if (singular) {
-    for (long t = tid; t < 2 * NM; t += blockDim.x) th[t] = 0.0;
+    for (long t = tid; t < 2 * NM; t += blockDim.x) {
+      th[t] = 0.0;
+      if (th_lo) store_lo(th_lo, lo_kind, (lo_row0 + t / M) * Mp + t % M, 0.0);
+    }
     if (tid == 0) {
       ld[0] = -INFINITY;
       ld[1] = 0.0;
@@ -135,6 +144,10 @@ __global__ void __launch_bounds__(256)
     }
     th[(long)j * M + p] = tr;
     th[NM + (long)j * M + p] = ti;
+    if (th_lo) {
+      store_lo(th_lo, lo_kind, (lo_row0 + j) * Mp + p, tr);
+      store_lo(th_lo, lo_kind, (lo_row0 + N + j) * Mp + p, ti);
+    }
   }
 }
 
@@ -180,9 +193,11 @@ __global__ void k_md_combine(int W, int nd, const double* logA, const double* ld
   ldout[2 * w + 1] = wrap_pi(atan2(ti, tr));
 }
 
-// t[w][c][g] = sum_(d,s) w_d (C_ds[(w,re)][g] + i C_ds[(w,im)][g]) as re/im planes.
-__global__ void k_md_fb_combine(int W, int nd, int G, const double* C, const double* wd,
-                                const double* wt, double* t) {
+// t[w][c][g] = sum_(d,s) w_d (C_ds[(w,re)][g] + i C_ds[(w,im)][g]) as re/im planes
+// (float64 traces and t on the float64 path, FP32 on the mixed path).
+template <typename TC>
+__global__ void k_md_fb_combine(int W, int nd, int G, const TC* C, const double* wd,
+                                const double* wt, TC* t) {
   const long n = (long)W * G;
   for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n;
        e += (long)gridDim.x * blockDim.x) {
@@ -193,22 +208,23 @@ __global__ void k_md_fb_combine(int W, int nd, int G, const double* C, const dou
       const double ar = wd[((long)w * nd + d) * 2], ai = wd[((long)w * nd + d) * 2 + 1];
       double cr = 0.0, ci = 0.0;
       for (int s = 0; s < 2; ++s) {
-        const double* Cd = C + (long)(2 * d + s) * 2 * W * G;
-        cr += Cd[(2L * w) * G + g];
-        ci += Cd[(2L * w + 1) * G + g];
+        const TC* Cd = C + (long)(2 * d + s) * 2 * W * G;
+        cr += (double)Cd[(2L * w) * G + g];
+        ci += (double)Cd[(2L * w + 1) * G + g];
       }
       sr += ar * cr - ai * ci;
       si += ar * ci + ai * cr;
     }
-    t[(2L * w) * G + g] = sr;
-    t[(2L * w + 1) * G + g] = si;
+    t[(2L * w) * G + g] = (TC)sr;
+    t[(2L * w + 1) * G + g] = (TC)si;
   }
 }
 
 // E_loc per walker (one block): sum_d w_d [one-body + Coulomb - exchange / 2] + H0.
+template <typename TC>
 __global__ void __launch_bounds__(256)
     k_md_eloc(int W, int nd, int M, int N, int G, int nchunk, double H0, const double* hh,
-              const double* theta, const double* C, const double* part, const double* wd,
+              const double* theta, const TC* C, const double* part, const double* wd,
               const double* wt, double* eloc) {
   __shared__ double sh[32];
   const int w = blockIdx.x;
@@ -236,9 +252,9 @@ __global__ void __launch_bounds__(256)
     for (int g = threadIdx.x; g < G; g += blockDim.x) {
       double tr = 0.0, ti = 0.0;
       for (int s = 0; s < 2; ++s) {
-        const double* Cd = C + (long)(2 * d + s) * 2 * W * G;
-        tr += Cd[(2L * w) * G + g];
-        ti += Cd[(2L * w + 1) * G + g];
+        const TC* Cd = C + (long)(2 * d + s) * 2 * W * G;
+        tr += (double)Cd[(2L * w) * G + g];
+        ti += (double)Cd[(2L * w + 1) * G + g];
       }
       cr += tr * tr - ti * ti;
       ci += 2.0 * tr * ti;
@@ -283,7 +299,7 @@ int md_overlap_update(afqmc_state* s, bool into_ld) {
   AFQ_CUDA(cudaFuncSetAttribute(k_md_overlap, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)smem));
   AFQ_LAUNCH(k_md_overlap, dim3(2 * nd, W), 256, smem, s->st, W, M, N, b.md_V, b.phiT, b.wt,
-             b.md_theta, b.md_ld);
+             b.md_theta, b.md_ld, b.mixed ? b.md_theta_lo : nullptr, b.lo_kind, b.Mp);
   AFQ_LAUNCH(k_md_combine, cdiv(W, 128), 128, 0, s->st, W, nd, b.md_logA, b.md_ld, b.wt,
              into_ld ? b.ld : b.ld_new, b.md_w);
   return AFQMC_OK;
@@ -312,12 +328,41 @@ static int md_traces(afqmc_state* s) {
   return gemm_nt_f64(g, s->st);
 }
 
+// Mixed path: the same traces on the tensor cores from the BF16/TF32 copies.
+static int md_traces_lo(afqmc_state* s) {
+  const afqmc_params& p = s->p;
+  const Bufs& b = s->b;
+  const int W = p.nwalkers, N = p.N, G = p.nchol, nd = p.ndet;
+  const long rowA = (long)N * b.Mp;
+  for (int ds = 0; ds < 2 * nd; ++ds) {
+    TcGemm g;
+    g.m = 2 * W;
+    g.n = G;
+    g.k = N * b.Mp;
+    g.A = static_cast<const char*>(b.md_theta_lo) + (size_t)ds * 2 * W * rowA * b.lo_bytes;
+    g.lda = rowA;
+    g.B = static_cast<const char*>(b.md_Lh_lo) + (size_t)ds * G * rowA * b.lo_bytes;
+    g.ldb = rowA;
+    g.tf32 = b.lo_kind == LO_TF32;
+    g.err = b.status;
+    AFQ_TRY(tc_gemm_store(g, b.md_C32 + (size_t)ds * 2 * W * G, G, 1.0f, s->st));
+  }
+  return AFQMC_OK;
+}
+
 int md_force_bias(afqmc_state* s) {
   const afqmc_params& p = s->p;
   const Bufs& b = s->b;
+  const unsigned grid = cdiv((size_t)p.nwalkers * p.nchol, 256);
+  if (b.mixed) {
+    AFQ_TRY(md_traces_lo(s));
+    AFQ_LAUNCH(k_md_fb_combine<float>, grid, 256, 0, s->st, p.nwalkers, p.ndet, p.nchol, b.md_C32,
+               b.md_w, b.wt, b.t32);
+    return AFQMC_OK;
+  }
   AFQ_TRY(md_traces(s));
-  AFQ_LAUNCH(k_md_fb_combine, cdiv((size_t)p.nwalkers * p.nchol, 256), 256, 0, s->st, p.nwalkers,
-             p.ndet, p.nchol, b.md_C, b.md_w, b.wt, b.t);
+  AFQ_LAUNCH(k_md_fb_combine<double>, grid, 256, 0, s->st, p.nwalkers, p.ndet, p.nchol, b.md_C,
+             b.md_w, b.wt, b.t);
   return AFQMC_OK;
 }
 
@@ -328,20 +373,33 @@ int md_local_energies(afqmc_state* s) {
   const int W = p.nwalkers, N = p.N, M = p.M, G = p.nchol, nd = p.ndet;
   const long NM = (long)N * M;
   for (int ds = 0; ds < 2 * nd; ++ds) {
-    ExchArgs ex{W,
-                M,
-                N,
-                G,
-                b.gc,
-                b.nchunk,
-                b.md_Lh + (long)ds * G * NM,
-                b.md_theta + (long)ds * W * 2 * NM,
-                b.md_part + (long)ds * W * b.nchunk * 2,
-                b.wt};
-    AFQ_TRY(launch_exchange(ex, s->st));
+    double* part = b.md_part + (long)ds * W * b.nchunk * 2;
+    if (b.mixed) {
+      // T_g = Lh_dsg Theta_ds and sum_ij T_ij T_ji on the tensor cores
+      const long rowA = (long)N * b.Mp;
+      TcGemm g;
+      g.m = G * N;
+      g.n = 2 * N * W;
+      g.k = M;
+      g.A = static_cast<const char*>(b.md_Lh_lo) + (size_t)ds * G * rowA * b.lo_bytes;
+      g.lda = b.Mp;
+      g.B = static_cast<const char*>(b.md_theta_lo) + (size_t)ds * 2 * W * rowA * b.lo_bytes;
+      g.ldb = b.Mp;
+      g.tf32 = b.lo_kind == LO_TF32;
+      g.err = b.status;
+      AFQ_TRY(tc_exchange(g, G, W, N, part, b.nchunk, s->st));
+    } else {
+      ExchArgs ex{W, M, N, G, b.gc, b.nchunk, b.md_Lh + (long)ds * G * NM,
+                  b.md_theta + (long)ds * W * 2 * NM, part, b.wt};
+      AFQ_TRY(launch_exchange(ex, s->st));
+    }
   }
-  AFQ_LAUNCH(k_md_eloc, W, 256, 0, s->st, W, nd, M, N, G, b.nchunk, p.H0, b.md_hh, b.md_theta,
-             b.md_C, b.md_part, b.md_w, b.wt, b.eloc);
+  if (b.mixed)
+    AFQ_LAUNCH(k_md_eloc<float>, W, 256, 0, s->st, W, nd, M, N, G, b.nchunk, p.H0, b.md_hh,
+               b.md_theta, b.md_C32, b.md_part, b.md_w, b.wt, b.eloc);
+  else
+    AFQ_LAUNCH(k_md_eloc<double>, W, 256, 0, s->st, W, nd, M, N, G, b.nchunk, p.H0, b.md_hh,
+               b.md_theta, b.md_C, b.md_part, b.md_w, b.wt, b.eloc);
   return AFQMC_OK;
 }
 
@@ -381,6 +439,12 @@ int md_setup(afqmc_state* s, const double* coef) {
     AFQ_TRY(gemm_nt_f64(h, s->st));
   }
   AFQ_LAUNCH(k_md_meanfield, G, 256, 0, s->st, G, NM, b.md_Lh, b.md_V, b.c);
+  if (b.mixed) {
+    // operand copies: the half-rotated vectors (pitch Mp) and Theta's padding
+    AFQ_TRY(launch_convert_lo(b.md_Lh, 2L * nd * G * N, M, M, b.md_Lh_lo, b.Mp, b.lo_kind, s->st));
+    AFQ_CUDA(cudaMemsetAsync(b.md_theta_lo, 0,
+                             (size_t)2 * nd * p.nwalkers * 2 * N * b.Mp * b.lo_bytes, s->st));
+  }
   std::vector<double> la(2 * (size_t)nd);
   for (int d = 0; d < nd; ++d) {
     const double ar = coef[2 * d], ai = coef[2 * d + 1];

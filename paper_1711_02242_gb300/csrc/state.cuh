@@ -60,6 +60,10 @@ struct Bufs {
   double *md_V = nullptr, *md_Lh = nullptr, *md_hh = nullptr, *md_theta = nullptr;
   double *md_ld = nullptr, *md_w = nullptr, *md_C = nullptr, *md_part = nullptr;
   double* md_logA = nullptr;
+  // mixed path: Theta_ds rows [2nd][W][2N][Mp] and Lh_ds rows [2nd][G N][Mp]
+  // as BF16/TF32, FP32 traces [2nd][2W][G]
+  void *md_theta_lo = nullptr, *md_Lh_lo = nullptr;
+  float* md_C32 = nullptr;
 };
 
 constexpr int kBpSlices = 8;
@@ -110,7 +114,8 @@ int bp_record_fields(afqmc_state* s);
 int bp_step_factor(afqmc_state* s);
 int bp_after_comb(afqmc_state* s);
 int apply_b_f64(afqmc_state* s, const double* phi_in, double* phi_out, const double* mask);
-int apply_b_mixed(afqmc_state* s, const void* phi_lo_in, double* phi_out, void* phi_lo_out);
+int apply_b_mixed(afqmc_state* s, const double* phi_in, const void* phi_lo_in, double* phi_out,
+                  void* phi_lo_out);
 int md_overlap_update(afqmc_state* s, bool into_ld);
 int md_force_bias(afqmc_state* s);
 int md_local_energies(afqmc_state* s);

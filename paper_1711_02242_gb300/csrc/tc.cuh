@@ -29,14 +29,17 @@ int tc_tune_store(const TcGemm& g, float* C, long ldc, float alpha, cudaStream_t
 // with the fused sum_ij T_ij T_ji epilogue; part [W][nchunk][2] (float64).
 // Propagation on tcgen05 (mixed path): first half step, Taylor terms, last
 // half step (see the epilogues in gemm_tc.cu for the operand layouts).
-int tc_prop_first(const TcGemm& g, float* acc, long ldacc, void* tb, int lo_kind, int N, int M,
-                  int Mp, cudaStream_t st);
+// (B = D_B = B_half - I; phi_id = the float64 orbitals, pitch M, whose
+// identity part the epilogue adds)
+int tc_prop_first(const TcGemm& g, float* acc, long ldacc, void* tb, const double* phi_id,
+                  int lo_kind, int N, int M, int Mp, cudaStream_t st);
 // S = T_k (first) or S += T_k, T_k = scale * (V T_{k-1}); pitch lds
 int tc_taylor_term(const TcGemm& g, float* S, long lds, bool first, void* tb_out, int lo_kind,
                    int W, int N, int M, int Mp, float scale, cudaStream_t st);
 // also writes the BF16/TF32 copy of the new orbitals (pitch Mp) for live walkers
+// (A = [T_0 | S] = acc_id, pitch 2 Mp; B = [D_B | D_B]; the epilogue adds T_0 + S)
 int tc_prop_last(const TcGemm& g, double* phiT, const double* wt, int N, int M, void* phi_lo,
-                 int lo_kind, int Mp, cudaStream_t st);
+                 int lo_kind, int Mp, const float* acc_id, cudaStream_t st);
 // V = i sqrt(dt) sum_g x_g L_g from the full transposed vectors (rows p*Mp+q)
 // written directly as [Re V | Im V] rows (pitch 2 Mp) of each walker.
 int tc_v_full(const TcGemm& g, void* V, int lo_kind, int W, int M, int Mp, double sdt,

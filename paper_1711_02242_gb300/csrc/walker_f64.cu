@@ -1120,19 +1120,20 @@ int launch_sumsq(const double* v, double* out, int n, cudaStream_t st) {
 // ------------------------------------------------- low-precision copies ----
 namespace afq {
 __global__ void k_convert_lo(const double* src, long rows, long cols, long lds, void* dst,
-                             long ldd, int kind) {
+                             long ldd, int kind, double minus_diag) {
   const long n = rows * ldd;
   for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (long)gridDim.x * blockDim.x) {
     const long r = i / ldd, c = i % ldd;
-    store_lo(dst, kind, i, c < cols ? src[r * lds + c] : 0.0);
+    const double v = c < cols ? src[r * lds + c] - (r == c ? minus_diag : 0.0) : 0.0;
+    store_lo(dst, kind, i, v);
   }
 }
 
 int launch_convert_lo(const double* src, long rows, long cols, long lds, void* dst, long ldd,
-                      int kind, cudaStream_t st) {
+                      int kind, cudaStream_t st, double minus_diag) {
   if (rows <= 0) return AFQMC_OK;
-  AFQ_LAUNCH(k_convert_lo, 152 * 8, 256, 0, st, src, rows, cols, lds, dst, ldd, kind);
+  AFQ_LAUNCH(k_convert_lo, 152 * 8, 256, 0, st, src, rows, cols, lds, dst, ldd, kind, minus_diag);
   return AFQMC_OK;
 }
 

@@ -14,9 +14,10 @@ Case "mcd": the modified Cholesky decomposition over index pairs
 (afqmc_modified_cholesky_pairs, delta = 1e-6) of the interaction of the seeded
 Hamiltonian with `--orbitals` M orbitals and 6M vectors (the pair matrix is
 16.3 GB at M = 300, 1.3 GB at M = 160); one launch per vector.
-Case "md": the float64 walk of the M=100 workload (10+10 electrons, 500
-vectors, 1024 walkers) with a trial of 1, 2 and 4 non-orthogonal determinants
-(rotations of the RHF determinant): time per step and per energy evaluation.
+Case "md": the walk of the M=100 workload (10+10 electrons, 500 vectors, 1024
+walkers) in the `--dtype` precision with a trial of 1, 2 and 4 non-orthogonal
+determinants (rotations of the RHF determinant): time per step and per energy
+evaluation.
 Case "bp": the M=300 walk (512 walkers, 1800 vectors, RHF trial) with a
 back-propagation window of `--window` steps: time per step without and with
 the window open, and the time of afqmc_bp_end (backward sweep and densities).
@@ -226,7 +227,8 @@ def md(a):
         dn = np.array([C] + [rotated() for _ in range(nd - 1)])
         coef = np.array([1.0] + [0.3 / nd] * (nd - 1), np.complex128)
         p = pkg.default_params(w.M, w.N, w.nchol, w.nwalkers, dt=w.dt, seed=w.seed, H0=H0,
-                               qr_period=w.qr_period, energy_period=0, ndet=nd)
+                               qr_period=w.qr_period, energy_period=0, ndet=nd,
+                               precision={"fp64": 0, "tf32": 1, "bf16": 2}[a.dtype])
         run = pkg.AfqmcRun(h1, L, (coef, up, dn), p, stream=st)
         run.propagate(2)
         st.synchronize()
@@ -241,7 +243,7 @@ def md(a):
         t0 = time.perf_counter()
         run.local_energies()
         te = 1e3 * (time.perf_counter() - t0)
-        print(f"case md fp64 M={w.M} N={w.N} nchol={w.nchol} walkers={w.nwalkers} ndet={nd}: "
+        print(f"case md {a.dtype} M={w.M} N={w.N} nchol={w.nchol} walkers={w.nwalkers} ndet={nd}: "
               f"ms/step={ms:.2f} walker-steps/s={w.nwalkers / ms * 1e3:.0f} energy-eval ms={te:.2f} "
               f"status={run.info().status} alive={run.info().alive}")
         run.close()

@@ -95,3 +95,32 @@ def test_mixed_full_size_runs_clean(pkg):
     r64 = pkg.AfqmcRun(h1, L, C, p64)
     e64 = r64.local_energies()[0]
     assert abs(e_mixed_trial - e64) < 5e-3 * abs(e64)
+
+
+@pytest.mark.parametrize("prec,tol_bias,tol_phi", [(2, 4e-3, 8e-3), (1, 2e-3, 2e-3)])
+def test_mixed_weights_carry_no_common_drift(pkg, prec, tol_bias, tol_phi):
+    """Seven steps of the mixed and float64 paths on the same fields: the
+    ratio of each walker's weight to its float64 value stays 1 on average.
+    B_half = exp(-dt v0'/2) has a diagonal close to 1; rounded to BF16/TF32 it
+    would scale every walker's orbitals by the same factor each step (a
+    common weight drift of about -1 %/step in BF16), so the half steps apply
+    it as I + (B_half - I) with the identity part exact."""
+    h1, L, _ = workloads.hamiltonian(24, 120, 6100, l_scale=workloads.l_amplitude(24, 120))
+    C, _, _, _ = scf.rhf(h1, L, 4)
+    out = []
+    for precision in (0, prec):
+        p = pkg.default_params(24, 4, 120, 64, dt=0.01, seed=4, qr_period=5, energy_period=1,
+                               precision=precision)
+        run = pkg.AfqmcRun(h1, L, C, p)
+        run.propagate(7)
+        out.append(run.get_walkers())
+        assert run.info().status == 0
+        run.close()
+    (phi0, w0, _), (phi1, w1, _) = out
+    alive = np.nonzero((w0 != 0) & (w1 != 0))[0]
+    assert alive.size > 32
+    ratio = (w1[alive] / w0[alive]).real
+    assert abs(np.mean(ratio) - 1) < tol_bias
+    d = np.linalg.norm((phi1 - phi0)[alive].reshape(alive.size, -1), axis=1)
+    n = np.linalg.norm(phi0[alive].reshape(alive.size, -1), axis=1)
+    assert np.max(d / n) < tol_phi

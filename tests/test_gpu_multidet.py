@@ -3,7 +3,8 @@ usesherman, precomputing2, localenergy2/3) against the oracle's
 multi-determinant walk (oracle.multidet).
 
 Float64 path: walkers, weights, log-overlaps and energy records agree with the
-oracle to 1e-10 relative at every checked step.  Trials: three non-orthogonal
+oracle to 1e-10 relative at every checked step; the mixed path agrees with
+the float64 path within the operand rounding.  Trials: three non-orthogonal
 determinants (each spin of each determinant a different rotation of the RHF
 orbitals, so spin-up and spin-down orbitals differ) with complex
 coefficients; a ragged shape with two determinants; a one-determinant trial
@@ -124,11 +125,43 @@ def test_one_determinant_is_the_single_determinant_walk(pkg):
     b.close()
 
 
+@pytest.mark.parametrize("prec,tol_e,tol_phi", [(2, 3e-3, 1.5e-2), (1, 4e-4, 2e-3)])
+def test_mixed_path_close_to_float64(pkg, prec, tol_e, tol_phi):
+    """The mixed path (the force-bias traces and the exchange of every
+    determinant and spin on the tensor cores from BF16/TF32 copies of Lh_ds and
+    Theta_ds; overlaps, weights and combinations in float64) against the
+    float64 path on the same trial, seed and steps: they differ by the operand
+    rounding only (BF16 2^-9, TF32 2^-11 relative per operand)."""
+    M, N, G, W, nd = 24, 4, 120, 64, 3
+    h1, L, coef, up, dn = noci_trial(M, N, G, 7300, nd)
+    out = []
+    for precision in (0, prec):
+        p = pkg.default_params(M, N, G, W, dt=0.01, seed=4, qr_period=5, energy_period=1,
+                               ndet=nd, precision=precision)
+        run = pkg.AfqmcRun(h1, L, (coef, up, dn), p)
+        e0 = run.local_energies()
+        run.propagate(7)
+        out.append((run.info().E_T, e0, run.get_walkers(), run.energy_log()))
+        assert run.info().status == 0
+        run.close()
+    (et0, e00, (phi0, w0, _), log0), (et1, e01, (phi1, w1, _), log1) = out
+    assert abs(et1 - et0) < tol_e * abs(et0)
+    assert np.max(np.abs(e01 - e00) / np.abs(e00)) < tol_e
+    alive = np.nonzero(w0 != 0)[0]
+    assert np.array_equal(np.nonzero(w1 != 0)[0], alive) and alive.size > W // 2
+    d = np.linalg.norm((phi1 - phi0)[alive].reshape(alive.size, -1), axis=1)
+    n = np.linalg.norm(phi0[alive].reshape(alive.size, -1), axis=1)
+    assert np.max(d / n) < tol_phi
+    assert np.max(np.abs(w1[alive] - w0[alive]) / w0[alive]) < tol_phi
+    assert log1.shape == log0.shape
+    assert np.max(np.abs(log1[:, 1] - log0[:, 1]) / np.abs(log0[:, 1])) < tol_e
+
+
 def test_errors(pkg):
     M, N, G, W = 12, 3, 48, 8
     h1, L, coef, up, dn = noci_trial(M, N, G, 7200, 2)
-    for kw in (dict(precision=pkg.AFQMC_MIXED_BF16), dict(pc_period=5), dict(bp_steps=4),
-               dict(mode=pkg.AFQMC_FREE)):
+    for kw in (dict(pc_period=5), dict(bp_steps=4), dict(mode=pkg.AFQMC_FREE),
+               dict(pc_period=5, precision=pkg.AFQMC_MIXED_BF16)):
         with pytest.raises(pkg.AfqmcError, match="EUNSUPPORTED"):
             pkg.afqmc_workspace_size(pkg.default_params(M, N, G, W, ndet=2, **kw))
     import ctypes
