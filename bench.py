@@ -178,6 +178,30 @@ def algorithmic_per_walker(w: workloads.Workload):
             "energy": 4 * G * N * M + 4 * G * N * N * M}
 
 
+def bytes_per_walker(w: workloads.Workload, precision):
+    """Algorithmic DRAM bytes per walker of the mixed path's FP32 kernels,
+    which are bound by memory traffic, not by their FP32 arithmetic:
+      theta  read Phi (2 N M float64) and S^-1 (N^2 complex), write Theta
+             (2 N M float64) and its BF16/TF32 copy (2 N Mp);
+      qr     read and write Phi (2 x 2 N M float64), write its BF16/TF32 copy."""
+    M, N = w.M, w.N
+    Mp = (M + 15) // 16 * 16
+    lo = 2 if precision == "bf16" else 4
+    return {"theta": 2 * N * M * 8 + N * N * 16 + 2 * N * M * 8 + 2 * N * Mp * lo,
+            "qr": 2 * (2 * N * M * 8) + 2 * N * Mp * lo}
+
+
+def kernel_of_phase(precision):
+    """Phase -> (kernel, bound, source file).  The mixed path computes Theta
+    and the Gram-Schmidt sweep in FP32 (HBM-bound kernels); the float64 path
+    keeps the FP64-pipe kernels."""
+    k = dict(KERNEL_OF_PHASE)
+    if precision != "fp64":
+        k["theta"] = ("k_theta_rows_f32", "hbm", "walker_f64.cu")
+        k["qr"] = ("k_mgs_f32", "hbm", "walker_f64.cu")
+    return k
+
+
 KERNEL_OF_PHASE = {"overlap": ("k_overlap", "alu", "walker_f64.cu"),
                    "theta": ("k_theta_rows", "alu", "walker_f64.cu"),
                    "qr": ("k_mgs", "alu", "walker_f64.cu"),
@@ -204,13 +228,26 @@ def rooflines(w, phases, precision, K):
     stream) against the peak of the pipe that bounds it."""
     pk, pk_kind = peaks()
     per = algorithmic_per_walker(w)
+    per_bytes = bytes_per_walker(w, precision)
     out = []
-    for ph, (kname, bound, src) in KERNEL_OF_PHASE.items():
+    for ph, (kname, bound, src) in kernel_of_phase(precision).items():
         v = phases[ph]
         if v["count"] == 0 or v["ms"] <= 0:
             continue
         ms_launch = v["ms"] / v["count"]
         work = per[ph] * w.nwalkers
+        if bound == "hbm":
+            # bytes per launch / time, against the measured copy bandwidth
+            peak, unit, src_peak = pk["hbm_gbs"], "GB/s", f"{pk_kind} HBM copy bandwidth"
+            achieved = per_bytes[ph] * w.nwalkers / (ms_launch * 1e-3) / 1e9
+            tr = TRAFFIC.get(ph)
+            traffic = tr["bytes"] if tr and tr.get("sha") == source_sha(src) else None
+            out.append({"phase": ph, "kernel": kname, "bound": bound, "achieved": achieved,
+                        "peak": peak, "unit": unit, "frac": achieved / peak, "traffic": traffic,
+                        "peak_source": src_peak, "ms_per_launch": ms_launch,
+                        "launches_per_step": v["count"] / K,
+                        "share_of_step": v["ms"] / sum(x["ms"] for x in phases.values())})
+            continue
         if bound == "alu" or precision == "fp64":
             peak, unit, src_peak = FP64_PEAK_TFLOPS, "TFLOP/s", (
                 "derived: 152 SMs x 2 FP64 FMA/clk x 2 x 2070 MHz")

@@ -383,6 +383,18 @@ AFQMC_API int afqmc_gaussian_fields(uint64_t seed, int64_t step, int32_t w0, int
                                     int32_t nchol, double* d_out, void* stream);
 
 /*
+ * The IEEE 754 conversions the mixed path's kernels use between the float64
+ * orbitals and their FP32 arithmetic (binary64 -> binary32 rounded to
+ * nearest, ties to even; binary32 -> binary64 exact), done in integer
+ * arithmetic.  d_in / d_out: n DEVICE elements owned by the caller
+ * (float64 -> float32 for afqmc_round_f32, float32 -> float64 for
+ * afqmc_widen_f32); asynchronous on `stream`.  The results are those of the
+ * hardware conversions, bit for bit.
+ */
+AFQMC_API int afqmc_round_f32(const double* d_in, float* d_out, int64_t n, void* stream);
+AFQMC_API int afqmc_widen_f32(const float* d_in, double* d_out, int64_t n, void* stream);
+
+/*
  * Local energies for callers that cannot allocate device memory.
  *
  * The paper has no counterpart: this is the float64 local-energy evaluation

@@ -35,7 +35,7 @@ EXPORTED = ["afqmc_default_params", "afqmc_workspace_size", "afqmc_init", "afqmc
             "afqmc_wait_flag", "afqmc_taylor_series", "afqmc_mcd_workspace_size",
             "afqmc_modified_cholesky", "afqmc_mcd_pairs_workspace_size",
             "afqmc_modified_cholesky_pairs", "afqmc_bp_begin", "afqmc_bp_end",
-            "afqmc_init_multidet"]
+            "afqmc_init_multidet", "afqmc_round_f32", "afqmc_widen_f32"]
 
 
 class Params(ctypes.Structure):
@@ -94,6 +94,8 @@ def lib():
         "afqmc_last_error": (ctypes.c_char_p, []),
         "afqmc_launch_count": (ctypes.c_int64, []),
         "afqmc_philox4x32_10": (ctypes.c_int, [ctypes.c_uint64, vp, ctypes.c_int64, vp, vp]),
+        "afqmc_round_f32": (ctypes.c_int, [vp, vp, ctypes.c_int64, vp]),
+        "afqmc_widen_f32": (ctypes.c_int, [vp, vp, ctypes.c_int64, vp]),
         "afqmc_gaussian_fields": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_int64, ctypes.c_int32,
                                                  ctypes.c_int32, ctypes.c_int32, vp, vp]),
         "afqmc_contract": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int64, ctypes.c_int64,
@@ -169,6 +171,31 @@ def afqmc_philox4x32_10(key: int, ctr):
     st = torch.cuda.current_stream(ctr.device)
     _check(lib().afqmc_philox4x32_10(key, ctypes.c_void_p(ctr.data_ptr()), ctr.shape[0],
                                      ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(st.cuda_stream)))
+    return out
+
+
+def afqmc_round_f32(x):
+    """float64 CUDA tensor -> float32 by the integer-arithmetic conversion the
+    mixed path's kernels use (round to nearest, ties to even)."""
+    import torch
+
+    x = x.contiguous()
+    out = torch.empty(x.shape, dtype=torch.float32, device=x.device)
+    st = torch.cuda.current_stream(x.device)
+    _check(lib().afqmc_round_f32(ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                 x.numel(), ctypes.c_void_p(st.cuda_stream)))
+    return out
+
+
+def afqmc_widen_f32(x):
+    """float32 CUDA tensor -> float64 (exact) by the mixed path's conversion."""
+    import torch
+
+    x = x.contiguous()
+    out = torch.empty(x.shape, dtype=torch.float64, device=x.device)
+    st = torch.cuda.current_stream(x.device)
+    _check(lib().afqmc_widen_f32(ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                 x.numel(), ctypes.c_void_p(st.cuda_stream)))
     return out
 
 

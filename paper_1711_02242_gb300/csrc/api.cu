@@ -262,6 +262,7 @@ int overlap_update(afqmc_state* s, bool into_ld, bool timed) {
     ov.th_lo = b.th_lo;
     ov.lo_kind = b.lo_kind;
     ov.Mp = b.Mp;
+    ov.Sinv32 = reinterpret_cast<float2*>(b.Sinv);  // FP32 elimination and Theta
   }
   if (timed) prof_begin(s, AFQMC_PH_OVERLAP);
   AFQ_TRY(launch_overlap(ov, s->st));
@@ -557,8 +558,14 @@ static int step_once(afqmc_state* s) {
     // Phi -> Q; Theta is unchanged and log det S drops by sum_k log r_kk,
     // which the kernel applies to ld (no new overlap needed)
     MgsArgs ma{W, M, N, b.phiT, b.wt, b.ld};
+    if (b.mixed) {
+      // FP32 sweep; the kernel also writes the operand copy of the orbitals
+      ma.f32 = 1;
+      ma.phi_lo = b.phi_lo;
+      ma.lo_kind = b.lo_kind;
+      ma.Mp = b.Mp;
+    }
     AFQ_TRY(launch_mgs(ma, s->st));
-    AFQ_TRY(refresh_phi_lo(s));
     prof_end(s);
   }
   if (p.pc_period && n % p.pc_period == 0) {
@@ -1421,6 +1428,8 @@ int launch_philox(uint64_t key, const uint32_t* ctr, long n, uint32_t* out, cuda
 int launch_wait_flag(const int* flag, long long max_polls, int* status, cudaStream_t st);
 int launch_fields(uint64_t seed, uint32_t step, int w0, int nw, int G, double* out,
                   cudaStream_t st);
+int launch_round_f32(const double* src, float* dst, long n, cudaStream_t st);
+int launch_widen_f32(const float* src, double* dst, long n, cudaStream_t st);
 }  // namespace afq
 
 extern "C" {
@@ -1440,6 +1449,22 @@ int afqmc_philox4x32_10(uint64_t key, const uint32_t* d_ctr, int64_t n, uint32_t
     return AFQMC_EINVAL;
   }
   return afq::launch_philox(key, d_ctr, (long)n, d_out, static_cast<cudaStream_t>(stream));
+}
+
+int afqmc_round_f32(const double* d_in, float* d_out, int64_t n, void* stream) {
+  if (n < 0 || (n > 0 && (!d_in || !d_out))) {
+    afq::set_error("bad arguments");
+    return AFQMC_EINVAL;
+  }
+  return afq::launch_round_f32(d_in, d_out, (long)n, static_cast<cudaStream_t>(stream));
+}
+
+int afqmc_widen_f32(const float* d_in, double* d_out, int64_t n, void* stream) {
+  if (n < 0 || (n > 0 && (!d_in || !d_out))) {
+    afq::set_error("bad arguments");
+    return AFQMC_EINVAL;
+  }
+  return afq::launch_widen_f32(d_in, d_out, (long)n, static_cast<cudaStream_t>(stream));
 }
 
 int afqmc_gaussian_fields(uint64_t seed, int64_t step, int32_t w0, int32_t nw, int32_t nchol,

@@ -331,11 +331,11 @@ __device__ __forceinline__ void put_term(void* tb, int kind, long wrow, int N, i
                                          int i, int p, float v) {
   const long rr = (wrow + i) * 2L * Mp, ri = (wrow + N + i) * 2L * Mp;
   if (c == 0) {
-    store_lo(tb, kind, rr + p, v);
-    store_lo(tb, kind, ri + Mp + p, v);
+    store_lo_f(tb, kind, rr + p, v);
+    store_lo_f(tb, kind, ri + Mp + p, v);
   } else {
-    store_lo(tb, kind, rr + Mp + p, -v);
-    store_lo(tb, kind, ri + p, v);
+    store_lo_f(tb, kind, rr + Mp + p, -v);
+    store_lo_f(tb, kind, ri + p, v);
   }
 }
 
@@ -647,7 +647,7 @@ struct EpiPhi {
       } else {
 #pragma unroll
         for (int u = 0; u < 16; ++u)
-          if (pb + u < M) store_lo(phi_lo, lo_kind, (long)row * Mp + pb + u, v[u]);
+          if (pb + u < M) store_lo_f(phi_lo, lo_kind, (long)row * Mp + pb + u, v[u]);
       }
     }
   }

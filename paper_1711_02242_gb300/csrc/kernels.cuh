@@ -23,6 +23,45 @@ __device__ __forceinline__ float round_tf32(float x) {
   return __uint_as_float(r);
 }
 
+// IEEE 754 binary64 -> binary32 with round to nearest, ties to even (IEEE
+// 754-2008, Secs. 4.3.1 and 5.4.2), in integer arithmetic: this GPU runs F2F
+// conversions on its narrow FP64 pipe, the integer pipe is many times wider.
+// Results that are normal floats (including a round-up to infinity from the
+// top binade) and zeros take the integer path; subnormal, overflowing,
+// infinite and NaN inputs take the hardware conversion.
+__device__ __forceinline__ float f64_to_f32(double x) {
+  const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
+  const uint32_t e = (hi >> 20) & 0x7ffu;
+  if (e - 897u < 254u) {
+    // sign, exponent re-biased from 1023 to 127, the top 23 of 52 mantissa bits
+    uint32_t r = (hi & 0x80000000u) | ((e - 896u) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+    const uint32_t rest = lo & 0x1fffffffu;  // the 29 bits dropped
+    r += (rest > 0x10000000u || (rest == 0x10000000u && (r & 1u))) ? 1u : 0u;
+    return __uint_as_float(r);
+  }
+  if (((hi << 1) | lo) == 0u) return __uint_as_float(hi & 0x80000000u);
+  return __double2float_rn(x);
+}
+
+// binary32 -> binary64 (exact) in integer arithmetic, as above.
+__device__ __forceinline__ double f32_to_f64(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t e = (u >> 23) & 0xffu;
+  if (e - 1u < 254u)
+    return __hiloint2double((int)((u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7fffffu) >> 3)),
+                            (int)(u << 29));
+  if ((u << 1) == 0u) return __hiloint2double((int)(u & 0x80000000u), 0);
+  return (double)f;
+}
+
+// FP32 value into a BF16 / TF32 operand copy (no float64 step).
+__device__ __forceinline__ void store_lo_f(void* base, int kind, long idx, float v) {
+  if (kind == LO_BF16)
+    reinterpret_cast<__nv_bfloat16*>(base)[idx] = __float2bfloat16_rn(v);
+  else
+    reinterpret_cast<float*>(base)[idx] = round_tf32(v);
+}
+
 __device__ __forceinline__ void store_lo(void* base, int kind, long idx, double v) {
   if (kind == LO_BF16)
     reinterpret_cast<__nv_bfloat16*>(base)[idx] = __double2bfloat16(v);
@@ -92,6 +131,7 @@ struct OverlapArgs {
   int lo_kind = LO_NONE, Mp = 0;
   int unit_trial = 0;  // VTt = [I_N | 0]: S is the top block of Phi, Theta's top rows I
   double2* Sinv = nullptr;  // [W][N][N] scratch: S^-1 of live walkers
+  float2* Sinv32 = nullptr;  // mixed path: FP32 elimination, S^-1 here and FP32 Theta
 };
 // S^-1 and log det (k_overlap), then Theta (k_theta_rows)
 int launch_overlap(const OverlapArgs& a, cudaStream_t st);
@@ -115,6 +155,9 @@ struct MgsArgs {
   double* phiT;  // [W][2][N][M] in place
   const double* wt;
   double* ld;    // [W][2]: log <Psi_T|Psi> of live walkers, lowered by 2 sum_k log r_kk
+  int f32 = 0;   // mixed path: FP32 sweep in shared memory where [N][M] fits
+  void* phi_lo = nullptr;  // and, if set, the BF16/TF32 copy of the result (pitch Mp)
+  int lo_kind = LO_NONE, Mp = 0;
 };
 int launch_mgs(const MgsArgs& a, cudaStream_t st);
 

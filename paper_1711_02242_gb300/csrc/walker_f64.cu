@@ -130,8 +130,8 @@ __global__ void __launch_bounds__(256) k_field_lo(FieldArgs a) {
       }
       float vr = xi - br, vi = -bi;
       if (!alive) vr = vi = 0.f;
-      store_lo(a.x_lo, a.lo_kind, xl + g, vr);
-      store_lo(a.x_lo, a.lo_kind, xl + a.Gp + g, vi);
+      store_lo_f(a.x_lo, a.lo_kind, xl + g, vr);
+      store_lo_f(a.x_lo, a.lo_kind, xl + a.Gp + g, vi);
       s[0] = fmaf(xi, br, s[0]);
       s[1] = fmaf(xi, bi, s[1]);
       s[2] += br * br - bi * bi;
@@ -268,23 +268,49 @@ int launch_taylor_term(const TaylorArgsT<double>& a, cudaStream_t st) { return l
 namespace {
 constexpr int OV_T = 256;
 }
+// Element traits of the overlap kernel: float64 on the float64 path; FP32 on
+// the mixed path, whose orbitals carry BF16/TF32 propagation errors far above
+// FP32 rounding (the log det sums stay float64).
+template <typename T>
+struct Vec2;
+template <>
+struct Vec2<double> {
+  using type = double2;
+  __device__ static double2 make(double x, double y) { return make_double2(x, y); }
+  __device__ static double from_f64(double x) { return x; }
+  __device__ static double to_f64(double x) { return x; }
+  __device__ static double2* sinv(const OverlapArgs& a) { return a.Sinv; }
+};
+template <>
+struct Vec2<float> {
+  using type = float2;
+  __device__ static float2 make(float x, float y) { return make_float2(x, y); }
+  __device__ static float from_f64(double x) { return f64_to_f32(x); }
+  __device__ static double to_f64(float x) { return f32_to_f64(x); }
+  __device__ static float2* sinv(const OverlapArgs& a) { return a.Sinv32; }
+};
+
+template <typename T>
 __global__ void __launch_bounds__(OV_T) k_overlap(OverlapArgs a) {
-  extern __shared__ double2 ov_sm[];
+  using T2 = typename Vec2<T>::type;
+  extern __shared__ __align__(16) unsigned char ov_raw[];
+  __shared__ __align__(16) unsigned char misc_raw[sizeof(T2) * 129];
   const int w = blockIdx.x;
   const bool live = !a.wt || walker_alive(a.wt, w);
   const int N = a.N, M = a.M;
-  double2* A = ov_sm;  // [N][N], inverted in place
+  T2* A = reinterpret_cast<T2*>(ov_raw);  // [N][N], inverted in place
   __shared__ int swaps, singular;
-  __shared__ double2 rpiv;
-  __shared__ double2 pivots[64];  // the pivots, for log det after the elimination
-  __shared__ double2 fac[64];     // a_rk / p of the current pivot column
+  T2& rpiv = reinterpret_cast<T2*>(misc_raw)[128];
+  T2* pivots = reinterpret_cast<T2*>(misc_raw);       // the pivots, for log det afterwards
+  T2* fac = reinterpret_cast<T2*>(misc_raw) + 64;     // a_rk / p of the current pivot column
   __shared__ int order[64], pos[64];
   const double* fr = a.phiT + (long)w * 2 * N * M;
   const double* fi = fr + (long)N * M;
   // S[i][j] = Phi[i][j], the top block of the orbitals
   for (int idx = threadIdx.x; idx < N * N; idx += OV_T) {
     const int i = idx / N, j = idx % N;
-    A[idx] = make_double2(fr[(long)j * M + i], fi[(long)j * M + i]);
+    A[idx] = Vec2<T>::make(Vec2<T>::from_f64(fr[(long)j * M + i]),
+                           Vec2<T>::from_f64(fi[(long)j * M + i]));
   }
   if (threadIdx.x < N) order[threadIdx.x] = threadIdx.x;
   if (threadIdx.x == 0) {
@@ -302,10 +328,10 @@ __global__ void __launch_bounds__(OV_T) k_overlap(OverlapArgs a) {
     if (threadIdx.x < 32) {
       // pivot: the largest |a_rk|^2 over rows r >= k, the first such row on ties
       int best = k;
-      double bv = -1.0;
+      T bv = -1;
       for (int r = k + threadIdx.x; r < N; r += 32) {
-        const double2 x = A[r * N + k];
-        const double v = x.x * x.x + x.y * x.y;
+        const T2 x = A[r * N + k];
+        const T v = x.x * x.x + x.y * x.y;
         if (v > bv) {
           bv = v;
           best = r;
@@ -313,17 +339,17 @@ __global__ void __launch_bounds__(OV_T) k_overlap(OverlapArgs a) {
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
-        const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        const T ov = __shfl_xor_sync(0xffffffffu, bv, o);
         const int ob = __shfl_xor_sync(0xffffffffu, best, o);
         if (ov > bv || (ov == bv && ob < best)) {
           bv = ov;
           best = ob;
         }
       }
-      if (bv > 0.0) {
+      if (bv > 0) {
         if (best != k) {
           for (int j = threadIdx.x; j < N; j += 32) {
-            const double2 t = A[k * N + j];
+            const T2 t = A[k * N + j];
             A[k * N + j] = A[best * N + j];
             A[best * N + j] = t;
           }
@@ -336,12 +362,12 @@ __global__ void __launch_bounds__(OV_T) k_overlap(OverlapArgs a) {
           __syncwarp();
         }
         // 1 / pivot once per lane (a float64 division runs long on the FP64 pipe)
-        const double2 pv = A[k * N + k];
-        const double den = pv.x * pv.x + pv.y * pv.y;
-        const double2 rp = make_double2(pv.x / den, -pv.y / den);
+        const T2 pv = A[k * N + k];
+        const T den = pv.x * pv.x + pv.y * pv.y;
+        const T2 rp = Vec2<T>::make(pv.x / den, -pv.y / den);
         for (int r = threadIdx.x; r < N; r += 32) {
-          const double2 x = A[r * N + k];
-          fac[r] = make_double2(x.x * rp.x - x.y * rp.y, x.x * rp.y + x.y * rp.x);
+          const T2 x = A[r * N + k];
+          fac[r] = Vec2<T>::make(x.x * rp.x - x.y * rp.y, x.x * rp.y + x.y * rp.x);
         }
         if (threadIdx.x == 0) {
           rpiv = rp;
@@ -358,26 +384,26 @@ __global__ void __launch_bounds__(OV_T) k_overlap(OverlapArgs a) {
     for (int idx = threadIdx.x; idx < n1 * n1; idx += blockDim.x) {
       const int ii = idx / n1, jj = idx - (idx / n1) * n1;
       const int i = ii < k ? ii : ii + 1, j = jj < k ? jj : jj + 1;
-      const double2 f = fac[i], v = A[k * N + j];
-      double2& d = A[i * N + j];
+      const T2 f = fac[i], v = A[k * N + j];
+      T2& d = A[i * N + j];
       d.x = fma(-f.x, v.x, fma(f.y, v.y, d.x));
       d.y = fma(-f.x, v.y, fma(-f.y, v.x, d.y));
     }
     __syncthreads();
     // pivot row / p, pivot column -a_ik / p, a_kk = 1 / p
-    const double2 rp = rpiv;
+    const T2 rp = rpiv;
     for (int t = threadIdx.x; t < 2 * N - 1; t += blockDim.x) {
       if (t < N) {
-        double2& d = A[k * N + t];
+        T2& d = A[k * N + t];
         if (t == k) {
           d = rp;
         } else {
-          const double2 v = d;
-          d = make_double2(v.x * rp.x - v.y * rp.y, v.x * rp.y + v.y * rp.x);
+          const T2 v = d;
+          d = Vec2<T>::make(v.x * rp.x - v.y * rp.y, v.x * rp.y + v.y * rp.x);
         }
       } else {
         const int i = t - N < k ? t - N : t - N + 1;
-        A[i * N + k] = make_double2(-fac[i].x, -fac[i].y);
+        A[i * N + k] = Vec2<T>::make(-fac[i].x, -fac[i].y);
       }
     }
     __syncthreads();
@@ -385,11 +411,13 @@ __global__ void __launch_bounds__(OV_T) k_overlap(OverlapArgs a) {
   if (threadIdx.x < N) pos[order[threadIdx.x]] = threadIdx.x;
   // log det = sum_k log |p_k| + i (sum_k arg p_k + pi swaps), the N logs and
   // phases in parallel, summed in a fixed order (warps 0 and 1: N <= 64)
+  // (float64 logs of the pivots also on the FP32 path: N per walker)
   double la = 0.0, ph = 0.0;
   if (!singular && threadIdx.x < N) {
-    const double2 pv = pivots[threadIdx.x];
-    la = 0.5 * log(pv.x * pv.x + pv.y * pv.y);
-    ph = atan2(pv.y, pv.x);
+    const double px = Vec2<T>::to_f64(pivots[threadIdx.x].x);
+    const double py = Vec2<T>::to_f64(pivots[threadIdx.x].y);
+    la = 0.5 * log(px * px + py * py);
+    ph = atan2(py, px);
   }
   __shared__ double red[4];
   if (threadIdx.x < 64) {
@@ -416,7 +444,7 @@ __global__ void __launch_bounds__(OV_T) k_overlap(OverlapArgs a) {
   // S^-1 of live, non-singular walkers for the Theta kernel: column c of the
   // inverse is column pos[c] of A (the row interchanges undone)
   if (singular || !live) return;
-  double2* si = a.Sinv + (long)w * N * N;
+  T2* si = Vec2<T>::sinv(a) + (long)w * N * N;
   for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x) {
     const int r = idx / N, c = idx - (idx / N) * N;
     si[idx] = A[r * N + pos[c]];
@@ -476,6 +504,82 @@ __global__ void __launch_bounds__(TH_T) k_theta_rows(OverlapArgs a) {
   }
 }
 
+// Mixed path: the same rows with FP32 arithmetic.  Theta only feeds the
+// BF16/TF32 contractions (force bias, exchange) and the one-body energy
+// there, so FP32 products (S^-1 and Phi rounded to FP32) lose nothing those do
+// not, and this GPU's FP32 pipe is ~60x its FP64 one: the kernel becomes bound
+// by the traffic of Phi and Theta.  The block's TH_P columns of Phi are staged
+// in shared memory as FP32 (all loads in flight at once, converted once);
+// one work item = row p and IB orbitals i, IB = N / ceil(N / 16) rounded up
+// (guarded tail of at most ceil(N / 16) - 1 lanes); S^-1 reads are warp-wide
+// broadcasts.  Conversions use the integer-pipe routines.
+template <int TF_IB>
+__global__ void __launch_bounds__(TH_T) k_theta_rows_f32(OverlapArgs a) {
+  extern __shared__ float2 th_sinv32[];  // [N][N], then Phi [2][N][TH_P] (FP32)
+  const int w = blockIdx.y, N = a.N, M = a.M;
+  if ((a.wt && !walker_alive(a.wt, w)) || !(a.logdet[2L * w] > -INFINITY)) return;
+  float* ph = reinterpret_cast<float*>(th_sinv32 + N * N);
+  const float2* si = a.Sinv32 + (long)w * N * N;
+  for (int idx = threadIdx.x; idx < N * N; idx += TH_T) th_sinv32[idx] = si[idx];
+  const double* phw = a.phiT + (long)w * 2 * N * M;
+  const int pb = blockIdx.x * TH_P, pe = min(M, pb + TH_P), np = pe - pb;
+#pragma unroll 4
+  for (int e = threadIdx.x; e < 2 * N * np; e += TH_T) {
+    const int row = e / np, pl = e - row * np;  // row = plane * N + j
+    ph[row * TH_P + pl] = f64_to_f32(phw[(long)row * M + pb + pl]);
+  }
+  __syncthreads();
+  double* tr = a.thetaT + (long)w * 2 * N * M;
+  double* ti = tr + (long)N * M;
+  const int nib = (N + TF_IB - 1) / TF_IB;
+  for (int item = threadIdx.x; item < np * nib; item += TH_T) {
+    const int pl = item % np, p = pb + pl, i0 = (item / np) * TF_IB;
+    float ar[TF_IB], ai[TF_IB];
+#pragma unroll
+    for (int u = 0; u < TF_IB; ++u) ar[u] = ai[u] = 0.f;
+    if (a.unit_trial && p < N) {
+#pragma unroll
+      for (int u = 0; u < TF_IB; ++u) ar[u] = (i0 + u == p) ? 1.f : 0.f;
+    } else {
+      for (int j = 0; j < N; ++j) {
+        const float xr = ph[j * TH_P + pl], xi = ph[(N + j) * TH_P + pl];
+        const float2* srow = th_sinv32 + j * N + i0;
+#pragma unroll
+        for (int u = 0; u < TF_IB; ++u) {
+          if (i0 + u < N) {
+            const float2 sv = srow[u];
+            ar[u] = fmaf(xr, sv.x, fmaf(-xi, sv.y, ar[u]));
+            ai[u] = fmaf(xr, sv.y, fmaf(xi, sv.x, ai[u]));
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < TF_IB; ++u) {
+      const int i = i0 + u;
+      if (i >= N) continue;
+      tr[(long)i * M + p] = f32_to_f64(ar[u]);
+      ti[(long)i * M + p] = f32_to_f64(ai[u]);
+      store_lo_f(a.th_lo, a.lo_kind, ((long)w * 2 * N + i) * a.Mp + p, ar[u]);
+      store_lo_f(a.th_lo, a.lo_kind, ((long)w * 2 * N + N + i) * a.Mp + p, ai[u]);
+    }
+  }
+}
+
+template <int IB>
+static int launch_theta_f32(const OverlapArgs& a, cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    AFQ_CUDA(cudaFuncSetAttribute(k_theta_rows_f32<IB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  100 * 1024));
+    attr = true;
+  }
+  dim3 grid(cdiv(a.M, TH_P), a.W);
+  const size_t smem = sizeof(float2) * (size_t)a.N * a.N + sizeof(float) * 2 * a.N * TH_P;
+  AFQ_LAUNCH(k_theta_rows_f32<IB>, grid, TH_T, smem, st, a);
+  return AFQMC_OK;
+}
+
 template <int IB>
 static int launch_theta_rows(const OverlapArgs& a, cudaStream_t st) {
   static bool attr = false;
@@ -502,15 +606,45 @@ int launch_overlap(const OverlapArgs& a, cudaStream_t st) {
   }
   static bool attr = false;
   if (!attr) {
-    AFQ_CUDA(cudaFuncSetAttribute(k_overlap, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    AFQ_CUDA(cudaFuncSetAttribute(k_overlap<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   200 * 1024));
     attr = true;
   }
-  AFQ_LAUNCH(k_overlap, a.W, OV_T, smem, st, a);
+  if (a.Sinv32) {
+    static bool attr32 = false;
+    if (!attr32) {
+      AFQ_CUDA(cudaFuncSetAttribute(k_overlap<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    200 * 1024));
+      attr32 = true;
+    }
+    AFQ_LAUNCH(k_overlap<float>, a.W, OV_T, smem / 2, st, a);
+    return AFQMC_OK;
+  }
+  AFQ_LAUNCH(k_overlap<double>, a.W, OV_T, smem, st, a);
   return AFQMC_OK;
 }
 
 int launch_theta(const OverlapArgs& a, cudaStream_t st) {
+  if (a.Sinv32) {
+    if (!a.th_lo) {
+      set_error("theta: the FP32 rows need the operand copy");
+      return AFQMC_EINVAL;
+    }
+    const int nib = (a.N + 15) / 16, ib = (a.N + nib - 1) / nib;
+    switch (ib) {
+#define AFQ_THETA32(n) \
+  case n:              \
+    return launch_theta_f32<n>(a, st);
+      AFQ_THETA32(1) AFQ_THETA32(2) AFQ_THETA32(3) AFQ_THETA32(4) AFQ_THETA32(5)
+      AFQ_THETA32(6) AFQ_THETA32(7) AFQ_THETA32(8) AFQ_THETA32(9) AFQ_THETA32(10)
+      AFQ_THETA32(11) AFQ_THETA32(12) AFQ_THETA32(13) AFQ_THETA32(14) AFQ_THETA32(15)
+      AFQ_THETA32(16)
+#undef AFQ_THETA32
+      default:
+        set_error("theta: IB=%d", ib);
+        return AFQMC_EINVAL;
+    }
+  }
   int ib = 8;
   while (a.N % ib) --ib;
   switch (ib) {
@@ -661,7 +795,107 @@ __global__ void __launch_bounds__(256) k_mgs(MgsArgs a) {
   if (threadIdx.x == 0 && a.ld) a.ld[2L * w] -= 2.0 * (sh[0] + sh[1]);
 }
 
+// Mixed path: the same sweep in FP32 with the walker's orbitals resident in
+// shared memory ([N][M] complex, read once from and written once to the
+// float64 orbitals), one warp per later column and lanes over p (contiguous,
+// conflict-free).  The orbitals only feed the BF16/TF32 propagation and the
+// float64 overlap, which is recomputed from the stored Q; the FP32 norms give
+// log det R to ~1e-7 relative.  Used when 8 N M bytes fit the block.
+__global__ void __launch_bounds__(256) k_mgs_f32(MgsArgs a) {
+  extern __shared__ float2 v_sm[];  // [N][M]
+  __shared__ float red[8];
+  __shared__ float inv_sh;
+  __shared__ double norms[64];
+  const int w = blockIdx.x;
+  if (!walker_alive(a.wt, w)) return;
+  const int M = a.M, N = a.N, NM = M * N;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double* re = a.phiT + (long)w * 2 * NM;
+  double* im = re + NM;
+  for (int e = threadIdx.x; e < NM; e += blockDim.x)
+    v_sm[e] = make_float2(f64_to_f32(re[e]), f64_to_f32(im[e]));
+  __syncthreads();
+  for (int k = 0; k < N; ++k) {
+    float2* vk = v_sm + k * M;
+    float nn = 0.f;
+    for (int p = threadIdx.x; p < M; p += blockDim.x) nn = fmaf(vk[p].x, vk[p].x, fmaf(vk[p].y, vk[p].y, nn));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) nn += __shfl_xor_sync(0xffffffffu, nn, o);
+    if (lane == 0) red[warp] = nn;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float t = 0.f;
+      for (int q = 0; q < 8; ++q) t += red[q];
+      norms[k] = (double)t;
+      inv_sh = 1.f / sqrtf(t);
+    }
+    __syncthreads();
+    const float inv = inv_sh;
+    for (int p = threadIdx.x; p < M; p += blockDim.x) vk[p] = make_float2(vk[p].x * inv, vk[p].y * inv);
+    __syncthreads();
+    // v_j -= <q_k|v_j> q_k for every later column j, one warp per column
+    for (int j = k + 1 + warp; j < N; j += 8) {
+      float2* vj = v_sm + j * M;
+      float sr = 0.f, si = 0.f;
+      for (int p = lane; p < M; p += 32) {
+        const float2 q = vk[p], v = vj[p];
+        sr = fmaf(q.x, v.x, fmaf(q.y, v.y, sr));
+        si = fmaf(q.x, v.y, fmaf(-q.y, v.x, si));
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        sr += __shfl_xor_sync(0xffffffffu, sr, o);
+        si += __shfl_xor_sync(0xffffffffu, si, o);
+      }
+      for (int p = lane; p < M; p += 32) {
+        const float2 q = vk[p], v = vj[p];
+        vj[p] = make_float2(fmaf(-sr, q.x, fmaf(si, q.y, v.x)), fmaf(-sr, q.y, fmaf(-si, q.x, v.y)));
+      }
+    }
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < NM; e += blockDim.x) {
+    const float2 v = v_sm[e];
+    re[e] = f32_to_f64(v.x);
+    im[e] = f32_to_f64(v.y);
+    if (a.phi_lo) {
+      // rows (w, c, k) of the operand copy, pitch Mp (pad columns stay zero)
+      const int k = e / M, p = e - k * M;
+      store_lo_f(a.phi_lo, a.lo_kind, ((long)w * 2 * N + k) * a.Mp + p, v.x);
+      store_lo_f(a.phi_lo, a.lo_kind, ((long)w * 2 * N + N + k) * a.Mp + p, v.y);
+    }
+  }
+  // log det R = sum_k log |v_k|, as in k_mgs
+  __shared__ double sh[2];
+  double lr = threadIdx.x < N ? 0.5 * log(norms[threadIdx.x]) : 0.0;
+  if (threadIdx.x < 64) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) lr += __shfl_xor_sync(0xffffffffu, lr, o);
+    if (lane == 0) sh[warp] = lr;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && a.ld) a.ld[2L * w] -= 2.0 * (sh[0] + sh[1]);
+}
+
 int launch_mgs(const MgsArgs& a, cudaStream_t st) {
+  const size_t smem32 = sizeof(float2) * (size_t)a.M * a.N;
+  if (a.f32 && smem32 <= 200 * 1024) {
+    static bool attr32 = false;
+    if (!attr32) {
+      AFQ_CUDA(cudaFuncSetAttribute(k_mgs_f32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    200 * 1024));
+      attr32 = true;
+    }
+    AFQ_LAUNCH(k_mgs_f32, a.W, 256, smem32, st, a);
+    return AFQMC_OK;
+  }
+  if (a.phi_lo) {
+    // the float64 sweep, then the operand copy of every walker
+    MgsArgs b = a;
+    b.phi_lo = nullptr;
+    AFQ_TRY(launch_mgs(b, st));
+    return launch_convert_lo(a.phiT, 2L * a.N * a.W, a.M, a.M, a.phi_lo, a.Mp, a.lo_kind, st);
+  }
   const size_t smem = sizeof(double2) * (size_t)a.M;
   if (smem > 200 * 1024) {
     set_error("mgs: M=%d too large", a.M);
@@ -1134,6 +1368,30 @@ int launch_convert_lo(const double* src, long rows, long cols, long lds, void* d
                       int kind, cudaStream_t st, double minus_diag) {
   if (rows <= 0) return AFQMC_OK;
   AFQ_LAUNCH(k_convert_lo, 152 * 8, 256, 0, st, src, rows, cols, lds, dst, ldd, kind, minus_diag);
+  return AFQMC_OK;
+}
+
+__global__ void k_round_f32(const double* src, float* dst, long n) {
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long)gridDim.x * blockDim.x)
+    dst[i] = f64_to_f32(src[i]);
+}
+
+__global__ void k_widen_f32(const float* src, double* dst, long n) {
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long)gridDim.x * blockDim.x)
+    dst[i] = f32_to_f64(src[i]);
+}
+
+int launch_round_f32(const double* src, float* dst, long n, cudaStream_t st) {
+  if (n <= 0) return AFQMC_OK;
+  AFQ_LAUNCH(k_round_f32, 152 * 8, 256, 0, st, src, dst, n);
+  return AFQMC_OK;
+}
+
+int launch_widen_f32(const float* src, double* dst, long n, cudaStream_t st) {
+  if (n <= 0) return AFQMC_OK;
+  AFQ_LAUNCH(k_widen_f32, 152 * 8, 256, 0, st, src, dst, n);
   return AFQMC_OK;
 }
 
