@@ -388,7 +388,7 @@ __device__ __forceinline__ void store8_lo(void* base, int kind, long idx, const 
 struct EpiProp0 {
   static constexpr int kSmemBytes = 0;
   static constexpr bool kB3D = false;  // B tile = one 2-D box at row n_origin
-  static constexpr int kWarps = 4;      // epilogue warps
+  static constexpr int kWarps = 8;      // epilogue warps: two per TMEM lane quarter
   static constexpr int kMT = 1;         // 128-row A tiles per output tile
   float* acc;
   long ldacc;
@@ -399,11 +399,12 @@ struct EpiProp0 {
   __device__ __forceinline__ int m_origin(int bx, int) const { return bx * BM; }
   __device__ __forceinline__ int n_origin(int, int by) const { return by * bn; }
   template <int BN>
-  __device__ __forceinline__ void run(uint32_t tmem, int q, int lane, int, int, int, int m0, int n0,
-                                      int, int, float*) const {
+  __device__ __forceinline__ void run(uint32_t tmem, int q, int lane, int ew, int, int, int m0,
+                                      int n0, int, int, float*) const {
     const int row = m0 + 32 * q + lane;
+    // the two warps of a lane quarter take alternate 16-column chunks
 #pragma unroll 1
-    for (int c0 = 0; c0 < BN; c0 += 16) {
+    for (int c0 = 16 * (ew >> 2); c0 < BN; c0 += 32) {
       float v[16];
       tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c0, v);
       if (row >= rows) continue;
@@ -525,7 +526,7 @@ struct EpiTaylor {
 struct EpiV {
   static constexpr int kSmemBytes = 0;
   static constexpr bool kB3D = false;  // B tile = one 2-D box at row n_origin
-  static constexpr int kWarps = 4;      // epilogue warps
+  static constexpr int kWarps = 8;      // epilogue warps: two per TMEM lane quarter
   static constexpr int kMT = 2;         // 256-row tiles: each Cholesky tile serves 128 walkers
   void* V;
   int lo_kind, W, M, Mp;
@@ -536,10 +537,10 @@ struct EpiV {
   // column pp * 16 + qq of the tile is V[16 P + pp][16 Q + qq].  The thread of
   // row (w, c) writes the block's 16 rows (16 contiguous q each) and, off the
   // diagonal, the mirrored block's 16 rows (V[q][p] = V[p][q]) in two halves
-  // of 8 contiguous p.
+  // of 8 contiguous p.  The two warps of a lane quarter take one half each.
   template <int BN>
-  __device__ __forceinline__ void run(uint32_t tmem, int q, int lane, int, int, int, int m0, int n0,
-                                      int, int, float*) const {
+  __device__ __forceinline__ void run(uint32_t tmem, int q, int lane, int ew, int, int, int m0,
+                                      int n0, int, int, float*) const {
     static_assert(BN == 256, "one 16 x 16 block per tile");
     const int row = m0 + 32 * q + lane;
     const bool valid = row < 2 * W;
@@ -554,7 +555,7 @@ struct EpiV {
     const int Q = P + rem;
     const long vb = (long)w * M * 2L * Mp + (c ? 0 : Mp);
 #pragma unroll 1
-    for (int h = 0; h < 2; ++h) {
+    for (int h = ew >> 2; h < 2; h += 2) {
       uint32_t r[8][16];
 #pragma unroll
       for (int u = 0; u < 8; ++u)
@@ -591,7 +592,7 @@ struct EpiV {
 struct EpiPhi {
   static constexpr int kSmemBytes = 0;
   static constexpr bool kB3D = false;  // B tile = one 2-D box at row n_origin
-  static constexpr int kWarps = 4;      // epilogue warps
+  static constexpr int kWarps = 8;      // epilogue warps: two per TMEM lane quarter
   static constexpr int kMT = 1;         // 128-row A tiles per output tile
   double* phiT;
   const double* wt;
@@ -605,12 +606,13 @@ struct EpiPhi {
   __device__ __forceinline__ int m_origin(int bx, int) const { return bx * BM; }
   __device__ __forceinline__ int n_origin(int, int by) const { return by * bn; }
   template <int BN>
-  __device__ __forceinline__ void run(uint32_t tmem, int q, int lane, int, int, int, int m0, int n0,
-                                      int, int, float*) const {
+  __device__ __forceinline__ void run(uint32_t tmem, int q, int lane, int ew, int, int, int m0,
+                                      int n0, int, int, float*) const {
     const int row = m0 + 32 * q + lane;
     const bool ok = row < rows && walker_alive(wt, row / (2 * N));
+    // the two warps of a lane quarter take alternate 16-column chunks
 #pragma unroll 1
-    for (int c0 = 0; c0 < BN; c0 += 16) {
+    for (int c0 = 16 * (ew >> 2); c0 < BN; c0 += 32) {
       float v[16];
       tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c0, v);
       if (!ok) continue;
