@@ -57,6 +57,8 @@ def peaks():
 # clock x 2 FLOP x 2070 MHz = 1.259 TFLOP/s (a DFMA probe kernel measured
 # 1.198 TFLOP/s on this machine, i.e. 2 FMA/clk/SM at the clock under load).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+# FP32 likewise: 152 SMs x 128 FMA per clock x 2 FLOP x 2070 MHz = 80.5 TFLOP/s.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 
 # DRAM bytes (read + write) per launch from one ncu capture of the M=300 BF16
 # step (energy: the exchange contraction, the phase's main kernel), with the
@@ -181,22 +183,24 @@ def algorithmic_per_walker(w: workloads.Workload):
 def bytes_per_walker(w: workloads.Workload, precision):
     """Algorithmic DRAM bytes per walker of the mixed path's FP32 kernels,
     which are bound by memory traffic, not by their FP32 arithmetic:
-      theta  read Phi (2 N M float64) and S^-1 (N^2 complex), write Theta
-             (2 N M float64) and its BF16/TF32 copy (2 N Mp);
+      theta  read Phi (2 N M float64) and the FP32 S^-1 (N^2 complex), write
+             Theta (2 N M float64) and its BF16/TF32 copy (2 N Mp);
       qr     read and write Phi (2 x 2 N M float64), write its BF16/TF32 copy."""
     M, N = w.M, w.N
     Mp = (M + 15) // 16 * 16
     lo = 2 if precision == "bf16" else 4
-    return {"theta": 2 * N * M * 8 + N * N * 16 + 2 * N * M * 8 + 2 * N * Mp * lo,
+    return {"theta": 2 * N * M * 8 + N * N * 8 + 2 * N * M * 8 + 2 * N * Mp * lo,
             "qr": 2 * (2 * N * M * 8) + 2 * N * Mp * lo}
 
 
 def kernel_of_phase(precision):
-    """Phase -> (kernel, bound, source file).  The mixed path computes Theta
-    and the Gram-Schmidt sweep in FP32 (HBM-bound kernels); the float64 path
-    keeps the FP64-pipe kernels."""
+    """Phase -> (kernel, bound, source file).  The mixed path runs the
+    elimination in FP32 (against the FP32 pipe) and Theta and the
+    Gram-Schmidt sweep in FP32 (HBM-bound); the float64 path keeps the
+    FP64-pipe kernels."""
     k = dict(KERNEL_OF_PHASE)
     if precision != "fp64":
+        k["overlap"] = ("k_overlap<float>", "alu32", "walker_f64.cu")
         k["theta"] = ("k_theta_rows_f32", "hbm", "walker_f64.cu")
         k["qr"] = ("k_mgs_f32", "hbm", "walker_f64.cu")
     return k
@@ -248,7 +252,11 @@ def rooflines(w, phases, precision, K):
                         "launches_per_step": v["count"] / K,
                         "share_of_step": v["ms"] / sum(x["ms"] for x in phases.values())})
             continue
-        if bound == "alu" or precision == "fp64":
+        if bound == "alu32":
+            peak, unit, src_peak = FP32_PEAK_TFLOPS, "TFLOP/s", (
+                "derived: 152 SMs x 128 FP32 FMA/clk x 2 x 2070 MHz")
+            bound = "alu"
+        elif bound == "alu" or precision == "fp64":
             peak, unit, src_peak = FP64_PEAK_TFLOPS, "TFLOP/s", (
                 "derived: 152 SMs x 2 FP64 FMA/clk x 2 x 2070 MHz")
             bound = "alu"

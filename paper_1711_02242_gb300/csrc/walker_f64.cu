@@ -290,24 +290,25 @@ struct Vec2<float> {
   __device__ static float2* sinv(const OverlapArgs& a) { return a.Sinv32; }
 };
 
+// Steps 1-2 for walker w by the whole block (blockDim >= 64): S into A
+// ([N][N] shared), its inverse in place with the columns in the rows' final
+// order (pos[c] = the column of A holding column c of S^-1), log det stored
+// for live walkers.  Returns true when S is singular (block-uniform).
 template <typename T>
-__global__ void __launch_bounds__(OV_T) k_overlap(OverlapArgs a) {
+__device__ __forceinline__ bool overlap_core(const OverlapArgs& a, int w, bool live,
+                                             typename Vec2<T>::type* A, int* pos) {
   using T2 = typename Vec2<T>::type;
-  extern __shared__ __align__(16) unsigned char ov_raw[];
   __shared__ __align__(16) unsigned char misc_raw[sizeof(T2) * 129];
-  const int w = blockIdx.x;
-  const bool live = !a.wt || walker_alive(a.wt, w);
   const int N = a.N, M = a.M;
-  T2* A = reinterpret_cast<T2*>(ov_raw);  // [N][N], inverted in place
   __shared__ int swaps, singular;
   T2& rpiv = reinterpret_cast<T2*>(misc_raw)[128];
   T2* pivots = reinterpret_cast<T2*>(misc_raw);       // the pivots, for log det afterwards
   T2* fac = reinterpret_cast<T2*>(misc_raw) + 64;     // a_rk / p of the current pivot column
-  __shared__ int order[64], pos[64];
+  __shared__ int order[64];
   const double* fr = a.phiT + (long)w * 2 * N * M;
   const double* fi = fr + (long)N * M;
   // S[i][j] = Phi[i][j], the top block of the orbitals
-  for (int idx = threadIdx.x; idx < N * N; idx += OV_T) {
+  for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x) {
     const int i = idx / N, j = idx % N;
     A[idx] = Vec2<T>::make(Vec2<T>::from_f64(fr[(long)j * M + i]),
                            Vec2<T>::from_f64(fi[(long)j * M + i]));
@@ -441,6 +442,18 @@ __global__ void __launch_bounds__(OV_T) k_overlap(OverlapArgs a) {
       a.logdet[2L * w + 1] = wrap_pi(2.0 * ((red[1] + red[3]) + 3.141592653589793 * swaps));
     }
   }
+  return singular != 0;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(OV_T) k_overlap(OverlapArgs a) {
+  using T2 = typename Vec2<T>::type;
+  extern __shared__ __align__(16) unsigned char ov_raw[];
+  __shared__ int pos[64];
+  const int w = blockIdx.x, N = a.N;
+  const bool live = !a.wt || walker_alive(a.wt, w);
+  T2* A = reinterpret_cast<T2*>(ov_raw);  // [N][N], inverted in place
+  const bool singular = overlap_core<T>(a, w, live, A, pos);
   // S^-1 of live, non-singular walkers for the Theta kernel: column c of the
   // inverse is column pos[c] of A (the row interchanges undone)
   if (singular || !live) return;

@@ -74,8 +74,17 @@ def test_rooflines_from_phase_times():
     assert per == 8 * 25 ** 3
     assert bench.algorithmic_per_walker(w)["theta"] == 8 * (300 - 25) * 25 * 25
     assert abs(ov["achieved"] - per * 512 / 1.3e-3 / 1e12) < 1e-12
-    assert ov["bound"] == "alu" and abs(ov["frac"] - ov["achieved"] / bench.FP64_PEAK_TFLOPS) < 1e-12
+    # the mixed path's elimination runs in FP32; the float64 path's on the FP64 pipe
+    assert ov["bound"] == "alu" and abs(ov["frac"] - ov["achieved"] / bench.FP32_PEAK_TFLOPS) < 1e-12
+    ov64 = bench.rooflines(w, ph, "fp64", K)[0]
+    assert ov64["phase"] == "overlap" and abs(ov64["frac"] - ov64["achieved"] / bench.FP64_PEAK_TFLOPS) < 1e-12
     assert roofs[1]["bound"] == "tensor"
+    # the mixed path's Gram-Schmidt sweep is measured against HBM bandwidth
+    qr = roofs[2]
+    pk, _ = bench.peaks()
+    assert qr["bound"] == "hbm" and qr["unit"] == "GB/s"
+    assert abs(qr["achieved"] - bench.bytes_per_walker(w, "bf16")["qr"] * 512 / 1.3e-3 / 1e9) < 1e-9
+    assert abs(qr["frac"] - qr["achieved"] / pk["hbm_gbs"]) < 1e-12
     assert abs(sum(r["share_of_step"] for r in roofs) - 1.0) < 1e-12
     # a recorded traffic figure counts only for the source it was taken from
     saved = dict(bench.TRAFFIC)
