@@ -63,14 +63,14 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # DRAM bytes (read + write) per launch from one ncu capture of the M=300 BF16
 # step (energy: the exchange contraction, the phase's main kernel), with the
 # SHA-256 of the source file the kernel was built from; a figure whose source
-# has changed since is reported as null.
+# has changed since, or taken at another precision, is reported as null.
 TRAFFIC = {
-    "theta": {"bytes": (64.544512 + 30.260480) * 1e6, "sha": "33719648246e485b7a441bb83f88a827089bc4b9d9aeb90658da27bacb7275fc"},
-    "overlap": {"bytes": (8.236800 + 0.000000) * 1e6, "sha": "33719648246e485b7a441bb83f88a827089bc4b9d9aeb90658da27bacb7275fc"},
-    "qr": {"bytes": (61.481984 + 34.477824) * 1e6, "sha": "33719648246e485b7a441bb83f88a827089bc4b9d9aeb90658da27bacb7275fc"},
-    "taylor": {"bytes": (218.600448 + 20.028672) * 1e6, "sha": "7d84c2b3465f764bb47983565617111a70bc45f2b5fbc4a888a139d84b0bbc1f"},
-    "v_assembly": {"bytes": (229.882624 + 184.216576) * 1e6, "sha": "ebefa405f32f3e93f694d160ec40a4f1211014674d6f73d7de534f53b4d1f9a3"},
-    "energy": {"bytes": (42.972416 + 0.417024) * 1e6, "sha": "ebefa405f32f3e93f694d160ec40a4f1211014674d6f73d7de534f53b4d1f9a3"},
+    "theta": {"bytes": (64.265728 + 25.652224) * 1e6, "sha": "954d18e281c00e53a5fe2c7476c19d20c0c69feeb260dd6da12f7f24e010ef97"},
+    "overlap": {"bytes": (8.234752 + 0.0) * 1e6, "sha": "954d18e281c00e53a5fe2c7476c19d20c0c69feeb260dd6da12f7f24e010ef97"},
+    "qr": {"bytes": (61.510144 + 15.014656) * 1e6, "sha": "954d18e281c00e53a5fe2c7476c19d20c0c69feeb260dd6da12f7f24e010ef97"},
+    "taylor": {"bytes": (218.379264 + 19.598080) * 1e6, "sha": "7d84c2b3465f764bb47983565617111a70bc45f2b5fbc4a888a139d84b0bbc1f"},
+    "v_assembly": {"bytes": (187.431680 + 145.291776) * 1e6, "sha": "e87b4db7d550e788be37b7c99656929c68c239e53519f64c4229575bbd0b27dd"},
+    "energy": {"bytes": (42.972160 + 0.562688) * 1e6, "sha": "e87b4db7d550e788be37b7c99656929c68c239e53519f64c4229575bbd0b27dd"},
 }
 
 
@@ -226,6 +226,15 @@ def source_sha(fname):
         return None
 
 
+def traffic_of(phase, src, precision):
+    """The recorded DRAM bytes of a phase's kernel, if taken from this source
+    at this precision (the captures are of the BF16 step)."""
+    tr = TRAFFIC.get(phase)
+    if not tr or tr.get("sha") != source_sha(src) or precision not in tr.get("precisions", ("bf16",)):
+        return None
+    return tr["bytes"]
+
+
 def rooflines(w, phases, precision, K):
     """Roofline entry per timed phase that is one kernel family: algorithmic
     work per launch / device time per launch (CUDA events on the state's
@@ -244,8 +253,7 @@ def rooflines(w, phases, precision, K):
             # bytes per launch / time, against the measured copy bandwidth
             peak, unit, src_peak = pk["hbm_gbs"], "GB/s", f"{pk_kind} HBM copy bandwidth"
             achieved = per_bytes[ph] * w.nwalkers / (ms_launch * 1e-3) / 1e9
-            tr = TRAFFIC.get(ph)
-            traffic = tr["bytes"] if tr and tr.get("sha") == source_sha(src) else None
+            traffic = traffic_of(ph, src, precision)
             out.append({"phase": ph, "kernel": kname, "bound": bound, "achieved": achieved,
                         "peak": peak, "unit": unit, "frac": achieved / peak, "traffic": traffic,
                         "peak_source": src_peak, "ms_per_launch": ms_launch,
@@ -267,8 +275,7 @@ def rooflines(w, phases, precision, K):
             src_peak = (f"{pk_kind} bf16 sustained" if precision == "bf16"
                         else f"{pk_kind} bf16 sustained / 2 (TF32 nominal ratio)")
         achieved = work / (ms_launch * 1e-3) / 1e12
-        tr = TRAFFIC.get(ph)
-        traffic = tr["bytes"] if tr and tr.get("sha") == source_sha(src) else None
+        traffic = traffic_of(ph, src, precision)
         out.append({"phase": ph, "kernel": kname, "bound": bound, "achieved": achieved,
                     "peak": peak, "unit": unit, "frac": achieved / peak, "traffic": traffic,
                     "peak_source": src_peak, "ms_per_launch": ms_launch,

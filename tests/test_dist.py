@@ -91,6 +91,8 @@ def test_rooflines_from_phase_times():
     try:
         bench.TRAFFIC["overlap"] = {"bytes": 1.0e8, "sha": bench.source_sha("walker_f64.cu")}
         assert bench.rooflines(w, ph, "bf16", K)[0]["traffic"] == 1.0e8
+        # the captures are of the BF16 step: another precision runs other kernels
+        assert bench.rooflines(w, ph, "tf32", K)[0]["traffic"] is None
         bench.TRAFFIC["overlap"] = {"bytes": 1.0e8, "sha": "0" * 64}
         assert bench.rooflines(w, ph, "bf16", K)[0]["traffic"] is None
     finally:
