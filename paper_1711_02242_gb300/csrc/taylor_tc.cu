@@ -9,7 +9,7 @@
 // memory, streams only V (from L2 after the first term) and writes S once.
 //
 //   A operand  [Re V | Im V] rows p of walker w (128-row tiles, K = 2 Mp),
-//              TMA ring of 128 x 128-byte boxes;
+//              TMA ring of 256 x 128-byte boxes (two 128-row MMA tiles each);
 //   B operand  the term T_{k-1} as K-major rows, NH = N rounded up to 16:
 //                 row i      = [Re T_i | -Im T_i]   (i < N)
 //                 row NH + i = [Im T_i |  Re T_i]
@@ -40,7 +40,8 @@
 namespace afq {
 namespace tc {
 
-constexpr int kVBox = BM * BKB;   // one V tile in the ring: 128 rows x 128 bytes
+constexpr int kVRows = 2 * BM;   // rows of one V box: two 128-row MMA tiles
+constexpr int kVBox = kVRows * BKB;  // one V box in the ring: 256 rows x 128 bytes
 constexpr int kEpiWarps = 8;      // epilogue warps (2 per TMEM lane quarter)
 constexpr int kEpiThreads = 32 * kEpiWarps;
 constexpr int kSeriesThreads = 64 + kEpiThreads;
@@ -53,6 +54,7 @@ struct SeriesArgs {
   int nb;       // 2 nh = MMA N
   int kblocks;  // 128-byte K blocks covering 2 Mp
   int ptiles;   // 128-row tiles covering p < M
+  int btiles;   // 256-row V boxes covering p < M
   int stages;   // depth of the V ring
   uint32_t tcols;
 };
@@ -152,7 +154,7 @@ __global__ void __launch_bounds__(kSeriesThreads, 1)
       for (int kb = 0; kb < a.kblocks; ++kb)
         tma_load_4d(bop + kb * opk, &tmT, bfull, kb * BK, 0, 0, w);
       for (int k = 1; k <= a.order && !stop; ++k)
-        for (int pt = 0; pt < a.ptiles && !stop; ++pt)
+        for (int bt = 0; bt < a.btiles && !stop; ++bt)
           for (int kb = 0; kb < a.kblocks; ++kb, ++it) {
             const int s = it % a.stages;
             if ((it >= a.stages && !mbar_wait(&empty[s], ((it / a.stages) - 1) & 1, err, 32)) ||
@@ -161,7 +163,7 @@ __global__ void __launch_bounds__(kSeriesThreads, 1)
               break;
             }
             mbar_expect_tx(&full[s], kVBox);
-            tma_load_3d(ring + s * kVBox, &tmV, &full[s], kb * BK, pt * BM, w);
+            tma_load_3d(ring + s * kVBox, &tmV, &full[s], kb * BK, bt * kVRows, w);
           }
     }
     if (stop) *abort_flag = 1;
@@ -178,8 +180,9 @@ __global__ void __launch_bounds__(kSeriesThreads, 1)
           break;
         }
         fence_after();
-        for (int pt = 0; pt < a.ptiles && !stop; ++pt) {
-          const uint32_t d = tmem + (uint32_t)(pt * a.nb);
+        // one box = the 128-row p-tiles 2 bt and 2 bt + 1 (the second absent
+        // past the last p-tile)
+        for (int bt = 0; bt < a.btiles && !stop; ++bt) {
           for (int kb = 0; kb < a.kblocks; ++kb, ++it) {
             const int s = it % a.stages;
             if (!mbar_wait(&full[s], (it / a.stages) & 1, err, 35)) {
@@ -192,8 +195,14 @@ __global__ void __launch_bounds__(kSeriesThreads, 1)
             const uint32_t bv = smem_u32(bop + kb * opk);
 #pragma unroll
             for (int kk = 0; kk < KSTEPS; ++kk)
-              mma<TF32>(d, sw128_desc(av + 32 * kk), sw128_desc(bv + 32 * kk), idesc,
-                        (kb > 0 || kk > 0) ? 1u : 0u);
+#pragma unroll
+              for (int sub = 0; sub < 2; ++sub) {
+                const int pt = 2 * bt + sub;
+                if (pt < a.ptiles)
+                  mma<TF32>(tmem + (uint32_t)(pt * a.nb),
+                            sw128_desc(av + (uint32_t)(sub * BM * BKB) + 32 * kk),
+                            sw128_desc(bv + 32 * kk), idesc, (kb > 0 || kk > 0) ? 1u : 0u);
+              }
             mma_commit(&empty[s]);
           }
         }
@@ -314,6 +323,7 @@ bool series_plan(int lo_kind, int N, int M, int Mp, tc::SeriesArgs* sa, int* sme
     sa->nb = nb;
     sa->kblocks = kblocks;
     sa->ptiles = ptiles;
+    sa->btiles = (ptiles + 1) / 2;
     sa->stages = stages;
     sa->tcols = tcols;
   }
@@ -345,7 +355,7 @@ int tc_taylor_series(const void* V, const void* T0, float* S, long lds, int lo_k
   const bool tf32 = lo_kind == LO_TF32;
   const int eb = tf32 ? 4 : 2;
   CUtensorMap tv, tt;
-  AFQ_TRY(make_tmap_3d(&tv, V, eb, W, M, 2L * Mp, 2L * Mp, (long)M * 2 * Mp, tc::BM));
+  AFQ_TRY(make_tmap_3d(&tv, V, eb, W, M, 2L * Mp, 2L * Mp, (long)M * 2 * Mp, tc::kVRows));
   // T0 rows (w, c, i) -> operand rows c NH + i: dims (K, i, c, w), box (K block, NH, 2, 1)
   const long tdims[4] = {2L * Mp, N, 2, W};
   const long tstr[3] = {2L * Mp * eb, (long)N * 2 * Mp * eb, 2L * N * 2 * Mp * eb};
