@@ -65,9 +65,9 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # SHA-256 of the source file the kernel was built from; a figure whose source
 # has changed since, or taken at another precision, is reported as null.
 TRAFFIC = {
-    "theta": {"bytes": (64.265728 + 25.652224) * 1e6, "sha": "954d18e281c00e53a5fe2c7476c19d20c0c69feeb260dd6da12f7f24e010ef97"},
-    "overlap": {"bytes": (8.234752 + 0.0) * 1e6, "sha": "954d18e281c00e53a5fe2c7476c19d20c0c69feeb260dd6da12f7f24e010ef97"},
-    "qr": {"bytes": (61.510144 + 15.014656) * 1e6, "sha": "954d18e281c00e53a5fe2c7476c19d20c0c69feeb260dd6da12f7f24e010ef97"},
+    "theta": {"bytes": (64.265728 + 25.652224) * 1e6, "sha": "9146d32418fd7e4850ca0735fdb706eb021503329f752f6d3047e5638c26688d"},
+    "overlap": {"bytes": (8.234752 + 0.0) * 1e6, "sha": "9146d32418fd7e4850ca0735fdb706eb021503329f752f6d3047e5638c26688d"},
+    "qr": {"bytes": (61.510144 + 15.014656) * 1e6, "sha": "9146d32418fd7e4850ca0735fdb706eb021503329f752f6d3047e5638c26688d"},
     "taylor": {"bytes": (218.379264 + 19.640064) * 1e6, "sha": "fa71a0b99da9edecc9d2774bf84475b771676eadf05941fcfb17a764107f753e"},
     "v_assembly": {"bytes": (187.431680 + 145.291776) * 1e6, "sha": "e87b4db7d550e788be37b7c99656929c68c239e53519f64c4229575bbd0b27dd"},
     "energy": {"bytes": (42.972160 + 0.562688) * 1e6, "sha": "e87b4db7d550e788be37b7c99656929c68c239e53519f64c4229575bbd0b27dd"},

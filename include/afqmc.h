@@ -68,8 +68,9 @@ typedef enum afqmc_status {
 enum {
   AFQMC_FP64 = 0,       /* every step in float64 / complex128                   */
   AFQMC_MIXED_TF32 = 1, /* contractions on tcgen05 tensor cores, TF32 inputs,   */
-                        /* FP32 accumulation; Theta, LU, overlap ratios,        */
-                        /* weights and Gram-Schmidt in FP64                     */
+                        /* FP32 accumulation; S^-1, Theta and Gram-Schmidt in   */
+                        /* FP32; log det sums, overlap ratios, weights and the  */
+                        /* identity part of the one-body half steps in FP64     */
   AFQMC_MIXED_BF16 = 2  /* as MIXED_TF32 with BF16 inputs to the contractions   */
 };
 

@@ -1,4 +1,5 @@
-// Per-walker kernels of the float64 path and the set-up kernels.
+// Per-walker kernels (float64, and the FP32 variants of the overlap, Theta and
+// Gram-Schmidt kernels used by the mixed path) and the set-up kernels.
 //
 // Layouts (W walkers, M orbitals, N electrons per spin, G Cholesky vectors,
 // P = M(M+1)/2):
@@ -256,8 +257,10 @@ static int launch_taylor(const TaylorArgsT<T>& a, cudaStream_t st) {
 int launch_taylor_term(const TaylorArgsT<double>& a, cudaStream_t st) { return launch_taylor(a, st); }
 
 // ------------------------------------------------------------- overlap ------
-// Float64 throughout (Theorem 1.1, Eq. precomputing), in the trial-adapted
-// basis where V_T = [I_N; 0].  k_overlap, one block per walker:
+// Theorem 1.1, Eq. precomputing, in the trial-adapted basis where V_T =
+// [I_N; 0]; float64 on the float64 path, FP32 with float64 log det sums on
+// the mixed path (k_overlap<float>, k_theta_rows_f32).  k_overlap, one block
+// per walker:
 //   1. S = V_T^T Phi is the top N x N block of Phi (a gather);
 //   2. Gauss-Jordan elimination with partial pivoting (largest |s_rk|^2, the
 //      first row on ties, searched by one warp): S^-1 and log det S = sum log
