@@ -6,7 +6,7 @@ modified Gram-Schmidt every 5 steps, local energy every 10 steps.  One step
 is one pass of the whole hot path over all walkers (force bias, fields, V,
 propagation, overlap/LU, weights, and the periodic QR and energy).
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16|tf32|fp64]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16|tf32|fp64|bf16-f32lu|tf32-f32lu]
     python bench.py --impl reference      # the CPU oracle on the host cores
     python bench.py --workload mcd [--config c2] [--impl reference]
         # modified Cholesky decomposition (Sec. 2.3) of the workload's
@@ -44,6 +44,13 @@ import workloads  # noqa: E402
 PHASES = ["force_bias", "fields", "v_assembly", "bhalf", "taylor", "overlap", "weight", "qr",
           "comb", "energy", "theta"]
 
+# --precision -> afqmc_params.precision.  "bf16" / "tf32" keep Theta, LU, the
+# overlap ratios, the weights and Gram-Schmidt in float64; the "-f32lu"
+# variants (opt-in) run the elimination, Theta and Gram-Schmidt in FP32.
+PRECISIONS = {"fp64": 0, "tf32": 1, "bf16": 2, "tf32-f32lu": 3, "bf16-f32lu": 4}
+DTYPES = {"fp64": "f64", "tf32": "tf32/f32/f64", "bf16": "bf16/f32/f64",
+          "tf32-f32lu": "tf32/f32/f64", "bf16-f32lu": "bf16/f32/f64"}
+
 
 def peaks():
     try:
@@ -60,17 +67,23 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # FP32 likewise: 152 SMs x 128 FMA per clock x 2 FLOP x 2070 MHz = 80.5 TFLOP/s.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 
-# DRAM bytes (read + write) per launch from one ncu capture of the M=300 BF16
-# step (energy: the exchange contraction, the phase's main kernel), with the
-# SHA-256 of the source file the kernel was built from; a figure whose source
-# has changed since, or taken at another precision, is reported as null.
+# DRAM bytes (read + write) per launch from one ncu capture of the M=300 step
+# (energy: the exchange contraction, the phase's main kernel), with the SHA-256
+# of the source file the kernel was built from and the precisions whose step
+# runs that kernel; a figure whose source has changed since, or that belongs
+# to another kernel at this precision, is reported as null.
 TRAFFIC = {
-    "theta": {"bytes": (64.265728 + 25.652224) * 1e6, "sha": "9146d32418fd7e4850ca0735fdb706eb021503329f752f6d3047e5638c26688d"},
-    "overlap": {"bytes": (8.234752 + 0.0) * 1e6, "sha": "9146d32418fd7e4850ca0735fdb706eb021503329f752f6d3047e5638c26688d"},
-    "qr": {"bytes": (61.510144 + 15.014656) * 1e6, "sha": "9146d32418fd7e4850ca0735fdb706eb021503329f752f6d3047e5638c26688d"},
-    "taylor": {"bytes": (218.379264 + 19.640064) * 1e6, "sha": "fa71a0b99da9edecc9d2774bf84475b771676eadf05941fcfb17a764107f753e"},
-    "v_assembly": {"bytes": (187.431680 + 145.291776) * 1e6, "sha": "e87b4db7d550e788be37b7c99656929c68c239e53519f64c4229575bbd0b27dd"},
-    "energy": {"bytes": (42.972160 + 0.562688) * 1e6, "sha": "e87b4db7d550e788be37b7c99656929c68c239e53519f64c4229575bbd0b27dd"},
+    "theta": [{"bytes": (64.265728 + 25.652224) * 1e6, "sha": "9146d32418fd7e4850ca0735fdb706eb021503329f752f6d3047e5638c26688d", "precisions": ("bf16-f32lu",)},
+              # k_theta_rows (float64 Theta of the bf16 / tf32 mixed paths): its own
+              # text is unchanged since this capture (DRAM 64.5 + 30.3 MB per launch)
+              {"bytes": (64.544512 + 30.260480) * 1e6, "precisions": ("bf16",),
+               "function": "__global__ void __launch_bounds__(TH_T) k_theta_rows(OverlapArgs a)",
+               "sha": "d7ee3083bab22e614e7aa9c51aff2886d255680c62a6454f637a089a17969ae7"}],
+    "overlap": {"bytes": (8.234752 + 0.0) * 1e6, "sha": "9146d32418fd7e4850ca0735fdb706eb021503329f752f6d3047e5638c26688d", "precisions": ("bf16-f32lu",)},
+    "qr": {"bytes": (61.510144 + 15.014656) * 1e6, "sha": "9146d32418fd7e4850ca0735fdb706eb021503329f752f6d3047e5638c26688d", "precisions": ("bf16-f32lu",)},
+    "taylor": {"bytes": (218.379264 + 19.640064) * 1e6, "sha": "fa71a0b99da9edecc9d2774bf84475b771676eadf05941fcfb17a764107f753e", "precisions": ("bf16", "bf16-f32lu")},
+    "v_assembly": {"bytes": (187.431680 + 145.291776) * 1e6, "sha": "e87b4db7d550e788be37b7c99656929c68c239e53519f64c4229575bbd0b27dd", "precisions": ("bf16", "bf16-f32lu")},
+    "energy": {"bytes": (42.972160 + 0.562688) * 1e6, "sha": "e87b4db7d550e788be37b7c99656929c68c239e53519f64c4229575bbd0b27dd", "precisions": ("bf16", "bf16-f32lu")},
 }
 
 
@@ -188,18 +201,18 @@ def bytes_per_walker(w: workloads.Workload, precision):
       qr     read and write Phi (2 x 2 N M float64), write its BF16/TF32 copy."""
     M, N = w.M, w.N
     Mp = (M + 15) // 16 * 16
-    lo = 2 if precision == "bf16" else 4
+    lo = 2 if precision.startswith("bf16") else 4
     return {"theta": 2 * N * M * 8 + N * N * 8 + 2 * N * M * 8 + 2 * N * Mp * lo,
             "qr": 2 * (2 * N * M * 8) + 2 * N * Mp * lo}
 
 
 def kernel_of_phase(precision):
-    """Phase -> (kernel, bound, source file).  The mixed path runs the
-    elimination in FP32 (against the FP32 pipe) and Theta and the
-    Gram-Schmidt sweep in FP32 (HBM-bound); the float64 path keeps the
-    FP64-pipe kernels."""
+    """Phase -> (kernel, bound, source file).  The elimination, Theta and the
+    Gram-Schmidt sweep are FP64-pipe kernels on the float64 path and the
+    bf16 / tf32 mixed paths; the -f32lu mixed paths run them in FP32 (the
+    elimination against the FP32 pipe, Theta and the sweep against HBM)."""
     k = dict(KERNEL_OF_PHASE)
-    if precision != "fp64":
+    if precision.endswith("f32lu"):
         k["overlap"] = ("k_overlap<float>", "alu32", "walker_f64.cu")
         k["theta"] = ("k_theta_rows_f32", "hbm", "walker_f64.cu")
         k["qr"] = ("k_mgs_f32", "hbm", "walker_f64.cu")
@@ -226,13 +239,46 @@ def source_sha(fname):
         return None
 
 
-def traffic_of(phase, src, precision):
-    """The recorded DRAM bytes of a phase's kernel, if taken from this source
-    at this precision (the captures are of the BF16 step)."""
-    tr = TRAFFIC.get(phase)
-    if not tr or tr.get("sha") != source_sha(src) or precision not in tr.get("precisions", ("bf16",)):
+def function_sha(fname, signature):
+    """SHA-256 of one function's text (from `signature` to its closing brace)
+    in a CUDA source file: a capture stays valid while that kernel's own source
+    is unchanged, whatever else the file holds."""
+    import hashlib
+
+    path = os.path.join(ROOT, "paper_1711_02242_gb300", "csrc", fname)
+    try:
+        with open(path) as f:
+            text = f.read()
+    except OSError:
         return None
-    return tr["bytes"]
+    i = text.find(signature)
+    if i < 0:
+        return None
+    depth, j = 0, text.find("{", i)
+    for k in range(j, len(text)):
+        if text[k] == "{":
+            depth += 1
+        elif text[k] == "}":
+            depth -= 1
+            if depth == 0:
+                return hashlib.sha256(text[i:k + 1].encode()).hexdigest()
+    return None
+
+
+def traffic_of(phase, src, precision):
+    """The recorded DRAM bytes of a phase's kernel at this precision, if its
+    source (the file, or the kernel's own text for entries that name it) is
+    the one the counters were taken from."""
+    entries = TRAFFIC.get(phase)
+    if not entries:
+        return None
+    for tr in entries if isinstance(entries, list) else [entries]:
+        if precision not in tr.get("precisions", ("bf16",)):
+            continue
+        sha = function_sha(src, tr["function"]) if "function" in tr else source_sha(src)
+        if tr.get("sha") == sha:
+            return tr["bytes"]
+    return None
 
 
 def rooflines(w, phases, precision, K):
@@ -270,9 +316,9 @@ def rooflines(w, phases, precision, K):
             bound = "alu"
         else:
             base = pk["bf16_tflops_sustained"]
-            peak = base if precision == "bf16" else base / 2
+            peak = base if precision.startswith("bf16") else base / 2
             unit = "TFLOP/s"
-            src_peak = (f"{pk_kind} bf16 sustained" if precision == "bf16"
+            src_peak = (f"{pk_kind} bf16 sustained" if precision.startswith("bf16")
                         else f"{pk_kind} bf16 sustained / 2 (TF32 nominal ratio)")
         achieved = work / (ms_launch * 1e-3) / 1e12
         traffic = traffic_of(ph, src, precision)
@@ -323,8 +369,7 @@ def run_gpu(args, w: workloads.Workload):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     b.build()
-    prec = {"fp64": pkg.AFQMC_FP64, "tf32": pkg.AFQMC_MIXED_TF32, "bf16": pkg.AFQMC_MIXED_BF16}[
-        args.precision]
+    prec = PRECISIONS[args.precision]
     h1, L, H0, C, conv, grad = make_inputs(w)
     p = pkg.default_params(w.M, w.N, w.nchol, w.nwalkers, dt=w.dt, seed=replica_seed(w.seed, rank),
                            qr_period=w.qr_period, energy_period=w.energy_period,
@@ -586,7 +631,7 @@ def run_batched(args):
     from paper_1711_02242_gb300 import build as b
 
     b.build()
-    prec = {"fp64": 0, "tf32": 1, "bf16": 2}[args.precision]
+    prec = PRECISIONS[args.precision]
     ws_ = workloads.batched_systems()
     inputs = _inputs_parallel(ws_, trial_iters=10)
     runs = []
@@ -628,8 +673,7 @@ def run_batched(args):
         "metric": "walker-steps/s, 16 uneven systems in one graph launch per block",
         "value": total_ws * K / (ms * 1e-3), "unit": "walker-steps/s", "n_gpus": 1, "steps": K,
         "warmup": blk, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": {"fp64": "f64", "tf32": "tf32/f32/f64",
-                                       "bf16": "bf16/f32/f64"}[args.precision],
+        "vs_baseline": None, "dtype": DTYPES[args.precision],
         "data": "synthetic",
         "config": {"workload": "16 systems, M in {40..200}, N=M/8, nchol=5M, walkers in {64..1024}",
                    "systems": [[w.M, w.N, w.nchol, w.nwalkers] for w in ws_],
@@ -655,7 +699,7 @@ def run_serve(args):
     from paper_1711_02242_gb300.serve import Request, Server, latency_stats
 
     b.build()
-    prec = {"fp64": 0, "tf32": 1, "bf16": 2}[args.precision]
+    prec = PRECISIONS[args.precision]
     stream = workloads.request_stream(count=args.requests, rate=args.rate, blocks=args.blocks,
                                       steps_per_block=args.steps_per_block)
     inputs = _inputs_parallel([w for _, w in stream])
@@ -690,7 +734,7 @@ def run_serve(args):
         "value": ws_total / makespan, "unit": "walker-steps/s", "n_gpus": 1,
         "steps": int(np.mean([r.nsteps for r in reqs])), "warmup": 0,
         "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": {"fp64": "f64", "tf32": "tf32/f32/f64", "bf16": "bf16/f32/f64"}[args.precision],
+        "dtype": DTYPES[args.precision],
         "data": "synthetic",
         "config": {"workload": f"{len(reqs)} requests, Poisson {args.rate}/s, M in [20,300], "
                                f"N in [2,M/8], nchol=5M, walkers in [128,2048], "
@@ -884,7 +928,7 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--precision", default="bf16", choices=["fp64", "tf32", "bf16"])
+    ap.add_argument("--precision", default="bf16", choices=list(PRECISIONS))
     ap.add_argument("--no-fp64-compare", action="store_true",
                     help="skip the FP64 path's own few-step measurement")
     ap.add_argument("--fp64-steps", type=int, default=5)
@@ -924,7 +968,7 @@ def main():
         "metric": f"walker-steps/s at M={w.M}", "value": value, "unit": "walker-steps/s",
         "n_gpus": N, "steps": K, "warmup": r["warmup"], "ms_per_step": ms_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": {"fp64": "f64", "tf32": "tf32/f32/f64", "bf16": "bf16/f32/f64"}[args.precision],
+        "dtype": DTYPES[args.precision],
         "data": "synthetic",
         "config": {"workload": workload_desc(w),
                    "precision": args.precision, "l2": "inputs larger than L2 (packed L "

@@ -68,10 +68,14 @@ typedef enum afqmc_status {
 enum {
   AFQMC_FP64 = 0,       /* every step in float64 / complex128                   */
   AFQMC_MIXED_TF32 = 1, /* contractions on tcgen05 tensor cores, TF32 inputs,   */
-                        /* FP32 accumulation; S^-1, Theta and Gram-Schmidt in   */
-                        /* FP32; log det sums, overlap ratios, weights and the  */
-                        /* identity part of the one-body half steps in FP64     */
-  AFQMC_MIXED_BF16 = 2  /* as MIXED_TF32 with BF16 inputs to the contractions   */
+                        /* FP32 accumulation; Theta, LU, overlap ratios,        */
+                        /* weights, Gram-Schmidt and the identity part of the   */
+                        /* one-body half steps in FP64                          */
+  AFQMC_MIXED_BF16 = 2, /* as MIXED_TF32 with BF16 inputs to the contractions   */
+  AFQMC_MIXED_TF32_F32LU = 3, /* as MIXED_TF32 with the elimination (S^-1),     */
+                              /* Theta and Gram-Schmidt in FP32 (log det sums,  */
+                              /* overlap ratios and weights stay FP64)          */
+  AFQMC_MIXED_BF16_F32LU = 4  /* as MIXED_BF16, the same three steps in FP32    */
 };
 
 /* Walker update rule. */

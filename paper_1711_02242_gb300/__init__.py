@@ -21,6 +21,8 @@ LIB_PATH = os.path.join(HERE, "libafqmc.so")
 
 AFQMC_OK = 0
 AFQMC_FP64, AFQMC_MIXED_TF32, AFQMC_MIXED_BF16 = 0, 1, 2
+# the mixed paths with S^-1, Theta and Gram-Schmidt in FP32 (opt-in)
+AFQMC_MIXED_TF32_F32LU, AFQMC_MIXED_BF16_F32LU = 3, 4
 AFQMC_PHASELESS, AFQMC_FREE = 0, 1
 STATUS = {0: "OK", -1: "EINVAL", -2: "ENOSPC", -3: "ENONFINITE", -4: "ECUDA",
           -5: "ETIMEOUT", -6: "ESTATE", -7: "EUNSUPPORTED"}

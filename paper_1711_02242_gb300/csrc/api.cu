@@ -45,7 +45,8 @@ size_t plan(const afqmc_params& p, Bufs* b, char* base) {
   const bool mixed = p.precision != AFQMC_FP64;
   size_t nchunk = (G + exchange_chunk(p.N, p.nchol) - 1) / exchange_chunk(p.N, p.nchol);
   if (mixed) nchunk = G;  // the tensor-core exchange leaves one partial per vector
-  const size_t lo = (p.precision == AFQMC_MIXED_BF16) ? 2 : 4;
+  const size_t lo =
+      (p.precision == AFQMC_MIXED_BF16 || p.precision == AFQMC_MIXED_BF16_F32LU) ? 2 : 4;
   // pitches: 16-byte rows for TMA; Mp a multiple of 16 so that 16-column
   // epilogue chunks of the flattened (p, q) index never straddle rows
   const size_t Gp = (G + 7) / 8 * 8, Mp = (M + 15) / 16 * 16, Pp = (P + 3) / 4 * 4;
@@ -115,6 +116,7 @@ size_t plan(const afqmc_params& p, Bufs* b, char* base) {
     b->bp_tmp = a.take<char>(row * W);
   }
   b->mixed = mixed;
+  b->f32lu = p.precision == AFQMC_MIXED_TF32_F32LU || p.precision == AFQMC_MIXED_BF16_F32LU;
   b->lo_kind = mixed ? (lo == 2 ? LO_BF16 : LO_TF32) : LO_NONE;
   b->lo_bytes = (int)lo;
   b->Gp = (int)Gp;
@@ -197,8 +199,7 @@ static int check_params(const afqmc_params* p) {
     set_error("the comb needs real weights: pc_period must be 0 for free projection");
     return AFQMC_EINVAL;
   }
-  if (p->precision != AFQMC_FP64 && p->precision != AFQMC_MIXED_TF32 &&
-      p->precision != AFQMC_MIXED_BF16) {
+  if (p->precision < AFQMC_FP64 || p->precision > AFQMC_MIXED_BF16_F32LU) {
     set_error("precision %d is not available in this build", p->precision);
     return AFQMC_EUNSUPPORTED;
   }
@@ -262,7 +263,8 @@ int overlap_update(afqmc_state* s, bool into_ld, bool timed) {
     ov.th_lo = b.th_lo;
     ov.lo_kind = b.lo_kind;
     ov.Mp = b.Mp;
-    ov.Sinv32 = reinterpret_cast<float2*>(b.Sinv);  // FP32 elimination and Theta
+    // FP32 elimination and Theta when asked for (else float64 with the copy)
+    if (b.f32lu) ov.Sinv32 = reinterpret_cast<float2*>(b.Sinv);
   }
   if (timed) prof_begin(s, AFQMC_PH_OVERLAP);
   AFQ_TRY(launch_overlap(ov, s->st));
@@ -559,8 +561,9 @@ static int step_once(afqmc_state* s) {
     // which the kernel applies to ld (no new overlap needed)
     MgsArgs ma{W, M, N, b.phiT, b.wt, b.ld};
     if (b.mixed) {
-      // FP32 sweep; the kernel also writes the operand copy of the orbitals
-      ma.f32 = 1;
+      // the sweep (FP32 in shared memory when asked for, else float64) also
+      // refreshes the operand copy of the orbitals
+      ma.f32 = b.f32lu ? 1 : 0;
       ma.phi_lo = b.phi_lo;
       ma.lo_kind = b.lo_kind;
       ma.Mp = b.Mp;

@@ -74,17 +74,20 @@ def test_rooflines_from_phase_times():
     assert per == 8 * 25 ** 3
     assert bench.algorithmic_per_walker(w)["theta"] == 8 * (300 - 25) * 25 * 25
     assert abs(ov["achieved"] - per * 512 / 1.3e-3 / 1e12) < 1e-12
-    # the mixed path's elimination runs in FP32; the float64 path's on the FP64 pipe
-    assert ov["bound"] == "alu" and abs(ov["frac"] - ov["achieved"] / bench.FP32_PEAK_TFLOPS) < 1e-12
-    ov64 = bench.rooflines(w, ph, "fp64", K)[0]
-    assert ov64["phase"] == "overlap" and abs(ov64["frac"] - ov64["achieved"] / bench.FP64_PEAK_TFLOPS) < 1e-12
+    # the bf16 mixed path keeps the elimination and Gram-Schmidt on the FP64 pipe
+    assert ov["bound"] == "alu" and abs(ov["frac"] - ov["achieved"] / bench.FP64_PEAK_TFLOPS) < 1e-12
     assert roofs[1]["bound"] == "tensor"
-    # the mixed path's Gram-Schmidt sweep is measured against HBM bandwidth
-    qr = roofs[2]
+    assert roofs[2]["bound"] == "alu" and roofs[2]["kernel"] == "k_mgs"
+    # the opt-in -f32lu path: the elimination against the FP32 pipe, the
+    # Gram-Schmidt sweep against HBM bandwidth
+    r32 = bench.rooflines(w, ph, "bf16-f32lu", K)
+    assert abs(r32[0]["frac"] - r32[0]["achieved"] / bench.FP32_PEAK_TFLOPS) < 1e-12
+    qr = r32[2]
     pk, _ = bench.peaks()
-    assert qr["bound"] == "hbm" and qr["unit"] == "GB/s"
-    assert abs(qr["achieved"] - bench.bytes_per_walker(w, "bf16")["qr"] * 512 / 1.3e-3 / 1e9) < 1e-9
+    assert qr["bound"] == "hbm" and qr["unit"] == "GB/s" and qr["kernel"] == "k_mgs_f32"
+    assert abs(qr["achieved"] - bench.bytes_per_walker(w, "bf16-f32lu")["qr"] * 512 / 1.3e-3 / 1e9) < 1e-9
     assert abs(qr["frac"] - qr["achieved"] / pk["hbm_gbs"]) < 1e-12
+    assert set(bench.PRECISIONS) == {"fp64", "tf32", "bf16", "tf32-f32lu", "bf16-f32lu"}
     assert abs(sum(r["share_of_step"] for r in roofs) - 1.0) < 1e-12
     # a recorded traffic figure counts only for the source it was taken from
     saved = dict(bench.TRAFFIC)
@@ -95,6 +98,14 @@ def test_rooflines_from_phase_times():
         assert bench.rooflines(w, ph, "tf32", K)[0]["traffic"] is None
         bench.TRAFFIC["overlap"] = {"bytes": 1.0e8, "sha": "0" * 64}
         assert bench.rooflines(w, ph, "bf16", K)[0]["traffic"] is None
+        # an entry may pin one kernel's own text instead of the whole file
+        sig = "__global__ void __launch_bounds__(OV_T) k_overlap(OverlapArgs a)"
+        fsha = bench.function_sha("walker_f64.cu", sig)
+        assert fsha is not None and fsha != bench.source_sha("walker_f64.cu")
+        bench.TRAFFIC["overlap"] = [{"bytes": 2.0e8, "function": sig, "sha": "1" * 64},
+                                    {"bytes": 3.0e8, "function": sig, "sha": fsha}]
+        assert bench.rooflines(w, ph, "bf16", K)[0]["traffic"] == 3.0e8
+        assert bench.function_sha("walker_f64.cu", "no such kernel") is None
     finally:
         bench.TRAFFIC.clear()
         bench.TRAFFIC.update(saved)

@@ -124,3 +124,33 @@ def test_mixed_weights_carry_no_common_drift(pkg, prec, tol_bias, tol_phi):
     d = np.linalg.norm((phi1 - phi0)[alive].reshape(alive.size, -1), axis=1)
     n = np.linalg.norm(phi0[alive].reshape(alive.size, -1), axis=1)
     assert np.max(d / n) < tol_phi
+
+
+@pytest.mark.parametrize("prec,prec32,tol_phi", [(2, 4, 1e-2), (1, 3, 3e-3)])
+def test_f32lu_precisions_close_to_float64_lu(pkg, prec, prec32, tol_phi):
+    """The opt-in _F32LU precisions (the elimination, Theta and Gram-Schmidt
+    in FP32; log det sums, overlap ratios and weights in float64) against the
+    same mixed precision with those steps in float64: seven steps on
+    identical fields differ by FP32 rounding fed through the BF16/TF32
+    contractions, with no common weight drift."""
+    h1, L, _ = workloads.hamiltonian(24, 120, 6100, l_scale=workloads.l_amplitude(24, 120))
+    C, _, _, _ = scf.rhf(h1, L, 4)
+    out = []
+    for precision in (prec, prec32):
+        p = pkg.default_params(24, 4, 120, 64, dt=0.01, seed=4, qr_period=5, energy_period=1,
+                               precision=precision)
+        run = pkg.AfqmcRun(h1, L, C, p)
+        e0 = run.local_energies()
+        run.propagate(7)
+        out.append((e0, run.get_walkers(), run.energy_log()))
+        assert run.info().status == 0
+        run.close()
+    (e0a, (pa, wa, _), la), (e0b, (pb, wb, _), lb) = out
+    assert np.max(np.abs(e0b - e0a) / np.abs(e0a)) < 1e-5
+    alive = np.nonzero((wa != 0) & (wb != 0))[0]
+    assert alive.size > 32
+    d = np.linalg.norm((pb - pa)[alive].reshape(alive.size, -1), axis=1)
+    n = np.linalg.norm(pa[alive].reshape(alive.size, -1), axis=1)
+    assert np.max(d / n) < tol_phi
+    assert abs(np.mean((wb[alive] / wa[alive]).real) - 1) < 2e-3
+    assert np.max(np.abs(lb[:, 1] - la[:, 1]) / np.abs(la[:, 1])) < 2e-4
