@@ -131,7 +131,7 @@ struct OverlapArgs {
   int lo_kind = LO_NONE, Mp = 0;
   int unit_trial = 0;  // VTt = [I_N | 0]: S is the top block of Phi, Theta's top rows I
   double2* Sinv = nullptr;  // [W][N][N] scratch: S^-1 of live walkers
-  float2* Sinv32 = nullptr;  // mixed path: FP32 elimination, S^-1 here and FP32 Theta
+  float2* Sinv32 = nullptr;  // _F32LU precisions: FP32 elimination, S^-1 here and FP32 Theta
 };
 // S^-1 and log det (k_overlap), then Theta (k_theta_rows)
 int launch_overlap(const OverlapArgs& a, cudaStream_t st);
@@ -155,7 +155,7 @@ struct MgsArgs {
   double* phiT;  // [W][2][N][M] in place
   const double* wt;
   double* ld;    // [W][2]: log <Psi_T|Psi> of live walkers, lowered by 2 sum_k log r_kk
-  int f32 = 0;   // mixed path: FP32 sweep in shared memory where [N][M] fits
+  int f32 = 0;   // _F32LU precisions: FP32 sweep in shared memory where [N][M] fits
   void* phi_lo = nullptr;  // and, if set, the BF16/TF32 copy of the result (pitch Mp)
   int lo_kind = LO_NONE, Mp = 0;
 };

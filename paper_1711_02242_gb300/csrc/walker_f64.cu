@@ -1,5 +1,6 @@
 // Per-walker kernels (float64, and the FP32 variants of the overlap, Theta and
-// Gram-Schmidt kernels used by the mixed path) and the set-up kernels.
+// Gram-Schmidt kernels used by the mixed path's _F32LU precisions) and the
+// set-up kernels.
 //
 // Layouts (W walkers, M orbitals, N electrons per spin, G Cholesky vectors,
 // P = M(M+1)/2):
@@ -259,7 +260,7 @@ int launch_taylor_term(const TaylorArgsT<double>& a, cudaStream_t st) { return l
 // ------------------------------------------------------------- overlap ------
 // Theorem 1.1, Eq. precomputing, in the trial-adapted basis where V_T =
 // [I_N; 0]; float64 on the float64 path, FP32 with float64 log det sums on
-// the mixed path (k_overlap<float>, k_theta_rows_f32).  k_overlap, one block
+// the _F32LU mixed precisions (k_overlap<float>, k_theta_rows_f32).  k_overlap, one block
 // per walker:
 //   1. S = V_T^T Phi is the top N x N block of Phi (a gather);
 //   2. Gauss-Jordan elimination with partial pivoting (largest |s_rk|^2, the
@@ -271,8 +272,8 @@ int launch_taylor_term(const TaylorArgsT<double>& a, cudaStream_t st) { return l
 namespace {
 constexpr int OV_T = 256;
 }
-// Element traits of the overlap kernel: float64 on the float64 path; FP32 on
-// the mixed path, whose orbitals carry BF16/TF32 propagation errors far above
+// Element traits of the overlap kernel: float64; FP32 for the _F32LU mixed
+// precisions, whose orbitals carry BF16/TF32 propagation errors far above
 // FP32 rounding (the log det sums stay float64).
 template <typename T>
 struct Vec2;
@@ -520,7 +521,7 @@ __global__ void __launch_bounds__(TH_T) k_theta_rows(OverlapArgs a) {
   }
 }
 
-// Mixed path: the same rows with FP32 arithmetic.  Theta only feeds the
+// _F32LU mixed precisions: the same rows with FP32 arithmetic.  Theta only feeds the
 // BF16/TF32 contractions (force bias, exchange) and the one-body energy
 // there, so FP32 products (S^-1 and Phi rounded to FP32) lose nothing those do
 // not, and this GPU's FP32 pipe is ~60x its FP64 one: the kernel becomes bound
@@ -811,7 +812,7 @@ __global__ void __launch_bounds__(256) k_mgs(MgsArgs a) {
   if (threadIdx.x == 0 && a.ld) a.ld[2L * w] -= 2.0 * (sh[0] + sh[1]);
 }
 
-// Mixed path: the same sweep in FP32 with the walker's orbitals resident in
+// _F32LU mixed precisions: the same sweep in FP32 with the walker's orbitals resident in
 // shared memory ([N][M] complex, read once from and written once to the
 // float64 orbitals), one warp per later column and lanes over p (contiguous,
 // conflict-free).  The orbitals only feed the BF16/TF32 propagation and the
