@@ -433,3 +433,142 @@ def test_population_control_keeps_total_weight_in_a_run():
     # every new walker is an exact copy of an old one
     e_after = afqmc.local_energy(o.setup, o.theta)
     assert all(np.min(np.abs(e_before - e)) == 0 for e in e_after)
+
+
+# -------------------------- phaseless projection and the caps (App. B) -------
+def _fock_force_bias(c, dt, phi):
+    """xbar_g = -sqrt(dt) (<v_g>_m - vbar_g) of Eq. fb with the mean-field
+    background, <v_g>_m = <Psi_T|v_g|Psi>/<Psi_T|Psi>, all in Fock space."""
+    F = c["F"]
+    psiT, psi = F.determinant(c["C"]), F.determinant(phi)
+    ov = psiT.conj() @ psi
+    out = []
+    for g in range(c["L"].shape[0]):
+        vg = 1j * F.one_body(c["L"][g]).toarray()
+        out.append(-math.sqrt(dt) * (psiT.conj() @ vg @ psi / ov - psiT.conj() @ vg @ psiT))
+    return np.array(out)
+
+
+def _fock_ratio_and_importance(c, st, dt, xi, xbar, phi):
+    """R = <Psi_T|B(xi - xbar)|Psi>/<Psi_T|Psi> (B with the mean-field scalar)
+    and I = R exp(xi.xbar - xbar.xbar/2) (Eq. hybrid-wt), from Fock-space
+    exponentials."""
+    F = c["F"]
+    psiT, psi = F.determinant(c["C"]), F.determinant(phi)
+    R = (psiT.conj() @ (_fock_propagator(c, st, xi - xbar, dt) @ psi)) / (psiT.conj() @ psi)
+    return R, R * np.exp(np.sum(xi * xbar) - 0.5 * np.sum(xbar * xbar))
+
+
+@pytest.mark.parametrize("dt,seed", [(1.0, 2), (1.0, 12), (0.5, 3), (0.5, 5)])
+def test_phaseless_weight_is_cos_projection_of_the_overlap_ratio(fock_case, dt, seed):
+    """Eqs. hybrid-wt, if_rle and weight_update_2: one phaseless step gives
+    W' = W |I| max(0, cos dtheta) with dtheta the phase of the overlap ratio R
+    of the shifted propagator (mean-field scalar included), not the phase of I
+    itself.  R, I and the force bias come from Fock space.  The cases: a
+    negative cos dtheta (weight exactly 0) whose Arg-I reading would keep the
+    walker (dt = 1, seed 2); a strongly negative one (seed 12); positive ones
+    where Arg I and Arg R give different weights (dt = 0.5)."""
+    c = fock_case
+    phi = c["phi"]
+    G = c["L"].shape[0]
+    p = afqmc.Params(dt=dt, taylor_order=60, qr_period=0, energy_period=0, seed=seed,
+                     fb_cap=-1.0, wmax=1e300)
+    o = afqmc.Oracle(c["h1"], c["L"], c["C"], 1, p, H0=c["H0"], phi0=phi)
+    xbar = _fock_force_bias(c, dt, phi)
+    assert np.max(np.abs(xbar)) < 1.0  # (the cap, pinned below, is off here anyway)
+    xi = philox.gaussian_fields(seed, 0, [0], G)[0]
+    R, I = _fock_ratio_and_importance(c, o.setup, dt, xi, xbar, phi)
+    expected = abs(I) * max(0.0, math.cos(np.angle(R)))
+    arg_i_reading = abs(I) * max(0.0, math.cos(np.angle(I)))
+    o.step()
+    if math.cos(np.angle(R)) < 0:
+        assert o.weight[0] == 0.0
+    else:
+        assert abs(o.weight[0] - expected) < 1e-12 * max(1.0, expected)
+    # the two readings of dtheta differ here by far more than the tolerance
+    assert abs(arg_i_reading - expected) > 1e-4 or (seed == 12 and expected == 0.0)
+
+
+def test_force_bias_cap_keeps_the_phase(fock_case):
+    """Appendix B: a force-bias component larger than v_max = 1 in magnitude is
+    scaled back to magnitude 1 with its phase kept; smaller ones are left
+    alone.  The oracle's xbar is read off the shifted fields x = xi - xbar it
+    records in a back-propagation window, xi from the generator, and compared
+    with the Fock-space force bias of Eq. fb."""
+    c = fock_case
+    phi = c["phi"]
+    G = c["L"].shape[0]
+    dt = 2.0
+    xbar = _fock_force_bias(c, dt, phi)
+    big = np.abs(xbar) > 1.0
+    assert 0 < np.count_nonzero(big) < G
+    # clamping Re xbar instead of |xbar| would give another answer
+    assert np.max(np.abs(np.abs(xbar[big].real) - 1.0)) > 1e-3
+    p = afqmc.Params(dt=dt, taylor_order=60, qr_period=0, energy_period=0, seed=7, fb_cap=1.0)
+    o = afqmc.Oracle(c["h1"], c["L"], c["C"], 1, p, H0=c["H0"], phi0=phi)
+    o.bp_begin()
+    o.step()
+    xi = philox.gaussian_fields(7, 0, [0], G)[0]
+    xbar_o = xi - o.bp["fields"][0][0]
+    capped = np.where(big, xbar / np.abs(xbar), xbar)
+    assert np.max(np.abs(xbar_o - capped)) < 1e-12
+    assert np.max(np.abs(np.abs(xbar_o[big]) - 1.0)) < 1e-14
+    assert np.max(np.abs(np.angle(xbar_o[big]) - np.angle(xbar[big]))) < 1e-12
+
+
+def test_weight_cap(fock_case):
+    """Appendix B: a weight above W_max is set to W_max.  Two walkers at the
+    same orbitals draw different fields; W_max between their Fock-space
+    phaseless weights caps one and leaves the other."""
+    c = fock_case
+    phi = c["phi"]
+    G = c["L"].shape[0]
+    dt = 0.05
+    st = afqmc.Setup(c["h1"], c["L"], c["C"], c["H0"], dt=dt)
+    xbar = _fock_force_bias(c, dt, phi)
+    ws = []
+    for w in range(2):
+        xi = philox.gaussian_fields(11, 0, [w], G)[0]
+        R, I = _fock_ratio_and_importance(c, st, dt, xi, xbar, phi)
+        ws.append(abs(I) * max(0.0, math.cos(np.angle(R))))
+    assert abs(ws[0] - ws[1]) > 1e-3
+    wmax = 0.5 * (ws[0] + ws[1])
+    p = afqmc.Params(dt=dt, taylor_order=40, qr_period=0, energy_period=0, seed=11,
+                     wmax=wmax)
+    o = afqmc.Oracle(c["h1"], c["L"], c["C"], 2, p, H0=c["H0"], phi0=phi)
+    o.step()
+    hi, lo = int(np.argmax(ws)), int(np.argmin(ws))
+    assert o.weight[hi] == wmax
+    assert abs(o.weight[lo] - ws[lo]) < 1e-12
+
+
+def test_local_energy_cap_in_the_mixed_estimator(fock_case):
+    """Eq. cap: in the mixed estimator Re E_loc is clamped to
+    E_T +- sqrt(C / dt).  Two walkers, one at the trial (inside the window) and
+    one far from it (outside); local energies and E_T from Fock space; the
+    estimator equals the hand-clamped weighted mean, and without the cap the
+    plain weighted mean."""
+    c = fock_case
+    F, H = c["F"], c["H"]
+    psiT = F.determinant(c["C"])
+    e_t = ((psiT.conj() @ (H @ psiT)) / (psiT.conj() @ psiT)).real
+    rng = np.random.default_rng(8)
+    far = c["C"] + 1.5 * rng.standard_normal(c["C"].shape) + 1.5j * rng.standard_normal(c["C"].shape)
+    phis = np.stack([c["C"].astype(complex), far])
+    e_loc = []
+    for ph in phis:
+        psi = F.determinant(ph)
+        e_loc.append((psiT.conj() @ (H @ psi)) / (psiT.conj() @ psi))
+    e_loc = np.array(e_loc).real
+    dt, C = 0.01, 1e-4
+    half = math.sqrt(C / dt)
+    assert abs(e_loc[0] - e_t) < half < abs(e_loc[1] - e_t)
+    wts = np.array([1.0, 2.5])
+    for cap in (C, -1.0):
+        o = afqmc.Oracle(c["h1"], c["L"], c["C"], 2,
+                         afqmc.Params(dt=dt, ecap_C=cap, energy_period=0), H0=c["H0"], phi0=phis)
+        o.weight[:] = wts
+        num, den = o.energy_sums()
+        e = np.clip(e_loc, e_t - half, e_t + half) if cap > 0 else e_loc
+        assert abs(den - wts.sum()) < 1e-15
+        assert abs(num / den - np.sum(wts * e) / wts.sum()) < 1e-11
