@@ -44,12 +44,15 @@ import workloads  # noqa: E402
 PHASES = ["force_bias", "fields", "v_assembly", "bhalf", "taylor", "overlap", "weight", "qr",
           "comb", "energy", "theta"]
 
-# --precision -> afqmc_params.precision.  "bf16" / "tf32" keep Theta, LU, the
-# overlap ratios, the weights and Gram-Schmidt in float64; the "-f32lu"
-# variants (opt-in) run the elimination, Theta and Gram-Schmidt in FP32.
-PRECISIONS = {"fp64": 0, "tf32": 1, "bf16": 2, "tf32-f32lu": 3, "bf16-f32lu": 4}
+# --precision -> afqmc_params.precision.  "bf16" / "tf32" keep S^-1 (the LU),
+# log det, the overlap ratios, the weights and Gram-Schmidt in float64 and form
+# Theta = Phi S^-1 in FP32; "-f64theta" forms Theta in float64 too; the
+# "-f32lu" variants (opt-in) run the elimination and Gram-Schmidt in FP32.
+PRECISIONS = {"fp64": 0, "tf32": 1, "bf16": 2, "tf32-f32lu": 3, "bf16-f32lu": 4,
+              "tf32-f64theta": 5, "bf16-f64theta": 6}
 DTYPES = {"fp64": "f64", "tf32": "tf32/f32/f64", "bf16": "bf16/f32/f64",
-          "tf32-f32lu": "tf32/f32/f64", "bf16-f32lu": "bf16/f32/f64"}
+          "tf32-f32lu": "tf32/f32/f64", "bf16-f32lu": "bf16/f32/f64",
+          "tf32-f64theta": "tf32/f32/f64", "bf16-f64theta": "bf16/f32/f64"}
 
 
 def peaks():
@@ -74,9 +77,9 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # to another kernel at this precision, is reported as null.
 TRAFFIC = {
     "theta": [{"bytes": (64.265728 + 25.652224) * 1e6, "sha": "d8af088925f6dd017e10c429fdb6a28ef844edf64bdcef66e2f823c786f2631e", "precisions": ("bf16-f32lu",)},
-              # k_theta_rows (float64 Theta of the bf16 / tf32 mixed paths): its own
+              # k_theta_rows (float64 Theta of the -f64theta mixed paths): its own
               # text is unchanged since this capture (DRAM 64.5 + 30.3 MB per launch)
-              {"bytes": (64.544512 + 30.260480) * 1e6, "precisions": ("bf16",),
+              {"bytes": (64.544512 + 30.260480) * 1e6, "precisions": ("bf16-f64theta",),
                "function": "__global__ void __launch_bounds__(TH_T) k_theta_rows(OverlapArgs a)",
                "sha": "d7ee3083bab22e614e7aa9c51aff2886d255680c62a6454f637a089a17969ae7"}],
     "overlap": {"bytes": (8.234752 + 0.0) * 1e6, "sha": "d8af088925f6dd017e10c429fdb6a28ef844edf64bdcef66e2f823c786f2631e", "precisions": ("bf16-f32lu",)},
@@ -196,25 +199,30 @@ def algorithmic_per_walker(w: workloads.Workload):
 def bytes_per_walker(w: workloads.Workload, precision):
     """Algorithmic DRAM bytes per walker of the mixed path's FP32 kernels,
     which are bound by memory traffic, not by their FP32 arithmetic:
-      theta  read Phi (2 N M float64) and the FP32 S^-1 (N^2 complex), write
-             Theta (2 N M float64) and its BF16/TF32 copy (2 N Mp);
+      theta  read Phi (2 N M float64) and S^-1 (N^2 complex: float64, or FP32
+             on the -f32lu paths), write Theta (2 N M float64) and its
+             BF16/TF32 copy (2 N Mp);
       qr     read and write Phi (2 x 2 N M float64), write its BF16/TF32 copy."""
     M, N = w.M, w.N
     Mp = (M + 15) // 16 * 16
     lo = 2 if precision.startswith("bf16") else 4
-    return {"theta": 2 * N * M * 8 + N * N * 8 + 2 * N * M * 8 + 2 * N * Mp * lo,
+    sinv = 8 if precision.endswith("f32lu") else 16
+    return {"theta": 2 * N * M * 8 + N * N * sinv + 2 * N * M * 8 + 2 * N * Mp * lo,
             "qr": 2 * (2 * N * M * 8) + 2 * N * Mp * lo}
 
 
 def kernel_of_phase(precision):
-    """Phase -> (kernel, bound, source file).  The elimination, Theta and the
+    """Phase -> (kernel, bound, source file).  The elimination and the
     Gram-Schmidt sweep are FP64-pipe kernels on the float64 path and the
-    bf16 / tf32 mixed paths; the -f32lu mixed paths run them in FP32 (the
-    elimination against the FP32 pipe, Theta and the sweep against HBM)."""
+    bf16 / tf32 mixed paths, and so is Theta = Phi S^-1 on the float64 path
+    and the -f64theta mixed paths; the bf16 / tf32 paths form Theta in FP32
+    (against HBM), and the -f32lu paths also run the elimination (against the
+    FP32 pipe) and the sweep (against HBM) in FP32."""
     k = dict(KERNEL_OF_PHASE)
+    if precision in ("bf16", "tf32") or precision.endswith("f32lu"):
+        k["theta"] = ("k_theta_rows_f32", "hbm", "walker_f64.cu")
     if precision.endswith("f32lu"):
         k["overlap"] = ("k_overlap<float>", "alu32", "walker_f64.cu")
-        k["theta"] = ("k_theta_rows_f32", "hbm", "walker_f64.cu")
         k["qr"] = ("k_mgs_f32", "hbm", "walker_f64.cu")
     return k
 

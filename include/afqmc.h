@@ -68,14 +68,20 @@ typedef enum afqmc_status {
 enum {
   AFQMC_FP64 = 0,       /* every step in float64 / complex128                   */
   AFQMC_MIXED_TF32 = 1, /* contractions on tcgen05 tensor cores, TF32 inputs,   */
-                        /* FP32 accumulation; Theta, LU, overlap ratios,        */
+                        /* FP32 accumulation; the overlap S = V_T^T Phi, its    */
+                        /* LU / inverse S^-1 and log det, the overlap ratios,   */
                         /* weights, Gram-Schmidt and the identity part of the   */
-                        /* one-body half steps in FP64                          */
+                        /* one-body half steps in FP64; the product             */
+                        /* Theta = Phi S^-1 (an operand of the contractions)    */
+                        /* in FP32 from the float64 S^-1                        */
   AFQMC_MIXED_BF16 = 2, /* as MIXED_TF32 with BF16 inputs to the contractions   */
-  AFQMC_MIXED_TF32_F32LU = 3, /* as MIXED_TF32 with the elimination (S^-1),     */
-                              /* Theta and Gram-Schmidt in FP32 (log det sums,  */
+  AFQMC_MIXED_TF32_F32LU = 3, /* as MIXED_TF32 with the elimination (S^-1) and  */
+                              /* Gram-Schmidt also in FP32 (log det sums,       */
                               /* overlap ratios and weights stay FP64)          */
-  AFQMC_MIXED_BF16_F32LU = 4  /* as MIXED_BF16, the same three steps in FP32    */
+  AFQMC_MIXED_BF16_F32LU = 4, /* as MIXED_BF16, the same steps in FP32          */
+  AFQMC_MIXED_TF32_F64THETA = 5, /* as MIXED_TF32 with Theta = Phi S^-1 also    */
+                                 /* formed in float64                           */
+  AFQMC_MIXED_BF16_F64THETA = 6  /* as MIXED_BF16 with Theta in float64         */
 };
 
 /* Walker update rule. */
@@ -97,7 +103,7 @@ typedef struct afqmc_params {
   int32_t qr_period;     /* steps between Gram-Schmidt passes (0 = never)      */
   int32_t pc_period;     /* steps between comb population controls (0 = off)   */
   int32_t energy_period; /* steps between energy measurements (0 = never)      */
-  int32_t precision;     /* AFQMC_FP64 / AFQMC_MIXED_TF32 / AFQMC_MIXED_BF16   */
+  int32_t precision;     /* AFQMC_FP64, AFQMC_MIXED_* (the enum above)         */
   int32_t mode;          /* AFQMC_PHASELESS / AFQMC_FREE                       */
   double ecap_C;         /* local-energy cap constant C of Eq. cap; <= 0: off  */
   double fb_cap;         /* force-bias magnitude cap v_max; <= 0: off          */
@@ -418,11 +424,16 @@ AFQMC_API int afqmc_widen_f32(const float* d_in, double* d_out, int64_t n, void*
  * Cholesky vectors one exchange block handles) live in one fixed 16 MiB array
  * inside the library, which every GPU that loads the library reserves until
  * the process exits.  Calls needing more return AFQMC_ENOSPC and launch
- * nothing (split the walkers over several calls).  Nothing is allocated:
- * no cudaMalloc, no cudaFree, no allocating library routine.
- * The first call on a device looks up the array's device address with
- * cudaGetSymbolAddress (with that device current); make that first call
- * before any stream capture.  Every call writes all of the array it later
+ * nothing (split the walkers over several calls); nwalkers above 65535
+ * returns AFQMC_EINVAL, also before anything is launched.  Nothing is
+ * allocated: no cudaMalloc, no cudaFree, no allocating library routine.
+ * Every call made outside stream capture looks up the array's device address
+ * on the current device with cudaGetSymbolAddress (the host-side name of the
+ * array is not a device address); a call made while `stream` is being
+ * captured reuses the address the last uncaptured call on that device found,
+ * so make at least one call on a device before capturing one (otherwise
+ * AFQMC_ESTATE), and after a cudaDeviceReset() make one again before
+ * capturing.  Every call writes all of the array it later
  * reads, so nothing needs clearing, but all calls share the one array: calls
  * that may overlap on the GPU (different streams, or different host threads
  * on the same device) race and must be serialised by the caller.

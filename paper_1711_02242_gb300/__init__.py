@@ -20,9 +20,13 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libafqmc.so")
 
 AFQMC_OK = 0
+# the mixed paths keep S^-1, log det, overlap ratios, weights and
+# Gram-Schmidt in float64 and form Theta = Phi S^-1 in FP32
 AFQMC_FP64, AFQMC_MIXED_TF32, AFQMC_MIXED_BF16 = 0, 1, 2
 # the mixed paths with S^-1, Theta and Gram-Schmidt in FP32 (opt-in)
 AFQMC_MIXED_TF32_F32LU, AFQMC_MIXED_BF16_F32LU = 3, 4
+# the mixed paths with Theta = Phi S^-1 also in float64
+AFQMC_MIXED_TF32_F64THETA, AFQMC_MIXED_BF16_F64THETA = 5, 6
 AFQMC_PHASELESS, AFQMC_FREE = 0, 1
 STATUS = {0: "OK", -1: "EINVAL", -2: "ENOSPC", -3: "ENONFINITE", -4: "ECUDA",
           -5: "ETIMEOUT", -6: "ESTATE", -7: "EUNSUPPORTED"}

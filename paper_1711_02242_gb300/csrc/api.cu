@@ -45,8 +45,10 @@ size_t plan(const afqmc_params& p, Bufs* b, char* base) {
   const bool mixed = p.precision != AFQMC_FP64;
   size_t nchunk = (G + exchange_chunk(p.N, p.nchol) - 1) / exchange_chunk(p.N, p.nchol);
   if (mixed) nchunk = G;  // the tensor-core exchange leaves one partial per vector
-  const size_t lo =
-      (p.precision == AFQMC_MIXED_BF16 || p.precision == AFQMC_MIXED_BF16_F32LU) ? 2 : 4;
+  const size_t lo = (p.precision == AFQMC_MIXED_BF16 || p.precision == AFQMC_MIXED_BF16_F32LU ||
+                     p.precision == AFQMC_MIXED_BF16_F64THETA)
+                        ? 2
+                        : 4;
   // pitches: 16-byte rows for TMA; Mp a multiple of 16 so that 16-column
   // epilogue chunks of the flattened (p, q) index never straddle rows
   const size_t Gp = (G + 7) / 8 * 8, Mp = (M + 15) / 16 * 16, Pp = (P + 3) / 4 * 4;
@@ -117,6 +119,8 @@ size_t plan(const afqmc_params& p, Bufs* b, char* base) {
   }
   b->mixed = mixed;
   b->f32lu = p.precision == AFQMC_MIXED_TF32_F32LU || p.precision == AFQMC_MIXED_BF16_F32LU;
+  b->theta32 = mixed && p.precision != AFQMC_MIXED_TF32_F64THETA &&
+               p.precision != AFQMC_MIXED_BF16_F64THETA;
   b->lo_kind = mixed ? (lo == 2 ? LO_BF16 : LO_TF32) : LO_NONE;
   b->lo_bytes = (int)lo;
   b->Gp = (int)Gp;
@@ -182,6 +186,11 @@ static int check_params(const afqmc_params* p) {
     set_error("N=%d: at most 64 electrons per spin are supported", p->N);
     return AFQMC_EUNSUPPORTED;
   }
+  if (p->nwalkers > 65535) {
+    // per-walker kernels put the walker index on the grid's y dimension
+    set_error("nwalkers=%d: at most 65535 walkers per state are supported", p->nwalkers);
+    return AFQMC_EUNSUPPORTED;
+  }
   if (!(p->dt > 0.0) || !std::isfinite(p->dt)) {
     set_error("dt must be positive and finite");
     return AFQMC_EINVAL;
@@ -199,7 +208,7 @@ static int check_params(const afqmc_params* p) {
     set_error("the comb needs real weights: pc_period must be 0 for free projection");
     return AFQMC_EINVAL;
   }
-  if (p->precision < AFQMC_FP64 || p->precision > AFQMC_MIXED_BF16_F32LU) {
+  if (p->precision < AFQMC_FP64 || p->precision > AFQMC_MIXED_BF16_F64THETA) {
     set_error("precision %d is not available in this build", p->precision);
     return AFQMC_EUNSUPPORTED;
   }
@@ -263,8 +272,10 @@ int overlap_update(afqmc_state* s, bool into_ld, bool timed) {
     ov.th_lo = b.th_lo;
     ov.lo_kind = b.lo_kind;
     ov.Mp = b.Mp;
-    // FP32 elimination and Theta when asked for (else float64 with the copy)
+    // FP32 elimination when asked for (_F32LU), else float64; the product
+    // Theta = Phi S^-1 in FP32 unless the precision keeps it in float64
     if (b.f32lu) ov.Sinv32 = reinterpret_cast<float2*>(b.Sinv);
+    ov.theta32 = b.theta32 ? 1 : 0;
   }
   if (timed) prof_begin(s, AFQMC_PH_OVERLAP);
   AFQ_TRY(launch_overlap(ov, s->st));

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 
@@ -45,6 +46,21 @@ extern int64_t g_launches;
   } while (0)
 
 static inline unsigned cdiv(size_t a, size_t b) { return (unsigned)((a + b - 1) / b); }
+
+// Raise a kernel's dynamic shared-memory limit on the current device, once per
+// device: the attribute belongs to each device's context, so a process that
+// drives several GPUs sets it on each (bit d of `done` = set on device d).
+// A cudaDeviceReset() drops it with the rest of that device's context.
+template <typename F>
+inline int smem_attr_once(F* kern, int bytes, std::atomic<unsigned long long>& done) {
+  int dev = 0;
+  AFQ_CUDA(cudaGetDevice(&dev));
+  const unsigned long long bit = dev >= 0 && dev < 64 ? (1ull << dev) : 0ull;
+  if (bit && (done.load(std::memory_order_acquire) & bit)) return AFQMC_OK;
+  AFQ_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  done.fetch_or(bit, std::memory_order_release);
+  return AFQMC_OK;
+}
 
 // -------------------------------------------------------------- Philox -----
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): 10 rounds of

@@ -793,11 +793,8 @@ static int launch_tc_persistent(const TcGemm& g, const Epi& epi, int gx, int gy,
   else
     AFQ_TRY(make_tmap(&tb, g.B, eb, g.n, g.k, g.ldb, BN));
   auto kern = tc::k_tc_gemm_persistent<BN, STAGES, TF32, Epi>;
-  static bool attr = false;
-  if (!attr) {
-    AFQ_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kTotal));
-    attr = true;
-  }
+  static std::atomic<unsigned long long> attr{0};
+  AFQ_TRY(smem_attr_once(kern, kTotal, attr));
   const long ntiles = (long)gx * gy;
   if (ntiles <= 0) return AFQMC_OK;
   if (ntiles > 0x7fffffffL) {

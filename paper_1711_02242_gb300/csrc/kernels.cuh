@@ -132,6 +132,7 @@ struct OverlapArgs {
   int unit_trial = 0;  // VTt = [I_N | 0]: S is the top block of Phi, Theta's top rows I
   double2* Sinv = nullptr;  // [W][N][N] scratch: S^-1 of live walkers
   float2* Sinv32 = nullptr;  // _F32LU precisions: FP32 elimination, S^-1 here and FP32 Theta
+  int theta32 = 0;  // FP32 product Theta = Phi S^-1 from the float64 S^-1 (Sinv32 unset)
 };
 // S^-1 and log det (k_overlap), then Theta (k_theta_rows)
 int launch_overlap(const OverlapArgs& a, cudaStream_t st);

@@ -23,20 +23,31 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 double* g_scratch_ptr[kMaxDevices] = {nullptr};
 
-// Device address of the scratch array on the current device, looked up once
-// per device (the host-side symbol is only a stand-in, never a device address).
-int scratch_on_current_device(double** out) {
+// Device address of the scratch array on the current device.  The host-side
+// symbol is only a stand-in, never a device address, so the address comes
+// from cudaGetSymbolAddress with the device current.  It is looked up again on
+// every call made outside stream capture (a cudaDeviceReset() or a new
+// primary context reloads the module at a new address, so a remembered one
+// could dangle); during capture the address remembered from the last call
+// outside capture on this device is used, and if there is none the call fails.
+int scratch_on_current_device(cudaStream_t st, double** out) {
   int dev = -1;
   AFQ_CUDA(cudaGetDevice(&dev));
   if (dev < 0 || dev >= kMaxDevices) {
     set_error("device ordinal %d out of range", dev);
     return AFQMC_EINVAL;
   }
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  AFQ_CUDA(cudaStreamIsCapturing(st, &cs));
   std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_scratch_ptr[dev]) {
+  if (cs == cudaStreamCaptureStatusNone) {
     void* p = nullptr;
     AFQ_CUDA(cudaGetSymbolAddress(&p, g_eloc_scratch));
     g_scratch_ptr[dev] = static_cast<double*>(p);
+  } else if (!g_scratch_ptr[dev]) {
+    set_error("afqmc_local_energies_noalloc: the first call on a device must come before any "
+              "stream capture (it looks up the scratch array's device address)");
+    return AFQMC_ESTATE;
   }
   *out = g_scratch_ptr[dev];
   return AFQMC_OK;
@@ -60,6 +71,12 @@ extern "C" AFQMC_API int afqmc_local_energies_noalloc(int32_t M, int32_t N, int3
     set_error("afqmc_local_energies_noalloc: N=%d above 64", N);
     return AFQMC_EUNSUPPORTED;
   }
+  if (nwalkers > 65535) {
+    // the exchange kernel's grid has one row of blocks per walker
+    set_error("afqmc_local_energies_noalloc: nwalkers=%d above 65535 (split the walkers over "
+              "several calls)", nwalkers);
+    return AFQMC_EINVAL;
+  }
   const int gc = exchange_chunk(N, nchol);
   const int nchunk = (nchol + gc - 1) / gc;
   const long need = (long)nwalkers * 2 * nchol + (long)nwalkers * nchunk * 2;
@@ -69,11 +86,11 @@ extern "C" AFQMC_API int afqmc_local_energies_noalloc(int32_t M, int32_t N, int3
               need, kScratchDoubles);
     return AFQMC_ENOSPC;
   }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
   double* scratch = nullptr;
-  AFQ_TRY(scratch_on_current_device(&scratch));
+  AFQ_TRY(scratch_on_current_device(st, &scratch));
   double* t = scratch;                            // [W][2][G], fully written below
   double* part = scratch + (long)nwalkers * 2 * nchol;  // [W][nchunk][2], fully written
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
   GemmF64 g;
   g.m = 2 * nwalkers;
   g.n = nchol;

@@ -30,6 +30,7 @@ struct Bufs {
   // mixed path: BF16 / TF32 operand copies and FP32 step buffers
   bool mixed = false;
   bool f32lu = false;  // S^-1, Theta and Gram-Schmidt in FP32 (the _F32LU precisions)
+  bool theta32 = false;  // Theta = Phi S^-1 in FP32 (every mixed precision but _F64THETA)
   int lo_kind = 0, lo_bytes = 0, Gp = 0, Mp = 0;
   long Pp = 0;
   // LbT_lo: Cholesky vectors transposed over the upper 16 x 16 blocks (P <= Q)

@@ -363,20 +363,12 @@ int tc_taylor_series(const void* V, const void* T0, float* S, long lds, int lo_k
   AFQ_TRY(make_tmap_nd(&tt, T0, eb, 4, tdims, tstr, tbox));
   const int grid = W < tc_sm_count() ? W : tc_sm_count();
   if (tf32) {
-    static bool attr = false;
-    if (!attr) {
-      AFQ_CUDA(cudaFuncSetAttribute(tc::k_taylor_series<true>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax));
-      attr = true;
-    }
+    static std::atomic<unsigned long long> attr{0};
+    AFQ_TRY(smem_attr_once(tc::k_taylor_series<true>, kSmemMax, attr));
     AFQ_LAUNCH(tc::k_taylor_series<true>, grid, tc::kSeriesThreads, smem, st, tv, tt, sa, err);
   } else {
-    static bool attr = false;
-    if (!attr) {
-      AFQ_CUDA(cudaFuncSetAttribute(tc::k_taylor_series<false>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax));
-      attr = true;
-    }
+    static std::atomic<unsigned long long> attr{0};
+    AFQ_TRY(smem_attr_once(tc::k_taylor_series<false>, kSmemMax, attr));
     AFQ_LAUNCH(tc::k_taylor_series<false>, grid, tc::kSeriesThreads, smem, st, tv, tt, sa, err);
   }
   return AFQMC_OK;

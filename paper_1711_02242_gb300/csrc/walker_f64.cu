@@ -521,11 +521,12 @@ __global__ void __launch_bounds__(TH_T) k_theta_rows(OverlapArgs a) {
   }
 }
 
-// _F32LU mixed precisions: the same rows with FP32 arithmetic.  Theta only feeds the
+// Mixed precisions: the same rows with FP32 arithmetic.  Theta only feeds the
 // BF16/TF32 contractions (force bias, exchange) and the one-body energy
 // there, so FP32 products (S^-1 and Phi rounded to FP32) lose nothing those do
 // not, and this GPU's FP32 pipe is ~60x its FP64 one: the kernel becomes bound
-// by the traffic of Phi and Theta.  The block's TH_P columns of Phi are staged
+// by the traffic of Phi and Theta.  S^-1 comes from the float64 elimination
+// (rounded once to FP32 here), or from the FP32 one of the _F32LU precisions.  The block's TH_P columns of Phi are staged
 // in shared memory as FP32 (all loads in flight at once, converted once);
 // one work item = row p and IB orbitals i, IB = N / ceil(N / 16) rounded up
 // (guarded tail of at most ceil(N / 16) - 1 lanes); S^-1 reads are warp-wide
@@ -536,8 +537,16 @@ __global__ void __launch_bounds__(TH_T) k_theta_rows_f32(OverlapArgs a) {
   const int w = blockIdx.y, N = a.N, M = a.M;
   if ((a.wt && !walker_alive(a.wt, w)) || !(a.logdet[2L * w] > -INFINITY)) return;
   float* ph = reinterpret_cast<float*>(th_sinv32 + N * N);
-  const float2* si = a.Sinv32 + (long)w * N * N;
-  for (int idx = threadIdx.x; idx < N * N; idx += TH_T) th_sinv32[idx] = si[idx];
+  if (a.Sinv32) {
+    const float2* si = a.Sinv32 + (long)w * N * N;
+    for (int idx = threadIdx.x; idx < N * N; idx += TH_T) th_sinv32[idx] = si[idx];
+  } else {
+    const double2* si = a.Sinv + (long)w * N * N;
+    for (int idx = threadIdx.x; idx < N * N; idx += TH_T) {
+      const double2 v = si[idx];
+      th_sinv32[idx] = make_float2(f64_to_f32(v.x), f64_to_f32(v.y));
+    }
+  }
   const double* phw = a.phiT + (long)w * 2 * N * M;
   const int pb = blockIdx.x * TH_P, pe = min(M, pb + TH_P), np = pe - pb;
 #pragma unroll 4
@@ -585,12 +594,8 @@ __global__ void __launch_bounds__(TH_T) k_theta_rows_f32(OverlapArgs a) {
 
 template <int IB>
 static int launch_theta_f32(const OverlapArgs& a, cudaStream_t st) {
-  static bool attr = false;
-  if (!attr) {
-    AFQ_CUDA(cudaFuncSetAttribute(k_theta_rows_f32<IB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  100 * 1024));
-    attr = true;
-  }
+  static std::atomic<unsigned long long> attr{0};
+  AFQ_TRY(smem_attr_once(k_theta_rows_f32<IB>, 100 * 1024, attr));
   dim3 grid(cdiv(a.M, TH_P), a.W);
   const size_t smem = sizeof(float2) * (size_t)a.N * a.N + sizeof(float) * 2 * a.N * TH_P;
   AFQ_LAUNCH(k_theta_rows_f32<IB>, grid, TH_T, smem, st, a);
@@ -599,13 +604,9 @@ static int launch_theta_f32(const OverlapArgs& a, cudaStream_t st) {
 
 template <int IB>
 static int launch_theta_rows(const OverlapArgs& a, cudaStream_t st) {
-  static bool attr = false;
+  static std::atomic<unsigned long long> attr{0};
   const size_t smem = sizeof(double2) * (size_t)a.N * a.N;
-  if (!attr) {
-    AFQ_CUDA(cudaFuncSetAttribute(k_theta_rows<IB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  100 * 1024));
-    attr = true;
-  }
+  AFQ_TRY(smem_attr_once(k_theta_rows<IB>, 100 * 1024, attr));
   dim3 grid(cdiv(a.M, TH_P), a.W);
   AFQ_LAUNCH(k_theta_rows<IB>, grid, TH_T, smem, st, a);
   return AFQMC_OK;
@@ -621,19 +622,11 @@ int launch_overlap(const OverlapArgs& a, cudaStream_t st) {
     set_error("overlap: N=%d too large", a.N);
     return AFQMC_EUNSUPPORTED;
   }
-  static bool attr = false;
-  if (!attr) {
-    AFQ_CUDA(cudaFuncSetAttribute(k_overlap<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  200 * 1024));
-    attr = true;
-  }
+  static std::atomic<unsigned long long> attr{0};
+  AFQ_TRY(smem_attr_once(k_overlap<double>, 200 * 1024, attr));
   if (a.Sinv32) {
-    static bool attr32 = false;
-    if (!attr32) {
-      AFQ_CUDA(cudaFuncSetAttribute(k_overlap<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    200 * 1024));
-      attr32 = true;
-    }
+    static std::atomic<unsigned long long> attr32{0};
+    AFQ_TRY(smem_attr_once(k_overlap<float>, 200 * 1024, attr32));
     AFQ_LAUNCH(k_overlap<float>, a.W, OV_T, smem / 2, st, a);
     return AFQMC_OK;
   }
@@ -642,7 +635,7 @@ int launch_overlap(const OverlapArgs& a, cudaStream_t st) {
 }
 
 int launch_theta(const OverlapArgs& a, cudaStream_t st) {
-  if (a.Sinv32) {
+  if (a.Sinv32 || a.theta32) {
     if (!a.th_lo) {
       set_error("theta: the FP32 rows need the operand copy");
       return AFQMC_EINVAL;
@@ -897,12 +890,8 @@ __global__ void __launch_bounds__(256) k_mgs_f32(MgsArgs a) {
 int launch_mgs(const MgsArgs& a, cudaStream_t st) {
   const size_t smem32 = sizeof(float2) * (size_t)a.M * a.N;
   if (a.f32 && smem32 <= 200 * 1024) {
-    static bool attr32 = false;
-    if (!attr32) {
-      AFQ_CUDA(cudaFuncSetAttribute(k_mgs_f32, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    200 * 1024));
-      attr32 = true;
-    }
+    static std::atomic<unsigned long long> attr32{0};
+    AFQ_TRY(smem_attr_once(k_mgs_f32, 200 * 1024, attr32));
     AFQ_LAUNCH(k_mgs_f32, a.W, 256, smem32, st, a);
     return AFQMC_OK;
   }
@@ -918,11 +907,8 @@ int launch_mgs(const MgsArgs& a, cudaStream_t st) {
     set_error("mgs: M=%d too large", a.M);
     return AFQMC_EUNSUPPORTED;
   }
-  static bool attr = false;
-  if (!attr) {
-    AFQ_CUDA(cudaFuncSetAttribute(k_mgs, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    attr = true;
-  }
+  static std::atomic<unsigned long long> attr{0};
+  AFQ_TRY(smem_attr_once(k_mgs, 200 * 1024, attr));
   AFQ_LAUNCH(k_mgs, a.W, 256, smem, st, a);
   return AFQMC_OK;
 }
@@ -1025,12 +1011,8 @@ int launch_exchange(const ExchArgs& a, cudaStream_t st) {
   size_t d1 = (size_t)a.gc * a.N * EX_P + 2ull * a.N * (EX_P + 1);
   size_t d2 = (size_t)a.gc * 2 * a.N * a.N;
   size_t smem = (d1 > d2 ? d1 : d2) * sizeof(double);
-  static bool attr = false;
-  if (!attr) {
-    AFQ_CUDA(cudaFuncSetAttribute(k_exchange, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  160 * 1024));
-    attr = true;
-  }
+  static std::atomic<unsigned long long> attr{0};
+  AFQ_TRY(smem_attr_once(k_exchange, 160 * 1024, attr));
   if (smem > 160 * 1024) {
     set_error("exchange: shared memory %zu too large", smem);
     return AFQMC_EUNSUPPORTED;

@@ -87,7 +87,17 @@ def test_rooflines_from_phase_times():
     assert qr["bound"] == "hbm" and qr["unit"] == "GB/s" and qr["kernel"] == "k_mgs_f32"
     assert abs(qr["achieved"] - bench.bytes_per_walker(w, "bf16-f32lu")["qr"] * 512 / 1.3e-3 / 1e9) < 1e-9
     assert abs(qr["frac"] - qr["achieved"] / pk["hbm_gbs"]) < 1e-12
-    assert set(bench.PRECISIONS) == {"fp64", "tf32", "bf16", "tf32-f32lu", "bf16-f32lu"}
+    assert set(bench.PRECISIONS) == {"fp64", "tf32", "bf16", "tf32-f32lu", "bf16-f32lu",
+                                     "tf32-f64theta", "bf16-f64theta"}
+    # Theta = Phi S^-1: FP32 from the float64 S^-1 on the default mixed path
+    # (against HBM: it reads the float64 S^-1), float64 on -f64theta
+    ph_t = dict(ph, theta={"ms": 0.5, "count": 10, "kernels": 10})
+    th = [r for r in bench.rooflines(w, ph_t, "bf16", K) if r["phase"] == "theta"][0]
+    assert th["bound"] == "hbm" and th["kernel"] == "k_theta_rows_f32"
+    b = bench.bytes_per_walker(w, "bf16")["theta"]
+    assert b == 2 * 25 * 300 * 8 * 2 + 25 * 25 * 16 + 2 * 25 * 304 * 2
+    th64 = [r for r in bench.rooflines(w, ph_t, "bf16-f64theta", K) if r["phase"] == "theta"][0]
+    assert th64["bound"] == "alu" and th64["kernel"] == "k_theta_rows"
     assert abs(sum(r["share_of_step"] for r in roofs) - 1.0) < 1e-12
     # a recorded traffic figure counts only for the source it was taken from
     saved = dict(bench.TRAFFIC)

@@ -42,7 +42,7 @@ def test_bounded_wait_times_out_and_context_survives(env):
     # a set flag ends the wait at once and leaves the status alone
     flag.fill_(1)
     status.zero_()
-    pkg._check(pkg.lib().afqmc_wait_flag(ctypes.c_void_p(flag.data_ptr()), 1 << 30,
+    pkg._check(pkg.lib().afqmc_wait_flag(ctypes.c_void_p(flag.data_ptr()), 1 << 20,
                                          ctypes.c_void_p(status.data_ptr()), ctypes.c_void_p(st)))
     torch.cuda.synchronize()
     assert int(status.item()) == 0

@@ -126,17 +126,11 @@ def test_mixed_weights_carry_no_common_drift(pkg, prec, tol_bias, tol_phi):
     assert np.max(d / n) < tol_phi
 
 
-@pytest.mark.parametrize("prec,prec32,tol_phi", [(2, 4, 1e-2), (1, 3, 3e-3)])
-def test_f32lu_precisions_close_to_float64_lu(pkg, prec, prec32, tol_phi):
-    """The opt-in _F32LU precisions (the elimination, Theta and Gram-Schmidt
-    in FP32; log det sums, overlap ratios and weights in float64) against the
-    same mixed precision with those steps in float64: seven steps on
-    identical fields differ by FP32 rounding fed through the BF16/TF32
-    contractions, with no common weight drift."""
+def _seven_steps(pkg, precisions):
     h1, L, _ = workloads.hamiltonian(24, 120, 6100, l_scale=workloads.l_amplitude(24, 120))
     C, _, _, _ = scf.rhf(h1, L, 4)
     out = []
-    for precision in (prec, prec32):
+    for precision in precisions:
         p = pkg.default_params(24, 4, 120, 64, dt=0.01, seed=4, qr_period=5, energy_period=1,
                                precision=precision)
         run = pkg.AfqmcRun(h1, L, C, p)
@@ -145,7 +139,17 @@ def test_f32lu_precisions_close_to_float64_lu(pkg, prec, prec32, tol_phi):
         out.append((e0, run.get_walkers(), run.energy_log()))
         assert run.info().status == 0
         run.close()
-    (e0a, (pa, wa, _), la), (e0b, (pb, wb, _), lb) = out
+    return out
+
+
+@pytest.mark.parametrize("base,prec32,tol_phi", [(6, 4, 1e-2), (5, 3, 3e-3)])
+def test_f32lu_precisions_close_to_float64_lu(pkg, base, prec32, tol_phi):
+    """The opt-in _F32LU precisions (the elimination, Theta and Gram-Schmidt
+    in FP32; log det sums, overlap ratios and weights in float64) against the
+    same mixed precision with those steps in float64: seven steps on
+    identical fields differ by FP32 rounding fed through the BF16/TF32
+    contractions, with no common weight drift."""
+    (e0a, (pa, wa, _), la), (e0b, (pb, wb, _), lb) = _seven_steps(pkg, (base, prec32))
     assert np.max(np.abs(e0b - e0a) / np.abs(e0a)) < 1e-5
     alive = np.nonzero((wa != 0) & (wb != 0))[0]
     assert alive.size > 32
@@ -154,3 +158,23 @@ def test_f32lu_precisions_close_to_float64_lu(pkg, prec, prec32, tol_phi):
     assert np.max(d / n) < tol_phi
     assert abs(np.mean((wb[alive] / wa[alive]).real) - 1) < 2e-3
     assert np.max(np.abs(lb[:, 1] - la[:, 1]) / np.abs(la[:, 1])) < 2e-4
+
+
+@pytest.mark.parametrize("base,prec,tol_phi", [(6, 2, 2e-3), (5, 1, 5e-4)])
+def test_fp32_theta_close_to_float64_theta(pkg, base, prec, tol_phi):
+    """The default mixed precisions form Theta = Phi S^-1 in FP32 from the
+    float64 S^-1 (the elimination, log det, overlap ratios, weights and
+    Gram-Schmidt stay float64): seven steps on identical fields against the
+    same precision with Theta formed in float64.  Theta only reaches the
+    BF16/TF32 operands and the one-body trace, so the walks agree to far
+    below the operand rounding, the weights carry no common drift, and the
+    overlaps (float64 on both sides) agree to the walkers' difference."""
+    (e0a, (pa, wa, la_ov), la), (e0b, (pb, wb, lb_ov), lb) = _seven_steps(pkg, (base, prec))
+    assert np.max(np.abs(e0b - e0a) / np.abs(e0a)) < 1e-7
+    alive = np.nonzero((wa != 0) & (wb != 0))[0]
+    assert alive.size > 32
+    d = np.linalg.norm((pb - pa)[alive].reshape(alive.size, -1), axis=1)
+    n = np.linalg.norm(pa[alive].reshape(alive.size, -1), axis=1)
+    assert np.max(d / n) < tol_phi
+    assert abs(np.mean((wb[alive] / wa[alive]).real) - 1) < 1e-3
+    assert np.max(np.abs(lb[:, 1] - la[:, 1]) / np.abs(la[:, 1])) < 5e-5
