@@ -75,8 +75,12 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # of the source file the kernel was built from and the precisions whose step
 # runs that kernel; a figure whose source has changed since, or that belongs
 # to another kernel at this precision, is reported as null.
+GEMM_KERNEL = "__global__ void __launch_bounds__(64 + 32 * Epi::kWarps, 1)"
 TRAFFIC = {
-    "theta": [{"bytes": (64.265728 + 25.652224) * 1e6, "sha": "d8af088925f6dd017e10c429fdb6a28ef844edf64bdcef66e2f823c786f2631e", "precisions": ("bf16-f32lu",)},
+    "theta": [# k_theta_rows_f32 on the float64 S^-1 (the bf16 default path)
+              {"bytes": (66.846720 + 26.307840) * 1e6, "precisions": ("bf16",),
+               "function": "__global__ void __launch_bounds__(TH_T) k_theta_rows_f32(OverlapArgs a)",
+               "sha": "95b521175a189697f17637210e88c7be80b91f899d89ffb387d05b3e718d9736"},
               # k_theta_rows (float64 Theta of the -f64theta mixed paths): its own
               # text is unchanged since this capture (DRAM 64.5 + 30.3 MB per launch)
               {"bytes": (64.544512 + 30.260480) * 1e6, "precisions": ("bf16-f64theta",),
@@ -84,9 +88,17 @@ TRAFFIC = {
                "sha": "d7ee3083bab22e614e7aa9c51aff2886d255680c62a6454f637a089a17969ae7"}],
     "overlap": {"bytes": (8.234752 + 0.0) * 1e6, "sha": "d8af088925f6dd017e10c429fdb6a28ef844edf64bdcef66e2f823c786f2631e", "precisions": ("bf16-f32lu",)},
     "qr": {"bytes": (61.510144 + 15.014656) * 1e6, "sha": "d8af088925f6dd017e10c429fdb6a28ef844edf64bdcef66e2f823c786f2631e", "precisions": ("bf16-f32lu",)},
-    "taylor": {"bytes": (218.379264 + 19.640064) * 1e6, "sha": "fa71a0b99da9edecc9d2774bf84475b771676eadf05941fcfb17a764107f753e", "precisions": ("bf16", "bf16-f32lu")},
-    "v_assembly": {"bytes": (187.431680 + 145.291776) * 1e6, "sha": "e87b4db7d550e788be37b7c99656929c68c239e53519f64c4229575bbd0b27dd", "precisions": ("bf16", "bf16-f32lu")},
-    "energy": {"bytes": (42.972160 + 0.562688) * 1e6, "sha": "e87b4db7d550e788be37b7c99656929c68c239e53519f64c4229575bbd0b27dd", "precisions": ("bf16", "bf16-f32lu")},
+    # the tensor-core kernels: pinned to the kernel's text (and its epilogue's),
+    # unchanged since these captures (only their host launchers changed)
+    "taylor": {"bytes": (218.379264 + 19.640064) * 1e6, "precisions": ("bf16", "bf16-f32lu", "bf16-f64theta"),
+               "function": "__global__ void __launch_bounds__(kSeriesThreads, 1)",
+               "sha": "0bd7f7fc981d513aebf1f41e918de5a243d5e63f2a01728f454f566a353c5b4b"},
+    "v_assembly": {"bytes": (187.431680 + 145.291776) * 1e6, "precisions": ("bf16", "bf16-f32lu", "bf16-f64theta"),
+                   "function": [GEMM_KERNEL, "struct EpiV {"],
+                   "sha": "63a321613a463e24104a01cc24fe168357d2aad1761c9cf5fd03fcc555f23358"},
+    "energy": {"bytes": (42.972160 + 0.562688) * 1e6, "precisions": ("bf16", "bf16-f32lu", "bf16-f64theta"),
+               "function": [GEMM_KERNEL, "struct EpiExchange {"],
+               "sha": "f831bafcaacbe7e7d559019a2ab9b036f4470a0aa657ef29fa518998f26c7810"},
 }
 
 
@@ -275,15 +287,24 @@ def function_sha(fname, signature):
 
 def traffic_of(phase, src, precision):
     """The recorded DRAM bytes of a phase's kernel at this precision, if its
-    source (the file, or the kernel's own text for entries that name it) is
-    the one the counters were taken from."""
+    source (the file, or the text of the kernel and of the device code it
+    names, for entries that list them) is the one the counters were taken
+    from."""
+    import hashlib
+
     entries = TRAFFIC.get(phase)
     if not entries:
         return None
     for tr in entries if isinstance(entries, list) else [entries]:
         if precision not in tr.get("precisions", ("bf16",)):
             continue
-        sha = function_sha(src, tr["function"]) if "function" in tr else source_sha(src)
+        if "function" in tr:
+            fns = tr["function"] if isinstance(tr["function"], (list, tuple)) else [tr["function"]]
+            shas = [function_sha(src, f) for f in fns]
+            sha = (shas[0] if len(shas) == 1 else
+                   None if None in shas else hashlib.sha256("".join(shas).encode()).hexdigest())
+        else:
+            sha = source_sha(src)
         if tr.get("sha") == sha:
             return tr["bytes"]
     return None
@@ -464,11 +485,14 @@ def run_gpu(args, w: workloads.Workload):
     fp64 = None
     if prec != 0 and rank == 0 and not args.no_fp64_compare:
         fp64 = fp64_compare(w, p, h1, L, C, dev, stream, args.fp64_steps)
+    bias = None
+    if prec != 0 and rank == 0 and not args.no_bias:
+        bias = bias_report(device=dev, stream=stream, c2_inputs=(h1, L, H0, C))
     return dict(ms_total=ms_total, phases=phases, launches=launches, info=info, E=E, wsum=wsum,
                 clocks=clk.summary(), e2e_s=t_e2e, trial_converged=conv, trial_grad=grad,
                 h2d_bytes=h1.nbytes + L.nbytes + C.nbytes, world=ws, rank=rank, warmup=Wm,
                 ms_profiled=ms_profiled, s_energy=s_energy, graph=not args.no_graph,
-                precision_report=prec_rep, fp64=fp64)
+                precision_report=prec_rep, fp64=fp64, bias=bias)
 
 
 def fp64_compare(w, p, h1, L, C, dev, stream, steps):
@@ -566,6 +590,114 @@ def precision_report(w: workloads.Workload, prec: int, h1, L, C, H0, nwalk=32):
     del runs
     torch.cuda.empty_cache()
     return out
+
+
+def bias_runs(w: workloads.Workload, precs, steps, energy_period, device=None, stream=None,
+              h1=None, L=None, C=None, H0=0.0, groups=16):
+    """Energy bias of the mixed precisions against the float64 path on
+    identical Philox fields (same seed, same initial walkers, same step
+    order): `steps` steps, a record every `energy_period`.  Without
+    population control the walkers are independent, so the population is cut
+    into `groups` groups of consecutive walkers, each an independent sample of
+    the run; per group and record the mixed estimator sum W Re E_loc / sum W
+    (Re E_loc capped as in the walk) is formed from the walkers' weights and
+    local energies read back from the GPU, then
+
+      run        time average over the records of E_mixed - E_fp64, the two
+                 walks' group estimators (the walks separate only by the mixed
+                 path's rounding);
+      estimator  the same for the mixed estimator evaluated on the float64
+                 walk's own walkers and weights (the evaluation's error alone);
+
+    as the mean over groups with its standard error (spread over groups), in
+    mHa."""
+    import torch
+
+    import paper_1711_02242_gb300 as pkg
+
+    if h1 is None:
+        h1, L, H0, C, _, _ = make_inputs(w)
+
+    def mk(prec):
+        p = pkg.default_params(w.M, w.N, w.nchol, w.nwalkers, dt=w.dt, seed=w.seed, H0=H0,
+                               qr_period=w.qr_period, energy_period=0,
+                               taylor_order=w.taylor_order, precision=prec)
+        return pkg.AfqmcRun(h1, L, C, p, device=device or "cuda:0", stream=stream)
+
+    nrec = steps // energy_period
+    r64 = mk(0)
+    mixed = {pr: mk(PRECISIONS[pr]) for pr in precs}
+    probe = {pr: mk(PRECISIONS[pr]) for pr in precs}
+    half = math.sqrt(2.0 / w.dt)  # the estimator's cap, C = 2 (Eq. cap)
+    gidx = np.array_split(np.arange(w.nwalkers), groups)
+
+    def group_estimates(wt, el, e_t):
+        er = np.clip(el.real, e_t - half, e_t + half)
+        wr = wt.real
+        return np.array([np.sum(wr[g] * er[g]) / np.sum(wr[g]) if np.sum(wr[g]) > 0 else np.nan
+                         for g in gidx])
+
+    e_t64 = r64.info().E_T
+    e_t = {pr: r.info().E_T for pr, r in mixed.items()}
+    g64, gmx, gpr = [], {pr: [] for pr in precs}, {pr: [] for pr in precs}
+    for _ in range(nrec):
+        r64.propagate(energy_period)
+        wt64, el64 = r64.weights(), r64.local_energies()
+        g64.append(group_estimates(wt64, el64, e_t64))
+        for pr, r in mixed.items():
+            r.propagate(energy_period)
+            gmx[pr].append(group_estimates(r.weights(), r.local_energies(), e_t[pr]))
+        phi, _, _ = r64.get_walkers()
+        for pr, r in probe.items():
+            r.set_walkers(phi, wt64)
+            gpr[pr].append(group_estimates(wt64, r.local_energies(), e_t[pr]))
+    g64 = np.array(g64)  # [records][groups]
+    out = {}
+    for pr in precs:
+        d_run = 1e3 * np.nanmean(np.array(gmx[pr]) - g64, axis=0)  # per group, time-averaged
+        d_est = 1e3 * np.nanmean(np.array(gpr[pr]) - g64, axis=0)
+        ok = np.isfinite(d_run) & np.isfinite(d_est)
+        n = int(np.count_nonzero(ok))
+        out[pr] = {"bias_run_mHa": float(np.mean(d_run[ok])),
+                   "se_run_mHa": float(np.std(d_run[ok], ddof=1) / math.sqrt(n)),
+                   "bias_estimator_mHa": float(np.mean(d_est[ok])),
+                   "se_estimator_mHa": float(np.std(d_est[ok], ddof=1) / math.sqrt(n)),
+                   "dE_trial_mHa": 1e3 * (e_t[pr] - e_t64), "groups_used": n,
+                   "status": int(mixed[pr].info().status)}
+    res = {"steps": steps, "energy_period": energy_period, "records": nrec,
+           "walkers": w.nwalkers, "groups": groups,
+           "E_fp64_mean_Ha": float(np.nanmean(g64)),
+           "alive_fp64_end": int(r64.info().alive), "precisions": out}
+    for r in [r64, *mixed.values(), *probe.values()]:
+        r.close()
+    del r64, mixed, probe
+    torch.cuda.empty_cache()
+    return res
+
+
+# workload: (mixed precisions, steps, energy period, walker groups)
+BIAS_CASES = {"c0": (("bf16", "tf32"), 40, 2, 8), "c1": (("tf32", "bf16"), 100, 5, 16),
+              "c2": (("bf16", "tf32"), 100, 5, 16)}
+
+
+def bias_report(device=None, stream=None, c2_inputs=None):
+    """bias_runs for the three single-system workloads (the M=12 one in both
+    mixed precisions, M=100 in TF32 and BF16, M=300 in BF16 and TF32)."""
+    rep = {}
+    for name, (precs, steps, ep, ng) in BIAS_CASES.items():
+        w = workloads.config(name)
+        kw = {}
+        if name == "c2" and c2_inputs is not None:
+            kw = dict(zip(("h1", "L", "H0", "C"), c2_inputs))
+        t0 = time.perf_counter()
+        rep[name] = bias_runs(w, precs, steps, ep, device=device, stream=stream, groups=ng, **kw)
+        rep[name]["seconds"] = time.perf_counter() - t0
+    rep["note"] = ("mixed minus float64 on identical Philox fields (same seed and initial "
+                   "walkers), no population control: 'run' compares the two walks' mixed "
+                   "estimators, 'estimator' evaluates the mixed estimator on the float64 "
+                   "walk's walkers and weights; time averages over the records per group of "
+                   "walkers, mean and standard error over the independent groups")
+    return rep
 
 
 def cpu_sample(w: workloads.Workload, n_walkers=32, n_steps=3):
@@ -920,7 +1052,7 @@ def dataclasses_replace(r):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", default="c2", choices=["c2", "batched", "serve", "mcd"],
+    ap.add_argument("--workload", default="c2", choices=["c2", "batched", "serve", "mcd", "bias"],
                     help="c2: the M=300 walker-steps/s line; batched / serve: the grouped and "
                          "served forms; mcd: the modified Cholesky decomposition of the "
                          "workload's interaction (their own JSON lines)")
@@ -945,6 +1077,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end pass")
     ap.add_argument("--no-graph", action="store_true", help="launch kernels one by one")
     ap.add_argument("--no-precision-report", action="store_true")
+    ap.add_argument("--no-bias", action="store_true",
+                    help="skip the run-level bias of the mixed precisions against float64")
     ap.add_argument("--ref-walkers", type=int, default=16)
     args = ap.parse_args()
     if args.warmup < 3:
@@ -955,6 +1089,13 @@ def main():
         return run_serve(args)
     if args.workload == "mcd":
         return run_mcd(args)
+    if args.workload == "bias":
+        from paper_1711_02242_gb300 import build as b
+
+        b.build()
+        print(json.dumps({"metric": "mixed-precision energy bias vs float64, mHa",
+                          "bias_vs_fp64": bias_report()}))
+        return 0
     w = workloads.config(args.config)
     if args.impl == "reference":
         return run_reference(args, w)
@@ -1005,6 +1146,8 @@ def main():
         line["precision_vs_fp64"] = r["precision_report"]
     if r.get("fp64"):
         line["fp64_same_gpu"] = r["fp64"]
+    if r.get("bias"):
+        line["bias_vs_fp64"] = r["bias"]
     if N == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_sample(w)
     print(json.dumps(line))

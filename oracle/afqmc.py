@@ -13,6 +13,12 @@ follows the paper's order of operations.  Notation (Motta & Zhang 2017):
   matrix phi because the trial is RHF and B(x) is spin independent (the
   one-body operators v_g of Sec. 2.3 act identically on both spins), so one
   block is propagated and every spin sum is a factor 2.
+  Two spin blocks (a trial with different spin-up and spin-down orbitals,
+  N_up != N_dn allowed; Theorem 1.1 takes the product over sigma): phi holds
+  the N_up spin-up columns followed by the N_dn spin-down ones, B(x) acts on
+  all of them alike, and every determinant, inverse, Gram-Schmidt sweep and
+  exchange trace is taken per block; each spin sum then has its two terms
+  instead of a factor 2.
   Trial V_T (M x N, real, orthonormal columns); P = V_T V_T^T.
   S = V_T^T phi, Theta = phi S^-1 (Sec. 3.4, Eq. precomputing), the overlap
   <Psi_T|Psi> = det(S)^2 (Theorem 1.1).
@@ -97,18 +103,33 @@ def wrap_phase(a):
 
 
 class Setup:
-    """Once-per-run quantities built from (h, L, V_T) (Secs. 2.3, 2.4, 3.4)."""
+    """Once-per-run quantities built from (h, L, V_T) (Secs. 2.3, 2.4, 3.4).
 
-    def __init__(self, h1, L, trial, H0=0.0, dt=0.005):
+    trial: the RHF orbitals (both spins), or with trial_dn given the spin-up
+    orbitals, trial_dn the spin-down ones (two spin blocks).  `blocks` lists
+    (first column, end column, trial orbitals) per block and `sf` is the
+    number of spins each block stands for (2 closed shell, 1 otherwise)."""
+
+    def __init__(self, h1, L, trial, H0=0.0, dt=0.005, trial_dn=None):
         h1 = np.asarray(h1, np.float64)
         L = np.asarray(L, np.float64)
-        VT = np.asarray(trial, np.float64)
+        Vu = np.asarray(trial, np.float64)
+        if trial_dn is None:
+            VT = Vu
+            self.blocks = [(0, Vu.shape[1], Vu)]
+            self.sf = 2.0
+        else:
+            Vd = np.asarray(trial_dn, np.float64)
+            VT = np.concatenate([Vu, Vd], axis=1)
+            self.blocks = [(0, Vu.shape[1], Vu), (Vu.shape[1], VT.shape[1], Vd)]
+            self.sf = 1.0
         self.h1, self.L, self.VT, self.H0, self.dt = h1, L, VT, float(H0), float(dt)
         self.nchol, self.M, _ = L.shape
         self.N = VT.shape[1]
-        P = VT @ VT.T
-        # c_g = 2 Tr(L_g P): the trial expectation of v_g is i c_g (Sec. 2.4).
-        self.c = 2.0 * np.einsum("gpq,qp->g", L, P)
+        # P = sum over spins of the trial's density V_sigma V_sigma^T
+        P = self.sf * (VT @ VT.T)
+        # c_g = Tr(L_g P): the trial expectation of v_g is i c_g (Sec. 2.4).
+        self.c = np.einsum("gpq,qp->g", L, P)
         # v0 = h - 1/2 sum_g L_g L_g (Eq. mcd1 with v_prrq = sum_g (L_g L_g)_pq)
         v0 = h1 - 0.5 * np.einsum("gpr,grq->pq", L, L)
         # v0' = v0 - sum_g vbar_g v_g = v0 + sum_g c_g L_g (mean-field shift)
@@ -125,34 +146,46 @@ class Setup:
 
 
 def overlap(setup: Setup, phi):
-    """S = V_T^T phi, log <Psi_T|Psi> = 2 log det S, Theta = phi S^-1.
+    """Per spin block S = V_T^T phi, Theta = phi S^-1, and
+    log <Psi_T|Psi> = sum_sigma log det S_sigma (Theorem 1.1): 2 log det S
+    for the closed-shell block.
 
     Returns (logdet (W,) complex with Im wrapped to (-pi, pi], Theta (W,M,N)).
     """
-    S = np.einsum("pi,wpj->wij", setup.VT, phi)
-    sign, logabs = np.linalg.slogdet(S)
-    logdet = 2.0 * logabs + 1j * wrap_phase(2.0 * np.angle(sign))
-    Sinv = np.linalg.inv(S)
-    theta = phi @ Sinv
+    theta = np.empty(phi.shape, np.complex128)
+    la = 0.0
+    ph = 0.0
+    for a, b, V in setup.blocks:
+        S = np.einsum("pi,wpj->wij", V, phi[:, :, a:b])
+        sign, logabs = np.linalg.slogdet(S)
+        la = la + setup.sf * logabs
+        ph = ph + setup.sf * np.angle(sign)
+        theta[:, :, a:b] = phi[:, :, a:b] @ np.linalg.inv(S)
+    logdet = la + 1j * wrap_phase(ph)
     return logdet, theta
 
 
 def force_bias_trace(setup: Setup, theta):
-    """t_g = sum_sigma Tr(Lh_g Theta_sigma) = 2 Tr(Lh_g Theta), shape (W, nchol)."""
-    return 2.0 * np.einsum("giq,wqi->wg", setup.Lh, theta)
+    """t_g = sum_sigma Tr(Lh_g,sigma Theta_sigma), shape (W, nchol): 2 Tr(Lh_g Theta)
+    for the closed-shell block, the sum of the two blocks' traces otherwise."""
+    return setup.sf * np.einsum("giq,wqi->wg", setup.Lh, theta)
 
 
 def local_energy(setup: Setup, theta):
-    """Mixed local energy <Psi_T|H|Psi>/<Psi_T|Psi> per walker (complex)."""
+    """Mixed local energy <Psi_T|H|Psi>/<Psi_T|Psi> per walker (complex):
+    H0 + sum_sigma Tr(hh_sigma Theta_sigma)
+       + 1/2 sum_g [t_g^2 - sum_sigma Tr(T_g,sigma T_g,sigma)],
+    T_g,sigma = Lh_g,sigma Theta_sigma (same-spin blocks only)."""
     W = theta.shape[0]
-    N = setup.N
-    e1 = 2.0 * np.einsum("iq,wqi->w", setup.hh, theta)
+    e1 = setup.sf * np.einsum("iq,wqi->w", setup.hh, theta)
     t = force_bias_trace(setup, theta)
-    Lh2 = setup.Lh.reshape(setup.nchol * N, setup.M)
-    exch = np.empty(W, np.complex128)
-    for w in range(W):
-        T = (Lh2 @ theta[w]).reshape(setup.nchol, N, N)  # T_g = Lh_g Theta
-        exch[w] = np.einsum("gij,gji->", T, T)
+    exch = np.zeros(W, np.complex128)
+    for a, b, _ in setup.blocks:
+        n = b - a
+        Lh2 = setup.Lh[:, a:b, :].reshape(setup.nchol * n, setup.M)
+        for w in range(W):
+            T = (Lh2 @ theta[w][:, a:b]).reshape(setup.nchol, n, n)  # T_g = Lh_g Theta
+            exch[w] += 0.5 * setup.sf * np.einsum("gij,gji->", T, T)
     return setup.H0 + e1 + 0.5 * np.sum(t * t, axis=1) - exch
 
 
@@ -176,18 +209,24 @@ def taylor(V, phi, order):
     return acc
 
 
-def mgs(phi):
+def mgs(phi, blocks=None):
     """Modified Gram-Schmidt over the orbital columns (Sec. 3.4.5).
 
     Column k is orthogonalised against the already-finished columns one at a
     time (each projection uses the partially updated vector), then scaled to
     unit norm: u_k <- u_k - <u'_j|u_k> u'_j for j < k; u'_k = u_k/|u_k|.
+    With spin blocks (a list of (first, end, ...) column ranges) each block is
+    swept on its own: a spin-down orbital is never projected on a spin-up one.
     """
     q = phi.copy()
     N = q.shape[2]
+    starts = [0] * N
+    for blk in blocks or [(0, N)]:
+        for k in range(blk[0], blk[1]):
+            starts[k] = blk[0]
     for k in range(N):
         v = q[:, :, k]
-        for j in range(k):
+        for j in range(starts[k], k):
             proj = np.einsum("wp,wp->w", q[:, :, j].conj(), v)
             v = v - proj[:, None] * q[:, :, j]
         nrm = np.sqrt(np.einsum("wp,wp->w", v.conj(), v).real)
@@ -222,22 +261,29 @@ def comb(weights, u):
     return parent, wtot / n
 
 
-def one_body_density(phi_bra, psi):
+def one_body_density(phi_bra, psi, setup: Setup | None = None):
     """Spin-summed one-body density <Phi|a+_p a_q|Psi>/<Phi|Psi> between
-    closed-shell determinants (both spin blocks the same M x N matrix), per
-    walker: rho_pq = 2 [Psi (Phi^H Psi)^-1 Phi^H]_qp, shape (W, M, M)."""
-    S = np.conj(np.swapaxes(phi_bra, 1, 2)) @ psi  # Phi^H Psi, (W, N, N)
-    G = psi @ np.linalg.inv(S) @ np.conj(np.swapaxes(phi_bra, 1, 2))  # (W, M, M)
-    return 2.0 * np.swapaxes(G, 1, 2)
+    determinants, per walker: rho_pq = sum_sigma [Psi_s (Phi_s^H Psi_s)^-1
+    Phi_s^H]_qp, shape (W, M, M); for closed-shell determinants (both spin
+    blocks the same M x N matrix) 2 [Psi (Phi^H Psi)^-1 Phi^H]_qp."""
+    blocks = setup.blocks if setup is not None else [(0, psi.shape[2], None)]
+    sf = setup.sf if setup is not None else 2.0
+    rho = 0.0
+    for a, b, _ in blocks:
+        bra = np.conj(np.swapaxes(phi_bra[:, :, a:b], 1, 2))
+        S = bra @ psi[:, :, a:b]  # Phi^H Psi, (W, n, n)
+        G = psi[:, :, a:b] @ np.linalg.inv(S) @ bra  # (W, M, M)
+        rho = rho + sf * np.swapaxes(G, 1, 2)
+    return rho
 
 
 class Oracle:
     """A population of walkers stepped by the phaseless AFQMC algorithm."""
 
     def __init__(self, h1, L, trial, nwalkers, params: Params | None = None,
-                 H0=0.0, phi0=None):
+                 H0=0.0, phi0=None, trial_dn=None):
         self.p = p = params or Params()
-        self.setup = Setup(h1, L, trial, H0, p.dt)
+        self.setup = Setup(h1, L, trial, H0, p.dt, trial_dn=trial_dn)
         st = self.setup
         self.W = int(nwalkers)
         if phi0 is None:
@@ -331,7 +377,7 @@ class Oracle:
     def orthonormalize(self):
         alive = np.nonzero(self.weight != 0)[0]
         if alive.size:
-            self.phi[alive] = mgs(self.phi[alive])
+            self.phi[alive] = mgs(self.phi[alive], self.setup.blocks)
             ld, th = overlap(self.setup, self.phi[alive])
             self.logdet[alive] = ld
             self.theta[alive] = th
@@ -376,7 +422,7 @@ class Oracle:
             V = assemble_V(st, -np.conj(x))
             phi = st.Bhalf @ taylor(V, st.Bhalf @ phi, p.taylor_order)
         alive = np.nonzero(self.weight != 0)[0]
-        rho = one_body_density(phi[alive], bp["psi_n"][alive])
+        rho = one_body_density(phi[alive], bp["psi_n"][alive], st)
         w = self.weight[alive]
         wp = w * bp["factor"][alive]
         rho_pres = np.einsum("w,wpq->pq", wp, rho) / np.sum(wp)

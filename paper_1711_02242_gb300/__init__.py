@@ -364,6 +364,12 @@ class AfqmcRun:
         _check(lib().afqmc_get_walkers(self.s, _dptr(phi), _dptr(wt), _dptr(lo)))
         return phi[..., 0] + 1j * phi[..., 1], wt[:, 0] + 1j * wt[:, 1], lo[:, 0] + 1j * lo[:, 1]
 
+    def weights(self):
+        """Walker weights W e^{i theta} (complex), without copying the orbitals."""
+        wt = np.empty((self.p.nwalkers, 2))
+        _check(lib().afqmc_get_walkers(self.s, None, _dptr(wt), None))
+        return wt[:, 0] + 1j * wt[:, 1]
+
     def set_walkers(self, phi, weight):
         W, M, N = self.p.nwalkers, self.p.M, self.p.N
         phi = np.asarray(phi, np.complex128).reshape(W, M, N)
