@@ -32,10 +32,14 @@
  *     Calls that return results to the host synchronise that stream.
  *   - One host thread at a time per state.  Different states are
  *     independent.
- *   - Spin: the walkers are restricted closed shell (N_up = N_dn = N); the
- *     up and down blocks of every walker are the same M x N matrix, because
- *     the trial is RHF and the propagator B(x) is spin independent
- *     (Sec. 2.3: v_g acts identically on both spins).
+ *   - Spin: by default the walkers are restricted closed shell
+ *     (N_up = N_dn = N); the up and down blocks of every walker are the same
+ *     M x N matrix, because the trial is RHF and the propagator B(x) is spin
+ *     independent (Sec. 2.3: v_g acts identically on both spins).  With
+ *     params.Ndn >= 1 a walker has two spin blocks, N_up = N spin-up and
+ *     N_dn = Ndn spin-down orbitals, stored as N + Ndn columns (spin up
+ *     first) that B(x) propagates alike; overlaps (the product over spins of
+ *     Theorem 1.1), Theta, the exchange and Gram-Schmidt are per block.
  */
 #ifndef AFQMC_H
 #define AFQMC_H
@@ -92,7 +96,8 @@ enum {
 
 typedef struct afqmc_params {
   int32_t M;             /* orbitals (orthonormal basis)                       */
-  int32_t N;             /* electrons per spin, N_up = N_dn = N, 1 <= N <= M   */
+  int32_t N;             /* spin-up electrons N_up (and N_dn when Ndn = 0),    */
+                         /* 1 <= N <= M                                         */
   int32_t nchol;         /* Cholesky vectors N_gamma                           */
   int32_t nwalkers;      /* population size N_w                                */
   double dt;             /* imaginary time step, > 0                           */
@@ -120,12 +125,21 @@ typedef struct afqmc_params {
   int32_t ndet;          /* determinants of a multi-determinant trial          */
                          /* (afqmc_init_multidet); 0: the single RHF trial of  */
                          /* afqmc_init                                          */
+  int32_t Ndn;           /* 0: restricted closed shell (one spin block, the    */
+                         /* spin-down orbitals are the spin-up ones, N_dn = N); */
+                         /* >= 1: two spin blocks, N_dn = Ndn spin-down         */
+                         /* electrons with their own trial orbitals (float64,   */
+                         /* N + Ndn <= 64; see afqmc_init)                      */
+  int32_t walker0;       /* global index of this state's first walker: walker  */
+                         /* w draws the fields of walker walker0 + w (one      */
+                         /* population sharded over several states, see        */
+                         /* afqmc_comb_plan); 0 for a state on its own         */
 } afqmc_params;
 
 /* Fill *p with the defaults: dt 0.005, e_shift NaN, H0 0, seed 1,
  * taylor_order 6, qr_period 5, pc_period 0, energy_period 1, FP64,
  * phaseless, ecap_C 2, fb_cap 1, wmax NaN, max_records 4096, use_graph 0, bp_steps 0,
- * ndet 0.  The sizes
+ * ndet 0, Ndn 0 (closed shell), walker0 0.  The sizes
  * (M, N, nchol, nwalkers) are set to 0 and must be filled in. */
 AFQMC_API void afqmc_default_params(afqmc_params* p);
 
@@ -139,21 +153,27 @@ typedef struct afqmc_state afqmc_state; /* opaque */
  *   h1     [M][M]         one-body matrix h_pq (Eq. bo_ham_matel), symmetric
  *   L      [nchol][M][M]  Cholesky vectors, v_pqrs = sum_g L[g]_pr L[g]_qs
  *                         (Sec. 2.3, Eq. chol), each L[g] symmetric
- *   trial  [M][N]         occupied orbitals V_T of the RHF trial, orthonormal
- *                         columns (Sec. 3.4.1)
+ *   trial_up [M][N]       occupied orbitals V_T of the trial, orthonormal
+ *                         columns (Sec. 3.4.1): the RHF orbitals of both
+ *                         spins when params.Ndn = 0, else the spin-up ones
+ *   trial_dn [M][Ndn]     spin-down orbitals, orthonormal columns, when
+ *                         params.Ndn >= 1 (two spin blocks); NULL when
+ *                         params.Ndn = 0
  * all host, row-major float64.  The set-up computes, on the GPU,
- * c_g = 2 Tr(L_g V_T V_T^T) (the mean-field background vbar_g = i c_g,
- * Sec. 2.4), v0' = h - 1/2 sum_g L_g^2 + sum_g c_g L_g, H0' = H0 -
- * 1/2 sum_g c_g^2, B_half = exp(-dt v0'/2), the half-rotated vectors
- * V_T^T L_g and V_T^T h (Eq. precomputing2) and the trial energy E_T, and
- * puts every walker at {V_T, W = 1, theta = 0} (algorithm outline, step 1).
+ * c_g = Tr(L_g P) with P = sum_sigma V_sigma V_sigma^T (the mean-field
+ * background vbar_g = i c_g, Sec. 2.4), v0' = h - 1/2 sum_g L_g^2 +
+ * sum_g c_g L_g, H0' = H0 - 1/2 sum_g c_g^2, B_half = exp(-dt v0'/2), the
+ * half-rotated vectors V_sigma^T L_g and V_sigma^T h (Eq. precomputing2) and
+ * the trial energy E_T, and puts every walker at {V_T, W = 1, theta = 0}
+ * (algorithm outline, step 1).  Two spin blocks run on the float64 path
+ * only, without back-propagation (else AFQMC_EUNSUPPORTED).
  * d_workspace: device buffer of ws_bytes >= afqmc_workspace_size(p).
  * stream: cudaStream_t (as void*) on which every kernel of the state runs.
  * Synchronises the stream.  On failure *out is NULL.
  */
 AFQMC_API int afqmc_init(const afqmc_params* p, const double* h1, const double* L,
-               const double* trial, void* d_workspace, size_t ws_bytes,
-               void* stream, afqmc_state** out);
+                         const double* trial_up, const double* trial_dn, void* d_workspace,
+                         size_t ws_bytes, void* stream, afqmc_state** out);
 
 /*
  * The same with a multi-determinant trial Psi_T = sum_d A_d Psi_d (Sec. 3.4,
@@ -205,11 +225,13 @@ AFQMC_API int afqmc_energy(afqmc_state* s, double* E, double* wsum);
 AFQMC_API int afqmc_local_energies(afqmc_state* s, double* eloc);
 
 /*
- * Copy walkers to the host: phi [nwalkers][M][N][2] (re, im, row-major
- * orbital coefficients), weight [nwalkers][2] (real and imaginary part of
- * the walker weight W e^{i theta}; theta = 0 for phaseless walks), logov
- * [nwalkers][2] (log <Psi_T|Psi> = 2 log det(V_T^T phi) for both spins: real
- * part and phase in (-pi, pi]).  Any pointer may be NULL.
+ * Copy walkers to the host: phi [nwalkers][M][Nt][2] (re, im, row-major
+ * orbital coefficients; Nt = N, or N + Ndn with two spin blocks, spin-up
+ * columns first), weight [nwalkers][2] (real and imaginary part of the
+ * walker weight W e^{i theta}; theta = 0 for phaseless walks), logov
+ * [nwalkers][2] (log <Psi_T|Psi> = 2 log det(V_T^T phi) for both spins, or
+ * the sum over the two blocks' log det: real part and phase in (-pi, pi]).
+ * Any pointer may be NULL.
  * Synchronises the stream.
  */
 AFQMC_API int afqmc_get_walkers(afqmc_state* s, double* phi, double* weight, double* logov);

@@ -54,7 +54,8 @@ class Params(ctypes.Structure):
                 ("mode", ctypes.c_int32), ("ecap_C", ctypes.c_double),
                 ("fb_cap", ctypes.c_double), ("wmax", ctypes.c_double),
                 ("max_records", ctypes.c_int32), ("use_graph", ctypes.c_int32),
-                ("bp_steps", ctypes.c_int32), ("ndet", ctypes.c_int32)]
+                ("bp_steps", ctypes.c_int32), ("ndet", ctypes.c_int32),
+                ("Ndn", ctypes.c_int32), ("walker0", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
@@ -86,7 +87,8 @@ def lib():
     sig = {
         "afqmc_default_params": (None, [P(Params)]),
         "afqmc_workspace_size": (ctypes.c_int, [P(Params), P(ctypes.c_size_t)]),
-        "afqmc_init": (ctypes.c_int, [P(Params), dp, dp, dp, vp, ctypes.c_size_t, vp, P(vp)]),
+        "afqmc_init": (ctypes.c_int, [P(Params), dp, dp, dp, dp, vp, ctypes.c_size_t, vp,
+                                      P(vp)]),
         "afqmc_propagate": (ctypes.c_int, [vp, ctypes.c_int32]),
         "afqmc_energy": (ctypes.c_int, [vp, dp, dp]),
         "afqmc_local_energies": (ctypes.c_int, [vp, dp]),
@@ -277,9 +279,11 @@ class AfqmcRun:
 
     def __init__(self, h1, L, trial, params: Params, device="cuda:0", stream=None,
                  workspace=None):
-        """trial: the RHF orbitals [M][N], or for a multi-determinant trial
-        (params.ndet >= 1) a tuple (coefficients [ndet] complex, spin-up orbitals
-        [ndet][M][N], spin-down orbitals [ndet][M][N])."""
+        """trial: the RHF orbitals [M][N]; with two spin blocks (params.Ndn >= 1)
+        a tuple (spin-up orbitals [M][N], spin-down orbitals [M][Ndn]); for a
+        multi-determinant trial (params.ndet >= 1) a tuple (coefficients
+        [ndet] complex, spin-up orbitals [ndet][M][N], spin-down orbitals
+        [ndet][M][N])."""
         import torch
 
         self.p = params
@@ -317,12 +321,20 @@ class AfqmcRun:
                                                _dptr(cf), _dptr(up), _dptr(dn), ws_ptr, ws_len,
                                                sptr, ctypes.byref(st))
         else:
-            trial = np.ascontiguousarray(trial, np.float64)
-            if trial.shape != (params.M, params.N):
+            if params.Ndn > 0:
+                up, dn = trial
+                dn = np.ascontiguousarray(dn, np.float64)
+                if dn.shape != (params.M, params.Ndn):
+                    raise AfqmcError("spin-down trial must be [M][Ndn]")
+            else:
+                up, dn = trial, None
+            up = np.ascontiguousarray(up, np.float64)
+            if up.shape != (params.M, params.N):
                 raise AfqmcError("input shapes do not match the parameters")
             with torch.cuda.device(self.device):
-                rc = lib().afqmc_init(ctypes.byref(params), _dptr(h1), _dptr(L), _dptr(trial),
-                                      ws_ptr, ws_len, sptr, ctypes.byref(st))
+                rc = lib().afqmc_init(ctypes.byref(params), _dptr(h1), _dptr(L), _dptr(up),
+                                      _dptr(dn) if dn is not None else None, ws_ptr, ws_len,
+                                      sptr, ctypes.byref(st))
         _check(rc)
         self.s = st
 
@@ -356,8 +368,13 @@ class AfqmcRun:
         return (rho[0] + 1j * rho[1], phl[0] + 1j * phl[1], complex(ws[0], ws[1]),
                 complex(ws[2], ws[3]), n.value)
 
+    @property
+    def ncols(self) -> int:
+        """Orbital columns per walker: N, or N_up + N_dn with two spin blocks."""
+        return self.p.N + (self.p.Ndn if self.p.Ndn > 0 else 0)
+
     def get_walkers(self):
-        W, M, N = self.p.nwalkers, self.p.M, self.p.N
+        W, M, N = self.p.nwalkers, self.p.M, self.ncols
         phi = np.empty((W, M, N, 2))
         wt = np.empty((W, 2))
         lo = np.empty((W, 2))
@@ -371,7 +388,7 @@ class AfqmcRun:
         return wt[:, 0] + 1j * wt[:, 1]
 
     def set_walkers(self, phi, weight):
-        W, M, N = self.p.nwalkers, self.p.M, self.p.N
+        W, M, N = self.p.nwalkers, self.p.M, self.ncols
         phi = np.asarray(phi, np.complex128).reshape(W, M, N)
         ph = np.ascontiguousarray(np.stack([phi.real, phi.imag], -1))
         w = np.asarray(weight, np.complex128).reshape(W)

@@ -40,10 +40,11 @@ struct Bump {
 size_t plan(const afqmc_params& p, Bufs* b, char* base) {
   Bufs tmp;
   if (!b) b = &tmp;
-  const size_t M = p.M, N = p.N, G = p.nchol, W = p.nwalkers;
+  // N: orbital columns per walker (N_up + N_dn with two spin blocks)
+  const size_t M = p.M, N = p.N + (p.Ndn > 0 ? p.Ndn : 0), G = p.nchol, W = p.nwalkers;
   const size_t P = M * (M + 1) / 2;
   const bool mixed = p.precision != AFQMC_FP64;
-  size_t nchunk = (G + exchange_chunk(p.N, p.nchol) - 1) / exchange_chunk(p.N, p.nchol);
+  size_t nchunk = (G + exchange_chunk((int)N, p.nchol) - 1) / exchange_chunk((int)N, p.nchol);
   if (mixed) nchunk = G;  // the tensor-core exchange leaves one partial per vector
   const size_t lo = (p.precision == AFQMC_MIXED_BF16 || p.precision == AFQMC_MIXED_BF16_F32LU ||
                      p.precision == AFQMC_MIXED_BF16_F64THETA)
@@ -167,7 +168,7 @@ size_t plan(const afqmc_params& p, Bufs* b, char* base) {
   b->Ych = s2.take<double>((size_t)b->ych * M * M);
   b->P = (int)P;
   b->nchunk = (int)nchunk;
-  b->gc = exchange_chunk(p.N, p.nchol);
+  b->gc = exchange_chunk((int)N, p.nchol);
   b->status = reinterpret_cast<int*>(b->counters + CTR_STATUS);
   return ((s1.off > s2.off ? s1.off : s2.off) + 255) & ~size_t(255);
 }
@@ -212,9 +213,21 @@ static int check_params(const afqmc_params* p) {
     set_error("precision %d is not available in this build", p->precision);
     return AFQMC_EUNSUPPORTED;
   }
-  if (p->bp_steps < 0 || p->ndet < 0) {
-    set_error("bp_steps < 0 or ndet < 0");
+  if (p->bp_steps < 0 || p->ndet < 0 || p->Ndn < 0 || p->Ndn > p->M || p->walker0 < 0 ||
+      (int64_t)p->walker0 + p->nwalkers > 0x7fffffffLL) {
+    set_error("bp_steps < 0, ndet < 0, Ndn outside [0, M] or walker0 outside [0, 2^31 - nwalkers)");
     return AFQMC_EINVAL;
+  }
+  if (p->Ndn > 0) {
+    if (p->N + p->Ndn > 64) {
+      set_error("two spin blocks: N + Ndn = %d above 64", p->N + p->Ndn);
+      return AFQMC_EUNSUPPORTED;
+    }
+    if (p->precision != AFQMC_FP64 || p->ndet || p->bp_steps) {
+      set_error("two spin blocks run on the float64 path, with a single-determinant trial and "
+                "no back-propagation window");
+      return AFQMC_EUNSUPPORTED;
+    }
   }
   if (p->ndet > 0 && (p->pc_period || p->bp_steps || p->mode != AFQMC_PHASELESS)) {
     set_error("a multi-determinant trial runs phaseless, without population control or "
@@ -255,6 +268,16 @@ int refresh_phi_lo(afqmc_state* s) {
                            s->st);
 }
 
+// The same for the operand copy of Theta (pitch Mp), which the Theta kernel
+// writes; the comb moves Theta without it.
+static int refresh_theta_lo(afqmc_state* s) {
+  const Bufs& b = s->b;
+  if (!b.mixed) return AFQMC_OK;
+  const afqmc_params& p = s->p;
+  return launch_convert_lo(b.thetaT, 2L * p.N * p.nwalkers, p.M, p.M, b.th_lo, b.Mp, b.lo_kind,
+                           s->st);
+}
+
 int overlap_update(afqmc_state* s, bool into_ld, bool timed) {
   const afqmc_params& p = s->p;
   const Bufs& b = s->b;
@@ -266,7 +289,11 @@ int overlap_update(afqmc_state* s, bool into_ld, bool timed) {
   }
   // S = V_T^T Phi, S^-1, log det and Theta in one float64 kernel per walker
   OverlapArgs ov{p.nwalkers, p.M, p.N, b.VTt, b.phiT, b.thetaT, into_ld ? b.ld : b.ld_new, b.wt};
-  ov.unit_trial = 1;  // V_T' = [I_N; 0] in the trial-adapted basis
+  // V_T' = [I_N; 0] in the trial-adapted basis; with two spin blocks only
+  // the spin-up block is, and S = V_T'^T Phi' is formed per block
+  ov.unit_trial = s->spin2 ? 0 : 1;
+  ov.nup = s->nup;
+  ov.sf = s->sf;
   ov.Sinv = reinterpret_cast<double2*>(b.Sinv);
   if (b.mixed) {
     ov.th_lo = b.th_lo;
@@ -316,7 +343,7 @@ int force_bias_gemm(afqmc_state* s) {
   g.m = 2 * p.nwalkers;
   g.n = p.nchol;
   g.k = p.N * p.M;
-  g.alpha = 2.0;
+  g.alpha = s->sf;  // sum over spins: 2 Tr(Lh_g Theta) for the closed-shell block
   g.A = b.thetaT;
   g.lda = (long)p.N * p.M;
   g.B = b.Lh;
@@ -349,12 +376,14 @@ int energy_eval(afqmc_state* s, bool append, bool record = true) {
     AFQ_TRY(tc_exchange(g, p.nchol, p.nwalkers, p.N, b.part, b.nchunk, s->st));
   } else {
     ExchArgs ex{p.nwalkers, p.M, p.N, p.nchol, b.gc, b.nchunk, b.Lh, b.thetaT, b.part, b.wt};
+    ex.nup = s->nup;
     AFQ_TRY(launch_exchange(ex, s->st));
   }
   if (p.ndet == 0) {
     ElocArgs el{p.nwalkers, p.M, p.N, p.nchol, b.nchunk, p.H0, b.hh, b.thetaT, b.t, b.part, b.eloc,
                 b.wt};
     el.t32 = b.mixed ? b.t32 : nullptr;
+    el.sf = s->sf;
     AFQ_TRY(launch_eloc(el, s->st));
   }
   if (!record) return AFQMC_OK;
@@ -440,6 +469,7 @@ static int propagate_f64(afqmc_state* s) {
   const int W = p.nwalkers, G = p.nchol;
   FieldArgs fa{W, G, p.mode, p.seed, s->sdt, p.fb_cap, b.t, b.c, b.wt, b.x, b.scal,
                reinterpret_cast<const int64_t*>(b.counters + CTR_STEP)};
+  fa.w0 = p.walker0;
   prof_begin(s, AFQMC_PH_FIELDS);
   AFQ_TRY(launch_field(fa, s->st));
   prof_end(s);
@@ -522,6 +552,7 @@ static int propagate_mixed(afqmc_state* s) {
   const int W = p.nwalkers, G = p.nchol;
   FieldArgs fa{W, G, p.mode, p.seed, s->sdt, p.fb_cap, nullptr, b.c, b.wt, nullptr, b.scal,
                reinterpret_cast<const int64_t*>(b.counters + CTR_STEP)};
+  fa.w0 = p.walker0;
   fa.t32 = b.t32;
   fa.x_lo = b.x_lo;
   fa.lo_kind = b.lo_kind;
@@ -571,6 +602,8 @@ static int step_once(afqmc_state* s) {
     // Phi -> Q; Theta is unchanged and log det S drops by sum_k log r_kk,
     // which the kernel applies to ld (no new overlap needed)
     MgsArgs ma{W, M, N, b.phiT, b.wt, b.ld};
+    ma.nup = s->nup;
+    ma.sf = s->sf;
     if (b.mixed) {
       // the sweep (FP32 in shared memory when asked for, else float64) also
       // refreshes the operand copy of the orbitals
@@ -588,6 +621,7 @@ static int step_once(afqmc_state* s) {
                 b.wt, b.cum, b.parent, b.phiT, b.thetaT, b.ld, b.T0, b.T1, b.tmp_ld, b.wtot};
     AFQ_TRY(launch_comb(ca, s->st));
     AFQ_TRY(refresh_phi_lo(s));
+    AFQ_TRY(refresh_theta_lo(s));
     if (s->bp_on) AFQ_TRY(bp_after_comb(s));
     s->t_fresh = false;  // the walkers moved: their force-bias traces are stale
     prof_end(s);
@@ -746,18 +780,21 @@ static double orthonormality_error(const double* V, int M, int N) {
 // leading spin-up orbitals md_up[0] are then the trial of the basis and of
 // the initial walkers.
 static int setup_device(afqmc_state* s, const double* h1, const double* L, const double* trial,
-                        const double* md_coef = nullptr, const double* md_up = nullptr,
-                        const double* md_dn = nullptr) {
+                        const double* trial_dn = nullptr, const double* md_coef = nullptr,
+                        const double* md_up = nullptr, const double* md_dn = nullptr) {
   const afqmc_params& p = s->p;
   const Bufs& b = s->b;
   const int M = p.M, N = p.N, G = p.nchol, W = p.nwalkers;
+  const int nup = s->nup;  // spin-up columns (N unless two spin blocks)
   cudaStream_t st = s->st;
   const bool md = p.ndet > 0;
   if (md) trial = md_up;
   // the trial's columns must be orthonormal
-  for (int ds = 0; ds < (md ? 2 * p.ndet : 1); ++ds) {
-    const double* V = md ? ((ds & 1) ? md_dn : md_up) + (size_t)(ds >> 1) * M * N : trial;
-    const double dev = orthonormality_error(V, M, N);
+  for (int ds = 0; ds < (md ? 2 * p.ndet : (s->spin2 ? 2 : 1)); ++ds) {
+    const double* V = md ? ((ds & 1) ? md_dn : md_up) + (size_t)(ds >> 1) * M * N
+                         : (ds ? trial_dn : trial);
+    const int nc = md ? N : (ds ? N - nup : nup);
+    const double dev = orthonormality_error(V, M, nc);
     if (!(dev < 1e-8)) {
       set_error("trial columns are not orthonormal (determinant %d spin %d: max |V^T V - I| = "
                 "%.3g)", ds >> 1, ds & 1, dev);
@@ -765,7 +802,7 @@ static int setup_device(afqmc_state* s, const double* h1, const double* L, const
     }
   }
   std::vector<double> qh, qt((size_t)M * M), vtt((size_t)N * M, 0.0);
-  complete_basis(trial, M, N, qh);
+  complete_basis(trial, M, nup, qh);
   if (md) {
     // the determinants' orbitals in the run's basis, V' = Q^T V, stored as
     // rows i = column i: [2 ndet][N][M]
@@ -786,7 +823,15 @@ static int setup_device(afqmc_state* s, const double* h1, const double* L, const
   }
   for (int r = 0; r < M; ++r)
     for (int c = 0; c < M; ++c) qt[(size_t)c * M + r] = qh[(size_t)r * M + c];
-  for (int i = 0; i < N; ++i) vtt[(size_t)i * M + i] = 1.0;
+  for (int i = 0; i < nup; ++i) vtt[(size_t)i * M + i] = 1.0;
+  // two spin blocks: rows nup.. are the spin-down orbitals in this basis,
+  // (Q^T V_dn)^T (the basis is adapted to the spin-up trial only)
+  for (int i = nup; i < N; ++i)
+    for (int r = 0; r < M; ++r) {
+      const double v = trial_dn[(size_t)r * (N - nup) + (i - nup)];
+      if (v == 0.0) continue;
+      for (int q = 0; q < M; ++q) vtt[(size_t)i * M + q] += v * qh[(size_t)r * M + q];
+    }
   AFQ_CUDA(cudaMemcpyAsync(b.Qb, qh.data(), sizeof(double) * M * M, cudaMemcpyHostToDevice, st));
   AFQ_CUDA(cudaMemcpyAsync(b.QTb, qt.data(), sizeof(double) * M * M, cudaMemcpyHostToDevice, st));
   AFQ_CUDA(cudaMemcpyAsync(b.VTt, vtt.data(), sizeof(double) * N * M, cudaMemcpyHostToDevice, st));
@@ -832,12 +877,13 @@ static int setup_device(afqmc_state* s, const double* h1, const double* L, const
     h.ldc = M;
     AFQ_TRY(gemm_nt_f64(h, st));
   }
-  // c_g = 2 Tr(L_g P) = 2 Tr(Lh_g V_T): vbar_g = i c_g (Sec. 2.4); with a
-  // multi-determinant trial the leading determinant's Tr(L_g (P_0u + P_0d))
+  // c_g = Tr(L_g P) = sf Tr(Lh_g V_T) summed over the spin blocks (2 Tr(Lh_g V_T)
+  // closed shell): vbar_g = i c_g (Sec. 2.4); with a multi-determinant trial
+  // the leading determinant's Tr(L_g (P_0u + P_0d))
   if (md)
     AFQ_TRY(md_setup(s, md_coef));
   else
-    AFQ_TRY(launch_rowdot(b.Lh, b.VTt, b.c, G, N * M, 2.0, st));
+    AFQ_TRY(launch_rowdot(b.Lh, b.VTt, b.c, G, N * M, s->sf, st));
   // sum_g L_g L_g
   {
     GemmF64 g;
@@ -936,7 +982,7 @@ static int setup_device(afqmc_state* s, const double* h1, const double* L, const
 
 }  // namespace afq
 
-static_assert(sizeof(afqmc_params) == 112, "afqmc_params layout");
+static_assert(sizeof(afqmc_params) == 120, "afqmc_params layout");
 static_assert(sizeof(afqmc_info) == 64, "afqmc_info layout");
 
 using namespace afq;
@@ -978,9 +1024,9 @@ int afqmc_workspace_size(const afqmc_params* p, size_t* bytes) {
 // Workspace checks, the state, the device set-up and the graph block, for
 // afqmc_init (trial) and afqmc_init_multidet (md_*).
 static int init_state(const afqmc_params* p, const double* h1, const double* L,
-                      const double* trial, const double* md_coef, const double* md_up,
-                      const double* md_dn, void* d_workspace, size_t ws_bytes, void* stream,
-                      afqmc_state** out) {
+                      const double* trial, const double* trial_dn, const double* md_coef,
+                      const double* md_up, const double* md_dn, void* d_workspace,
+                      size_t ws_bytes, void* stream, afqmc_state** out) {
   if (reinterpret_cast<uintptr_t>(d_workspace) % 256) {
     set_error("workspace must be 256-byte aligned");
     return AFQMC_EINVAL;
@@ -1003,7 +1049,8 @@ static int init_state(const afqmc_params* p, const double* h1, const double* L,
     AFQ_TRY(all_finite(md_up, nd * M * N, "trial_up"));
     AFQ_TRY(all_finite(md_dn, nd * M * N, "trial_dn"));
   } else {
-    AFQ_TRY(all_finite(trial, M * N, "trial"));
+    AFQ_TRY(all_finite(trial, M * N, "trial_up"));
+    if (p->Ndn > 0) AFQ_TRY(all_finite(trial_dn, M * (size_t)p->Ndn, "trial_dn"));
   }
   AFQ_TRY(all_finite(L, G * M * M, "L"));
   afqmc_state* s = new (std::nothrow) afqmc_state();
@@ -1012,12 +1059,21 @@ static int init_state(const afqmc_params* p, const double* h1, const double* L,
     return AFQMC_EINVAL;
   }
   s->p = *p;
+  // internally N counts every orbital column of a walker: with two spin
+  // blocks the N_up spin-up columns are followed by the N_dn spin-down ones
+  s->nup = p->N;
+  if (p->Ndn > 0) {
+    s->spin2 = true;
+    s->sf = 1.0;
+    s->p.N = p->N + p->Ndn;
+    s->p.Ndn = 0;
+  }
   s->st = static_cast<cudaStream_t>(stream);
   s->ws = static_cast<char*>(d_workspace);
   s->ws_bytes = ws_bytes;
-  plan(*p, &s->b, s->ws);
+  plan(s->p, &s->b, s->ws);
   s->sdt = std::sqrt(p->dt);
-  int r = setup_device(s, h1, L, trial, md_coef, md_up, md_dn);
+  int r = setup_device(s, h1, L, trial, trial_dn, md_coef, md_up, md_dn);
   if (r != AFQMC_OK) {
     delete s;
     return r;
@@ -1044,8 +1100,9 @@ static int init_state(const afqmc_params* p, const double* h1, const double* L,
 
 extern "C" {
 
-int afqmc_init(const afqmc_params* p, const double* h1, const double* L, const double* trial,
-               void* d_workspace, size_t ws_bytes, void* stream, afqmc_state** out) {
+int afqmc_init(const afqmc_params* p, const double* h1, const double* L, const double* trial_up,
+               const double* trial_dn, void* d_workspace, size_t ws_bytes, void* stream,
+               afqmc_state** out) {
   if (!out) {
     set_error("out is NULL");
     return AFQMC_EINVAL;
@@ -1056,12 +1113,17 @@ int afqmc_init(const afqmc_params* p, const double* h1, const double* L, const d
     set_error("ndet = %d: a multi-determinant trial is set up by afqmc_init_multidet", p->ndet);
     return AFQMC_EINVAL;
   }
-  if (!h1 || !L || !trial || !d_workspace) {
-    set_error("h1, L, trial and d_workspace are required");
+  if (!h1 || !L || !trial_up || !d_workspace) {
+    set_error("h1, L, trial_up and d_workspace are required");
     return AFQMC_EINVAL;
   }
-  return init_state(p, h1, L, trial, nullptr, nullptr, nullptr, d_workspace, ws_bytes, stream,
-                    out);
+  if ((p->Ndn > 0) != (trial_dn != nullptr)) {
+    set_error("trial_dn is required with two spin blocks (params.Ndn >= 1) and must be NULL "
+              "otherwise");
+    return AFQMC_EINVAL;
+  }
+  return init_state(p, h1, L, trial_up, trial_dn, nullptr, nullptr, nullptr, d_workspace,
+                    ws_bytes, stream, out);
 }
 
 int afqmc_init_multidet(const afqmc_params* p, const double* h1, const double* L, int32_t ndet,
@@ -1082,8 +1144,8 @@ int afqmc_init_multidet(const afqmc_params* p, const double* h1, const double* L
     set_error("h1, L, coef, trial_up, trial_dn and d_workspace are required");
     return AFQMC_EINVAL;
   }
-  return init_state(p, h1, L, nullptr, coef, trial_up, trial_dn, d_workspace, ws_bytes, stream,
-                    out);
+  return init_state(p, h1, L, nullptr, nullptr, coef, trial_up, trial_dn, d_workspace, ws_bytes,
+                    stream, out);
 }
 
 #define AFQ_STATE(s)                       \
@@ -1342,7 +1404,7 @@ struct CkptHeader {
   int64_t step;
   uint64_t records, nonfinite;
   uint64_t seed;
-  int32_t max_records, reserved;
+  int32_t max_records, nup;  // nup: spin-up columns of a two-block walker, 0 closed shell
 };
 constexpr uint64_t kMagic = 0x31434D5146414731ull;
 }  // namespace
@@ -1378,7 +1440,7 @@ int afqmc_save(afqmc_state* s, void* buf, size_t* bytes) {
                            sizeof(double) * 4 * p.max_records, cudaMemcpyDeviceToHost, s->st));
   AFQ_CUDA(cudaStreamSynchronize(s->st));
   CkptHeader h{kMagic, p.M, p.N, p.nchol, p.nwalkers, s->h_step, ctr[CTR_RECORDS],
-               ctr[CTR_NONFINITE], p.seed, p.max_records, 0};
+               ctr[CTR_NONFINITE], p.seed, p.max_records, s->spin2 ? s->nup : 0};
   std::memcpy(buf, &h, sizeof(h));
   *bytes = need;
   return AFQMC_OK;
@@ -1398,7 +1460,7 @@ int afqmc_load(afqmc_state* s, const void* buf, size_t bytes) {
                       sizeof(double) * (2 * nw + 4 * (size_t)p.nwalkers + 4 * (size_t)p.max_records);
   if (h.magic != kMagic || h.M != p.M || h.N != p.N || h.nchol != p.nchol ||
       h.nwalkers != p.nwalkers || h.max_records != p.max_records || h.seed != p.seed ||
-      bytes < need) {
+      h.nup != (s->spin2 ? s->nup : 0) || bytes < need) {
     set_error("checkpoint does not match this state");
     return AFQMC_EINVAL;
   }
@@ -1406,6 +1468,7 @@ int afqmc_load(afqmc_state* s, const void* buf, size_t bytes) {
   AFQ_CUDA(cudaMemcpyAsync(s->b.phiT, d, sizeof(double) * nw, cudaMemcpyHostToDevice, s->st));
   AFQ_TRY(refresh_phi_lo(s));
   AFQ_CUDA(cudaMemcpyAsync(s->b.thetaT, d + nw, sizeof(double) * nw, cudaMemcpyHostToDevice, s->st));
+  AFQ_TRY(refresh_theta_lo(s));
   AFQ_CUDA(cudaMemcpyAsync(s->b.wt, d + 2 * nw, sizeof(double) * 2 * p.nwalkers, cudaMemcpyHostToDevice, s->st));
   AFQ_CUDA(cudaMemcpyAsync(s->b.ld, d + 2 * nw + 2 * p.nwalkers, sizeof(double) * 2 * p.nwalkers,
                            cudaMemcpyHostToDevice, s->st));

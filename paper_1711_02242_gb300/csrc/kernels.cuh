@@ -103,6 +103,7 @@ struct FieldArgs {
   const float* t32 = nullptr;
   void* x_lo = nullptr;
   int lo_kind = LO_NONE, Gp = 0;
+  int w0 = 0;  // global index of walker 0 in the Philox counter (sharded populations)
 };
 int launch_field(const FieldArgs& a, cudaStream_t st);
 
@@ -133,6 +134,10 @@ struct OverlapArgs {
   double2* Sinv = nullptr;  // [W][N][N] scratch: S^-1 of live walkers
   float2* Sinv32 = nullptr;  // _F32LU precisions: FP32 elimination, S^-1 here and FP32 Theta
   int theta32 = 0;  // FP32 product Theta = Phi S^-1 from the float64 S^-1 (Sinv32 unset)
+  // spin blocks: columns [0, nup) spin up, [nup, N) spin down (nup = N: one
+  // closed-shell block standing for both spins); sf = spins per block (2 or 1)
+  int nup = 0;
+  double sf = 2.0;
 };
 // S^-1 and log det (k_overlap), then Theta (k_theta_rows)
 int launch_overlap(const OverlapArgs& a, cudaStream_t st);
@@ -159,6 +164,8 @@ struct MgsArgs {
   int f32 = 0;   // _F32LU precisions: FP32 sweep in shared memory where [N][M] fits
   void* phi_lo = nullptr;  // and, if set, the BF16/TF32 copy of the result (pitch Mp)
   int lo_kind = LO_NONE, Mp = 0;
+  int nup = 0;      // spin blocks as in OverlapArgs (0: one block), swept separately
+  double sf = 2.0;  // spins per block: log <Psi_T|Psi> drops by sf sum_k log r_kk
 };
 int launch_mgs(const MgsArgs& a, cudaStream_t st);
 
@@ -168,6 +175,7 @@ struct ExchArgs {
   const double* thetaT;  // [W][2][N][M]
   double* part;          // [W][nchunk][2]
   const double* wt;
+  int nup = 0;  // spin blocks (0: one block): only same-spin pairs (i, j) are summed
 };
 int exchange_chunk(int N, int G);
 int launch_exchange(const ExchArgs& a, cudaStream_t st);
@@ -182,6 +190,7 @@ struct ElocArgs {
   double* eloc;          // [W][2]
   const double* wt;
   const float* t32 = nullptr;  // mixed path: t as float
+  double sf = 2.0;  // spins per block: E = H0 + sf e1 + c / 2 - sf x / 2
 };
 int launch_eloc(const ElocArgs& a, cudaStream_t st);
 

@@ -107,6 +107,11 @@ struct afqmc_state {
   // back-propagation window: open, and steps recorded since it opened
   bool bp_on = false;
   int bp_m = 0;
+  // spin blocks: p.N counts all orbital columns; the first nup are spin up.
+  // Closed shell (one block standing for both spins): nup = p.N, sf = 2.
+  bool spin2 = false;
+  int nup = 0;
+  double sf = 2.0;
 };
 
 namespace afq {

@@ -40,9 +40,9 @@ __global__ void __launch_bounds__(256) k_field(FieldArgs a) {
   for (int k = threadIdx.x; k < npair; k += blockDim.x) {
     double xa, xb;
     if (a.x_lo)
-      field_pair_f32(a.seed, (uint32_t)*a.dstep, (uint32_t)w, (uint32_t)k, &xa, &xb);
+      field_pair_f32(a.seed, (uint32_t)*a.dstep, (uint32_t)(a.w0 + w), (uint32_t)k, &xa, &xb);
     else
-      field_pair(a.seed, (uint32_t)*a.dstep, (uint32_t)w, (uint32_t)k, &xa, &xb);
+      field_pair(a.seed, (uint32_t)*a.dstep, (uint32_t)(a.w0 + w), (uint32_t)k, &xa, &xb);
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int g = 2 * k + h;
@@ -110,7 +110,7 @@ __global__ void __launch_bounds__(256) k_field_lo(FieldArgs a) {
   const int npair = (a.G + 1) / 2;
   for (int k = threadIdx.x; k < npair; k += blockDim.x) {
     double xa, xb;
-    field_pair_f32(a.seed, step, (uint32_t)w, (uint32_t)k, &xa, &xb);
+    field_pair_f32(a.seed, step, (uint32_t)(a.w0 + w), (uint32_t)k, &xa, &xb);
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int g = 2 * k + h;
@@ -268,6 +268,9 @@ int launch_taylor_term(const TaylorArgsT<double>& a, cudaStream_t st) { return l
 //      p_k (+ i pi per row swap), S^-1 written for k_theta_rows;
 // then k_theta_rows forms Theta^T[i][p] = sum_j S^-1[j][i] Phi^T[j][p].
 // log <Psi_T|Psi> = 2 log det S (both spins), phase wrapped to (-pi, pi].
+// With two spin blocks (a float64 run whose spin-down trial differs from the
+// spin-up one) S is the block-diagonal product V_T^T Phi instead of a gather,
+// and log <Psi_T|Psi> = log det S_up + log det S_dn.
 // Every walker is computed; S^-1 and log det are stored for live walkers.
 namespace {
 constexpr int OV_T = 256;
@@ -311,11 +314,30 @@ __device__ __forceinline__ bool overlap_core(const OverlapArgs& a, int w, bool l
   __shared__ int order[64];
   const double* fr = a.phiT + (long)w * 2 * N * M;
   const double* fi = fr + (long)N * M;
-  // S[i][j] = Phi[i][j], the top block of the orbitals
-  for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x) {
-    const int i = idx / N, j = idx % N;
-    A[idx] = Vec2<T>::make(Vec2<T>::from_f64(fr[(long)j * M + i]),
-                           Vec2<T>::from_f64(fi[(long)j * M + i]));
+  if (a.unit_trial) {
+    // S[i][j] = Phi[i][j], the top block of the orbitals
+    for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x) {
+      const int i = idx / N, j = idx % N;
+      A[idx] = Vec2<T>::make(Vec2<T>::from_f64(fr[(long)j * M + i]),
+                             Vec2<T>::from_f64(fi[(long)j * M + i]));
+    }
+  } else {
+    // two spin blocks: S = blockdiag(V_up^T Phi_up, V_dn^T Phi_dn), zero
+    // between the blocks, so that the elimination below never pivots across
+    // them and its pivots give det S_up det S_dn (Theorem 1.1)
+    const int nup = a.nup > 0 ? a.nup : N;
+    for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x) {
+      const int i = idx / N, j = idx % N;
+      double sr = 0.0, si = 0.0;
+      if ((i < nup) == (j < nup)) {
+        const double* v = a.VTt + (long)i * M;
+        for (int p = 0; p < M; ++p) {
+          sr = fma(v[p], fr[(long)j * M + p], sr);
+          si = fma(v[p], fi[(long)j * M + p], si);
+        }
+      }
+      A[idx] = Vec2<T>::make(Vec2<T>::from_f64(sr), Vec2<T>::from_f64(si));
+    }
   }
   if (threadIdx.x < N) order[threadIdx.x] = threadIdx.x;
   if (threadIdx.x == 0) {
@@ -442,8 +464,8 @@ __device__ __forceinline__ bool overlap_core(const OverlapArgs& a, int w, bool l
       a.logdet[2L * w] = -INFINITY;
       a.logdet[2L * w + 1] = 0.0;
     } else {
-      a.logdet[2L * w] = 2.0 * (red[0] + red[2]);
-      a.logdet[2L * w + 1] = wrap_pi(2.0 * ((red[1] + red[3]) + 3.141592653589793 * swaps));
+      a.logdet[2L * w] = a.sf * (red[0] + red[2]);
+      a.logdet[2L * w + 1] = wrap_pi(a.sf * ((red[1] + red[3]) + 3.141592653589793 * swaps));
     }
   }
   return singular != 0;
@@ -614,8 +636,9 @@ static int launch_theta_rows(const OverlapArgs& a, cudaStream_t st) {
 
 int launch_overlap(const OverlapArgs& a, cudaStream_t st) {
   const size_t smem = 2ull * a.N * a.N * sizeof(double2);
-  if (!a.unit_trial || !a.Sinv) {
-    set_error("overlap: the trial-adapted basis (V_T = [I; 0]) and S^-1 scratch are required");
+  if (!a.Sinv || (!a.unit_trial && (a.Sinv32 || a.nup <= 0 || a.nup > a.N))) {
+    set_error("overlap: S^-1 scratch is required, and a trial other than V_T = [I; 0] only "
+              "in float64 with two spin blocks");
     return AFQMC_EINVAL;
   }
   if (smem > 200 * 1024) {
@@ -766,9 +789,11 @@ __global__ void __launch_bounds__(256) k_mgs(MgsArgs a) {
     // product is reduced over 8 lanes (3 shuffle levels) instead of 32, which
     // keeps the FP64 pipe - the bound of this kernel - on the projections
     const int grp = lane >> 3, gl = lane & 7, ngrp = 4 * nwarp;
-    for (int j0 = k + 1; j0 < N; j0 += ngrp) {
+    // later columns of the same spin block only
+    const int jend = (a.nup > 0 && k < a.nup) ? a.nup : N;
+    for (int j0 = k + 1; j0 < jend; j0 += ngrp) {
       const int j = j0 + 4 * warp + grp;
-      const bool act = j < N;
+      const bool act = j < jend;
       double* ur = re + (long)(act ? j : k) * M;
       double* ui = im + (long)(act ? j : k) * M;
       // <q_k|v_j> and v_j -= <q_k|v_j> q_k as chains of FMAs
@@ -802,7 +827,7 @@ __global__ void __launch_bounds__(256) k_mgs(MgsArgs a) {
     if (lane == 0) sh[warp] = lr;
   }
   __syncthreads();
-  if (threadIdx.x == 0 && a.ld) a.ld[2L * w] -= 2.0 * (sh[0] + sh[1]);
+  if (threadIdx.x == 0 && a.ld) a.ld[2L * w] -= a.sf * (sh[0] + sh[1]);
 }
 
 // _F32LU mixed precisions: the same sweep in FP32 with the walker's orbitals resident in
@@ -983,9 +1008,11 @@ __global__ void __launch_bounds__(EX_T) k_exchange(ExchArgs a) {
   }
   __syncthreads();
   double er = 0.0, ei = 0.0;
+  const int nup = a.nup > 0 ? a.nup : N;
   for (int idx = threadIdx.x; idx < gcount * N * N; idx += blockDim.x) {
     const int g = idx / (N * N), ij = idx % (N * N);
     const int i = ij / N, j = ij % N;
+    if ((i < nup) != (j < nup)) continue;  // T_g is taken per spin block
     const double* Tr = Tm + (long)(2 * g) * N * N;
     const double* Ti = Tr + (long)N * N;
     const double ar = Tr[i * N + j], ai = Ti[i * N + j];
@@ -1024,7 +1051,10 @@ int launch_exchange(const ExchArgs& a, cudaStream_t st) {
 
 // ---------------------------------------------------------- local energy --
 // E_loc = H0 + 2 Tr(hh Theta) + 1/2 sum_g t_g^2 - sum_g Tr(T_g T_g)
-// (Eqs. localenergy2/3; the 1/2 is that of H_2 in Eq. bo_ham2).
+// (Eqs. localenergy2/3; the 1/2 is that of H_2 in Eq. bo_ham2) for the
+// closed-shell block; with two spin blocks (sf = 1) the one-body trace and the
+// exchange are the sums over the blocks, E_loc = H0 + Tr(hh Theta) +
+// 1/2 sum_g [t_g^2 - sum_sigma Tr(T_g,sigma T_g,sigma)].
 __global__ void __launch_bounds__(256) k_eloc(ElocArgs a) {
   __shared__ double sh[32];
   const int w = blockIdx.x;
@@ -1062,8 +1092,8 @@ __global__ void __launch_bounds__(256) k_eloc(ElocArgs a) {
   xr = block_sum(xr, sh);
   xi = block_sum(xi, sh);
   if (threadIdx.x == 0) {
-    a.eloc[2 * w] = a.H0 + 2.0 * e1r + 0.5 * cr - xr;
-    a.eloc[2 * w + 1] = 2.0 * e1i + 0.5 * ci - xi;
+    a.eloc[2 * w] = a.H0 + a.sf * e1r + 0.5 * cr - (0.5 * a.sf) * xr;
+    a.eloc[2 * w + 1] = a.sf * e1i + 0.5 * ci - (0.5 * a.sf) * xi;
   }
 }
 

@@ -44,8 +44,8 @@ def test_params_struct_matches_header_defaults(built):
     assert (p.dt, p.taylor_order, p.qr_period, p.pc_period) == (0.005, 6, 5, 0)
     assert p.ecap_C == 2.0 and p.fb_cap == 1.0 and p.max_records == 4096
     assert p.e_shift != p.e_shift and p.wmax != p.wmax  # NaN defaults
-    assert ctypes.sizeof(built.Params) == 112
-    assert p.bp_steps == 0 and p.ndet == 0
+    assert ctypes.sizeof(built.Params) == 120
+    assert p.bp_steps == 0 and p.ndet == 0 and p.Ndn == 0 and p.walker0 == 0
 
 
 def test_workspace_size_and_validation_without_gpu(built):
@@ -58,6 +58,30 @@ def test_workspace_size_and_validation_without_gpu(built):
         built.afqmc_workspace_size(built.default_params(10, 11, 5, 4))
     with pytest.raises(built.AfqmcError, match="EINVAL"):
         built.afqmc_workspace_size(built.default_params(10, 2, 5, 4, dt=-1.0))
+
+
+def test_spin_block_parameters_without_gpu(built):
+    """Two spin blocks (Ndn >= 1): the workspace holds N_up + N_dn orbital
+    columns per walker; they run on the float64 path only, with at most 64
+    columns; walker0 is a non-negative field counter offset."""
+    n1 = built.afqmc_workspace_size(built.default_params(12, 3, 48, 32))
+    n2 = built.afqmc_workspace_size(built.default_params(12, 3, 48, 32, Ndn=2))
+    n3 = built.afqmc_workspace_size(built.default_params(12, 5, 48, 32))
+    assert n1 < n2 <= n3
+    for kw, err in ((dict(Ndn=2, precision=2), "EUNSUPPORTED"), (dict(Ndn=2, bp_steps=4), "EUNSUPPORTED"),
+                    (dict(Ndn=13), "EINVAL"), (dict(Ndn=-1), "EINVAL"), (dict(walker0=-1), "EINVAL")):
+        with pytest.raises(built.AfqmcError, match=err):
+            built.afqmc_workspace_size(built.default_params(12, 3, 48, 32, **kw))
+    with pytest.raises(built.AfqmcError, match="EUNSUPPORTED"):
+        built.afqmc_workspace_size(built.default_params(100, 40, 48, 32, Ndn=30))
+    # the spin-down trial is required exactly when Ndn >= 1 (refused before any device call)
+    st = ctypes.c_void_p()
+    lib = built.lib()
+    h = (ctypes.c_double * 144)()
+    p = built.default_params(12, 3, 48, 32, Ndn=2)
+    assert lib.afqmc_init(ctypes.byref(p), h, h, h, None, ctypes.c_void_p(256), 1 << 30, None,
+                          ctypes.byref(st)) == -1
+    assert b"trial_dn" in lib.afqmc_last_error()
 
 
 def test_library_has_no_oracle_dependency():

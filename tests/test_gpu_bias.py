@@ -1,0 +1,42 @@
+"""Run-level energy bias of the mixed precisions against the float64 path on
+identical fields, for the 100-orbital workload (10+10 electrons, 500
+vectors, 1024 walkers, 100 steps, a record every 5 steps).
+
+The walkers are independent without population control, so 16 groups of 64
+walkers give 16 independent estimates of each bias.  Bounds (mHa), from the
+measured values with room for their spread:
+  TF32  estimator |bias| < 0.02 (measured 0.005), run |bias| < 0.2 (-0.12)
+  BF16  estimator |bias| < 0.3  (measured 0.195), run |bias| < 0.35 (0.17)
+and each standard error below a quarter of its bound.  A regression of the
+mixed path's rounding (a dropped identity split of exp(-dt v0'/2), a biased
+operand rounding) moves these by far more.
+"""
+import pytest
+
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def report():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import bench
+
+    return bench.bias_runs(workloads.config("c1"), ("tf32", "bf16"), 100, 5, groups=16)
+
+
+@pytest.mark.parametrize("prec,est_bound,run_bound", [("tf32", 0.02, 0.2), ("bf16", 0.3, 0.35)])
+def test_mixed_bias_within_stated_bounds(report, prec, est_bound, run_bound):
+    r = report["precisions"][prec]
+    assert r["status"] == 0 and r["groups_used"] == 16
+    assert abs(r["bias_estimator_mHa"]) < est_bound
+    assert r["se_estimator_mHa"] < est_bound / 4
+    assert abs(r["bias_run_mHa"]) < run_bound
+    assert r["se_run_mHa"] < run_bound / 4
+    assert report["alive_fp64_end"] == 1024

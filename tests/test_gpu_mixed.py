@@ -178,3 +178,34 @@ def test_fp32_theta_close_to_float64_theta(pkg, base, prec, tol_phi):
     assert np.max(d / n) < tol_phi
     assert abs(np.mean((wb[alive] / wa[alive]).real) - 1) < 1e-3
     assert np.max(np.abs(lb[:, 1] - la[:, 1]) / np.abs(la[:, 1])) < 5e-5
+
+
+@pytest.mark.parametrize("prec", [2, 1])
+def test_mixed_energies_after_comb_and_restore_match_fresh_evaluation(pkg, prec):
+    """The comb moves walkers (orbitals, Theta, overlaps) between slots and a
+    checkpoint restore replaces them: the local energies the state then
+    evaluates (force bias and exchange from the BF16/TF32 operand copies)
+    equal those of a state given the same walkers by set_walkers, which
+    recomputes every operand from the orbitals (to the last bits of the
+    basis rotation set_walkers applies: an operand whose BF16/TF32 rounding
+    flips moves an energy by far less than 2e-5 relative, a stale operand of
+    a copied walker by orders of magnitude more); after the restore the
+    energies are bitwise those before the save."""
+    w = workloads.config("c0")
+    h1, L, _ = w.hamiltonian()
+    C, _, _, _ = scf.rhf(h1, L, w.N)
+    kw = dict(dt=w.dt, seed=w.seed, qr_period=0, energy_period=0, precision=prec)
+    run = pkg.AfqmcRun(h1, L, C, pkg.default_params(w.M, w.N, w.nchol, w.nwalkers, pc_period=3,
+                                                    **kw))
+    fresh = pkg.AfqmcRun(h1, L, C, pkg.default_params(w.M, w.N, w.nchol, w.nwalkers, **kw))
+    run.propagate(3)  # ends with a comb
+    phi, wt, _ = run.get_walkers()
+    assert len(set(np.round(np.abs(phi[:, 0, 0]), 12))) < w.nwalkers  # copies were made
+    e_run = run.local_energies()
+    fresh.set_walkers(phi, wt)
+    e_fresh = fresh.local_energies()
+    assert np.max(np.abs(e_run - e_fresh) / np.abs(e_fresh)) < 2e-5
+    blob = run.save()
+    run.propagate(2)
+    run.load(blob)
+    assert np.array_equal(run.local_energies(), e_run)

@@ -169,7 +169,7 @@ def test_errors(pkg):
     # afqmc_init takes the single RHF trial only (ndet = 0)
     p = pkg.default_params(M, N, G, W, ndet=2)
     st = ctypes.c_void_p()
-    assert pkg.lib().afqmc_init(ctypes.byref(p), None, None, None, None, 0, None,
+    assert pkg.lib().afqmc_init(ctypes.byref(p), None, None, None, None, None, 0, None,
                                 ctypes.byref(st)) == -1
     bad = up.copy()
     bad[1] *= 1.5
