@@ -17,10 +17,12 @@ configuration's precision); the line also carries the same workload's FP64
 path measured on the same GPU (a few steps) and the mixed path's energy bias
 against it on identical walkers and fields.
 
-Prints one JSON line.  Under torchrun (N > 1) every rank runs an independent
-replica (its own walker population and Philox seed) on its own GPU; time is
+Prints one JSON line.  Under torchrun (N > 1) the ranks hold one population
+of N x 512 walkers, 512 per GPU (paper_1711_02242_gb300.dist): each rank
+steps its share, the mixed estimator is summed over the ranks and, with
+--pc-period, the comb spans all ranks (walkers move between GPUs).  Time is
 the max over ranks and the value the walker-steps of all ranks per second
-(weak scaling, no collective on the data path).
+(weak scaling).
 """
 from __future__ import annotations
 
@@ -164,11 +166,6 @@ def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
-
-
-def replica_seed(base: int, rank: int) -> int:
-    """Each rank runs an independent replica: its own Philox key."""
-    return base + 1000 * rank
 
 
 def max_over_ranks(value: float, device="cpu") -> float:
@@ -400,18 +397,37 @@ def run_gpu(args, w: workloads.Workload):
     b.build()
     prec = PRECISIONS[args.precision]
     h1, L, H0, C, conv, grad = make_inputs(w)
-    p = pkg.default_params(w.M, w.N, w.nchol, w.nwalkers, dt=w.dt, seed=replica_seed(w.seed, rank),
-                           qr_period=w.qr_period, energy_period=w.energy_period,
-                           taylor_order=w.taylor_order, precision=prec, H0=H0,
-                           use_graph=0 if args.no_graph else 1)
+    pc = args.pc_period if args.pc_period is not None else w.pc_period
+    sharded = ws > 1
+    if sharded:
+        # one population of ws x W walkers: this rank steps the global walkers
+        # [rank W, (rank + 1) W) (same seed everywhere, fields keyed by the
+        # global index); the comb and the estimator span all ranks
+        p = pkg.default_params(w.M, w.N, w.nchol, w.nwalkers, dt=w.dt, seed=w.seed,
+                               qr_period=w.qr_period, energy_period=0, pc_period=0,
+                               taylor_order=w.taylor_order, precision=prec, H0=H0,
+                               use_graph=0 if args.no_graph else 1, walker0=rank * w.nwalkers)
+    else:
+        p = pkg.default_params(w.M, w.N, w.nchol, w.nwalkers, dt=w.dt, seed=w.seed,
+                               qr_period=w.qr_period, energy_period=w.energy_period,
+                               pc_period=pc, taylor_order=w.taylor_order, precision=prec, H0=H0,
+                               use_graph=0 if args.no_graph else 1)
     stream = torch.cuda.Stream(device=dev)
     run = pkg.AfqmcRun(h1, L, C, p, device=dev, stream=stream)
     K = args.steps
+    pop = None
+    if sharded:
+        from paper_1711_02242_gb300.dist import ShardedPopulation, StateShard
+
+        pop = ShardedPopulation(StateShard(run), pc_period=pc, energy_period=w.energy_period)
     # warm-up: at least one whole graph block (capture + first replay)
-    blk = math.lcm(*[x for x in (w.qr_period, w.pc_period, w.energy_period) if x]) or 1
+    blk = math.lcm(*[x for x in (w.qr_period, pc, w.energy_period) if x]) or 1
     Wm = max(args.warmup, blk)
     Wm = -(-Wm // blk) * blk
-    run.propagate(Wm)
+    if pop is not None:
+        pop.run(Wm)
+    else:
+        run.propagate(Wm)
     stream.synchronize()
 
     def barrier():
@@ -428,7 +444,10 @@ def run_gpu(args, w: workloads.Workload):
     torch.cuda.synchronize(dev)
     with ClockSampler(local) as clk:
         e0.record(stream)
-        run.propagate(K)
+        if pop is not None:
+            pop.run(K)
+        else:
+            run.propagate(K)
         e1.record(stream)
         stream.synchronize()
     torch.cuda.synchronize(dev)
@@ -460,7 +479,10 @@ def run_gpu(args, w: workloads.Workload):
     s_energy = (time.perf_counter() - t0) / n_e
     ms_total = max_over_ranks(ms_total, device=dev)
     info = run.info()
-    E, wsum = run.energy()
+    if pop is not None:
+        E, wsum = pop.energy()  # the whole population's estimator
+    else:
+        E, wsum = run.energy()
     run.close()
     del run
     torch.cuda.empty_cache()
@@ -492,6 +514,7 @@ def run_gpu(args, w: workloads.Workload):
                 clocks=clk.summary(), e2e_s=t_e2e, trial_converged=conv, trial_grad=grad,
                 h2d_bytes=h1.nbytes + L.nbytes + C.nbytes, world=ws, rank=rank, warmup=Wm,
                 ms_profiled=ms_profiled, s_energy=s_energy, graph=not args.no_graph,
+                sharded=sharded, pc_period=pc,
                 precision_report=prec_rep, fp64=fp64, bias=bias)
 
 
@@ -713,7 +736,9 @@ def cpu_sample(w: workloads.Workload, n_walkers=32, n_steps=3):
 
 def workload_desc(w: workloads.Workload) -> str:
     return (f"M={w.M} N_up=N_dn={w.N} nchol={w.nchol} walkers={w.nwalkers} dt={w.dt} "
-            f"qr/{w.qr_period} energy/{w.energy_period} taylor {w.taylor_order}")
+            f"qr/{w.qr_period} energy/{w.energy_period} taylor {w.taylor_order}; synthetic "
+            f"Hamiltonian, Cholesky amplitude {workloads.l_amplitude(w.M, w.nchol):.3g} "
+            f"(0.5 at M=12, scaled so that sum_g |L_g|_F^2 is the M=12 value)")
 
 
 def run_reference(args, w):
@@ -1080,6 +1105,9 @@ def main():
     ap.add_argument("--no-bias", action="store_true",
                     help="skip the run-level bias of the mixed precisions against float64")
     ap.add_argument("--ref-walkers", type=int, default=16)
+    ap.add_argument("--pc-period", type=int, default=None,
+                    help="steps between combs (default: the workload's, 0 = off); under "
+                         "torchrun the comb spans all ranks")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -1120,6 +1148,9 @@ def main():
         "dtype": DTYPES[args.precision],
         "data": "synthetic",
         "config": {"workload": workload_desc(w),
+                   "parallelism": (f"one population sharded over {N} GPUs ({w.nwalkers} "
+                                   f"walkers each; comb every {r['pc_period'] or 'never'}, "
+                                   "estimator summed over ranks)" if r["sharded"] else "1 GPU"),
                    "precision": args.precision, "l2": "inputs larger than L2 (packed L "
                    f"{w.M * (w.M + 1) // 2 * w.nchol * 8 / 1e6:.0f} MB float64)",
                    "trial": f"RHF (25 iterations, converged={r['trial_converged']}, "

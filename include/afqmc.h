@@ -296,6 +296,49 @@ AFQMC_API int afqmc_group_create(afqmc_state* const* states, int32_t n, void* st
 AFQMC_API int afqmc_group_propagate(afqmc_group* g, int32_t nsteps);
 AFQMC_API int afqmc_group_destroy(afqmc_group* g);
 
+/*
+ * One population sharded over several states (typically one per GPU, each in
+ * its own process).  Walkers are independent between population controls
+ * (Sec. 3.5), so each state steps its own n_s walkers, created with
+ * params.walker0 = the global index of its first walker (the fields are keyed
+ * by the global index), the same seed, and pc_period = 0; every p steps a
+ * host driver runs the comb of Sec. 3.4.4 over the whole population:
+ *   1. afqmc_export_weights: the state's n_s real weights into d_weights
+ *      (DEVICE float64 [n_s]); the driver gathers every state's weights, in
+ *      global walker order, into d_weights_all [n_all] on every state's device;
+ *   2. afqmc_comb_plan: on every state the same parents for all n_all new
+ *      slots, d_parent_all [n_all] (DEVICE int32 global walker indices; all -1
+ *      if no weight is left), with the single-state comb's arithmetic:
+ *      sequential float64 cumulative weights (d_cum [n_all], DEVICE scratch),
+ *      u from the Philox counter (0, 0xffffffff, step - 1, 0) of the seed,
+ *      tooth k = ((k + u) W_tot) / n_all, copies in walker order; W_tot is kept
+ *      in the state;
+ *   3. afqmc_pack_walkers / afqmc_unpack_walkers: the driver moves the
+ *      parents' rows (afqmc_walker_row_bytes each: Phi, Theta and the log
+ *      overlap in float64) to the states owning the new slots; unpack writes
+ *      them into its slots, sets their weight to W_tot / n_all and refreshes
+ *      the mixed path's operand copies.  Every slot of every state must be
+ *      written (rows of parents on the same state included), so a state's
+ *      own rows are packed before any unpack.
+ * With one state holding the whole population this reproduces the
+ * state's own comb (pc_period > 0) exactly.  afqmc_energy_sums copies the
+ * last estimator evaluation's sums (sum W Re E_loc, sum W, sum W Im E_loc /
+ * the imaginary parts for free projection, as afqmc_energy leaves them) to
+ * d_sums (DEVICE float64 [4]) for a reduction over states.  All calls are
+ * asynchronous on the state's stream; buffers are caller-owned.  Phaseless,
+ * single-determinant, no open back-propagation window (else
+ * AFQMC_EUNSUPPORTED).
+ */
+AFQMC_API int afqmc_walker_row_bytes(afqmc_state* s, size_t* bytes);
+AFQMC_API int afqmc_export_weights(afqmc_state* s, double* d_weights);
+AFQMC_API int afqmc_comb_plan(afqmc_state* s, const double* d_weights_all, int64_t n_all,
+                              double* d_cum, int32_t* d_parent_all);
+AFQMC_API int afqmc_pack_walkers(afqmc_state* s, const int32_t* d_index, int32_t n,
+                                 void* d_rows);
+AFQMC_API int afqmc_unpack_walkers(afqmc_state* s, const int32_t* d_slot, int32_t n,
+                                   const void* d_rows);
+AFQMC_API int afqmc_energy_sums(afqmc_state* s, double* d_sums);
+
 /* Release the host side of a state (the workspace stays the caller's). */
 AFQMC_API int afqmc_destroy(afqmc_state* s);
 

@@ -93,6 +93,9 @@ class Params:
     # "complex_is": importance sampling with the force bias and complex
     #               weights W <- W I, no phaseless projection (exact).
     mode: str = "phaseless"
+    # global index of walker 0: walker w draws the fields of walker walker0 + w
+    # (a population split over several oracles)
+    walker0: int = 0
 
 
 def wrap_phase(a):
@@ -311,7 +314,7 @@ class Oracle:
         if alive.size:
             phi = self.phi[alive]
             theta = self.theta[alive]
-            xi = philox.gaussian_fields(p.seed, k, alive, st.nchol)
+            xi = philox.gaussian_fields(p.seed, k, alive + p.walker0, st.nchol)
             if p.mode == "free":
                 xbar = np.zeros((alive.size, st.nchol), np.complex128)
             else:

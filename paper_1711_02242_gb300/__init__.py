@@ -41,7 +41,9 @@ EXPORTED = ["afqmc_default_params", "afqmc_workspace_size", "afqmc_init", "afqmc
             "afqmc_wait_flag", "afqmc_taylor_series", "afqmc_mcd_workspace_size",
             "afqmc_modified_cholesky", "afqmc_mcd_pairs_workspace_size",
             "afqmc_modified_cholesky_pairs", "afqmc_bp_begin", "afqmc_bp_end",
-            "afqmc_init_multidet", "afqmc_round_f32", "afqmc_widen_f32"]
+            "afqmc_init_multidet", "afqmc_round_f32", "afqmc_widen_f32",
+            "afqmc_walker_row_bytes", "afqmc_export_weights", "afqmc_comb_plan",
+            "afqmc_pack_walkers", "afqmc_unpack_walkers", "afqmc_energy_sums"]
 
 
 class Params(ctypes.Structure):
@@ -127,6 +129,12 @@ def lib():
                                                    dp, vp, ctypes.c_size_t, vp]),
         "afqmc_init_multidet": (ctypes.c_int, [P(Params), dp, dp, ctypes.c_int32, dp, dp, dp, vp,
                                                ctypes.c_size_t, vp, P(vp)]),
+        "afqmc_walker_row_bytes": (ctypes.c_int, [vp, P(ctypes.c_size_t)]),
+        "afqmc_export_weights": (ctypes.c_int, [vp, vp]),
+        "afqmc_comb_plan": (ctypes.c_int, [vp, vp, ctypes.c_int64, vp, vp]),
+        "afqmc_pack_walkers": (ctypes.c_int, [vp, vp, ctypes.c_int32, vp]),
+        "afqmc_unpack_walkers": (ctypes.c_int, [vp, vp, ctypes.c_int32, vp]),
+        "afqmc_energy_sums": (ctypes.c_int, [vp, vp]),
         "afqmc_bp_begin": (ctypes.c_int, [vp]),
         "afqmc_bp_end": (ctypes.c_int, [vp, dp, dp, dp, P(ctypes.c_int32)]),
         "afqmc_mcd_pairs_workspace_size": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32,

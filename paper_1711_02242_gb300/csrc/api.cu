@@ -270,7 +270,7 @@ int refresh_phi_lo(afqmc_state* s) {
 
 // The same for the operand copy of Theta (pitch Mp), which the Theta kernel
 // writes; the comb moves Theta without it.
-static int refresh_theta_lo(afqmc_state* s) {
+int refresh_theta_lo(afqmc_state* s) {
   const Bufs& b = s->b;
   if (!b.mixed) return AFQMC_OK;
   const afqmc_params& p = s->p;

@@ -112,6 +112,8 @@ struct afqmc_state {
   bool spin2 = false;
   int nup = 0;
   double sf = 2.0;
+  // population size of the last afqmc_comb_plan (sharded comb), 0 before one
+  int64_t comb_nall = 0;
 };
 
 namespace afq {
