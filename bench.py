@@ -551,10 +551,11 @@ def fp64_compare(w, p, h1, L, C, dev, stream, steps):
 
 class OracleSampler:
     """The oracle as it stands, stepping a bounded sample of the workload's
-    walkers.  At the M=300 scale the sampled walkers die within a step (their
-    weights overflow) and the oracle then skips them, so every timed step
-    starts again from the initial walkers: each timed step is a full step of
-    the sampled walkers (the set-up, like afqmc_init on the GPU, is untimed)."""
+    walkers: the first n_walkers walkers of the population (the oracle skips
+    the others, whose weight is set to 0) from the initial walkers, step after
+    step with the workload's Gram-Schmidt and energy periods, so that a run of
+    consecutive steps costs what the same steps of the whole walk cost per
+    walker.  The set-up, like afqmc_init on the GPU, is untimed."""
 
     def __init__(self, w: workloads.Workload, n_walkers: int):
         from oracle import afqmc
@@ -564,13 +565,9 @@ class OracleSampler:
                          energy_period=w.energy_period, taylor_order=w.taylor_order)
         self.orc = afqmc.Oracle(h1, L, C, w.nwalkers, p, H0=H0)
         self.orc.weight[n_walkers:] = 0.0  # the oracle skips zero-weight walkers
-        self.init = {k: getattr(self.orc, k).copy() for k in ("phi", "weight", "logdet", "theta")}
         self.n = n_walkers
 
     def step(self):
-        for k, v in self.init.items():
-            setattr(self.orc, k, v.copy())
-        self.orc.step_count = 0
         t0 = time.perf_counter()
         self.orc.step()
         return time.perf_counter() - t0
@@ -724,13 +721,15 @@ def bias_report(device=None, stream=None, c2_inputs=None):
     return rep
 
 
-def cpu_sample(w: workloads.Workload, n_walkers=32, n_steps=3):
-    """Oracle walker-steps/s on n_steps full steps of n_walkers walkers."""
+def cpu_sample(w: workloads.Workload, n_walkers=16, n_steps=10):
+    """Oracle walker-steps/s on the first n_steps steps (one energy evaluation
+    and two Gram-Schmidt passes at the M=300 periods) of n_walkers walkers."""
     s = OracleSampler(w, n_walkers)
     dt = sum(s.step() for _ in range(n_steps))
     cores = len(os.sched_getaffinity(0))
     return dict(value=n_walkers * n_steps / dt, unit="walker-steps/s", cores=cores, kind="oracle",
-                sample=f"{n_steps} full steps of {n_walkers} of the {w.nwalkers} walkers of the "
+                sample=f"steps 1-{n_steps} (Gram-Schmidt every {w.qr_period}, energy every "
+                       f"{w.energy_period}) of {n_walkers} of the {w.nwalkers} walkers of the "
                        f"M={w.M} workload (set-up untimed), numpy float64, {cores} host threads",
                 seconds=dt)
 
@@ -761,7 +760,9 @@ def run_reference(args, w):
         "config": {"workload": workload_desc(w), "sampled_walkers": sample,
                    "note": "the float64 oracle on the host cores, a bounded sample of the walkers"},
         "cpu_baseline": {"value": val, "unit": "walker-steps/s", "cores": cores, "kind": "oracle",
-                         "sample": f"{sample} walkers x {args.steps} steps per run"},
+                         "sample": f"{sample} walkers, steps {args.warmup + 1}-"
+                          f"{args.warmup + args.steps} of the walk (Gram-Schmidt every "
+                          f"{w.qr_period}, energy every {w.energy_period})"},
         "e2e": {"value": val, "unit": "walker-steps/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -1299,6 +1300,58 @@ def _case_md(a):
         run.close()
 
 
+def run_peaks(args):
+    """Dense float64 and float32 matrix-multiply throughput through PyTorch
+    (cuBLAS; TF32 off for float32), the counterpart of the driver's BF16
+    measurement for the FP64 and FP32 pipes: best of 5 after warm-up and 4 s
+    back to back, n^3 with n = 8192 (float64: 16384 for the sustained loop's
+    operands would not change the rate; 8192 keeps it short)."""
+    import torch
+
+    torch.backends.cuda.matmul.allow_tf32 = False
+    dev = torch.device("cuda", 0)
+    out = {}
+    for name, dt in (("fp64", torch.float64), ("fp32", torch.float32)):
+        n = 8192
+        a = torch.randn((n, n), dtype=dt, device=dev)
+        b = torch.randn((n, n), dtype=dt, device=dev)
+        c = torch.empty((n, n), dtype=dt, device=dev)
+        for _ in range(3):
+            torch.matmul(a, b, out=c)
+        torch.cuda.synchronize()
+        best = float("inf")
+        for _ in range(5):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.matmul(a, b, out=c)
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        reps, t0 = 0, time.perf_counter()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(0) as clk:
+            e0.record()
+            while time.perf_counter() - t0 < 4.0:
+                for _ in range(4):
+                    torch.matmul(a, b, out=c)
+                reps += 4
+                torch.cuda.synchronize()
+            e1.record()
+            torch.cuda.synchronize()
+        sus = e0.elapsed_time(e1) / reps
+        out[name] = {"n": n, "burst_tflops": 2 * n ** 3 / (best * 1e-3) / 1e12,
+                     "sustained_tflops": 2 * n ** 3 / (sus * 1e-3) / 1e12,
+                     "clocks": clk.summary()}
+        del a, b, c
+        torch.cuda.empty_cache()
+    derived = {"fp64": FP64_PEAK_TFLOPS, "fp32": FP32_PEAK_TFLOPS}
+    for k in out:
+        out[k]["derived_tflops"] = derived[k]
+        out[k]["frac_of_derived"] = out[k]["burst_tflops"] / derived[k]
+    print(json.dumps({"metric": "dense GEMM TFLOP/s (torch.matmul, cuBLAS)", "peaks": out}))
+    return 0
+
+
 def dataclasses_replace(r):
     import dataclasses
 
@@ -1308,7 +1361,7 @@ def dataclasses_replace(r):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="c2",
-                    choices=["c2", "batched", "serve", "mcd", "bias", "case"],
+                    choices=["c2", "batched", "serve", "mcd", "bias", "case", "peaks"],
                     help="c2: the M=300 walker-steps/s line; batched / serve: the grouped and "
                          "served forms; mcd: the modified Cholesky decomposition of the "
                          "workload's interaction (their own JSON lines)")
@@ -1355,6 +1408,8 @@ def main():
         return run_serve(args)
     if args.workload == "mcd":
         return run_mcd(args)
+    if args.workload == "peaks":
+        return run_peaks(args)
     if args.workload == "case":
         _case_main(args)
         return 0

@@ -201,3 +201,96 @@ def test_two_identical_blocks_are_the_closed_shell_walk():
     ea = np.array([r[1] / r[2] for r in a.records])
     eb = np.array([r[1] / r[2] for r in b.records])
     assert np.max(np.abs(eb - ea) / np.abs(ea)) < 1e-12
+
+
+def test_real_propagator_projection_is_the_constrained_path():
+    """P9 (Sec. 3.3, the constrained-path limit): with a real propagator the
+    overlap ratio R is real, so max(0, cos Arg R) is 1 or 0 and the phaseless
+    weight update becomes the constrained path: a walker whose overlap with
+    the trial changes sign is removed, the others are multiplied by R.  No
+    two-body term (L = 0: no fields, no force bias, B = exp(-dt h)), real
+    two-block walkers near a node of the spin-up overlap (with a closed-shell
+    walker det(S)^2 could never change sign).  R from scipy's expm of h."""
+    M, dt = 4, 0.1
+    rng = np.random.default_rng(3)
+    h = rng.standard_normal((M, M))
+    h = 0.5 * (h + h.T)
+    h[0, 1] = h[1, 0] = 2.0
+    L = np.zeros((1, M, M))
+    Vu, Vd = np.eye(M)[:, :1], np.eye(M)[:, 1:2]
+    B = sla.expm(-dt * h)
+    eps = np.array([0.05, 1.0, -0.02, 0.6])  # spin-up overlaps near and far from the node
+    phi = np.zeros((eps.size, M, 2))
+    phi[:, 0, 0] = eps
+    phi[:, 1, 0] = 1.0
+    phi[:, 2, 1] = 1.0
+    phi[:, 1, 1] = 0.3
+    p = afqmc.Params(dt=dt, taylor_order=4, qr_period=0, energy_period=0, fb_cap=-1.0,
+                     wmax=1e300, seed=1)
+    o = afqmc.Oracle(h, L, Vu, eps.size, p, phi0=phi.astype(complex), trial_dn=Vd)
+    e_shift = o.e_shift
+    o.step()
+    flips = 0
+    for w in range(eps.size):
+        up, dn = B @ phi[w][:, :1], B @ phi[w][:, 1:]
+        R = (np.linalg.det(Vu.T @ up) * np.linalg.det(Vd.T @ dn)
+             / (np.linalg.det(Vu.T @ phi[w][:, :1]) * np.linalg.det(Vd.T @ phi[w][:, 1:])))
+        R *= math.exp(-dt * (0.0 - e_shift))
+        if R < 0:
+            flips += 1
+            assert o.weight[w] == 0.0
+        else:
+            assert abs(o.weight[w] - R) < 1e-12 * R
+    assert 0 < flips < eps.size
+
+
+def test_trotter_error_of_the_energy_falls_as_dt_squared():
+    """P12 (Sec. 3.3: the Trotter error is O(dt^2)): the oracle's step averaged
+    exactly over its field (one Cholesky vector, Gauss-Hermite quadrature)
+    is a Fock-space operator T(dt); the energy <Psi_T|H T^n|Psi_T> /
+    <Psi_T|T^n|Psi_T> at beta = n dt = 1 approaches the exact
+    <Psi_T|H e^(-beta H)|Psi_T> / <Psi_T|e^(-beta H)|Psi_T> with an error that
+    falls 4x per halving of dt.  Two spin blocks (N_up = 2, N_dn = 1), so T
+    is built on every determinant of the sector, spin-up and spin-down
+    orbitals differing."""
+    M_, nu, nd, G_ = 4, 2, 1, 1
+    h1, L, _ = workloads.hamiltonian(M_, G_, 31)
+    L = 1.5 * L
+    rng = np.random.default_rng(31)
+    Vu = np.linalg.qr(rng.standard_normal((M_, nu)))[0]
+    Vd = np.linalg.qr(rng.standard_normal((M_, nd)))[0]
+    F = Fock(M_)
+    H = F.hamiltonian(h1, eri_from_cholesky(L), 0.0).toarray()
+    sec = F.number_sector(nu, nd)
+    Hs = H[np.ix_(sec, sec)]
+    psiT = F.determinant(Vu, Vd)[sec]
+    xk, wk = np.polynomial.hermite_e.hermegauss(30)
+    wk = wk / math.sqrt(2 * math.pi)
+    dets = [(np.eye(M_)[:, list(u)], np.eye(M_)[:, list(d)])
+            for u in itertools.combinations(range(M_), nu)
+            for d in itertools.combinations(range(M_), nd)]
+
+    def field_averaged_step(dt):
+        st = afqmc.Setup(h1, L, Vu, 0.0, dt=dt, trial_dn=Vd)
+        U = np.zeros((sec.size, len(dets)), complex)
+        TU = np.zeros_like(U)
+        for b, (Pu, Pd) in enumerate(dets):
+            phi = np.concatenate([Pu, Pd], 1).astype(complex)
+            U[:, b] = F.determinant(Pu, Pd)[sec]
+            for x, wx in zip(xk, wk):
+                xv = np.array([x], complex)
+                V = afqmc.assemble_V(st, xv[None])
+                phi1 = st.Bhalf @ afqmc.taylor(V, (st.Bhalf @ phi)[None], 40)[0]
+                scal = math.exp(-dt * st.H0p) * np.exp(-1j * math.sqrt(dt) * (xv @ st.c))
+                TU[:, b] += wx * scal * F.determinant(phi1[:, :nu], phi1[:, nu:])[sec]
+        return TU @ np.linalg.inv(U)
+
+    ev, Us = np.linalg.eigh(Hs)
+    pb = Us @ (np.exp(-(ev - ev[0])) * (Us.conj().T @ psiT))
+    exact = ((psiT.conj() @ Hs @ pb) / (psiT.conj() @ pb)).real
+    errs = []
+    for dt in (0.1, 0.05, 0.025):
+        v = np.linalg.matrix_power(field_averaged_step(dt), int(round(1.0 / dt))) @ psiT
+        errs.append(abs(((psiT.conj() @ Hs @ v) / (psiT.conj() @ v)).real - exact))
+    assert 3.5 < errs[0] / errs[1] < 4.8 and 3.5 < errs[1] / errs[2] < 4.8
+    assert errs[2] < 1e-3
