@@ -721,9 +721,10 @@ def bias_report(device=None, stream=None, c2_inputs=None):
     return rep
 
 
-def cpu_sample(w: workloads.Workload, n_walkers=16, n_steps=10):
-    """Oracle walker-steps/s on the first n_steps steps (one energy evaluation
-    and two Gram-Schmidt passes at the M=300 periods) of n_walkers walkers."""
+def cpu_sample(w: workloads.Workload, n_walkers=16, n_steps=20):
+    """Oracle walker-steps/s on the first n_steps steps (two energy
+    evaluations and four Gram-Schmidt passes at the M=300 periods, about 12 s
+    on 16 Grace cores) of n_walkers walkers."""
     s = OracleSampler(w, n_walkers)
     dt = sum(s.step() for _ in range(n_steps))
     cores = len(os.sched_getaffinity(0))

@@ -141,42 +141,11 @@ def test_local_energies_random_walkers(pkg):
 ])
 def test_ragged_shapes_match_oracle(pkg, shape):
     w = workloads.Workload("edge", seed=11, ham_seed=500 + shape["M"], qr_period=2, **shape)
-    # half-filled N=33 of M=65 with full-size vectors makes S = V_T^T Phi
-    # ill-conditioned within a few steps (|Phi| ~ 700, cond(S) ~ 1e6), which
-    # amplifies rounding beyond 1e-10 on either side; weaker vectors keep the
-    # comparison about the kernels
-    orc, run = make_pair(pkg, w, lscale=0.25 if shape["N"] > 32 else 1.0)
+    orc, run = make_pair(pkg, w)
     for _ in range(6):
         run.propagate(1)
         orc.step()
         compare_state(run, orc)
-
-
-def test_half_filled_n33_at_full_strength_within_conditioning(pkg):
-    """N=33 of M=65 with the full-strength vectors: S = V_T^T Phi grows
-    ill-conditioned within a few steps, and rounding (on either side) is
-    amplified by cond(S).  Each walker is held to 1e-10 + 1e-14 cond(S_w), the
-    forward error of the overlap, its inverse and Theta at about 50 x eps
-    cond(S)."""
-    shape = dict(M=65, N=33, nchol=40, nwalkers=2)
-    w = workloads.Workload("edge", seed=11, ham_seed=565, qr_period=2, **shape)
-    orc, run = make_pair(pkg, w)
-    worst = 0.0
-    for _ in range(6):
-        run.propagate(1)
-        orc.step()
-        phi, wt, lo = run.get_walkers()
-        alive = np.nonzero(orc.weight != 0)[0]
-        assert np.array_equal(np.nonzero(wt != 0)[0], alive)
-        for k in alive:
-            S = orc.setup.VT.T @ orc.phi[k]
-            tol = 1e-10 + 1e-14 * np.linalg.cond(S)
-            worst = max(worst, np.linalg.cond(S))
-            d = np.linalg.norm(phi[k] - orc.phi[k]) / np.linalg.norm(orc.phi[k])
-            assert d < tol
-            assert abs(wt[k] - orc.weight[k]) / abs(orc.weight[k]) < tol
-            assert abs(lo[k].real - orc.logdet[k].real) / (1 + abs(orc.logdet[k].real)) < tol
-    assert worst > 1e3  # the case this test exists for
 
 
 def test_free_projection_matches_oracle(pkg):
