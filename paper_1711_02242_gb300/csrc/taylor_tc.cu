@@ -9,7 +9,9 @@
 // memory, streams only V (from L2 after the first term) and writes S once.
 //
 //   A operand  [Re V | Im V] rows p of walker w (128-row tiles, K = 2 Mp),
-//              TMA ring of 256 x 128-byte boxes (two 128-row MMA tiles each);
+//              TMA ring whose stage is one 128-byte K block of every p-tile
+//              (one 128-row box per tile), so that each stage feeds the MMAs
+//              of all p-tiles, interleaved over independent accumulators;
 //   B operand  the term T_{k-1} as K-major rows, NH = N rounded up to 16:
 //                 row i      = [Re T_i | -Im T_i]   (i < N)
 //                 row NH + i = [Im T_i |  Re T_i]
@@ -40,8 +42,7 @@
 namespace afq {
 namespace tc {
 
-constexpr int kVRows = 2 * BM;   // rows of one V box: two 128-row MMA tiles
-constexpr int kVBox = kVRows * BKB;  // one V box in the ring: 256 rows x 128 bytes
+constexpr int kVBox = BM * BKB;   // one V box: a 128-row p-tile x 128 bytes of K
 constexpr int kEpiWarps = 8;      // epilogue warps (2 per TMEM lane quarter)
 constexpr int kEpiThreads = 32 * kEpiWarps;
 constexpr int kSeriesThreads = 64 + kEpiThreads;
@@ -54,8 +55,7 @@ struct SeriesArgs {
   int nb;       // 2 nh = MMA N
   int kblocks;  // 128-byte K blocks covering 2 Mp
   int ptiles;   // 128-row tiles covering p < M
-  int btiles;   // 256-row V boxes covering p < M
-  int stages;   // depth of the V ring
+  int stages;   // depth of the V ring (a stage: one K block of every p-tile)
   uint32_t tcols;
 };
 
@@ -103,7 +103,8 @@ __global__ void __launch_bounds__(kSeriesThreads, 1)
   const uint32_t opk = (uint32_t)a.nb * BKB;  // bytes of one K block of the term operand
   uint8_t* bop = smem;
   uint8_t* ring = smem + (size_t)a.kblocks * opk;
-  uint64_t* full = reinterpret_cast<uint64_t*>(ring + (size_t)a.stages * kVBox);
+  const uint32_t stage_bytes = (uint32_t)a.ptiles * kVBox;
+  uint64_t* full = reinterpret_cast<uint64_t*>(ring + (size_t)a.stages * stage_bytes);
   uint64_t* empty = full + a.stages;
   uint64_t* bfull = empty + a.stages;  // T_0 of the walker has landed
   uint64_t* bfree = bfull + 1;         // the walker's last MMAs are done: operand space free
@@ -143,7 +144,8 @@ __global__ void __launch_bounds__(kSeriesThreads, 1)
   if (warp == 0 && lane == 0) {
     // producer: per walker T_0 once (rows (c, i) -> c NH + i by a 4-D box),
     // then the V tiles of every term
-    int it = 0, j = 0;
+    int it = 0, j = 0, s = 0;
+    uint32_t ph = 0;  // ring slot s and its fill round's parity, kept incrementally
     bool stop = false;
     for (int w = blockIdx.x; w < a.W && !stop; w += gridDim.x, ++j) {
       if (j > 0 && !mbar_wait(bfree, (j - 1) & 1, err, 31)) {
@@ -154,23 +156,26 @@ __global__ void __launch_bounds__(kSeriesThreads, 1)
       for (int kb = 0; kb < a.kblocks; ++kb)
         tma_load_4d(bop + kb * opk, &tmT, bfull, kb * BK, 0, 0, w);
       for (int k = 1; k <= a.order && !stop; ++k)
-        for (int bt = 0; bt < a.btiles && !stop; ++bt)
-          for (int kb = 0; kb < a.kblocks; ++kb, ++it) {
-            const int s = it % a.stages;
-            if ((it >= a.stages && !mbar_wait(&empty[s], ((it / a.stages) - 1) & 1, err, 32)) ||
-                *abort_flag) {
-              stop = true;
-              break;
-            }
-            mbar_expect_tx(&full[s], kVBox);
-            tma_load_3d(ring + s * kVBox, &tmV, &full[s], kb * BK, bt * kVRows, w);
+        for (int kb = 0; kb < a.kblocks; ++kb, ++it) {
+          if ((it >= a.stages && !mbar_wait(&empty[s], ph ^ 1u, err, 32)) || *abort_flag) {
+            stop = true;
+            break;
           }
+          mbar_expect_tx(&full[s], stage_bytes);
+          for (int pt = 0; pt < a.ptiles; ++pt)
+            tma_load_3d(ring + s * stage_bytes + pt * kVBox, &tmV, &full[s], kb * BK, pt * BM, w);
+          if (++s == a.stages) {
+            s = 0;
+            ph ^= 1u;
+          }
+        }
     }
     if (stop) *abort_flag = 1;
   } else if (warp == 1 && lane == 0) {
     // MMA thread
     const uint32_t idesc = instr_desc(TF32 ? 2u : 1u, (uint32_t)a.nb);
-    int it = 0, g = 0, j = 0;
+    int g = 0, j = 0, s = 0;
+    uint32_t ph = 0;
     bool stop = false;
     for (int w = blockIdx.x; w < a.W && !stop; w += gridDim.x, ++j) {
       for (int k = 1; k <= a.order; ++k, ++g) {
@@ -180,30 +185,29 @@ __global__ void __launch_bounds__(kSeriesThreads, 1)
           break;
         }
         fence_after();
-        // one box = the 128-row p-tiles 2 bt and 2 bt + 1 (the second absent
-        // past the last p-tile)
-        for (int bt = 0; bt < a.btiles && !stop; ++bt) {
-          for (int kb = 0; kb < a.kblocks; ++kb, ++it) {
-            const int s = it % a.stages;
-            if (!mbar_wait(&full[s], (it / a.stages) & 1, err, 35)) {
-              *abort_flag = 1;
-              stop = true;
-              break;
-            }
-            fence_after();
-            const uint32_t av = smem_u32(ring + s * kVBox);
-            const uint32_t bv = smem_u32(bop + kb * opk);
+        // one stage = one K block of every p-tile: the p-tiles' MMAs are
+        // interleaved (independent accumulators)
+        for (int kb = 0; kb < a.kblocks; ++kb) {
+          if (!mbar_wait(&full[s], ph, err, 35)) {
+            *abort_flag = 1;
+            stop = true;
+            break;
+          }
+          fence_after();
+          const uint32_t av = smem_u32(ring + s * stage_bytes);
+          const uint32_t bv = smem_u32(bop + kb * opk);
 #pragma unroll
-            for (int kk = 0; kk < KSTEPS; ++kk)
+          for (int kk = 0; kk < KSTEPS; ++kk)
 #pragma unroll
-              for (int sub = 0; sub < 2; ++sub) {
-                const int pt = 2 * bt + sub;
-                if (pt < a.ptiles)
-                  mma<TF32>(tmem + (uint32_t)(pt * a.nb),
-                            sw128_desc(av + (uint32_t)(sub * BM * BKB) + 32 * kk),
-                            sw128_desc(bv + 32 * kk), idesc, (kb > 0 || kk > 0) ? 1u : 0u);
-              }
-            mma_commit(&empty[s]);
+            for (int pt = 0; pt < 4; ++pt)
+              if (pt < a.ptiles)
+                mma<TF32>(tmem + (uint32_t)(pt * a.nb),
+                          sw128_desc(av + (uint32_t)(pt * kVBox) + 32 * kk),
+                          sw128_desc(bv + 32 * kk), idesc, (kb > 0 || kk > 0) ? 1u : 0u);
+          mma_commit(&empty[s]);
+          if (++s == a.stages) {
+            s = 0;
+            ph ^= 1u;
           }
         }
         mma_commit(dfull);
@@ -224,7 +228,7 @@ __global__ void __launch_bounds__(kSeriesThreads, 1)
     bool stop = false;
     for (int w = blockIdx.x; w < a.W && !stop; w += gridDim.x) {
       for (int k = 1; k <= a.order; ++k, ++g) {
-        bool bad = !mbar_wait(dfull, g & 1, err, 36) || *abort_flag;
+        bool bad = !mbar_wait_sleep(dfull, g & 1, err, 36) || *abort_flag;
         fence_after();
         if (epi_sync_or(bad)) {
           stop = true;
@@ -310,10 +314,10 @@ bool series_plan(int lo_kind, int N, int M, int Mp, tc::SeriesArgs* sa, int* sme
   const int kblocks = (2 * Mp * elem + tc::BKB - 1) / tc::BKB;
   const int ptiles = (M + tc::BM - 1) / tc::BM;
   // the product and the running sum side by side in tensor memory
-  if (nb > 256 || 2 * ptiles * nb > 512) return false;
+  if (nb > 256 || 2 * ptiles * nb > 512 || ptiles > 4) return false;
   const long op = (long)kblocks * nb * tc::BKB;
   long room = kSmemMax - kSmemFixed - op;
-  int stages = (int)(room / tc::kVBox);
+  int stages = (int)(room / ((long)ptiles * tc::kVBox));
   if (stages > 8) stages = 8;
   if (stages < 2) return false;
   uint32_t tcols = 32;
@@ -323,11 +327,10 @@ bool series_plan(int lo_kind, int N, int M, int Mp, tc::SeriesArgs* sa, int* sme
     sa->nb = nb;
     sa->kblocks = kblocks;
     sa->ptiles = ptiles;
-    sa->btiles = (ptiles + 1) / 2;
     sa->stages = stages;
     sa->tcols = tcols;
   }
-  if (smem) *smem = (int)(op + (long)stages * tc::kVBox + kSmemFixed);
+  if (smem) *smem = (int)(op + (long)stages * ptiles * tc::kVBox + kSmemFixed);
   return true;
 }
 }  // namespace
@@ -355,7 +358,7 @@ int tc_taylor_series(const void* V, const void* T0, float* S, long lds, int lo_k
   const bool tf32 = lo_kind == LO_TF32;
   const int eb = tf32 ? 4 : 2;
   CUtensorMap tv, tt;
-  AFQ_TRY(make_tmap_3d(&tv, V, eb, W, M, 2L * Mp, 2L * Mp, (long)M * 2 * Mp, tc::kVRows));
+  AFQ_TRY(make_tmap_3d(&tv, V, eb, W, M, 2L * Mp, 2L * Mp, (long)M * 2 * Mp, tc::BM));
   // T0 rows (w, c, i) -> operand rows c NH + i: dims (K, i, c, w), box (K block, NH, 2, 1)
   const long tdims[4] = {2L * Mp, N, 2, W};
   const long tstr[3] = {2L * Mp * eb, (long)N * 2 * Mp * eb, 2L * N * 2 * Mp * eb};

@@ -43,6 +43,18 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* e
   return false;
 }
 
+// The same for waits expected to last long (an epilogue waiting for a whole
+// term of MMAs): after a failed poll the thread sleeps briefly, so that the
+// polling warps leave the issue slots to the MMA and TMA threads.
+__device__ __forceinline__ bool mbar_wait_sleep(uint64_t* bar, uint32_t parity, int* err, int code) {
+  for (uint32_t i = 0; i < (1u << 21); ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    __nanosleep(64);
+  }
+  atomicCAS(err, 0, code);
+  return false;
+}
+
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x,
                                             int y) {
   asm volatile(
