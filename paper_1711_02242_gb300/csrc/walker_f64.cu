@@ -830,63 +830,78 @@ __global__ void __launch_bounds__(256) k_mgs(MgsArgs a) {
   if (threadIdx.x == 0 && a.ld) a.ld[2L * w] -= a.sf * (sh[0] + sh[1]);
 }
 
-// _F32LU mixed precisions: the same sweep in FP32 with the walker's orbitals resident in
-// shared memory ([N][M] complex, read once from and written once to the
-// float64 orbitals), one warp per later column and lanes over p (contiguous,
-// conflict-free).  The orbitals only feed the BF16/TF32 propagation and the
-// float64 overlap, which is recomputed from the stored Q; the FP32 norms give
-// log det R to ~1e-7 relative.  Used when 8 N M bytes fit the block.
+// Mixed precisions: the same sweep in FP32 with the walker's orbitals resident
+// in shared memory ([N][M] complex, read once from and written once to the
+// float64 orbitals).  With two spin blocks the blocks are independent sweeps
+// and run side by side, one half of the warps each; within a block one warp
+// per later column, lanes over p (contiguous, conflict-free).  The orbitals
+// only feed the low-precision propagation and the overlap, whose float64 log
+// det is lowered by the FP32 norms' sum of logs.
 __global__ void __launch_bounds__(256) k_mgs_f32(MgsArgs a) {
   extern __shared__ float2 v_sm[];  // [N][M]
   __shared__ float red[8];
-  __shared__ float inv_sh;
+  __shared__ float inv_sh[2];
   __shared__ double norms[64];
+  __shared__ double sh[2];
   const int w = blockIdx.x;
   if (!walker_alive(a.wt, w)) return;
   const int M = a.M, N = a.N, NM = M * N;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // group g of wpg warps sweeps columns [c0, c1): the whole set, or spin block g
+  const int ng = a.nup > 0 ? 2 : 1;
+  const int wpg = 8 / ng;
+  const int g = warp / wpg, gw = warp - g * wpg, gt = gw * 32 + lane;
+  const int c0 = g == 0 ? 0 : a.nup;
+  const int c1 = (ng == 2 && g == 0) ? a.nup : N;
+  const int nk = ng == 2 ? (a.nup > N - a.nup ? a.nup : N - a.nup) : N;
   double* re = a.phiT + (long)w * 2 * NM;
   double* im = re + NM;
   for (int e = threadIdx.x; e < NM; e += blockDim.x)
     v_sm[e] = make_float2(f64_to_f32(re[e]), f64_to_f32(im[e]));
   __syncthreads();
-  for (int k = 0; k < N; ++k) {
-    float2* vk = v_sm + k * M;
+  for (int k = 0; k < nk; ++k) {
+    const int col = c0 + k;
+    const bool live = col < c1;
+    float2* vk = v_sm + (long)(live ? col : c0) * M;
     float nn = 0.f;
-    for (int p = threadIdx.x; p < M; p += blockDim.x) nn = fmaf(vk[p].x, vk[p].x, fmaf(vk[p].y, vk[p].y, nn));
+    if (live)
+      for (int p = gt; p < M; p += 32 * wpg) nn = fmaf(vk[p].x, vk[p].x, fmaf(vk[p].y, vk[p].y, nn));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) nn += __shfl_xor_sync(0xffffffffu, nn, o);
     if (lane == 0) red[warp] = nn;
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (live && gt == 0) {
       float t = 0.f;
-      for (int q = 0; q < 8; ++q) t += red[q];
-      norms[k] = (double)t;
-      inv_sh = 1.f / sqrtf(t);
+      for (int q = 0; q < wpg; ++q) t += red[g * wpg + q];
+      norms[col] = (double)t;
+      inv_sh[g] = 1.f / sqrtf(t);
     }
     __syncthreads();
-    const float inv = inv_sh;
-    for (int p = threadIdx.x; p < M; p += blockDim.x) vk[p] = make_float2(vk[p].x * inv, vk[p].y * inv);
+    if (live) {
+      const float inv = inv_sh[g];
+      for (int p = gt; p < M; p += 32 * wpg) vk[p] = make_float2(vk[p].x * inv, vk[p].y * inv);
+    }
     __syncthreads();
-    // v_j -= <q_k|v_j> q_k for every later column j, one warp per column
-    for (int j = k + 1 + warp; j < N; j += 8) {
-      float2* vj = v_sm + j * M;
-      float sr = 0.f, si = 0.f;
-      for (int p = lane; p < M; p += 32) {
-        const float2 q = vk[p], v = vj[p];
-        sr = fmaf(q.x, v.x, fmaf(q.y, v.y, sr));
-        si = fmaf(q.x, v.y, fmaf(-q.y, v.x, si));
-      }
+    // v_j -= <q_k|v_j> q_k for every later column j of the block, one warp per column
+    if (live)
+      for (int j = col + 1 + gw; j < c1; j += wpg) {
+        float2* vj = v_sm + j * M;
+        float sr = 0.f, si = 0.f;
+        for (int p = lane; p < M; p += 32) {
+          const float2 q = vk[p], v = vj[p];
+          sr = fmaf(q.x, v.x, fmaf(q.y, v.y, sr));
+          si = fmaf(q.x, v.y, fmaf(-q.y, v.x, si));
+        }
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        sr += __shfl_xor_sync(0xffffffffu, sr, o);
-        si += __shfl_xor_sync(0xffffffffu, si, o);
+        for (int o = 16; o > 0; o >>= 1) {
+          sr += __shfl_xor_sync(0xffffffffu, sr, o);
+          si += __shfl_xor_sync(0xffffffffu, si, o);
+        }
+        for (int p = lane; p < M; p += 32) {
+          const float2 q = vk[p], v = vj[p];
+          vj[p] = make_float2(fmaf(-sr, q.x, fmaf(si, q.y, v.x)), fmaf(-sr, q.y, fmaf(-si, q.x, v.y)));
+        }
       }
-      for (int p = lane; p < M; p += 32) {
-        const float2 q = vk[p], v = vj[p];
-        vj[p] = make_float2(fmaf(-sr, q.x, fmaf(si, q.y, v.x)), fmaf(-sr, q.y, fmaf(-si, q.x, v.y)));
-      }
-    }
     __syncthreads();
   }
   for (int e = threadIdx.x; e < NM; e += blockDim.x) {
@@ -901,7 +916,6 @@ __global__ void __launch_bounds__(256) k_mgs_f32(MgsArgs a) {
     }
   }
   // log det R = sum_k log |v_k|, as in k_mgs
-  __shared__ double sh[2];
   double lr = threadIdx.x < N ? 0.5 * log(norms[threadIdx.x]) : 0.0;
   if (threadIdx.x < 64) {
 #pragma unroll
@@ -909,7 +923,7 @@ __global__ void __launch_bounds__(256) k_mgs_f32(MgsArgs a) {
     if (lane == 0) sh[warp] = lr;
   }
   __syncthreads();
-  if (threadIdx.x == 0 && a.ld) a.ld[2L * w] -= 2.0 * (sh[0] + sh[1]);
+  if (threadIdx.x == 0 && a.ld) a.ld[2L * w] -= a.sf * (sh[0] + sh[1]);
 }
 
 int launch_mgs(const MgsArgs& a, cudaStream_t st) {
