@@ -188,10 +188,17 @@ AFQMC_API int afqmc_init(const afqmc_params* p, const double* h1, const double* 
  * energy are the determinant-weighted sums of Eqs. precomputing2 and
  * localenergy3; the mean-field background comes from determinant 0,
  * c_g = Tr(L_g (P_0u + P_0d)), and E_T is the local energy of the initial
- * walkers.  Either precision: the mixed paths run the per-determinant
- * force-bias traces and exchange on the tensor cores (BF16/TF32 operands)
- * and keep overlaps, weights and their combinations in float64.  Phaseless,
- * population control off, no back-propagation window (else
+ * walkers.  When ndet >= 2, N <= 32 and every determinant differs from
+ * determinant 0 in at most 4 columns per spin (the other columns equal, in
+ * the same positions: a CI expansion about determinant 0), the determinants
+ * are evaluated relative to determinant 0 by low-rank updates (the
+ * Sherman-Morrison-Woodbury remark of Sec. 3.4) in float64 on either
+ * precision; that form stays finite where a determinant's overlap with a
+ * walker vanishes.  Otherwise each determinant is evaluated in full, the
+ * mixed paths running its force-bias traces and exchange on the tensor
+ * cores (BF16/TF32 operands) with overlaps, weights and their combinations
+ * in float64; a determinant orthogonal to a walker then gets weight 0.
+ * Phaseless, population control off, no back-propagation window (else
  * AFQMC_EUNSUPPORTED).  Everything else as afqmc_init.
  */
 AFQMC_API int afqmc_init_multidet(const afqmc_params* p, const double* h1, const double* L,

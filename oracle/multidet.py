@@ -36,10 +36,8 @@ Readings (the paper leaves them open):
     the method is meant for non-orthogonal determinants (e.g. different
     rotations of a reference), not for CI expansions about the walkers' own
     determinant.
-  * the Sherman-Morrison-Woodbury evaluation relative to a reference
-    determinant (which resolves those limits and is faster for determinants
-    that differ by a few orbitals) is not used: every determinant is handled
-    in full.
+  * every determinant is handled in full here; the evaluation relative to
+    a reference determinant, which resolves those limits, is oracle.smw.
 
 The walk itself (fields, propagation, phaseless weights, Gram-Schmidt, energy
 records) follows oracle.afqmc.Oracle step for step.

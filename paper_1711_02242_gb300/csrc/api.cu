@@ -94,6 +94,12 @@ size_t plan(const afqmc_params& p, Bufs* b, char* base) {
     b->md_C = a.take<double>(nd2 * 2 * W * G);
     b->md_part = a.take<double>(nd2 * W * nchunk * 2);
     b->md_logA = a.take<double>(nd2);
+    const size_t ks = (size_t)kSmwMaxK * p.ndet;
+    const size_t nchk = (G + kSmwGC - 1) / kSmwGC;
+    b->smw_tab = a.take<int>(nd2 * 8);
+    b->smw_prow = a.take<int>(2 * ks);
+    b->smw_xi = a.take<double>(W * 2 * ks * N * 2);
+    b->smw_part = a.take<double>(W * (nchk + 1) * p.ndet * 2);
     if (mixed) {
       b->md_theta_lo = a.take<char>(nd2 * W * 2 * N * Mp * lo);
       b->md_Lh_lo = a.take<char>(nd2 * G * N * Mp * lo);
@@ -820,6 +826,7 @@ static int setup_device(afqmc_state* s, const double* h1, const double* L, const
     AFQ_CUDA(cudaMemcpyAsync(b.md_V, mv.data(), sizeof(double) * mv.size(),
                              cudaMemcpyHostToDevice, st));
     AFQ_CUDA(cudaStreamSynchronize(st));
+    AFQ_TRY(smw_detect(s, md_up, md_dn));
   }
   for (int r = 0; r < M; ++r)
     for (int c = 0; c < M; ++c) qt[(size_t)c * M + r] = qh[(size_t)r * M + c];

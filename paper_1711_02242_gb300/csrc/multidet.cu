@@ -14,10 +14,33 @@
 // On the mixed path the traces and the exchange of each (d, s) run on the
 // tensor cores from BF16/TF32 copies of Lh_ds and Theta_ds (written by the
 // overlap kernel); overlaps, weights and the combinations stay float64.
-// Every determinant is handled in full (the Sherman-Morrison-Woodbury
-// shortcut for determinants differing by a few orbitals is not used).  All in
-// the run's orthonormal basis, whose first N vectors are the leading spin-up
-// determinant's orbitals.
+// All in the run's orthonormal basis, whose first N vectors are the leading
+// spin-up determinant's orbitals.
+//
+// Determinants that differ from determinant 0 in at most kSmwMaxK columns per
+// spin (the other columns equal, in place: a CI expansion about a reference)
+// are evaluated relative to it in float64 (on either path), as the
+// Sherman-Morrison-Woodbury remark of Sec. 3.4 suggests.  With S_0s = V_0s^T phi, Theta_0s =
+// phi S_0s^-1 and, for a one-body X, Y = V_ds^T X Theta_0s, determinant d
+// enters through the polynomial
+//   det(M_ds + e Y) = r_ds + e c1_ds(X) + e^2 c2_ds(X) + ...,  M_ds = V_ds^T Theta_0s,
+// r_ds = det(V_ds^T phi) / det S_0s, c1 = r Tr(X G_ds), 2 c2 = r [Tr(X G_ds)^2 -
+// Tr(X G_ds X G_ds)] (G_ds determinant d's Green's function), which stay
+// finite where det(V_ds^T phi) = 0 (the limits the full evaluation cannot
+// take).  M_ds is the identity but for the rows of the holes H (column h_l
+// of V_0s replaced by the particle u_l): with Xi = U^T Theta_0s (rows u_l),
+// Y0 = V_0s^T X Theta_0s and Yp = U^T X Theta_0s, reordering H first and
+// taking the Schur complement of the unit block,
+//   det(M + e Y) = det(I + e Z) det(P + e S1 + e^2 S2) + O(e^3),
+//   P = Xi[:, H],  Z = Y0[Hc, Hc],
+//   S1 = Yp[:, H] - Xi[:, Hc] Y0[Hc, H],
+//   S2 = Xi[:, Hc] Z Y0[Hc, H] - Yp[:, Hc] Y0[Hc, H],
+// and det(P + e S1 + e^2 S2) = p0 + e p1 + e^2 p2 by multilinearity in the
+// k <= kSmwMaxK rows, so that r = p0, c1 = p1 + p0 Tr Z, c2 = p2 + p1 Tr Z +
+// p0 (Tr(Z)^2 - Tr(Z^2)) / 2.  Then with A_d^* / Z_T = a_d, Z_T = sum_d A_d^*
+// r_du r_dd:  <Psi_T|Psi> = det S_0u det S_0d Z_T,  t_g = sum_d a_d
+// [c1_du r_dd + r_du c1_dd](L_g), E_loc = sum_d a_d [H0 r_du r_dd + (c1_du
+// r_dd + r_du c1_dd)(h) + sum_g (c2_du r_dd + r_du c2_dd + c1_du c1_dd)(L_g)].
 #include "state.cuh"
 #include "tc.cuh"
 
@@ -289,9 +312,431 @@ __global__ void k_md_meanfield(int G, long NM, const double* Lh, const double* V
   if (threadIdx.x == 0) c[g] = v;
 }
 
+// ---------------------------------------- determinants relative to d = 0 --
+__device__ inline double2 zadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ inline double2 zsub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ inline double2 zscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+__device__ inline double2 zdivd(double2 a, double2 b) {
+  const double den = b.x * b.x + b.y * b.y;
+  return make_double2((a.x * b.x + a.y * b.y) / den, (a.y * b.x - a.x * b.y) / den);
+}
+__device__ inline double2 zshfl(double2 v, int src) {
+  return make_double2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
+}
+__device__ inline double2 zwarp_sum(double2 v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+    v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+  }
+  return v;
+}
+
+typedef double2 SmallMat[kSmwMaxK][kSmwMaxK];
+
+// det of the leading k x k block (k <= kSmwMaxK; k = 0 gives 1) by Gaussian
+// elimination with partial pivoting; A is overwritten.
+__device__ double2 small_det(SmallMat& A, int k) {
+  double2 det = make_double2(1.0, 0.0);
+  for (int c = 0; c < k; ++c) {
+    int piv = c;
+    double best = A[c][c].x * A[c][c].x + A[c][c].y * A[c][c].y;
+    for (int r = c + 1; r < k; ++r) {
+      const double m2 = A[r][c].x * A[r][c].x + A[r][c].y * A[r][c].y;
+      if (m2 > best) {
+        best = m2;
+        piv = r;
+      }
+    }
+    if (!(best > 0.0)) return make_double2(0.0, 0.0);
+    if (piv != c) {
+      for (int q = 0; q < k; ++q) {
+        const double2 t = A[c][q];
+        A[c][q] = A[piv][q];
+        A[piv][q] = t;
+      }
+      det = make_double2(-det.x, -det.y);
+    }
+    det = zmul(det, A[c][c]);
+    const double2 inv = zdivd(make_double2(1.0, 0.0), A[c][c]);
+    for (int r = c + 1; r < k; ++r) {
+      const double2 f = zmul(A[r][c], inv);
+      for (int q = c; q < k; ++q) A[r][q] = zsub(A[r][q], zmul(f, A[c][q]));
+    }
+  }
+  return det;
+}
+
+// p0, p1, p2 of det(P + e S1 + e^2 S2) by multilinearity in the rows (p2 only
+// if `second`).
+__device__ void small_poly(const SmallMat& P, const SmallMat& S1, const SmallMat& S2, int k,
+                           bool second, double2* p0, double2* p1, double2* p2) {
+  SmallMat A;
+  auto load = [&](int l1, const SmallMat* R1, int l2, const SmallMat* R2) {
+    for (int l = 0; l < k; ++l)
+      for (int m = 0; m < k; ++m)
+        A[l][m] = l == l1 ? (*R1)[l][m] : (l == l2 ? (*R2)[l][m] : P[l][m]);
+  };
+  load(-1, nullptr, -1, nullptr);
+  *p0 = small_det(A, k);
+  *p1 = make_double2(0.0, 0.0);
+  *p2 = make_double2(0.0, 0.0);
+  for (int l = 0; l < k; ++l) {
+    load(l, &S1, -1, nullptr);
+    *p1 = zadd(*p1, small_det(A, k));
+  }
+  if (!second) return;
+  for (int l = 0; l < k; ++l) {
+    load(l, &S2, -1, nullptr);
+    *p2 = zadd(*p2, small_det(A, k));
+    for (int m = l + 1; m < k; ++m) {
+      load(l, &S1, m, &S1);
+      *p2 = zadd(*p2, small_det(A, k));
+    }
+  }
+}
+
+// One block per walker: Xi_s = U_s^T Theta_0s (particle rows of md_V), the
+// ratios r_ds = det Xi_s[o_ds + l][h_m], Z_T = sum_d A_d^* r_du r_dd in the
+// order of d, log <Psi_T|Psi> = log det S_0u + log det S_0d + log Z_T, and
+// a_d = A_d^* / Z_T.  tab[(d, s)] = [k, o, h_0 .. h_3, -, -].
+__global__ void __launch_bounds__(128)
+    k_smw_ratio(int W, int M, int N, int nd, int ks, int np0, int np1, const int* __restrict__ tab,
+                const int* __restrict__ prow, const double* __restrict__ Vt,
+                const double* __restrict__ theta, const double* __restrict__ ld0,
+                const double* __restrict__ logA, const double* wt, double* xi, double* aw,
+                double* ldout) {
+  __shared__ double2 zt;
+  const int w = blockIdx.x, tid = threadIdx.x;
+  if (!walker_alive(wt, w)) return;
+  const long NM = (long)N * M;
+  double2* aw2 = reinterpret_cast<double2*>(aw) + (long)w * nd;
+  for (int s = 0; s < 2; ++s) {
+    const int np = s ? np1 : np0;
+    const double* th = theta + ((long)s * W + w) * 2 * NM;  // Theta_0s rows [2][N][M]
+    double2* xs = reinterpret_cast<double2*>(xi) + ((long)w * 2 + s) * ks * N;
+    for (int e = tid; e < np * N; e += blockDim.x) {
+      const int pl = e / N, j = e - (e / N) * N;
+      const double* u = Vt + (long)prow[s * ks + pl] * M;
+      double re = 0.0, im = 0.0;
+      for (int q = 0; q < M; ++q) {
+        re += u[q] * th[(long)j * M + q];
+        im += u[q] * th[NM + (long)j * M + q];
+      }
+      xs[(long)pl * N + j] = make_double2(re, im);
+    }
+  }
+  __syncthreads();
+  for (int d = tid; d < nd; d += blockDim.x) {
+    double2 r[2];
+    for (int s = 0; s < 2; ++s) {
+      const int* tb = tab + (d * 2 + s) * 8;
+      const int k = tb[0], o = tb[1];
+      const double2* xs = reinterpret_cast<const double2*>(xi) + ((long)w * 2 + s) * ks * N;
+      SmallMat P;
+      for (int l = 0; l < k; ++l)
+        for (int m = 0; m < k; ++m) P[l][m] = xs[(long)(o + l) * N + tb[2 + m]];
+      r[s] = small_det(P, k);
+    }
+    double sn, cs;
+    sincos(logA[2 * d + 1], &sn, &cs);
+    const double am = exp(logA[2 * d]);
+    aw2[d] = zmul(make_double2(am * cs, am * sn), zmul(r[0], r[1]));
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double2 z = make_double2(0.0, 0.0);
+    for (int d = 0; d < nd; ++d) z = zadd(z, aw2[d]);
+    const double* l0 = ld0 + (long)w * 4;  // [spin][re, im] of log det S_0s
+    ldout[2 * w] = l0[0] + l0[2] + 0.5 * log(z.x * z.x + z.y * z.y);
+    ldout[2 * w + 1] = wrap_pi(l0[1] + l0[3] + atan2(z.y, z.x));
+    zt = z;
+  }
+  __syncthreads();
+  for (int d = tid; d < nd; d += blockDim.x) {
+    double sn, cs;
+    sincos(logA[2 * d + 1], &sn, &cs);
+    const double am = exp(logA[2 * d]);
+    aw2[d] = zdivd(make_double2(am * cs, am * sn), zt);
+  }
+}
+
+// Block (chunk c, walker w), 8 warps: for each vector g of the chunk
+// (kSmwGC of them; with ENERGY the extra chunk c = nchk takes h instead),
+// Y0_s = Lh_0sg Theta_0s in shared memory, then one warp per determinant
+// (lane j = column j) forms Yp and Xi Y0 at its holes, the k x k matrices P,
+// S1 (and S2) and the coefficients; the force bias sums a_d [c1_du r_dd +
+// r_du c1_dd] over d (per warp in the order of d, then over warps in order);
+// the energy keeps per (w, c, d) the sum over the chunk of c2_du r_dd + r_du
+// c2_dd + c1_du c1_dd (H0 r_du r_dd + c1_du r_dd + r_du c1_dd for h).
+template <bool ENERGY>
+__global__ void __launch_bounds__(256)
+    k_smw_terms(int W, int M, int N, int G, int nd, int ks, int nchk, double H0,
+                const int* __restrict__ tab, const double* __restrict__ Lh,
+                const double* __restrict__ hh, const double* __restrict__ theta,
+                const double* __restrict__ xi, const double* __restrict__ aw, const double* wt,
+                double* t, double* part) {
+  extern __shared__ double2 y0[];  // [2][N][N]
+  __shared__ double2 rj[2][kSmwMaxN + 1];  // Sum_i Y0[j][i] Y0[i][j]; [N]: Tr(Y0^2)
+  __shared__ double2 trs[2];
+  __shared__ double2 wsum[8];
+  const int c = blockIdx.x, w = blockIdx.y, tid = threadIdx.x;
+  if (!walker_alive(wt, w)) return;
+  const bool onebody = ENERGY && c == nchk;
+  const int g0 = onebody ? 0 : c * kSmwGC;
+  const int g1 = onebody ? 1 : (G < g0 + kSmwGC ? G : g0 + kSmwGC);
+  const long NM = (long)N * M;
+  const int lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+  const bool lj = lane < N;
+  const double2* xw = reinterpret_cast<const double2*>(xi) + (long)w * 2 * ks * N;
+  const double2* aw2 = reinterpret_cast<const double2*>(aw) + (long)w * nd;
+  // operator rows of (d, s) for vector g (or h)
+  auto xrow = [&](int ds, int g, int i) -> const double* {
+    return onebody ? hh + ((long)ds * N + i) * M : Lh + (((long)ds * G + g) * N + i) * M;
+  };
+  for (int g = g0; g < g1; ++g) {
+    for (int e = tid; e < 2 * N * N; e += blockDim.x) {
+      const int s = e / (N * N), i = (e / N) % N, j = e % N;
+      const double* x = xrow(s, g, i);  // determinant 0: ds = s
+      const double* th = theta + ((long)s * W + w) * 2 * NM;
+      double re = 0.0, im = 0.0;
+      for (int q = 0; q < M; ++q) {
+        re += x[q] * th[(long)j * M + q];
+        im += x[q] * th[NM + (long)j * M + q];
+      }
+      y0[e] = make_double2(re, im);
+    }
+    __syncthreads();
+    if (tid < 2) {
+      double2 tr = make_double2(0.0, 0.0);
+      for (int i = 0; i < N; ++i) tr = zadd(tr, y0[tid * N * N + i * N + i]);
+      trs[tid] = tr;
+    }
+    if (ENERGY && !onebody)
+      for (int e = tid; e < 2 * N; e += blockDim.x) {
+        const int s = e / N, j = e % N;
+        const double2* Y = y0 + s * N * N;
+        double2 v = make_double2(0.0, 0.0);
+        for (int i = 0; i < N; ++i) v = zadd(v, zmul(Y[j * N + i], Y[i * N + j]));
+        rj[s][j] = v;
+      }
+    __syncthreads();
+    if (ENERGY && !onebody && tid < 2) {
+      double2 v = make_double2(0.0, 0.0);
+      for (int j = 0; j < N; ++j) v = zadd(v, rj[tid][j]);
+      rj[tid][N] = v;
+    }
+    __syncthreads();
+    double2 fsum = make_double2(0.0, 0.0);
+    for (int d = warp; d < nd; d += nwarp) {
+      double2 rr[2], c1[2], c2[2];
+      for (int s = 0; s < 2; ++s) {
+        const int* tb = tab + (d * 2 + s) * 8;
+        const int k = tb[0], o = tb[1];
+        const double2* Y = y0 + s * N * N;
+        const double2* X = xw + (long)s * ks * N;  // Xi_s rows
+        const double* th = theta + ((long)s * W + w) * 2 * NM;
+        double2 yp[kSmwMaxK], xy[kSmwMaxK];
+        for (int l = 0; l < k; ++l) {
+          yp[l] = xy[l] = make_double2(0.0, 0.0);
+          if (!lj) continue;
+          const double* x = xrow(2 * d + s, g, tb[2 + l]);
+          double re = 0.0, im = 0.0;
+          for (int q = 0; q < M; ++q) {
+            re += x[q] * th[(long)lane * M + q];
+            im += x[q] * th[NM + (long)lane * M + q];
+          }
+          yp[l] = make_double2(re, im);
+          double2 v = make_double2(0.0, 0.0);
+          for (int i = 0; i < N; ++i) v = zadd(v, zmul(X[(long)(o + l) * N + i], Y[i * N + lane]));
+          xy[l] = v;
+        }
+        SmallMat P, S1, S2;
+        for (int l = 0; l < k; ++l)
+          for (int m = 0; m < k; ++m) {
+            const int hm = tb[2 + m];
+            const double2 ypv = zshfl(yp[l], hm), xyv = zshfl(xy[l], hm);
+            double2 corr = make_double2(0.0, 0.0);
+            for (int i = 0; i < k; ++i)
+              corr = zadd(corr, zmul(X[(long)(o + l) * N + tb[2 + i]], Y[tb[2 + i] * N + hm]));
+            P[l][m] = X[(long)(o + l) * N + hm];
+            S1[l][m] = zadd(zsub(ypv, xyv), corr);
+          }
+        double2 tz = trs[s];
+        for (int m = 0; m < k; ++m) tz = zsub(tz, Y[tb[2 + m] * N + tb[2 + m]]);
+        double2 e2 = make_double2(0.0, 0.0);
+        if (ENERGY && !onebody) {
+          bool hole = false;
+          for (int m = 0; m < k; ++m) hole = hole || tb[2 + m] == lane;
+          for (int l = 0; l < k; ++l) {
+            double2 F = make_double2(0.0, 0.0);
+            if (lj && !hole) {
+              F = zsub(xy[l], yp[l]);
+              for (int i = 0; i < k; ++i)
+                F = zsub(F, zmul(X[(long)(o + l) * N + tb[2 + i]], Y[tb[2 + i] * N + lane]));
+            }
+            for (int m = 0; m < k; ++m)
+              S2[l][m] = zwarp_sum(lj ? zmul(F, Y[lane * N + tb[2 + m]]) : make_double2(0.0, 0.0));
+          }
+          double2 tz2 = rj[s][N];
+          for (int m = 0; m < k; ++m) {
+            tz2 = zsub(tz2, zscale(rj[s][tb[2 + m]], 2.0));
+            for (int m2 = 0; m2 < k; ++m2)
+              tz2 = zadd(tz2, zmul(Y[tb[2 + m] * N + tb[2 + m2]], Y[tb[2 + m2] * N + tb[2 + m]]));
+          }
+          e2 = zscale(zsub(zmul(tz, tz), tz2), 0.5);
+        }
+        double2 p0, p1, p2;
+        small_poly(P, S1, S2, k, ENERGY && !onebody, &p0, &p1, &p2);
+        rr[s] = p0;
+        c1[s] = zadd(p1, zmul(p0, tz));
+        c2[s] = zadd(zadd(p2, zmul(p1, tz)), zmul(p0, e2));
+      }
+      if (lane == 0) {
+        if (!ENERGY) {
+          fsum = zadd(fsum, zmul(aw2[d], zadd(zmul(c1[0], rr[1]), zmul(rr[0], c1[1]))));
+        } else {
+          double2 v;
+          if (onebody)
+            v = zadd(zscale(zmul(rr[0], rr[1]), H0), zadd(zmul(c1[0], rr[1]), zmul(rr[0], c1[1])));
+          else
+            v = zadd(zadd(zmul(c2[0], rr[1]), zmul(rr[0], c2[1])), zmul(c1[0], c1[1]));
+          double2* pp = reinterpret_cast<double2*>(part) + ((long)w * (nchk + 1) + c) * nd + d;
+          *pp = g == g0 ? v : zadd(*pp, v);
+        }
+      }
+    }
+    if (!ENERGY) {
+      if (lane == 0) wsum[warp] = fsum;
+      __syncthreads();
+      if (tid == 0) {
+        double2 tot = make_double2(0.0, 0.0);
+        for (int q = 0; q < nwarp; ++q) tot = zadd(tot, wsum[q]);
+        t[(2L * w) * G + g] = tot.x;
+        t[(2L * w + 1) * G + g] = tot.y;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// The mixed path's fields read FP32 traces.
+__global__ void k_smw_t32(long n, const double* t, float* t32) {
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x)
+    t32[e] = (float)t[e];
+}
+
+// E_loc = sum_d a_d sum_c part[w][c][d] (chunks in order), one thread per walker.
+__global__ void k_smw_eloc(int W, int nd, int nchk, const double* aw, const double* part,
+                           const double* wt, double* eloc) {
+  const int w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= W || !walker_alive(wt, w)) return;
+  const double2* a = reinterpret_cast<const double2*>(aw) + (long)w * nd;
+  const double2* pw = reinterpret_cast<const double2*>(part) + (long)w * (nchk + 1) * nd;
+  double2 e = make_double2(0.0, 0.0);
+  for (int d = 0; d < nd; ++d) {
+    double2 sd = make_double2(0.0, 0.0);
+    for (int c = 0; c <= nchk; ++c) sd = zadd(sd, pw[(long)c * nd + d]);
+    e = zadd(e, zmul(a[d], sd));
+  }
+  eloc[2 * w] = e.x;
+  eloc[2 * w + 1] = e.y;
+}
+
 }  // namespace
 
+// Holes and particles of every (d, s) relative to determinant 0 from the
+// host orbitals ([nd][M][N] row-major): column i of V_ds is a hole when any
+// entry differs from column i of V_0s.  The low-rank evaluation is taken on
+// float64 (on either path: the mixed path then keeps its low-precision
+// propagation and takes the force bias in FP32 from it) when every
+// determinant differs in at most kSmwMaxK columns per spin and N <= kSmwMaxN
+// (two or more determinants); else each determinant is evaluated in full.
+int smw_detect(afqmc_state* s, const double* up, const double* dn) {
+  const afqmc_params& p = s->p;
+  const Bufs& b = s->b;
+  const int nd = p.ndet, N = p.N, M = p.M;
+  s->smw = false;
+  if (nd < 2 || N > kSmwMaxN) return AFQMC_OK;
+  const int ks = kSmwMaxK * nd;
+  std::vector<int> tab((size_t)nd * 2 * 8, 0), prow((size_t)2 * ks, 0);
+  int np[2] = {0, 0};
+  for (int d = 0; d < nd; ++d)
+    for (int sp = 0; sp < 2; ++sp) {
+      const double* V0 = sp ? dn : up;
+      const double* Vd = V0 + (size_t)d * M * N;
+      int* tb = tab.data() + (size_t)(d * 2 + sp) * 8;
+      int k = 0;
+      for (int i = 0; i < N; ++i) {
+        bool same = true;
+        for (int r = 0; r < M && same; ++r) same = Vd[(size_t)r * N + i] == V0[(size_t)r * N + i];
+        if (same) continue;
+        if (k == kSmwMaxK) return AFQMC_OK;
+        tb[2 + k++] = i;
+      }
+      tb[0] = k;
+      tb[1] = np[sp];
+      for (int l = 0; l < k; ++l) prow[(size_t)sp * ks + np[sp]++] = (2 * d + sp) * N + tb[2 + l];
+    }
+  AFQ_CUDA(cudaMemcpyAsync(b.smw_tab, tab.data(), sizeof(int) * tab.size(), cudaMemcpyHostToDevice,
+                           s->st));
+  AFQ_CUDA(cudaMemcpyAsync(b.smw_prow, prow.data(), sizeof(int) * prow.size(),
+                           cudaMemcpyHostToDevice, s->st));
+  AFQ_CUDA(cudaStreamSynchronize(s->st));
+  s->smw = true;
+  s->smw_np[0] = np[0];
+  s->smw_np[1] = np[1];
+  return AFQMC_OK;
+}
+
+static int smw_chunks(const afqmc_params& p) { return (p.nchol + kSmwGC - 1) / kSmwGC; }
+
+static int smw_overlap_update(afqmc_state* s, bool into_ld) {
+  const afqmc_params& p = s->p;
+  const Bufs& b = s->b;
+  const int W = p.nwalkers, N = p.N, M = p.M, nd = p.ndet;
+  const size_t smem = sizeof(double2) * (size_t)N * 2 * N;
+  AFQ_CUDA(cudaFuncSetAttribute(k_md_overlap, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem));
+  // determinant 0 only: S_0s, log det, Theta_0s (md_ld rows [w][s])
+  AFQ_LAUNCH(k_md_overlap, dim3(2, W), 256, smem, s->st, W, M, N, b.md_V, b.phiT, b.wt,
+             b.md_theta, b.md_ld, nullptr, b.lo_kind, b.Mp);
+  AFQ_LAUNCH(k_smw_ratio, W, 128, 0, s->st, W, M, N, nd, kSmwMaxK * nd, s->smw_np[0],
+             s->smw_np[1], b.smw_tab, b.smw_prow, b.md_V, b.md_theta, b.md_ld, b.md_logA, b.wt,
+             b.smw_xi, b.md_w, into_ld ? b.ld : b.ld_new);
+  return AFQMC_OK;
+}
+
+static int smw_force_bias(afqmc_state* s) {
+  const afqmc_params& p = s->p;
+  const Bufs& b = s->b;
+  const int nchk = smw_chunks(p);
+  const size_t smem = sizeof(double2) * 2 * (size_t)p.N * p.N;
+  AFQ_LAUNCH(k_smw_terms<false>, dim3(nchk, p.nwalkers), 256, smem, s->st, p.nwalkers, p.M, p.N,
+             p.nchol, p.ndet, kSmwMaxK * p.ndet, nchk, p.H0, b.smw_tab, b.md_Lh, b.md_hh,
+             b.md_theta, b.smw_xi, b.md_w, b.wt, b.t, nullptr);
+  if (b.mixed) {
+    const long n = 2L * p.nwalkers * p.nchol;
+    AFQ_LAUNCH(k_smw_t32, cdiv((size_t)n, 256), 256, 0, s->st, n, b.t, b.t32);
+  }
+  return AFQMC_OK;
+}
+
+static int smw_local_energies(afqmc_state* s) {
+  const afqmc_params& p = s->p;
+  const Bufs& b = s->b;
+  const int nchk = smw_chunks(p);
+  const size_t smem = sizeof(double2) * 2 * (size_t)p.N * p.N;
+  AFQ_LAUNCH(k_smw_terms<true>, dim3(nchk + 1, p.nwalkers), 256, smem, s->st, p.nwalkers, p.M,
+             p.N, p.nchol, p.ndet, kSmwMaxK * p.ndet, nchk, p.H0, b.smw_tab, b.md_Lh, b.md_hh,
+             b.md_theta, b.smw_xi, b.md_w, b.wt, nullptr, b.smw_part);
+  AFQ_LAUNCH(k_smw_eloc, cdiv(p.nwalkers, 128), 128, 0, s->st, p.nwalkers, p.ndet, nchk, b.md_w,
+             b.smw_part, b.wt, b.eloc);
+  return AFQMC_OK;
+}
+
 int md_overlap_update(afqmc_state* s, bool into_ld) {
+  if (s->smw) return smw_overlap_update(s, into_ld);
   const afqmc_params& p = s->p;
   const Bufs& b = s->b;
   const int W = p.nwalkers, N = p.N, M = p.M, nd = p.ndet;
@@ -351,6 +796,7 @@ static int md_traces_lo(afqmc_state* s) {
 }
 
 int md_force_bias(afqmc_state* s) {
+  if (s->smw) return smw_force_bias(s);
   const afqmc_params& p = s->p;
   const Bufs& b = s->b;
   const unsigned grid = cdiv((size_t)p.nwalkers * p.nchol, 256);
@@ -368,6 +814,7 @@ int md_force_bias(afqmc_state* s) {
 
 // Local energies into b.eloc (the traces md_C are current after md_force_bias).
 int md_local_energies(afqmc_state* s) {
+  if (s->smw) return smw_local_energies(s);
   const afqmc_params& p = s->p;
   const Bufs& b = s->b;
   const int W = p.nwalkers, N = p.N, M = p.M, G = p.nchol, nd = p.ndet;

@@ -66,7 +66,18 @@ struct Bufs {
   // as BF16/TF32, FP32 traces [2nd][2W][G]
   void *md_theta_lo = nullptr, *md_Lh_lo = nullptr;
   float* md_C32 = nullptr;
+  // determinants taken relative to determinant 0 (holes and particles, see
+  // multidet.cu): per (d, s) [k, particle offset, holes h_0..h_3, -, -],
+  // particle rows (2 d + s) N + h of md_V / md_Lh / md_hh per spin
+  // [2][kSmwMaxK nd], Xi_s = U_s^T Theta_0s [W][2][kSmwMaxK nd][N] complex,
+  // energy partials [W][nchunk + 1][nd] complex
+  int *smw_tab = nullptr, *smw_prow = nullptr;
+  double *smw_xi = nullptr, *smw_part = nullptr;
 };
+
+constexpr int kSmwMaxK = 4;   // columns a determinant may differ from determinant 0 in, per spin
+constexpr int kSmwMaxN = 32;  // orbitals per spin (one lane per column)
+constexpr int kSmwGC = 8;     // Cholesky vectors per block of the low-rank kernels
 
 constexpr int kBpSlices = 8;
 
@@ -114,6 +125,10 @@ struct afqmc_state {
   double sf = 2.0;
   // population size of the last afqmc_comb_plan (sharded comb), 0 before one
   int64_t comb_nall = 0;
+  // multi-determinant trial evaluated relative to determinant 0 (float64),
+  // with the particle count of each spin
+  bool smw = false;
+  int smw_np[2] = {0, 0};
 };
 
 namespace afq {
@@ -129,6 +144,7 @@ int md_overlap_update(afqmc_state* s, bool into_ld);
 int md_force_bias(afqmc_state* s);
 int md_local_energies(afqmc_state* s);
 int md_setup(afqmc_state* s, const double* coef);
+int smw_detect(afqmc_state* s, const double* up, const double* dn);
 }  // namespace afq
 
 namespace afq {

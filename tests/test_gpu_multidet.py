@@ -10,9 +10,13 @@ orbitals, so spin-up and spin-down orbitals differ) with complex
 coefficients; a ragged shape with two determinants; a one-determinant trial
 given through the multi-determinant entry point, which must reproduce the
 single-determinant walk of afqmc_init; and the unsupported combinations and
-bad inputs.  (Determinants orthogonal to a walker, as in CI expansions about
-the walker's own determinant, make each w_d E_d a 0/0 limit that this
-per-determinant evaluation does not resolve; they are not used here.)
+bad inputs.  With three orbitals per spin every determinant differs from the
+leading one in at most four columns, so the library evaluates that trial
+relative to determinant 0 (the low-rank route of tests/test_gpu_smw.py) and
+the per-determinant oracle checks it; five orbitals per spin take the
+per-determinant route.  (CI expansions about the walker's own determinant,
+where each w_d E_d of the per-determinant evaluation is a 0/0 limit, are
+covered by tests/test_gpu_smw.py.)
 """
 import numpy as np
 import pytest
@@ -132,7 +136,7 @@ def test_mixed_path_close_to_float64(pkg, prec, tol_e, tol_phi):
     Theta_ds; overlaps, weights and combinations in float64) against the
     float64 path on the same trial, seed and steps: they differ by the operand
     rounding only (BF16 2^-9, TF32 2^-11 relative per operand)."""
-    M, N, G, W, nd = 24, 4, 120, 64, 3
+    M, N, G, W, nd = 24, 5, 120, 64, 3  # five columns per spin differ: per-determinant route
     h1, L, coef, up, dn = noci_trial(M, N, G, 7300, nd)
     out = []
     for precision in (0, prec):
