@@ -811,18 +811,29 @@ def run_batched(args):
     g = pkg.AfqmcGroup(runs)
     blk = 10
     K = -(-args.steps // blk) * blk
-    g.propagate(blk)  # capture + first replay
-    g.synchronize()
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    l0 = pkg.afqmc_launch_count()
-    with ClockSampler(0) as clk:
+
+    def timed(mode, clk=None):
+        # the block's capture chosen (default: four trial blocks, two each way)
+        g.set_grouped(mode)
+        g.propagate(4 * blk if mode == "auto" else blk)
+        g.synchronize()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0 = pkg.afqmc_launch_count()
+        if clk:
+            clk.__enter__()
         e0.record(g.stream)
         g.propagate(K)
         e1.record(g.stream)
         torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
-    launches = pkg.afqmc_launch_count() - l0
+        if clk:
+            clk.__exit__(None, None, None)
+        return e0.elapsed_time(e1), pkg.afqmc_launch_count() - l0, g.tiles()
+
+    clk = ClockSampler(0)
+    ms, launches, (grouped_on, tiles) = timed("auto", clk)
+    ms_grouped, _, (_, tiles_g) = timed(True)
+    ms_branches, _, _ = timed(False)
     total_ws = sum(w.nwalkers for w in ws_)
     # the same systems one after the other, each with its own graph replay
     torch.cuda.synchronize()
@@ -839,6 +850,12 @@ def run_batched(args):
     ms_seq = s0.elapsed_time(s1)
     line = {
         "metric": "walker-steps/s, 16 uneven systems in one graph launch per block",
+        "capture": "grouped" if grouped_on else "graph branches",
+        "grouped": {"value": total_ws * K / (ms_grouped * 1e-3), "ms_per_step": ms_grouped / K,
+                    "tiles": dict(zip(("force_bias", "v", "half_step_1", "half_step_2"), tiles_g)),
+                    "note": "each of the step's four tensor-core contractions of all 16 systems "
+                            "as one persistent launch over (system, tile); tile widths timed on "
+                            "the systems' buffers"},
         "value": total_ws * K / (ms * 1e-3), "unit": "walker-steps/s", "n_gpus": 1, "steps": K,
         "warmup": blk, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": DTYPES[args.precision],
@@ -848,6 +865,11 @@ def run_batched(args):
                    "trial": "RHF, 10 DIIS iterations"},
         "one_by_one": {"value": total_ws * K / (ms_seq * 1e-3), "ms_per_step": ms_seq / K,
                        "note": "same systems propagated one after another (own graphs)"},
+        "graph_branches": {"value": total_ws * K / (ms_branches * 1e-3),
+                           "ms_per_step": ms_branches / K,
+                           "note": "same block captured as each system's own kernels on its own "
+                                   "stream (branches of one graph), no grouped launches"},
+        "note": "value: the group's default capture, chosen by timing one block each way",
         "gpu_launches": launches, "clocks": clk.summary(),
         "e2e": None,
     }

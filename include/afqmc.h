@@ -294,6 +294,21 @@ AFQMC_API int afqmc_load(afqmc_state* s, const void* buf, size_t bytes);
  * graph block length, must be on the current device, and must stay valid
  * while the group exists.  Each state's results are bit-identical to
  * stepping it alone.
+ *
+ * When every state runs the same mixed precision with the same periods
+ * (single-determinant, closed shell, no back-propagation window), the block
+ * is captured step by step instead: each of the step's four tensor-core
+ * contractions (force bias, V, the two half steps) of ALL states is one
+ * persistent launch over a work list of (state, output tile), each state's
+ * operands addressed through its own tensor maps in a small device table the
+ * group allocates; the per-state kernels between them run on the states'
+ * streams.  The tile widths of the force-bias and half-step launches are
+ * chosen when the grouped launches are set up, by timing the candidates on
+ * the states' own buffers (outputs that are scratch at that point).  By
+ * default the group replays its first four blocks two each way, times the
+ * second block of each (synchronising the stream then) and keeps the faster
+ * capture.  Results stay bit-identical to stepping each state alone either
+ * way.
  */
 typedef struct afqmc_group afqmc_group; /* opaque */
 AFQMC_API int afqmc_group_create(afqmc_state* const* states, int32_t n, void* stream,
@@ -301,6 +316,14 @@ AFQMC_API int afqmc_group_create(afqmc_state* const* states, int32_t n, void* st
 /* nsteps must be a multiple of the block length and every state must sit on
  * a block boundary.  Asynchronous on `stream` (which joins all branches). */
 AFQMC_API int afqmc_group_propagate(afqmc_group* g, int32_t nsteps);
+/* mode 0: capture each state's own kernel sequence; 1: the grouped
+ * contractions where the states allow; 2 (default): choose between the two
+ * by timing (restarts the trial).  Takes effect on the next block. */
+AFQMC_API int afqmc_group_set_grouped(afqmc_group* g, int32_t mode);
+/* 1 when the grouped contractions are in use (after a propagate), else 0;
+ * bn[4] receives their tile widths (force bias, V, first and last half step;
+ * 0 when not grouped).  Negative on bad arguments. */
+AFQMC_API int afqmc_group_tiles(const afqmc_group* g, int32_t* bn);
 AFQMC_API int afqmc_group_destroy(afqmc_group* g);
 
 /*

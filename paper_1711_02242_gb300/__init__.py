@@ -38,6 +38,7 @@ EXPORTED = ["afqmc_default_params", "afqmc_workspace_size", "afqmc_init", "afqmc
             "afqmc_philox4x32_10", "afqmc_gaussian_fields", "afqmc_contract",
             "afqmc_profile_start", "afqmc_profile_stop", "afqmc_local_energies_noalloc",
             "afqmc_group_create", "afqmc_group_propagate", "afqmc_group_destroy",
+            "afqmc_group_set_grouped", "afqmc_group_tiles",
             "afqmc_wait_flag", "afqmc_taylor_series", "afqmc_mcd_workspace_size",
             "afqmc_modified_cholesky", "afqmc_mcd_pairs_workspace_size",
             "afqmc_modified_cholesky_pairs", "afqmc_bp_begin", "afqmc_bp_end",
@@ -118,6 +119,8 @@ def lib():
         "afqmc_group_create": (ctypes.c_int, [P(vp), ctypes.c_int32, vp, P(vp)]),
         "afqmc_group_propagate": (ctypes.c_int, [vp, ctypes.c_int32]),
         "afqmc_group_destroy": (ctypes.c_int, [vp]),
+        "afqmc_group_set_grouped": (ctypes.c_int, [vp, ctypes.c_int32]),
+        "afqmc_group_tiles": (ctypes.c_int, [vp, P(ctypes.c_int32)]),
         "afqmc_wait_flag": (ctypes.c_int, [vp, ctypes.c_int64, vp, vp]),
         "afqmc_taylor_series": (ctypes.c_int, [ctypes.c_int32] + [ctypes.c_int64] * 4 +
                                 [ctypes.c_int32, vp, vp, vp, vp, ctypes.c_int64, ctypes.c_int32,
@@ -458,6 +461,21 @@ class AfqmcGroup:
 
     def propagate(self, nsteps: int):
         _check(lib().afqmc_group_propagate(self.g, int(nsteps)))
+
+    def set_grouped(self, on):
+        """True: grouped tensor-core contractions (one persistent launch per
+        phase for all runs) where the runs allow; False: each run's own
+        kernels; "auto" (the default): the faster of the two, by timing."""
+        _check(lib().afqmc_group_set_grouped(self.g, 2 if on == "auto" else (1 if on else 0)))
+
+    def tiles(self):
+        """(grouped?, tile widths of the force-bias, V, first and last half-step
+        launches) as chosen on the first propagate."""
+        bn = (ctypes.c_int32 * 4)()
+        r = lib().afqmc_group_tiles(self.g, bn)
+        if r < 0:
+            _check(r)
+        return bool(r), list(bn)
 
     def synchronize(self):
         self.stream.synchronize()

@@ -321,6 +321,103 @@ int overlap_update(afqmc_state* s, bool into_ld, bool timed) {
   return AFQMC_OK;
 }
 
+// ---- the mixed path's per-step contractions as job descriptors --------------
+// t[(w,c)][g] = 2 sum_(i,p) Theta^T_lo[(w,c)][(i,p)] Lh_lo[g][(i,p)] on tcgen05
+void desc_force_bias(afqmc_state* s, TcJobDesc* d) {
+  const afqmc_params& p = s->p;
+  const Bufs& b = s->b;
+  d->kind = TC_JOB_STORE;
+  d->g.m = 2 * p.nwalkers;
+  d->g.n = p.nchol;
+  d->g.k = p.N * b.Mp;
+  d->g.A = b.th_lo;
+  d->g.lda = (long)p.N * b.Mp;
+  d->g.B = b.Lh_lo;
+  d->g.ldb = (long)p.N * b.Mp;
+  d->g.tf32 = b.lo_kind == LO_TF32;
+  d->g.err = b.status;
+  d->C = b.t32;
+  d->ldc = p.nchol;
+  d->alpha = 2.0f;
+}
+
+// V = i sqrt(dt) sum_g x_g L_g over the upper 16 x 16 blocks of the (p, q)
+// grid (V is symmetric), each block and its mirror written straight into the
+// [Re V | Im V] operand rows of the Taylor terms
+void desc_v(afqmc_state* s, TcJobDesc* d) {
+  const afqmc_params& p = s->p;
+  const Bufs& b = s->b;
+  d->kind = TC_JOB_V;
+  d->g.m = 2 * p.nwalkers;
+  d->g.n = b.nblkV * 256;
+  d->g.k = p.nchol;
+  d->g.A = b.x_lo;
+  d->g.lda = b.Gp;
+  d->g.B = b.LbT_lo;
+  d->g.ldb = b.Gp;
+  d->g.tf32 = b.lo_kind == LO_TF32;
+  d->g.err = b.status;
+  d->V = b.V_lo;
+  d->lo_kind = b.lo_kind;
+  d->W = p.nwalkers;
+  d->M = p.M;
+  d->Mp = b.Mp;
+  d->sdt = s->sdt;
+}
+
+// first half step: T_0 = (B_half Phi)^T = Phi^T + (Phi_lo D_B)^T, D_B =
+// B_half - I (the identity part added in float64 orbitals by the epilogue),
+// into columns [0, Mp) of the FP32 rows of acc (pitch 2 Mp) and, as the 0th
+// Taylor operand, into Tb0
+void desc_half1(afqmc_state* s, const double* phi_in, const void* phi_lo_in, TcJobDesc* d) {
+  const afqmc_params& p = s->p;
+  const Bufs& b = s->b;
+  d->kind = TC_JOB_PROP0;
+  d->g.m = 2 * p.N * p.nwalkers;
+  d->g.n = p.M;
+  d->g.k = p.M;
+  d->g.A = phi_lo_in;
+  d->g.lda = b.Mp;
+  d->g.B = b.Bh_lo;
+  d->g.ldb = b.Mp;
+  d->g.tf32 = b.lo_kind == LO_TF32;
+  d->g.err = b.status;
+  d->acc = b.acc32;
+  d->ldacc = 2L * b.Mp;
+  d->tb = b.Tb0;
+  d->phi_id = phi_in;
+  d->lo_kind = b.lo_kind;
+  d->N = p.N;
+  d->M = p.M;
+  d->Mp = b.Mp;
+}
+
+// last half step (TF32): Phi <- B_half (T_0 + S) = (T_0 + S) + [T_0 | S]
+// [D_B | D_B] (one K = 2 Mp product; T_0 + S added in the epilogue); stored
+// for live walkers
+void desc_half2(afqmc_state* s, double* phi_out, void* phi_lo_out, TcJobDesc* d) {
+  const afqmc_params& p = s->p;
+  const Bufs& b = s->b;
+  d->kind = TC_JOB_PHI;
+  d->g.m = 2 * p.N * p.nwalkers;
+  d->g.n = p.M;
+  d->g.k = 2 * b.Mp;
+  d->g.A = b.acc32;
+  d->g.lda = 2L * b.Mp;
+  d->g.B = b.Bh_tf;
+  d->g.ldb = 2L * b.Mp;
+  d->g.tf32 = true;
+  d->g.err = b.status;
+  d->phiT = phi_out;
+  d->wt = b.wt;
+  d->N = p.N;
+  d->M = p.M;
+  d->phi_lo = phi_lo_out;
+  d->lo_kind = b.lo_kind;
+  d->Mp = b.Mp;
+  d->acc_id = b.acc32;
+}
+
 int force_bias_gemm(afqmc_state* s) {
   const afqmc_params& p = s->p;
   const Bufs& b = s->b;
@@ -330,18 +427,9 @@ int force_bias_gemm(afqmc_state* s) {
     return AFQMC_OK;
   }
   if (b.mixed) {
-    // t[(w,c)][g] = 2 sum_(i,p) Theta^T_lo[(w,c)][(i,p)] Lh_lo[g][(i,p)] on tcgen05
-    TcGemm g;
-    g.m = 2 * p.nwalkers;
-    g.n = p.nchol;
-    g.k = p.N * b.Mp;
-    g.A = b.th_lo;
-    g.lda = (long)p.N * b.Mp;
-    g.B = b.Lh_lo;
-    g.ldb = (long)p.N * b.Mp;
-    g.tf32 = b.lo_kind == LO_TF32;
-    g.err = b.status;
-    AFQ_TRY(tc_gemm_store(g, b.t32, p.nchol, 2.0f, s->st));
+    TcJobDesc d;
+    desc_force_bias(s, &d);
+    AFQ_TRY(tc_job_launch(d, s->st));
     s->t_fresh = true;
     return AFQMC_OK;
   }
@@ -488,71 +576,43 @@ static int propagate_f64(afqmc_state* s) {
 // step from the operand copy phi_lo_in, the Taylor series and the last half
 // step (TF32), which stores float64 orbitals (walkers with W != 0) and their
 // operand copy.
-int apply_b_mixed(afqmc_state* s, const double* phi_in, const void* phi_lo_in, double* phi_out,
-                  void* phi_lo_out) {
+// terms k = 1..n of the Taylor series: S = T_1 + ... + T_n into columns
+// [Mp, 2 Mp) of acc; the whole series in one launch when the term fits in
+// shared memory, else one launch per term
+int step_taylor(afqmc_state* s) {
   const afqmc_params& p = s->p;
   const Bufs& b = s->b;
-  const int W = p.nwalkers, N = p.N, M = p.M, G = p.nchol;
-  // V = i sqrt(dt) sum_g x_g L_g over the upper 16 x 16 blocks of the (p, q)
-  // grid (V is symmetric), each block and its mirror written straight into
-  // the [Re V | Im V] operand rows of the Taylor terms
-  prof_begin(s, AFQMC_PH_V);
-  TcGemm g;
-  g.m = 2 * W;
-  g.n = b.nblkV * 256;
-  g.k = G;
-  g.A = b.x_lo;
-  g.lda = b.Gp;
-  g.B = b.LbT_lo;
-  g.ldb = b.Gp;
-  g.tf32 = b.lo_kind == LO_TF32;
-  g.err = b.status;
-  AFQ_TRY(tc_v_full(g, b.V_lo, b.lo_kind, W, M, b.Mp, s->sdt, s->st));
-  prof_end(s);
-  // first half step: T_0 = (B_half Phi)^T = Phi^T + (Phi_lo D_B)^T, D_B =
-  // B_half - I (the identity part added in float64 orbitals by the epilogue),
-  // into columns [0, Mp) of the FP32 rows of acc (pitch 2 Mp) and, as the 0th
-  // Taylor operand, into Tb0
-  prof_begin(s, AFQMC_PH_BHALF);
-  TcGemm h1;
-  h1.m = 2 * N * W;
-  h1.n = M;
-  h1.k = M;
-  h1.A = phi_lo_in;
-  h1.lda = b.Mp;
-  h1.B = b.Bh_lo;
-  h1.ldb = b.Mp;
-  h1.tf32 = b.lo_kind == LO_TF32;
-  h1.err = b.status;
-  AFQ_TRY(tc_prop_first(h1, b.acc32, 2L * b.Mp, b.Tb0, phi_in, b.lo_kind, N, M, b.Mp, s->st));
-  prof_end(s);
-  // terms k = 1..n: T_k = V T_{k-1} / k, S = T_1 + ... + T_n into columns
-  // [Mp, 2 Mp) of acc; the whole series in one launch when the term fits in
-  // shared memory, else one launch per term
   prof_begin(s, AFQMC_PH_TAYLOR);
-  AFQ_TRY(taylor_apply(b.V_lo, b.Tb0, b.Tb1, b.acc32 + b.Mp, 2L * b.Mp, b.lo_kind, W, N, M, b.Mp,
-                       p.taylor_order, false, b.status, s->st));
-  prof_end(s);
-  // last half step (TF32): Phi <- B_half (T_0 + S) = (T_0 + S) + [T_0 | S]
-  // [D_B | D_B] (one K = 2 Mp product; T_0 + S added in the epilogue); stored
-  // for live walkers
-  prof_begin(s, AFQMC_PH_BHALF);
-  TcGemm h2;
-  h2.m = 2 * N * W;
-  h2.n = M;
-  h2.k = 2 * b.Mp;
-  h2.A = b.acc32;
-  h2.lda = 2L * b.Mp;
-  h2.B = b.Bh_tf;
-  h2.ldb = 2L * b.Mp;
-  h2.tf32 = true;
-  h2.err = b.status;
-  AFQ_TRY(tc_prop_last(h2, phi_out, b.wt, N, M, phi_lo_out, b.lo_kind, b.Mp, b.acc32, s->st));
+  AFQ_TRY(taylor_apply(b.V_lo, b.Tb0, b.Tb1, b.acc32 + b.Mp, 2L * b.Mp, b.lo_kind, p.nwalkers, p.N,
+                       p.M, b.Mp, p.taylor_order, false, b.status, s->st));
   prof_end(s);
   return AFQMC_OK;
 }
 
-static int propagate_mixed(afqmc_state* s) {
+int apply_b_mixed(afqmc_state* s, const double* phi_in, const void* phi_lo_in, double* phi_out,
+                  void* phi_lo_out) {
+  TcJobDesc d;
+  prof_begin(s, AFQMC_PH_V);
+  desc_v(s, &d);
+  AFQ_TRY(tc_job_launch(d, s->st));
+  prof_end(s);
+  prof_begin(s, AFQMC_PH_BHALF);
+  d = TcJobDesc();
+  desc_half1(s, phi_in, phi_lo_in, &d);
+  AFQ_TRY(tc_job_launch(d, s->st));
+  prof_end(s);
+  AFQ_TRY(step_taylor(s));
+  prof_begin(s, AFQMC_PH_BHALF);
+  d = TcJobDesc();
+  desc_half2(s, phi_out, phi_lo_out, &d);
+  AFQ_TRY(tc_job_launch(d, s->st));
+  prof_end(s);
+  return AFQMC_OK;
+}
+
+// fields x = xi - xbar from the (fresh) force bias; on the mixed path also
+// their BF16/TF32 operand rows
+int step_fields(afqmc_state* s) {
   const afqmc_params& p = s->p;
   const Bufs& b = s->b;
   const int W = p.nwalkers, G = p.nchol;
@@ -567,13 +627,19 @@ static int propagate_mixed(afqmc_state* s) {
   AFQ_TRY(launch_field(fa, s->st));
   prof_end(s);
   if (s->bp_on) AFQ_TRY(bp_record_fields(s));
+  return AFQMC_OK;
+}
+
+static int propagate_mixed(afqmc_state* s) {
+  const Bufs& b = s->b;
+  AFQ_TRY(step_fields(s));
   return apply_b_mixed(s, b.phiT, b.phi_lo, b.phiT, b.phi_lo);
 }
 
+int step_after(afqmc_state* s);
+
 static int step_once(afqmc_state* s) {
-  const afqmc_params& p = s->p;
   const Bufs& b = s->b;
-  const int W = p.nwalkers, N = p.N, M = p.M;
   // force bias traces t = 2 Tr(Lh_g Theta) for every walker (Eq. precomputing2)
   if (!s->t_fresh) {
     prof_begin(s, AFQMC_PH_FORCE_BIAS);
@@ -583,7 +649,15 @@ static int step_once(afqmc_state* s) {
   // fields, the force bias and x = xi - xbar; then exp(-dt v0'/2) T_n(V)
   // exp(-dt v0'/2) applied to every walker's orbitals
   AFQ_TRY(b.mixed ? propagate_mixed(s) : propagate_f64(s));
-  // new overlap, log det, Theta; then the weights (and step += 1)
+  return step_after(s);
+}
+
+// After the propagation: new overlap, log det, Theta; the weights (and step +=
+// 1); then the periodic Gram-Schmidt, comb and energy record.
+int step_after(afqmc_state* s) {
+  const afqmc_params& p = s->p;
+  const Bufs& b = s->b;
+  const int W = p.nwalkers, N = p.N, M = p.M;
   AFQ_TRY(overlap_update(s, false, true));
   WeightArgs wa{W, p.mode, p.dt, s->sdt, s->H0p, s->e_shift, s->wmax, b.ld_new, b.ld, b.scal,
                 b.wt, b.counters + CTR_NONFINITE,

@@ -19,6 +19,7 @@
 
 #include <map>
 #include <mutex>
+#include <vector>
 
 #include "kernels.cuh"
 #include "tc.cuh"
@@ -50,19 +51,61 @@ __device__ __forceinline__ bool epi_bar_or(bool flag) {
   return out != 0;
 }
 
-// Persistent variant for epilogues that need no shared memory: one CTA per SM
-// walks the output tiles t = blockIdx.x, blockIdx.x + gridDim.x, ... (tile
-// (bx, by) = (t % gx, t / gx), so CTAs running together share B tiles in L2).
-// Two TMEM accumulators of BN columns: the epilogue warps drain tile j while
-// the MMA thread fills tile j + 1 (tfull / tempty mbarriers per accumulator).
-// With Epi::kMT = 2 a tile is 256 rows: one 256-row A box per stage feeds two
-// M=128 MMAs against the same B tile (half the B traffic per output), and when
-// two such tiles do not fit in tensor memory a single accumulator is used.
-template <int BN, int STAGES, bool TF32, class Epi>
-__global__ void __launch_bounds__(64 + 32 * Epi::kWarps, 1)
-    k_tc_gemm_persistent(const __grid_constant__ CUtensorMap tmA,
-                         const __grid_constant__ CUtensorMap tmB, int M, int N, int K, int gx,
-                         int ntiles, Epi epi, int* err) {
+// One contraction of a grouped launch: its operands' tensor maps, sizes,
+// output tiles (numbered from tile0 in the launch) and epilogue.
+template <class Epi>
+struct alignas(64) GemmJob {
+  CUtensorMap tmA, tmB;
+  int M, N, K, gx, ntiles, tile0;
+  int* err;
+  Epi epi;
+};
+
+// What the kernel needs of the contraction that owns tile t.
+template <class Epi>
+struct JobView {
+  const CUtensorMap* tmA;
+  const CUtensorMap* tmB;
+  int M, N, K, gx, t0;
+  int* err;
+  const Epi* epi;
+};
+
+// The contractions of a launch: one from the kernel parameters, or a table
+// in global memory (jobs in order of tile0; a linear search, the tables are short).
+template <class Epi, bool GROUPED>
+struct JobTable {
+  const GemmJob<Epi>* jobs;
+  int njobs;
+  const CUtensorMap* a;
+  const CUtensorMap* b;
+  int M, N, K, gx;
+  int* err;
+  const Epi* epi;
+  __device__ __forceinline__ JobView<Epi> at(int t) const {
+    if constexpr (!GROUPED) {
+      return {a, b, M, N, K, gx, 0, err, epi};
+    } else {
+      int j = 0;
+      while (j + 1 < njobs && jobs[j + 1].tile0 <= t) ++j;
+      const GemmJob<Epi>& J = jobs[j];
+      return {&J.tmA, &J.tmB, J.M, J.N, J.K, J.gx, J.tile0, J.err, &J.epi};
+    }
+  }
+};
+
+// Persistent contraction body for epilogues that need no shared memory: one
+// CTA per SM walks the output tiles t = blockIdx.x, blockIdx.x + gridDim.x,
+// ... of all contractions of the launch (tile (bx, by) = (lt % gx, lt / gx)
+// of its contraction, lt = t - tile0, so CTAs running together share B tiles
+// in L2).  Two TMEM accumulators of BN columns: the epilogue warps drain tile j
+// while the MMA thread fills tile j + 1 (tfull / tempty mbarriers per
+// accumulator).  With Epi::kMT = 2 a tile is 256 rows: one 256-row A box per
+// stage feeds two M=128 MMAs against the same B tile (half the B traffic per
+// output), and when two such tiles do not fit in tensor memory a single
+// accumulator is used.
+template <int BN, int STAGES, bool TF32, class Epi, bool GROUPED>
+__device__ __forceinline__ void gemm_body(const JobTable<Epi, GROUPED>& tab, int ntiles) {
   extern __shared__ uint8_t smem_raw[];
   constexpr int MT = Epi::kMT;
   using S = Smem<BN, STAGES, MT>;
@@ -78,7 +121,6 @@ __global__ void __launch_bounds__(64 + 32 * Epi::kWarps, 1)
   constexpr int ELEM = TF32 ? 4 : 2;
   constexpr int BK = BKB / ELEM;
   constexpr int KSTEPS = BKB / 32;
-  const int nk = (K + BK - 1) / BK;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -112,29 +154,33 @@ __global__ void __launch_bounds__(64 + 32 * Epi::kWarps, 1)
   if (warp == 0 && lane == 0) {
     int it = 0;
     for (int t = blockIdx.x; t < ntiles && !*(volatile int*)abort_flag; t += gridDim.x) {
-      const int bx = t % gx, by = t / gx;
-      const int m0 = epi.m_origin(bx, by), n0 = epi.n_origin(bx, by);
+      const JobView<Epi> v = tab.at(t);
+      const int lt = t - v.t0, bx = lt % v.gx, by = lt / v.gx;
+      const int m0 = v.epi->m_origin(bx, by), n0 = v.epi->n_origin(bx, by);
+      const int nk = (v.K + BK - 1) / BK;
       for (int kb = 0; kb < nk; ++kb, ++it) {
         const int s = it % STAGES;
-        if (it >= STAGES && !mbar_wait(&empty[s], ((it / STAGES) - 1) & 1, err, 11)) {
+        if (it >= STAGES && !mbar_wait(&empty[s], ((it / STAGES) - 1) & 1, v.err, 11)) {
           *(volatile int*)abort_flag = 1;
           break;
         }
         uint8_t* a = smem + s * S::STAGE;
         mbar_expect_tx(&full[s], S::STAGE);
-        tma_load_2d(a, &tmA, &full[s], kb * BK, m0);
+        tma_load_2d(a, v.tmA, &full[s], kb * BK, m0);
         if constexpr (Epi::kB3D)
-          tma_load_3d(a + S::A_BYTES, &tmB, &full[s], kb * BK, 0, epi.b_plane(bx, by));
+          tma_load_3d(a + S::A_BYTES, v.tmB, &full[s], kb * BK, 0, v.epi->b_plane(bx, by));
         else
-          tma_load_2d(a + S::A_BYTES, &tmB, &full[s], kb * BK, n0);
+          tma_load_2d(a + S::A_BYTES, v.tmB, &full[s], kb * BK, n0);
       }
     }
   } else if (warp == 1 && lane == 0) {
     constexpr uint32_t idesc = instr_desc(TF32 ? 2u : 1u, (uint32_t)BN);
     int it = 0, j = 0;
     for (int t = blockIdx.x; t < ntiles && !*(volatile int*)abort_flag; t += gridDim.x, ++j) {
+      const JobView<Epi> v = tab.at(t);
+      const int nk = (v.K + BK - 1) / BK;
       const int acc = NBUF == 2 ? (j & 1) : 0;
-      if (j >= NBUF && !mbar_wait(&tempty[acc], ((j / NBUF) - 1) & 1, err, 12)) {
+      if (j >= NBUF && !mbar_wait(&tempty[acc], ((j / NBUF) - 1) & 1, v.err, 12)) {
         *(volatile int*)abort_flag = 1;
         break;
       }
@@ -143,7 +189,7 @@ __global__ void __launch_bounds__(64 + 32 * Epi::kWarps, 1)
       bool ok = true;
       for (int kb = 0; kb < nk; ++kb, ++it) {
         const int s = it % STAGES;
-        if (!mbar_wait(&full[s], (it / STAGES) & 1, err, 13)) {
+        if (!mbar_wait(&full[s], (it / STAGES) & 1, v.err, 13)) {
           ok = false;
           break;
         }
@@ -169,20 +215,22 @@ __global__ void __launch_bounds__(64 + 32 * Epi::kWarps, 1)
     float* esm = Epi::kSmemBytes ? reinterpret_cast<float*>(smem + S::RING + 256) : nullptr;
     int j = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++j) {
+      const JobView<Epi> v = tab.at(t);
       const int acc = NBUF == 2 ? (j & 1) : 0;
-      bool bad = !mbar_wait(&tfull[acc], (j / NBUF) & 1, err, 14);
+      bool bad = !mbar_wait(&tfull[acc], (j / NBUF) & 1, v.err, 14);
       fence_after();
       // one decision for every epilogue warp (barrier 1 with an OR of the flags)
       if (epi_bar_or<Epi::kWarps>(bad || *(volatile int*)abort_flag)) {
         *(volatile int*)abort_flag = 1;
         break;
       }
-      const int bx = t % gx, by = t / gx;
+      const int lt = t - v.t0, bx = lt % v.gx, by = lt / v.gx;
+      const Epi& epi = *v.epi;
 #pragma unroll
       for (int mt = 0; mt < MT; ++mt)
         epi.template run<BN>(tmem + (uint32_t)acc * ASTRIDE + (uint32_t)(mt * BN), q, lane,
                              warp - 2, bx, by, epi.m_origin(bx, by) + mt * BM,
-                             epi.n_origin(bx, by), M, N, esm);
+                             epi.n_origin(bx, by), v.M, v.N, esm);
       fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&tempty[acc]);
@@ -195,6 +243,25 @@ __global__ void __launch_bounds__(64 + 32 * Epi::kWarps, 1)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                  "r"(TCOLS));
   }
+}
+
+// One contraction, its tensor maps and epilogue as kernel parameters.
+template <int BN, int STAGES, bool TF32, class Epi>
+__global__ void __launch_bounds__(64 + 32 * Epi::kWarps, 1)
+    k_tc_gemm_persistent(const __grid_constant__ CUtensorMap tmA,
+                         const __grid_constant__ CUtensorMap tmB, int M, int N, int K, int gx,
+                         int ntiles, const __grid_constant__ Epi epi, int* err) {
+  const JobTable<Epi, false> tab{nullptr, 1, &tmA, &tmB, M, N, K, gx, err, &epi};
+  gemm_body<BN, STAGES, TF32, Epi, false>(tab, ntiles);
+}
+
+// Several contractions (of several independent states) in one persistent
+// launch: a work list over (contraction, tile).
+template <int BN, int STAGES, bool TF32, class Epi>
+__global__ void __launch_bounds__(64 + 32 * Epi::kWarps, 1)
+    k_tc_gemm_grouped(const GemmJob<Epi>* __restrict__ jobs, int njobs, int ntiles) {
+  const JobTable<Epi, true> tab{jobs, njobs, nullptr, nullptr, 0, 0, 0, 0, nullptr, nullptr};
+  gemm_body<BN, STAGES, TF32, Epi, true>(tab, ntiles);
 }
 
 // ------------------------------------------------------------ epilogues -----
@@ -957,6 +1024,252 @@ int tc_prop_last(const TcGemm& g, double* phiT, const double* wt, int N, int M, 
   }
   if (g.tf32) return launch_tc_persistent<256, 4, true>(g, e, gx, gy, st);
   return launch_tc_persistent<256, 4, false>(g, e, gx, gy, st);
+}
+
+// ---- per-step contractions as job descriptors, alone or grouped ------------
+int tc_job_launch(const TcJobDesc& d, cudaStream_t st) {
+  switch (d.kind) {
+    case TC_JOB_STORE:
+      return tc_gemm_store(d.g, d.C, d.ldc, d.alpha, st);
+    case TC_JOB_V:
+      return tc_v_full(d.g, d.V, d.lo_kind, d.W, d.M, d.Mp, d.sdt, st);
+    case TC_JOB_PROP0:
+      return tc_prop_first(d.g, d.acc, d.ldacc, d.tb, d.phi_id, d.lo_kind, d.N, d.M, d.Mp, st);
+    case TC_JOB_PHI:
+      return tc_prop_last(d.g, d.phiT, d.wt, d.N, d.M, d.phi_lo, d.lo_kind, d.Mp, d.acc_id, st);
+  }
+  set_error("tc job: unknown kind %d", d.kind);
+  return AFQMC_EINVAL;
+}
+
+struct TcGrouped {
+  int kind = 0, bn = 0, stages = 0, njobs = 0, ntiles = 0;
+  bool tf32 = false;
+  void* d_jobs = nullptr;
+};
+
+namespace {
+// The job of one descriptor with tile width bn: operand maps, grid, epilogue.
+template <class Epi>
+int fill_job(tc::GemmJob<Epi>* j, const TcGemm& g, int bn, int gx, int gy, const Epi& e) {
+  const int eb = g.tf32 ? 4 : 2;
+  AFQ_TRY(make_tmap(&j->tmA, g.A, eb, g.m, g.k, g.lda, tc::BM * Epi::kMT));
+  AFQ_TRY(make_tmap(&j->tmB, g.B, eb, g.n, g.k, g.ldb, bn));
+  j->M = g.m;
+  j->N = g.n;
+  j->K = g.k;
+  j->gx = gx;
+  j->ntiles = gx * gy;
+  j->tile0 = 0;
+  j->err = g.err;
+  j->epi = e;
+  return AFQMC_OK;
+}
+
+int make_job(const TcJobDesc& d, int bn, tc::GemmJob<tc::EpiStore>* j) {
+  tc::EpiStore e{d.C, d.ldc, d.alpha, bn};
+  return fill_job(j, d.g, bn, cdiv(d.g.m, tc::BM), cdiv(d.g.n, bn), e);
+}
+int make_job(const TcJobDesc& d, int bn, tc::GemmJob<tc::EpiV>* j) {
+  const int nb = d.Mp / 16;
+  if (d.Mp % 16 || d.g.n != nb * (nb + 1) / 2 * 256) {
+    set_error("grouped V: Mp=%d and %d operand rows do not match", d.Mp, d.g.n);
+    return AFQMC_EINVAL;
+  }
+  tc::EpiV e{d.V, d.lo_kind, d.W, d.M, d.Mp, (float)d.sdt};
+  return fill_job(j, d.g, bn, cdiv(d.g.m, tc::BM * tc::EpiV::kMT), nb * (nb + 1) / 2, e);
+}
+int make_job(const TcJobDesc& d, int bn, tc::GemmJob<tc::EpiProp0>* j) {
+  tc::EpiProp0 e{d.acc, d.ldacc, d.tb, d.phi_id, d.lo_kind, d.N, d.M, d.Mp, d.g.m, bn};
+  return fill_job(j, d.g, bn, cdiv(d.g.m, tc::BM), cdiv(d.M, bn), e);
+}
+int make_job(const TcJobDesc& d, int bn, tc::GemmJob<tc::EpiPhi>* j) {
+  if (d.g.lda != 2L * d.Mp) {
+    set_error("grouped last half step: operand pitch %ld, want 2 Mp = %d", d.g.lda, 2 * d.Mp);
+    return AFQMC_EINVAL;
+  }
+  tc::EpiPhi e{d.phiT, d.wt, d.N, d.M, d.g.m, bn, d.phi_lo, d.lo_kind, d.Mp, d.acc_id};
+  return fill_job(j, d.g, bn, cdiv(d.g.m, tc::BM), cdiv(d.M, bn), e);
+}
+
+// Host table of the n jobs (tile0 = running tile count), copied to the device.
+template <class Epi>
+int build_table(const TcJobDesc* d, int n, int bn, TcGrouped* gr) {
+  std::vector<tc::GemmJob<Epi>> jobs((size_t)n);
+  long tiles = 0;
+  for (int i = 0; i < n; ++i) {
+    AFQ_TRY(make_job(d[i], bn, &jobs[i]));
+    jobs[i].tile0 = (int)tiles;
+    tiles += jobs[i].ntiles;
+  }
+  if (tiles > 0x7fffffffL) {
+    set_error("grouped contraction: too many tiles");
+    return AFQMC_EINVAL;
+  }
+  AFQ_CUDA(cudaMalloc(&gr->d_jobs, sizeof(tc::GemmJob<Epi>) * (size_t)n));
+  AFQ_CUDA(cudaMemcpy(gr->d_jobs, jobs.data(), sizeof(tc::GemmJob<Epi>) * (size_t)n,
+                      cudaMemcpyHostToDevice));
+  gr->njobs = n;
+  gr->ntiles = (int)tiles;
+  return AFQMC_OK;
+}
+
+template <int BN, int STAGES, bool TF32, class Epi>
+int launch_grouped(const TcGrouped& gr, cudaStream_t st) {
+  constexpr int kTotal = tc::Smem<BN, STAGES, Epi::kMT>::TOTAL + Epi::kSmemBytes;
+  static_assert(kTotal <= 232448, "shared memory");
+  auto kern = tc::k_tc_gemm_grouped<BN, STAGES, TF32, Epi>;
+  static std::atomic<unsigned long long> attr{0};
+  AFQ_TRY(smem_attr_once(kern, kTotal, attr));
+  if (gr.ntiles <= 0) return AFQMC_OK;
+  const int grid = gr.ntiles < tc_sm_count() ? gr.ntiles : tc_sm_count();
+  AFQ_LAUNCH(kern, grid, 64 + 32 * Epi::kWarps, kTotal, st,
+             static_cast<const tc::GemmJob<Epi>*>(gr.d_jobs), gr.njobs, gr.ntiles);
+  return AFQMC_OK;
+}
+
+template <bool TF32>
+int dispatch_grouped(const TcGrouped& gr, cudaStream_t st) {
+  switch (gr.kind) {
+    case TC_JOB_STORE:
+      if (gr.bn == 64) return launch_grouped<64, 8, TF32, tc::EpiStore>(gr, st);
+      if (gr.bn == 128) return launch_grouped<128, 6, TF32, tc::EpiStore>(gr, st);
+      return launch_grouped<256, 4, TF32, tc::EpiStore>(gr, st);
+    case TC_JOB_V:
+      return launch_grouped<256, 3, TF32, tc::EpiV>(gr, st);
+    case TC_JOB_PROP0:
+      if (gr.bn == 160) return launch_grouped<160, 6, TF32, tc::EpiProp0>(gr, st);
+      return launch_grouped<256, 4, TF32, tc::EpiProp0>(gr, st);
+    case TC_JOB_PHI:
+      if (gr.bn == 160) return launch_grouped<160, 6, TF32, tc::EpiPhi>(gr, st);
+      return launch_grouped<256, 4, TF32, tc::EpiPhi>(gr, st);
+  }
+  set_error("grouped contraction: unknown kind %d", gr.kind);
+  return AFQMC_EINVAL;
+}
+
+// Tile-width candidates of each kind (the ones with an instantiated kernel).
+std::vector<int> bn_candidates(int kind) {
+  switch (kind) {
+    case TC_JOB_STORE:
+      return {256, 128, 64};
+    case TC_JOB_V:
+      return {256};
+    default:
+      return {160, 256};
+  }
+}
+}  // namespace
+
+int tc_grouped_create(const TcJobDesc* d, int n, int bn, TcGrouped** out) {
+  *out = nullptr;
+  if (n < 1) {
+    set_error("grouped contraction: no jobs");
+    return AFQMC_EINVAL;
+  }
+  for (int i = 1; i < n; ++i)
+    if (d[i].kind != d[0].kind || d[i].g.tf32 != d[0].g.tf32) {
+      set_error("grouped contraction: jobs of different kinds or precisions");
+      return AFQMC_EINVAL;
+    }
+  const int kind = d[0].kind;
+  if (bn == 0) bn = kind == TC_JOB_STORE || kind == TC_JOB_V ? 256 : half_step_bn(d[0].M);
+  bool ok = false;
+  for (int c : bn_candidates(kind)) ok = ok || c == bn;
+  if (!ok) {
+    set_error("grouped contraction: no kernel for tile width %d", bn);
+    return AFQMC_EINVAL;
+  }
+  TcGrouped* gr = new TcGrouped();
+  gr->kind = kind;
+  gr->bn = bn;
+  gr->tf32 = d[0].g.tf32;
+  int r = AFQMC_OK;
+  switch (kind) {
+    case TC_JOB_STORE:
+      r = build_table<tc::EpiStore>(d, n, bn, gr);
+      break;
+    case TC_JOB_V:
+      r = build_table<tc::EpiV>(d, n, bn, gr);
+      break;
+    case TC_JOB_PROP0:
+      r = build_table<tc::EpiProp0>(d, n, bn, gr);
+      break;
+    case TC_JOB_PHI:
+      r = build_table<tc::EpiPhi>(d, n, bn, gr);
+      break;
+    default:
+      set_error("grouped contraction: unknown kind %d", kind);
+      r = AFQMC_EINVAL;
+  }
+  if (r != AFQMC_OK) {
+    tc_grouped_destroy(gr);
+    return r;
+  }
+  *out = gr;
+  return AFQMC_OK;
+}
+
+int tc_grouped_launch(const TcGrouped* gr, cudaStream_t st) {
+  return gr->tf32 ? dispatch_grouped<true>(*gr, st) : dispatch_grouped<false>(*gr, st);
+}
+
+int tc_grouped_tune(const TcJobDesc* d, int n, cudaStream_t st, TcGrouped** out) {
+  *out = nullptr;
+  if (n < 1 || d[0].kind == TC_JOB_PHI) {
+    set_error("grouped tune: no jobs, or a kind whose epilogue overwrites the walkers");
+    return AFQMC_EINVAL;
+  }
+  cudaEvent_t e0, e1;
+  AFQ_CUDA(cudaEventCreate(&e0));
+  AFQ_CUDA(cudaEventCreate(&e1));
+  TcGrouped* best = nullptr;
+  float best_ms = 1e30f;
+  int r = AFQMC_OK;
+  for (int bn : bn_candidates(d[0].kind)) {
+    TcGrouped* gr = nullptr;
+    r = tc_grouped_create(d, n, bn, &gr);
+    if (r != AFQMC_OK) break;
+    float ms = 0.f;
+    r = tc_grouped_launch(gr, st);  // warm-up (and first-use set-up)
+    if (r == AFQMC_OK && cudaEventRecord(e0, st) == cudaSuccess) {
+      for (int rep = 0; rep < 2 && r == AFQMC_OK; ++rep) r = tc_grouped_launch(gr, st);
+      if (r == AFQMC_OK && (cudaEventRecord(e1, st) != cudaSuccess ||
+                            cudaEventSynchronize(e1) != cudaSuccess ||
+                            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)) {
+        set_error("grouped tune: event timing failed");
+        r = AFQMC_ECUDA;
+      }
+    }
+    if (r != AFQMC_OK) {
+      tc_grouped_destroy(gr);
+      break;
+    }
+    if (ms < best_ms) {
+      best_ms = ms;
+      tc_grouped_destroy(best);
+      best = gr;
+    } else {
+      tc_grouped_destroy(gr);
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (r != AFQMC_OK) {
+    tc_grouped_destroy(best);
+    return r;
+  }
+  *out = best;
+  return AFQMC_OK;
+}
+
+int tc_grouped_bn(const TcGrouped* gr) { return gr ? gr->bn : 0; }
+int tc_grouped_tiles(const TcGrouped* gr) { return gr ? gr->ntiles : 0; }
+
+void tc_grouped_destroy(TcGrouped* gr) {
+  if (!gr) return;
+  if (gr->d_jobs) cudaFree(gr->d_jobs);
+  delete gr;
 }
 
 // Exchange blocking: RG Cholesky vectors x CW walkers per 128 x 256 tile.

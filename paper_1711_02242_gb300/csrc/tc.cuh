@@ -70,6 +70,46 @@ int make_tmap_nd(CUtensorMap* m, const void* base, int elem_bytes, int rank, con
                  const long* stride_bytes, const int* box);
 int tc_sm_count();
 
+// A per-step contraction of the mixed path as a state describes it: run on
+// its own (tc_job_launch, the same launches as tc_gemm_store / tc_v_full /
+// tc_prop_first / tc_prop_last) or together with other states' contractions
+// of the same kind in one persistent launch (TcGrouped: a work list over
+// (contraction, tile), each contraction's tensor maps in a device table).
+enum TcJobKind { TC_JOB_STORE = 0, TC_JOB_V = 1, TC_JOB_PROP0 = 2, TC_JOB_PHI = 3 };
+struct TcJobDesc {
+  int kind = TC_JOB_STORE;
+  TcGemm g;
+  float* C = nullptr;  // store: C = alpha * D, pitch ldc
+  long ldc = 0;
+  float alpha = 1.f;
+  void* V = nullptr;  // V: the [Re V | Im V] operand rows
+  int W = 0;
+  double sdt = 0.0;
+  int lo_kind = 0, N = 0, M = 0, Mp = 0;
+  float* acc = nullptr;  // first half step (tc_prop_first's arguments)
+  long ldacc = 0;
+  void* tb = nullptr;
+  const double* phi_id = nullptr;
+  double* phiT = nullptr;  // last half step (tc_prop_last's arguments)
+  const double* wt = nullptr;
+  void* phi_lo = nullptr;
+  const float* acc_id = nullptr;
+};
+int tc_job_launch(const TcJobDesc& d, cudaStream_t st);
+
+struct TcGrouped;  // one grouped launch: its device job table and tile configuration
+// Build the grouped launch of n descriptors of one kind and precision with
+// tile width bn (0: the kind's default); allocates the device table.
+int tc_grouped_create(const TcJobDesc* d, int n, int bn, TcGrouped** out);
+// Time the kind's tile-width candidates (not under capture; every candidate
+// runs on the descriptors' own buffers, so not for TC_JOB_PHI, whose epilogue
+// overwrites the orbitals) and keep the fastest.
+int tc_grouped_tune(const TcJobDesc* d, int n, cudaStream_t st, TcGrouped** out);
+int tc_grouped_launch(const TcGrouped* g, cudaStream_t st);
+int tc_grouped_bn(const TcGrouped* g);
+int tc_grouped_tiles(const TcGrouped* g);
+void tc_grouped_destroy(TcGrouped* g);
+
 // Exchange blocking: RG Cholesky vectors x CW walkers per 128 x 256 tile, the
 // 2N columns of a walker padded to NPAD (a power of two >= 16).
 void exchange_tile(int N, int* RG, int* CW, int* NPAD);

@@ -1,5 +1,9 @@
 """Uneven systems advanced by one graph launch per block (afqmc_group_*):
-each run is bit-identical to the same run stepped alone."""
+each run is bit-identical to the same run stepped alone, whether the block is
+captured as every run's own kernels or - mixed precision - with each of the
+step's four tensor-core contractions of all runs as one grouped persistent
+launch (tile widths timed on the runs' buffers), or switched between the two
+by the group's timed choice."""
 import numpy as np
 import pytest
 
@@ -39,17 +43,25 @@ def make(pkg, w, prec):
     return pkg.AfqmcRun(h1, L, C, p, stream=torch.cuda.Stream())
 
 
-@pytest.mark.parametrize("prec", [0, 2])
-def test_group_matches_runs_stepped_alone(pkg, prec):
+@pytest.mark.parametrize("prec,grouped", [(0, True), (2, True), (2, False), (1, True),
+                                          (2, "auto")])
+def test_group_matches_runs_stepped_alone(pkg, prec, grouped):
     alone = [make(pkg, w, prec) for w in SYSTEMS]
     for r in alone:
         r.propagate(20)
-    grouped = [make(pkg, w, prec) for w in SYSTEMS]
-    g = pkg.AfqmcGroup(grouped)
+    grouped_runs = [make(pkg, w, prec) for w in SYSTEMS]
+    g = pkg.AfqmcGroup(grouped_runs)
+    g.set_grouped(grouped)
     g.propagate(10)
+    on, bn = g.tiles()
+    # the grouped contractions serve mixed runs only (in the timed choice the
+    # first blocks use them)
+    assert on == (bool(grouped) and prec != 0)
+    if on:
+        assert bn[0] in (64, 128, 256) and bn[1] == 256 and bn[2] in (160, 256) and bn[3] == bn[2]
     g.propagate(10)
     g.synchronize()
-    for a, b in zip(alone, grouped):
+    for a, b in zip(alone, grouped_runs):
         pa, wa, la = a.get_walkers()
         pb, wb, lb = b.get_walkers()
         assert np.array_equal(pa, pb) and np.array_equal(wa, wb) and np.array_equal(la, lb)
