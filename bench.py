@@ -78,7 +78,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # of the source file the kernel was built from and the precisions whose step
 # runs that kernel; a figure whose source has changed since, or that belongs
 # to another kernel at this precision, is reported as null.
-GEMM_KERNEL = "__global__ void __launch_bounds__(64 + 32 * Epi::kWarps, 1)"
+GEMM_KERNEL = "__device__ __forceinline__ void gemm_body("
 TRAFFIC = {
     "theta": [# k_theta_rows_f32 on the float64 S^-1 (the bf16 default path)
               {"bytes": (66.846720 + 26.307840) * 1e6, "precisions": ("bf16",),
@@ -89,19 +89,26 @@ TRAFFIC = {
               {"bytes": (64.544512 + 30.260480) * 1e6, "precisions": ("bf16-f64theta",),
                "function": "__global__ void __launch_bounds__(TH_T) k_theta_rows(OverlapArgs a)",
                "sha": "d7ee3083bab22e614e7aa9c51aff2886d255680c62a6454f637a089a17969ae7"}],
-    "overlap": {"bytes": (8.234752 + 0.0) * 1e6, "sha": "d8af088925f6dd017e10c429fdb6a28ef844edf64bdcef66e2f823c786f2631e", "precisions": ("bf16-f32lu",)},
-    "qr": {"bytes": (61.510144 + 15.014656) * 1e6, "sha": "d8af088925f6dd017e10c429fdb6a28ef844edf64bdcef66e2f823c786f2631e", "precisions": ("bf16-f32lu",)},
+    # k_overlap<double> and k_mgs (float64, the bf16 default path), pinned to
+    # their own text (captures in profiles/overlap_inverse_m300_bf16.md and
+    # profiles/mgs_m300_bf16.md)
+    "overlap": {"bytes": (8.244992 + 0.0) * 1e6, "precisions": ("bf16",),
+                "function": "__global__ void __launch_bounds__(OV_T) k_overlap(OverlapArgs a)",
+                "sha": "5905df615412e8d5881361e99808acd80656d2a0414eef96dd142e0f6e82e0bc"},
+    "qr": {"bytes": (61.483264 + 34.291200) * 1e6, "precisions": ("bf16",),
+           "function": "__global__ void __launch_bounds__(256) k_mgs(MgsArgs a)",
+           "sha": "4e08b7f77fcd6fee61eeb48c18f47fe8220b9dacfe0af8c3a22f28d76f55f22f"},
     # the tensor-core kernels: pinned to the kernel's text (and its epilogue's),
     # unchanged since these captures (only their host launchers changed)
-    "taylor": {"bytes": (218.379264 + 19.640064) * 1e6, "precisions": ("bf16", "bf16-f32lu", "bf16-f64theta"),
+    "taylor": {"bytes": (218.451456 + 20.324864) * 1e6, "precisions": ("bf16", "bf16-f32lu", "bf16-f64theta"),
                "function": "__global__ void __launch_bounds__(kSeriesThreads, 1)",
-               "sha": "0bd7f7fc981d513aebf1f41e918de5a243d5e63f2a01728f454f566a353c5b4b"},
-    "v_assembly": {"bytes": (187.431680 + 145.291776) * 1e6, "precisions": ("bf16", "bf16-f32lu", "bf16-f64theta"),
+               "sha": "6d2e94948e5abf9e9c52d41024ea33c2b85f59a4aedbf4e136518d477df98307"},
+    "v_assembly": {"bytes": (184.437504 + 144.337152) * 1e6, "precisions": ("bf16", "bf16-f32lu", "bf16-f64theta"),
                    "function": [GEMM_KERNEL, "struct EpiV {"],
-                   "sha": "63a321613a463e24104a01cc24fe168357d2aad1761c9cf5fd03fcc555f23358"},
-    "energy": {"bytes": (42.972160 + 0.562688) * 1e6, "precisions": ("bf16", "bf16-f32lu", "bf16-f64theta"),
+                   "sha": "1f48944952d9cf1ab9dcf3bd47e9c2c2abc7ba790bc874768e3a1df4490e6737"},
+    "energy": {"bytes": (42.972416 + 0.393216) * 1e6, "precisions": ("bf16", "bf16-f32lu", "bf16-f64theta"),
                "function": [GEMM_KERNEL, "struct EpiExchange {"],
-               "sha": "f831bafcaacbe7e7d559019a2ab9b036f4470a0aa657ef29fa518998f26c7810"},
+               "sha": "8fd54d7d642a9e625eb9e6ba51f4eae5d844d0c676664f8aec125effd5fb236f"},
 }
 
 
