@@ -1132,6 +1132,8 @@ def _case_main(a):
         return _case_bp(a)
     if a.case == "md":
         return _case_md(a)
+    if a.case == "ci":
+        return _case_ci(a)
     if a.case == "v":
         m, n, k, pitch = 1024, 45150, 1800, 1800
     else:
@@ -1330,6 +1332,65 @@ def _case_md(a):
         run.close()
 
 
+def _case_ci(a):
+    """A CI expansion about the RHF determinant on the M=100 workload (10 + 10
+    electrons, 500 vectors, 1024 walkers): 1 + 2 x 8 singles and 8 doubles
+    per spin (25 determinants, at most 2 columns each) evaluated relative to
+    the reference; ms per step and per local-energy evaluation."""
+    import time
+
+    import paper_1711_02242_gb300 as pkg
+    import torch
+
+    import workloads
+    from paper_1711_02242_gb300.rhf import rhf_trial
+
+    w = workloads.config("c1")
+    h1, L, H0 = w.hamiltonian()
+    C, _, _ = rhf_trial(h1, L, w.N, max_iter=25)
+    rng = np.random.default_rng(12)
+    q, _ = np.linalg.qr(np.hstack([C, rng.standard_normal((w.M, w.M - w.N))]))
+    virt = q[:, w.N:]
+    up, dn, coef = [C], [C], [1.0]
+    for s in range(2):
+        for k in range(8):
+            V = C.copy()
+            V[:, w.N - 1 - k % w.N] = virt[:, k]
+            (up if s == 0 else dn).append(V)
+            (dn if s == 0 else up).append(C)
+            coef.append(0.05 * (1 + k) / 8 * (1j if s else 1.0))
+    for k in range(8):
+        V = C.copy()
+        V[:, w.N - 1] = virt[:, k]
+        V[:, w.N - 2] = virt[:, k + 8]
+        up.append(V)
+        dn.append(V)
+        coef.append(-0.02)
+    nd = len(coef)
+    st = torch.cuda.Stream()
+    steps = 10
+    p = pkg.default_params(w.M, w.N, w.nchol, w.nwalkers, dt=w.dt, seed=w.seed, H0=H0,
+                           qr_period=w.qr_period, energy_period=0, ndet=nd,
+                           precision={"fp64": 0, "tf32": 1, "bf16": 2}[a.dtype])
+    run = pkg.AfqmcRun(h1, L, (np.array(coef, np.complex128), np.array(up), np.array(dn)), p,
+                       stream=st)
+    run.propagate(2)
+    st.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    run.propagate(steps)
+    e1.record(st)
+    st.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    t0 = time.perf_counter()
+    run.local_energies()
+    te = 1e3 * (time.perf_counter() - t0)
+    print(f"case ci {a.dtype} M={w.M} N={w.N} nchol={w.nchol} walkers={w.nwalkers} ndet={nd}: "
+          f"ms/step={ms:.2f} walker-steps/s={w.nwalkers / ms * 1e3:.0f} energy-eval ms={te:.2f} "
+          f"E_T={run.info().E_T:.6f} status={run.info().status} alive={run.info().alive}")
+    run.close()
+
+
 def run_peaks(args):
     """Dense float64 and float32 matrix-multiply throughput through PyTorch
     (cuBLAS; TF32 off for float32), the counterpart of the driver's BF16
@@ -1419,7 +1480,7 @@ def main():
     ap.add_argument("--no-bias", action="store_true",
                     help="skip the run-level bias of the mixed precisions against float64")
     ap.add_argument("--ref-walkers", type=int, default=16)
-    ap.add_argument("--case", default="v", choices=["v", "fb", "taylor", "mcd", "bp", "md"],
+    ap.add_argument("--case", default="v", choices=["v", "fb", "taylor", "mcd", "bp", "md", "ci"],
                     help="--workload case: one kernel or contraction of the step, for profiling")
     ap.add_argument("--dtype", default="bf16", choices=["bf16", "tf32", "fp64"])
     ap.add_argument("--reps", type=int, default=3)

@@ -461,14 +461,139 @@ __global__ void __launch_bounds__(128)
   }
 }
 
+// p0, p1, p2 of det(P + e S1 + e^2 S2) for k <= KM; KM = 2 in registers
+// (closed forms), else the elimination above.
+template <int KM>
+__device__ __forceinline__ void poly_k(const double2 (&P)[KM][KM], const double2 (&S1)[KM][KM],
+                                       const double2 (&S2)[KM][KM], int k, bool second,
+                                       double2* p0, double2* p1, double2* p2) {
+  if constexpr (KM == 2) {
+    const double2 z = make_double2(0.0, 0.0);
+    if (k == 0) {
+      *p0 = make_double2(1.0, 0.0);
+      *p1 = *p2 = z;
+    } else if (k == 1) {
+      *p0 = P[0][0];
+      *p1 = S1[0][0];
+      *p2 = second ? S2[0][0] : z;
+    } else {
+      auto det2 = [](double2 a, double2 b, double2 c, double2 d) { return zsub(zmul(a, d), zmul(b, c)); };
+      *p0 = det2(P[0][0], P[0][1], P[1][0], P[1][1]);
+      *p1 = zadd(det2(S1[0][0], S1[0][1], P[1][0], P[1][1]), det2(P[0][0], P[0][1], S1[1][0], S1[1][1]));
+      *p2 = second ? zadd(det2(S1[0][0], S1[0][1], S1[1][0], S1[1][1]),
+                          zadd(det2(S2[0][0], S2[0][1], P[1][0], P[1][1]),
+                               det2(P[0][0], P[0][1], S2[1][0], S2[1][1])))
+                   : z;
+    }
+  } else {
+    SmallMat A, B, C;
+    for (int l = 0; l < k; ++l)
+      for (int m = 0; m < k; ++m) {
+        A[l][m] = P[l][m];
+        B[l][m] = S1[l][m];
+        C[l][m] = S2[l][m];
+      }
+    small_poly(A, B, C, k, second, p0, p1, p2);
+  }
+}
+
+// Determinant d, spin s, operator rows X (Lh_g or h of (d, s)) for the warp
+// of that determinant (lane = column j < N): r, c1 and (second) c2.  KM >= k
+// bounds the hole count, so the per-hole arrays are unrolled into registers.
+template <int KM, bool SECOND>
+__device__ __forceinline__ void det_coeffs(const int* tb, int N, int M, int lane,
+                                           const double2* __restrict__ Y,
+                                           const double2* __restrict__ X,
+                                           const double* __restrict__ th, long NM,
+                                           const double* __restrict__ xbase, long xstride_h,
+                                           double2 trY, const double2* rjs, double2* rr,
+                                           double2* c1, double2* c2) {
+  const int k = tb[0], o = tb[1];
+  const bool lj = lane < N;
+  int h[KM];
+#pragma unroll
+  for (int l = 0; l < KM; ++l) h[l] = l < k ? tb[2 + l] : 0;
+  double2 yp[KM], xy[KM];
+#pragma unroll
+  for (int l = 0; l < KM; ++l) {
+    yp[l] = xy[l] = make_double2(0.0, 0.0);
+    if (l >= k || !lj) continue;
+    const double* x = xbase + (long)h[l] * xstride_h;
+    double re = 0.0, im = 0.0;
+    for (int q = 0; q < M; ++q) {
+      re += x[q] * th[(long)lane * M + q];
+      im += x[q] * th[NM + (long)lane * M + q];
+    }
+    yp[l] = make_double2(re, im);
+    double2 v = make_double2(0.0, 0.0);
+    for (int i = 0; i < N; ++i) v = zadd(v, zmul(X[(long)(o + l) * N + i], Y[i * N + lane]));
+    xy[l] = v;
+  }
+  double2 P[KM][KM], S1[KM][KM], S2[KM][KM];
+#pragma unroll
+  for (int l = 0; l < KM; ++l)
+#pragma unroll
+    for (int m = 0; m < KM; ++m) {
+      P[l][m] = S1[l][m] = S2[l][m] = make_double2(0.0, 0.0);
+      if (l >= k || m >= k) continue;
+      const double2 ypv = zshfl(yp[l], h[m]), xyv = zshfl(xy[l], h[m]);
+      double2 corr = make_double2(0.0, 0.0);
+#pragma unroll
+      for (int i = 0; i < KM; ++i)
+        if (i < k) corr = zadd(corr, zmul(X[(long)(o + l) * N + h[i]], Y[h[i] * N + h[m]]));
+      P[l][m] = X[(long)(o + l) * N + h[m]];
+      S1[l][m] = zadd(zsub(ypv, xyv), corr);
+    }
+  double2 tz = trY;
+#pragma unroll
+  for (int m = 0; m < KM; ++m)
+    if (m < k) tz = zsub(tz, Y[h[m] * N + h[m]]);
+  double2 e2 = make_double2(0.0, 0.0);
+  if constexpr (SECOND) {
+    bool hole = false;
+#pragma unroll
+    for (int m = 0; m < KM; ++m) hole = hole || (m < k && h[m] == lane);
+#pragma unroll
+    for (int l = 0; l < KM; ++l) {
+      if (l >= k) continue;
+      double2 F = make_double2(0.0, 0.0);
+      if (lj && !hole) {
+        F = zsub(xy[l], yp[l]);
+#pragma unroll
+        for (int i = 0; i < KM; ++i)
+          if (i < k) F = zsub(F, zmul(X[(long)(o + l) * N + h[i]], Y[h[i] * N + lane]));
+      }
+#pragma unroll
+      for (int m = 0; m < KM; ++m)
+        if (m < k) S2[l][m] = zwarp_sum(lj ? zmul(F, Y[lane * N + h[m]]) : make_double2(0.0, 0.0));
+    }
+    double2 tz2 = rjs[N];
+#pragma unroll
+    for (int m = 0; m < KM; ++m) {
+      if (m >= k) continue;
+      tz2 = zsub(tz2, zscale(rjs[h[m]], 2.0));
+#pragma unroll
+      for (int m2 = 0; m2 < KM; ++m2)
+        if (m2 < k) tz2 = zadd(tz2, zmul(Y[h[m] * N + h[m2]], Y[h[m2] * N + h[m]]));
+    }
+    e2 = zscale(zsub(zmul(tz, tz), tz2), 0.5);
+  }
+  double2 p0, p1, p2;
+  poly_k<KM>(P, S1, S2, k, SECOND, &p0, &p1, &p2);
+  *rr = p0;
+  *c1 = zadd(p1, zmul(p0, tz));
+  *c2 = zadd(zadd(p2, zmul(p1, tz)), zmul(p0, e2));
+}
+
 // Block (chunk c, walker w), 8 warps: for each vector g of the chunk
 // (kSmwGC of them; with ENERGY the extra chunk c = nchk takes h instead),
 // Y0_s = Lh_0sg Theta_0s in shared memory, then one warp per determinant
 // (lane j = column j) forms Yp and Xi Y0 at its holes, the k x k matrices P,
-// S1 (and S2) and the coefficients; the force bias sums a_d [c1_du r_dd +
-// r_du c1_dd] over d (per warp in the order of d, then over warps in order);
-// the energy keeps per (w, c, d) the sum over the chunk of c2_du r_dd + r_du
-// c2_dd + c1_du c1_dd (H0 r_du r_dd + c1_du r_dd + r_du c1_dd for h).
+// S1 (and S2) and the coefficients (det_coeffs); the force bias sums a_d
+// [c1_du r_dd + r_du c1_dd] over d (per warp in the order of d, then over
+// warps in order); the energy keeps per (w, c, d) the sum over the chunk of
+// c2_du r_dd + r_du c2_dd + c1_du c1_dd (H0 r_du r_dd + c1_du r_dd + r_du c1_dd
+// for h).
 template <bool ENERGY>
 __global__ void __launch_bounds__(256)
     k_smw_terms(int W, int M, int N, int G, int nd, int ks, int nchk, double H0,
@@ -487,17 +612,16 @@ __global__ void __launch_bounds__(256)
   const int g1 = onebody ? 1 : (G < g0 + kSmwGC ? G : g0 + kSmwGC);
   const long NM = (long)N * M;
   const int lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
-  const bool lj = lane < N;
   const double2* xw = reinterpret_cast<const double2*>(xi) + (long)w * 2 * ks * N;
   const double2* aw2 = reinterpret_cast<const double2*>(aw) + (long)w * nd;
-  // operator rows of (d, s) for vector g (or h)
-  auto xrow = [&](int ds, int g, int i) -> const double* {
-    return onebody ? hh + ((long)ds * N + i) * M : Lh + (((long)ds * G + g) * N + i) * M;
+  // operator rows of (d, s) for vector g (or h): row i at xrow(ds, g) + i M
+  auto xrow = [&](int ds, int g) -> const double* {
+    return onebody ? hh + (long)ds * NM : Lh + ((long)ds * G + g) * NM;
   };
   for (int g = g0; g < g1; ++g) {
     for (int e = tid; e < 2 * N * N; e += blockDim.x) {
       const int s = e / (N * N), i = (e / N) % N, j = e % N;
-      const double* x = xrow(s, g, i);  // determinant 0: ds = s
+      const double* x = xrow(s, g) + (long)i * M;  // determinant 0: ds = s
       const double* th = theta + ((long)s * W + w) * 2 * NM;
       double re = 0.0, im = 0.0;
       for (int q = 0; q < M; ++q) {
@@ -530,67 +654,26 @@ __global__ void __launch_bounds__(256)
     double2 fsum = make_double2(0.0, 0.0);
     for (int d = warp; d < nd; d += nwarp) {
       double2 rr[2], c1[2], c2[2];
+      const int kmax = tab[(d * 2) * 8] > tab[(d * 2 + 1) * 8] ? tab[(d * 2) * 8] : tab[(d * 2 + 1) * 8];
       for (int s = 0; s < 2; ++s) {
         const int* tb = tab + (d * 2 + s) * 8;
-        const int k = tb[0], o = tb[1];
         const double2* Y = y0 + s * N * N;
         const double2* X = xw + (long)s * ks * N;  // Xi_s rows
         const double* th = theta + ((long)s * W + w) * 2 * NM;
-        double2 yp[kSmwMaxK], xy[kSmwMaxK];
-        for (int l = 0; l < k; ++l) {
-          yp[l] = xy[l] = make_double2(0.0, 0.0);
-          if (!lj) continue;
-          const double* x = xrow(2 * d + s, g, tb[2 + l]);
-          double re = 0.0, im = 0.0;
-          for (int q = 0; q < M; ++q) {
-            re += x[q] * th[(long)lane * M + q];
-            im += x[q] * th[NM + (long)lane * M + q];
-          }
-          yp[l] = make_double2(re, im);
-          double2 v = make_double2(0.0, 0.0);
-          for (int i = 0; i < N; ++i) v = zadd(v, zmul(X[(long)(o + l) * N + i], Y[i * N + lane]));
-          xy[l] = v;
-        }
-        SmallMat P, S1, S2;
-        for (int l = 0; l < k; ++l)
-          for (int m = 0; m < k; ++m) {
-            const int hm = tb[2 + m];
-            const double2 ypv = zshfl(yp[l], hm), xyv = zshfl(xy[l], hm);
-            double2 corr = make_double2(0.0, 0.0);
-            for (int i = 0; i < k; ++i)
-              corr = zadd(corr, zmul(X[(long)(o + l) * N + tb[2 + i]], Y[tb[2 + i] * N + hm]));
-            P[l][m] = X[(long)(o + l) * N + hm];
-            S1[l][m] = zadd(zsub(ypv, xyv), corr);
-          }
-        double2 tz = trs[s];
-        for (int m = 0; m < k; ++m) tz = zsub(tz, Y[tb[2 + m] * N + tb[2 + m]]);
-        double2 e2 = make_double2(0.0, 0.0);
+        const double* xb = xrow(2 * d + s, g);
         if (ENERGY && !onebody) {
-          bool hole = false;
-          for (int m = 0; m < k; ++m) hole = hole || tb[2 + m] == lane;
-          for (int l = 0; l < k; ++l) {
-            double2 F = make_double2(0.0, 0.0);
-            if (lj && !hole) {
-              F = zsub(xy[l], yp[l]);
-              for (int i = 0; i < k; ++i)
-                F = zsub(F, zmul(X[(long)(o + l) * N + tb[2 + i]], Y[tb[2 + i] * N + lane]));
-            }
-            for (int m = 0; m < k; ++m)
-              S2[l][m] = zwarp_sum(lj ? zmul(F, Y[lane * N + tb[2 + m]]) : make_double2(0.0, 0.0));
-          }
-          double2 tz2 = rj[s][N];
-          for (int m = 0; m < k; ++m) {
-            tz2 = zsub(tz2, zscale(rj[s][tb[2 + m]], 2.0));
-            for (int m2 = 0; m2 < k; ++m2)
-              tz2 = zadd(tz2, zmul(Y[tb[2 + m] * N + tb[2 + m2]], Y[tb[2 + m2] * N + tb[2 + m]]));
-          }
-          e2 = zscale(zsub(zmul(tz, tz), tz2), 0.5);
+          if (kmax <= 2)
+            det_coeffs<2, true>(tb, N, M, lane, Y, X, th, NM, xb, M, trs[s], rj[s], &rr[s], &c1[s], &c2[s]);
+          else
+            det_coeffs<kSmwMaxK, true>(tb, N, M, lane, Y, X, th, NM, xb, M, trs[s], rj[s], &rr[s],
+                                       &c1[s], &c2[s]);
+        } else {
+          if (kmax <= 2)
+            det_coeffs<2, false>(tb, N, M, lane, Y, X, th, NM, xb, M, trs[s], rj[s], &rr[s], &c1[s], &c2[s]);
+          else
+            det_coeffs<kSmwMaxK, false>(tb, N, M, lane, Y, X, th, NM, xb, M, trs[s], rj[s], &rr[s],
+                                        &c1[s], &c2[s]);
         }
-        double2 p0, p1, p2;
-        small_poly(P, S1, S2, k, ENERGY && !onebody, &p0, &p1, &p2);
-        rr[s] = p0;
-        c1[s] = zadd(p1, zmul(p0, tz));
-        c2[s] = zadd(zadd(p2, zmul(p1, tz)), zmul(p0, e2));
       }
       if (lane == 0) {
         if (!ENERGY) {
