@@ -1044,6 +1044,10 @@ static int setup_device(afqmc_state* s, const double* h1, const double* L, const
     gf.tf32 = b.lo_kind == LO_TF32;
     gf.err = b.status;
     AFQ_TRY(tc_tune_store(gf, b.t32, G, 2.0f, st, &s->bn_fb));
+    // and of the V contraction (its output, the Taylor operand, is scratch here)
+    TcJobDesc dv;
+    desc_v(s, &dv);
+    AFQ_TRY(tc_tune_v(dv.g, dv.V, dv.lo_kind, dv.W, dv.M, dv.Mp, dv.sdt, st, &s->bn_v));
     s->t_fresh = false;
     AFQ_CUDA(cudaStreamSynchronize(st));
   }

@@ -598,17 +598,23 @@ struct EpiV {
   void* V;
   int lo_kind, W, M, Mp;
   float sdt;
+  int bn;  // tile width: 256 (one 16 x 16 block) or 128 (half a block)
   __device__ __forceinline__ int m_origin(int bx, int) const { return bx * BM * kMT; }
-  __device__ __forceinline__ int n_origin(int, int by) const { return by * 256; }
-  // Output tile by = one 16 x 16 block (P, Q), P <= Q, of the symmetric V:
-  // column pp * 16 + qq of the tile is V[16 P + pp][16 Q + qq].  The thread of
-  // row (w, c) writes the block's 16 rows (16 contiguous q each) and, off the
+  __device__ __forceinline__ int n_origin(int, int by) const { return by * bn; }
+  // Output block (P, Q), P <= Q, of the symmetric V (blocks of 256 operand
+  // rows in the order of P, then Q): column pp * 16 + qq of the block is
+  // V[16 P + pp][16 Q + qq].  BN = 256: the tile is the block and the thread
+  // of row (w, c) writes its 16 rows (16 contiguous q each) and, off the
   // diagonal, the mirrored block's 16 rows (V[q][p] = V[p][q]) in two halves
-  // of 8 contiguous p.  The two warps of a lane quarter take one half each.
+  // of 8 contiguous p, the two warps of a lane quarter one half each.  BN =
+  // 128: the tile is half h of the block (pp in [8 h, 8 h + 8)), so two
+  // accumulators fit tensor memory and the epilogue overlaps the next tile's
+  // MMAs; one warp of the quarter writes the 8 rows, the other the mirror's
+  // 16 rows of 8 contiguous p.
   template <int BN>
   __device__ __forceinline__ void run(uint32_t tmem, int q, int lane, int ew, int, int, int m0,
                                       int n0, int, int, float*) const {
-    static_assert(BN == 256, "one 16 x 16 block per tile");
+    static_assert(BN == 256 || BN == 128, "a 16 x 16 block or half of one per tile");
     const int row = m0 + 32 * q + lane;
     const bool valid = row < 2 * W;
     const int w = row >> 1, c = row & 1;
@@ -621,14 +627,18 @@ struct EpiV {
     }
     const int Q = P + rem;
     const long vb = (long)w * M * 2L * Mp + (c ? 0 : Mp);
-#pragma unroll 1
-    for (int h = ew >> 2; h < 2; h += 2) {
-      uint32_t r[8][16];
+    const uint32_t tq = tmem + ((uint32_t)(32 * q) << 16);
+    // half h of the block and whether this warp writes the block's rows or the mirror's
+    const int h = BN == 256 ? (ew >> 2) : ((n0 / 128) & 1);
+    const bool rows = BN == 256 || (ew >> 2) == 0;
+    const bool mirror = BN == 256 || (ew >> 2) == 1;
+    uint32_t r[8][16];
 #pragma unroll
-      for (int u = 0; u < 8; ++u)
-        tmem_ld16_async(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)((8 * h + u) * 16), r[u]);
-      tmem_ld_wait();
-      if (!valid) continue;
+    for (int u = 0; u < 8; ++u)
+      tmem_ld16_async(tq + (uint32_t)(((BN == 256 ? 8 * h : 0) + u) * 16), r[u]);
+    tmem_ld_wait();
+    if (!valid) return;
+    if (rows) {
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
         const int p = 16 * P + 8 * h + u;
@@ -639,16 +649,16 @@ struct EpiV {
           store16_lo(V, lo_kind, vb + (long)p * 2 * Mp + 16 * Q, v, sign);
         }
       }
-      if (P == Q) continue;
+    }
+    if (P == Q || !mirror) return;
 #pragma unroll
-      for (int t = 0; t < 16; ++t) {
-        const int qr = 16 * Q + t;
-        if (qr < M) {
-          float v[8];
+    for (int t = 0; t < 16; ++t) {
+      const int qr = 16 * Q + t;
+      if (qr < M) {
+        float v[8];
 #pragma unroll
-          for (int u = 0; u < 8; ++u) v[u] = __uint_as_float(r[u][t]);
-          store8_lo(V, lo_kind, vb + (long)qr * 2 * Mp + 16 * P + 8 * h, v, sign);
-        }
+        for (int u = 0; u < 8; ++u) v[u] = __uint_as_float(r[u][t]);
+        store8_lo(V, lo_kind, vb + (long)qr * 2 * Mp + 16 * P + 8 * h, v, sign);
       }
     }
   }
@@ -891,7 +901,7 @@ struct ShapeKey {
   }
 };
 std::mutex g_tune_mu;
-std::map<ShapeKey, int> g_tuned_bn;
+std::map<ShapeKey, int> g_tuned_bn, g_tuned_bn_v;
 }  // namespace
 
 static int launch_store_bn(const TcGemm& g, float* C, long ldc, float alpha, int bn,
@@ -991,6 +1001,20 @@ int tc_taylor_term(const TcGemm& g, float* S, long lds, bool first, void* tb_out
   return launch_tc_persistent<BN, 6, false>(g, e, cdiv(M, BN), W, st);
 }
 
+// V with tile width 128 (half blocks, double-buffered accumulators) or 256.
+static int launch_v_bn(const TcGemm& g, void* V, int lo_kind, int W, int M, int Mp, double sdt,
+                       int bn, cudaStream_t st) {
+  const int nb = Mp / 16;
+  tc::EpiV e{V, lo_kind, W, M, Mp, (float)sdt, bn};
+  const int gx = cdiv(g.m, tc::BM * tc::EpiV::kMT), gy = nb * (nb + 1) / 2 * (256 / bn);
+  if (bn == 128) {
+    if (g.tf32) return launch_tc_persistent<128, 4, true>(g, e, gx, gy, st);
+    return launch_tc_persistent<128, 4, false>(g, e, gx, gy, st);
+  }
+  if (g.tf32) return launch_tc_persistent<256, 3, true>(g, e, gx, gy, st);
+  return launch_tc_persistent<256, 3, false>(g, e, gx, gy, st);
+}
+
 int tc_v_full(const TcGemm& g, void* V, int lo_kind, int W, int M, int Mp, double sdt,
               cudaStream_t st) {
   if (Mp % 16) {
@@ -1003,10 +1027,45 @@ int tc_v_full(const TcGemm& g, void* V, int lo_kind, int W, int M, int Mp, doubl
               nb * (nb + 1) / 2, Mp, nb * (nb + 1) / 2 * 256);
     return AFQMC_EINVAL;
   }
-  tc::EpiV e{V, lo_kind, W, M, Mp, (float)sdt};
-  const int gx = cdiv(g.m, tc::BM * tc::EpiV::kMT), gy = nb * (nb + 1) / 2;
-  if (g.tf32) return launch_tc_persistent<256, 3, true>(g, e, gx, gy, st);
-  return launch_tc_persistent<256, 3, false>(g, e, gx, gy, st);
+  int bn = 128;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tuned_bn_v.find(ShapeKey{g.m, g.n, g.k, g.tf32});
+    if (it != g_tuned_bn_v.end()) bn = it->second;
+  }
+  return launch_v_bn(g, V, lo_kind, W, M, Mp, sdt, bn, st);
+}
+
+int tc_tune_v(const TcGemm& g, void* V, int lo_kind, int W, int M, int Mp, double sdt,
+              cudaStream_t st, int* chosen) {
+  if (g.m <= 0 || g.n <= 0 || g.k <= 0) return AFQMC_OK;
+  cudaEvent_t e0, e1;
+  AFQ_CUDA(cudaEventCreate(&e0));
+  AFQ_CUDA(cudaEventCreate(&e1));
+  int best = 128;
+  float best_ms = 1e30f;
+  for (int bn : {128, 256}) {
+    AFQ_TRY(launch_v_bn(g, V, lo_kind, W, M, Mp, sdt, bn, st));  // warm-up
+    AFQ_CUDA(cudaEventRecord(e0, st));
+    AFQ_TRY(launch_v_bn(g, V, lo_kind, W, M, Mp, sdt, bn, st));
+    AFQ_TRY(launch_v_bn(g, V, lo_kind, W, M, Mp, sdt, bn, st));
+    AFQ_CUDA(cudaEventRecord(e1, st));
+    AFQ_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    AFQ_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = bn;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuned_bn_v[ShapeKey{g.m, g.n, g.k, g.tf32}] = best;
+  }
+  if (chosen) *chosen = best;
+  return AFQMC_OK;
 }
 
 int tc_prop_last(const TcGemm& g, double* phiT, const double* wt, int N, int M, void* phi_lo,
@@ -1076,8 +1135,9 @@ int make_job(const TcJobDesc& d, int bn, tc::GemmJob<tc::EpiV>* j) {
     set_error("grouped V: Mp=%d and %d operand rows do not match", d.Mp, d.g.n);
     return AFQMC_EINVAL;
   }
-  tc::EpiV e{d.V, d.lo_kind, d.W, d.M, d.Mp, (float)d.sdt};
-  return fill_job(j, d.g, bn, cdiv(d.g.m, tc::BM * tc::EpiV::kMT), nb * (nb + 1) / 2, e);
+  tc::EpiV e{d.V, d.lo_kind, d.W, d.M, d.Mp, (float)d.sdt, bn};
+  return fill_job(j, d.g, bn, cdiv(d.g.m, tc::BM * tc::EpiV::kMT), nb * (nb + 1) / 2 * (256 / bn),
+                  e);
 }
 int make_job(const TcJobDesc& d, int bn, tc::GemmJob<tc::EpiProp0>* j) {
   tc::EpiProp0 e{d.acc, d.ldacc, d.tb, d.phi_id, d.lo_kind, d.N, d.M, d.Mp, d.g.m, bn};
@@ -1136,6 +1196,7 @@ int dispatch_grouped(const TcGrouped& gr, cudaStream_t st) {
       if (gr.bn == 128) return launch_grouped<128, 6, TF32, tc::EpiStore>(gr, st);
       return launch_grouped<256, 4, TF32, tc::EpiStore>(gr, st);
     case TC_JOB_V:
+      if (gr.bn == 128) return launch_grouped<128, 4, TF32, tc::EpiV>(gr, st);
       return launch_grouped<256, 3, TF32, tc::EpiV>(gr, st);
     case TC_JOB_PROP0:
       if (gr.bn == 160) return launch_grouped<160, 6, TF32, tc::EpiProp0>(gr, st);
@@ -1154,7 +1215,7 @@ std::vector<int> bn_candidates(int kind) {
     case TC_JOB_STORE:
       return {256, 128, 64};
     case TC_JOB_V:
-      return {256};
+      return {128, 256};
     default:
       return {160, 256};
   }
@@ -1173,7 +1234,7 @@ int tc_grouped_create(const TcJobDesc* d, int n, int bn, TcGrouped** out) {
       return AFQMC_EINVAL;
     }
   const int kind = d[0].kind;
-  if (bn == 0) bn = kind == TC_JOB_STORE || kind == TC_JOB_V ? 256 : half_step_bn(d[0].M);
+  if (bn == 0) bn = kind == TC_JOB_STORE ? 256 : kind == TC_JOB_V ? 128 : half_step_bn(d[0].M);
   bool ok = false;
   for (int c : bn_candidates(kind)) ok = ok || c == bn;
   if (!ok) {

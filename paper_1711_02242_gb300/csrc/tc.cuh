@@ -44,6 +44,10 @@ int tc_prop_last(const TcGemm& g, double* phiT, const double* wt, int N, int M, 
 // written directly as [Re V | Im V] rows (pitch 2 Mp) of each walker.
 int tc_v_full(const TcGemm& g, void* V, int lo_kind, int W, int M, int Mp, double sdt,
               cudaStream_t st);
+// Time V's tile-width candidates (128: half blocks, two accumulators; 256:
+// whole blocks) on the given buffers and remember the faster for tc_v_full().
+int tc_tune_v(const TcGemm& g, void* V, int lo_kind, int W, int M, int Mp, double sdt,
+              cudaStream_t st, int* chosen);
 
 // Whole Taylor series per walker in one launch (one CTA per walker at a time):
 // the term stays in shared memory and the walker's [Re V | Im V] rows are
