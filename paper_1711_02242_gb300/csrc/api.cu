@@ -576,6 +576,13 @@ static int propagate_f64(afqmc_state* s) {
 // step from the operand copy phi_lo_in, the Taylor series and the last half
 // step (TF32), which stores float64 orbitals (walkers with W != 0) and their
 // operand copy.
+int join_side(afqmc_state* s) {
+  if (!s->side_pending) return AFQMC_OK;
+  AFQ_CUDA(cudaStreamWaitEvent(s->st, s->ev_side, 0));
+  s->side_pending = false;
+  return AFQMC_OK;
+}
+
 // terms k = 1..n of the Taylor series: S = T_1 + ... + T_n into columns
 // [Mp, 2 Mp) of acc; the whole series in one launch when the term fits in
 // shared memory, else one launch per term
@@ -596,6 +603,8 @@ int apply_b_mixed(afqmc_state* s, const double* phi_in, const void* phi_lo_in, d
   desc_v(s, &d);
   AFQ_TRY(tc_job_launch(d, s->st));
   prof_end(s);
+  // the first half step reads the orbitals: a side-stream Gram-Schmidt must be done
+  AFQ_TRY(join_side(s));
   prof_begin(s, AFQMC_PH_BHALF);
   d = TcJobDesc();
   desc_half1(s, phi_in, phi_lo_in, &d);
@@ -677,7 +686,20 @@ int step_after(afqmc_state* s) {
     AFQ_TRY(bp_step_factor(s));
     s->bp_m += 1;
   }
-  if (p.qr_period && n % p.qr_period == 0) {
+  const bool qr_due = p.qr_period && n % p.qr_period == 0;
+  const bool pc_due = p.pc_period && n % p.pc_period == 0;
+  const bool e_due = p.energy_period && n % p.energy_period == 0;
+  // Gram-Schmidt on the side stream when nothing of this step after it reads
+  // the orbitals before the next first half step (no comb due): then the
+  // energy evaluation, which reads neither Phi nor ld, is enqueued first so
+  // that its persistent contraction takes the SMs and the sweep fills in
+  const bool side = qr_due && !pc_due && s->side && !s->prof.on && !s->bp_on;
+  if (side && e_due) {
+    prof_begin(s, AFQMC_PH_ENERGY);
+    AFQ_TRY(energy_eval(s, true));
+    prof_end(s);
+  }
+  if (qr_due) {
     prof_begin(s, AFQMC_PH_QR);
     // Phi -> Q; Theta is unchanged and log det S drops by sum_k log r_kk,
     // which the kernel applies to ld (no new overlap needed)
@@ -692,10 +714,20 @@ int step_after(afqmc_state* s) {
       ma.lo_kind = b.lo_kind;
       ma.Mp = b.Mp;
     }
-    AFQ_TRY(launch_mgs(ma, s->st));
+    if (side) {
+      // join_side() before the next reader (the next first half step)
+      AFQ_CUDA(cudaEventRecord(s->ev_fork, s->st));
+      AFQ_CUDA(cudaStreamWaitEvent(s->side, s->ev_fork, 0));
+      AFQ_TRY(launch_mgs(ma, s->side));
+      AFQ_CUDA(cudaEventRecord(s->ev_side, s->side));
+      s->side_pending = true;
+    } else {
+      AFQ_TRY(launch_mgs(ma, s->st));
+    }
     prof_end(s);
   }
-  if (p.pc_period && n % p.pc_period == 0) {
+  if (pc_due) {
+    AFQ_TRY(join_side(s));
     prof_begin(s, AFQMC_PH_COMB);
     CombArgs ca{W, M, N, p.seed, reinterpret_cast<const int64_t*>(b.counters + CTR_STEP),
                 b.wt, b.cum, b.parent, b.phiT, b.thetaT, b.ld, b.T0, b.T1, b.tmp_ld, b.wtot};
@@ -706,8 +738,7 @@ int step_after(afqmc_state* s) {
     s->t_fresh = false;  // the walkers moved: their force-bias traces are stale
     prof_end(s);
   }
-  const bool e_due = p.energy_period && n % p.energy_period == 0;
-  if (e_due) {
+  if (e_due && !(side && e_due)) {
     prof_begin(s, AFQMC_PH_ENERGY);
     AFQ_TRY(energy_eval(s, true));
     prof_end(s);
@@ -718,7 +749,7 @@ int step_after(afqmc_state* s) {
 // One graph block of steps launched kernel by kernel (captured by groups).
 int step_block(afqmc_state* s) {
   for (int i = 0; i < s->graph_block; ++i) AFQ_TRY(step_once(s));
-  return AFQMC_OK;
+  return join_side(s);
 }
 
 // B_half = exp(X), X = -dt v0'/2, by scaling and squaring of a degree-18
@@ -1163,6 +1194,20 @@ static int init_state(const afqmc_params* p, const double* h1, const double* L,
     delete s;
     return r;
   }
+  if (s->b.mixed) {
+    // lowest priority: the main stream's blocks are scheduled first
+    int lo_pri = 0, hi_pri = 0;
+    cudaDeviceGetStreamPriorityRange(&lo_pri, &hi_pri);
+    if (cudaStreamCreateWithPriority(&s->side, cudaStreamNonBlocking, lo_pri) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s->ev_side, cudaEventDisableTiming) != cudaSuccess) {
+      if (s->side) cudaStreamDestroy(s->side);
+      if (s->ev_fork) cudaEventDestroy(s->ev_fork);
+      set_error("side stream or events could not be created");
+      delete s;
+      return AFQMC_ECUDA;
+    }
+  }
   // graph block: least common multiple of the non-zero periods (at most 64 steps)
   {
     long blk = 1;
@@ -1257,6 +1302,7 @@ int afqmc_propagate(afqmc_state* s, int32_t nsteps) {
     // the rest (and every step while profiling) launches kernels one by one
     if (s->p.use_graph && blk > 0 && s->h_step % blk == 0 && nsteps >= blk && !s->prof.on &&
         !s->bp_on) {
+      AFQ_TRY(join_side(s));  // the graph starts from a joined stream
       s->t_fresh = false;  // the block recomputes the force-bias traces itself
       if (!s->graph) {
         const int64_t l0 = g_launches;
@@ -1264,6 +1310,7 @@ int afqmc_propagate(afqmc_state* s, int32_t nsteps) {
         AFQ_CUDA(cudaStreamBeginCapture(s->st, cudaStreamCaptureModeThreadLocal));
         int r = AFQMC_OK;
         for (int i = 0; i < blk && r == AFQMC_OK; ++i) r = step_once(s);
+        if (r == AFQMC_OK) r = join_side(s);
         cudaGraph_t g = nullptr;
         cudaError_t e = cudaStreamEndCapture(s->st, &g);
         s->h_step = h0;  // nothing ran yet: the launch below takes the steps
@@ -1296,7 +1343,7 @@ int afqmc_propagate(afqmc_state* s, int32_t nsteps) {
       --nsteps;
     }
   }
-  return AFQMC_OK;
+  return join_side(s);
 }
 
 int afqmc_energy(afqmc_state* s, double* E, double* wsum) {
@@ -1574,6 +1621,12 @@ int afqmc_destroy(afqmc_state* s) {
   if (!s) return AFQMC_OK;
   s->valid = false;
   if (s->graph) cudaGraphExecDestroy(s->graph);
+  if (s->side) {
+    cudaStreamSynchronize(s->side);
+    cudaStreamDestroy(s->side);
+  }
+  if (s->ev_fork) cudaEventDestroy(s->ev_fork);
+  if (s->ev_side) cudaEventDestroy(s->ev_side);
   for (cudaEvent_t e : s->prof.ev) cudaEventDestroy(e);
   delete s;
   return AFQMC_OK;

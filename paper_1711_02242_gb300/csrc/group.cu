@@ -187,7 +187,10 @@ static int grouped_block(afqmc_group* g) {
     AFQ_TRY(afq::tc_grouped_launch(g->gx[2], g->root));
     AFQ_TRY(per_state(g, [](afqmc_state* s) { return afq::step_taylor(s); }));
     AFQ_TRY(afq::tc_grouped_launch(g->gx[3], g->root));
-    AFQ_TRY(per_state(g, [](afqmc_state* s) { return afq::step_after(s); }));
+    AFQ_TRY(per_state(g, [](afqmc_state* s) {
+      AFQ_TRY(afq::step_after(s));
+      return afq::join_side(s);
+    }));
   }
   return AFQMC_OK;
 }

@@ -125,6 +125,12 @@ struct afqmc_state {
   double sf = 2.0;
   // population size of the last afqmc_comb_plan (sharded comb), 0 before one
   int64_t comb_nall = 0;
+  // mixed path: Gram-Schmidt on a side stream, overlapping the work that does
+  // not read the orbitals or log <Psi_T|Psi> (the energy evaluation, the next
+  // step's force bias, fields and V); joined before the next reader
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_side = nullptr;
+  bool side_pending = false;
   // multi-determinant trial evaluated relative to determinant 0 (float64),
   // with the particle count of each spin
   bool smw = false;
@@ -145,6 +151,8 @@ int md_force_bias(afqmc_state* s);
 int md_local_energies(afqmc_state* s);
 int md_setup(afqmc_state* s, const double* coef);
 int smw_detect(afqmc_state* s, const double* up, const double* dn);
+// Make the state's stream wait for a pending side-stream Gram-Schmidt.
+int join_side(afqmc_state* s);
 }  // namespace afq
 
 namespace afq {
