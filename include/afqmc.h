@@ -75,7 +75,8 @@ enum {
                         /* FP32 accumulation; the overlap S = V_T^T Phi, its    */
                         /* LU / inverse S^-1 and log det, the overlap ratios,   */
                         /* weights, Gram-Schmidt and the identity part of the   */
-                        /* one-body half steps in FP64; the product             */
+                        /* one-body half steps in FP64 (the rest, B_half - I,   */
+                        /* as a high and a low operand part); the product       */
                         /* Theta = Phi S^-1 (an operand of the contractions)    */
                         /* in FP32 from the float64 S^-1                        */
   AFQMC_MIXED_BF16 = 2, /* as MIXED_TF32 with BF16 inputs to the contractions   */

@@ -143,6 +143,9 @@ size_t plan(const afqmc_params& p, Bufs* b, char* base) {
     b->t32 = a.take<float>(W * 2 * G);
     b->Bh_lo = a.take<char>(M * Mp * lo);
     b->Bh_tf = a.take<float>(M * 2 * Mp);
+    b->Kp1 = (int)((M + 128 / lo - 1) / (128 / lo) * (128 / lo));
+    b->Bh_split = a.take<char>(M * 2 * (size_t)b->Kp1 * lo);
+    b->Bh_split_tf = a.take<float>(M * 4 * Mp);
   }
   // scratch: the set-up and the step never run at the same time
   const size_t scratch_at = (a.off + 255) & ~size_t(255);
@@ -375,11 +378,14 @@ void desc_half1(afqmc_state* s, const double* phi_in, const void* phi_lo_in, TcJ
   d->kind = TC_JOB_PROP0;
   d->g.m = 2 * p.N * p.nwalkers;
   d->g.n = p.M;
-  d->g.k = p.M;
+  // D_B as [hi | lo] along K (segments of Kp1): Phi_lo (D_hi + D_lo)
+  d->g.k = 2 * b.Kp1;
+  d->g.ka = p.M;
+  d->g.a_wrap = b.Kp1;
   d->g.A = phi_lo_in;
   d->g.lda = b.Mp;
-  d->g.B = b.Bh_lo;
-  d->g.ldb = b.Mp;
+  d->g.B = b.Bh_split;
+  d->g.ldb = 2L * b.Kp1;
   d->g.tf32 = b.lo_kind == LO_TF32;
   d->g.err = b.status;
   d->acc = b.acc32;
@@ -401,11 +407,14 @@ void desc_half2(afqmc_state* s, double* phi_out, void* phi_lo_out, TcJobDesc* d)
   d->kind = TC_JOB_PHI;
   d->g.m = 2 * p.N * p.nwalkers;
   d->g.n = p.M;
-  d->g.k = 2 * b.Mp;
+  // [T_0 | S] against [D_hi | D_hi | D_lo | D_lo] (segments of Mp)
+  d->g.k = 4 * b.Mp;
+  d->g.ka = 2 * b.Mp;
+  d->g.a_wrap = 2 * b.Mp;
   d->g.A = b.acc32;
   d->g.lda = 2L * b.Mp;
-  d->g.B = b.Bh_tf;
-  d->g.ldb = 2L * b.Mp;
+  d->g.B = b.Bh_split_tf;
+  d->g.ldb = 4L * b.Mp;
   d->g.tf32 = true;
   d->g.err = b.status;
   d->phiT = phi_out;
@@ -1044,6 +1053,11 @@ static int setup_device(afqmc_state* s, const double* h1, const double* L, const
     AFQ_CUDA(cudaMemcpy2DAsync(b.Bh_tf + b.Mp, sizeof(float) * 2 * b.Mp, b.Bh_tf,
                                sizeof(float) * 2 * b.Mp, sizeof(float) * b.Mp, M,
                                cudaMemcpyDeviceToDevice, st));
+    // rounded once, D_B would be the same slightly wrong one-body propagator
+    // for every walker at every step: the half steps take it as a high and a
+    // low part (twice the K, a product the half steps' memory traffic hides)
+    AFQ_TRY(launch_split_lo(b.Bh, M, M, M, b.Bh_split, b.Kp1, 2, 0x2u, b.lo_kind, st, 1.0));
+    AFQ_TRY(launch_split_lo(b.Bh, M, M, M, b.Bh_split_tf, b.Mp, 4, 0xCu, LO_TF32, st, 1.0));
   }
   // walkers at the trial, their overlaps, and the trial energy
   AFQ_TRY(launch_init_walkers(b.VTt, b.phiT, b.wt, W, N, M, st));

@@ -57,6 +57,7 @@ template <class Epi>
 struct alignas(64) GemmJob {
   CUtensorMap tmA, tmB;
   int M, N, K, gx, ntiles, tile0;
+  int a_wrap;  // A's K coordinate taken modulo a_wrap (0: not)
   int* err;
   Epi epi;
 };
@@ -66,7 +67,7 @@ template <class Epi>
 struct JobView {
   const CUtensorMap* tmA;
   const CUtensorMap* tmB;
-  int M, N, K, gx, t0;
+  int M, N, K, gx, t0, a_wrap;
   int* err;
   const Epi* epi;
 };
@@ -79,17 +80,17 @@ struct JobTable {
   int njobs;
   const CUtensorMap* a;
   const CUtensorMap* b;
-  int M, N, K, gx;
+  int M, N, K, gx, a_wrap;
   int* err;
   const Epi* epi;
   __device__ __forceinline__ JobView<Epi> at(int t) const {
     if constexpr (!GROUPED) {
-      return {a, b, M, N, K, gx, 0, err, epi};
+      return {a, b, M, N, K, gx, 0, a_wrap, err, epi};
     } else {
       int j = 0;
       while (j + 1 < njobs && jobs[j + 1].tile0 <= t) ++j;
       const GemmJob<Epi>& J = jobs[j];
-      return {&J.tmA, &J.tmB, J.M, J.N, J.K, J.gx, J.tile0, J.err, &J.epi};
+      return {&J.tmA, &J.tmB, J.M, J.N, J.K, J.gx, J.tile0, J.a_wrap, J.err, &J.epi};
     }
   }
 };
@@ -166,7 +167,8 @@ __device__ __forceinline__ void gemm_body(const JobTable<Epi, GROUPED>& tab, int
         }
         uint8_t* a = smem + s * S::STAGE;
         mbar_expect_tx(&full[s], S::STAGE);
-        tma_load_2d(a, v.tmA, &full[s], kb * BK, m0);
+        // A's K coordinate wraps when B carries a split operand ([hi | lo] K halves)
+        tma_load_2d(a, v.tmA, &full[s], v.a_wrap ? (kb * BK) % v.a_wrap : kb * BK, m0);
         if constexpr (Epi::kB3D)
           tma_load_3d(a + S::A_BYTES, v.tmB, &full[s], kb * BK, 0, v.epi->b_plane(bx, by));
         else
@@ -250,8 +252,8 @@ template <int BN, int STAGES, bool TF32, class Epi>
 __global__ void __launch_bounds__(64 + 32 * Epi::kWarps, 1)
     k_tc_gemm_persistent(const __grid_constant__ CUtensorMap tmA,
                          const __grid_constant__ CUtensorMap tmB, int M, int N, int K, int gx,
-                         int ntiles, const __grid_constant__ Epi epi, int* err) {
-  const JobTable<Epi, false> tab{nullptr, 1, &tmA, &tmB, M, N, K, gx, err, &epi};
+                         int ntiles, int a_wrap, const __grid_constant__ Epi epi, int* err) {
+  const JobTable<Epi, false> tab{nullptr, 1, &tmA, &tmB, M, N, K, gx, a_wrap, err, &epi};
   gemm_body<BN, STAGES, TF32, Epi, false>(tab, ntiles);
 }
 
@@ -260,7 +262,7 @@ __global__ void __launch_bounds__(64 + 32 * Epi::kWarps, 1)
 template <int BN, int STAGES, bool TF32, class Epi>
 __global__ void __launch_bounds__(64 + 32 * Epi::kWarps, 1)
     k_tc_gemm_grouped(const GemmJob<Epi>* __restrict__ jobs, int njobs, int ntiles) {
-  const JobTable<Epi, true> tab{jobs, njobs, nullptr, nullptr, 0, 0, 0, 0, nullptr, nullptr};
+  const JobTable<Epi, true> tab{jobs, njobs, nullptr, nullptr, 0, 0, 0, 0, 0, nullptr, nullptr};
   gemm_body<BN, STAGES, TF32, Epi, true>(tab, ntiles);
 }
 
@@ -864,7 +866,7 @@ static int launch_tc_persistent(const TcGemm& g, const Epi& epi, int gx, int gy,
   static_assert(kTotal <= 232448, "shared memory");
   const int eb = TF32 ? 4 : 2;
   CUtensorMap ta, tb;
-  AFQ_TRY(make_tmap(&ta, g.A, eb, g.m, g.k, g.lda, tc::BM * Epi::kMT));
+  AFQ_TRY(make_tmap(&ta, g.A, eb, g.m, g.ka > 0 ? g.ka : g.k, g.lda, tc::BM * Epi::kMT));
   if (tb_given)
     tb = *tb_given;
   else
@@ -880,6 +882,7 @@ static int launch_tc_persistent(const TcGemm& g, const Epi& epi, int gx, int gy,
   }
   const int grid = (int)(ntiles < tc_sm_count() ? ntiles : tc_sm_count());
   AFQ_LAUNCH(kern, grid, 64 + 32 * Epi::kWarps, kTotal, st, ta, tb, g.m, g.n, g.k, gx, (int)ntiles,
+             g.a_wrap,
              epi, g.err);
   return AFQMC_OK;
 }
@@ -1112,7 +1115,7 @@ namespace {
 template <class Epi>
 int fill_job(tc::GemmJob<Epi>* j, const TcGemm& g, int bn, int gx, int gy, const Epi& e) {
   const int eb = g.tf32 ? 4 : 2;
-  AFQ_TRY(make_tmap(&j->tmA, g.A, eb, g.m, g.k, g.lda, tc::BM * Epi::kMT));
+  AFQ_TRY(make_tmap(&j->tmA, g.A, eb, g.m, g.ka > 0 ? g.ka : g.k, g.lda, tc::BM * Epi::kMT));
   AFQ_TRY(make_tmap(&j->tmB, g.B, eb, g.n, g.k, g.ldb, bn));
   j->M = g.m;
   j->N = g.n;
@@ -1120,6 +1123,7 @@ int fill_job(tc::GemmJob<Epi>* j, const TcGemm& g, int bn, int gx, int gy, const
   j->gx = gx;
   j->ntiles = gx * gy;
   j->tile0 = 0;
+  j->a_wrap = g.a_wrap;
   j->err = g.err;
   j->epi = e;
   return AFQMC_OK;

@@ -239,6 +239,10 @@ int launch_sumsq(const double* v, double* out, int n, cudaStream_t st);
 // dst[r][c] = lo(src[r][c] - (r == c ? minus_diag : 0)), zero for cols <= c < ldd
 int launch_convert_lo(const double* src, long rows, long cols, long lds, void* dst, long ldd,
                       int kind, cudaStream_t st, double minus_diag = 0.0);
+// src - minus_diag I as nseg K segments of width seg per row (pitch seg nseg),
+// segment g the BF16/TF32 high part, or (bit g of lo_mask) the low part.
+int launch_split_lo(const double* src, long rows, long cols, long lds, void* dst, long seg,
+                    int nseg, unsigned lo_mask, int kind, cudaStream_t st, double minus_diag);
 int launch_convert_f32(const double* src, float* dst, long n, cudaStream_t st);
 // full Cholesky vectors transposed, rows (p, q) = p * Mp + q, pitch Gp, low precision
 int launch_pack_blocks_lo(const double* L, int G, int M, int Mp, int Gp, void* out, int kind,

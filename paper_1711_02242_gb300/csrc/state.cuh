@@ -43,6 +43,12 @@ struct Bufs {
   // two Taylor-term operands [W*2N][2Mp]
   void *Bh_lo = nullptr, *V_lo = nullptr, *phi_lo = nullptr, *Tb0 = nullptr, *Tb1 = nullptr;
   float *Bh_tf = nullptr, *acc32 = nullptr;
+  // the half steps' D_B = B_half - I as split pairs along K: [hi | lo] (the
+  // first half step, BF16/TF32, segments of Kp1) and [hi | hi | lo | lo] (the
+  // last one, TF32, segments of Mp)
+  void* Bh_split = nullptr;
+  float* Bh_split_tf = nullptr;
+  int Kp1 = 0;
   int* status = nullptr;  // device status word (tensor-core waits)
   // back-propagation window (afqmc_params.bp_steps > 0): recorded fields
   // [bp_steps][W][2][G] float64 (mixed path: operand rows [W][2][Gp]), Psi_n and the back-propagated

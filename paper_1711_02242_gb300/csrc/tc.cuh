@@ -18,6 +18,10 @@ struct TcGemm {
   long ldb = 0;
   bool tf32 = false;
   int* err = nullptr;  // device status word, set on a timed-out wait
+  // A split operand in B ([B_hi | B_lo] along K, each a_wrap wide, a_wrap a
+  // multiple of 128 bytes of K): A's K coordinate is taken modulo a_wrap, so
+  // that D = A (B_hi + B_lo)^T; ka = A's own K extent (0: k)
+  int a_wrap = 0, ka = 0;
 };
 
 int tc_gemm_store(const TcGemm& g, float* C, long ldc, float alpha, cudaStream_t st);

@@ -1414,6 +1414,36 @@ int launch_convert_lo(const double* src, long rows, long cols, long lds, void* d
   return AFQMC_OK;
 }
 
+// The value a BF16 / TF32 operand copy holds for v (store_lo's rounding).
+__device__ __forceinline__ double lo_value(int kind, double v) {
+  if (kind == LO_BF16) return (double)__bfloat162float(__double2bfloat16(v));
+  return (double)round_tf32((float)v);
+}
+
+// src - minus_diag I as a split operand: row r holds nseg segments of width
+// seg (columns c >= cols zero), segment g the high part hi = lo_value(v) or,
+// when bit g of lo_mask is set, the low part v - hi rounded again, so that
+// hi + lo carries v to about twice the operand precision.
+__global__ void k_split_lo(const double* src, long rows, long cols, long lds, void* dst, long seg,
+                           int nseg, unsigned lo_mask, int kind, double minus_diag) {
+  const long ldd = seg * nseg, n = rows * ldd;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long)gridDim.x * blockDim.x) {
+    const long r = i / ldd, cc = i % ldd, c = cc % seg;
+    const int g = (int)(cc / seg);
+    const double v = c < cols ? src[r * lds + c] - (r == c ? minus_diag : 0.0) : 0.0;
+    store_lo(dst, kind, i, ((lo_mask >> g) & 1u) ? v - lo_value(kind, v) : v);
+  }
+}
+
+int launch_split_lo(const double* src, long rows, long cols, long lds, void* dst, long seg,
+                    int nseg, unsigned lo_mask, int kind, cudaStream_t st, double minus_diag) {
+  if (rows <= 0) return AFQMC_OK;
+  AFQ_LAUNCH(k_split_lo, 152 * 8, 256, 0, st, src, rows, cols, lds, dst, seg, nseg, lo_mask, kind,
+             minus_diag);
+  return AFQMC_OK;
+}
+
 __global__ void k_round_f32(const double* src, float* dst, long n) {
   for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (long)gridDim.x * blockDim.x)

@@ -3,13 +3,16 @@ identical fields, for the 100-orbital workload (10+10 electrons, 500
 vectors, 1024 walkers, 100 steps, a record every 5 steps).
 
 The walkers are independent without population control, so 16 groups of 64
-walkers give 16 independent estimates of each bias.  Bounds (mHa), from the
-measured values with room for their spread:
-  TF32  estimator |bias| < 0.02 (measured 0.005), run |bias| < 0.2 (-0.12)
-  BF16  estimator |bias| < 0.3  (measured 0.195), run |bias| < 0.35 (0.17)
+walkers give 16 independent estimates of each bias.  Bounds (mHa):
+  TF32  estimator |bias| < 0.02 (measured 0.005), run |bias| < 0.1 (-0.047):
+        this workload's mixed path is specified in TF32 within 0.1 mHa of the
+        float64 path;
+  BF16  estimator |bias| < 0.3  (measured 0.195), run |bias| < 0.35 (0.23)
 and each standard error below a quarter of its bound.  A regression of the
-mixed path's rounding (a dropped identity split of exp(-dt v0'/2), a biased
-operand rounding) moves these by far more.
+mixed path's rounding (a dropped identity split of exp(-dt v0'/2), D_B =
+exp(-dt v0'/2) - I taken in one rounding instead of a high and a low part
+(TF32 run bias -0.12), a biased operand rounding) moves these by as much or
+more.
 """
 import pytest
 
@@ -31,7 +34,7 @@ def report():
     return bench.bias_runs(workloads.config("c1"), ("tf32", "bf16"), 100, 5, groups=16)
 
 
-@pytest.mark.parametrize("prec,est_bound,run_bound", [("tf32", 0.02, 0.2), ("bf16", 0.3, 0.35)])
+@pytest.mark.parametrize("prec,est_bound,run_bound", [("tf32", 0.02, 0.1), ("bf16", 0.3, 0.35)])
 def test_mixed_bias_within_stated_bounds(report, prec, est_bound, run_bound):
     r = report["precisions"][prec]
     assert r["status"] == 0 and r["groups_used"] == 16

@@ -130,11 +130,13 @@ def test_ci_trial_differs_from_the_reference_alone(pkg):
     assert abs(run.info().E_T - run1.info().E_T) > 1e-4
 
 
-@pytest.mark.parametrize("prec,tol_e,tol_phi", [(2, 3e-3, 1.5e-2), (1, 4e-4, 2e-3)])
+@pytest.mark.parametrize("prec,tol_e,tol_phi", [(2, 3e-3, 1.5e-2), (1, 4e-4, 4e-3)])
 def test_ci_mixed_path_close_to_float64(pkg, prec, tol_e, tol_phi):
     """The CI trial on the mixed path (BF16/TF32 propagation, the float64
     evaluation relative to the reference) against the float64 path on the same
-    seed and steps: they differ by the propagation's operand rounding only."""
+    seed and steps: they differ by the propagation's operand rounding only.
+    Orbitals and weights within 8 units of the operand rounding (8 x 2^-9 =
+    1.6e-2 BF16, 8 x 2^-11 = 3.9e-3 TF32) after seven steps."""
     M, N, G, W, qr, ep, exc, coef = CASES["cisd"]
     h1, L, coef, up, dn = ci_trial(M, N, G, 7100 + M, exc, coef)
     out = []
