@@ -1005,20 +1005,39 @@ static int setup_device(afqmc_state* s, const double* h1, const double* L, const
     AFQ_TRY(md_setup(s, md_coef));
   else
     AFQ_TRY(launch_rowdot(b.Lh, b.VTt, b.c, G, N * M, s->sf, st));
-  // sum_g L_g L_g
+  // sum_g L_g L_g: one M x M output with K = G M would occupy a few dozen
+  // CTAs, so the vectors go in ych - 1 equal chunks plus the remainder, each
+  // chunk's sum a partial in Ych, the partials then added in order
   {
+    const int np = b.ych > 1 ? b.ych - 1 : 1;
+    const int chunk = G / np, rem = G - np * chunk;
     GemmF64 g;
     g.m = g.n = g.k = M;
-    g.kb = G;
+    g.kb = chunk;
+    g.batch = np;
     g.A = b.Lfull;
     g.lda = M;
     g.sAk = (long)M * M;
+    g.sAb = (long)chunk * M * M;
     g.B = b.Lfull;
     g.ldb = M;
     g.sBk = (long)M * M;
-    g.C = b.L2;
+    g.sBb = (long)chunk * M * M;
+    g.C = b.Ych;
     g.ldc = M;
-    AFQ_TRY(gemm_nt_f64(g, st));
+    g.sCb = (long)M * M;
+    if (chunk > 0) AFQ_TRY(gemm_nt_f64(g, st));
+    if (rem > 0) {
+      GemmF64 r = g;
+      r.kb = rem;
+      r.batch = 1;
+      r.A = b.Lfull + (size_t)np * chunk * M * M;
+      r.B = r.A;
+      r.C = b.Ych + (size_t)np * M * M;
+      AFQ_TRY(gemm_nt_f64(r, st));
+    }
+    AFQ_TRY(launch_sum_parts(chunk > 0 ? b.Ych : b.Ych + (size_t)np * M * M,
+                             (chunk > 0 ? np : 0) + (rem > 0 ? 1 : 0), (long)M * M, b.L2, st));
   }
   // sum_g c_g L_g (packed)
   {

@@ -232,6 +232,8 @@ int launch_v0p(const double* h1, const double* L2, const double* cLp, double* X,
 int launch_norm1(const double* X, double* out, int M, cudaStream_t st);
 int launch_fill_identity(double* X, int M, double scale_diag, cudaStream_t st);
 int launch_scale(double* X, long n, double s, cudaStream_t st);
+// dst = sum of nparts arrays of n doubles (parts[j][e]), added in the order of j
+int launch_sum_parts(const double* parts, int nparts, long n, double* dst, cudaStream_t st);
 int launch_init_walkers(const double* VTt, double* phiT, double* wt, int W, int N, int M,
                         cudaStream_t st);
 int launch_sumsq(const double* v, double* out, int n, cudaStream_t st);

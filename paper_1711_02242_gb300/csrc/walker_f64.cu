@@ -1347,6 +1347,22 @@ int launch_fill_identity(double* X, int M, double d, cudaStream_t st) {
   return AFQMC_OK;
 }
 
+// dst[e] = sum_{j < nparts} parts[j][e], the parts added in order.
+__global__ void k_sum_parts(const double* parts, int nparts, long n, double* dst) {
+  for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (long)gridDim.x * blockDim.x) {
+    double v = 0.0;
+    for (int j = 0; j < nparts; ++j) v += parts[(long)j * n + e];
+    dst[e] = v;
+  }
+}
+
+int launch_sum_parts(const double* parts, int nparts, long n, double* dst, cudaStream_t st) {
+  if (n <= 0) return AFQMC_OK;
+  AFQ_LAUNCH(k_sum_parts, cdiv((size_t)n, 256), 256, 0, st, parts, nparts, n, dst);
+  return AFQMC_OK;
+}
+
 __global__ void k_scale(double* X, long n, double s) {
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) X[i] *= s;
