@@ -953,6 +953,15 @@ static int setup_device(afqmc_state* s, const double* h1, const double* L, const
       if (v == 0.0) continue;
       for (int q = 0; q < M; ++q) vtt[(size_t)i * M + q] += v * qh[(size_t)r * M + q];
     }
+  // the trial's orbitals in the caller's basis, (Q V_T')^T (N x M): spin-up
+  // the first nup columns of Q, spin-down Q (Q^T V_dn)
+  std::vector<double> vto((size_t)N * M, 0.0);
+  for (int i = 0; i < N; ++i)
+    for (int r = 0; r < M; ++r) {
+      double v = 0.0;
+      for (int q = 0; q < M; ++q) v += qh[(size_t)r * M + q] * vtt[(size_t)i * M + q];
+      vto[(size_t)i * M + r] = v;
+    }
   AFQ_CUDA(cudaMemcpyAsync(b.Qb, qh.data(), sizeof(double) * M * M, cudaMemcpyHostToDevice, st));
   AFQ_CUDA(cudaMemcpyAsync(b.QTb, qt.data(), sizeof(double) * M * M, cudaMemcpyHostToDevice, st));
   AFQ_CUDA(cudaMemcpyAsync(b.VTt, vtt.data(), sizeof(double) * N * M, cudaMemcpyHostToDevice, st));
@@ -962,11 +971,77 @@ static int setup_device(afqmc_state* s, const double* h1, const double* L, const
   // h' = Q^T h Q and L'_g = Q^T L_g Q (h, L_g symmetric: B = h reads h^T)
   AFQ_TRY(gemm_sq(b.QTb, 0, b.X, 0, b.E0, 0, M, 1, st));
   AFQ_TRY(gemm_sq(b.E0, 0, b.QTb, 0, b.h1, 0, M, 1, st));
+  // Single-determinant mixed path: the rotated L'_g only feed the BF16/TF32
+  // operands and B_half (applied as BF16/TF32 high and low parts), so they are
+  // rotated with FP32 products; the half-rotated vectors Lh_g (force bias and
+  // c_g in float64) are formed in float64 from the caller's basis first,
+  // Lh_g = V_T'^T Q^T L_g Q = ((Q V_T')^T L_g) Q.
+  const bool f32_rot = b.mixed && !md;
+  if (f32_rot) {
+    AFQ_CUDA(cudaMemcpyAsync(b.E1, vto.data(), sizeof(double) * N * M, cudaMemcpyHostToDevice, st));
+    const int cz = (int)std::max<long>(1, (long)b.ych * M / N);  // vectors per chunk of Ych
+    for (int g0 = 0; g0 < G; g0 += cz) {
+      const int nb = G - g0 < cz ? G - g0 : cz;
+      GemmF64 z;  // Z_g = (Q V_T')^T L_g, N x M per vector
+      z.m = N;
+      z.n = z.k = M;
+      z.batch = nb;
+      z.A = b.E1;
+      z.lda = M;
+      z.B = b.Lfull + (size_t)g0 * M * M;
+      z.ldb = M;
+      z.sBb = (long)M * M;
+      z.C = b.Ych;
+      z.ldc = M;
+      z.sCb = (long)N * M;
+      AFQ_TRY(gemm_nt_f64(z, st));
+      GemmF64 l;  // Lh_g = Z_g Q for the chunk's nb N rows at once
+      l.m = nb * N;
+      l.n = l.k = M;
+      l.A = b.Ych;
+      l.lda = M;
+      l.B = b.QTb;
+      l.ldb = M;
+      l.C = b.Lh + (size_t)g0 * N * M;
+      l.ldc = M;
+      AFQ_TRY(gemm_nt_f64(l, st));
+    }
+    // Q^T in FP32 (E0 is free once h' is formed)
+    AFQ_TRY(launch_round_f32(b.QTb, reinterpret_cast<float*>(b.E0), (long)M * M, st));
+  }
   for (int g0 = 0; g0 < G; g0 += b.ych) {
     const int nb = G - g0 < b.ych ? G - g0 : b.ych;
     double* Lg = b.Lfull + (size_t)g0 * M * M;
-    AFQ_TRY(gemm_sq(b.QTb, 0, Lg, (long)M * M, b.Ych, (long)M * M, M, nb, st));
-    AFQ_TRY(gemm_sq(b.Ych, (long)M * M, b.QTb, 0, Lg, (long)M * M, M, nb, st));
+    if (f32_rot) {
+      float* Y = reinterpret_cast<float*>(b.Ych);
+      GemmNT<double, double, float> y;  // Q^T L_g
+      y.m = y.n = y.k = M;
+      y.batch = nb;
+      y.A = b.QTb;
+      y.lda = M;
+      y.B = Lg;
+      y.ldb = M;
+      y.sBb = (long)M * M;
+      y.C = Y;
+      y.ldc = M;
+      y.sCb = (long)M * M;
+      AFQ_TRY(gemm_nt_ddf(y, st));
+      GemmNT<float, float, double> r;  // (Q^T L_g) Q
+      r.m = r.n = r.k = M;
+      r.batch = nb;
+      r.A = Y;
+      r.lda = M;
+      r.sAb = (long)M * M;
+      r.B = reinterpret_cast<const float*>(b.E0);
+      r.ldb = M;
+      r.C = Lg;
+      r.ldc = M;
+      r.sCb = (long)M * M;
+      AFQ_TRY(gemm_nt_ffd(r, st));
+    } else {
+      AFQ_TRY(gemm_sq(b.QTb, 0, Lg, (long)M * M, b.Ych, (long)M * M, M, nb, st));
+      AFQ_TRY(gemm_sq(b.Ych, (long)M * M, b.QTb, 0, Lg, (long)M * M, M, nb, st));
+    }
   }
   // packed, transposed Cholesky vectors for the V contraction
   AFQ_TRY(launch_pack_transpose(b.Lfull, b.LpT, G, M, st));
@@ -985,7 +1060,7 @@ static int setup_device(afqmc_state* s, const double* h1, const double* L, const
     g.C = b.Lh;
     g.ldc = M;
     g.sCb = (long)N * M;
-    AFQ_TRY(gemm_nt_f64(g, st));
+    if (!f32_rot) AFQ_TRY(gemm_nt_f64(g, st));
     GemmF64 h;
     h.m = N;
     h.n = M;
@@ -1026,7 +1101,9 @@ static int setup_device(afqmc_state* s, const double* h1, const double* L, const
     g.C = b.Ych;
     g.ldc = M;
     g.sCb = (long)M * M;
-    if (chunk > 0) AFQ_TRY(gemm_nt_f64(g, st));
+    // (mixed path: FP32 products, summed in float64 across 16-term blocks)
+    auto run = f32_rot ? gemm_nt_f32_split : gemm_nt_f64;
+    if (chunk > 0) AFQ_TRY(run(g, st));
     if (rem > 0) {
       GemmF64 r = g;
       r.kb = rem;
@@ -1034,7 +1111,7 @@ static int setup_device(afqmc_state* s, const double* h1, const double* L, const
       r.A = b.Lfull + (size_t)np * chunk * M * M;
       r.B = r.A;
       r.C = b.Ych + (size_t)np * M * M;
-      AFQ_TRY(gemm_nt_f64(r, st));
+      AFQ_TRY(run(r, st));
     }
     AFQ_TRY(launch_sum_parts(chunk > 0 ? b.Ych : b.Ych + (size_t)np * M * M,
                              (chunk > 0 ? np : 0) + (rem > 0 ? 1 : 0), (long)M * M, b.L2, st));

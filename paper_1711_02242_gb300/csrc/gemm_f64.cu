@@ -9,7 +9,11 @@
 // FP64 pipe whatever the tiling; a 64x64 tile with a 4x4 register block per
 // thread keeps it busy with a few resident warps per SM.
 // Mixed instances (FP32 accumulation) multiply the exp(-dt v0'/2) factor
-// into float64 or float32 walkers and store float32 or float64.
+// into float64 or float32 walkers and store float32 or float64, and form the
+// set-up products of the mixed path that only feed BF16/TF32 operands (the
+// basis rotation of the Cholesky vectors, sum_g L_g L_g).
+#include <type_traits>
+
 #include "kernels.cuh"
 
 namespace afq {
@@ -17,21 +21,25 @@ namespace afq {
 namespace {
 constexpr int BM = 64, BN = 64, BK = 16, TPB = 256;
 
-template <typename TA, typename TB, typename TC, typename ACC>
+// SPLIT (FP32 ACC): the products of each BK-term block of K are summed in
+// FP32 and the block sums in float64, so the rounding error no longer grows
+// with K (used for sums over all Cholesky vectors, K = G M).
+template <typename TA, typename TB, typename TC, typename ACC, bool SPLIT = false>
 __global__ void __launch_bounds__(TPB) k_gemm_nt(GemmNT<TA, TB, TC> g) {
   __shared__ ACC As[BK][BM + 1];
   __shared__ ACC Bs[BK][BN + 1];
+  using SUM = typename std::conditional<SPLIT, double, ACC>::type;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
   const long z = blockIdx.z;
   const TA* A = g.A + z * g.sAb;
   const TB* B = g.B + z * g.sBb;
   TC* C = g.C + z * g.sCb;
-  ACC acc[4][4];
+  SUM acc[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = ACC(0);
+    for (int j = 0; j < 4; ++j) acc[i][j] = SUM(0);
 
   for (int b = 0; b < g.kb; ++b) {
     const TA* Ab = A + (long)b * g.sAk;
@@ -47,6 +55,11 @@ __global__ void __launch_bounds__(TPB) k_gemm_nt(GemmNT<TA, TB, TC> g) {
         Bs[col][row] = (gn < g.n && gk < g.k) ? ACC(Bb[(long)gn * g.ldb + gk]) : ACC(0);
       }
       __syncthreads();
+      ACC blk[4][4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) blk[i][j] = SPLIT ? ACC(0) : ACC(acc[i][j]);
 #pragma unroll
       for (int kk = 0; kk < BK; ++kk) {
         ACC a[4], bv[4];
@@ -57,8 +70,12 @@ __global__ void __launch_bounds__(TPB) k_gemm_nt(GemmNT<TA, TB, TC> g) {
 #pragma unroll
         for (int i = 0; i < 4; ++i)
 #pragma unroll
-          for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], bv[j], acc[i][j]);
+          for (int j = 0; j < 4; ++j) blk[i][j] = fma(a[i], bv[j], blk[i][j]);
       }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = SPLIT ? acc[i][j] + SUM(blk[i][j]) : SUM(blk[i][j]);
       __syncthreads();
     }
   }
@@ -72,15 +89,15 @@ __global__ void __launch_bounds__(TPB) k_gemm_nt(GemmNT<TA, TB, TC> g) {
       int gn = n0 + tx + 16 * j;
       if (gn >= g.n) continue;
       TC* c = C + (long)gm * g.ldc + gn;
-      ACC v = ACC(g.alpha) * acc[i][j];
-      if (g.beta != 0.0) v = fma(ACC(g.beta), ACC(*c), v);
+      SUM v = SUM(g.alpha) * acc[i][j];
+      if (g.beta != 0.0) v = fma(SUM(g.beta), SUM(*c), v);
       *c = TC(v);
     }
   }
 }
 }  // namespace
 
-template <typename TA, typename TB, typename TC, typename ACC>
+template <typename TA, typename TB, typename TC, typename ACC, bool SPLIT = false>
 static int launch_gemm(const GemmNT<TA, TB, TC>& g, cudaStream_t st) {
   if (g.m <= 0 || g.n <= 0 || g.batch <= 0) return AFQMC_OK;
   if (g.k < 0 || g.kb < 1) {
@@ -96,7 +113,7 @@ static int launch_gemm(const GemmNT<TA, TB, TC>& g, cudaStream_t st) {
     set_error("gemm_nt: grid too large (m=%d batch=%d)", g.m, g.batch);
     return AFQMC_EINVAL;
   }
-  AFQ_LAUNCH((k_gemm_nt<TA, TB, TC, ACC>), grid, TPB, 0, st, g);
+  AFQ_LAUNCH((k_gemm_nt<TA, TB, TC, ACC, SPLIT>), grid, TPB, 0, st, g);
   return AFQMC_OK;
 }
 
@@ -106,6 +123,12 @@ int gemm_nt_dff(const GemmNT<double, float, float>& g, cudaStream_t st) {
 }
 int gemm_nt_ffd(const GemmNT<float, float, double>& g, cudaStream_t st) {
   return launch_gemm<float, float, double, float>(g, st);
+}
+int gemm_nt_ddf(const GemmNT<double, double, float>& g, cudaStream_t st) {
+  return launch_gemm<double, double, float, float>(g, st);
+}
+int gemm_nt_f32_split(const GemmF64& g, cudaStream_t st) {
+  return launch_gemm<double, double, double, float, true>(g, st);
 }
 
 }  // namespace afq

@@ -446,18 +446,62 @@ __device__ __forceinline__ void store8_lo(void* base, int kind, long idx, const 
   }
 }
 
+// 4 consecutive values (times sign) into a BF16 or TF32 row at element idx
+// (idx a multiple of 4 elements): one 8- or 16-byte store.
+__device__ __forceinline__ void store4_lo(void* base, int kind, long idx, const float* v,
+                                          float sign) {
+  if (kind == LO_BF16) {
+    uint2 w;
+    __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(&w);
+    h[0] = __floats2bfloat162_rn(sign * v[0], sign * v[1]);
+    h[1] = __floats2bfloat162_rn(sign * v[2], sign * v[3]);
+    *reinterpret_cast<uint2*>(reinterpret_cast<__nv_bfloat16*>(base) + idx) = w;
+  } else {
+    *reinterpret_cast<float4*>(reinterpret_cast<float*>(base) + idx) =
+        make_float4(round_tf32(sign * v[0]), round_tf32(sign * v[1]), round_tf32(sign * v[2]),
+                    round_tf32(sign * v[3]));
+  }
+}
+
+// Row-contiguous epilogue access for the half steps.  A TMEM load gives each
+// lane one row and 16 consecutive columns; written as such, a warp's global
+// accesses touch 32 rows per instruction.  The chunk is passed through 2 KB of
+// shared memory per warp instead (16-byte slots, XOR-swizzled by row so that
+// both the row-per-lane writes and the reads below are free of bank
+// conflicts), and read back as 8 rows x 4 groups of 4 columns per pass: every
+// global instruction then covers whole 32-byte sectors of 8 rows.
+struct ChunkStage {
+  static constexpr int kBytesPerWarp = 32 * 16 * 4;
+  float* sm;  // this warp's 32 x 16 floats
+  __device__ __forceinline__ static int slot(int r, int s) { return r * 16 + 4 * (s ^ ((r >> 1) & 3)); }
+  __device__ __forceinline__ void put(int lane, const float* v) const {
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+      *reinterpret_cast<float4*>(sm + slot(lane, s)) = make_float4(v[4 * s], v[4 * s + 1], v[4 * s + 2], v[4 * s + 3]);
+  }
+  // pass k: row 8k + lane / 4, columns 4 (lane % 4) .. + 3
+  __device__ __forceinline__ void get(int lane, int k, float* x) const {
+    const float4 f = *reinterpret_cast<const float4*>(sm + slot(8 * k + (lane >> 2), lane & 3));
+    x[0] = f.x;
+    x[1] = f.y;
+    x[2] = f.z;
+    x[3] = f.w;
+  }
+};
+
 // First half step: rows (w,c,i) of Phi^T, columns p.  B_half = I + D_B is
 // applied as Phi + Phi D_B: the product runs with the BF16/TF32 copies of Phi
 // and D_B = B_half - I, and the epilogue adds the float64 orbitals phi_id
 // (pitch M, same rows) so that the identity part is exact (rounding B_half's
 // diagonal, close to 1, to BF16/TF32 would scale every walker's orbitals by
 // the same factor each step).  acc[(w,c,i)][p] = (B_half Phi)^T (FP32, pitch
-// ldacc) and Tb holds the 0th Taylor term.  Each thread owns one row and 16
-// consecutive p per chunk: vector stores.
+// ldacc, a multiple of 4) and Tb holds the 0th Taylor term.  Chunks of 16
+// columns go through ChunkStage: each lane then reads and writes 4
+// consecutive p of one row.
 struct EpiProp0 {
-  static constexpr int kSmemBytes = 0;
-  static constexpr bool kB3D = false;  // B tile = one 2-D box at row n_origin
   static constexpr int kWarps = 8;      // epilogue warps: two per TMEM lane quarter
+  static constexpr int kSmemBytes = kWarps * ChunkStage::kBytesPerWarp;
+  static constexpr bool kB3D = false;  // B tile = one 2-D box at row n_origin
   static constexpr int kMT = 1;         // 128-row A tiles per output tile
   float* acc;
   long ldacc;
@@ -469,52 +513,87 @@ struct EpiProp0 {
   __device__ __forceinline__ int n_origin(int, int by) const { return by * bn; }
   template <int BN>
   __device__ __forceinline__ void run(uint32_t tmem, int q, int lane, int ew, int, int, int m0,
-                                      int n0, int, int, float*) const {
-    const int row = m0 + 32 * q + lane;
-    // the two warps of a lane quarter take alternate 16-column chunks
+                                      int n0, int, int, float* esm) const {
+    const ChunkStage cs{esm + ew * 512};
+    const int cq = 4 * (lane & 3);
+    // the four rows this lane writes (row 8k + lane / 4 of the quarter, k < 4):
+    // Tb row offsets and the sign of the -Im block, fixed for the whole tile
+    long fr[4], t1[4], t2[4];
+    float s2[4];
+    bool live[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int row = m0 + 32 * q + 8 * k + (lane >> 2);
+      live[k] = row < rows;
+      const int w = row / (2 * N), rem = row % (2 * N), c = rem / N, i = rem % N;
+      const long rr = ((long)w * 2 * N + i) * 2L * Mp, ri = ((long)w * 2 * N + N + i) * 2L * Mp;
+      fr[k] = (long)row;
+      t1[k] = c == 0 ? rr : ri;            // Re -> rr[p],      Im -> ri[p]
+      t2[k] = c == 0 ? ri + Mp : rr + Mp;  // Re -> ri[Mp + p], Im -> -rr[Mp + p]
+      s2[k] = c == 0 ? 1.f : -1.f;
+    }
+    // this lane's float64 orbitals for the chunk at column c0 (zeros outside)
+    auto load = [&](double (&f)[4][4], int c0) {
+      const int p = n0 + c0 + cq;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const long fi = fr[k] * M + p;
+        if (live[k] && p + 4 <= M && (fi & 1) == 0) {
+          const double2 d0 = __ldg(reinterpret_cast<const double2*>(phi_id + fi));
+          const double2 d1 = __ldg(reinterpret_cast<const double2*>(phi_id + fi + 2));
+          f[k][0] = d0.x;
+          f[k][1] = d0.y;
+          f[k][2] = d1.x;
+          f[k][3] = d1.y;
+        } else {
+#pragma unroll
+          for (int u = 0; u < 4; ++u) f[k][u] = (live[k] && p + u < M) ? __ldg(phi_id + fi + u) : 0.0;
+        }
+      }
+    };
+    // the two warps of a lane quarter take alternate 16-column chunks; the
+    // next chunk's loads are in flight while this one is written
+    double fn[4][4];
+    int c0 = 16 * (ew >> 2);
+    if (c0 < BN) load(fn, c0);
 #pragma unroll 1
-    for (int c0 = 16 * (ew >> 2); c0 < BN; c0 += 32) {
+    for (; c0 < BN; c0 += 32) {
+      double f[4][4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) f[k][u] = fn[k][u];
+      if (c0 + 32 < BN) load(fn, c0 + 32);
       float v[16];
       tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c0, v);
-      if (row >= rows) continue;
-      const int w = row / (2 * N), rem = row % (2 * N), c = rem / N, i = rem % N;
-      const int pb = n0 + c0;
-      if (pb >= M) continue;
-      const double* f = phi_id + (long)row * M + pb;
-      if (pb + 16 <= M && (((long)row * M + pb) & 1) == 0) {
+      if (n0 + c0 >= M) continue;  // the same for the whole warp
+      const int p = n0 + c0 + cq;
+      const bool full4 = p + 4 <= M;
+      cs.put(lane, v);
+      __syncwarp();
 #pragma unroll
-        for (int u = 0; u < 16; u += 2) {
-          const double2 d = __ldg(reinterpret_cast<const double2*>(f + u));
-          v[u] += (float)d.x;
-          v[u + 1] += (float)d.y;
-        }
-      } else {
+      for (int k = 0; k < 4; ++k) {
+        float x[4];
+        cs.get(lane, k, x);
+        if (!live[k] || p >= M) continue;
 #pragma unroll
-        for (int u = 0; u < 16; ++u)
-          if (pb + u < M) v[u] += (float)__ldg(f + u);
-      }
-      if (pb + 16 <= M) {
-        float4* a4 = reinterpret_cast<float4*>(acc + (long)row * ldacc + pb);
-#pragma unroll
-        for (int k = 0; k < 4; ++k) a4[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
-        const long rr = ((long)w * 2 * N + i) * 2L * Mp, ri = ((long)w * 2 * N + N + i) * 2L * Mp;
-        if (c == 0) {
-          store16_lo(tb, lo_kind, rr + pb, v, 1.f);
-          store16_lo(tb, lo_kind, ri + Mp + pb, v, 1.f);
+        for (int u = 0; u < 4; ++u) x[u] += (float)f[k][u];
+        float* a = acc + fr[k] * ldacc + p;
+        if (full4) {
+          *reinterpret_cast<float4*>(a) = make_float4(x[0], x[1], x[2], x[3]);
+          store4_lo(tb, lo_kind, t1[k] + p, x, 1.f);
+          store4_lo(tb, lo_kind, t2[k] + p, x, s2[k]);
         } else {
-          store16_lo(tb, lo_kind, rr + Mp + pb, v, -1.f);
-          store16_lo(tb, lo_kind, ri + pb, v, 1.f);
-        }
-      } else {
 #pragma unroll
-        for (int u = 0; u < 16; ++u) {
-          const int p = pb + u;
-          if (p < M) {
-            acc[(long)row * ldacc + p] = v[u];
-            put_term(tb, lo_kind, (long)w * 2 * N, N, Mp, c, i, p, v[u]);
-          }
+          for (int u = 0; u < 4; ++u)
+            if (p + u < M) {
+              a[u] = x[u];
+              store_lo_f(tb, lo_kind, t1[k] + p + u, x[u]);
+              store_lo_f(tb, lo_kind, t2[k] + p + u, s2[k] * x[u]);
+            }
         }
       }
+      __syncwarp();  // the next chunk overwrites this warp's stage
     }
   }
 };
@@ -667,11 +746,12 @@ struct EpiV {
 };
 
 // Last half step: rows (w,c,i) of the series sum, columns p; the product is
-// stored as the new float64 orbitals of live walkers.
+// stored as the new float64 orbitals of live walkers.  Chunks of 16 columns go
+// through ChunkStage, as in EpiProp0.
 struct EpiPhi {
-  static constexpr int kSmemBytes = 0;
-  static constexpr bool kB3D = false;  // B tile = one 2-D box at row n_origin
   static constexpr int kWarps = 8;      // epilogue warps: two per TMEM lane quarter
+  static constexpr int kSmemBytes = kWarps * ChunkStage::kBytesPerWarp;
+  static constexpr bool kB3D = false;  // B tile = one 2-D box at row n_origin
   static constexpr int kMT = 1;         // 128-row A tiles per output tile
   double* phiT;
   const double* wt;
@@ -686,50 +766,93 @@ struct EpiPhi {
   __device__ __forceinline__ int n_origin(int, int by) const { return by * bn; }
   template <int BN>
   __device__ __forceinline__ void run(uint32_t tmem, int q, int lane, int ew, int, int, int m0,
-                                      int n0, int, int, float*) const {
-    const int row = m0 + 32 * q + lane;
-    const bool ok = row < rows && walker_alive(wt, row / (2 * N));
-    // the two warps of a lane quarter take alternate 16-column chunks
+                                      int n0, int, int, float* esm) const {
+    const ChunkStage cs{esm + ew * 512};
+    const int cq = 4 * (lane & 3);
+    // the four rows this lane writes (row 8k + lane / 4 of the quarter, k < 4)
+    long fr[4];
+    bool live[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int row = m0 + 32 * q + 8 * k + (lane >> 2);
+      fr[k] = (long)row;
+      live[k] = row < rows && walker_alive(wt, row / (2 * N));
+    }
+    // this lane's T_0 and S for the chunk at column c0 (zeros outside); they
+    // are summed where used, so that nothing waits on the loads early
+    auto load = [&](float (&id)[4][8], int c0) {
+      const int p = n0 + c0 + cq;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const float* t0 = acc_id + fr[k] * 2 * Mp + p;
+        if (live[k] && p + 4 <= M) {
+          const float4 a = __ldg(reinterpret_cast<const float4*>(t0));
+          const float4 b = __ldg(reinterpret_cast<const float4*>(t0 + Mp));
+          id[k][0] = a.x;
+          id[k][1] = a.y;
+          id[k][2] = a.z;
+          id[k][3] = a.w;
+          id[k][4] = b.x;
+          id[k][5] = b.y;
+          id[k][6] = b.z;
+          id[k][7] = b.w;
+        } else {
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const bool in = live[k] && p + u < M;
+            id[k][u] = in ? __ldg(t0 + u) : 0.f;
+            id[k][4 + u] = in ? __ldg(t0 + Mp + u) : 0.f;
+          }
+        }
+      }
+    };
+    // the two warps of a lane quarter take alternate 16-column chunks; the
+    // next chunk's loads are in flight while this one is written
+    float idn[4][8];
+    int c0 = 16 * (ew >> 2);
+    if (c0 < BN) load(idn, c0);
 #pragma unroll 1
-    for (int c0 = 16 * (ew >> 2); c0 < BN; c0 += 32) {
+    for (; c0 < BN; c0 += 32) {
+      float id[4][8];
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int u = 0; u < 8; ++u) id[k][u] = idn[k][u];
+      if (c0 + 32 < BN) load(idn, c0 + 32);
       float v[16];
       tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c0, v);
-      if (!ok) continue;
-      const int pb = n0 + c0;
-      if (pb >= M) continue;
-      const float* t0 = acc_id + (long)row * 2 * Mp + pb;
-      if (pb + 16 <= M) {
+      if (n0 + c0 >= M) continue;  // the same for the whole warp
+      const int p = n0 + c0 + cq;
+      const bool full4 = p + 4 <= M;
+      cs.put(lane, v);
+      __syncwarp();
 #pragma unroll
-        for (int u = 0; u < 16; u += 4) {
-          const float4 a = __ldg(reinterpret_cast<const float4*>(t0 + u));
-          const float4 b = __ldg(reinterpret_cast<const float4*>(t0 + Mp + u));
-          v[u] += a.x + b.x;
-          v[u + 1] += a.y + b.y;
-          v[u + 2] += a.z + b.z;
-          v[u + 3] += a.w + b.w;
+      for (int k = 0; k < 4; ++k) {
+        float x[4];
+        cs.get(lane, k, x);
+        if (!live[k] || p >= M) continue;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) x[u] += id[k][u] + id[k][4 + u];
+        double* o = phiT + fr[k] * M + p;
+        if (full4) {
+          if (((fr[k] * M + p) & 1) == 0) {
+            reinterpret_cast<double2*>(o)[0] = make_double2((double)x[0], (double)x[1]);
+            reinterpret_cast<double2*>(o)[1] = make_double2((double)x[2], (double)x[3]);
+          } else {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) o[u] = (double)x[u];
+          }
+          store4_lo(phi_lo, lo_kind, fr[k] * Mp + p, x, 1.f);
+        } else {
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            if (p + u < M) {
+              o[u] = (double)x[u];
+              store_lo_f(phi_lo, lo_kind, fr[k] * Mp + p + u, x[u]);
+            }
         }
-      } else {
-#pragma unroll
-        for (int u = 0; u < 16; ++u)
-          if (pb + u < M) v[u] += __ldg(t0 + u) + __ldg(t0 + Mp + u);
       }
-      double* o = phiT + (long)row * M + pb;
-      if (pb + 16 <= M && (((long)row * M + pb) & 1) == 0) {
-#pragma unroll
-        for (int u = 0; u < 16; u += 2)
-          *reinterpret_cast<double2*>(o + u) = make_double2((double)v[u], (double)v[u + 1]);
-      } else {
-#pragma unroll
-        for (int u = 0; u < 16; ++u)
-          if (pb + u < M) o[u] = (double)v[u];
-      }
-      if (pb + 16 <= M) {
-        store16_lo(phi_lo, lo_kind, (long)row * Mp + pb, v, 1.f);
-      } else {
-#pragma unroll
-        for (int u = 0; u < 16; ++u)
-          if (pb + u < M) store_lo_f(phi_lo, lo_kind, (long)row * Mp + pb + u, v[u]);
-      }
+      __syncwarp();  // the next chunk overwrites this warp's stage
     }
   }
 };
@@ -970,6 +1093,8 @@ int tc_tune_store(const TcGemm& g, float* C, long ldc, float alpha, cudaStream_t
 }
 
 // Tile width for an output of n columns: 160 or 256, whichever pads less.
+// At 160 the ring keeps five 36 KB stages beside the epilogue's 16 KB stage.
+constexpr int kHalfStages160 = 5;
 static int half_step_bn(int n) {
   const int pad160 = cdiv(n, 160) * 160 - n, pad256 = cdiv(n, 256) * 256 - n;
   return pad160 < pad256 ? 160 : 256;
@@ -981,8 +1106,8 @@ int tc_prop_first(const TcGemm& g, float* acc, long ldacc, void* tb, const doubl
   tc::EpiProp0 e{acc, ldacc, tb, phi_id, lo_kind, N, M, Mp, g.m, bn};
   const int gx = cdiv(g.m, tc::BM), gy = cdiv(M, bn);
   if (bn == 160) {
-    if (g.tf32) return launch_tc_persistent<160, 6, true>(g, e, gx, gy, st);
-    return launch_tc_persistent<160, 6, false>(g, e, gx, gy, st);
+    if (g.tf32) return launch_tc_persistent<160, kHalfStages160, true>(g, e, gx, gy, st);
+    return launch_tc_persistent<160, kHalfStages160, false>(g, e, gx, gy, st);
   }
   if (g.tf32) return launch_tc_persistent<256, 4, true>(g, e, gx, gy, st);
   return launch_tc_persistent<256, 4, false>(g, e, gx, gy, st);
@@ -1081,8 +1206,8 @@ int tc_prop_last(const TcGemm& g, double* phiT, const double* wt, int N, int M, 
   tc::EpiPhi e{phiT, wt, N, M, g.m, bn, phi_lo, lo_kind, Mp, acc_id};
   const int gx = cdiv(g.m, tc::BM), gy = cdiv(M, bn);
   if (bn == 160) {
-    if (g.tf32) return launch_tc_persistent<160, 6, true>(g, e, gx, gy, st);
-    return launch_tc_persistent<160, 6, false>(g, e, gx, gy, st);
+    if (g.tf32) return launch_tc_persistent<160, kHalfStages160, true>(g, e, gx, gy, st);
+    return launch_tc_persistent<160, kHalfStages160, false>(g, e, gx, gy, st);
   }
   if (g.tf32) return launch_tc_persistent<256, 4, true>(g, e, gx, gy, st);
   return launch_tc_persistent<256, 4, false>(g, e, gx, gy, st);
@@ -1203,10 +1328,10 @@ int dispatch_grouped(const TcGrouped& gr, cudaStream_t st) {
       if (gr.bn == 128) return launch_grouped<128, 4, TF32, tc::EpiV>(gr, st);
       return launch_grouped<256, 3, TF32, tc::EpiV>(gr, st);
     case TC_JOB_PROP0:
-      if (gr.bn == 160) return launch_grouped<160, 6, TF32, tc::EpiProp0>(gr, st);
+      if (gr.bn == 160) return launch_grouped<160, kHalfStages160, TF32, tc::EpiProp0>(gr, st);
       return launch_grouped<256, 4, TF32, tc::EpiProp0>(gr, st);
     case TC_JOB_PHI:
-      if (gr.bn == 160) return launch_grouped<160, 6, TF32, tc::EpiPhi>(gr, st);
+      if (gr.bn == 160) return launch_grouped<160, kHalfStages160, TF32, tc::EpiPhi>(gr, st);
       return launch_grouped<256, 4, TF32, tc::EpiPhi>(gr, st);
   }
   set_error("grouped contraction: unknown kind %d", gr.kind);

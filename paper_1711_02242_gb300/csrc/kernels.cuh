@@ -87,6 +87,12 @@ int gemm_nt_f64(const GemmF64& g, cudaStream_t st);
 // FP32 accumulation: float64 A -> float32 C, and float32 A -> float64 C
 int gemm_nt_dff(const GemmNT<double, float, float>& g, cudaStream_t st);
 int gemm_nt_ffd(const GemmNT<float, float, double>& g, cudaStream_t st);
+int gemm_nt_ddf(const GemmNT<double, double, float>& g, cudaStream_t st);
+// float64 operands, FP32 products summed in FP32 over each 16-term block of K
+// and in float64 across the blocks
+int gemm_nt_f32_split(const GemmF64& g, cudaStream_t st);
+// float64 -> FP32, round to nearest even
+int launch_round_f32(const double* src, float* dst, long n, cudaStream_t st);
 
 // ---- step kernels (float64) -------------------------------------------------
 struct FieldArgs {
