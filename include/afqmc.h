@@ -170,7 +170,13 @@ typedef struct afqmc_state afqmc_state; /* opaque */
  * only, without back-propagation (else AFQMC_EUNSUPPORTED).
  * d_workspace: device buffer of ws_bytes >= afqmc_workspace_size(p).
  * stream: cudaStream_t (as void*) on which every kernel of the state runs.
- * Synchronises the stream.  On failure *out is NULL.
+ * Synchronises the stream.  On failure *out is NULL.  A NaN or infinity in
+ * h1, the trial or L gives AFQMC_ENONFINITE, with the first such index in
+ * afqmc_last_error() (L is checked on the device right after its upload).
+ * On the mixed precisions (single determinant) the rotation of L to the
+ * trial's basis and sum_g L_g^2 use FP32 products (they feed the BF16/TF32
+ * operands and B_half, applied as BF16/TF32 parts); V_sigma^T L_g, c_g and
+ * H0' stay float64.
  */
 AFQMC_API int afqmc_init(const afqmc_params* p, const double* h1, const double* L,
                          const double* trial_up, const double* trial_dn, void* d_workspace,

@@ -953,71 +953,72 @@ static int setup_device(afqmc_state* s, const double* h1, const double* L, const
       if (v == 0.0) continue;
       for (int q = 0; q < M; ++q) vtt[(size_t)i * M + q] += v * qh[(size_t)r * M + q];
     }
-  // the trial's orbitals in the caller's basis, (Q V_T')^T (N x M): spin-up
-  // the first nup columns of Q, spin-down Q (Q^T V_dn)
-  std::vector<double> vto((size_t)N * M, 0.0);
-  for (int i = 0; i < N; ++i)
-    for (int r = 0; r < M; ++r) {
-      double v = 0.0;
-      for (int q = 0; q < M; ++q) v += qh[(size_t)r * M + q] * vtt[(size_t)i * M + q];
-      vto[(size_t)i * M + r] = v;
-    }
+  // sf P = sf sum_i v_i v_i^T with v_i the trial's orbitals in the caller's
+  // basis (the first nup columns of Q): c_g = Tr(L_g P) without the rotation
+  std::vector<double> Pt;
+  if (b.mixed && !md && !s->spin2) {
+    Pt.assign((size_t)M * M, 0.0);
+    for (int r = 0; r < M; ++r)
+      for (int q = 0; q < M; ++q) {
+        double v = 0.0;
+        for (int i = 0; i < nup; ++i) v += qh[(size_t)r * M + i] * qh[(size_t)q * M + i];
+        Pt[(size_t)r * M + q] = s->sf * v;
+      }
+  }
   AFQ_CUDA(cudaMemcpyAsync(b.Qb, qh.data(), sizeof(double) * M * M, cudaMemcpyHostToDevice, st));
   AFQ_CUDA(cudaMemcpyAsync(b.QTb, qt.data(), sizeof(double) * M * M, cudaMemcpyHostToDevice, st));
   AFQ_CUDA(cudaMemcpyAsync(b.VTt, vtt.data(), sizeof(double) * N * M, cudaMemcpyHostToDevice, st));
   AFQ_CUDA(cudaMemcpyAsync(b.X, h1, sizeof(double) * M * M, cudaMemcpyHostToDevice, st));
   AFQ_CUDA(cudaMemcpyAsync(b.Lfull, L, sizeof(double) * G * M * M, cudaMemcpyHostToDevice, st));
+  {
+    // the Cholesky vectors must be finite: one pass on the device (a scan on
+    // the host would cost more than the rest of the set-up)
+    auto* first = reinterpret_cast<unsigned long long*>(b.red + 4);
+    AFQ_CUDA(cudaMemsetAsync(first, 0xff, sizeof(unsigned long long), st));
+    AFQ_TRY(launch_first_nonfinite(b.Lfull, (long)G * M * M, first, st));
+    unsigned long long bad = 0;
+    AFQ_CUDA(cudaMemcpyAsync(&bad, first, sizeof(bad), cudaMemcpyDeviceToHost, st));
+    AFQ_CUDA(cudaStreamSynchronize(st));
+    if (bad != ~0ull) {
+      set_error("L[%llu] is not finite", bad);
+      return AFQMC_ENONFINITE;
+    }
+  }
   AFQ_CUDA(cudaMemsetAsync(b.counters, 0, 8 * sizeof(unsigned long long), st));
   // h' = Q^T h Q and L'_g = Q^T L_g Q (h, L_g symmetric: B = h reads h^T)
   AFQ_TRY(gemm_sq(b.QTb, 0, b.X, 0, b.E0, 0, M, 1, st));
   AFQ_TRY(gemm_sq(b.E0, 0, b.QTb, 0, b.h1, 0, M, 1, st));
-  // Single-determinant mixed path: the rotated L'_g only feed the BF16/TF32
-  // operands and B_half (applied as BF16/TF32 high and low parts), so they are
-  // rotated with FP32 products; the half-rotated vectors Lh_g (force bias and
-  // c_g in float64) are formed in float64 from the caller's basis first,
-  // Lh_g = V_T'^T Q^T L_g Q = ((Q V_T')^T L_g) Q.
-  const bool f32_rot = b.mixed && !md;
+  // Single-determinant mixed path (closed shell): the rotated L'_g only feed
+  // the BF16/TF32 operands, Lh_lo and B_half (applied as BF16/TF32 high and
+  // low parts), so they are rotated in FP32.  What stays float64 is taken in
+  // the caller's basis first: c_g = Tr(L_g P) (the mean field, H0') and
+  // sum_g c_g L_g, rotated as one M x M matrix.
+  const bool f32_rot = !Pt.empty();
+  const long nL = (long)G * M * M, cL = (long)b.ych * M * M;  // chunk: Ych's doubles
+  float* Lf = reinterpret_cast<float*>(b.Lfull);
   if (f32_rot) {
-    AFQ_CUDA(cudaMemcpyAsync(b.E1, vto.data(), sizeof(double) * N * M, cudaMemcpyHostToDevice, st));
-    const int cz = (int)std::max<long>(1, (long)b.ych * M / N);  // vectors per chunk of Ych
-    for (int g0 = 0; g0 < G; g0 += cz) {
-      const int nb = G - g0 < cz ? G - g0 : cz;
-      GemmF64 z;  // Z_g = (Q V_T')^T L_g, N x M per vector
-      z.m = N;
-      z.n = z.k = M;
-      z.batch = nb;
-      z.A = b.E1;
-      z.lda = M;
-      z.B = b.Lfull + (size_t)g0 * M * M;
-      z.ldb = M;
-      z.sBb = (long)M * M;
-      z.C = b.Ych;
-      z.ldc = M;
-      z.sCb = (long)N * M;
-      AFQ_TRY(gemm_nt_f64(z, st));
-      GemmF64 l;  // Lh_g = Z_g Q for the chunk's nb N rows at once
-      l.m = nb * N;
-      l.n = l.k = M;
-      l.A = b.Ych;
-      l.lda = M;
-      l.B = b.QTb;
-      l.ldb = M;
-      l.C = b.Lh + (size_t)g0 * N * M;
-      l.ldc = M;
-      AFQ_TRY(gemm_nt_f64(l, st));
-    }
-    // Q^T in FP32 (E0 is free once h' is formed)
+    AFQ_CUDA(cudaMemcpyAsync(b.E1, Pt.data(), sizeof(double) * M * M, cudaMemcpyHostToDevice, st));
+    AFQ_TRY(launch_rowdot(b.Lfull, b.E1, b.c, G, M * M, 1.0, st));
+    const int nz = (int)std::min<long>(b.ych, G);
+    AFQ_TRY(launch_wsum_rows(b.Lfull, b.c, G, (long)M * M, nz, b.Ych, st));
+    AFQ_TRY(launch_sum_parts(b.Ych, nz, (long)M * M, b.X, st));  // sum_g c_g L_g
+    AFQ_TRY(gemm_sq(b.QTb, 0, b.X, 0, b.E0, 0, M, 1, st));
+    AFQ_TRY(gemm_sq(b.E0, 0, b.QTb, 0, b.E1, 0, M, 1, st));
+    AFQ_TRY(launch_pack_transpose(b.E1, b.cLp, 1, M, st));  // packed, as v0p reads it
+    // L and Q^T to FP32 (L in place: the FP32 array starts at Lfull)
+    AFQ_TRY(launch_round_f32_inplace(b.Lfull, nL, cL, reinterpret_cast<float*>(b.Ych), st));
     AFQ_TRY(launch_round_f32(b.QTb, reinterpret_cast<float*>(b.E0), (long)M * M, st));
   }
   for (int g0 = 0; g0 < G; g0 += b.ych) {
     const int nb = G - g0 < b.ych ? G - g0 : b.ych;
-    double* Lg = b.Lfull + (size_t)g0 * M * M;
     if (f32_rot) {
       float* Y = reinterpret_cast<float*>(b.Ych);
-      GemmNT<double, double, float> y;  // Q^T L_g
+      const float* QTf = reinterpret_cast<const float*>(b.E0);
+      float* Lg = Lf + (size_t)g0 * M * M;
+      GemmNT<float, float, float> y;  // Q^T L_g
       y.m = y.n = y.k = M;
       y.batch = nb;
-      y.A = b.QTb;
+      y.A = QTf;
       y.lda = M;
       y.B = Lg;
       y.ldb = M;
@@ -1025,26 +1026,22 @@ static int setup_device(afqmc_state* s, const double* h1, const double* L, const
       y.C = Y;
       y.ldc = M;
       y.sCb = (long)M * M;
-      AFQ_TRY(gemm_nt_ddf(y, st));
-      GemmNT<float, float, double> r;  // (Q^T L_g) Q
-      r.m = r.n = r.k = M;
-      r.batch = nb;
+      AFQ_TRY(gemm_nt_fff(y, st));
+      GemmNT<float, float, float> r = y;  // (Q^T L_g) Q, back into L_g's place
       r.A = Y;
-      r.lda = M;
       r.sAb = (long)M * M;
-      r.B = reinterpret_cast<const float*>(b.E0);
-      r.ldb = M;
+      r.B = QTf;
+      r.sBb = 0;
       r.C = Lg;
-      r.ldc = M;
-      r.sCb = (long)M * M;
-      AFQ_TRY(gemm_nt_ffd(r, st));
+      AFQ_TRY(gemm_nt_fff(r, st));
     } else {
+      double* Lg = b.Lfull + (size_t)g0 * M * M;
       AFQ_TRY(gemm_sq(b.QTb, 0, Lg, (long)M * M, b.Ych, (long)M * M, M, nb, st));
       AFQ_TRY(gemm_sq(b.Ych, (long)M * M, b.QTb, 0, Lg, (long)M * M, M, nb, st));
     }
   }
-  // packed, transposed Cholesky vectors for the V contraction
-  AFQ_TRY(launch_pack_transpose(b.Lfull, b.LpT, G, M, st));
+  // packed, transposed Cholesky vectors for the float64 V contraction
+  if (!f32_rot) AFQ_TRY(launch_pack_transpose(b.Lfull, b.LpT, G, M, st));
   // half-rotated vectors Lh_g = V_T^T L_g and hh = V_T^T h (Eq. precomputing2)
   {
     GemmF64 g;
@@ -1060,7 +1057,10 @@ static int setup_device(afqmc_state* s, const double* h1, const double* L, const
     g.C = b.Lh;
     g.ldc = M;
     g.sCb = (long)N * M;
-    if (!f32_rot) AFQ_TRY(gemm_nt_f64(g, st));
+    if (f32_rot)  // V_T' = [I_N; 0]: the first N rows of each L'_g
+      AFQ_TRY(launch_widen_rows(Lf, (long)M * M, (long)N * M, G, b.Lh, st));
+    else
+      AFQ_TRY(gemm_nt_f64(g, st));
     GemmF64 h;
     h.m = N;
     h.n = M;
@@ -1078,7 +1078,7 @@ static int setup_device(afqmc_state* s, const double* h1, const double* L, const
   // the leading determinant's Tr(L_g (P_0u + P_0d))
   if (md)
     AFQ_TRY(md_setup(s, md_coef));
-  else
+  else if (!f32_rot)
     AFQ_TRY(launch_rowdot(b.Lh, b.VTt, b.c, G, N * M, s->sf, st));
   // sum_g L_g L_g: one M x M output with K = G M would occupy a few dozen
   // CTAs, so the vectors go in ych - 1 equal chunks plus the remainder, each
@@ -1101,9 +1101,19 @@ static int setup_device(afqmc_state* s, const double* h1, const double* L, const
     g.C = b.Ych;
     g.ldc = M;
     g.sCb = (long)M * M;
-    // (mixed path: FP32 products, summed in float64 across 16-term blocks)
-    auto run = f32_rot ? gemm_nt_f32_split : gemm_nt_f64;
-    if (chunk > 0) AFQ_TRY(run(g, st));
+    // (mixed path: the FP32 L', FP32 products summed in float64 across 16-term blocks)
+    GemmNT<float, float, double> gf;
+    gf.m = gf.n = gf.k = M;
+    gf.kb = chunk;
+    gf.batch = np;
+    gf.A = gf.B = Lf;
+    gf.lda = gf.ldb = M;
+    gf.sAk = gf.sBk = (long)M * M;
+    gf.sAb = gf.sBb = (long)chunk * M * M;
+    gf.C = b.Ych;
+    gf.ldc = M;
+    gf.sCb = (long)M * M;
+    if (chunk > 0) AFQ_TRY(f32_rot ? gemm_nt_ffd_split(gf, st) : gemm_nt_f64(g, st));
     if (rem > 0) {
       GemmF64 r = g;
       r.kb = rem;
@@ -1111,25 +1121,19 @@ static int setup_device(afqmc_state* s, const double* h1, const double* L, const
       r.A = b.Lfull + (size_t)np * chunk * M * M;
       r.B = r.A;
       r.C = b.Ych + (size_t)np * M * M;
-      AFQ_TRY(run(r, st));
+      GemmNT<float, float, double> rf = gf;
+      rf.kb = rem;
+      rf.batch = 1;
+      rf.A = rf.B = Lf + (size_t)np * chunk * M * M;
+      rf.C = r.C;
+      AFQ_TRY(f32_rot ? gemm_nt_ffd_split(rf, st) : gemm_nt_f64(r, st));
     }
     AFQ_TRY(launch_sum_parts(chunk > 0 ? b.Ych : b.Ych + (size_t)np * M * M,
                              (chunk > 0 ? np : 0) + (rem > 0 ? 1 : 0), (long)M * M, b.L2, st));
   }
-  // sum_g c_g L_g (packed)
-  {
-    GemmF64 g;
-    g.m = 1;
-    g.n = b.P;
-    g.k = G;
-    g.A = b.c;
-    g.lda = G;
-    g.B = b.LpT;
-    g.ldb = G;
-    g.C = b.cLp;
-    g.ldc = b.P;
-    AFQ_TRY(gemm_nt_f64(g, st));
-  }
+  // sum_g c_g L_g (packed: one dot over g per pair p <= q; the mixed path
+  // formed it above)
+  if (!f32_rot) AFQ_TRY(launch_rowdot(b.LpT, b.c, b.cLp, b.P, G, 1.0, st));
   AFQ_TRY(launch_v0p(b.h1, b.L2, b.cLp, b.X, M, -0.5 * p.dt, st));
   AFQ_TRY(launch_sumsq(b.c, b.red + 1, G, st));
   double sumc2 = 0.0;
@@ -1138,7 +1142,10 @@ static int setup_device(afqmc_state* s, const double* h1, const double* L, const
   s->H0p = p.H0 - 0.5 * sumc2;
   if (b.mixed) {
     // BF16 / TF32 copies of the contraction operands (zero-padded pitches)
-    AFQ_TRY(launch_pack_blocks_lo(b.Lfull, G, M, b.Mp, b.Gp, b.LbT_lo, b.lo_kind, st));
+    if (f32_rot)
+      AFQ_TRY(launch_pack_blocks_lo(Lf, G, M, b.Mp, b.Gp, b.LbT_lo, b.lo_kind, st));
+    else
+      AFQ_TRY(launch_pack_blocks_lo(b.Lfull, G, M, b.Mp, b.Gp, b.LbT_lo, b.lo_kind, st));
     AFQ_TRY(launch_convert_lo(b.Lh, (long)G * N, M, M, b.Lh_lo, b.Mp, b.lo_kind, st));
     AFQ_CUDA(cudaMemsetAsync(b.th_lo, 0, (size_t)W * 2 * N * b.Mp * b.lo_bytes, st));
     AFQ_CUDA(cudaMemsetAsync(b.x_lo, 0, (size_t)W * 2 * b.Gp * b.lo_bytes, st));
@@ -1267,7 +1274,7 @@ static int init_state(const afqmc_params* p, const double* h1, const double* L,
     set_error("workspace %zu bytes < %zu needed", ws_bytes, need);
     return AFQMC_ENOSPC;
   }
-  const size_t M = p->M, N = p->N, G = p->nchol;
+  const size_t M = p->M, N = p->N;
   const size_t nd = p->ndet > 0 ? p->ndet : 0;
   AFQ_TRY(all_finite(h1, M * M, "h1"));
   if (nd) {
@@ -1278,7 +1285,7 @@ static int init_state(const afqmc_params* p, const double* h1, const double* L,
     AFQ_TRY(all_finite(trial, M * N, "trial_up"));
     if (p->Ndn > 0) AFQ_TRY(all_finite(trial_dn, M * (size_t)p->Ndn, "trial_dn"));
   }
-  AFQ_TRY(all_finite(L, G * M * M, "L"));
+  // L (G M^2 values) is checked on the device after its upload (setup_device)
   afqmc_state* s = new (std::nothrow) afqmc_state();
   if (!s) {
     set_error("out of host memory");

@@ -127,6 +127,12 @@ int gemm_nt_ffd(const GemmNT<float, float, double>& g, cudaStream_t st) {
 int gemm_nt_ddf(const GemmNT<double, double, float>& g, cudaStream_t st) {
   return launch_gemm<double, double, float, float>(g, st);
 }
+int gemm_nt_fff(const GemmNT<float, float, float>& g, cudaStream_t st) {
+  return launch_gemm<float, float, float, float>(g, st);
+}
+int gemm_nt_ffd_split(const GemmNT<float, float, double>& g, cudaStream_t st) {
+  return launch_gemm<float, float, double, float, true>(g, st);
+}
 int gemm_nt_f32_split(const GemmF64& g, cudaStream_t st) {
   return launch_gemm<double, double, double, float, true>(g, st);
 }

@@ -88,11 +88,25 @@ int gemm_nt_f64(const GemmF64& g, cudaStream_t st);
 int gemm_nt_dff(const GemmNT<double, float, float>& g, cudaStream_t st);
 int gemm_nt_ffd(const GemmNT<float, float, double>& g, cudaStream_t st);
 int gemm_nt_ddf(const GemmNT<double, double, float>& g, cudaStream_t st);
+int gemm_nt_fff(const GemmNT<float, float, float>& g, cudaStream_t st);
+// FP32 operands and products, summed in FP32 over each 16-term block of K and
+// in float64 across the blocks
+int gemm_nt_ffd_split(const GemmNT<float, float, double>& g, cudaStream_t st);
 // float64 operands, FP32 products summed in FP32 over each 16-term block of K
 // and in float64 across the blocks
 int gemm_nt_f32_split(const GemmF64& g, cudaStream_t st);
 // float64 -> FP32, round to nearest even
 int launch_round_f32(const double* src, float* dst, long n, cudaStream_t st);
+// float64 array rounded to FP32 in place, in chunks of c values (tmp: c floats)
+int launch_round_f32_inplace(double* buf, long n, long c, float* tmp, cudaStream_t st);
+// part[z][i] = sum over the z-th of nz chunks of rows g of c[g] A[g][i]
+int launch_wsum_rows(const double* A, const double* c, int G, long n, int nz, double* part,
+                     cudaStream_t st);
+// dst[g][0 .. len) = src[g * sstride + 0 .. len), FP32 -> float64
+int launch_widen_rows(const float* src, long sstride, long len, int G, double* dst,
+                      cudaStream_t st);
+// smallest index of a non-finite value into *first (which the caller sets to ~0)
+int launch_first_nonfinite(const double* v, long n, unsigned long long* first, cudaStream_t st);
 
 // ---- step kernels (float64) -------------------------------------------------
 struct FieldArgs {
@@ -254,6 +268,8 @@ int launch_split_lo(const double* src, long rows, long cols, long lds, void* dst
 int launch_convert_f32(const double* src, float* dst, long n, cudaStream_t st);
 // full Cholesky vectors transposed, rows (p, q) = p * Mp + q, pitch Gp, low precision
 int launch_pack_blocks_lo(const double* L, int G, int M, int Mp, int Gp, void* out, int kind,
+                          cudaStream_t st);
+int launch_pack_blocks_lo(const float* L, int G, int M, int Mp, int Gp, void* out, int kind,
                           cudaStream_t st);
 
 }  // namespace afq

@@ -1472,9 +1472,78 @@ __global__ void k_widen_f32(const float* src, double* dst, long n) {
     dst[i] = f32_to_f64(src[i]);
 }
 
+// Smallest index i with v[i] not finite (NaN or +-inf) into *first (left
+// unchanged when every value is finite): exponent bits all ones.
+__global__ void k_first_nonfinite(const double* v, long n, unsigned long long* first) {
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long)gridDim.x * blockDim.x)
+    if ((__double2hiint(v[i]) & 0x7ff00000) == 0x7ff00000) atomicMin(first, (unsigned long long)i);
+}
+
+int launch_first_nonfinite(const double* v, long n, unsigned long long* first, cudaStream_t st) {
+  if (n <= 0) return AFQMC_OK;
+  AFQ_LAUNCH(k_first_nonfinite, 152 * 8, 256, 0, st, v, n, first);
+  return AFQMC_OK;
+}
+
+// part[z][i] = sum_{g in chunk z} c[g] A[g][i] over nz equal chunks of the
+// G rows (float64; the partials are then added in order by launch_sum_parts).
+__global__ void k_wsum_rows(const double* A, const double* c, int G, long n, int nz,
+                            double* part) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int z = blockIdx.y, per = (G + nz - 1) / nz, g0 = z * per, g1 = min(G, g0 + per);
+  double s = 0.0;
+  for (int g = g0; g < g1; ++g) s += c[g] * A[(long)g * n + i];
+  part[(long)z * n + i] = s;
+}
+
+int launch_wsum_rows(const double* A, const double* c, int G, long n, int nz, double* part,
+                     cudaStream_t st) {
+  if (n <= 0 || nz < 1) return AFQMC_OK;
+  dim3 grid((unsigned)cdiv(n, 256), nz);
+  AFQ_LAUNCH(k_wsum_rows, grid, 256, 0, st, A, c, G, n, nz, part);
+  return AFQMC_OK;
+}
+
+// dst[g][j] = src[g * sstride + j] (FP32 -> float64, exact) for j < len.
+__global__ void k_widen_rows(const float* src, long sstride, long len, int G, double* dst) {
+  const long j = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= len) return;
+  const int g = blockIdx.y;
+  dst[(long)g * len + j] = f32_to_f64(src[(long)g * sstride + j]);
+}
+
+int launch_widen_rows(const float* src, long sstride, long len, int G, double* dst,
+                      cudaStream_t st) {
+  if (len <= 0 || G <= 0) return AFQMC_OK;
+  dim3 grid((unsigned)cdiv(len, 256), G);
+  AFQ_LAUNCH(k_widen_rows, grid, 256, 0, st, src, sstride, len, G, dst);
+  return AFQMC_OK;
+}
+
 int launch_round_f32(const double* src, float* dst, long n, cudaStream_t st) {
   if (n <= 0) return AFQMC_OK;
   AFQ_LAUNCH(k_round_f32, 152 * 8, 256, 0, st, src, dst, n);
+  return AFQMC_OK;
+}
+
+// n float64 values at buf rounded to FP32 in place (the FP32 array then starts
+// at buf).  Chunk k >= 1 of c values reads bytes [8kc, 8(k+1)c) and writes
+// [4kc, 4(k+1)c): disjoint, and below the chunks still to be read.  Chunk 0
+// goes through tmp (room for c floats) and is copied to the front last.
+int launch_round_f32_inplace(double* buf, long n, long c, float* tmp, cudaStream_t st) {
+  if (n <= 0) return AFQMC_OK;
+  if (c < 1) {
+    set_error("round_f32_inplace: chunk %ld", c);
+    return AFQMC_EINVAL;
+  }
+  float* out = reinterpret_cast<float*>(buf);
+  const long c0 = n < c ? n : c;
+  AFQ_TRY(launch_round_f32(buf, tmp, c0, st));
+  for (long k0 = c; k0 < n; k0 += c)
+    AFQ_TRY(launch_round_f32(buf + k0, out + k0, (n - k0 < c ? n - k0 : c), st));
+  AFQ_CUDA(cudaMemcpyAsync(out, tmp, sizeof(float) * c0, cudaMemcpyDeviceToDevice, st));
   return AFQMC_OK;
 }
 
@@ -1497,7 +1566,8 @@ __global__ void k_convert_f32(const double* src, float* dst, long n) {
 // P <= Q, of each Mp x Mp vector L[g] (zero beyond M), row-major over the
 // blocks; row blk * 256 + pp * 16 + qq of out holds L[g][16 P + pp][16 Q + qq]
 // for g < Gp (zero for g >= G).  Block (x, y): 32 vectors, one (blk, pp) row.
-__global__ void k_pack_blocks_lo(const double* L, int G, int M, int Mp, int Gp, void* out,
+template <typename T>
+__global__ void k_pack_blocks_lo(const T* L, int G, int M, int Mp, int Gp, void* out,
                                  int kind) {
   __shared__ double tile[32][17];
   const int g0 = blockIdx.x * 32;
@@ -1513,7 +1583,7 @@ __global__ void k_pack_blocks_lo(const double* L, int G, int M, int Mp, int Gp, 
   for (int e = threadIdx.x; e < 32 * 16; e += blockDim.x) {
     const int r = e >> 4, c = e & 15;
     const int g = g0 + r, q = q0 + c;
-    tile[r][c] = (g < G && p < M && q < M) ? L[((long)g * M + p) * M + q] : 0.0;
+    tile[r][c] = (g < G && p < M && q < M) ? (double)L[((long)g * M + p) * M + q] : 0.0;
   }
   __syncthreads();
   const long n0 = (long)blk * 256 + pp * 16;
@@ -1523,12 +1593,23 @@ __global__ void k_pack_blocks_lo(const double* L, int G, int M, int Mp, int Gp, 
   }
 }
 
-int launch_pack_blocks_lo(const double* L, int G, int M, int Mp, int Gp, void* out, int kind,
+template <typename T>
+static int pack_blocks_lo(const T* L, int G, int M, int Mp, int Gp, void* out, int kind,
                           cudaStream_t st) {
   const int nb = Mp / 16;
   dim3 grid(cdiv(Gp, 32), nb * (nb + 1) / 2 * 16);
-  AFQ_LAUNCH(k_pack_blocks_lo, grid, 256, 0, st, L, G, M, Mp, Gp, out, kind);
+  AFQ_LAUNCH(k_pack_blocks_lo<T>, grid, 256, 0, st, L, G, M, Mp, Gp, out, kind);
   return AFQMC_OK;
+}
+
+int launch_pack_blocks_lo(const double* L, int G, int M, int Mp, int Gp, void* out, int kind,
+                          cudaStream_t st) {
+  return pack_blocks_lo(L, G, M, Mp, Gp, out, kind, st);
+}
+
+int launch_pack_blocks_lo(const float* L, int G, int M, int Mp, int Gp, void* out, int kind,
+                          cudaStream_t st) {
+  return pack_blocks_lo(L, G, M, Mp, Gp, out, kind, st);
 }
 
 int launch_convert_f32(const double* src, float* dst, long n, cudaStream_t st) {

@@ -3,8 +3,10 @@
 Device side: a bounded wait on a flag that nothing sets gives up, writes
 AFQMC_ETIMEOUT to a status word and returns; the context stays usable.
 Host side: non-finite inputs, a short workspace and bad parameters are
-rejected before anything is launched; walkers whose weights overflow are
-zeroed and counted, never propagated as NaN into the estimator.
+rejected before the state is created (the Cholesky vectors by one pass on
+the device after their upload, the smaller inputs on the host); walkers
+whose weights overflow are zeroed and counted, never propagated as NaN into
+the estimator.
 """
 import ctypes
 import math
@@ -68,3 +70,27 @@ def test_overflowing_weights_are_zeroed_and_counted(env):
     log = run.energy_log()
     live = log[:, 3] > 0
     assert np.all(np.isfinite(log[live, 1]))
+
+
+@pytest.mark.parametrize("where", ["L", "h1"])
+def test_nonfinite_inputs_are_rejected_with_their_index(env, where):
+    torch, pkg = env
+    w = workloads.config("c0")
+    h1, L, _ = w.hamiltonian()
+    C = np.linalg.eigh(h1)[1][:, :w.N]
+    p = pkg.default_params(w.M, w.N, w.nchol, w.nwalkers)
+    for value in (np.nan, np.inf, -np.inf):
+        h, l = h1.copy(), L.copy()
+        if where == "L":
+            idx = (w.nchol - 3) * w.M * w.M + 5 * w.M + 7  # a late vector
+            l.reshape(-1)[idx] = value
+            l.reshape(-1)[idx + 11] = value  # the first bad index is named
+        else:
+            idx = 2 * w.M + 1
+            h.reshape(-1)[idx] = value
+        with pytest.raises(pkg.AfqmcError, match=rf"{where}\[{idx}\] is not finite"):
+            pkg.AfqmcRun(h, l, C, p)
+    # the device is usable afterwards, and the clean inputs set up
+    run = pkg.AfqmcRun(h1, L, C, p)
+    assert run.info().status == 0
+    run.close()
