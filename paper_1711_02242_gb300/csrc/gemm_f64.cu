@@ -19,11 +19,12 @@
 namespace afq {
 
 namespace {
-constexpr int BM = 64, BN = 64, BK = 16, TPB = 256;
+constexpr int BM = 64, BN = 64, BK = 16, TPB = 256, kSplitRun = 16;
 
-// SPLIT (FP32 ACC): the products of each BK-term block of K are summed in
-// FP32 and the block sums in float64, so the rounding error no longer grows
-// with K (used for sums over all Cholesky vectors, K = G M).
+// SPLIT (FP32 ACC): the products of each run of kSplitRun BK-term blocks of K
+// (256 terms) are summed in FP32 and the run sums in float64, so the rounding
+// error no longer grows with K (sums over all Cholesky vectors, K = G M); the
+// float64 adds, on GB300's slow float64 pipe, stay a small part of the work.
 template <typename TA, typename TB, typename TC, typename ACC, bool SPLIT = false>
 __global__ void __launch_bounds__(TPB) k_gemm_nt(GemmNT<TA, TB, TC> g) {
   __shared__ ACC As[BK][BM + 1];
@@ -41,6 +42,12 @@ __global__ void __launch_bounds__(TPB) k_gemm_nt(GemmNT<TA, TB, TC> g) {
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = SUM(0);
 
+  ACC blk[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) blk[i][j] = ACC(0);
+  int run = 0;  // BK blocks summed in blk since the last float64 add (SPLIT)
   for (int b = 0; b < g.kb; ++b) {
     const TA* Ab = A + (long)b * g.sAk;
     const TB* Bb = B + (long)b * g.sBk;
@@ -55,11 +62,12 @@ __global__ void __launch_bounds__(TPB) k_gemm_nt(GemmNT<TA, TB, TC> g) {
         Bs[col][row] = (gn < g.n && gk < g.k) ? ACC(Bb[(long)gn * g.ldb + gk]) : ACC(0);
       }
       __syncthreads();
-      ACC blk[4][4];
+      if (!SPLIT) {
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+        for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) blk[i][j] = SPLIT ? ACC(0) : ACC(acc[i][j]);
+          for (int j = 0; j < 4; ++j) blk[i][j] = ACC(acc[i][j]);
+      }
 #pragma unroll
       for (int kk = 0; kk < BK; ++kk) {
         ACC a[4], bv[4];
@@ -72,12 +80,29 @@ __global__ void __launch_bounds__(TPB) k_gemm_nt(GemmNT<TA, TB, TC> g) {
 #pragma unroll
           for (int j = 0; j < 4; ++j) blk[i][j] = fma(a[i], bv[j], blk[i][j]);
       }
+      if (!SPLIT) {
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+        for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = SPLIT ? acc[i][j] + SUM(blk[i][j]) : SUM(blk[i][j]);
+          for (int j = 0; j < 4; ++j) acc[i][j] = SUM(blk[i][j]);
+      } else if (++run == kSplitRun) {
+        run = 0;
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            acc[i][j] += SUM(blk[i][j]);
+            blk[i][j] = ACC(0);
+          }
+      }
       __syncthreads();
     }
+  }
+  if (SPLIT && run > 0) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] += SUM(blk[i][j]);
   }
 #pragma unroll
   for (int i = 0; i < 4; ++i) {

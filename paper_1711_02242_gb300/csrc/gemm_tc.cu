@@ -311,10 +311,10 @@ struct EpiStore {
 // CW walkers x NPAD rows (the 2N rows of a walker, zero-padded to a power of
 // two), so walker wl of the tile owns accumulator columns [wl NPAD, wl NPAD +
 // 2N).  The accumulator is copied to this epilogue's own shared memory; the
-// thread of row (g, i) then forms e_i = sum_j T_ij T_ji (complex) from its own
-// row and column i of the block, the N values of a vector are summed, and
-// part[w][g][2] receives one partial per (g, w) (nchunk = G), summed later in
-// a fixed order.  T never reaches global memory.
+// thread of row (g, i) then forms its share of sum_ij T_ij T_ji (complex) from
+// its own row and column i of the block, the N shares of a vector are summed,
+// and part[w][g][2] receives one partial per (g, w) (nchunk = G), summed later
+// in a fixed order.  T never reaches global memory.
 struct EpiExchange {
   static constexpr int kSmemBytes = 128 * 257 * 4;  // one 128 x 256 FP32 tile
   static constexpr bool kB3D = true;
@@ -331,29 +331,55 @@ struct EpiExchange {
                                       int, int, int, float* sm) const {
     constexpr int LD = BN + 1;  // odd pitch: row and column walks are conflict-free
     const int r = 32 * q + lane, half = ew >> 2;
+    const uint32_t tq = tmem + ((uint32_t)(32 * q) << 16);
+    // the two warps of a lane quarter take alternate 16-column chunks, two
+    // TMEM loads in flight per wait
 #pragma unroll 1
-    for (int c0 = 16 * half; c0 < BN; c0 += 32) {
-      float v[16];
-      tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c0, v);
+    for (int c0 = 16 * half; c0 < BN; c0 += 64) {
+      uint32_t ra[16], rb[16];
+      tmem_ld16_async(tq + (uint32_t)c0, ra);
+      if (c0 + 32 < BN) tmem_ld16_async(tq + (uint32_t)(c0 + 32), rb);
+      tmem_ld_wait();
 #pragma unroll
-      for (int i = 0; i < 16; ++i) sm[r * LD + c0 + i] = v[i];
+      for (int i = 0; i < 16; ++i) sm[r * LD + c0 + i] = __uint_as_float(ra[i]);
+      if (c0 + 32 < BN) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) sm[r * LD + c0 + 32 + i] = __uint_as_float(rb[i]);
+      }
     }
     asm volatile("bar.sync 1, 256;" ::: "memory");
     const int gl = r / N, i = r - gl * N;
     const bool rv = gl < RG;
-    // FP32 sums (the products come from FP32 accumulators; GB300's float64
-    // pipe is ~60x slower than FP32 and would dominate the kernel); the two
-    // warps of a row take alternate walkers
+    // sum_ij T_ij T_ji of a vector only enters summed over i, so each unordered
+    // pair {i, j} is taken once, by the thread of row i with j = i + d (mod N),
+    // d = 1 .. (N - 1) / 2, at twice its weight (for even N the pairs d = N / 2
+    // are met from both ends, once each); plus T_ii^2.  FP32 sums (the products
+    // come from FP32 accumulators; GB300's float64 pipe is ~60x slower than
+    // FP32 and would dominate the kernel); the two warps of a row take
+    // alternate walkers.
+    const int nd = (N - 1) / 2;
     float e[kMaxCW];
 #pragma unroll
     for (int h = 0; h < kMaxCW / 2; ++h) {
       const int wl = 2 * h + half;
       float er = 0.f, ei = 0.f;
       if (wl < CW && rv) {
-        const float* own = sm + r * LD + wl * NPAD;            // T_ij: [j], [N + j]
+        const float* own = sm + r * LD + wl * NPAD;             // T_ij: [j], [N + j]
         const float* col = sm + (gl * N) * LD + wl * NPAD + i;  // T_ji: [j LD], [j LD + N]
+        const float dr = own[i], di = own[N + i];
+        float pr = 0.f, pi = 0.f;
 #pragma unroll 4
-        for (int j = 0; j < N; ++j) {
+        for (int d = 1; d <= nd; ++d) {
+          const int j = i + d < N ? i + d : i + d - N;
+          const float ar = own[j], ai = own[N + j];
+          const float br = col[j * LD], bi = col[j * LD + N];
+          pr = fmaf(ar, br, fmaf(-ai, bi, pr));
+          pi = fmaf(ar, bi, fmaf(ai, br, pi));
+        }
+        er = fmaf(dr, dr, fmaf(-di, di, 2.f * pr));
+        ei = fmaf(2.f * dr, di, 2.f * pi);
+        if ((N & 1) == 0) {
+          const int j = i + N / 2 < N ? i + N / 2 : i - N / 2;
           const float ar = own[j], ai = own[N + j];
           const float br = col[j * LD], bi = col[j * LD + N];
           er = fmaf(ar, br, fmaf(-ai, bi, er));
@@ -373,18 +399,23 @@ struct EpiExchange {
       }
     }
     asm volatile("bar.sync 1, 256;" ::: "memory");
+    // one thread per (vector, walker, re/im): the N rows' shares added in
+    // four interleaved partial sums, combined in a fixed order
     const int g0 = bx * RG, w0 = by * CW;
-    for (int item = r + 128 * half; item < RG * CW; item += 256) {
-      const int g = item / CW, wl = item - g * CW;
+    for (int item = r + 128 * half; item < 2 * RG * CW; item += 256) {
+      const int c = item & 1, gw = item >> 1, g = gw / CW, wl = gw - g * CW;
       if (g0 + g >= G || w0 + wl >= W) continue;
-      float sr = 0.f, si = 0.f;
-      for (int i2 = 0; i2 < N; ++i2) {
-        sr += sm[(g * N + i2) * LD + 2 * wl];
-        si += sm[(g * N + i2) * LD + 2 * wl + 1];
+      const float* src = sm + (g * N) * LD + 2 * wl + c;
+      float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+      int i2 = 0;
+      for (; i2 + 4 <= N; i2 += 4) {
+        s0 += src[i2 * LD];
+        s1 += src[(i2 + 1) * LD];
+        s2 += src[(i2 + 2) * LD];
+        s3 += src[(i2 + 3) * LD];
       }
-      double* o = part + ((long)(w0 + wl) * nchunk + g0 + g) * 2;
-      o[0] = (double)sr;
-      o[1] = (double)si;
+      for (; i2 < N; ++i2) s0 += src[i2 * LD];
+      part[((long)(w0 + wl) * nchunk + g0 + g) * 2 + c] = (double)((s0 + s1) + (s2 + s3));
     }
     // the next tile's copy into sm must wait until every warp is done reading
     asm volatile("bar.sync 1, 256;" ::: "memory");
