@@ -19,16 +19,38 @@
 namespace afq {
 
 namespace {
-constexpr int BM = 64, BN = 64, BK = 16, TPB = 256, kSplitRun = 16;
+constexpr int BK = 16, TPB = 256, kSplitRun = 16;
+
+// Four consecutive shared-memory values (16- or 32-byte aligned) in one or two
+// vector loads.
+__device__ __forceinline__ void ld4(const float* p, float* v) {
+  const float4 x = *reinterpret_cast<const float4*>(p);
+  v[0] = x.x;
+  v[1] = x.y;
+  v[2] = x.z;
+  v[3] = x.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double* v) {
+  const double2 x = reinterpret_cast<const double2*>(p)[0], y = reinterpret_cast<const double2*>(p)[1];
+  v[0] = x.x;
+  v[1] = x.y;
+  v[2] = y.x;
+  v[3] = y.y;
+}
 
 // SPLIT (FP32 ACC): the products of each run of kSplitRun BK-term blocks of K
 // (256 terms) are summed in FP32 and the run sums in float64, so the rounding
 // error no longer grows with K (sums over all Cholesky vectors, K = G M); the
 // float64 adds, on GB300's slow float64 pipe, stay a small part of the work.
-template <typename TA, typename TB, typename TC, typename ACC, bool SPLIT = false>
+// TM: rows (and columns) per thread; the tile is 16 TM x 16 TM, thread (tx, ty)
+// owns rows TM ty .. TM ty + TM - 1 and columns TM tx .. (vector loads of its
+// operands from shared memory when TM = 4).  Every output element is summed
+// over k in the same order whatever the tile, so results do not depend on it.
+template <typename TA, typename TB, typename TC, typename ACC, bool SPLIT = false, int TM = 4>
 __global__ void __launch_bounds__(TPB) k_gemm_nt(GemmNT<TA, TB, TC> g) {
-  __shared__ ACC As[BK][BM + 1];
-  __shared__ ACC Bs[BK][BN + 1];
+  constexpr int BM = 16 * TM, BN = 16 * TM, PAD = TM == 4 ? 4 : 1;
+  __shared__ __align__(16) ACC As[BK][BM + PAD];
+  __shared__ __align__(16) ACC Bs[BK][BN + PAD];
   using SUM = typename std::conditional<SPLIT, double, ACC>::type;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
@@ -36,17 +58,17 @@ __global__ void __launch_bounds__(TPB) k_gemm_nt(GemmNT<TA, TB, TC> g) {
   const TA* A = g.A + z * g.sAb;
   const TB* B = g.B + z * g.sBb;
   TC* C = g.C + z * g.sCb;
-  SUM acc[4][4];
+  SUM acc[TM][TM];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < TM; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = SUM(0);
+    for (int j = 0; j < TM; ++j) acc[i][j] = SUM(0);
 
-  ACC blk[4][4];
+  ACC blk[TM][TM];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < TM; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) blk[i][j] = ACC(0);
+    for (int j = 0; j < TM; ++j) blk[i][j] = ACC(0);
   int run = 0;  // BK blocks summed in blk since the last float64 add (SPLIT)
   for (int b = 0; b < g.kb; ++b) {
     const TA* Ab = A + (long)b * g.sAk;
@@ -64,33 +86,38 @@ __global__ void __launch_bounds__(TPB) k_gemm_nt(GemmNT<TA, TB, TC> g) {
       __syncthreads();
       if (!SPLIT) {
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+        for (int i = 0; i < TM; ++i)
 #pragma unroll
-          for (int j = 0; j < 4; ++j) blk[i][j] = ACC(acc[i][j]);
+          for (int j = 0; j < TM; ++j) blk[i][j] = ACC(acc[i][j]);
       }
 #pragma unroll
       for (int kk = 0; kk < BK; ++kk) {
-        ACC a[4], bv[4];
+        ACC a[TM], bv[TM];
+        if constexpr (TM == 4) {
+          ld4(&As[kk][TM * ty], a);
+          ld4(&Bs[kk][TM * tx], bv);
+        } else {
 #pragma unroll
-        for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+          for (int i = 0; i < TM; ++i) a[i] = As[kk][TM * ty + i];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx + 16 * j];
+          for (int j = 0; j < TM; ++j) bv[j] = Bs[kk][TM * tx + j];
+        }
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+        for (int i = 0; i < TM; ++i)
 #pragma unroll
-          for (int j = 0; j < 4; ++j) blk[i][j] = fma(a[i], bv[j], blk[i][j]);
+          for (int j = 0; j < TM; ++j) blk[i][j] = fma(a[i], bv[j], blk[i][j]);
       }
       if (!SPLIT) {
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+        for (int i = 0; i < TM; ++i)
 #pragma unroll
-          for (int j = 0; j < 4; ++j) acc[i][j] = SUM(blk[i][j]);
+          for (int j = 0; j < TM; ++j) acc[i][j] = SUM(blk[i][j]);
       } else if (++run == kSplitRun) {
         run = 0;
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+        for (int i = 0; i < TM; ++i)
 #pragma unroll
-          for (int j = 0; j < 4; ++j) {
+          for (int j = 0; j < TM; ++j) {
             acc[i][j] += SUM(blk[i][j]);
             blk[i][j] = ACC(0);
           }
@@ -100,18 +127,18 @@ __global__ void __launch_bounds__(TPB) k_gemm_nt(GemmNT<TA, TB, TC> g) {
   }
   if (SPLIT && run > 0) {
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < TM; ++i)
 #pragma unroll
-      for (int j = 0; j < 4; ++j) acc[i][j] += SUM(blk[i][j]);
+      for (int j = 0; j < TM; ++j) acc[i][j] += SUM(blk[i][j]);
   }
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    int gm = m0 + ty + 16 * i;
+  for (int i = 0; i < TM; ++i) {
+    int gm = m0 + TM * ty + i;
     if (gm >= g.m) continue;
     if (g.mask && !walker_alive(g.mask, gm / g.mask_rows)) continue;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      int gn = n0 + tx + 16 * j;
+    for (int j = 0; j < TM; ++j) {
+      int gn = n0 + TM * tx + j;
       if (gn >= g.n) continue;
       TC* c = C + (long)gm * g.ldc + gn;
       SUM v = SUM(g.alpha) * acc[i][j];
@@ -124,6 +151,7 @@ __global__ void __launch_bounds__(TPB) k_gemm_nt(GemmNT<TA, TB, TC> g) {
 
 template <typename TA, typename TB, typename TC, typename ACC, bool SPLIT = false>
 static int launch_gemm(const GemmNT<TA, TB, TC>& g, cudaStream_t st) {
+  constexpr int BM = 64, BN = 64;
   if (g.m <= 0 || g.n <= 0 || g.batch <= 0) return AFQMC_OK;
   if (g.k < 0 || g.kb < 1) {
     set_error("gemm_nt: bad k=%d kb=%d", g.k, g.kb);
@@ -138,7 +166,16 @@ static int launch_gemm(const GemmNT<TA, TB, TC>& g, cudaStream_t st) {
     set_error("gemm_nt: grid too large (m=%d batch=%d)", g.m, g.batch);
     return AFQMC_EINVAL;
   }
-  AFQ_LAUNCH((k_gemm_nt<TA, TB, TC, ACC, SPLIT>), grid, TPB, 0, st, g);
+  // a product too small to give every SM a 64 x 64 tile (the M x M steps of
+  // the set-up's exp) takes 32 x 32 tiles: four times the CTAs
+  if ((long)grid.x * grid.y * grid.z < 152) {
+    dim3 g2(cdiv(g.n, 32), cdiv(g.m, 32), g.batch);
+    if (g2.y <= 65535u) {
+      AFQ_LAUNCH((k_gemm_nt<TA, TB, TC, ACC, SPLIT, 2>), g2, TPB, 0, st, g);
+      return AFQMC_OK;
+    }
+  }
+  AFQ_LAUNCH((k_gemm_nt<TA, TB, TC, ACC, SPLIT, 4>), grid, TPB, 0, st, g);
   return AFQMC_OK;
 }
 
