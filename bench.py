@@ -80,8 +80,8 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # to another kernel at this precision, is reported as null.
 GEMM_KERNEL = "__device__ __forceinline__ void gemm_body("
 TRAFFIC = {
-    "theta": [# k_theta_rows_f32 on the float64 S^-1 (the bf16 path with N > 32)
-              {"bytes": (66.846720 + 26.307840) * 1e6, "precisions": ("bf16-inverse",),
+    "theta": [# k_theta_rows_f32 on the float64 S^-1 (the bf16 default path)
+              {"bytes": (66.846720 + 26.307840) * 1e6, "precisions": ("bf16",),
                "function": "__global__ void __launch_bounds__(TH_T) k_theta_rows_f32(OverlapArgs a)",
                "sha": "95b521175a189697f17637210e88c7be80b91f899d89ffb387d05b3e718d9736"},
               # k_theta_rows (float64 Theta of the -f64theta mixed paths): its own
@@ -92,7 +92,7 @@ TRAFFIC = {
     # k_overlap<double> and k_mgs (float64, the bf16 default path), pinned to
     # their own text (captures in profiles/overlap_inverse_m300_bf16.md and
     # profiles/mgs_m300_bf16.md)
-    "overlap": {"bytes": (8.244992 + 0.0) * 1e6, "precisions": ("bf16-f64theta",),
+    "overlap": {"bytes": (8.244992 + 0.0) * 1e6, "precisions": ("bf16",),
                 "function": "__global__ void __launch_bounds__(OV_T) k_overlap(OverlapArgs a)",
                 "sha": "5905df615412e8d5881361e99808acd80656d2a0414eef96dd142e0f6e82e0bc"},
     "qr": {"bytes": (61.483264 + 34.291200) * 1e6, "precisions": ("bf16",),
@@ -202,19 +202,12 @@ def job_throughput(walkers_per_rank: int, steps: int, ms_max: float, world: int)
     return world * walkers_per_rank * steps / (ms_max * 1e-3)
 
 
-def lu_path(w: workloads.Workload, precision):
-    """The bf16 / tf32 defaults factor S = P L U in float64 and take S^-1 from
-    the factors in FP32 (N <= 32); the other precisions invert S."""
-    return precision in ("bf16", "tf32") and w.N <= 32
-
-
-def algorithmic_per_walker(w: workloads.Workload, precision="f64"):
+def algorithmic_per_walker(w: workloads.Workload):
     """Algorithmic work of the step's kernels per walker (one spin block; the
     closed-shell walker's two blocks are the same matrix), as used for the
     roofline fractions:
       overlap  FP64: Gauss-Jordan inverse of S, 8 N^3 (in the trial-adapted
-               basis S is the top block of Phi), or its LU factors, 8 N^3 / 3,
-               on the bf16 / tf32 defaults;
+               basis S is the top block of Phi);
       theta    FP64: Theta's M - N non-trivial rows, 8 (M - N) N^2 (the top
                N rows are I);
       qr       FP64: modified Gram-Schmidt, 8 M N^2, every qr_period steps;
@@ -224,8 +217,7 @@ def algorithmic_per_walker(w: workloads.Workload, precision="f64"):
       energy   tensor: force bias 4 N_g N M and exchange 4 N_g N^2 M (the
                T_g = Lh_g Theta products), per evaluation."""
     M, N, G, n = w.M, w.N, w.nchol, w.taylor_order
-    return {"overlap": 8 * N ** 3 // (3 if lu_path(w, precision) else 1),
-            "theta": 8 * (M - N) * N * N, "qr": 8 * M * N * N,
+    return {"overlap": 8 * N ** 3, "theta": 8 * (M - N) * N * N, "qr": 8 * M * N * N,
             "v_assembly": 2 * G * M * (M + 1), "taylor": 8 * n * M * M * N,
             "energy": 4 * G * N * M + 4 * G * N * N * M}
 
@@ -233,14 +225,14 @@ def algorithmic_per_walker(w: workloads.Workload, precision="f64"):
 def bytes_per_walker(w: workloads.Workload, precision):
     """Algorithmic DRAM bytes per walker of the mixed path's FP32 kernels,
     which are bound by memory traffic, not by their FP32 arithmetic:
-      theta  read Phi (2 N M float64) and S^-1 (N^2 complex: FP32 on the bf16 /
-             tf32 defaults and the -f32lu paths, float64 otherwise), write Theta
-             (2 N M float64) and its BF16/TF32 copy (2 N Mp);
+      theta  read Phi (2 N M float64) and S^-1 (N^2 complex: float64, or FP32
+             on the -f32lu paths), write Theta (2 N M float64) and its
+             BF16/TF32 copy (2 N Mp);
       qr     read and write Phi (2 x 2 N M float64), write its BF16/TF32 copy."""
     M, N = w.M, w.N
     Mp = (M + 15) // 16 * 16
     lo = 2 if precision.startswith("bf16") else 4
-    sinv = 8 if precision.endswith("f32lu") or lu_path(w, precision) else 16
+    sinv = 8 if precision.endswith("f32lu") else 16
     return {"theta": 2 * N * M * 8 + N * N * sinv + 2 * N * M * 8 + 2 * N * Mp * lo,
             "qr": 2 * (2 * N * M * 8) + 2 * N * Mp * lo}
 
@@ -255,9 +247,6 @@ def kernel_of_phase(precision):
     k = dict(KERNEL_OF_PHASE)
     if precision in ("bf16", "tf32") or precision.endswith("f32lu"):
         k["theta"] = ("k_theta_rows_f32", "hbm", "walker_f64.cu")
-    if precision in ("bf16", "tf32"):
-        # S = P L U (float64), S^-1 from the factors in FP32 (N <= 32)
-        k["overlap"] = ("k_overlap_lu", "alu", "walker_f64.cu")
     if precision.endswith("f32lu"):
         k["overlap"] = ("k_overlap<float>", "alu32", "walker_f64.cu")
         k["qr"] = ("k_mgs_f32", "hbm", "walker_f64.cu")
@@ -340,7 +329,7 @@ def rooflines(w, phases, precision, K):
     work per launch / device time per launch (CUDA events on the state's
     stream) against the peak of the pipe that bounds it."""
     pk, pk_kind = peaks()
-    per = algorithmic_per_walker(w, precision)
+    per = algorithmic_per_walker(w)
     per_bytes = bytes_per_walker(w, precision)
     out = []
     for ph, (kname, bound, src) in kernel_of_phase(precision).items():

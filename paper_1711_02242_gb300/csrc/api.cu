@@ -313,12 +313,8 @@ int overlap_update(afqmc_state* s, bool into_ld, bool timed) {
     if (b.f32lu) ov.Sinv32 = reinterpret_cast<float2*>(b.Sinv);
     ov.theta32 = b.theta32 ? 1 : 0;
   }
-  // the default mixed precisions: S = P L U in float64 (a third of the
-  // float64 work of the inverse), S^-1 from the factors in FP32
-  const bool lu = b.mixed && b.theta32 && !b.f32lu && ov.unit_trial && p.N <= kLuMaxN;
-  if (lu) ov.Sinv32 = reinterpret_cast<float2*>(b.Sinv);
   if (timed) prof_begin(s, AFQMC_PH_OVERLAP);
-  AFQ_TRY(lu ? launch_overlap_lu(ov, s->st) : launch_overlap(ov, s->st));
+  AFQ_TRY(launch_overlap(ov, s->st));
   if (timed) {
     prof_end(s);
     prof_begin(s, AFQMC_PH_THETA);

@@ -162,11 +162,6 @@ struct OverlapArgs {
 // S^-1 and log det (k_overlap), then Theta (k_theta_rows)
 int launch_overlap(const OverlapArgs& a, cudaStream_t st);
 int launch_theta(const OverlapArgs& a, cudaStream_t st);
-// the mixed path's default for N <= kLuMaxN: float64 LU and log det, S^-1
-// from the factors in FP32 into Sinv32 (k_overlap_lu); Theta from it by
-// launch_theta
-constexpr int kLuMaxN = 32;
-int launch_overlap_lu(const OverlapArgs& a, cudaStream_t st);
 
 struct WeightArgs {
   int W, mode;

@@ -301,12 +301,7 @@ struct Vec2<float> {
 // ([N][N] shared), its inverse in place with the columns in the rows' final
 // order (pos[c] = the column of A holding column c of S^-1), log det stored
 // for live walkers.  Returns true when S is singular (block-uniform).
-// LU: stop at the factorisation P^T S = L U (partial pivoting, L unit lower
-// with its multipliers below the diagonal, U on and above it; pos[c] = the
-// position of row c of S): the same trailing updates as Gauss-Jordan on rows
-// and columns past the pivot only (the pivots and log det come out bitwise
-// the same), a third of its float64 work.
-template <typename T, bool LU = false>
+template <typename T>
 __device__ __forceinline__ bool overlap_core(const OverlapArgs& a, int w, bool live,
                                              typename Vec2<T>::type* A, int* pos) {
   using T2 = typename Vec2<T>::type;
@@ -411,20 +406,6 @@ __device__ __forceinline__ bool overlap_core(const OverlapArgs& a, int w, bool l
     }
     __syncthreads();
     if (singular) break;
-    if (LU) {
-      // a_ij -= (a_ik / p) a_kj for i, j > k, and the multipliers into column k
-      const int n1 = N - 1 - k;
-      for (int idx = threadIdx.x; idx < n1 * n1; idx += blockDim.x) {
-        const int i = k + 1 + idx / n1, j = k + 1 + (idx - (idx / n1) * n1);
-        const T2 f = fac[i], v = A[k * N + j];
-        T2& d = A[i * N + j];
-        d.x = fma(-f.x, v.x, fma(f.y, v.y, d.x));
-        d.y = fma(-f.x, v.y, fma(-f.y, v.x, d.y));
-      }
-      for (int i = k + 1 + threadIdx.x; i < N; i += blockDim.x) A[i * N + k] = fac[i];
-      __syncthreads();
-      continue;
-    }
     // a_ij -= (a_ik / p) a_kj for i, j != k
     const int n1 = N - 1;
     for (int idx = threadIdx.x; idx < n1 * n1; idx += blockDim.x) {
@@ -507,74 +488,6 @@ __global__ void __launch_bounds__(OV_T) k_overlap(OverlapArgs a) {
     const int r = idx / N, c = idx - (idx / N) * N;
     si[idx] = A[r * N + pos[c]];
   }
-}
-
-// The mixed path's default: S = P L U in float64 (the pivots, hence log det,
-// overlap ratios and weights, bitwise as from the inverse), then S^-1 from the
-// factors rounded to FP32, on the FP32 pipe: thread c solves S x = e_c, i.e.
-// L z = e_{pos[c]} forward and U x = z backward (P^T e_c = e_{pos[c]}), into
-// column c of X.  S^-1 goes to the FP32 scratch that k_theta_rows_f32 reads.
-__global__ void __launch_bounds__(OV_T) k_overlap_lu(OverlapArgs a) {
-  extern __shared__ __align__(16) unsigned char ov_raw[];
-  __shared__ int pos[64];
-  const int w = blockIdx.x, N = a.N;
-  const bool live = !a.wt || walker_alive(a.wt, w);
-  double2* A = reinterpret_cast<double2*>(ov_raw);               // [N][N] L\U (float64)
-  float2* F = reinterpret_cast<float2*>(A + N * N);              // [N][N] L\U (FP32)
-  float2* X = F + N * N;                                         // [N][N] S^-1 (FP32)
-  const bool singular = overlap_core<double, true>(a, w, live, A, pos);
-  if (singular || !live) return;
-  for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x)
-    F[idx] = make_float2(f64_to_f32(A[idx].x), f64_to_f32(A[idx].y));
-  __syncthreads();
-  // (each sum in two interleaved partials: half the dependent chain)
-  const int c = threadIdx.x;
-  if (c < N) {
-    const int pc = pos[c];
-    for (int k = 0; k < N; ++k) {
-      float vr = k == pc ? 1.f : 0.f, vi = 0.f, wr = 0.f, wi = 0.f;
-      int m = pc;
-      for (; m + 1 < k; m += 2) {
-        const float2 l = F[k * N + m], x = X[m * N + c];
-        const float2 l1 = F[k * N + m + 1], x1 = X[(m + 1) * N + c];
-        vr = fmaf(-l.x, x.x, fmaf(l.y, x.y, vr));
-        vi = fmaf(-l.x, x.y, fmaf(-l.y, x.x, vi));
-        wr = fmaf(-l1.x, x1.x, fmaf(l1.y, x1.y, wr));
-        wi = fmaf(-l1.x, x1.y, fmaf(-l1.y, x1.x, wi));
-      }
-      if (m < k) {
-        const float2 l = F[k * N + m], x = X[m * N + c];
-        vr = fmaf(-l.x, x.x, fmaf(l.y, x.y, vr));
-        vi = fmaf(-l.x, x.y, fmaf(-l.y, x.x, vi));
-      }
-      X[k * N + c] = make_float2(vr + wr, vi + wi);
-    }
-    for (int k = N - 1; k >= 0; --k) {
-      float vr = X[k * N + c].x, vi = X[k * N + c].y, wr = 0.f, wi = 0.f;
-      int m = k + 1;
-      for (; m + 1 < N; m += 2) {
-        const float2 u = F[k * N + m], x = X[m * N + c];
-        const float2 u1 = F[k * N + m + 1], x1 = X[(m + 1) * N + c];
-        vr = fmaf(-u.x, x.x, fmaf(u.y, x.y, vr));
-        vi = fmaf(-u.x, x.y, fmaf(-u.y, x.x, vi));
-        wr = fmaf(-u1.x, x1.x, fmaf(u1.y, x1.y, wr));
-        wi = fmaf(-u1.x, x1.y, fmaf(-u1.y, x1.x, wi));
-      }
-      if (m < N) {
-        const float2 u = F[k * N + m], x = X[m * N + c];
-        vr = fmaf(-u.x, x.x, fmaf(u.y, x.y, vr));
-        vi = fmaf(-u.x, x.y, fmaf(-u.y, x.x, vi));
-      }
-      vr += wr;
-      vi += wi;
-      const float2 d = F[k * N + k];
-      const float den = d.x * d.x + d.y * d.y;
-      X[k * N + c] = make_float2((vr * d.x + vi * d.y) / den, (vi * d.x - vr * d.y) / den);
-    }
-  }
-  __syncthreads();
-  float2* si = a.Sinv32 + (long)w * N * N;
-  for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x) si[idx] = X[idx];
 }
 
 // Theta^T[i][p] = sum_j S^-1[j][i] Phi^T[j][p]: block (x, w) takes rows
@@ -718,17 +631,6 @@ static int launch_theta_rows(const OverlapArgs& a, cudaStream_t st) {
   AFQ_TRY(smem_attr_once(k_theta_rows<IB>, 100 * 1024, attr));
   dim3 grid(cdiv(a.M, TH_P), a.W);
   AFQ_LAUNCH(k_theta_rows<IB>, grid, TH_T, smem, st, a);
-  return AFQMC_OK;
-}
-
-int launch_overlap_lu(const OverlapArgs& a, cudaStream_t st) {
-  if (!a.Sinv32 || !a.unit_trial || a.N > kLuMaxN) {
-    set_error("overlap (LU): the unit trial, the FP32 S^-1 scratch and N <= %d are required",
-              kLuMaxN);
-    return AFQMC_EINVAL;
-  }
-  const size_t smem = 2ull * a.N * a.N * sizeof(double2);
-  AFQ_LAUNCH(k_overlap_lu, a.W, OV_T, smem, st, a);
   return AFQMC_OK;
 }
 
