@@ -105,7 +105,12 @@ struct JobTable {
 // stage feeds two M=128 MMAs against the same B tile (half the B traffic per
 // output), and when two such tiles do not fit in tensor memory a single
 // accumulator is used.
-template <int BN, int STAGES, bool TF32, class Epi, bool GROUPED>
+// MC (one contraction, CTA pairs): the two CTAs of a cluster take tiles 2u and
+// 2u + 1 of a row of tiles that share their B tile (gx even), and each loads
+// half of that B tile for both (TMA multicast): half the B bytes per CTA.  A
+// ring slot is refilled only when both CTAs' MMAs have released it (every
+// MMA commit arrives on both CTAs' empty barrier).
+template <int BN, int STAGES, bool TF32, class Epi, bool GROUPED, bool MC = false>
 __device__ __forceinline__ void gemm_body(const JobTable<Epi, GROUPED>& tab, int ntiles) {
   extern __shared__ uint8_t smem_raw[];
   constexpr int MT = Epi::kMT;
@@ -123,10 +128,14 @@ __device__ __forceinline__ void gemm_body(const JobTable<Epi, GROUPED>& tab, int
   constexpr int BK = BKB / ELEM;
   constexpr int KSTEPS = BKB / 32;
 
+  // tiles of this CTA: t0, t0 + tstep, ...
+  const uint32_t rank = MC ? cluster_rank() : 0u;
+  const int t0 = MC ? (int)(2 * cluster_id_x() + rank) : (int)blockIdx.x;
+  const int tstep = MC ? (int)(2 * cluster_count_x()) : (int)gridDim.x;
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 1);
+      mbar_init(&empty[s], MC ? 2 : 1);
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(&tfull[a], 1);
@@ -150,11 +159,14 @@ __device__ __forceinline__ void gemm_body(const JobTable<Epi, GROUPED>& tab, int
   fence_before();
   __syncthreads();
   fence_after();
+  // the peer's multicasts and commits target this CTA's barriers: both CTAs
+  // have initialised theirs past this point
+  if constexpr (MC) cluster_sync();
   const uint32_t tmem = *tmem_slot;
 
   if (warp == 0 && lane == 0) {
     int it = 0;
-    for (int t = blockIdx.x; t < ntiles && !*(volatile int*)abort_flag; t += gridDim.x) {
+    for (int t = t0; t < ntiles && !*(volatile int*)abort_flag; t += tstep) {
       const JobView<Epi> v = tab.at(t);
       const int lt = t - v.t0, bx = lt % v.gx, by = lt / v.gx;
       const int m0 = v.epi->m_origin(bx, by), n0 = v.epi->n_origin(bx, by);
@@ -169,7 +181,10 @@ __device__ __forceinline__ void gemm_body(const JobTable<Epi, GROUPED>& tab, int
         mbar_expect_tx(&full[s], S::STAGE);
         // A's K coordinate wraps when B carries a split operand ([hi | lo] K halves)
         tma_load_2d(a, v.tmA, &full[s], v.a_wrap ? (kb * BK) % v.a_wrap : kb * BK, m0);
-        if constexpr (Epi::kB3D)
+        if constexpr (MC)
+          tma_load_2d_mc(a + S::A_BYTES + rank * (BN / 2) * BKB, v.tmB, &full[s], kb * BK,
+                         n0 + (int)rank * (BN / 2), (uint16_t)3);
+        else if constexpr (Epi::kB3D)
           tma_load_3d(a + S::A_BYTES, v.tmB, &full[s], kb * BK, 0, v.epi->b_plane(bx, by));
         else
           tma_load_2d(a + S::A_BYTES, v.tmB, &full[s], kb * BK, n0);
@@ -178,7 +193,7 @@ __device__ __forceinline__ void gemm_body(const JobTable<Epi, GROUPED>& tab, int
   } else if (warp == 1 && lane == 0) {
     constexpr uint32_t idesc = instr_desc(TF32 ? 2u : 1u, (uint32_t)BN);
     int it = 0, j = 0;
-    for (int t = blockIdx.x; t < ntiles && !*(volatile int*)abort_flag; t += gridDim.x, ++j) {
+    for (int t = t0; t < ntiles && !*(volatile int*)abort_flag; t += tstep, ++j) {
       const JobView<Epi> v = tab.at(t);
       const int nk = (v.K + BK - 1) / BK;
       const int acc = NBUF == 2 ? (j & 1) : 0;
@@ -204,7 +219,10 @@ __device__ __forceinline__ void gemm_body(const JobTable<Epi, GROUPED>& tab, int
           for (int mt = 0; mt < MT; ++mt)
             mma<TF32>(d + (uint32_t)(mt * BN), sw128_desc(a + mt * BM * BKB + 32 * k),
                       sw128_desc(b + 32 * k), idesc, (kb > 0 || k > 0) ? 1u : 0u);
-        mma_commit(&empty[s]);
+        if constexpr (MC)
+          mma_commit_mc(&empty[s], (uint16_t)3);
+        else
+          mma_commit(&empty[s]);
       }
       mma_commit(&tfull[acc]);
       if (!ok) {
@@ -216,7 +234,7 @@ __device__ __forceinline__ void gemm_body(const JobTable<Epi, GROUPED>& tab, int
     const int q = warp & 3;
     float* esm = Epi::kSmemBytes ? reinterpret_cast<float*>(smem + S::RING + 256) : nullptr;
     int j = 0;
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++j) {
+    for (int t = t0; t < ntiles; t += tstep, ++j) {
       const JobView<Epi> v = tab.at(t);
       const int acc = NBUF == 2 ? (j & 1) : 0;
       bool bad = !mbar_wait(&tfull[acc], (j / NBUF) & 1, v.err, 14);
@@ -245,6 +263,8 @@ __device__ __forceinline__ void gemm_body(const JobTable<Epi, GROUPED>& tab, int
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                  "r"(TCOLS));
   }
+  // the peer's last commits arrive on this CTA's barriers: neither leaves first
+  if constexpr (MC) cluster_sync();
 }
 
 // One contraction, its tensor maps and epilogue as kernel parameters.
@@ -255,6 +275,16 @@ __global__ void __launch_bounds__(64 + 32 * Epi::kWarps, 1)
                          int ntiles, int a_wrap, const __grid_constant__ Epi epi, int* err) {
   const JobTable<Epi, false> tab{nullptr, 1, &tmA, &tmB, M, N, K, gx, a_wrap, err, &epi};
   gemm_body<BN, STAGES, TF32, Epi, false>(tab, ntiles);
+}
+
+// One contraction on CTA pairs sharing B tiles by multicast (cluster of 2).
+template <int BN, int STAGES, bool TF32, class Epi>
+__global__ void __launch_bounds__(64 + 32 * Epi::kWarps, 1)
+    k_tc_gemm_pairs(const __grid_constant__ CUtensorMap tmA,
+                    const __grid_constant__ CUtensorMap tmB, int M, int N, int K, int gx,
+                    int ntiles, int a_wrap, const __grid_constant__ Epi epi, int* err) {
+  const JobTable<Epi, false> tab{nullptr, 1, &tmA, &tmB, M, N, K, gx, a_wrap, err, &epi};
+  gemm_body<BN, STAGES, TF32, Epi, false, true>(tab, ntiles);
 }
 
 // Several contractions (of several independent states) in one persistent
@@ -1041,6 +1071,50 @@ static int launch_tc_persistent(const TcGemm& g, const Epi& epi, int gx, int gy,
   return AFQMC_OK;
 }
 
+// One contraction on CTA pairs (clusters of two, B tiles shared by TMA
+// multicast): gx and the tile count must be even; the grid is even.
+template <int BN, int STAGES, bool TF32, class Epi>
+static int launch_tc_pairs(const TcGemm& g, const Epi& epi, int gx, int gy, cudaStream_t st) {
+  constexpr int kTotal = tc::Smem<BN, STAGES, Epi::kMT>::TOTAL + Epi::kSmemBytes;
+  static_assert(kTotal <= 232448, "shared memory");
+  static_assert(!Epi::kB3D && BN % 16 == 0, "2-D B tiles, halves of whole swizzle atoms");
+  const long ntiles = (long)gx * gy;
+  if (ntiles <= 0) return AFQMC_OK;
+  if ((gx & 1) || ntiles > 0x7fffffffL) {
+    set_error("tc gemm (pairs): gx=%d must be even", gx);
+    return AFQMC_EINVAL;
+  }
+  const int eb = TF32 ? 4 : 2;
+  CUtensorMap ta, tb;
+  AFQ_TRY(make_tmap(&ta, g.A, eb, g.m, g.ka > 0 ? g.ka : g.k, g.lda, tc::BM * Epi::kMT));
+  AFQ_TRY(make_tmap(&tb, g.B, eb, g.n, g.k, g.ldb, BN / 2));
+  auto kern = tc::k_tc_gemm_pairs<BN, STAGES, TF32, Epi>;
+  static std::atomic<unsigned long long> attr{0};
+  AFQ_TRY(smem_attr_once(kern, kTotal, attr));
+  const int sms = tc_sm_count() & ~1;
+  const int grid = (int)(ntiles < sms ? ntiles : sms);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(64 + 32 * Epi::kWarps);
+  cfg.dynamicSmemBytes = kTotal;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 2;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, kern, ta, tb, g.m, g.n, g.k, gx, (int)ntiles,
+                                           g.a_wrap, epi, g.err);
+  ++g_launches;
+  if (e != cudaSuccess) {
+    set_error("launch k_tc_gemm_pairs: %s", cudaGetErrorString(e));
+    return AFQMC_ECUDA;
+  }
+  return AFQMC_OK;
+}
+
 // ---- plain-store contraction with an autotuned tile width --------------------
 // Candidates: BN = 256 (4 stages, one CTA per SM), 128 (3 stages) and 64
 // (4 stages), the last two small enough for two CTAs per SM.  tc_tune_store()
@@ -1169,6 +1243,12 @@ static int launch_v_bn(const TcGemm& g, void* V, int lo_kind, int W, int M, int 
   if (bn == 128) {
     if (g.tf32) return launch_tc_persistent<128, 4, true>(g, e, gx, gy, st);
     return launch_tc_persistent<128, 4, false>(g, e, gx, gy, st);
+  }
+  // BN = 256: CTA pairs share the Cholesky tile (every output row of tiles
+  // is gx = 2W / 256 tiles wide: pairs need gx even)
+  if (gx % 2 == 0) {
+    if (g.tf32) return launch_tc_pairs<256, 3, true>(g, e, gx, gy, st);
+    return launch_tc_pairs<256, 3, false>(g, e, gx, gy, st);
   }
   if (g.tf32) return launch_tc_persistent<256, 3, true>(g, e, gx, gy, st);
   return launch_tc_persistent<256, 3, false>(g, e, gx, gy, st);
