@@ -1175,16 +1175,20 @@ int tc_tune_store(const TcGemm& g, float* C, long ldc, float alpha, cudaStream_t
   float best_ms = 1e30f;
   for (int bn : {256, 128, 64}) {
     AFQ_TRY(launch_store_bn(g, C, ldc, alpha, bn, st));  // warm-up (and first-use set-up)
-    AFQ_CUDA(cudaEventRecord(e0, st));
-    AFQ_TRY(launch_store_bn(g, C, ldc, alpha, bn, st));
-    AFQ_TRY(launch_store_bn(g, C, ldc, alpha, bn, st));
-    AFQ_CUDA(cudaEventRecord(e1, st));
-    AFQ_CUDA(cudaEventSynchronize(e1));
-    float ms = 0.f;
-    AFQ_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-    if (ms < best_ms) {
-      best_ms = ms;
-      best = bn;
+    // the fastest of three timings of two launches: one slow timing (another
+    // kernel of the device, a clock step) must not decide the tile
+    for (int rep = 0; rep < 3; ++rep) {
+      AFQ_CUDA(cudaEventRecord(e0, st));
+      AFQ_TRY(launch_store_bn(g, C, ldc, alpha, bn, st));
+      AFQ_TRY(launch_store_bn(g, C, ldc, alpha, bn, st));
+      AFQ_CUDA(cudaEventRecord(e1, st));
+      AFQ_CUDA(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      AFQ_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = bn;
+      }
     }
   }
   cudaEventDestroy(e0);
@@ -1285,16 +1289,18 @@ int tc_tune_v(const TcGemm& g, void* V, int lo_kind, int W, int M, int Mp, doubl
   float best_ms = 1e30f;
   for (int bn : {128, 256}) {
     AFQ_TRY(launch_v_bn(g, V, lo_kind, W, M, Mp, sdt, bn, st));  // warm-up
-    AFQ_CUDA(cudaEventRecord(e0, st));
-    AFQ_TRY(launch_v_bn(g, V, lo_kind, W, M, Mp, sdt, bn, st));
-    AFQ_TRY(launch_v_bn(g, V, lo_kind, W, M, Mp, sdt, bn, st));
-    AFQ_CUDA(cudaEventRecord(e1, st));
-    AFQ_CUDA(cudaEventSynchronize(e1));
-    float ms = 0.f;
-    AFQ_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-    if (ms < best_ms) {
-      best_ms = ms;
-      best = bn;
+    for (int rep = 0; rep < 3; ++rep) {  // the fastest of three timings
+      AFQ_CUDA(cudaEventRecord(e0, st));
+      AFQ_TRY(launch_v_bn(g, V, lo_kind, W, M, Mp, sdt, bn, st));
+      AFQ_TRY(launch_v_bn(g, V, lo_kind, W, M, Mp, sdt, bn, st));
+      AFQ_CUDA(cudaEventRecord(e1, st));
+      AFQ_CUDA(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      AFQ_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = bn;
+      }
     }
   }
   cudaEventDestroy(e0);
@@ -1531,16 +1537,24 @@ int tc_grouped_tune(const TcJobDesc* d, int n, cudaStream_t st, TcGrouped** out)
     TcGrouped* gr = nullptr;
     r = tc_grouped_create(d, n, bn, &gr);
     if (r != AFQMC_OK) break;
-    float ms = 0.f;
+    float ms = 1e30f;
     r = tc_grouped_launch(gr, st);  // warm-up (and first-use set-up)
-    if (r == AFQMC_OK && cudaEventRecord(e0, st) == cudaSuccess) {
+    // the fastest of three timings of two launches
+    for (int trial = 0; trial < 3 && r == AFQMC_OK; ++trial) {
+      float t = 0.f;
+      if (cudaEventRecord(e0, st) != cudaSuccess) {
+        set_error("grouped tune: event timing failed");
+        r = AFQMC_ECUDA;
+        break;
+      }
       for (int rep = 0; rep < 2 && r == AFQMC_OK; ++rep) r = tc_grouped_launch(gr, st);
       if (r == AFQMC_OK && (cudaEventRecord(e1, st) != cudaSuccess ||
                             cudaEventSynchronize(e1) != cudaSuccess ||
-                            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)) {
+                            cudaEventElapsedTime(&t, e0, e1) != cudaSuccess)) {
         set_error("grouped tune: event timing failed");
         r = AFQMC_ECUDA;
       }
+      if (t < ms) ms = t;
     }
     if (r != AFQMC_OK) {
       tc_grouped_destroy(gr);

@@ -56,11 +56,13 @@ def test_trial_energy_mixed_vs_fp64(pkg, prec, tol):
 
 
 @pytest.mark.parametrize("prec,tol_phi,tol_e", [(2, 3e-2, 5e-3), (1, 5e-3, 5e-4)])
-@pytest.mark.parametrize("nwalkers", [32, 200])
+@pytest.mark.parametrize("nwalkers", [32, 200, 400, 520])
 def test_one_step_mixed_vs_fp64(pkg, prec, tol_phi, tol_e, nwalkers):
     """One full step of the 12-orbital workload on identical Philox fields;
     200 walkers put field rows in both halves of a 256-row V tile and in a
-    ragged last tile."""
+    ragged last tile.  With an even number of 256-row V tiles (200, 400
+    walkers) the V contraction runs on CTA pairs sharing the Cholesky tile by
+    multicast, with an odd number (32, 520) on single CTAs."""
     w = workloads.config("c0")
     r = runs(pkg, w, [0, prec], nwalkers=nwalkers, energy_period=1)
     for x in r.values():
