@@ -106,7 +106,7 @@ TRAFFIC = {
     # the V contraction at the tile width the set-up chooses at M=300 (BN = 256,
     # on CTA pairs)
     "v_assembly": {"bytes": (190.053376 + 146.681344) * 1e6, "precisions": ("bf16", "bf16-f32lu", "bf16-f64theta"),
-                   "function": [GEMM_KERNEL, "struct EpiV {"],
+                   "function": [GEMM_KERNEL, "struct EpiVT {"],
                    "sha": "a28af4f74addb34ab6966d2ac63a1913a2bec47f48a3e4f70ee6511a021b6e86"},
     "energy": {"bytes": (42.981120 + 0.896512) * 1e6, "precisions": ("bf16", "bf16-f32lu", "bf16-f64theta"),
                "function": [GEMM_KERNEL, "struct EpiExchange {"],

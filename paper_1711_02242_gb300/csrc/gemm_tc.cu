@@ -732,11 +732,15 @@ struct EpiTaylor {
 // of the full Cholesky vectors; Re V = -sqrt(dt) (Im x . L) and Im V =
 // sqrt(dt) (Re x . L) land in row (w, p) of [Re V | Im V] at column q or
 // Mp + q, 16 consecutive q per thread (pad columns come out zero).
-struct EpiV {
+// MT_ = 2: 256-row tiles (each Cholesky tile serves 128 walkers, one
+// 512-column accumulator at BN = 256); MT_ = 1: 128-row tiles (two 256-column
+// accumulators at BN = 256: the epilogue overlaps the next tile's MMAs).
+template <int MT_>
+struct EpiVT {
   static constexpr int kSmemBytes = 0;
   static constexpr bool kB3D = false;  // B tile = one 2-D box at row n_origin
   static constexpr int kWarps = 8;      // epilogue warps: two per TMEM lane quarter
-  static constexpr int kMT = 2;         // 256-row tiles: each Cholesky tile serves 128 walkers
+  static constexpr int kMT = MT_;
   void* V;
   int lo_kind, W, M, Mp;
   float sdt;
@@ -805,6 +809,8 @@ struct EpiV {
     }
   }
 };
+using EpiV = EpiVT<2>;
+using EpiV1 = EpiVT<1>;
 
 // Last half step: rows (w,c,i) of the series sum, columns p; the product is
 // stored as the new float64 orbitals of live walkers.  Chunks of 16 columns go
@@ -1238,10 +1244,25 @@ int tc_taylor_term(const TcGemm& g, float* S, long lds, bool first, void* tb_out
   return launch_tc_persistent<BN, 6, false>(g, e, cdiv(M, BN), W, st);
 }
 
-// V with tile width 128 (half blocks, double-buffered accumulators) or 256.
+// V in one of three forms, chosen at set-up by timing: tile width 128 (half
+// blocks, double-buffered accumulators, 256-row tiles), 256 on 256-row tiles
+// (one accumulator; CTA pairs when the tile rows pair up), or kV256Pairs128:
+// 256 on 128-row tiles on CTA pairs (double-buffered accumulators, the
+// Cholesky tile shared by the pair).
+constexpr int kV256Pairs128 = 257;
 static int launch_v_bn(const TcGemm& g, void* V, int lo_kind, int W, int M, int Mp, double sdt,
                        int bn, cudaStream_t st) {
   const int nb = Mp / 16;
+  if (bn == kV256Pairs128) {
+    tc::EpiV1 e1{V, lo_kind, W, M, Mp, (float)sdt, 256};
+    const int gx1 = cdiv(g.m, tc::BM), gy1 = nb * (nb + 1) / 2;
+    if (gx1 % 2) {
+      set_error("tc V: 128-row tiles on CTA pairs need an even number of them (%d)", gx1);
+      return AFQMC_EINVAL;
+    }
+    if (g.tf32) return launch_tc_pairs<256, 4, true>(g, e1, gx1, gy1, st);
+    return launch_tc_pairs<256, 4, false>(g, e1, gx1, gy1, st);
+  }
   tc::EpiV e{V, lo_kind, W, M, Mp, (float)sdt, bn};
   const int gx = cdiv(g.m, tc::BM * tc::EpiV::kMT), gy = nb * (nb + 1) / 2 * (256 / bn);
   if (bn == 128) {
@@ -1287,7 +1308,9 @@ int tc_tune_v(const TcGemm& g, void* V, int lo_kind, int W, int M, int Mp, doubl
   AFQ_CUDA(cudaEventCreate(&e1));
   int best = 128;
   float best_ms = 1e30f;
-  for (int bn : {128, 256}) {
+  std::vector<int> forms = {128, 256};
+  if (cdiv(g.m, tc::BM) % 2 == 0) forms.push_back(kV256Pairs128);
+  for (int bn : forms) {
     AFQ_TRY(launch_v_bn(g, V, lo_kind, W, M, Mp, sdt, bn, st));  // warm-up
     for (int rep = 0; rep < 3; ++rep) {  // the fastest of three timings
       AFQ_CUDA(cudaEventRecord(e0, st));
@@ -1309,7 +1332,7 @@ int tc_tune_v(const TcGemm& g, void* V, int lo_kind, int W, int M, int Mp, doubl
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tuned_bn_v[ShapeKey{g.m, g.n, g.k, g.tf32}] = best;
   }
-  if (chosen) *chosen = best;
+  if (chosen) *chosen = best == kV256Pairs128 ? 256 : best;
   return AFQMC_OK;
 }
 
