@@ -30,7 +30,7 @@
 // and its rows share their position within the 8-row swizzle atoms, so each
 // thread computes the swizzled offsets of its two K columns (p and Mp + p)
 // once per tile and a store costs one add.  Warp roles: warp 0 TMA producer,
-// warp 1 TMEM allocation and the MMA thread, warps 2-9 epilogue (two warps
+// warp 1 TMEM allocation and the MMA thread, warps 2-17 epilogue (four warps
 // per 32-lane quarter of TMEM, splitting the chunks).  Every wait is bounded;
 // on time-out the kernel records an error and stops.
 #include <cuda_bf16.h>
@@ -43,7 +43,7 @@ namespace afq {
 namespace tc {
 
 constexpr int kVBox = BM * BKB;   // one V box: a 128-row p-tile x 128 bytes of K
-constexpr int kEpiWarps = 8;      // epilogue warps (2 per TMEM lane quarter)
+constexpr int kEpiWarps = 16;     // epilogue warps (4 per TMEM lane quarter)
 constexpr int kEpiThreads = 32 * kEpiWarps;
 constexpr int kSeriesThreads = 64 + kEpiThreads;
 
@@ -218,7 +218,7 @@ __global__ void __launch_bounds__(kSeriesThreads, 1)
     if (stop) *abort_flag = 1;
   } else if (warp >= 2) {
     // epilogue: warp quarter q holds TMEM lanes (p within the tile) 32q .. 32q + 31;
-    // the two warps of a quarter take alternate 16-column chunks
+    // the four warps of a quarter take every fourth 16-column chunk
     const int q = warp & 3, half = (warp - 2) >> 2;
     const uint32_t tl = tmem + ((uint32_t)(32 * q) << 16);
     const uint32_t soff = (uint32_t)(a.ptiles * a.nb);  // columns of the running sum
@@ -244,7 +244,7 @@ __global__ void __launch_bounds__(kSeriesThreads, 1)
           column_offsets<TF32>(p, opk, offp);
           column_offsets<TF32>(a.Mp + p, opk, offq);
 #pragma unroll 1
-          for (int ch = half; ch < nchunk; ch += 2) {
+          for (int ch = half; ch < nchunk; ch += kEpiWarps / 4) {
             const int c0 = ch * 16;
             const int cpart = c0 >= NH ? 1 : 0, i0 = c0 - cpart * NH;
             if (i0 >= N) continue;  // a chunk of padding rows only
