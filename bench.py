@@ -198,6 +198,21 @@ def max_over_ranks(value: float, device="cpu") -> float:
     return float(t.item())
 
 
+L2_BYTES = 129e6  # GB300 L2
+
+
+def l2_note(w: workloads.Workload) -> str:
+    """How the timed steps stand against L2: the packed Cholesky vectors and the
+    walkers' orbitals are read every step; no flush between steps."""
+    L_bytes = w.M * (w.M + 1) // 2 * w.nchol * 8
+    phi_bytes = w.nwalkers * 2 * w.N * w.M * 8
+    if L_bytes > L2_BYTES:
+        return f"inputs larger than L2 (packed L {L_bytes / 1e6:.0f} MB float64)"
+    size = lambda n: f"{n / 1e6:.1f} MB" if n >= 1e6 else f"{n / 1e3:.0f} KB"  # noqa: E731
+    return (f"inputs fit in L2 (packed L {size(L_bytes)}, orbitals {size(phi_bytes)} float64): "
+            "L2-resident steps, no flush")
+
+
 def job_throughput(walkers_per_rank: int, steps: int, ms_max: float, world: int) -> float:
     """Walker-steps of all ranks per second of the slowest rank."""
     return world * walkers_per_rank * steps / (ms_max * 1e-3)
@@ -1550,8 +1565,7 @@ def main():
                    "parallelism": (f"one population sharded over {N} GPUs ({w.nwalkers} "
                                    f"walkers each; comb every {r['pc_period'] or 'never'}, "
                                    "estimator summed over ranks)" if r["sharded"] else "1 GPU"),
-                   "precision": args.precision, "l2": "inputs larger than L2 (packed L "
-                   f"{w.M * (w.M + 1) // 2 * w.nchol * 8 / 1e6:.0f} MB float64)",
+                   "precision": args.precision, "l2": l2_note(w),
                    "trial": f"RHF (25 iterations, converged={r['trial_converged']}, "
                             f"|FD-DF|={r['trial_grad']:.2e})"},
         "roofline": roof,
