@@ -54,6 +54,17 @@ def test_job_throughput_counts_all_ranks():
     assert bench.max_over_ranks(7.5) == 7.5  # no process group: local value
 
 
+def test_l2_note_states_whether_the_inputs_fit_in_l2():
+    """The bench line says whether a step's inputs exceed the 129 MB L2 (no
+    flush between steps is needed then) or are L2-resident."""
+    import bench
+    import workloads
+
+    assert bench.l2_note(workloads.config("c2")).startswith("inputs larger than L2 (packed L 650 MB")
+    for c in ("c0", "c1"):
+        assert bench.l2_note(workloads.config(c)).startswith("inputs fit in L2")
+
+
 def test_rooflines_from_phase_times():
     """Per-phase roofline entries: algorithmic work / time per launch, the
     dominant phase first, and a traffic figure only while its source matches."""
