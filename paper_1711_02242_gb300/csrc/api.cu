@@ -1308,6 +1308,9 @@ static int init_state(const afqmc_params* p, const double* h1, const double* L,
   s->sdt = std::sqrt(p->dt);
   int r = setup_device(s, h1, L, trial, trial_dn, md_coef, md_up, md_dn);
   if (r != AFQMC_OK) {
+    // work enqueued before the failing call still runs in the caller's
+    // workspace: let it finish before the caller may free that memory
+    cudaStreamSynchronize(s->st);
     delete s;
     return r;
   }
